@@ -1,0 +1,1036 @@
+/*
+ * ORACLE -- test infrastructure only.  Only tests/, __graft_entry__.smoke()
+ * and the cpu_baseline leg of bench.py may load this code.  It shares no
+ * code, header, table or constant generator with the CUDA library.
+ *
+ * Brute-force kernel statistics by literal enumeration of the loop domain
+ * (Section "Gathering Kernel Statistics", Algorithm 1 and Algorithm 2), plus
+ * plain reference outputs of every kernel (FP64 sums, or bit-exact FP32/FP64
+ * replays where the kernel's operation order is fixed by its definition).
+ *
+ * How a kernel is described here: a walker function literally executes the
+ * kernel's loop nest for ONE work-item (group id g[3], local id l[3]) and
+ * reports each executed statement instance via X(ctx, stmt, loopvars) and
+ * each barrier via BAR(ctx).  Each statement lists its floating point
+ * operations and its memory access sites; each site has an index function of
+ * (g, l, loopvars).  From these the enumerator computes:
+ *   - per statement: sub-group (SG) instance counts, i.e. how many distinct
+ *     (statement, loop-variable) instances the 32 lanes of a sub-group execute
+ *     (on-chip work is counted per SG, Section "Gathering Kernel Statistics");
+ *   - per access site: work-item (WI) access count, SG count, local/global
+ *     strides as finite differences of the index along each thread axis
+ *     (checked constant over the whole domain = affinity check), the stride
+ *     along the innermost enclosing sequential loop (Table "ab_pattern"), and
+ *     the footprint = number of distinct indices touched (Algorithm 2, applied
+ *     per access site);
+ *   - barriers encountered by a single work-item (Section "Gathering Kernel
+ *     Statistics", barrier counting), work-group count, one kernel launch.
+ * Sub-groups are lanes 32q..32q+31 of the linear id lid0 + L0*lid1 + L0*L1*lid2.
+ *
+ * Every function in this file is pinned by tests in tests/test_oracle_*.py
+ * against closed forms and values the paper fixes.
+ */
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+#include <math.h>
+#include <stdio.h>
+
+#define MAXSITE 24
+#define MAXSTMT 24
+#define MAXLOOP 3
+#define SGSIZE 32
+
+enum { MEM_GLOBAL = 0, MEM_LOCAL = 1 };
+enum { DIR_LOAD = 0, DIR_STORE = 1 };
+enum { DT_F32 = 0, DT_F64 = 1 };
+
+typedef struct ctx ctx;
+typedef long long (*idx_fn)(const ctx *c, const long long *g, const long long *l, const long long *lv);
+
+typedef struct {
+    char tag[24];
+    int mem, dir, dsize;
+    char dtype[16];
+    idx_fn idx;
+} site_t;
+
+typedef struct {
+    int nloop;
+    int n_add, n_mul, n_madd;   /* scalar floating point ops per instance */
+    int dt;                     /* DT_F32 / DT_F64 */
+    int nsite;
+    int site[8];
+} stmt_t;
+
+/* open-addressing set of non-negative 64-bit keys (-1 = empty) */
+typedef struct {
+    long long *k;
+    size_t cap, n;
+} kset;
+
+static void ks_init(kset *s, size_t cap) {
+    s->cap = cap; s->n = 0;
+    s->k = (long long *)malloc(cap * sizeof(long long));
+    for (size_t i = 0; i < cap; i++) s->k[i] = -1;
+}
+static void ks_free(kset *s) { free(s->k); s->k = NULL; s->cap = s->n = 0; }
+static void ks_clear(kset *s) { for (size_t i = 0; i < s->cap; i++) s->k[i] = -1; s->n = 0; }
+static size_t ks_hash(long long x) {
+    unsigned long long z = (unsigned long long)x + 0x9E3779B97F4A7C15ULL;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ULL;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBULL;
+    return (size_t)(z ^ (z >> 31));
+}
+static int ks_insert(kset *s, long long key);
+static void ks_grow(kset *s) {
+    kset t; ks_init(&t, s->cap * 2);
+    for (size_t i = 0; i < s->cap; i++) if (s->k[i] >= 0) ks_insert(&t, s->k[i]);
+    free(s->k); *s = t;
+}
+/* returns 1 if newly inserted */
+static int ks_insert(kset *s, long long key) {
+    if ((s->n + 1) * 2 > s->cap) ks_grow(s);
+    size_t m = s->cap - 1, h = ks_hash(key) & m;
+    while (s->k[h] >= 0) {
+        if (s->k[h] == key) return 0;
+        h = (h + 1) & m;
+    }
+    s->k[h] = key; s->n++;
+    return 1;
+}
+
+typedef struct {
+    unsigned long long wi, sg;
+    kset foot;
+    long long lstr[3], gstr[3], loopstr;
+    int have_str, affine, have_loop;
+} site_stat;
+
+struct ctx {
+    long long P[8];          /* kernel parameters (meaning per kernel) */
+    long long D[8];          /* derived constants */
+    long long grid[3], wg[3];
+    int nsite, nstmt;
+    site_t site[MAXSITE];
+    stmt_t stmt[MAXSTMT];
+    void (*walk)(ctx *c);
+    /* current work-item */
+    long long g[3], l[3];
+    /* accumulators */
+    site_stat ss[MAXSITE];
+    unsigned long long op_wi[2][3], op_sg[2][3];  /* [dtype][add,mul,madd] */
+    unsigned long long stmt_sg[MAXSTMT], stmt_wi[MAXSTMT];
+    long long bar_cur, bar_min, bar_max;
+    kset sgset;              /* distinct statement instances of the current SG */
+    int err;
+};
+
+static int add_site(ctx *c, const char *tag, int mem, int dir, const char *dtype, int dsize, idx_fn f) {
+    site_t *s = &c->site[c->nsite];
+    memset(s, 0, sizeof *s);
+    strncpy(s->tag, tag, sizeof s->tag - 1);
+    strncpy(s->dtype, dtype, sizeof s->dtype - 1);
+    s->mem = mem; s->dir = dir; s->dsize = dsize; s->idx = f;
+    return c->nsite++;
+}
+static int add_stmt(ctx *c, int nloop, int dt, int nadd, int nmul, int nmadd) {
+    stmt_t *s = &c->stmt[c->nstmt];
+    memset(s, 0, sizeof *s);
+    s->nloop = nloop; s->dt = dt; s->n_add = nadd; s->n_mul = nmul; s->n_madd = nmadd;
+    return c->nstmt++;
+}
+static void stmt_site(ctx *c, int st, int site) { stmt_t *s = &c->stmt[st]; s->site[s->nsite++] = site; }
+
+/* one executed statement instance of the current work-item */
+static void X(ctx *c, int st, const long long *lv) {
+    const stmt_t *S = &c->stmt[st];
+    long long key = st;
+    for (int i = 0; i < S->nloop; i++) {
+        if (lv[i] < 0 || lv[i] >= (1LL << 19)) { c->err = 1; return; }
+        key = key | (lv[i] << (6 + 19 * i));
+    }
+    int fresh = ks_insert(&c->sgset, key);
+    c->stmt_wi[st]++;
+    c->op_wi[S->dt][0] += S->n_add; c->op_wi[S->dt][1] += S->n_mul; c->op_wi[S->dt][2] += S->n_madd;
+    if (fresh) {
+        c->stmt_sg[st]++;
+        c->op_sg[S->dt][0] += S->n_add; c->op_sg[S->dt][1] += S->n_mul; c->op_sg[S->dt][2] += S->n_madd;
+    }
+    for (int a = 0; a < S->nsite; a++) {
+        int si = S->site[a];
+        site_stat *t = &c->ss[si];
+        idx_fn f = c->site[si].idx;
+        long long base = f(c, c->g, c->l, lv);
+        if (base < 0) { c->err = 2; return; }
+        t->wi++;
+        if (fresh) t->sg++;
+        ks_insert(&t->foot, base);
+        long long ls[3], gs[3], lps = 0;
+        for (int ax = 0; ax < 3; ax++) {
+            long long l2[3] = {c->l[0], c->l[1], c->l[2]};
+            long long g2[3] = {c->g[0], c->g[1], c->g[2]};
+            l2[ax] += 1; g2[ax] += 1;
+            ls[ax] = f(c, c->g, l2, lv) - base;
+            gs[ax] = f(c, g2, c->l, lv) - base;
+        }
+        if (S->nloop > 0) {
+            long long lv2[MAXLOOP];
+            for (int i = 0; i < S->nloop; i++) lv2[i] = lv[i];
+            lv2[S->nloop - 1] += 1;
+            lps = f(c, c->g, c->l, lv2) - base;
+        }
+        if (!t->have_str) {
+            for (int ax = 0; ax < 3; ax++) { t->lstr[ax] = ls[ax]; t->gstr[ax] = gs[ax]; }
+            t->loopstr = lps; t->have_loop = S->nloop > 0;
+            t->have_str = 1; t->affine = 1;
+        } else {
+            for (int ax = 0; ax < 3; ax++)
+                if (t->lstr[ax] != ls[ax] || t->gstr[ax] != gs[ax]) t->affine = 0;
+            if (t->loopstr != lps) t->affine = 0;
+        }
+    }
+}
+static void BAR(ctx *c) { c->bar_cur++; }
+
+/* ---------------------------------------------------------------- helpers */
+#define G0 (g[0])
+#define G1 (g[1])
+#define L0_ (l[0])
+#define L1_ (l[1])
+static long long cdiv(long long a, long long b) { return (a + b - 1) / b; }
+
+/* ======================================================================
+ * Calibration suite (Section "Measurement Kernel Design")
+ * ====================================================================== */
+
+/* stream: result[pattern] = sum_{a<L} in_a[pattern]   (global memory access
+ * measurement kernel, AFR 1).  P = {dtype, vec, N, s, L, shape, W}.
+ * vec: 0 scalar, 1 16-byte vectors (float32x4 / float64x2).
+ * shape 0: 1-D work-group of 256, index = s*lid0 + gid0 + 256*s*gid1,
+ *          grid (s, M/(256 s)), M = N/w vectors.
+ * shape 1: 16x16 work-group over a row-major M/W x W array:
+ *          index = lid0 + W*lid1 + 16*gid0 + 16*W*gid1, grid (W/16, M/(16W)). */
+static long long ix_stream(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)lv;
+    if (c->P[5] == 0) { long long s = c->P[3]; return s * L0_ + G0 + 256 * s * G1; }
+    long long W = c->P[6];
+    return L0_ + W * L1_ + 16 * G0 + 16 * W * G1;
+}
+static void walk_stream(ctx *c) { X(c, 0, NULL); }
+static int setup_stream(ctx *c) {
+    long long dt = c->P[0], vec = c->P[1], N = c->P[2], s = c->P[3], L = c->P[4], shape = c->P[5], W = c->P[6];
+    if (dt < 0 || dt > 1 || vec < 0 || vec > 1 || L < 1 || L > 4 || N <= 0) return -1;
+    long long w = vec ? (dt == DT_F32 ? 4 : 2) : 1;
+    if (N % w) return -1;
+    long long M = N / w;
+    const char *dn = dt == DT_F32 ? (vec ? "float32x4" : "float32") : (vec ? "float64x2" : "float64");
+    int ds = vec ? 16 : (dt == DT_F32 ? 4 : 8);
+    if (shape == 0) {
+        if (s < 1 || M % (256 * s)) return -1;
+        c->grid[0] = s; c->grid[1] = M / (256 * s); c->grid[2] = 1;
+        c->wg[0] = 256; c->wg[1] = 1; c->wg[2] = 1;
+    } else if (shape == 1) {
+        if (W < 16 || W % 16 || M % (16 * W)) return -1;
+        c->grid[0] = W / 16; c->grid[1] = M / (16 * W); c->grid[2] = 1;
+        c->wg[0] = 16; c->wg[1] = 16; c->wg[2] = 1;
+    } else return -1;
+    int st = add_stmt(c, 0, (int)dt, (int)((L - 1) * w), 0, 0);
+    static const char *nm[4] = {"in0", "in1", "in2", "in3"};
+    for (int a = 0; a < L; a++) stmt_site(c, st, add_site(c, nm[a], MEM_GLOBAL, DIR_LOAD, dn, ds, ix_stream));
+    stmt_site(c, st, add_site(c, "out", MEM_GLOBAL, DIR_STORE, dn, ds, ix_stream));
+    c->walk = walk_stream;
+    return 0;
+}
+
+/* arithmetic kernel: 32 private variables per work-item, each updated F/32
+ * times with the target operation; no update reads a variable written by the
+ * four most recent updates (each variable only reads itself).  P = {dtype, op, F, G}
+ * op 0 add, 1 mul, 2 madd.  Work-group 256, G groups. */
+static long long ix_lin(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)c; (void)lv; return 256 * G0 + L0_;
+}
+static void walk_fma(ctx *c) {
+    long long lv[2];
+    X(c, 0, NULL);                                       /* u = seed[gtid] */
+    for (lv[0] = 0; lv[0] < 32; lv[0]++) X(c, 1, lv);    /* x_t = u + c_t */
+    long long R = c->P[2] / 32;
+    for (lv[0] = 0; lv[0] < R; lv[0]++)
+        for (lv[1] = 0; lv[1] < 32; lv[1]++) X(c, 2, lv); /* x_t = op(x_t) */
+    for (lv[0] = 1; lv[0] < 32; lv[0]++) X(c, 3, lv);    /* s = s + x_t */
+    X(c, 4, NULL);                                       /* out[gtid] = s */
+}
+static int setup_fma(ctx *c) {
+    long long dt = c->P[0], op = c->P[1], F = c->P[2], G = c->P[3];
+    if (dt < 0 || dt > 1 || op < 0 || op > 2 || F < 32 || F % 32 || G < 1) return -1;
+    const char *dn = dt == DT_F32 ? "float32" : "float64";
+    int ds = dt == DT_F32 ? 4 : 8;
+    c->grid[0] = G; c->grid[1] = 1; c->grid[2] = 1;
+    c->wg[0] = 256; c->wg[1] = 1; c->wg[2] = 1;
+    int s0 = add_stmt(c, 0, (int)dt, 0, 0, 0);
+    stmt_site(c, s0, add_site(c, "seed", MEM_GLOBAL, DIR_LOAD, dn, ds, ix_lin));
+    add_stmt(c, 1, (int)dt, 1, 0, 0);
+    add_stmt(c, 2, (int)dt, op == 0, op == 1, op == 2);
+    add_stmt(c, 1, (int)dt, 1, 0, 0);
+    int s4 = add_stmt(c, 0, (int)dt, 0, 0, 0);
+    stmt_site(c, s4, add_site(c, "out", MEM_GLOBAL, DIR_STORE, dn, ds, ix_lin));
+    c->walk = walk_fma;
+    return 0;
+}
+
+/* local memory shuffle kernel.  P = {R, sync, G}.  Each work-item stores one
+ * element into a 512-element local array, passes a barrier, then moves its
+ * element between slot lid0 and slot 256+lid0 R/2 times (R local accesses in
+ * the loop, 4 per iteration), optionally with a barrier per iteration, and
+ * finally writes the element to global memory. */
+static long long ix_lA(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)c; (void)g; (void)lv; return L0_;
+}
+static long long ix_lB(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)c; (void)g; (void)lv; return 256 + L0_;
+}
+static void walk_smem(ctx *c) {
+    long long lv[1];
+    X(c, 0, NULL);          /* v = in[gtid] ; s[lid0] = v */
+    BAR(c);
+    for (lv[0] = 0; lv[0] < c->P[0] / 4; lv[0]++) {
+        X(c, 1, lv);        /* s[256+lid0] = s[lid0] */
+        X(c, 2, lv);        /* s[lid0] = s[256+lid0] */
+        if (c->P[1]) BAR(c);
+    }
+    X(c, 3, NULL);          /* out[gtid] = s[lid0] */
+}
+static int setup_smem(ctx *c) {
+    long long R = c->P[0], sync = c->P[1], G = c->P[2];
+    if (R < 4 || R % 4 || sync < 0 || sync > 1 || G < 1) return -1;
+    c->grid[0] = G; c->grid[1] = 1; c->grid[2] = 1;
+    c->wg[0] = 256; c->wg[1] = 1; c->wg[2] = 1;
+    int s0 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+    stmt_site(c, s0, add_site(c, "in", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_lin));
+    stmt_site(c, s0, add_site(c, "s_init", MEM_LOCAL, DIR_STORE, "float32", 4, ix_lA));
+    int s1 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+    stmt_site(c, s1, add_site(c, "s_ldA", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_lA));
+    stmt_site(c, s1, add_site(c, "s_stB", MEM_LOCAL, DIR_STORE, "float32", 4, ix_lB));
+    int s2 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+    stmt_site(c, s2, add_site(c, "s_ldB", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_lB));
+    stmt_site(c, s2, add_site(c, "s_stA", MEM_LOCAL, DIR_STORE, "float32", 4, ix_lA));
+    int s3 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+    stmt_site(c, s3, add_site(c, "s_fin", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_lA));
+    stmt_site(c, s3, add_site(c, "out", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_lin));
+    c->walk = walk_smem;
+    return 0;
+}
+
+/* local barrier kernel.  P = {B, G}: v = in[gtid]; B barriers; out[gtid] = v. */
+static void walk_barrier(ctx *c) {
+    X(c, 0, NULL);
+    for (long long b = 0; b < c->P[0]; b++) BAR(c);
+    X(c, 1, NULL);
+}
+static int setup_barrier(ctx *c) {
+    long long B = c->P[0], G = c->P[1];
+    if (B < 0 || G < 1) return -1;
+    c->grid[0] = G; c->grid[1] = 1; c->grid[2] = 1;
+    c->wg[0] = 256; c->wg[1] = 1; c->wg[2] = 1;
+    int s0 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+    stmt_site(c, s0, add_site(c, "in", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_lin));
+    int s1 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+    stmt_site(c, s1, add_site(c, "out", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_lin));
+    c->walk = walk_barrier;
+    return 0;
+}
+
+/* local/global overlap kernel (Section "Modeling Operation Overlap"):
+ * one global load, m local store-load pairs, one global store.  P = {m, N}. */
+static void walk_overlap(ctx *c) {
+    long long lv[1];
+    X(c, 0, NULL);
+    for (lv[0] = 0; lv[0] < c->P[0]; lv[0]++) { X(c, 1, lv); X(c, 2, lv); }
+    X(c, 3, NULL);
+}
+static int setup_overlap(ctx *c) {
+    long long m = c->P[0], N = c->P[1];
+    if (m < 0 || N < 256 || N % 256) return -1;
+    c->grid[0] = N / 256; c->grid[1] = 1; c->grid[2] = 1;
+    c->wg[0] = 256; c->wg[1] = 1; c->wg[2] = 1;
+    int s0 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+    stmt_site(c, s0, add_site(c, "in", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_lin));
+    int s1 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+    stmt_site(c, s1, add_site(c, "s_st", MEM_LOCAL, DIR_STORE, "float32", 4, ix_lA));
+    int s2 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+    stmt_site(c, s2, add_site(c, "s_ld", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_lA));
+    int s3 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+    stmt_site(c, s3, add_site(c, "out", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_lin));
+    c->walk = walk_overlap;
+    return 0;
+}
+
+/* empty kernel: G work-groups of 256 with no instructions.  P = {G}. */
+static void walk_empty(ctx *c) { (void)c; }
+static int setup_empty(ctx *c) {
+    if (c->P[0] < 1) return -1;
+    c->grid[0] = c->P[0]; c->grid[1] = 1; c->grid[2] = 1;
+    c->wg[0] = 256; c->wg[1] = 1; c->wg[2] = 1;
+    c->walk = walk_empty;
+    return 0;
+}
+
+/* ======================================================================
+ * Matrix multiplication (Sections "Illustrative Example", "Matrix
+ * Multiplication"), C = A B, n x n fp32 row-major, 16x16 work-groups,
+ * gid0 -> column tile, gid1 -> row tile.  P = {n}.
+ * ====================================================================== */
+static long long ix_mm_a_pf(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long n = c->P[0]; return n * (16 * G1 + L1_) + 16 * lv[0] + L0_;
+}
+static long long ix_mm_b_pf(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long n = c->P[0]; return n * (16 * lv[0] + L1_) + 16 * G0 + L0_;
+}
+static long long ix_mm_tile_st(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)c; (void)g; (void)lv; return 16 * L1_ + L0_;
+}
+static long long ix_mm_af_ld(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)c; (void)g; return 16 * L1_ + lv[1];
+}
+static long long ix_mm_bf_ld(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)c; (void)g; return 16 * lv[1] + L0_;
+}
+static long long ix_mm_c(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)lv; long long n = c->P[0]; return n * (16 * G1 + L1_) + 16 * G0 + L0_;
+}
+static long long ix_mm_a_np(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long n = c->P[0]; return n * (16 * G1 + L1_) + lv[0];
+}
+static long long ix_mm_b_np(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long n = c->P[0]; return n * lv[0] + 16 * G0 + L0_;
+}
+
+/* variants: 0 PF, 1 noPF, 2 PF-a twin, 3 PF-b twin, 4 noPF-a twin, 5 noPF-b twin */
+static void walk_mm(ctx *c) {
+    long long n = c->P[0], v = c->D[0], lv[2];
+    switch (v) {
+    case 0:
+        for (lv[0] = 0; lv[0] < n / 16; lv[0]++) {
+            BAR(c);
+            X(c, 0, lv);                      /* a tile -> local */
+            X(c, 1, lv);                      /* b tile -> local */
+            BAR(c);
+            for (lv[1] = 0; lv[1] < 16; lv[1]++) X(c, 2, lv);   /* acc += af*bf */
+        }
+        X(c, 3, NULL);
+        break;
+    case 1:
+        for (lv[0] = 0; lv[0] < n; lv[0]++) X(c, 0, lv);        /* acc += a*b */
+        X(c, 1, NULL);
+        break;
+    case 2: case 3:
+        for (lv[0] = 0; lv[0] < n / 16; lv[0]++) X(c, 0, lv);   /* tgt += a|b */
+        X(c, 1, NULL);
+        break;
+    case 4: case 5:
+        for (lv[0] = 0; lv[0] < n; lv[0]++) X(c, 0, lv);
+        X(c, 1, NULL);
+        break;
+    }
+}
+static int setup_mm(ctx *c, int v) {
+    long long n = c->P[0];
+    if (n < 16 || n % 16) return -1;
+    c->D[0] = v;
+    c->grid[0] = n / 16; c->grid[1] = n / 16; c->grid[2] = 1;
+    c->wg[0] = 16; c->wg[1] = 16; c->wg[2] = 1;
+    if (v == 0) {
+        int s0 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+        stmt_site(c, s0, add_site(c, "mm-PF-a", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_mm_a_pf));
+        stmt_site(c, s0, add_site(c, "a_fetch_st", MEM_LOCAL, DIR_STORE, "float32", 4, ix_mm_tile_st));
+        int s1 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+        stmt_site(c, s1, add_site(c, "mm-PF-b", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_mm_b_pf));
+        stmt_site(c, s1, add_site(c, "b_fetch_st", MEM_LOCAL, DIR_STORE, "float32", 4, ix_mm_tile_st));
+        int s2 = add_stmt(c, 2, DT_F32, 0, 0, 1);
+        stmt_site(c, s2, add_site(c, "a_fetch_ld", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_mm_af_ld));
+        stmt_site(c, s2, add_site(c, "b_fetch_ld", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_mm_bf_ld));
+        int s3 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+        stmt_site(c, s3, add_site(c, "c", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_mm_c));
+    } else if (v == 1) {
+        int s0 = add_stmt(c, 1, DT_F32, 0, 0, 1);
+        stmt_site(c, s0, add_site(c, "mm-noPF-a", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_mm_a_np));
+        stmt_site(c, s0, add_site(c, "mm-noPF-b", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_mm_b_np));
+        int s1 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+        stmt_site(c, s1, add_site(c, "c", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_mm_c));
+    } else {
+        idx_fn f = v == 2 ? ix_mm_a_pf : v == 3 ? ix_mm_b_pf : v == 4 ? ix_mm_a_np : ix_mm_b_np;
+        const char *tag = v == 2 ? "mm-PF-a" : v == 3 ? "mm-PF-b" : v == 4 ? "mm-noPF-a" : "mm-noPF-b";
+        int s0 = add_stmt(c, 1, DT_F32, 1, 0, 0);
+        stmt_site(c, s0, add_site(c, tag, MEM_GLOBAL, DIR_LOAD, "float32", 4, f));
+        int s1 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+        stmt_site(c, s1, add_site(c, "tgt_dest", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_mm_c));
+    }
+    c->walk = walk_mm;
+    return 0;
+}
+
+/* ======================================================================
+ * DG differentiation (Section "DG"): res[m,k,i] = sum_j D[m,i,j] u[k,j],
+ * m < 3, D: 3 x Np x Np, u: Nel x Np, res: 3 x Nel x Np, all row-major fp32.
+ * k = L0*gid0 + lid0 (k split by lsize0), i = L1*gid1 + lid1 (i split by
+ * lsize1), guard i < Np.  P = {Np, Nel, L0, L1}.
+ * variants: 0 noPF, 1 dmPF (D tiles L1 x L0 prefetched to local memory,
+ * j split by L0), 2 noPF-u twin, 3 noPF-dm twin, 4 dmPF-u twin,
+ * 5 dmPF-dm twin, 6 res twin (store pattern only).
+ * Twins without a kept store write tgt to tgt_dest[(L1 gid1 + lid1) * Nel + k]
+ * (one entry per work-item, every work-item).
+ * ====================================================================== */
+#define DG_K(c, g, l) ((c)->P[2] * (g)[0] + (l)[0])
+#define DG_I(c, g, l) ((c)->P[3] * (g)[1] + (l)[1])
+static long long ix_dg_D(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long Np = c->P[0]; return Np * Np * lv[0] + Np * DG_I(c, g, l) + lv[1];
+}
+static long long ix_dg_u(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long Np = c->P[0]; return Np * DG_K(c, g, l) + lv[1];
+}
+static long long ix_dg_res(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long Np = c->P[0], Nel = c->P[1]; return Nel * Np * lv[0] + Np * DG_K(c, g, l) + DG_I(c, g, l);
+}
+/* dmPF: lv = {m, jo, ji} */
+static long long ix_dg_Dfetch(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long Np = c->P[0], L0 = c->P[2];
+    return Np * Np * lv[0] + Np * DG_I(c, g, l) + L0 * lv[1] + l[0];
+}
+static long long ix_dg_Dt_st(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; (void)lv; return c->P[2] * l[1] + l[0];
+}
+static long long ix_dg_Dt_ld(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; return c->P[2] * l[1] + lv[2];
+}
+static long long ix_dg_u_pf(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long Np = c->P[0], L0 = c->P[2]; return Np * DG_K(c, g, l) + L0 * lv[1] + lv[2];
+}
+static long long ix_dg_dest(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)lv; return c->P[1] * DG_I(c, g, l) + DG_K(c, g, l);
+}
+static void walk_dg(ctx *c) {
+    long long Np = c->P[0], L0 = c->P[2], v = c->D[0], lv[3];
+    long long i = DG_I(c, c->g, c->l);
+    long long nj = cdiv(Np, L0);
+    switch (v) {
+    case 0: case 2: case 3:
+        if (i < Np)
+            for (lv[0] = 0; lv[0] < 3; lv[0]++) {
+                for (lv[1] = 0; lv[1] < Np; lv[1]++) X(c, 0, lv);
+                if (v == 0) X(c, 1, lv);
+            }
+        if (v != 0) X(c, 1, NULL);
+        break;
+    case 1:
+        for (lv[0] = 0; lv[0] < 3; lv[0]++) {
+            for (lv[1] = 0; lv[1] < nj; lv[1]++) {
+                BAR(c);
+                if (i < Np && L0 * lv[1] + c->l[0] < Np) X(c, 0, lv);
+                BAR(c);
+                if (i < Np)
+                    for (lv[2] = 0; lv[2] < L0; lv[2]++)
+                        if (L0 * lv[1] + lv[2] < Np) X(c, 1, lv);
+            }
+            if (i < Np) X(c, 2, lv);
+        }
+        break;
+    case 4:
+        if (i < Np)
+            for (lv[0] = 0; lv[0] < 3; lv[0]++)
+                for (lv[1] = 0; lv[1] < nj; lv[1]++)
+                    for (lv[2] = 0; lv[2] < L0; lv[2]++)
+                        if (L0 * lv[1] + lv[2] < Np) X(c, 0, lv);
+        X(c, 1, NULL);
+        break;
+    case 5:
+        for (lv[0] = 0; lv[0] < 3; lv[0]++)
+            for (lv[1] = 0; lv[1] < nj; lv[1]++)
+                if (i < Np && L0 * lv[1] + c->l[0] < Np) X(c, 0, lv);
+        X(c, 1, NULL);
+        break;
+    case 6:
+        if (i < Np)
+            for (lv[0] = 0; lv[0] < 3; lv[0]++) X(c, 0, lv);
+        break;
+    }
+}
+static int setup_dg(ctx *c, int v) {
+    long long Np = c->P[0], Nel = c->P[1], L0 = c->P[2], L1 = c->P[3];
+    if (Np < 1 || Nel < 1 || L0 < 1 || L1 < 1 || L0 * L1 > 1024 || Nel % L0) return -1;
+    c->D[0] = v;
+    c->grid[0] = Nel / L0; c->grid[1] = cdiv(Np, L1); c->grid[2] = 1;
+    c->wg[0] = L0; c->wg[1] = L1; c->wg[2] = 1;
+    char t_nu[48], t_ndm[48], t_pu[48], t_pdm[48], t_res[48];
+    snprintf(t_nu, sizeof t_nu, "dg-noPF-u-%dx%d", (int)L0, (int)L1);
+    snprintf(t_ndm, sizeof t_ndm, "dg-noPF-dm-%dx%d", (int)L0, (int)L1);
+    snprintf(t_pu, sizeof t_pu, "dg-dmPF-u-%dx%d", (int)L0, (int)L1);
+    snprintf(t_pdm, sizeof t_pdm, "dg-dmPF-dm-%dx%d", (int)L0, (int)L1);
+    snprintf(t_res, sizeof t_res, "dg-res-%dx%d", (int)L0, (int)L1);
+    switch (v) {
+    case 0: {
+        int s0 = add_stmt(c, 2, DT_F32, 0, 0, 1);
+        stmt_site(c, s0, add_site(c, t_ndm, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dg_D));
+        stmt_site(c, s0, add_site(c, t_nu, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dg_u));
+        int s1 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+        stmt_site(c, s1, add_site(c, t_res, MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dg_res));
+        break; }
+    case 1: {
+        int s0 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+        stmt_site(c, s0, add_site(c, t_pdm, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dg_Dfetch));
+        stmt_site(c, s0, add_site(c, "dm_fetch_st", MEM_LOCAL, DIR_STORE, "float32", 4, ix_dg_Dt_st));
+        int s1 = add_stmt(c, 3, DT_F32, 0, 0, 1);
+        stmt_site(c, s1, add_site(c, "dm_fetch_ld", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_dg_Dt_ld));
+        stmt_site(c, s1, add_site(c, t_pu, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dg_u_pf));
+        int s2 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+        stmt_site(c, s2, add_site(c, t_res, MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dg_res));
+        break; }
+    case 2: case 3: {
+        int s0 = add_stmt(c, 2, DT_F32, 1, 0, 0);
+        if (v == 2) stmt_site(c, s0, add_site(c, t_nu, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dg_u));
+        else stmt_site(c, s0, add_site(c, t_ndm, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dg_D));
+        int s1 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+        stmt_site(c, s1, add_site(c, "tgt_dest", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dg_dest));
+        break; }
+    case 4: {
+        int s0 = add_stmt(c, 3, DT_F32, 1, 0, 0);
+        stmt_site(c, s0, add_site(c, t_pu, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dg_u_pf));
+        int s1 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+        stmt_site(c, s1, add_site(c, "tgt_dest", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dg_dest));
+        break; }
+    case 5: {
+        int s0 = add_stmt(c, 2, DT_F32, 1, 0, 0);
+        stmt_site(c, s0, add_site(c, t_pdm, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dg_Dfetch));
+        int s1 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+        stmt_site(c, s1, add_site(c, "tgt_dest", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dg_dest));
+        break; }
+    case 6: {
+        int s0 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+        stmt_site(c, s0, add_site(c, t_res, MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dg_res));
+        break; }
+    default: return -1;
+    }
+    c->walk = walk_dg;
+    return 0;
+}
+
+/* ======================================================================
+ * 2-D five-point finite difference stencil (Section "Finite Differences"):
+ * res[i,j] = c0*u[i+1,j+1] + c1*(u[i,j+1] + u[i+2,j+1] + u[i+1,j] + u[i+1,j+2]),
+ * u: (n+2) x (n+2), res: n x n, fp32 row-major.  P = {n}.
+ * variants: 0 tile (16x16 work-group fetches a 16x16 tile of u to local
+ * memory, the 14x14 interior computes, group stride 14), 1 direct (16x16
+ * work-group, one output per work-item, five global loads), 2 tile-u twin,
+ * 3 tile-res twin, 4 direct-u twin, 5 direct-res twin.
+ * Twins without a kept store write to tgt_dest[(16 gid1 + lid1)*(16 G0) + 16 gid0 + lid0].
+ * ====================================================================== */
+#define FD_W(c) ((c)->P[0] + 2)
+static long long ix_fd_fetch(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)lv; return FD_W(c) * (14 * G1 + L1_) + 14 * G0 + L0_;
+}
+static long long ix_fd_tile_st(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)c; (void)g; (void)lv; return 16 * L1_ + L0_;
+}
+static long long ix_fd_tC(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)c; (void)g; (void)lv; return 16 * L1_ + L0_;
+}
+static long long ix_fd_tN(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)c; (void)g; (void)lv; return 16 * (L1_ - 1) + L0_;
+}
+static long long ix_fd_tS(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)c; (void)g; (void)lv; return 16 * (L1_ + 1) + L0_;
+}
+static long long ix_fd_tW(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)c; (void)g; (void)lv; return 16 * L1_ + L0_ - 1;
+}
+static long long ix_fd_tE(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)c; (void)g; (void)lv; return 16 * L1_ + L0_ + 1;
+}
+static long long ix_fd_res_tile(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)lv; return c->P[0] * (14 * G1 + L1_ - 1) + 14 * G0 + L0_ - 1;
+}
+#define FD_DI(c, g, l) (16 * (g)[1] + (l)[1])
+#define FD_DJ(c, g, l) (16 * (g)[0] + (l)[0])
+static long long ix_fd_uC(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)lv; return FD_W(c) * (FD_DI(c, g, l) + 1) + FD_DJ(c, g, l) + 1;
+}
+static long long ix_fd_uN(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)lv; return FD_W(c) * FD_DI(c, g, l) + FD_DJ(c, g, l) + 1;
+}
+static long long ix_fd_uS(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)lv; return FD_W(c) * (FD_DI(c, g, l) + 2) + FD_DJ(c, g, l) + 1;
+}
+static long long ix_fd_uW(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)lv; return FD_W(c) * (FD_DI(c, g, l) + 1) + FD_DJ(c, g, l);
+}
+static long long ix_fd_uE(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)lv; return FD_W(c) * (FD_DI(c, g, l) + 1) + FD_DJ(c, g, l) + 2;
+}
+static long long ix_fd_res_direct(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)lv; return c->P[0] * FD_DI(c, g, l) + FD_DJ(c, g, l);
+}
+static long long ix_fd_dest(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)lv; return 16 * c->grid[0] * (16 * G1 + L1_) + 16 * G0 + L0_;
+}
+static void walk_fd(ctx *c) {
+    long long n = c->P[0], W = n + 2, v = c->D[0];
+    const long long *g = c->g, *l = c->l;
+    if (v == 0 || v == 2 || v == 3) {
+        long long r = 14 * G1 + L1_, q = 14 * G0 + L0_;
+        int fetch = r < W && q < W;
+        int comp = L0_ >= 1 && L0_ <= 14 && L1_ >= 1 && L1_ <= 14 && r - 1 < n && q - 1 < n;
+        if (v == 0) {
+            if (fetch) X(c, 0, NULL);
+            BAR(c);
+            if (comp) X(c, 1, NULL);
+        } else if (v == 2) {
+            if (fetch) X(c, 0, NULL);
+            X(c, 1, NULL);
+        } else {
+            if (comp) X(c, 0, NULL);
+        }
+    } else {
+        long long i = FD_DI(c, g, l), j = FD_DJ(c, g, l);
+        int comp = i < n && j < n;
+        if (v == 1 || v == 5) { if (comp) X(c, 0, NULL); }
+        else {
+            if (comp) for (int s = 0; s < 5; s++) X(c, s, NULL);
+            X(c, 5, NULL);
+        }
+    }
+}
+static int setup_fd(ctx *c, int v) {
+    long long n = c->P[0];
+    if (n < 1) return -1;
+    c->D[0] = v;
+    c->wg[0] = 16; c->wg[1] = 16; c->wg[2] = 1;
+    if (v == 0 || v == 2 || v == 3) { c->grid[0] = cdiv(n, 14); c->grid[1] = cdiv(n, 14); }
+    else { c->grid[0] = cdiv(n, 16); c->grid[1] = cdiv(n, 16); }
+    c->grid[2] = 1;
+    switch (v) {
+    case 0: {
+        int s0 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+        stmt_site(c, s0, add_site(c, "fd-tile-u", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_fd_fetch));
+        stmt_site(c, s0, add_site(c, "u_fetch_st", MEM_LOCAL, DIR_STORE, "float32", 4, ix_fd_tile_st));
+        int s1 = add_stmt(c, 0, DT_F32, 3, 1, 1);
+        stmt_site(c, s1, add_site(c, "u_fetch_c", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_fd_tC));
+        stmt_site(c, s1, add_site(c, "u_fetch_n", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_fd_tN));
+        stmt_site(c, s1, add_site(c, "u_fetch_s", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_fd_tS));
+        stmt_site(c, s1, add_site(c, "u_fetch_w", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_fd_tW));
+        stmt_site(c, s1, add_site(c, "u_fetch_e", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_fd_tE));
+        stmt_site(c, s1, add_site(c, "fd-tile-res", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_fd_res_tile));
+        break; }
+    case 1: {
+        int s0 = add_stmt(c, 0, DT_F32, 3, 1, 1);
+        stmt_site(c, s0, add_site(c, "u_c", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_fd_uC));
+        stmt_site(c, s0, add_site(c, "u_n", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_fd_uN));
+        stmt_site(c, s0, add_site(c, "u_s", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_fd_uS));
+        stmt_site(c, s0, add_site(c, "u_w", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_fd_uW));
+        stmt_site(c, s0, add_site(c, "u_e", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_fd_uE));
+        stmt_site(c, s0, add_site(c, "res", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_fd_res_direct));
+        break; }
+    case 2: {
+        int s0 = add_stmt(c, 0, DT_F32, 1, 0, 0);
+        stmt_site(c, s0, add_site(c, "fd-tile-u", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_fd_fetch));
+        int s1 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+        stmt_site(c, s1, add_site(c, "tgt_dest", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_fd_dest));
+        break; }
+    case 3: {
+        int s0 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+        stmt_site(c, s0, add_site(c, "fd-tile-res", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_fd_res_tile));
+        break; }
+    case 4: {
+        static const char *nm[5] = {"u_c", "u_n", "u_s", "u_w", "u_e"};
+        idx_fn fs[5] = {ix_fd_uC, ix_fd_uN, ix_fd_uS, ix_fd_uW, ix_fd_uE};
+        for (int s = 0; s < 5; s++) {
+            int st = add_stmt(c, 0, DT_F32, 1, 0, 0);
+            stmt_site(c, st, add_site(c, nm[s], MEM_GLOBAL, DIR_LOAD, "float32", 4, fs[s]));
+        }
+        int s5 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+        stmt_site(c, s5, add_site(c, "tgt_dest", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_fd_dest));
+        break; }
+    case 5: {
+        int s0 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+        stmt_site(c, s0, add_site(c, "res", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_fd_res_direct));
+        break; }
+    default: return -1;
+    }
+    c->walk = walk_fd;
+    return 0;
+}
+
+/* ======================================================================
+ * Public oracle entry: enumerate every (group, sub-group, lane) point.
+ * ====================================================================== */
+typedef struct {
+    int kind;                 /* 0 op, 1 mem access site, 2 barrier, 3 groups, 4 launch, 5 grid */
+    char name[24];            /* op: "add"/"mul"/"madd"; site: tag */
+    char dtype[16];
+    int mem, dir, dsize, uniform, affine;
+    long long lstr[3], gstr[3], loopstr;
+    unsigned long long wi, sg, footprint;
+} orec;
+
+static const struct { const char *name; int fam, v; } KTAB[] = {
+    {"stream", 0, 0}, {"fma", 1, 0}, {"smem", 2, 0}, {"barrier", 3, 0}, {"overlap", 4, 0}, {"empty", 5, 0},
+    {"mm_pf", 6, 0}, {"mm_nopf", 6, 1}, {"mm_pf_a", 6, 2}, {"mm_pf_b", 6, 3}, {"mm_nopf_a", 6, 4}, {"mm_nopf_b", 6, 5},
+    {"dg_nopf", 7, 0}, {"dg_dmpf", 7, 1}, {"dg_nopf_u", 7, 2}, {"dg_nopf_dm", 7, 3}, {"dg_dmpf_u", 7, 4},
+    {"dg_dmpf_dm", 7, 5}, {"dg_res", 7, 6},
+    {"fd_tile", 8, 0}, {"fd_direct", 8, 1}, {"fd_tile_u", 8, 2}, {"fd_tile_res", 8, 3}, {"fd_direct_u", 8, 4},
+    {"fd_direct_res", 8, 5},
+};
+
+int oracle_counts(const char *kernel, const long long *P, int nP, orec *out, int cap, int *n_out) {
+    ctx *c = (ctx *)calloc(1, sizeof(ctx));
+    int fam = -1, v = 0, rc = 0;
+    for (size_t i = 0; i < sizeof KTAB / sizeof KTAB[0]; i++)
+        if (!strcmp(KTAB[i].name, kernel)) { fam = KTAB[i].fam; v = KTAB[i].v; }
+    if (fam < 0 || nP > 8) { free(c); return -1; }
+    for (int i = 0; i < nP; i++) c->P[i] = P[i];
+    switch (fam) {
+    case 0: rc = setup_stream(c); break;
+    case 1: rc = setup_fma(c); break;
+    case 2: rc = setup_smem(c); break;
+    case 3: rc = setup_barrier(c); break;
+    case 4: rc = setup_overlap(c); break;
+    case 5: rc = setup_empty(c); break;
+    case 6: rc = setup_mm(c, v); break;
+    case 7: rc = setup_dg(c, v); break;
+    case 8: rc = setup_fd(c, v); break;
+    }
+    if (rc) { free(c); return -2; }
+    for (int s = 0; s < c->nsite; s++) ks_init(&c->ss[s].foot, 1024);
+    ks_init(&c->sgset, 1024);
+    c->bar_min = -1; c->bar_max = -1;
+    long long L0 = c->wg[0], L1 = c->wg[1], L2 = c->wg[2], T = L0 * L1 * L2;
+    long long g[3];
+    for (g[2] = 0; g[2] < c->grid[2]; g[2]++)
+    for (g[1] = 0; g[1] < c->grid[1]; g[1]++)
+    for (g[0] = 0; g[0] < c->grid[0]; g[0]++) {
+        for (long long q = 0; q * SGSIZE < T; q++) {
+            ks_clear(&c->sgset);
+            for (long long lane = 0; lane < SGSIZE && q * SGSIZE + lane < T; lane++) {
+                long long t = q * SGSIZE + lane;
+                c->g[0] = g[0]; c->g[1] = g[1]; c->g[2] = g[2];
+                c->l[0] = t % L0; c->l[1] = (t / L0) % L1; c->l[2] = t / (L0 * L1);
+                c->bar_cur = 0;
+                c->walk(c);
+                if (c->bar_min < 0 || c->bar_cur < c->bar_min) c->bar_min = c->bar_cur;
+                if (c->bar_cur > c->bar_max) c->bar_max = c->bar_cur;
+            }
+        }
+    }
+    if (c->err) { rc = -3; goto done; }
+    int n = 0;
+#define EMIT() do { if (n >= cap) { rc = -4; goto done; } memset(&out[n], 0, sizeof(orec)); } while (0)
+    static const char *opn[3] = {"add", "mul", "madd"};
+    for (int dt = 0; dt < 2; dt++)
+        for (int o = 0; o < 3; o++)
+            if (c->op_wi[dt][o]) {
+                EMIT();
+                out[n].kind = 0;
+                strcpy(out[n].name, opn[o]);
+                strcpy(out[n].dtype, dt == 0 ? "float32" : "float64");
+                out[n].wi = c->op_wi[dt][o]; out[n].sg = c->op_sg[dt][o];
+                n++;
+            }
+    for (int s = 0; s < c->nsite; s++) {
+        if (c->ss[s].wi == 0) continue;
+        EMIT();
+        orec *r = &out[n++];
+        r->kind = 1;
+        strncpy(r->name, c->site[s].tag, sizeof r->name - 1);
+        strncpy(r->dtype, c->site[s].dtype, sizeof r->dtype - 1);
+        r->mem = c->site[s].mem; r->dir = c->site[s].dir; r->dsize = c->site[s].dsize;
+        for (int a = 0; a < 3; a++) { r->lstr[a] = c->ss[s].lstr[a]; r->gstr[a] = c->ss[s].gstr[a]; }
+        r->loopstr = c->ss[s].loopstr;
+        r->affine = c->ss[s].affine;
+        r->uniform = r->lstr[0] == 0;
+        r->wi = c->ss[s].wi; r->sg = c->ss[s].sg; r->footprint = c->ss[s].foot.n;
+    }
+    EMIT(); out[n].kind = 2; strcpy(out[n].name, "barrier_local");
+    out[n].wi = (unsigned long long)(c->bar_max < 0 ? 0 : c->bar_max);
+    out[n].sg = (unsigned long long)(c->bar_min < 0 ? 0 : c->bar_min); n++;
+    EMIT(); out[n].kind = 3; strcpy(out[n].name, "thread_groups");
+    out[n].wi = (unsigned long long)(c->grid[0] * c->grid[1] * c->grid[2]); n++;
+    EMIT(); out[n].kind = 4; strcpy(out[n].name, "kernel_launch"); out[n].wi = 1; n++;
+    EMIT(); out[n].kind = 5; strcpy(out[n].name, "grid");
+    for (int a = 0; a < 3; a++) { out[n].lstr[a] = c->wg[a]; out[n].gstr[a] = c->grid[a]; }
+    n++;
+    *n_out = n;
+done:
+    for (int s = 0; s < c->nsite; s++) ks_free(&c->ss[s].foot);
+    ks_free(&c->sgset);
+    free(c);
+    return rc;
+}
+
+int oracle_sizeof_orec(void) { return (int)sizeof(orec); }
+
+/* ======================================================================
+ * Reference outputs.  FP64 references follow the mathematical definition;
+ * bit-exact replays follow the kernel definition's operation order (this
+ * file is compiled with -ffp-contract=off so no multiply-add is fused
+ * unless fma()/fmaf() is called explicitly).
+ * ====================================================================== */
+
+/* stream: out[e] = ((in0[e] + in1[e]) + in2[e]) + ..., in the kernel's dtype */
+void oracle_stream_ref(int dtype, int L, long long N, const void *const *ins, void *out) {
+    if (dtype == DT_F32) {
+        const float *const *x = (const float *const *)ins; float *o = (float *)out;
+        for (long long e = 0; e < N; e++) { float s = x[0][e]; for (int a = 1; a < L; a++) s = s + x[a][e]; o[e] = s; }
+    } else {
+        const double *const *x = (const double *const *)ins; double *o = (double *)out;
+        for (long long e = 0; e < N; e++) { double s = x[0][e]; for (int a = 1; a < L; a++) s = s + x[a][e]; o[e] = s; }
+    }
+}
+
+/* arithmetic kernel constants (the kernel's definition):
+ *   x_t = u + t/32;  add: x += 2^-13;  mul: x *= 1 - 2^-12;
+ *   madd: x = x*(1 - 2^-10) + 2^-10;   out = x_0 + x_1 + ... + x_31 */
+void oracle_fma_ref(int dtype, int op, long long F, long long nthreads, const void *seed, void *out) {
+    long long R = F / 32;
+    if (dtype == DT_F32) {
+        const float *u = (const float *)seed; float *o = (float *)out;
+        const float ca = 0.0001220703125f, ma = 0.999755859375f, fa = 0.9990234375f, fb = 0.0009765625f;
+        for (long long t = 0; t < nthreads; t++) {
+            float x[32];
+            for (int k = 0; k < 32; k++) x[k] = u[t] + (float)k * 0.03125f;
+            for (long long r = 0; r < R; r++)
+                for (int k = 0; k < 32; k++) {
+                    if (op == 0) x[k] = x[k] + ca;
+                    else if (op == 1) x[k] = x[k] * ma;
+                    else x[k] = fmaf(x[k], fa, fb);
+                }
+            float s = x[0];
+            for (int k = 1; k < 32; k++) s = s + x[k];
+            o[t] = s;
+        }
+    } else {
+        const double *u = (const double *)seed; double *o = (double *)out;
+        const double ca = 0.0001220703125, ma = 0.999755859375, fa = 0.9990234375, fb = 0.0009765625;
+        for (long long t = 0; t < nthreads; t++) {
+            double x[32];
+            for (int k = 0; k < 32; k++) x[k] = u[t] + (double)k * 0.03125;
+            for (long long r = 0; r < R; r++)
+                for (int k = 0; k < 32; k++) {
+                    if (op == 0) x[k] = x[k] + ca;
+                    else if (op == 1) x[k] = x[k] * ma;
+                    else x[k] = fma(x[k], fa, fb);
+                }
+            double s = x[0];
+            for (int k = 1; k < 32; k++) s = s + x[k];
+            o[t] = s;
+        }
+    }
+}
+
+/* matmul FP64 reference and the per-element absolute-value sum sum_k |a_ik b_kj| */
+void oracle_mm_ref(long long n, const float *a, const float *b, double *c, double *cabs) {
+    for (long long i = 0; i < n; i++)
+        for (long long j = 0; j < n; j++) {
+            double s = 0.0, sa = 0.0;
+            for (long long k = 0; k < n; k++) {
+                double p = (double)a[n * i + k] * (double)b[n * k + j];
+                s += p; sa += fabs(p);
+            }
+            c[n * i + j] = s; cabs[n * i + j] = sa;
+        }
+}
+
+/* DG FP64 reference: res[m,k,i] = sum_j D[m,i,j] u[k,j] (and |.| sums) */
+void oracle_dg_ref(long long Np, long long Nel, const float *D, const float *u, double *res, double *rabs) {
+    for (long long m = 0; m < 3; m++)
+        for (long long k = 0; k < Nel; k++)
+            for (long long i = 0; i < Np; i++) {
+                double s = 0.0, sa = 0.0;
+                for (long long j = 0; j < Np; j++) {
+                    double p = (double)D[Np * Np * m + Np * i + j] * (double)u[Np * k + j];
+                    s += p; sa += fabs(p);
+                }
+                res[Nel * Np * m + Np * k + i] = s; rabs[Nel * Np * m + Np * k + i] = sa;
+            }
+}
+
+/* stencil FP64 reference */
+void oracle_fd_ref(long long n, double c0, double c1, const float *u, double *res, double *rabs) {
+    long long W = n + 2;
+    for (long long i = 0; i < n; i++)
+        for (long long j = 0; j < n; j++) {
+            double C = u[W * (i + 1) + j + 1], N_ = u[W * i + j + 1], S = u[W * (i + 2) + j + 1];
+            double Wv = u[W * (i + 1) + j], E = u[W * (i + 1) + j + 2];
+            res[n * i + j] = c0 * C + c1 * (N_ + S + Wv + E);
+            rabs[n * i + j] = fabs(c0 * C) + fabs(c1) * (fabs(N_) + fabs(S) + fabs(Wv) + fabs(E));
+        }
+}
+
+/* bit-exact FP32 replay of the work-removed (gmem-only) twins: each work-item
+ * sums its loads sequentially, starting from 0.0f, in loop order. */
+void oracle_mm_twin_ref(int v, long long n, const float *x, float *dest) {
+    /* v: 2 PF-a, 3 PF-b, 4 noPF-a, 5 noPF-b; dest is n x n (one entry per WI) */
+    for (long long i = 0; i < n; i++)
+        for (long long j = 0; j < n; j++) {
+            float t = 0.0f;
+            long long g0 = j / 16, l0 = j % 16, g1 = i / 16, l1 = i % 16;
+            if (v == 2) for (long long ko = 0; ko < n / 16; ko++) t = t + x[n * (16 * g1 + l1) + 16 * ko + l0];
+            if (v == 3) for (long long ko = 0; ko < n / 16; ko++) t = t + x[n * (16 * ko + l1) + 16 * g0 + l0];
+            if (v == 4) for (long long k = 0; k < n; k++) t = t + x[n * i + k];
+            if (v == 5) for (long long k = 0; k < n; k++) t = t + x[n * k + j];
+            dest[n * i + j] = t;
+        }
+}
+
+void oracle_dg_twin_ref(int v, long long Np, long long Nel, long long L0, long long L1, const float *D,
+                        const float *u, float *dest) {
+    /* v: 2 noPF-u, 3 noPF-dm, 4 dmPF-u, 5 dmPF-dm; dest rows = ceil(Np/L1)*L1, cols = Nel */
+    long long rows = cdiv(Np, L1) * L1, nj = cdiv(Np, L0);
+    for (long long i = 0; i < rows; i++)
+        for (long long k = 0; k < Nel; k++) {
+            float t = 0.0f;
+            long long l0 = k % L0;
+            if (i < Np) for (long long m = 0; m < 3; m++) {
+                if (v == 2 || v == 4) for (long long j = 0; j < Np; j++) t = t + u[Np * k + j];
+                if (v == 3) for (long long j = 0; j < Np; j++) t = t + D[Np * Np * m + Np * i + j];
+                if (v == 5) for (long long jo = 0; jo < nj; jo++)
+                    if (L0 * jo + l0 < Np) t = t + D[Np * Np * m + Np * i + L0 * jo + l0];
+            }
+            dest[Nel * i + k] = t;
+        }
+}
+
+void oracle_fd_twin_ref(int v, long long n, const float *u, float *dest) {
+    /* v: 2 tile-u (dest is (16*G1) x (16*G0), G = ceil(n/14)),
+     *    4 direct-u (dest is (16*G1) x (16*G0), G = ceil(n/16)) */
+    long long W = n + 2;
+    if (v == 2) {
+        long long G = cdiv(n, 14), cols = 16 * G;
+        for (long long gi = 0; gi < G; gi++) for (long long gj = 0; gj < G; gj++)
+        for (long long l1 = 0; l1 < 16; l1++) for (long long l0 = 0; l0 < 16; l0++) {
+            long long r = 14 * gi + l1, q = 14 * gj + l0;
+            float t = 0.0f;
+            if (r < W && q < W) t = t + u[W * r + q];
+            dest[cols * (16 * gi + l1) + 16 * gj + l0] = t;
+        }
+    } else {
+        long long G = cdiv(n, 16), cols = 16 * G;
+        for (long long i = 0; i < 16 * G; i++) for (long long j = 0; j < 16 * G; j++) {
+            float t = 0.0f;
+            if (i < n && j < n) {
+                t = t + u[W * (i + 1) + j + 1];
+                t = t + u[W * i + j + 1];
+                t = t + u[W * (i + 2) + j + 1];
+                t = t + u[W * (i + 1) + j];
+                t = t + u[W * (i + 1) + j + 2];
+            }
+            dest[cols * i + j] = t;
+        }
+    }
+}
+
+/* worked example of Section "Gathering Kernel Statistics": number of integer
+ * points (i, j) with p <= i < n and p <= j < i + 1, by brute force. */
+long long oracle_count_example(long long n, long long p) {
+    long long cnt = 0;
+    for (long long i = p; i < n; i++)
+        for (long long j = p; j < i + 1; j++) cnt++;
+    return cnt;
+}

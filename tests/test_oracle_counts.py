@@ -1,0 +1,234 @@
+"""Pins of the oracle's brute-force counting against what the paper and the
+mathematics fix (closed forms, worked examples, Table 'ab_pattern',
+coverage invariants).  CPU only."""
+import json
+import os
+
+import pytest
+
+import oracle
+from oracle.features import features, feature_value, parse_feature, matches
+from oracle.quasipoly import extrapolate
+
+GOLD = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "paper_tables.json")))
+
+
+def by_tag(fs, tag):
+    out = [f for f in fs if f["kind"] == "mem" and f["tag"] == tag]
+    assert len(out) == 1, (tag, [f["name"] for f in fs])
+    return out[0]
+
+
+def op(fs, dtype, o, wi=False):
+    for f in fs:
+        if f["kind"] == "op" and f["dtype"] == dtype and f["op"] == o:
+            return f["count_wi"] if wi else f["count"]
+    return 0
+
+
+def single(fs, kind):
+    return [f for f in fs if f["kind"] == kind][0]["count"]
+
+
+def test_worked_count_example():
+    # Section "Gathering Kernel Statistics": |{p<=i<n, p<=j<i+1}| = (n^2+p^2-2np+n-p)/2
+    for n in range(0, 41):
+        for p in range(0, n + 1):
+            assert 2 * oracle.count_example(n, p) == n * n + p * p - 2 * n * p + n - p
+
+
+@pytest.mark.parametrize("n", [16, 32, 48, 64])
+def test_mm_pf_closed_forms(n):
+    fs = features("mm_pf", n=n)
+    assert op(fs, "float32", "madd", wi=True) == n ** 3           # 2n^3 flops
+    assert op(fs, "float32", "madd") == n ** 3 // 32               # per sub-group
+    a, b = by_tag(fs, "mm-PF-a"), by_tag(fs, "mm-PF-b")
+    assert a["count"] == b["count"] == n ** 3 // 16 and a["gran"] == "WI"
+    # Table ab_pattern
+    assert a["lstr"] == (1, n) and a["gstr"] == (0, 16 * n) and a["loopstr"] == 16
+    assert b["lstr"] == (1, n) and b["gstr"] == (16, 0) and b["loopstr"] == 16 * n
+    assert a["accesses"] * 16 == n * a["footprint"] and b["accesses"] * 16 == n * b["footprint"]  # AFR n/16
+    # Section "Matrix Multiplication": 2n^3 local loads, 2n^3/16 local stores
+    loc = [f for f in fs if f["kind"] == "mem" and f["mem"] == "local"]
+    assert sum(f["count_wi"] for f in loc if f["dir"] == "load") == 2 * n ** 3
+    assert sum(f["count_wi"] for f in loc if f["dir"] == "store") == 2 * n ** 3 // 16
+    c = by_tag(fs, "c")
+    assert c["count"] == c["footprint"] == n * n
+    assert single(fs, "sync") == n // 8
+    assert single(fs, "groups") == n * n // 256
+    assert single(fs, "launch") == 1
+
+
+@pytest.mark.parametrize("n", [16, 32, 48])
+def test_mm_nopf_closed_forms(n):
+    fs = features("mm_nopf", n=n)
+    a, b = by_tag(fs, "mm-noPF-a"), by_tag(fs, "mm-noPF-b")
+    # lid(0) stride 0: uniform, counted once per sub-group (Table mm_param_vals, MCG SG)
+    assert a["lstr"][0] == 0 and a["gran"] == "SG" and a["count"] == n ** 3 // 32
+    assert b["gran"] == "WI" and b["count"] == n ** 3
+    # 16x fewer global loads with prefetching (Section "Matrix Multiplication")
+    pf = features("mm_pf", n=n)
+    assert by_tag(pf, "mm-PF-a")["count_wi"] * 16 == a["count_wi"]
+    assert single(fs, "sync") == 0
+    assert op(fs, "float32", "madd", wi=True) == n ** 3
+
+
+def test_mm_counts_at_paper_sizes_by_interpolation():
+    # Counts are polynomials in n on the class n = 0 mod 16; brute force at
+    # n = 16..80 fixes them exactly; compare with the closed forms at the
+    # configuration sizes.
+    def cnt(n, what):
+        fs = features("mm_pf", n=n)
+        return {"madd": op(fs, "float32", "madd", wi=True),
+                "gld": by_tag(fs, "mm-PF-a")["count"] + by_tag(fs, "mm-PF-b")["count"],
+                "gst": by_tag(fs, "c")["count"], "wg": single(fs, "groups"), "bar": single(fs, "sync")}[what]
+    cache = {}
+
+    def f(what):
+        def g(n):
+            key = (n, what)
+            if key not in cache:
+                cache[key] = cnt(n, what)
+            return cache[key]
+        return g
+    for n in (256, 768, 896):
+        assert extrapolate(f("madd"), n, 16, 3, 16) == n ** 3
+        assert extrapolate(f("gld"), n, 16, 3, 16) == n ** 3 // 8
+        assert extrapolate(f("gst"), n, 16, 2, 16) == n ** 2
+        assert extrapolate(f("wg"), n, 16, 2, 16) == n ** 2 // 256
+        assert extrapolate(f("bar"), n, 16, 1, 16) == n // 8
+
+
+def test_paper_constraint_features_select_a_and_b():
+    # Section "Data Motion Features": pattern-based features pick the a and b loads
+    n = 48
+    fs = features("mm_pf", n=n)
+    fa = "f_mem_access_global_float32_load_lstrides:{0:1;1:>15}_gstrides:{0:0}_afr:>1"
+    fb = "f_mem_access_global_float32_load_lstrides:{0:1;1:>15}_gstrides:{0:16}_afr:>1"
+    assert feature_value(fa, fs) == by_tag(fs, "mm-PF-a")["count"]
+    assert feature_value(fb, fs) == by_tag(fs, "mm-PF-b")["count"]
+    assert [f["tag"] for f in fs if f["kind"] == "mem" and matches(parse_feature(fa), f)] == ["mm-PF-a"]
+    assert feature_value("f_mem_access_tag:mm-PF-a", fs) == n ** 3 // 16
+    assert feature_value("f_mem_access_local_float32", fs) == (2 * n ** 3 + 2 * n ** 3 // 16) // 32
+    assert feature_value("f_op_float32_madd", fs) == n ** 3 // 32
+    with pytest.raises(ValueError):
+        parse_feature("f_mem_access_float32_global")     # fields out of order
+
+
+@pytest.mark.parametrize("kernel,tag,loads_per_wi", [
+    ("mm_pf_a", "mm-PF-a", lambda n: n // 16), ("mm_pf_b", "mm-PF-b", lambda n: n // 16),
+    ("mm_nopf_a", "mm-noPF-a", lambda n: n), ("mm_nopf_b", "mm-noPF-b", lambda n: n)])
+def test_mm_twins_keep_parent_pattern(kernel, tag, loads_per_wi):
+    # Algorithm 3: the kept load keeps its pattern; one add per kept load; a
+    # per-work-item store of tgt is added.
+    n = 32
+    parent = features("mm_pf" if "_pf_" in kernel else "mm_nopf", n=n)
+    twin = features(kernel, n=n)
+    p, t = by_tag(parent, tag), by_tag(twin, tag)
+    for key in ("lstr", "gstr", "loopstr", "count", "gran", "footprint", "accesses"):
+        assert p[key] == t[key], key
+    assert op(twin, "float32", "add", wi=True) == n * n * loads_per_wi(n)
+    dest = by_tag(twin, "tgt_dest")
+    assert dest["count"] == dest["footprint"] == n * n
+    assert single(twin, "sync") == 0
+
+
+@pytest.mark.parametrize("Np,Nel,L0,L1", [(20, 32, 16, 16), (35, 64, 32, 8), (32, 32, 16, 16), (56, 32, 32, 8)])
+def test_dg_closed_forms(Np, Nel, L0, L1):
+    sh = "%dx%d" % (L0, L1)
+    for v in ("dg_nopf", "dg_dmpf"):
+        fs = features(v, Np=Np, Nel=Nel, L0=L0, L1=L1)
+        assert op(fs, "float32", "madd", wi=True) == 3 * Nel * Np * Np    # 6 Nel Np^2 flops
+        res = by_tag(fs, "dg-res-" + sh)
+        assert res["count"] == res["footprint"] == 3 * Nel * Np              # every output once
+        pre = "dg-noPF" if v == "dg_nopf" else "dg-dmPF"
+        u = by_tag(fs, pre + "-u-" + sh)
+        assert u["count_wi"] == 3 * Nel * Np * Np and u["footprint"] == Nel * Np
+        assert u["lstr"] == (Np, 0) and u["gstr"][0] == L0 * Np
+        d = by_tag(fs, pre + "-dm-" + sh)
+        assert d["footprint"] == 3 * Np * Np
+        if v == "dg_nopf":
+            assert d["lstr"][0] == 0 and d["gran"] == "SG" and d["count_wi"] == 3 * Nel * Np * Np
+            assert single(fs, "sync") == 0
+            if Np % (2 * 32 // L0) == 0:   # sub-groups all full
+                assert d["count"] == d["count_wi"] // 32
+        else:
+            # each D element fetched once per k-tile: AFR = Nel / L0
+            assert d["count_wi"] == 3 * Np * Np * (Nel // L0)
+            assert single(fs, "sync") == 2 * 3 * (-(-Np // L0))
+            loc = [f for f in fs if f["kind"] == "mem" and f["mem"] == "local"]
+            assert sum(f["count_wi"] for f in loc if f["dir"] == "load") == 3 * Nel * Np * Np
+            assert sum(f["count_wi"] for f in loc if f["dir"] == "store") == 3 * Np * Np * (Nel // L0)
+        assert single(fs, "groups") == (Nel // L0) * (-(-Np // L1))
+
+
+@pytest.mark.parametrize("n", [14, 20, 33, 48])
+def test_fd_closed_forms(n):
+    W = n + 2
+    t = features("fd_tile", n=n)
+    assert op(t, "float32", "madd", wi=True) == n * n
+    assert op(t, "float32", "add", wi=True) == 3 * n * n
+    assert op(t, "float32", "mul", wi=True) == n * n
+    r = by_tag(t, "fd-tile-res")
+    assert r["count"] == r["footprint"] == n * n
+    u = by_tag(t, "fd-tile-u")
+    assert u["footprint"] == W * W and u["lstr"] == (1, W) and u["gstr"] == (14, 14 * W)
+    G = -(-n // 14)
+    per_axis = sum(min(16, W - 14 * g) for g in range(G))
+    assert u["count"] == per_axis * per_axis
+    loc = [f for f in t if f["kind"] == "mem" and f["mem"] == "local"]
+    assert sum(f["count_wi"] for f in loc if f["dir"] == "load") == 5 * n * n
+    assert single(t, "sync") == 1
+    d = features("fd_direct", n=n)
+    loads = [f for f in d if f["kind"] == "mem" and f["dir"] == "load"]
+    assert len(loads) == 5
+    for f in loads:
+        assert f["count"] == f["footprint"] == n * n and f["lstr"] == (1, W) and f["gstr"] == (16, 16 * W)
+    assert op(d, "float32", "madd", wi=True) == n * n
+
+
+@pytest.mark.parametrize("dtype,vec,s,L,shape", [(0, 0, 1, 1, 0), (0, 1, 4, 3, 0), (1, 0, 32, 4, 0),
+                                                 (1, 1, 2, 2, 0), (0, 0, 1, 2, 1), (0, 1, 1, 4, 1)])
+def test_stream_pattern(dtype, vec, s, L, shape):
+    N = 256 * 32 * 8 * 4
+    Wd = 64
+    fs = features("stream", dtype=dtype, vec=vec, N=N, s=s, L=L, shape=shape, W=Wd)
+    w = (4 if dtype == 0 else 2) if vec else 1
+    M = N // w
+    sites = [f for f in fs if f["kind"] == "mem"]
+    assert len(sites) == L + 1
+    for f in sites:
+        assert f["count"] == f["footprint"] == M           # AFR 1: every element once
+        if shape == 0:
+            assert f["lstr"] == (s,) and f["gstr"] == (1, 256 * s)
+        else:
+            assert f["lstr"] == (1, Wd) and f["gstr"] == (16, 16 * Wd)
+    dn = "float32" if dtype == 0 else "float64"
+    assert op(fs, dn, "add") == (L - 1) * N // 32
+
+
+@pytest.mark.parametrize("dtype,o,F", [(0, 0, 64), (0, 1, 128), (0, 2, 1024), (1, 2, 96)])
+def test_fma_counts(dtype, o, F):
+    G = 3
+    fs = features("fma", dtype=dtype, op=o, F=F, G=G)
+    dn = "float32" if dtype == 0 else "float64"
+    nsg = G * 256 // 32
+    target = ("add", "mul", "madd")[o]
+    adds = 32 + 31 + (F if target == "add" else 0)
+    assert op(fs, dn, "add") == adds * nsg
+    if target != "add":
+        assert op(fs, dn, target) == F * nsg
+
+
+@pytest.mark.parametrize("R,sync", [(4, 0), (256, 0), (64, 1)])
+def test_smem_and_barrier_counts(R, sync):
+    fs = features("smem", R=R, sync=sync, G=2)
+    assert feature_value("f_mem_access_local_float32", fs) == (R + 2) * 2 * 8
+    assert single(fs, "sync") == 1 + (R // 4 if sync else 0)
+    b = features("barrier", B=37, G=3)
+    assert single(b, "sync") == 37 and single(b, "groups") == 3
+    o = features("overlap", m=5, N=1024)
+    assert feature_value("f_mem_access_local_float32", o) == 2 * 5 * 1024 // 32
+    e = features("empty", G=64)
+    assert single(e, "groups") == 64 and single(e, "launch") == 1
+    assert [f for f in e if f["kind"] == "mem"] == []
