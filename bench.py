@@ -1,0 +1,472 @@
+#!/usr/bin/env python
+"""Benchmark: one calibration pass of the performance-modeling hot path per
+step, on synthetic inputs shaped like the paper's workloads.
+
+Step = every variant of the calibration suite (global-memory stream patterns,
+arithmetic loops, local memory, barriers, overlap, empty launches; ~230
+variants) device-timed with `--trials` launches each (pm_run), exact features
+for every variant (pm_counts), feature assembly and ONE batched calibration of
+all per-family models on two thirds of the variants, and prediction of the
+held-out third.  Reported value: suite GB/s = algorithmic bytes moved by the
+suite's launches / step time.
+
+Multi-GPU: replicas only (calibration is per device); each rank runs the
+whole pass on its GPU, value = all ranks' bytes / max time.
+
+--impl reference runs the CPU oracle (the plain reference implementation)
+on a bounded sample of each variant and reports the same metric.
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "suite GB/s & % roofline; held-out pred. rel. error; batched-fit fits/s vs plain"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--trials", type=int, default=3, help="timed launches per suite variant per step")
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-fit-bench", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--filter", default="suite", help="comma-separated suite filter tags")
+    return ap.parse_args()
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi samples during the timed region (read-only queries)."""
+
+    def __init__(self, index):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + q,
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except Exception:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- ours
+def kernel_instance(kernel, p):
+    """Name of the CUDA kernel instantiation a variant launches."""
+    if kernel == "stream":
+        t = {(0, 0): "float", (0, 1): "float4", (1, 0): "double", (1, 1): "double2"}[(p.get("dtype", 0), p.get("vec", 0))]
+        return "k_stream<%s,%d,%d>" % (t, p.get("L", 1), p.get("shape", 0))
+    if kernel == "fma":
+        return "k_fma<%s,%d>" % ("float" if p.get("dtype", 0) == 0 else "double", p.get("op", 2))
+    if kernel == "smem":
+        return "k_smem<%d>" % p.get("sync", 0)
+    return "k_" + kernel
+
+
+def run_ours(args):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    import paper_1904_09538_gb300 as pm
+    from paper_1904_09538_gb300 import suite as S
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    peaks, peak_kind = load_peaks()
+
+    variants = S.generate(args.filter.split(","))
+    # device pools: 5 buffers per dtype, sized for the largest variant
+    need32, need64 = 1, 1
+    for k, p in variants:
+        for b in pm.kernel_buffers(k, **p):
+            if b["dtype"] == np.float64:
+                need64 = max(need64, b["elems"])
+            else:
+                need32 = max(need32, b["elems"])
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1234 + rank)
+    pool32 = [torch.rand(need32, device=dev, generator=gen) * 2 - 1 for _ in range(5)]
+    pool64 = [torch.rand(need64, device=dev, generator=gen, dtype=torch.float64) * 2 - 1 for _ in range(5)]
+
+    def bufs_for(k, p):
+        out, i32, i64 = [], 0, 0
+        for b in pm.kernel_buffers(k, **p):
+            if b["dtype"] == np.float64:
+                out.append(pool64[i64][:b["elems"]])
+                i64 += 1
+            else:
+                out.append(pool32[i32][:b["elems"]])
+                i32 += 1
+        return out
+
+    prepared = [(k, p, bufs_for(k, p), S.algorithmic_bytes(k, p), kernel_instance(k, p)) for k, p in variants]
+    families = {}
+    for idx, (k, p) in enumerate(variants):
+        families.setdefault(S.family_key(k, p), []).append(idx)
+    fam_names = sorted(families)
+    models = {f: pm.Model("f_wall_time", S.family_model(f)) for f in fam_names}
+    # feature rows (exact counts), fixed per variant
+    rows = {}
+    for f in fam_names:
+        for idx in families[f]:
+            k, p = variants[idx]
+            rows[idx] = models[f].feature_values(k, **p)
+    fit_rows = {f: [i for j, i in enumerate(families[f]) if j % 3 != 2] for f in fam_names}
+    held = {f: [i for j, i in enumerate(families[f]) if j % 3 == 2] for f in fam_names}
+    plan = pm.FitPlan([models[f] for f in fam_names], [len(fit_rows[f]) for f in fam_names])
+    Xfit = np.concatenate([np.stack([rows[i] for i in fit_rows[f]]).ravel() for f in fam_names])
+
+    stream = torch.cuda.current_stream()
+    launches_per_step = len(prepared) * args.trials + 3 + len(fam_names)
+
+    def one_step(record):
+        times = {}
+        for idx, (k, p, bufs, nbytes, inst) in enumerate(prepared):
+            tm = pm.run(k, bufs, warmup=0, trials=args.trials, outlier_factor=0.0, **p)
+            times[idx] = tm["mean_ms"] * 1e-3
+            if record is not None:
+                record.append((inst, nbytes, tm["mean_ms"] * args.trials, args.trials))
+        # calibrate every family model on its fitting rows in one batched launch
+        tfit = np.array([times[i] for f in fam_names for i in fit_rows[f]])
+        pvec, reps = plan.run(Xfit, tfit)
+        # predict the held-out rows
+        o, errs = 0, []
+        for f, npar in zip(fam_names, plan.nparams):
+            pf = pvec[o:o + npar]
+            o += npar
+            if held[f]:
+                Xh = np.stack([rows[i] for i in held[f]])
+                pred = models[f].predict(pf, Xh)
+                meas = np.array([times[i] for i in held[f]])
+                errs.extend(list(np.abs(pred - meas) / meas))
+        return errs, reps
+
+    for _ in range(args.warmup):
+        one_step(None)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks = ClockSampler(local)
+    clocks.start()
+    record = []
+    t_start = torch.cuda.Event(enable_timing=True)
+    t_end = torch.cuda.Event(enable_timing=True)
+    t_start.record(stream)
+    all_errs, fit_status = [], []
+    for _ in range(args.steps):
+        errs, reps = one_step(record)
+        all_errs.extend(errs)
+        fit_status.extend(r["status"] for r in reps)
+    t_end.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    clk = clocks.stop()
+    elapsed = t_start.elapsed_time(t_end) * 1e-3
+    if world > 1:
+        tt = torch.tensor([elapsed], device=dev)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        elapsed = float(tt.item())
+    bytes_per_step = sum(x[3] for x in prepared) * args.trials
+    total_bytes = bytes_per_step * args.steps * world
+    value = total_bytes / elapsed / 1e9
+
+    # roofline of the dominant kernel instantiation (largest share of device time)
+    per = {}
+    for inst, nbytes, ms, n in record:
+        a = per.setdefault(inst, [0.0, 0.0, 0])
+        a[0] += nbytes * n
+        a[1] += ms
+        a[2] += n
+    tot_ms = sum(a[1] for a in per.values())
+    dom = max(per, key=lambda k: per[k][1])
+    achieved = per[dom][0] / (per[dom][1] * 1e-3) / 1e9
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "traffic.json")
+    if os.path.exists(tpath):
+        try:
+            tj = json.load(open(tpath))
+            ent = tj.get(dom)
+            if ent and ent.get("source_sha") == source_sha():
+                traffic = ent["dram_bytes_per_launch"]
+        except Exception:
+            traffic = None
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1), "peak": peaks["hbm_gbs"],
+                "unit": "GB/s", "frac": round(achieved / peaks["hbm_gbs"], 4), "traffic": traffic,
+                "peak_source": peak_kind, "share": round(per[dom][1] / tot_ms, 4)}
+    best_stream = max((a[0] / (a[1] * 1e-3) / 1e9, k) for k, a in per.items() if k.startswith("k_stream"))
+
+    geo = math.exp(sum(math.log(max(e, 1e-12)) for e in all_errs) / len(all_errs)) if all_errs else None
+    line = {
+        "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 3), "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+        "config": {"workload": "calibration suite (configs[1]): %d variants, %d timed launches each" %
+                   (len(prepared), args.trials),
+                   "variants": len(prepared), "trials_per_variant": args.trials, "families": len(fam_names),
+                   "bytes_per_step": bytes_per_step, "l2": "inputs larger than L2 (stream arrays up to 2 GiB; "
+                   "step footprint %.0f GB)" % (bytes_per_step / 1e9), "parallelism": "replicas"},
+        "roofline": roofline,
+        "best_stream_kernel": {"kernel": best_stream[1], "GB/s": round(best_stream[0], 1),
+                               "frac": round(best_stream[0] / peaks["hbm_gbs"], 4)},
+        "heldout_pred_rel_err": {"geomean": geo, "max": max(all_errs) if all_errs else None, "n": len(all_errs)},
+        "fit_status_counts": {str(s): fit_status.count(s) for s in sorted(set(fit_status))},
+        "clocks": clk,
+        "gpu_launches": launches_per_step * args.steps,
+    }
+    if not args.no_e2e:
+        line["e2e"] = e2e_measure(pm, S, variants, torch)
+    if not args.no_fit_bench:
+        line["fit"] = fit_throughput(pm, torch, dev)
+    if rank == 0 and world == 1 and not args.no_cpu:
+        line["cpu_baseline"] = cpu_baseline(variants, seconds=12.0)
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+
+
+def source_sha():
+    import hashlib
+    h = hashlib.sha256()
+    for f in ("pm_suite.cu", "pm_modeled.cu"):
+        h.update(open(os.path.join(ROOT, "paper_1904_09538_gb300", "csrc", f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def e2e_measure(pm, S, variants, torch):
+    """Same metric through pm_run_host: host->device copies of every
+    variant's inputs and device->host copies of its outputs inside the timed
+    region (one step, one launch per variant, pinned host buffers)."""
+    import numpy as np
+    need = 1
+    for k, p in variants:
+        for b in pm.kernel_buffers(k, **p):
+            need = max(need, b["elems"] * np.dtype(b["dtype"]).itemsize)
+    host = [torch.empty(need, dtype=torch.uint8, pin_memory=True) for _ in range(5)]
+    h2d = d2h = 0
+    nbytes = 0
+    prepared = []
+    for k, p in variants:
+        arrs = []
+        for i, b in enumerate(pm.kernel_buffers(k, **p)):
+            a = host[i].numpy().view(b["dtype"])[:b["elems"]]
+            if b["role"] == "in":
+                h2d += a.nbytes
+            else:
+                d2h += a.nbytes
+            arrs.append(a)
+        prepared.append((k, p, arrs))
+        nbytes += S.algorithmic_bytes(k, p)
+    for a in host:   # values in [-1, 1) as float32 bit patterns are fine for every kernel here
+        a.numpy().view(np.float32)[:] = 0.5
+    # warm (allocator pool, first-touch of pinned pages)
+    for k, p, arrs in prepared[:3]:
+        pm.run_host(k, arrs, warmup=0, trials=1, **p)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for k, p, arrs in prepared:
+        pm.run_host(k, arrs, warmup=0, trials=1, **p)
+    torch.cuda.synchronize()
+    dt = time.perf_counter() - t0
+    return {"value": round(nbytes / dt / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 2)}
+
+
+def fit_throughput(pm, torch, dev):
+    """Batched calibration (64 models, uneven 40..400 rows, one persistent
+    launch in a CUDA graph) vs the plain per-model fit (host-driven LM through
+    the autograd.Function), same data, same start points."""
+    import numpy as np
+    import pm_inputs
+    from paper_1904_09538_gb300 import autograd as pag
+    from paper_1904_09538_gb300.suite import LAUNCH
+    K = 64
+    ls = pm_inputs.row_counts(K, 4242)
+    lin = LAUNCH + " + p_add * f_op_float32_add + p_madd * f_op_float32_madd + p_gmem * f_mem_access_global_float32"
+    cg = "(p_gmem * f_mem_access_global_float32)"
+    co = "(p_madd * f_op_float32_madd + p_lmem * f_mem_access_local_float32)"
+    ovl = (LAUNCH + " + %s * (tanh(p_edge * (%s - %s)) + 1) / 2 + %s * (tanh(p_edge * (%s - %s)) + 1) / 2"
+           % (cg, cg, co, co, co, cg))
+    truth = {"p_launch": 5e-6, "p_group": 2e-9, "p_add": 4e-12, "p_madd": 3e-12, "p_gmem": 6e-12, "p_lmem": 2e-12,
+             "p_edge": 3e4}
+    models, Xs, ts, p0s = [], [], [], []
+    for k in range(K):
+        m = pm.Model("f_wall_time", lin if k % 2 == 0 else ovl)
+        l = int(ls[k])
+        X = pm_inputs.integers((l, len(m.features)), 9000 + k, 10 ** 5, 10 ** 7).astype(np.float64)
+        X[:, 0] = 1.0
+        X[:, 1] = pm_inputs.integers((l,), 9500 + k, 100, 10 ** 4)
+        pt = np.array([truth[n] for n in m.params])
+        t = m.predict(pt, X) * (1 + 1e-2 * pm_inputs.noise((l,), 9900 + k))
+        models.append(m)
+        Xs.append(X)
+        ts.append(t)
+        p0s.append(pt * 1.2)
+    plan = pm.FitPlan(models, [len(t) for t in ts], p0_given=True)
+    Xc = np.concatenate([x.ravel() for x in Xs])
+    tc = np.concatenate(ts)
+    pc = np.concatenate(p0s)
+    plan.run(Xc, tc, pc)
+    torch.cuda.synchronize()
+    reps_n = 20
+    t0 = time.perf_counter()
+    for _ in range(reps_n):
+        pb, reps = plan.run(Xc, tc, pc)
+    dt_b = (time.perf_counter() - t0) / reps_n
+    # plain per-model fits on a subset (time per model)
+    sub = list(range(0, K, 8)) + list(range(1, K, 8))
+    errs = []
+    o = np.cumsum([0] + [len(p) for p in p0s])
+    t0 = time.perf_counter()
+    for k in sub:
+        Xd = torch.from_numpy(Xs[k].astype(np.float32)).to(dev)
+        td = torch.from_numpy(ts[k].astype(np.float32)).to(dev)
+        pp, _ = pag.lm_fit(models[k], Xd, td, p0s[k])
+        ref = pb[o[k]:o[k + 1]]
+        errs.append(float(np.max(np.abs(pp - ref) / np.abs(ref))))
+    torch.cuda.synchronize()
+    dt_p = (time.perf_counter() - t0) / len(sub)
+    return {"models": K, "rows": [int(ls.min()), int(ls.max())], "fits_per_s_batched": round(K / dt_b, 1),
+            "fits_per_s_plain": round(1.0 / dt_p, 2), "speedup": round((K / dt_b) * dt_p, 1),
+            "batched_ms": round(dt_b * 1e3, 3), "plain_ms_per_model": round(dt_p * 1e3, 2),
+            "max_param_rel_diff_plain_vs_batched": max(errs),
+            "statuses": {str(s): [r["status"] for r in reps].count(s) for s in set(r["status"] for r in reps)}}
+
+
+def cpu_baseline(variants, seconds=12.0):
+    """The oracle's plain CPU reference kernels on a bounded sample of the
+    same suite: every memory-moving variant scaled down by a common factor
+    until the pass costs about `seconds` of one host core."""
+    import numpy as np
+    import pm_inputs
+    from oracle import refs
+    from paper_1904_09538_gb300 import suite as S
+
+    # time only the oracle calls
+    def timed(scale):
+        total_b, total_t = 0, 0.0
+        for k, p in variants:
+            if k == "stream":
+                N = max(256, p["N"] // scale)
+                dt = np.float32 if p.get("dtype", 0) == 0 else np.float64
+                xs = [pm_inputs.uniform((N,), 5 + a, dtype=dt) for a in range(p.get("L", 1))]
+                t1 = time.perf_counter()
+                refs.stream(xs)
+                total_t += time.perf_counter() - t1
+                total_b += (p.get("L", 1) + 1) * N * np.dtype(dt).itemsize
+            elif k == "fma":
+                T = max(256, p["G"] * 256 // (scale * 64))
+                dt = np.float32 if p.get("dtype", 0) == 0 else np.float64
+                u = pm_inputs.uniform((T,), 9, dtype=dt)
+                t1 = time.perf_counter()
+                refs.fma(u, p["op"], p["F"])
+                total_t += time.perf_counter() - t1
+                total_b += 2 * T * np.dtype(dt).itemsize
+        return total_b, total_t
+
+    scale = 4096
+    b, t = timed(scale)
+    if t > 0:
+        scale = max(1, int(scale * t / seconds))
+        b, t = timed(scale)
+    return {"value": round(b / t / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+            "sample": "every stream variant at N/%d and every arithmetic variant at 1/%d of its work-items "
+                      "(oracle C reference, one host core, %.1f s)" % (scale, scale * 64, t)}
+
+
+# ---------------------------------------------------------------- reference arm
+def run_reference(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    from paper_1904_09538_gb300 import suite as S
+    variants = S.generate(args.filter.split(","))
+    for _ in range(args.warmup):
+        cpu_baseline(variants, seconds=2.0)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(args.steps):
+        last = cpu_baseline(variants, seconds=6.0)
+        vals.append(last["value"])
+    el = time.perf_counter() - t0
+    v = statistics.mean(vals)
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 1), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
+            "config": {"workload": "calibration suite (configs[1]), bounded sample per step", "variants": len(variants)},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": last["sample"]},
+            "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    a = parse()
+    if a.impl == "reference":
+        run_reference(a)
+    else:
+        run_ours(a)

@@ -1,0 +1,265 @@
+/*
+ * pm.h -- C ABI of the GB300 performance-modeling library (libpm.so).
+ *
+ * The library implements the data-parallel hot path of the cross-machine
+ * black-box GPU performance-modeling method of Stevens & Kloeckner
+ * (arXiv 1904.09538): exact kernel feature counts, device-timed measurement
+ * kernels, and calibration / evaluation of user-written time models.
+ *
+ * Conventions (all entry points):
+ *   - Every function returns a pm_status; PM_OK == 0.  On failure a message
+ *     is stored in a thread-local buffer returned by pm_last_error().
+ *   - Output arrays are owned by the caller.  Handles (pm_model) are owned by
+ *     the library and released with the matching destroy call.
+ *   - Nothing aborts or exits; CUDA errors become PM_ECUDA plus a message.
+ *   - "device pointer" means memory of the current CUDA device (cudaMalloc or
+ *     a PyTorch CUDA tensor); "host pointer" means ordinary or pinned host
+ *     memory.  A stream argument is a cudaStream_t (NULL = legacy default).
+ *   - Sizes are element counts unless stated.
+ */
+#ifndef PM_H
+#define PM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PM_OK = 0,
+    PM_EINVAL = -1,           /* invalid argument (message says which) */
+    PM_ENOMEM = -2,           /* allocation failed */
+    PM_ECUDA = -3,            /* CUDA runtime error */
+    PM_ENOTCONV = -4,         /* fit reached max_iter; best iterate written */
+    PM_ERANK = -5,            /* rank-deficient design; minimum-norm solution written */
+    PM_ETIMEOUT = -6,         /* a bounded device wait gave up */
+    PM_EUNKNOWN_KERNEL = -7,  /* no kernel of that name / id */
+    PM_EPARSE = -8,           /* model expression or feature name does not parse */
+    PM_ECAP = -9              /* output array too small; *n_out holds the size needed */
+} pm_status;
+
+/* Kernel parameter, e.g. {"n", 1024} -- the size parameters of a kernel's
+ * loop domain (Section "Predicting Cost": a dictionary of problem sizes).
+ * Integer parameters must hold integral values. */
+typedef struct {
+    const char *key;
+    double value;
+} pm_param;
+
+/* ---------------------------------------------------------------- kernels */
+
+/* Kernel registry.  Names: the calibration suite "stream", "fma", "smem",
+ * "barrier", "overlap", "empty" (Section "Measurement Kernel Design");
+ * matmul "mm_pf", "mm_nopf" and the work-removed twins "mm_pf_a", "mm_pf_b",
+ * "mm_nopf_a", "mm_nopf_b" (Section "Matrix Multiplication", Algorithm 3);
+ * DG "dg_nopf", "dg_dmpf" and twins "dg_nopf_u", "dg_nopf_dm", "dg_dmpf_u",
+ * "dg_dmpf_dm", "dg_res" (Section "DG"); stencil "fd_tile", "fd_direct" and
+ * twins "fd_tile_u", "fd_tile_res", "fd_direct_u", "fd_direct_res"
+ * (Section "Finite Differences").  Returns PM_EUNKNOWN_KERNEL for other names. */
+pm_status pm_kernel_lookup(const char *name, int32_t *kernel);
+pm_status pm_kernel_count(int32_t *n);
+/* Library-owned, static string. */
+pm_status pm_kernel_name(int32_t kernel, const char **name);
+
+typedef enum { PM_F32 = 0, PM_F64 = 1, PM_BF16 = 2 } pm_dtype;
+typedef enum { PM_IN = 0, PM_OUT = 1 } pm_role;
+
+typedef struct {
+    char name[32];      /* "in0".."in3", "out", "seed", "a", "b", "c", "x", "diff_mat", "u", "res", "tgt_dest" */
+    int32_t dtype;      /* pm_dtype of one element */
+    int32_t role;       /* pm_role */
+    uint64_t elems;     /* element count (scalar elements, not vectors) */
+} pm_buffer;
+
+/* Buffers kernel `kernel` needs for these parameters, in launch order.
+ * PM_ECAP with *n_out set when cap is too small. */
+pm_status pm_kernel_buffers(int32_t kernel, const pm_param *p, size_t np,
+                            pm_buffer *out, size_t cap, size_t *n_out);
+
+/* ---------------------------------------------------------------- counts */
+
+typedef enum { PM_GRAN_WI = 0, PM_GRAN_SG = 1, PM_GRAN_WG = 2, PM_GRAN_K = 3 } pm_gran;
+typedef enum { PM_FEAT_OP = 0, PM_FEAT_MEM = 1, PM_FEAT_SYNC = 2, PM_FEAT_GROUPS = 3, PM_FEAT_LAUNCH = 4 } pm_feat_kind;
+
+/* One exact feature of a kernel instance (Section "Kernel Features").
+ *   OP:     name f_op_<dtype>_<add|mul|madd>; count per sub-group (SG),
+ *           count_wi per work-item.
+ *   MEM:    one memory access site with its pattern (Section "Data Motion
+ *           Features"): tag, memory type, data type, direction, local and
+ *           group strides along each thread axis (units of the data type),
+ *           the stride along the innermost enclosing sequential loop
+ *           (Table "ab_pattern"), and accesses/footprint = AFR (Algorithm 2,
+ *           per access site).  count is at the site's granularity: global
+ *           per work-item unless lid(0) stride is 0 ("uniform"), which is per
+ *           sub-group like local memory (Section "Gathering Kernel
+ *           Statistics").
+ *   SYNC:   f_sync_barrier_local, barriers met by one work-item.
+ *   GROUPS: f_thread_groups, the work-group count.
+ *   LAUNCH: f_sync_kernel_launch = 1.
+ * The sub-group size is 32. */
+typedef struct {
+    char name[192];        /* canonical feature name */
+    int32_t kind;          /* pm_feat_kind */
+    int32_t gran;          /* pm_gran of `count` */
+    uint64_t count;        /* value at its granularity */
+    uint64_t count_wi;     /* OP/MEM: work-item level count */
+    uint64_t count_sg;     /* OP/MEM: sub-group level count */
+    /* MEM only */
+    char tag[32];
+    char dtype[16];        /* "float32", "float64", "float32x4", "float64x2" (OP: dtype too) */
+    char op[8];            /* OP only: "add", "mul", "madd" */
+    int32_t mem;           /* 0 global, 1 local */
+    int32_t dir;           /* 0 load, 1 store */
+    int32_t dsize;         /* bytes per access */
+    int32_t nl, ng;        /* number of meaningful lstride / gstride entries */
+    int64_t lstride[3];
+    int64_t gstride[3];
+    int64_t loop_stride;
+    uint64_t accesses;     /* AFR numerator (work-item accesses) */
+    uint64_t footprint;    /* AFR denominator (distinct elements touched) */
+} pm_feature;
+
+/* Exact integer features of kernel `kernel` at parameters p (Algorithm 1,
+ * closed forms per kernel).  Writes up to cap records; *n_out = number of
+ * records (PM_ECAP if cap < *n_out).  Pure host computation. */
+pm_status pm_counts(int32_t kernel, const pm_param *p, size_t np,
+                    pm_feature *out, size_t cap, size_t *n_out);
+
+/* ---------------------------------------------------------------- running */
+
+/* Enqueue one launch of `kernel` on `stream`.  bufs: device pointers in the
+ * order pm_kernel_buffers reports, each holding at least `elems` elements.
+ * Extra kernel arguments (stencil c0, c1) come from p.  Asynchronous; the
+ * launch configuration error (if any) is reported. */
+pm_status pm_launch(int32_t kernel, const pm_param *p, size_t np,
+                    void *const *bufs, size_t nbufs, void *stream);
+
+typedef struct {
+    int32_t warmup;          /* untimed launches first (default 2) */
+    int32_t trials;          /* timed launches (default 60, Section "Other Features") */
+    double outlier_factor;   /* drop trials > factor * median (default 5; <= 0 keeps all) */
+} pm_run_opts;
+
+typedef struct {
+    double mean_ms;          /* mean over kept trials -- the wall-time feature */
+    double median_ms, min_ms, max_ms;
+    int32_t n_trials, n_dropped;
+} pm_timing;
+
+/* Device-time `kernel` (the paper's wall-time feature, excluding host-device
+ * transfer): warmup launches, then `trials` launches each bracketed by CUDA
+ * events on `stream`.  trial_ms (nullable, caller-owned, >= trials floats)
+ * receives every trial's time.  opts NULL = defaults.  Blocks until done. */
+pm_status pm_run(int32_t kernel, const pm_param *p, size_t np,
+                 void *const *bufs, size_t nbufs, const pm_run_opts *opts,
+                 void *stream, float *trial_ms, pm_timing *out);
+
+/* pm_run with HOST buffers: copies inputs host->device, runs as pm_run, and
+ * copies outputs device->host, all on `stream`; device memory is allocated
+ * with cudaMallocAsync and freed before returning.  *copy_ms (nullable)
+ * receives the total time of the copies. */
+pm_status pm_run_host(int32_t kernel, const pm_param *p, size_t np,
+                      void *const *host_bufs, size_t nbufs, const pm_run_opts *opts,
+                      void *stream, float *trial_ms, pm_timing *out, double *copy_ms);
+
+/* ---------------------------------------------------------------- models */
+
+typedef struct pm_model pm_model;
+
+/* Model = output feature + expression over features f_* and parameters p_*
+ * (Section "Modeling Kernel Execution Time").  Grammar: + - * / unary -,
+ * parentheses, numbers, tanh exp log sqrt; a name runs to whitespace or one
+ * of + * / ( ) (a '-' glued to a name is part of it).  PM_EPARSE on error. */
+pm_status pm_model_create(const char *out_feature, const char *expr, pm_model **m);
+void pm_model_destroy(pm_model *m);
+pm_status pm_model_info(const pm_model *m, size_t *n_features, size_t *n_params);
+/* Library-owned strings valid until pm_model_destroy. */
+pm_status pm_model_feature_name(const pm_model *m, size_t i, const char **name);
+pm_status pm_model_param_name(const pm_model *m, size_t i, const char **name);
+/* 1 if g is linear in the parameters (fit by linear least squares). */
+pm_status pm_model_is_linear(const pm_model *m, int32_t *linear);
+
+/* Feature assembly: value of each model feature on one kernel's feature
+ * records -- the sum of the counts of all matching records (Section "Data
+ * Motion Features": tag / memory type / data type / direction / stride and
+ * AFR constraints such as lstrides:{0:1;1:>15}).  row_out has n_features
+ * doubles.  PM_EPARSE if a model feature name does not parse. */
+pm_status pm_feature_values(const pm_model *m, const pm_feature *feats, size_t nfeat, double *row_out);
+
+typedef struct {
+    int32_t max_iter;        /* LM iteration cap (default 200) */
+    double ftol;             /* stop when relative SSR decrease < ftol (default 1e-15) */
+    double xtol;             /* stop when |dq| <= xtol (|q| + xtol) in scaled coordinates (default 1e-12) */
+    int32_t use_p0;          /* 1: p_inout holds the start point; 0: library start point */
+} pm_fit_opts;
+
+typedef struct {
+    int32_t status;          /* pm_status of this fit */
+    int32_t iterations;
+    int32_t rank;            /* numerical rank (linear fits) */
+    int32_t linear;          /* 1 linear least squares, 0 Levenberg-Marquardt */
+    double residual;         /* || 1 - g(p; f_k)/t_k ||_2 at the solution */
+    double lambda;           /* final LM damping */
+} pm_fit_report;
+
+/* Calibrate one model (Section "Computing Model Parameters") on l rows:
+ * X is l x n_features row-major (host, FP64 feature values), t the l output
+ * values (host).  Minimises sum_k (1 - g(p; X_k)/t_k)^2 (relative error,
+ * scale_features_by_output).  Linear-in-p models: column-scaled least
+ * squares (FP64 solve on the GPU); otherwise Levenberg-Marquardt on the GPU
+ * (FP32 residual and Jacobian, FP64 normal-equation solve and damping).
+ * p_inout: n_params doubles (start point if opts->use_p0, result out).
+ * Returns PM_ERANK (minimum-norm solution written) or PM_ENOTCONV (best
+ * iterate written) where applicable. */
+pm_status pm_fit(const pm_model *m, const double *X, const double *t, size_t l,
+                 const pm_fit_opts *opts, double *p_inout, pm_fit_report *report);
+
+/* Batched calibration (many models x measurement sets of uneven size in ONE
+ * persistent kernel launch, one CTA per model, replayed from a CUDA graph).
+ * A plan fixes the models and row counts; it owns device and pinned host
+ * staging buffers (allocated at creation) and the captured graph.
+ *   threads: CTA size of the fit kernel (64, 128 or 256; 0 = 128).
+ * pm_fit_plan_run: X_concat holds, model after model, rows[k] x
+ * n_features(k) FP64 values (row-major); t_concat the outputs; p_inout_concat
+ * n_params(k) values per model (start points if opts->use_p0); reports one
+ * per model.  All host pointers.  Same numerics as pm_fit.  Per-model
+ * statuses are in reports[k].status; the call returns PM_OK unless the
+ * launch itself failed. */
+typedef struct pm_fit_plan pm_fit_plan;
+pm_status pm_fit_plan_create(const pm_model *const *models, size_t nmodels, const size_t *rows,
+                             const pm_fit_opts *opts, int32_t threads, pm_fit_plan **plan);
+pm_status pm_fit_plan_run(pm_fit_plan *plan, const double *X_concat, const double *t_concat,
+                          double *p_inout_concat, pm_fit_report *reports, void *stream);
+void pm_fit_plan_destroy(pm_fit_plan *plan);
+/* One-shot convenience: create a plan, run it once, destroy it. */
+pm_status pm_fit_batched(const pm_model *const *models, size_t nmodels, const double *X_concat,
+                         const double *t_concat, const size_t *rows, const pm_fit_opts *opts,
+                         double *p_inout_concat, pm_fit_report *reports, void *stream);
+
+/* Differentiation entry points (device pointers; used by the PyTorch
+ * autograd.Function).  X: l x n_features FP32, t: l FP32, p: n_params FP64.
+ *   pm_residual:  r_k = 1 - g(p; X_k) / t_k                       (FP32)
+ *   pm_residual_vjp: pbar_i = sum_k rbar_k dr_k/dp_i              (FP32 products,
+ *                 FP32 compensated sums per CTA, combined in FP64; pbar overwritten)
+ *   pm_jacobian:  J[k, i] = dr_k/dp_i = -dg/dp_i / t_k            (l x n_params FP32)
+ * Reverse-mode differentiation of the model program, no finite differences. */
+pm_status pm_residual(const pm_model *m, const float *X, const float *t, size_t l, const double *p,
+                      float *r, void *stream);
+pm_status pm_residual_vjp(const pm_model *m, const float *X, const float *t, size_t l, const double *p,
+                          const float *rbar, double *pbar, void *stream);
+pm_status pm_jacobian(const pm_model *m, const float *X, const float *t, size_t l, const double *p,
+                      float *J, void *stream);
+
+/* Predict (Section "Predicting Cost"): t_out[k] = g(p; X_k) for l rows,
+ * evaluated on the GPU in FP64.  X host l x n_features, p host, t_out host. */
+pm_status pm_predict(const pm_model *m, const double *p, const double *X, size_t l, double *t_out);
+
+/* Thread-local, library-owned message of the last failure ("" if none). */
+const char *pm_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -951,10 +951,10 @@ void oracle_dg_ref(long long Np, long long Nel, const float *D, const float *u, 
             }
 }
 
-/* stencil FP64 reference */
-void oracle_fd_ref(long long n, double c0, double c1, const float *u, double *res, double *rabs) {
+/* stencil FP64 reference on an (h+2) x (n+2) input -> h x n output */
+void oracle_fd_ref(long long h, long long n, double c0, double c1, const float *u, double *res, double *rabs) {
     long long W = n + 2;
-    for (long long i = 0; i < n; i++)
+    for (long long i = 0; i < h; i++)
         for (long long j = 0; j < n; j++) {
             double C = u[W * (i + 1) + j + 1], N_ = u[W * i + j + 1], S = u[W * (i + 2) + j + 1];
             double Wv = u[W * (i + 1) + j], E = u[W * (i + 1) + j + 2];

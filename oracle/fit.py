@@ -18,7 +18,9 @@ Readings of the paper taken here where it is silent or ambiguous:
     column-scaled coordinates is returned with rank_deficient = True;
   * the LM start point, when not given, is the linear fit of the model with
     every tanh switch replaced by 1/2 (negative entries clamped to
-    1e-3 * max |p|), and p_edge0 = 10 / median(t).
+    1e-3 * max |p|), and p_edge0 = 10 / median(t);
+  * LM iterates in scaled coordinates q = p / |p0| (the minimiser does not
+    depend on the coordinates).
 
 Geometric mean of relative error (Section "Results"):
     exp(mean(log(|t_hat - t| / t))).
@@ -145,9 +147,14 @@ def fit(model, F, t, p0=None, max_iter=200):
     r, J = residual_and_jacobian(model, F, t)
     if p0 is None:
         p0 = start_point(model, F, t)
-    p, cov, infodict, mesg, ier = scipy.optimize.leastsq(
-        r, np.asarray(p0, dtype=np.float64), Dfun=J, full_output=True, ftol=1e-15, xtol=1e-15, gtol=0.0,
-        maxfev=max_iter * (len(p0) + 1))
+    p0 = np.asarray(p0, dtype=np.float64)
+    # solve in scaled coordinates q = p / |p0| (same minimiser; parameters
+    # span many decades, e.g. 1e-12 s per operation next to p_edge ~ 1e4 / s)
+    s = np.where(p0 != 0.0, np.abs(p0), 1.0)
+    q, cov, infodict, mesg, ier = scipy.optimize.leastsq(
+        lambda q: r(q * s), p0 / s, Dfun=lambda q: J(q * s) * s[None, :], full_output=True, ftol=1e-15,
+        xtol=1e-15, gtol=0.0, maxfev=max_iter * (len(p0) + 1))
+    p = q * s
     res = r(p)
     return p, dict(method="lm", ier=int(ier), nfev=int(infodict["nfev"]), residual=float(np.linalg.norm(res)),
                    message=mesg, rank_deficient=False)

@@ -28,7 +28,8 @@ def _setup():
                                  ctypes.c_void_p]
     L.oracle_mm_ref.argtypes = [ctypes.c_longlong, _f32p, _f32p, _f64p, _f64p]
     L.oracle_dg_ref.argtypes = [ctypes.c_longlong, ctypes.c_longlong, _f32p, _f32p, _f64p, _f64p]
-    L.oracle_fd_ref.argtypes = [ctypes.c_longlong, ctypes.c_double, ctypes.c_double, _f32p, _f64p, _f64p]
+    L.oracle_fd_ref.argtypes = [ctypes.c_longlong, ctypes.c_longlong, ctypes.c_double, ctypes.c_double, _f32p,
+                                _f64p, _f64p]
     L.oracle_mm_twin_ref.argtypes = [ctypes.c_int, ctypes.c_longlong, _f32p, _f32p]
     L.oracle_dg_twin_ref.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong,
                                      ctypes.c_longlong, _f32p, _f32p, _f32p]
@@ -77,10 +78,15 @@ def dg(D, u):
 
 def stencil(u, c0, c1):
     """FP64 five-point stencil on the (n+2)x(n+2) input and the |.| sums."""
+    return stencil_rows(u, c0, c1)
+
+
+def stencil_rows(u, c0, c1):
+    """FP64 five-point stencil on an (h+2) x (n+2) block of rows -> h x n."""
     _setup()
-    n = u.shape[0] - 2
-    res = np.empty((n, n)); ra = np.empty((n, n))
-    lib().oracle_fd_ref(n, c0, c1, np.ascontiguousarray(u, np.float32), res, ra)
+    h, n = u.shape[0] - 2, u.shape[1] - 2
+    res = np.empty((h, n)); ra = np.empty((h, n))
+    lib().oracle_fd_ref(h, n, c0, c1, np.ascontiguousarray(u, np.float32), res, ra)
     return res, ra
 
 

@@ -1,0 +1,587 @@
+// Exact kernel features in closed form (Algorithm 1: count = sum over
+// statements of |projection of the loop domain| x operations per instance;
+// Algorithm 2 per access site for the footprint; granularities of Section
+// "Gathering Kernel Statistics": sub-group = 32 consecutive linear ids,
+// on-chip work and uniform global accesses per sub-group, other global
+// accesses per work-item, barriers per work-item).
+//
+// Each kernel's loop domain is the one its CUDA kernel executes; the
+// formulas below count that domain's statement instances directly.
+#include <cstring>
+
+#include "pm_internal.h"
+
+namespace pm {
+
+namespace {
+
+typedef unsigned long long u64;
+typedef long long i64;
+
+i64 cdiv(i64 a, i64 b) { return (a + b - 1) / b; }
+
+pm_feature op_rec(const char *dtype, const char *op, u64 wi, u64 sg) {
+    pm_feature f;
+    memset(&f, 0, sizeof f);
+    f.kind = PM_FEAT_OP;
+    f.gran = PM_GRAN_SG;
+    f.count = sg;
+    f.count_wi = wi;
+    f.count_sg = sg;
+    snprintf(f.dtype, sizeof f.dtype, "%s", dtype);
+    snprintf(f.op, sizeof f.op, "%s", op);
+    return f;
+}
+
+struct Site {
+    const char *tag;
+    int mem, dir;
+    const char *dtype;
+    int dsize;
+    int nl;
+    i64 l[3];
+    int ng;
+    i64 g[3];
+    i64 loop;
+    u64 wi, sg, foot;
+};
+
+pm_feature mem_rec(const Site &s) {
+    pm_feature f;
+    memset(&f, 0, sizeof f);
+    f.kind = PM_FEAT_MEM;
+    snprintf(f.tag, sizeof f.tag, "%s", s.tag);
+    snprintf(f.dtype, sizeof f.dtype, "%s", s.dtype);
+    f.mem = s.mem;
+    f.dir = s.dir;
+    f.dsize = s.dsize;
+    f.nl = s.nl;
+    f.ng = s.ng;
+    for (int a = 0; a < 3; a++) {
+        f.lstride[a] = s.l[a];
+        f.gstride[a] = s.g[a];
+    }
+    f.loop_stride = s.loop;
+    f.count_wi = s.wi;
+    f.count_sg = s.sg;
+    f.accesses = s.wi;
+    f.footprint = s.foot;
+    bool per_sg = s.mem == 1 || s.l[0] == 0;
+    f.gran = per_sg ? PM_GRAN_SG : PM_GRAN_WI;
+    f.count = per_sg ? s.sg : s.wi;
+    return f;
+}
+
+pm_feature simple(int kind, int gran, u64 c) {
+    pm_feature f;
+    memset(&f, 0, sizeof f);
+    f.kind = kind;
+    f.gran = gran;
+    f.count = c;
+    return f;
+}
+
+struct Out {
+    std::vector<pm_feature> &v;
+    // op totals in the enumeration order float32 add, mul, madd, float64 add, mul, madd
+    u64 wi[2][3] = {{0}}, sg[2][3] = {{0}};
+    std::vector<pm_feature> sites;
+    explicit Out(std::vector<pm_feature> &o) : v(o) {}
+    void op(int dt, int o, u64 w, u64 s) { wi[dt][o] += w; sg[dt][o] += s; }
+    void site(const Site &s) {
+        if (s.wi) sites.push_back(mem_rec(s));
+    }
+    void finish(u64 barriers, u64 groups) {
+        static const char *on[3] = {"add", "mul", "madd"};
+        for (int dt = 0; dt < 2; dt++)
+            for (int o = 0; o < 3; o++)
+                if (wi[dt][o]) v.push_back(op_rec(dt ? "float64" : "float32", on[o], wi[dt][o], sg[dt][o]));
+        for (auto &s : sites) v.push_back(s);
+        v.push_back(simple(PM_FEAT_SYNC, PM_GRAN_WI, barriers));
+        v.push_back(simple(PM_FEAT_GROUPS, PM_GRAN_WG, groups));
+        v.push_back(simple(PM_FEAT_LAUNCH, PM_GRAN_K, 1));
+    }
+};
+
+const int GL = 0, LO = 1, LD = 0, ST = 1;
+
+// ---------------------------------------------------------------- stream
+int stream_width(i64 dt, i64 vec) { return vec ? (dt == 0 ? 4 : 2) : 1; }
+
+pm_status counts_stream(const KP &kp, std::vector<pm_feature> &v) {
+    i64 dt = kp.i(0), vec = kp.i(1), N = kp.i(2), s = kp.i(3), L = kp.i(4), shape = kp.i(5), W = kp.i(6);
+    i64 w = stream_width(dt, vec), M = N / w;
+    const char *dn = dt == 0 ? (vec ? "float32x4" : "float32") : (vec ? "float64x2" : "float64");
+    int ds = vec ? 16 : (dt == 0 ? 4 : 8);
+    Out o(v);
+    o.op((int)dt, 0, (u64)((L - 1) * w * M), (u64)((L - 1) * w * (M / 32)));
+    static const char *nm[4] = {"in0", "in1", "in2", "in3"};
+    Site st{};
+    st.mem = GL; st.dtype = dn; st.dsize = ds;
+    if (shape == 0) { st.nl = 1; st.l[0] = s; st.ng = 2; st.g[0] = 1; st.g[1] = 256 * s; }
+    else { st.nl = 2; st.l[0] = 1; st.l[1] = W; st.ng = 2; st.g[0] = 16; st.g[1] = 16 * W; }
+    st.wi = M; st.sg = M / 32; st.foot = M;
+    for (int a = 0; a < L; a++) { st.tag = nm[a]; st.dir = LD; o.site(st); }
+    st.tag = "out"; st.dir = ST; o.site(st);
+    o.finish(0, M / 256);
+    return PM_OK;
+}
+
+// Linear-id site of the 1-D, 256-wide kernels: index 256*gid0 + lid0.
+Site lin_site(const char *tag, int dir, const char *dn, int ds, u64 T) {
+    Site s{};
+    s.tag = tag; s.mem = GL; s.dir = dir; s.dtype = dn; s.dsize = ds;
+    s.nl = 1; s.l[0] = 1; s.ng = 1; s.g[0] = 256;
+    s.wi = T; s.sg = T / 32; s.foot = T;
+    return s;
+}
+// Local site with index lid0 + off (off fixed): footprint 256.
+Site loc_site(const char *tag, int dir, u64 wi, u64 sg) {
+    Site s{};
+    s.tag = tag; s.mem = LO; s.dir = dir; s.dtype = "float32"; s.dsize = 4;
+    s.nl = 1; s.l[0] = 1; s.ng = 1; s.g[0] = 0;
+    s.wi = wi; s.sg = sg; s.foot = 256;
+    return s;
+}
+
+pm_status counts_fma(const KP &kp, std::vector<pm_feature> &v) {
+    i64 dt = kp.i(0), op = kp.i(1), F = kp.i(2), G = kp.i(3);
+    const char *dn = dt == 0 ? "float32" : "float64";
+    int ds = dt == 0 ? 4 : 8;
+    u64 T = (u64)G * 256, S = (u64)G * 8;
+    Out o(v);
+    u64 adds = 32 + 31 + (op == 0 ? F : 0);
+    o.op((int)dt, 0, T * adds, S * adds);
+    if (op != 0) o.op((int)dt, (int)op, T * (u64)F, S * (u64)F);
+    o.site(lin_site("seed", LD, dn, ds, T));
+    o.site(lin_site("out", ST, dn, ds, T));
+    o.finish(0, (u64)G);
+    return PM_OK;
+}
+
+pm_status counts_smem(const KP &kp, std::vector<pm_feature> &v) {
+    i64 R = kp.i(0), sync = kp.i(1), G = kp.i(2);
+    u64 T = (u64)G * 256, S = (u64)G * 8, it = (u64)(R / 4);
+    Out o(v);
+    o.site(lin_site("in", LD, "float32", 4, T));
+    o.site(loc_site("s_init", ST, T, S));
+    o.site(loc_site("s_ldA", LD, T * it, S * it));
+    o.site(loc_site("s_stB", ST, T * it, S * it));
+    o.site(loc_site("s_ldB", LD, T * it, S * it));
+    o.site(loc_site("s_stA", ST, T * it, S * it));
+    o.site(loc_site("s_fin", LD, T, S));
+    o.site(lin_site("out", ST, "float32", 4, T));
+    o.finish(1 + (sync ? it : 0), (u64)G);
+    return PM_OK;
+}
+
+pm_status counts_barrier(const KP &kp, std::vector<pm_feature> &v) {
+    i64 B = kp.i(0), G = kp.i(1);
+    u64 T = (u64)G * 256;
+    Out o(v);
+    o.site(lin_site("in", LD, "float32", 4, T));
+    o.site(lin_site("out", ST, "float32", 4, T));
+    o.finish((u64)B, (u64)G);
+    return PM_OK;
+}
+
+pm_status counts_overlap(const KP &kp, std::vector<pm_feature> &v) {
+    i64 m = kp.i(0), N = kp.i(1);
+    u64 T = (u64)N, S = T / 32;
+    Out o(v);
+    o.site(lin_site("in", LD, "float32", 4, T));
+    o.site(loc_site("s_st", ST, T * (u64)m, S * (u64)m));
+    o.site(loc_site("s_ld", LD, T * (u64)m, S * (u64)m));
+    o.site(lin_site("out", ST, "float32", 4, T));
+    o.finish(0, T / 256);
+    return PM_OK;
+}
+
+pm_status counts_empty(const KP &kp, std::vector<pm_feature> &v) {
+    Out o(v);
+    o.finish(0, (u64)kp.i(0));
+    return PM_OK;
+}
+
+// ---------------------------------------------------------------- matmul
+pm_status counts_mm(const KP &kp, std::vector<pm_feature> &v) {
+    i64 n = kp.i(0);
+    int var = kp.def->variant;
+    u64 N2 = (u64)n * n, S2 = N2 / 32, K = (u64)(n / 16);
+    Out o(v);
+    auto gsite = [&](const char *tag, int dir, i64 l0, i64 l1, i64 g0, i64 g1, i64 loop, u64 wi, u64 sg) {
+        Site s{};
+        s.tag = tag; s.mem = GL; s.dir = dir; s.dtype = "float32"; s.dsize = 4;
+        s.nl = 2; s.l[0] = l0; s.l[1] = l1; s.ng = 2; s.g[0] = g0; s.g[1] = g1; s.loop = loop;
+        s.wi = wi; s.sg = sg; s.foot = N2;
+        o.site(s);
+    };
+    auto lsite = [&](const char *tag, int dir, i64 l0, i64 l1, i64 loop, u64 wi, u64 sg) {
+        Site s{};
+        s.tag = tag; s.mem = LO; s.dir = dir; s.dtype = "float32"; s.dsize = 4;
+        s.nl = 2; s.l[0] = l0; s.l[1] = l1; s.ng = 2; s.loop = loop;
+        s.wi = wi; s.sg = sg; s.foot = 256;
+        o.site(s);
+    };
+    const char *ta = var == 0 || var == 2 ? "mm-PF-a" : "mm-noPF-a";
+    const char *tb = var == 0 || var == 3 ? "mm-PF-b" : "mm-noPF-b";
+    switch (var) {
+    case 0:  // PF: per k-tile: 2 fetches, 2 barriers, 16 madds
+        o.op(0, 2, N2 * (u64)n, S2 * (u64)n);
+        gsite(ta, LD, 1, n, 0, 16 * n, 16, N2 * K, S2 * K);
+        lsite("a_fetch_st", ST, 1, 16, 0, N2 * K, S2 * K);
+        gsite(tb, LD, 1, n, 16, 0, 16 * n, N2 * K, S2 * K);
+        lsite("b_fetch_st", ST, 1, 16, 0, N2 * K, S2 * K);
+        lsite("a_fetch_ld", LD, 0, 16, 1, N2 * (u64)n, S2 * (u64)n);
+        lsite("b_fetch_ld", LD, 1, 0, 16, N2 * (u64)n, S2 * (u64)n);
+        gsite("c", ST, 1, n, 16, 16 * n, 0, N2, S2);
+        o.finish(2 * K, N2 / 256);
+        break;
+    case 1:  // noPF
+        o.op(0, 2, N2 * (u64)n, S2 * (u64)n);
+        gsite(ta, LD, 0, n, 0, 16 * n, 1, N2 * (u64)n, S2 * (u64)n);
+        gsite(tb, LD, 1, 0, 16, 0, n, N2 * (u64)n, S2 * (u64)n);
+        gsite("c", ST, 1, n, 16, 16 * n, 0, N2, S2);
+        o.finish(0, N2 / 256);
+        break;
+    default: {  // work-removed twins: tgt += x per kept load, then tgt_dest
+        u64 per = (var == 2 || var == 3) ? K : (u64)n;
+        o.op(0, 0, N2 * per, S2 * per);
+        if (var == 2) gsite(ta, LD, 1, n, 0, 16 * n, 16, N2 * K, S2 * K);
+        if (var == 3) gsite(tb, LD, 1, n, 16, 0, 16 * n, N2 * K, S2 * K);
+        if (var == 4) gsite(ta, LD, 0, n, 0, 16 * n, 1, N2 * (u64)n, S2 * (u64)n);
+        if (var == 5) gsite(tb, LD, 1, 0, 16, 0, n, N2 * (u64)n, S2 * (u64)n);
+        gsite("tgt_dest", ST, 1, n, 16, 16 * n, 0, N2, S2);
+        o.finish(0, N2 / 256);
+    }
+    }
+    return PM_OK;
+}
+
+// ---------------------------------------------------------------- DG
+// k = L0*gid0 + lid0, i = L1*gid1 + lid1, guard i < Np.  A sub-group holds
+// r = 32/L0 whole rows (lid1 values); rows never straddle work-groups since
+// L1 is a multiple of r, so the number of sub-groups with an active first
+// row, per gid0, is ceil(Np / r).
+pm_status counts_dg(const KP &kp, std::vector<pm_feature> &v) {
+    i64 Np = kp.i(0), Nel = kp.i(1), L0 = kp.i(2), L1 = kp.i(3);
+    int var = kp.def->variant;
+    i64 G0 = Nel / L0, G1 = cdiv(Np, L1), r = 32 / L0, nj = cdiv(Np, L0);
+    u64 SGa = (u64)(G0 * cdiv(Np, r));          // active sub-groups
+    u64 WIa = (u64)(Nel * Np);                   // active work-items
+    u64 Np2 = (u64)(Np * Np);
+    u64 WIall = (u64)(G0 * G1 * L0 * L1), SGall = (u64)(G0 * G1 * (L0 * L1 / 32));
+    char t_nu[32], t_ndm[32], t_pu[32], t_pdm[32], t_res[32];
+    snprintf(t_nu, sizeof t_nu, "dg-noPF-u-%dx%d", (int)L0, (int)L1);
+    snprintf(t_ndm, sizeof t_ndm, "dg-noPF-dm-%dx%d", (int)L0, (int)L1);
+    snprintf(t_pu, sizeof t_pu, "dg-dmPF-u-%dx%d", (int)L0, (int)L1);
+    snprintf(t_pdm, sizeof t_pdm, "dg-dmPF-dm-%dx%d", (int)L0, (int)L1);
+    snprintf(t_res, sizeof t_res, "dg-res-%dx%d", (int)L0, (int)L1);
+    Out o(v);
+    auto site = [&](const char *tag, int mem, int dir, i64 l0, i64 l1, i64 g0, i64 g1, i64 loop, u64 wi, u64 sg,
+                    u64 foot) {
+        Site s{};
+        s.tag = tag; s.mem = mem; s.dir = dir; s.dtype = "float32"; s.dsize = 4;
+        s.nl = 2; s.l[0] = l0; s.l[1] = l1; s.ng = 2; s.g[0] = g0; s.g[1] = g1; s.loop = loop;
+        s.wi = wi; s.sg = sg; s.foot = foot;
+        o.site(s);
+    };
+    const u64 inner = 3 * (u64)Np;  // (m, j) instances per active work-item
+    // u[Np*k + j], D[Np^2 m + Np i + j], res[Nel Np m + Np k + i]
+    auto u_site = [&](const char *tag) {
+        site(tag, GL, LD, Np, 0, L0 * Np, 0, 1, WIa * inner, SGa * inner, (u64)(Nel * Np));
+    };
+    auto d_site = [&](const char *tag) {
+        site(tag, GL, LD, 0, Np, 0, L1 * Np, 1, WIa * inner, SGa * inner, 3 * Np2);
+    };
+    auto res_site = [&]() {
+        site(t_res, GL, ST, Np, 1, L0 * Np, L1, Nel * Np, WIa * 3, SGa * 3, (u64)(3 * Nel * Np));
+    };
+    auto dest_site = [&]() {
+        site("tgt_dest", GL, ST, 1, Nel, L0, L1 * Nel, 0, WIall, SGall, WIall);
+    };
+    // dmPF D fetch: guard i < Np and L0*jo + lid0 < Np; per (m, jo) the active
+    // columns over all jo total Np, so work-items 3 G0 Np^2; every active
+    // sub-group has an active lane for every jo.
+    u64 fWI = 3 * (u64)G0 * Np2, fSG = 3 * (u64)nj * SGa;
+    u64 tileFoot = (u64)(std::min(L1, Np) * std::min(L0, Np));
+    switch (var) {
+    case 0:
+        o.op(0, 2, WIa * inner, SGa * inner);
+        d_site(t_ndm);
+        u_site(t_nu);
+        res_site();
+        o.finish(0, (u64)(G0 * G1));
+        break;
+    case 1:
+        o.op(0, 2, WIa * inner, SGa * inner);
+        site(t_pdm, GL, LD, 1, Np, 0, L1 * Np, L0, fWI, fSG, 3 * Np2);
+        site("dm_fetch_st", LO, ST, 1, L0, 0, 0, 0, fWI, fSG, tileFoot);
+        site("dm_fetch_ld", LO, LD, 0, L0, 0, 0, 1, WIa * inner, SGa * inner, tileFoot);
+        site(t_pu, GL, LD, Np, 0, L0 * Np, 0, 1, WIa * inner, SGa * inner, (u64)(Nel * Np));
+        res_site();
+        o.finish(6 * (u64)nj, (u64)(G0 * G1));
+        break;
+    case 2: case 3:
+        o.op(0, 0, WIa * inner, SGa * inner);
+        if (var == 2) u_site(t_nu);
+        else d_site(t_ndm);
+        dest_site();
+        o.finish(0, (u64)(G0 * G1));
+        break;
+    case 4:
+        o.op(0, 0, WIa * inner, SGa * inner);
+        site(t_pu, GL, LD, Np, 0, L0 * Np, 0, 1, WIa * inner, SGa * inner, (u64)(Nel * Np));
+        dest_site();
+        o.finish(0, (u64)(G0 * G1));
+        break;
+    case 5:
+        o.op(0, 0, fWI, fSG);
+        site(t_pdm, GL, LD, 1, Np, 0, L1 * Np, L0, fWI, fSG, 3 * Np2);
+        dest_site();
+        o.finish(0, (u64)(G0 * G1));
+        break;
+    case 6:
+        res_site();
+        o.finish(0, (u64)(G0 * G1));
+        break;
+    }
+    return PM_OK;
+}
+
+// ---------------------------------------------------------------- stencil
+pm_status counts_fd(const KP &kp, std::vector<pm_feature> &v) {
+    i64 n = kp.i(0), W = n + 2;
+    int var = kp.def->variant;
+    Out o(v);
+    auto site = [&](const char *tag, int mem, int dir, i64 l0, i64 l1, i64 g0, i64 g1, u64 wi, u64 sg, u64 foot) {
+        Site s{};
+        s.tag = tag; s.mem = mem; s.dir = dir; s.dtype = "float32"; s.dsize = 4;
+        s.nl = 2; s.l[0] = l0; s.l[1] = l1; s.ng = 2; s.g[0] = g0; s.g[1] = g1;
+        s.wi = wi; s.sg = sg; s.foot = foot;
+        o.site(s);
+    };
+    u64 N2 = (u64)(n * n);
+    if (var == 0 || var == 2 || var == 3) {
+        // 16x16 work-group, tile origin 14*gid; a sub-group is rows {2q, 2q+1}.
+        i64 G = cdiv(n, 14);
+        u64 S = 0, Qf = 0, Qc = 0;
+        for (i64 g = 0; g < G; g++) {
+            S += (u64)std::min<i64>(16, W - 14 * g);             // fetching rows (or columns) of tile g
+            Qf += (u64)std::min<i64>(8, cdiv(W - 14 * g, 2));    // sub-groups with a fetching first row
+            Qc += (u64)(std::min<i64>(14, n - 14 * g) / 2 + 1);  // sub-groups with a computing row
+        }
+        u64 fWI = S * S, fSG = (u64)G * Qf, cSG = (u64)G * Qc;
+        u64 tf = (u64)(std::min<i64>(16, W) * std::min<i64>(16, W));
+        u64 cf = (u64)(std::min<i64>(14, n) * std::min<i64>(14, n));
+        if (var == 0) {
+            o.op(0, 0, 3 * N2, 3 * cSG);
+            o.op(0, 1, N2, cSG);
+            o.op(0, 2, N2, cSG);
+            site("fd-tile-u", GL, LD, 1, W, 14, 14 * W, fWI, fSG, (u64)(W * W));
+            site("u_fetch_st", LO, ST, 1, 16, 0, 0, fWI, fSG, tf);
+            static const char *nm[5] = {"u_fetch_c", "u_fetch_n", "u_fetch_s", "u_fetch_w", "u_fetch_e"};
+            for (int k = 0; k < 5; k++) site(nm[k], LO, LD, 1, 16, 0, 0, N2, cSG, cf);
+            site("fd-tile-res", GL, ST, 1, n, 14, 14 * n, N2, cSG, N2);
+            o.finish(1, (u64)(G * G));
+        } else if (var == 2) {
+            o.op(0, 0, fWI, fSG);
+            site("fd-tile-u", GL, LD, 1, W, 14, 14 * W, fWI, fSG, (u64)(W * W));
+            u64 all = (u64)(256 * G * G);
+            site("tgt_dest", GL, ST, 1, 16 * G, 16, 256 * G, all, all / 32, all);
+            o.finish(0, (u64)(G * G));
+        } else {
+            site("fd-tile-res", GL, ST, 1, n, 14, 14 * n, N2, cSG, N2);
+            o.finish(0, (u64)(G * G));
+        }
+    } else {
+        i64 G = cdiv(n, 16);
+        u64 Q = 0;
+        for (i64 g = 0; g < G; g++) Q += (u64)std::min<i64>(8, cdiv(n - 16 * g, 2));
+        u64 cSG = (u64)G * Q;
+        static const char *nm[5] = {"u_c", "u_n", "u_s", "u_w", "u_e"};
+        if (var == 1) {
+            o.op(0, 0, 3 * N2, 3 * cSG);
+            o.op(0, 1, N2, cSG);
+            o.op(0, 2, N2, cSG);
+            for (int k = 0; k < 5; k++) site(nm[k], GL, LD, 1, W, 16, 16 * W, N2, cSG, N2);
+            site("res", GL, ST, 1, n, 16, 16 * n, N2, cSG, N2);
+        } else if (var == 4) {
+            o.op(0, 0, 5 * N2, 5 * cSG);
+            for (int k = 0; k < 5; k++) site(nm[k], GL, LD, 1, W, 16, 16 * W, N2, cSG, N2);
+            u64 all = (u64)(256 * G * G);
+            site("tgt_dest", GL, ST, 1, 16 * G, 16, 256 * G, all, all / 32, all);
+        } else {
+            site("res", GL, ST, 1, n, 16, 16 * n, N2, cSG, N2);
+        }
+        o.finish(0, (u64)(G * G));
+    }
+    return PM_OK;
+}
+
+bool pow2(i64 x) { return x > 0 && (x & (x - 1)) == 0; }
+
+}  // namespace
+
+pm_status validate(const KP &kp) {
+    const char *nm = kp.def->name;
+    switch (kp.def->fam) {
+    case FAM_STREAM: {
+        i64 dt = kp.i(0), vec = kp.i(1), N = kp.i(2), s = kp.i(3), L = kp.i(4), shape = kp.i(5), W = kp.i(6);
+        if (dt < 0 || dt > 1) return fail(PM_EINVAL, "%s: dtype must be 0 (float32) or 1 (float64)", nm);
+        if (vec < 0 || vec > 1) return fail(PM_EINVAL, "%s: vec must be 0 or 1", nm);
+        if (L < 1 || L > 4) return fail(PM_EINVAL, "%s: L must be 1..4", nm);
+        i64 w = stream_width(dt, vec);
+        if (N <= 0 || N % w || N / w > (1LL << 31) - 1)
+            return fail(PM_EINVAL, "%s: N must be a positive multiple of %lld below 2^31 vectors", nm, (long long)w);
+        i64 M = N / w;
+        if (shape == 0) {
+            if (!pow2(s) || s > 1024) return fail(PM_EINVAL, "%s: s must be a power of two <= 1024", nm);
+            if (M % (256 * s)) return fail(PM_EINVAL, "%s: N/%lld must be a multiple of 256*s", nm, (long long)w);
+        } else if (shape == 1) {
+            if (W < 16 || W % 16) return fail(PM_EINVAL, "%s: W must be a positive multiple of 16", nm);
+            if (M % (16 * W)) return fail(PM_EINVAL, "%s: N/%lld must be a multiple of 16*W", nm, (long long)w);
+        } else
+            return fail(PM_EINVAL, "%s: shape must be 0 or 1", nm);
+        return PM_OK;
+    }
+    case FAM_FMA:
+        if (kp.i(0) < 0 || kp.i(0) > 1) return fail(PM_EINVAL, "%s: dtype must be 0 or 1", nm);
+        if (kp.i(1) < 0 || kp.i(1) > 2) return fail(PM_EINVAL, "%s: op must be 0 (add), 1 (mul), 2 (madd)", nm);
+        if (kp.i(2) < 32 || kp.i(2) % 32 || kp.i(2) > (1LL << 30))
+            return fail(PM_EINVAL, "%s: F must be a positive multiple of 32", nm);
+        if (kp.i(3) < 1 || kp.i(3) > (1LL << 23)) return fail(PM_EINVAL, "%s: G must be 1..2^23", nm);
+        return PM_OK;
+    case FAM_SMEM:
+        if (kp.i(0) < 4 || kp.i(0) % 4 || kp.i(0) > (1LL << 30))
+            return fail(PM_EINVAL, "%s: R must be a positive multiple of 4", nm);
+        if (kp.i(1) < 0 || kp.i(1) > 1) return fail(PM_EINVAL, "%s: sync must be 0 or 1", nm);
+        if (kp.i(2) < 1 || kp.i(2) > (1LL << 23)) return fail(PM_EINVAL, "%s: G must be 1..2^23", nm);
+        return PM_OK;
+    case FAM_BARRIER:
+        if (kp.i(0) < 0 || kp.i(0) > (1LL << 30)) return fail(PM_EINVAL, "%s: B must be >= 0", nm);
+        if (kp.i(1) < 1 || kp.i(1) > (1LL << 23)) return fail(PM_EINVAL, "%s: G must be 1..2^23", nm);
+        return PM_OK;
+    case FAM_OVERLAP:
+        if (kp.i(0) < 0 || kp.i(0) > (1LL << 30)) return fail(PM_EINVAL, "%s: m must be >= 0", nm);
+        if (kp.i(1) < 256 || kp.i(1) % 256 || kp.i(1) > (1LL << 31))
+            return fail(PM_EINVAL, "%s: N must be a positive multiple of 256", nm);
+        return PM_OK;
+    case FAM_EMPTY:
+        if (kp.i(0) < 1 || kp.i(0) > (1LL << 31) - 1) return fail(PM_EINVAL, "%s: G must be 1..2^31-1", nm);
+        return PM_OK;
+    case FAM_MM:
+        if (kp.i(0) < 16 || kp.i(0) % 16 || kp.i(0) > 32768)
+            return fail(PM_EINVAL, "%s: n must be a multiple of 16 in [16, 32768]", nm);
+        return PM_OK;
+    case FAM_DG: {
+        i64 Np = kp.i(0), Nel = kp.i(1), L0 = kp.i(2), L1 = kp.i(3);
+        if (!((L0 == 16 && L1 == 16) || (L0 == 32 && L1 == 8)))
+            return fail(PM_EINVAL, "%s: work-group (L0, L1) must be (16, 16) or (32, 8)", nm);
+        if (Np < 1 || Np > 512) return fail(PM_EINVAL, "%s: Np must be 1..512", nm);
+        if (Nel < L0 || Nel % L0 || Nel > (1LL << 24))
+            return fail(PM_EINVAL, "%s: Nel must be a positive multiple of L0 (<= 2^24)", nm);
+        return PM_OK;
+    }
+    case FAM_FD:
+        if (kp.i(0) < 1 || kp.i(0) > 46000) return fail(PM_EINVAL, "%s: n must be 1..46000", nm);
+        return PM_OK;
+    }
+    return fail(PM_EINVAL, "unknown family");
+}
+
+pm_status counts(const KP &kp, std::vector<pm_feature> &out) {
+    pm_status s = validate(kp);
+    if (s) return s;
+    switch (kp.def->fam) {
+    case FAM_STREAM: return counts_stream(kp, out);
+    case FAM_FMA: return counts_fma(kp, out);
+    case FAM_SMEM: return counts_smem(kp, out);
+    case FAM_BARRIER: return counts_barrier(kp, out);
+    case FAM_OVERLAP: return counts_overlap(kp, out);
+    case FAM_EMPTY: return counts_empty(kp, out);
+    case FAM_MM: return counts_mm(kp, out);
+    case FAM_DG: return counts_dg(kp, out);
+    case FAM_FD: return counts_fd(kp, out);
+    }
+    return fail(PM_EINVAL, "unknown family");
+}
+
+pm_status buffers(const KP &kp, std::vector<BufSpec> &b) {
+    int var = kp.def->variant;
+    switch (kp.def->fam) {
+    case FAM_STREAM: {
+        int dt = (int)kp.i(0);
+        uint64_t N = (uint64_t)kp.i(2);
+        static const char *nm[4] = {"in0", "in1", "in2", "in3"};
+        for (int a = 0; a < kp.i(4); a++) b.push_back({nm[a], dt, PM_IN, N});
+        b.push_back({"out", dt, PM_OUT, N});
+        break;
+    }
+    case FAM_FMA: {
+        uint64_t T = (uint64_t)kp.i(3) * 256;
+        b.push_back({"seed", (int)kp.i(0), PM_IN, T});
+        b.push_back({"out", (int)kp.i(0), PM_OUT, T});
+        break;
+    }
+    case FAM_SMEM: case FAM_BARRIER: {
+        uint64_t T = (uint64_t)kp.i(kp.def->fam == FAM_SMEM ? 2 : 1) * 256;
+        b.push_back({"in", PM_F32, PM_IN, T});
+        b.push_back({"out", PM_F32, PM_OUT, T});
+        break;
+    }
+    case FAM_OVERLAP:
+        b.push_back({"in", PM_F32, PM_IN, (uint64_t)kp.i(1)});
+        b.push_back({"out", PM_F32, PM_OUT, (uint64_t)kp.i(1)});
+        break;
+    case FAM_EMPTY: break;
+    case FAM_MM: {
+        uint64_t N2 = (uint64_t)kp.i(0) * (uint64_t)kp.i(0);
+        if (var <= 1) {
+            b.push_back({"a", PM_F32, PM_IN, N2});
+            b.push_back({"b", PM_F32, PM_IN, N2});
+            b.push_back({"c", PM_F32, PM_OUT, N2});
+        } else {
+            b.push_back({(var == 2 || var == 4) ? "a" : "b", PM_F32, PM_IN, N2});
+            b.push_back({"tgt_dest", PM_F32, PM_OUT, N2});
+        }
+        break;
+    }
+    case FAM_DG: {
+        uint64_t Np = (uint64_t)kp.i(0), Nel = (uint64_t)kp.i(1), L1 = (uint64_t)kp.i(3);
+        uint64_t rows = (uint64_t)cdiv((i64)Np, (i64)L1) * L1;
+        if (var <= 1) {
+            b.push_back({"diff_mat", PM_F32, PM_IN, 3 * Np * Np});
+            b.push_back({"u", PM_F32, PM_IN, Nel * Np});
+            b.push_back({"res", PM_F32, PM_OUT, 3 * Nel * Np});
+        } else if (var == 2 || var == 4) {
+            b.push_back({"u", PM_F32, PM_IN, Nel * Np});
+            b.push_back({"tgt_dest", PM_F32, PM_OUT, rows * Nel});
+        } else if (var == 3 || var == 5) {
+            b.push_back({"diff_mat", PM_F32, PM_IN, 3 * Np * Np});
+            b.push_back({"tgt_dest", PM_F32, PM_OUT, rows * Nel});
+        } else {
+            b.push_back({"res", PM_F32, PM_OUT, 3 * Nel * Np});
+        }
+        break;
+    }
+    case FAM_FD: {
+        uint64_t n = (uint64_t)kp.i(0), W = n + 2;
+        uint64_t Gt = (uint64_t)cdiv((i64)n, 14), Gd = (uint64_t)cdiv((i64)n, 16);
+        if (var == 0 || var == 1) {
+            b.push_back({"u", PM_F32, PM_IN, W * W});
+            b.push_back({"res", PM_F32, PM_OUT, n * n});
+        } else if (var == 2 || var == 4) {
+            uint64_t G = var == 2 ? Gt : Gd;
+            b.push_back({"u", PM_F32, PM_IN, W * W});
+            b.push_back({"tgt_dest", PM_F32, PM_OUT, 256 * G * G});
+        } else {
+            b.push_back({"res", PM_F32, PM_OUT, n * n});
+        }
+        break;
+    }
+    }
+    return PM_OK;
+}
+
+}  // namespace pm

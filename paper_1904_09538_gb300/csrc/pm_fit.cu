@@ -1,0 +1,993 @@
+// Calibration and prediction (Section "Computing Model Parameters",
+// Section "Predicting Cost", Eq. overlap_differentiable / Eq. tanh).
+//
+// Residual r_k = 1 - g(p; f_k)/t_k (relative error, the paper's
+// scale_features_by_output); Jacobian by reverse-mode differentiation of the
+// model's SSA program (the paper differentiates the model symbolically).
+//
+// Precision: residuals, Jacobians and their reductions (J^T J, J^T r, SSR)
+// run in FP32 with compensated (TwoSum) FP32 accumulation; FP64 is used for
+// the normal-equation solve (Cholesky, or a Jacobi eigen-decomposition for
+// rank-deficient linear designs) and the Levenberg-Marquardt damping update.
+//
+// Batched path: one CTA per model in one persistent kernel launch; a plan
+// captures [H2D copies -> FP64->FP32 conversion -> fit kernel -> D2H copies]
+// in a CUDA graph.  Every loop is bounded (max_iter, 16 damping retries, 12
+// Jacobi sweeps); no kernel waits on another.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <cuda_runtime.h>
+#include <new>
+#include <vector>
+
+#include "pm_internal.h"
+#include "pm_model.h"
+
+pm_model::~pm_model() {
+    if (d_code) cudaFree(d_code);
+}
+
+namespace pm {
+namespace {
+
+constexpr int MP = kMaxParamsFit;               // max parameters
+constexpr int NENT = MP * (MP + 1) / 2 + MP + 1; // A (upper), b, ssr
+constexpr float EPS32 = 5.9604645e-8f;
+
+struct FitJob {
+    const Ins *code;
+    const Ins *start_code;
+    int n_code, n_start;
+    int m, nf, l;
+    int linear, use_p0;
+    unsigned start_mask;
+    const float *X;   // l x nf
+    const float *t;   // l
+    double *p;        // m, in/out
+    double *rep;      // 8 per job
+};
+
+struct FitCfg {
+    int max_iter;
+    double ftol, xtol;
+};
+
+// ---------------------------------------------------------------- evaluator
+__device__ __forceinline__ float fn32(int op, float x) {
+    switch (op) {
+    case OP_TANH: return tanhf(x);
+    case OP_EXP: return expf(x);
+    case OP_LOG: return logf(x);
+    default: return sqrtf(x);
+    }
+}
+__device__ __forceinline__ double fn64(int op, double x) {
+    switch (op) {
+    case OP_TANH: return tanh(x);
+    case OP_EXP: return exp(x);
+    case OP_LOG: return log(x);
+    default: return sqrt(x);
+    }
+}
+
+// Forward sweep over the SSA program; v[k] receives every value.
+template <typename T, typename F>
+__device__ T forward(const Ins *code, int n, const F *frow, const T *par, T *v) {
+    for (int k = 0; k < n; k++) {
+        const Ins in = code[k];
+        T x;
+        switch (in.op) {
+        case OP_FEAT: x = (T)frow[in.arg]; break;
+        case OP_PAR: x = par[in.arg]; break;
+        case OP_CONST: x = (T)in.c; break;
+        case OP_ADD: x = v[in.a] + v[in.b]; break;
+        case OP_SUB: x = v[in.a] - v[in.b]; break;
+        case OP_MUL: x = v[in.a] * v[in.b]; break;
+        case OP_DIV: x = v[in.a] / v[in.b]; break;
+        case OP_NEG: x = -v[in.a]; break;
+        default:
+            if (sizeof(T) == 4) x = (T)fn32(in.op, (float)v[in.a]);
+            else x = (T)fn64(in.op, (double)v[in.a]);
+        }
+        v[k] = x;
+    }
+    return v[n - 1];
+}
+
+// Reverse sweep: g[i] = dv[n-1]/dpar[i] (FP32).
+__device__ void reverse(const Ins *code, int n, const float *v, float *adj, float *g, int m) {
+    for (int k = 0; k < n; k++) adj[k] = 0.0f;
+    for (int i = 0; i < m; i++) g[i] = 0.0f;
+    adj[n - 1] = 1.0f;
+    for (int k = n - 1; k >= 0; k--) {
+        const float a = adj[k];
+        if (a == 0.0f) continue;
+        const Ins in = code[k];
+        switch (in.op) {
+        case OP_PAR: g[in.arg] += a; break;
+        case OP_ADD: adj[in.a] += a; adj[in.b] += a; break;
+        case OP_SUB: adj[in.a] += a; adj[in.b] -= a; break;
+        case OP_MUL: adj[in.a] += a * v[in.b]; adj[in.b] += a * v[in.a]; break;
+        case OP_DIV: adj[in.a] += a / v[in.b]; adj[in.b] -= a * v[k] / v[in.b]; break;
+        case OP_NEG: adj[in.a] -= a; break;
+        case OP_TANH: adj[in.a] += a * (1.0f - v[k] * v[k]); break;
+        case OP_EXP: adj[in.a] += a * v[k]; break;
+        case OP_LOG: adj[in.a] += a / v[in.a]; break;
+        case OP_SQRT: adj[in.a] += a * 0.5f / v[k]; break;
+        default: break;
+        }
+    }
+}
+
+// Compensated FP32 sum (TwoSum error-free transformation).
+struct CSum {
+    float s, c;
+    __device__ void init() { s = 0.0f; c = 0.0f; }
+    __device__ void add(float x) {
+        const float t = __fadd_rn(s, x);
+        const float z = __fsub_rn(t, s);
+        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z));
+        s = t;
+        c = __fadd_rn(c, e);
+    }
+    __device__ double value() const { return (double)s + (double)c; }
+};
+
+// ---------------------------------------------------------------- per-CTA state
+template <int T>
+struct Smem {
+    Ins code[kMaxIns];
+    float J[T * (MP + 1)];
+    float r[T];
+    double acc[NENT];
+    double q[MP], s[MP], dq[MP], qt[MP];
+    float pf[MP];
+    double M[MP][MP + 1], V[MP][MP + 1], rhs[MP], y[MP];
+    int idx[MP];
+    double red[T / 32];
+    double ssr, ssr_new, pred, lambda, med[2];
+    int nact, ok, rankdef, rank;
+};
+
+template <int T>
+__device__ void load_code(Smem<T> &S, const Ins *code, int n) {
+    for (int k = threadIdx.x; k < n; k += T) S.code[k] = code[k];
+    __syncthreads();
+}
+
+// p = s * q (per active parameter) -> FP32 copy for evaluation
+template <int T>
+__device__ void set_params(Smem<T> &S, const double *q, int m) {
+    if (threadIdx.x < m) S.pf[threadIdx.x] = (float)(S.s[threadIdx.x] * q[threadIdx.x]);
+    __syncthreads();
+}
+
+// Assemble over all rows of the job: A = J^T J (upper, if want_A), b = J^T r,
+// ssr = r^T r, with J_ki = -(dg_k/dp_i) s_i / t_k (scaled coordinates q).
+// Parameters outside `mask` get a zero column.
+template <int T>
+__device__ void assemble(Smem<T> &S, const FitJob &jb, int n, unsigned mask, bool want_A) {
+    const int m = jb.m, tid = threadIdx.x;
+    const int nA = m * (m + 1) / 2, nE = nA + m + 1;
+    CSum acc[3];
+    for (int u = 0; u < 3; u++) acc[u].init();
+    float v[kMaxIns], adj[kMaxIns], g[MP];
+    for (int base = 0; base < jb.l; base += T) {
+        const int row = base + tid;
+        float rr = 0.0f;
+        if (row < jb.l) {
+            const float *frow = jb.X + (size_t)row * jb.nf;
+            const float tk = jb.t[row];
+            const float gk = forward<float, float>(S.code, n, frow, S.pf, v);
+            rr = 1.0f - gk / tk;
+            reverse(S.code, n, v, adj, g, m);
+            for (int i = 0; i < m; i++)
+                S.J[tid * (MP + 1) + i] = ((mask >> i) & 1u) ? -g[i] * (float)S.s[i] / tk : 0.0f;
+        } else {
+            for (int i = 0; i < m; i++) S.J[tid * (MP + 1) + i] = 0.0f;
+        }
+        S.r[tid] = rr;
+        __syncthreads();
+        const int rows = min(T, jb.l - base);
+        for (int u = 0; u < 3; u++) {
+            const int e = tid + u * T;
+            if (e >= nE) break;
+            if (e < nA) {
+                if (!want_A) continue;
+                // e -> (i, j), i <= j, row-major upper triangle
+                int i = 0, rem = e;
+                while (rem >= m - i) { rem -= m - i; i++; }
+                const int j = i + rem;
+                for (int k = 0; k < rows; k++) acc[u].add(S.J[k * (MP + 1) + i] * S.J[k * (MP + 1) + j]);
+            } else if (e < nA + m) {
+                const int i = e - nA;
+                for (int k = 0; k < rows; k++) acc[u].add(S.J[k * (MP + 1) + i] * S.r[k]);
+            } else {
+                for (int k = 0; k < rows; k++) acc[u].add(S.r[k] * S.r[k]);
+            }
+        }
+        __syncthreads();
+    }
+    for (int u = 0; u < 3; u++) {
+        const int e = tid + u * T;
+        if (e < nE && (want_A || e >= nA)) S.acc[e] = acc[u].value();
+    }
+    __syncthreads();
+    if (tid == 0) S.ssr = S.acc[nE - 1];
+    __syncthreads();
+}
+
+// SSR only, at parameters S.pf.
+template <int T>
+__device__ double ssr_pass(Smem<T> &S, const FitJob &jb, int n) {
+    CSum a;
+    a.init();
+    float v[kMaxIns];
+    for (int row = threadIdx.x; row < jb.l; row += T) {
+        const float gk = forward<float, float>(S.code, n, jb.X + (size_t)row * jb.nf, S.pf, v);
+        const float rr = 1.0f - gk / jb.t[row];
+        a.add(rr * rr);
+    }
+    double x = a.value();
+    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+    if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = x;
+    __syncthreads();
+    double tot = 0.0;
+    for (int w = 0; w < T / 32; w++) tot += S.red[w];
+    __syncthreads();
+    return tot;
+}
+
+__device__ __forceinline__ double A_at(const double *acc, int m, int i, int j) {
+    if (i > j) { const int t = i; i = j; j = t; }
+    return acc[i * m - i * (i - 1) / 2 + (j - i)];
+}
+
+// Warp 0: solve (Ahat + lambda I) y = -bhat on the active set, Ahat the
+// unit-diagonal scaling of A; dq = y / sqrt(diag A).  S.ok = 0 when a
+// pivot is not positive (relative 1e-10).  Also S.pred = predicted SSR
+// decrease -(2 dq.b + dq^T A dq).
+template <int T>
+__device__ void solve_chol(Smem<T> &S, int m, double lambda) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, n = S.nact;
+        const double *acc = S.acc;
+        const int nA = m * (m + 1) / 2;
+        if (lane < n) {
+            const int gi = S.idx[lane];
+            const double di = sqrt(A_at(acc, m, gi, gi));
+            for (int c = 0; c < n; c++) {
+                const int gj = S.idx[c];
+                const double dj = sqrt(A_at(acc, m, gj, gj));
+                S.M[lane][c] = A_at(acc, m, gi, gj) / (di * dj) + (c == lane ? lambda : 0.0);
+            }
+            S.rhs[lane] = -acc[nA + gi] / di;
+        }
+        if (lane == 0) S.ok = 1;
+        __syncwarp();
+        for (int k = 0; k < n; k++) {
+            if (lane == 0) {
+                const double d = S.M[k][k];
+                if (!(d > 1e-10)) S.ok = 0;
+                S.M[k][k] = sqrt(fmax(d, 1e-300));
+            }
+            __syncwarp();
+            if (lane > k && lane < n) S.M[lane][k] /= S.M[k][k];
+            __syncwarp();
+            if (lane > k && lane < n)
+                for (int j = k + 1; j <= lane; j++) S.M[lane][j] -= S.M[lane][k] * S.M[j][k];
+            __syncwarp();
+        }
+        // forward: L z = rhs
+        for (int k = 0; k < n; k++) {
+            if (lane == 0) S.rhs[k] /= S.M[k][k];
+            __syncwarp();
+            if (lane > k && lane < n) S.rhs[lane] -= S.M[lane][k] * S.rhs[k];
+            __syncwarp();
+        }
+        // backward: L^T y = z
+        for (int k = n - 1; k >= 0; k--) {
+            if (lane == 0) S.rhs[k] /= S.M[k][k];
+            __syncwarp();
+            if (lane < k) S.rhs[lane] -= S.M[k][lane] * S.rhs[k];
+            __syncwarp();
+        }
+        if (lane < m) S.dq[lane] = 0.0;
+        __syncwarp();
+        if (lane < n) {
+            const int gi = S.idx[lane];
+            S.dq[gi] = S.rhs[lane] / sqrt(A_at(acc, m, gi, gi));
+        }
+        __syncwarp();
+        if (lane == 0) {
+            double db = 0.0, dAd = 0.0;
+            for (int i = 0; i < m; i++) {
+                db += S.dq[i] * acc[nA + i];
+                for (int j = 0; j < m; j++) dAd += S.dq[i] * A_at(acc, m, i, j) * S.dq[j];
+            }
+            S.pred = -(2.0 * db + dAd);
+        }
+    }
+    __syncthreads();
+}
+
+// Warp 0: cyclic Jacobi eigen-decomposition of Ahat (unit diagonal) on the
+// active set -> S.V (columns = eigenvectors), S.y (eigenvalues), S.rank.
+template <int T>
+__device__ void eigen(Smem<T> &S, int m) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, n = S.nact;
+        if (lane < n) {
+            const int gi = S.idx[lane];
+            const double di = sqrt(A_at(S.acc, m, gi, gi));
+            for (int c = 0; c < n; c++) {
+                const int gj = S.idx[c];
+                S.M[lane][c] = A_at(S.acc, m, gi, gj) / (di * sqrt(A_at(S.acc, m, gj, gj)));
+                S.V[lane][c] = lane == c ? 1.0 : 0.0;
+            }
+        }
+        __syncwarp();
+        for (int sweep = 0; sweep < 12; sweep++) {
+            double off = 0.0;
+            for (int i = 0; i < n; i++)
+                for (int j = i + 1; j < n; j++) off += S.M[i][j] * S.M[i][j];
+            if (off < 1e-30) break;
+            for (int p = 0; p < n; p++)
+                for (int qq = p + 1; qq < n; qq++) {
+                    const double apq = S.M[p][qq];
+                    if (fabs(apq) < 1e-300) continue;
+                    const double theta = (S.M[qq][qq] - S.M[p][p]) / (2.0 * apq);
+                    const double tt = (theta >= 0 ? 1.0 : -1.0) / (fabs(theta) + sqrt(theta * theta + 1.0));
+                    const double c = 1.0 / sqrt(tt * tt + 1.0), s = tt * c;
+                    __syncwarp();
+                    if (lane < n) {
+                        const double akp = S.M[lane][p], akq = S.M[lane][qq];
+                        S.M[lane][p] = c * akp - s * akq;
+                        S.M[lane][qq] = s * akp + c * akq;
+                    }
+                    __syncwarp();
+                    if (lane < n) {
+                        const double apk = S.M[p][lane], aqk = S.M[qq][lane];
+                        S.M[p][lane] = c * apk - s * aqk;
+                        S.M[qq][lane] = s * apk + c * aqk;
+                        const double vkp = S.V[lane][p], vkq = S.V[lane][qq];
+                        S.V[lane][p] = c * vkp - s * vkq;
+                        S.V[lane][qq] = s * vkp + c * vkq;
+                    }
+                    __syncwarp();
+                }
+        }
+        if (lane == 0) {
+            double emax = 0.0;
+            for (int i = 0; i < n; i++) emax = fmax(emax, S.M[i][i]);
+            int r = 0;
+            // singular value threshold 1e-5 relative (FP32 data): eigenvalue 1e-10
+            for (int i = 0; i < n; i++) {
+                S.y[i] = S.M[i][i] > 1e-10 * emax ? S.M[i][i] : 0.0;
+                r += S.y[i] > 0.0;
+            }
+            S.rank = r;
+        }
+    }
+    __syncthreads();
+}
+
+// Warp 0: dq = -D^-1/2 V diag(1/e) V^T D^-1/2 b (truncated pseudo-inverse).
+template <int T>
+__device__ void solve_pinv(Smem<T> &S, int m) {
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, n = S.nact, nA = m * (m + 1) / 2;
+        if (lane < n) {
+            const int gi = S.idx[lane];
+            S.rhs[lane] = -S.acc[nA + gi] / sqrt(A_at(S.acc, m, gi, gi));
+        }
+        __syncwarp();
+        double w = 0.0;
+        if (lane < n && S.y[lane] > 0.0) {
+            for (int k = 0; k < n; k++) w += S.V[k][lane] * S.rhs[k];
+            w /= S.y[lane];
+        }
+        __syncwarp();
+        if (lane < n) S.qt[lane] = w;  // temporary: coefficients in the eigenbasis
+        __syncwarp();
+        if (lane < m) S.dq[lane] = 0.0;
+        __syncwarp();
+        if (lane < n) {
+            double z = 0.0;
+            for (int k = 0; k < n; k++) z += S.V[lane][k] * S.qt[k];
+            const int gi = S.idx[lane];
+            S.dq[gi] = z / sqrt(A_at(S.acc, m, gi, gi));
+        }
+    }
+    __syncthreads();
+}
+
+template <int T>
+__device__ void set_active(Smem<T> &S, int m, unsigned mask) {
+    if (threadIdx.x == 0) {
+        int n = 0;
+        for (int i = 0; i < m; i++)
+            if ((mask >> i) & 1u) {
+                if (A_at(S.acc, m, i, i) > 0.0) S.idx[n++] = i;
+            }
+        S.nact = n;
+    }
+    __syncthreads();
+}
+
+// Linear least squares on `code` for the parameters in mask; S.s must be set.
+// Result (scaled) in S.q; S.rank, S.rankdef set.
+template <int T>
+__device__ void linear_fit(Smem<T> &S, const FitJob &jb, int n, unsigned mask) {
+    const int m = jb.m;
+    if (threadIdx.x < m) S.q[threadIdx.x] = 0.0;
+    __syncthreads();
+    set_params(S, S.q, m);
+    assemble(S, jb, n, mask, true);
+    set_active(S, m, mask);
+    solve_chol(S, m, 0.0);
+    const bool pinv = !S.ok;
+    if (pinv) eigen(S, m);
+    if (threadIdx.x == 0) {
+        S.rankdef = pinv && S.rank < S.nact;
+        if (!pinv) S.rank = S.nact;
+    }
+    __syncthreads();
+    for (int it = 0; it < 3; it++) {  // solve, then iterative refinement (b at the new q)
+        if (it > 0) {
+            set_params(S, S.q, m);
+            assemble(S, jb, n, mask, false);
+            if (pinv) solve_pinv(S, m);
+            else {
+                // A unchanged (linear): reuse the factorisation by re-solving
+                solve_chol(S, m, 0.0);
+            }
+        } else if (pinv) {
+            solve_pinv(S, m);
+        }
+        if (threadIdx.x < m) S.q[threadIdx.x] += S.dq[threadIdx.x];
+        __syncthreads();
+    }
+    set_params(S, S.q, m);
+    const double ssr = ssr_pass(S, jb, n);
+    if (threadIdx.x == 0) S.ssr = ssr;
+    __syncthreads();
+}
+
+template <int T>
+__global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitCfg cfg) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    Smem<T> &S = *reinterpret_cast<Smem<T> *>(smem_raw);
+    const FitJob jb = jobs[blockIdx.x];
+    const int m = jb.m, tid = threadIdx.x;
+    const unsigned all = m >= 32 ? 0xffffffffu : ((1u << m) - 1u);
+    int status = PM_OK, iters = 0;
+
+    if (jb.linear) {
+        if (tid < m) S.s[tid] = 1.0;
+        __syncthreads();
+        load_code(S, jb.code, jb.n_code);
+        linear_fit(S, jb, jb.n_code, all);
+        if (tid < m) jb.p[tid] = S.q[tid] * S.s[tid];
+        if (tid == 0) {
+            jb.rep[0] = S.rankdef ? PM_ERANK : PM_OK;
+            jb.rep[1] = 1;
+            jb.rep[2] = S.rank;
+            jb.rep[3] = 1;
+            jb.rep[4] = sqrt(S.ssr);
+            jb.rep[5] = 0.0;
+        }
+        return;
+    }
+
+    // ---- start point
+    if (!jb.use_p0) {
+        if (tid < m) S.s[tid] = 1.0;
+        __syncthreads();
+        load_code(S, jb.start_code, jb.n_start);
+        linear_fit(S, jb, jb.n_start, jb.start_mask);
+        // median of t (rank selection; ties handled by rank ranges)
+        const int k1 = (jb.l - 1) / 2, k2 = jb.l / 2;
+        for (int i = tid; i < jb.l; i += T) {
+            const float x = jb.t[i];
+            int lt = 0, eq = 0;
+            for (int j = 0; j < jb.l; j++) {
+                const float y = jb.t[j];
+                lt += y < x;
+                eq += y == x;
+            }
+            if (lt <= k1 && k1 < lt + eq) S.med[0] = x;
+            if (lt <= k2 && k2 < lt + eq) S.med[1] = x;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            double big = 0.0;
+            for (int i = 0; i < m; i++)
+                if ((jb.start_mask >> i) & 1u) big = fmax(big, fabs(S.q[i]));
+            big = fmax(big, 1e-300);
+            const double pe = 10.0 / (0.5 * (S.med[0] + S.med[1]));
+            for (int i = 0; i < m; i++) {
+                if ((jb.start_mask >> i) & 1u) S.q[i] = S.q[i] > 0.0 ? S.q[i] : 1e-3 * big;
+                else S.q[i] = pe;
+            }
+        }
+        __syncthreads();
+    } else {
+        if (tid < m) S.q[tid] = jb.p[tid];
+        __syncthreads();
+    }
+
+    // ---- Levenberg-Marquardt in scaled coordinates q = p / s, s = |p0|
+    if (tid < m) {
+        const double p0 = S.q[tid];
+        S.s[tid] = p0 != 0.0 ? fabs(p0) : 1.0;
+        S.q[tid] = p0 / S.s[tid];
+    }
+    if (tid == 0) S.lambda = 1e-3;
+    __syncthreads();
+    load_code(S, jb.code, jb.n_code);
+    set_params(S, S.q, m);
+    assemble(S, jb, jb.n_code, all, true);
+    set_active(S, m, all);
+    bool converged = false;
+    for (int it = 0; it < cfg.max_iter; it++) {
+        bool accepted = false;
+        double ssr_old = S.ssr;
+        // noise floor of an SSR built from FP32 residuals
+        const double noise = 4.0 * EPS32 * sqrt((double)jb.l * ssr_old) + (double)jb.l * EPS32 * EPS32;
+        for (int tr = 0; tr < 16; tr++) {
+            solve_chol(S, m, S.lambda);
+            if (!S.ok) {
+                if (tid == 0) S.lambda *= 10.0;
+                __syncthreads();
+                continue;
+            }
+            if (tid < m) S.qt[tid] = S.q[tid] + S.dq[tid];
+            __syncthreads();
+            set_params(S, S.qt, m);
+            const double sn = ssr_pass(S, jb, jb.n_code);
+            const double pred = S.pred;
+            if (isfinite(sn) && (sn <= ssr_old || pred <= noise)) {
+                accepted = true;
+                if (tid == 0) S.ssr_new = sn;
+                __syncthreads();
+                break;
+            }
+            if (tid == 0) S.lambda *= 10.0;
+            __syncthreads();
+        }
+        if (!accepted) {
+            converged = true;  // no decrease possible above the noise floor
+            break;
+        }
+        double dn = 0.0, qn = 0.0;
+        for (int i = 0; i < m; i++) {
+            dn += S.dq[i] * S.dq[i];
+            qn += S.qt[i] * S.qt[i];
+        }
+        dn = sqrt(dn);
+        qn = sqrt(qn);
+        const double pred = S.pred;
+        __syncthreads();
+        if (tid < m) S.q[tid] = S.qt[tid];
+        if (tid == 0) S.lambda = fmax(S.lambda * 0.1, 1e-12);
+        __syncthreads();
+        iters++;
+        set_params(S, S.q, m);
+        assemble(S, jb, jb.n_code, all, true);
+        set_active(S, m, all);
+        if (dn <= cfg.xtol * (qn + cfg.xtol) || pred <= noise ||
+            (ssr_old - S.ssr) <= cfg.ftol * ssr_old) {
+            converged = true;
+            break;
+        }
+    }
+    if (!converged) status = PM_ENOTCONV;
+    if (tid < m) jb.p[tid] = S.q[tid] * S.s[tid];
+    if (tid == 0) {
+        jb.rep[0] = status;
+        jb.rep[1] = iters;
+        jb.rep[2] = S.nact;
+        jb.rep[3] = 0;
+        jb.rep[4] = sqrt(S.ssr);
+        jb.rep[5] = S.lambda;
+    }
+}
+
+__global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        b[i] = (float)a[i];
+}
+
+// ---------------------------------------------------------------- autograd kernels
+__global__ void k_residual(const Ins *__restrict__ code, int n, int m, int nf, const float *__restrict__ X,
+                           const float *__restrict__ t, size_t l, const double *__restrict__ p, float *__restrict__ r) {
+    __shared__ float pf[MP];
+    __shared__ Ins cs[kMaxIns];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) cs[k] = code[k];
+    if (threadIdx.x < m) pf[threadIdx.x] = (float)p[threadIdx.x];
+    __syncthreads();
+    float v[kMaxIns];
+    for (size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x; row < l; row += (size_t)gridDim.x * blockDim.x)
+        r[row] = 1.0f - forward<float, float>(cs, n, X + row * nf, pf, v) / t[row];
+}
+
+// mode 0: pbar += sum_k rbar_k J_k (vjp); mode 1: write J rows
+__global__ void k_jac(const Ins *__restrict__ code, int n, int m, int nf, const float *__restrict__ X,
+                      const float *__restrict__ t, size_t l, const double *__restrict__ p,
+                      const float *__restrict__ rbar, double *__restrict__ pbar, float *__restrict__ J, int mode) {
+    __shared__ float pf[MP];
+    __shared__ Ins cs[kMaxIns];
+    __shared__ double red[MP][8];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) cs[k] = code[k];
+    if (threadIdx.x < m) pf[threadIdx.x] = (float)p[threadIdx.x];
+    __syncthreads();
+    float v[kMaxIns], adj[kMaxIns], g[MP];
+    CSum acc[MP];
+    for (int i = 0; i < MP; i++) acc[i].init();
+    for (size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x; row < l; row += (size_t)gridDim.x * blockDim.x) {
+        forward<float, float>(cs, n, X + row * nf, pf, v);
+        reverse(cs, n, v, adj, g, m);
+        const float inv = -1.0f / t[row];
+        if (mode == 1) {
+            for (int i = 0; i < m; i++) J[row * m + i] = g[i] * inv;
+        } else {
+            const float w = rbar[row] * inv;
+            for (int i = 0; i < m; i++) acc[i].add(g[i] * w);
+        }
+    }
+    if (mode == 1) return;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    for (int i = 0; i < m; i++) {
+        double x = acc[i].value();
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) red[i][warp] = x;
+    }
+    __syncthreads();
+    if (threadIdx.x < m) {
+        double x = 0.0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); w++) x += red[threadIdx.x][w];
+        atomicAdd(&pbar[threadIdx.x], x);
+    }
+}
+
+__global__ void k_predict(const Ins *__restrict__ code, int n, int nf, const double *__restrict__ X, size_t l,
+                          const double *__restrict__ p, double *__restrict__ out, int m) {
+    __shared__ double pd[MP];
+    __shared__ Ins cs[kMaxIns];
+    for (int k = threadIdx.x; k < n; k += blockDim.x) cs[k] = code[k];
+    if (threadIdx.x < m) pd[threadIdx.x] = p[threadIdx.x];
+    __syncthreads();
+    double v[kMaxIns];
+    for (size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x; row < l; row += (size_t)gridDim.x * blockDim.x)
+        out[row] = forward<double, double>(cs, n, X + row * nf, pd, v);
+}
+
+template <int T>
+size_t smem_bytes() { return sizeof(Smem<T>); }
+
+template <int T>
+pm_status launch_fit_t(const FitJob *jobs, int njobs, FitCfg cfg, cudaStream_t st) {
+    const size_t sb = smem_bytes<T>();
+    PM_CUDA_TRY(cudaFuncSetAttribute(k_fit<T>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sb));
+    k_fit<T><<<njobs, T, sb, st>>>(jobs, cfg);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status launch_fit(int threads, const FitJob *jobs, int njobs, FitCfg cfg, cudaStream_t st) {
+    switch (threads) {
+    case 64: return launch_fit_t<64>(jobs, njobs, cfg, st);
+    case 256: return launch_fit_t<256>(jobs, njobs, cfg, st);
+    default: return launch_fit_t<128>(jobs, njobs, cfg, st);
+    }
+}
+
+bool finite_pos(double x) { return std::isfinite(x) && x > 0.0; }
+
+}  // namespace
+}  // namespace pm
+
+using namespace pm;
+
+struct pm_fit_plan {
+    std::vector<const pm_model *> models;
+    std::vector<size_t> rows, xoff, poff;
+    size_t nx = 0, nt = 0, np = 0;
+    int threads = 128;
+    FitCfg cfg{};
+    int use_p0 = 0;
+    // device
+    double *dX64 = nullptr, *dt64 = nullptr, *dp = nullptr, *drep = nullptr;
+    float *dX32 = nullptr, *dt32 = nullptr;
+    Ins *dcode = nullptr;
+    FitJob *djobs = nullptr;
+    // pinned host staging
+    double *hX = nullptr, *ht = nullptr, *hp = nullptr, *hrep = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraph_t graph = nullptr;
+    cudaGraphExec_t exec = nullptr;
+    ~pm_fit_plan() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (graph) cudaGraphDestroy(graph);
+        if (cap) cudaStreamDestroy(cap);
+        cudaFree(dX64); cudaFree(dt64); cudaFree(dp); cudaFree(drep);
+        cudaFree(dX32); cudaFree(dt32); cudaFree(dcode); cudaFree(djobs);
+        cudaFreeHost(hX); cudaFreeHost(ht); cudaFreeHost(hp); cudaFreeHost(hrep);
+    }
+};
+
+namespace pm {
+namespace {
+
+pm_status plan_build(pm_fit_plan *P) {
+    const size_t K = P->models.size();
+    std::vector<Ins> code;
+    std::vector<size_t> coff(K), soff(K);
+    for (size_t k = 0; k < K; k++) {
+        coff[k] = code.size();
+        code.insert(code.end(), P->models[k]->code.begin(), P->models[k]->code.end());
+        soff[k] = code.size();
+        code.insert(code.end(), P->models[k]->start_code.begin(), P->models[k]->start_code.end());
+    }
+    PM_CUDA_TRY(cudaMalloc(&P->dX64, std::max<size_t>(P->nx, 1) * 8));
+    PM_CUDA_TRY(cudaMalloc(&P->dX32, std::max<size_t>(P->nx, 1) * 4));
+    PM_CUDA_TRY(cudaMalloc(&P->dt64, P->nt * 8));
+    PM_CUDA_TRY(cudaMalloc(&P->dt32, P->nt * 4));
+    PM_CUDA_TRY(cudaMalloc(&P->dp, P->np * 8));
+    PM_CUDA_TRY(cudaMalloc(&P->drep, K * 8 * 8));
+    PM_CUDA_TRY(cudaMalloc(&P->dcode, code.size() * sizeof(Ins)));
+    PM_CUDA_TRY(cudaMalloc(&P->djobs, K * sizeof(FitJob)));
+    PM_CUDA_TRY(cudaMallocHost(&P->hX, std::max<size_t>(P->nx, 1) * 8));
+    PM_CUDA_TRY(cudaMallocHost(&P->ht, P->nt * 8));
+    PM_CUDA_TRY(cudaMallocHost(&P->hp, P->np * 8));
+    PM_CUDA_TRY(cudaMallocHost(&P->hrep, K * 8 * 8));
+    std::vector<FitJob> jobs(K);
+    size_t toff = 0;
+    for (size_t k = 0; k < K; k++) {
+        const pm_model *md = P->models[k];
+        FitJob &j = jobs[k];
+        j.code = P->dcode + coff[k];
+        j.start_code = P->dcode + soff[k];
+        j.n_code = (int)md->code.size();
+        j.n_start = (int)md->start_code.size();
+        j.m = (int)md->params.size();
+        j.nf = (int)md->features.size();
+        j.l = (int)P->rows[k];
+        j.linear = md->linear;
+        j.use_p0 = P->use_p0;
+        j.start_mask = md->start_mask;
+        j.X = P->dX32 + P->xoff[k];
+        j.t = P->dt32 + toff;
+        j.p = P->dp + P->poff[k];
+        j.rep = P->drep + 8 * k;
+        toff += P->rows[k];
+    }
+    PM_CUDA_TRY(cudaMemcpy(P->dcode, code.data(), code.size() * sizeof(Ins), cudaMemcpyHostToDevice));
+    PM_CUDA_TRY(cudaMemcpy(P->djobs, jobs.data(), K * sizeof(FitJob), cudaMemcpyHostToDevice));
+    // capture the per-run work into a graph
+    PM_CUDA_TRY(cudaStreamCreateWithFlags(&P->cap, cudaStreamNonBlocking));
+    PM_CUDA_TRY(cudaStreamBeginCapture(P->cap, cudaStreamCaptureModeThreadLocal));
+    pm_status s = PM_OK;
+    cudaError_t e = cudaSuccess;
+    if (P->nx) e = cudaMemcpyAsync(P->dX64, P->hX, P->nx * 8, cudaMemcpyHostToDevice, P->cap);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P->dt64, P->ht, P->nt * 8, cudaMemcpyHostToDevice, P->cap);
+    if (e == cudaSuccess) e = cudaMemcpyAsync(P->dp, P->hp, P->np * 8, cudaMemcpyHostToDevice, P->cap);
+    if (e == cudaSuccess && P->nx) {
+        k_to_f32<<<152, 256, 0, P->cap>>>(P->dX64, P->dX32, P->nx);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) {
+        k_to_f32<<<152, 256, 0, P->cap>>>(P->dt64, P->dt32, P->nt);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) s = launch_fit(P->threads, P->djobs, (int)K, P->cfg, P->cap);
+    if (e == cudaSuccess && s == PM_OK) e = cudaMemcpyAsync(P->hp, P->dp, P->np * 8, cudaMemcpyDeviceToHost, P->cap);
+    if (e == cudaSuccess && s == PM_OK)
+        e = cudaMemcpyAsync(P->hrep, P->drep, K * 64, cudaMemcpyDeviceToHost, P->cap);
+    cudaError_t e2 = cudaStreamEndCapture(P->cap, &P->graph);
+    if (s) return s;
+    if (e != cudaSuccess) return fail(PM_ECUDA, "fit plan capture: %s", cudaGetErrorString(e));
+    if (e2 != cudaSuccess) return fail(PM_ECUDA, "fit plan capture: %s", cudaGetErrorString(e2));
+    PM_CUDA_TRY(cudaGraphInstantiate(&P->exec, P->graph, 0));
+    return PM_OK;
+}
+
+pm_status check_opts(const pm_fit_opts *o, FitCfg &cfg, int &use_p0) {
+    cfg.max_iter = 200;
+    cfg.ftol = 1e-15;
+    cfg.xtol = 1e-12;
+    use_p0 = 0;
+    if (o) {
+        if (o->max_iter < 1 || o->max_iter > 100000) return fail(PM_EINVAL, "fit: max_iter must be 1..100000");
+        if (!(o->ftol >= 0) || !(o->xtol >= 0)) return fail(PM_EINVAL, "fit: ftol and xtol must be >= 0");
+        cfg.max_iter = o->max_iter;
+        cfg.ftol = o->ftol;
+        cfg.xtol = o->xtol;
+        use_p0 = o->use_p0 ? 1 : 0;
+    }
+    return PM_OK;
+}
+
+pm_status ensure_device_code(const pm_model *m) {
+    int dev = 0;
+    PM_CUDA_TRY(cudaGetDevice(&dev));
+    pm_model *mm = const_cast<pm_model *>(m);
+    if (mm->d_code && mm->d_device == dev) return PM_OK;
+    if (mm->d_code) {
+        cudaFree(mm->d_code);
+        mm->d_code = nullptr;
+    }
+    PM_CUDA_TRY(cudaMalloc(&mm->d_code, m->code.size() * sizeof(Ins)));
+    PM_CUDA_TRY(cudaMemcpy(mm->d_code, m->code.data(), m->code.size() * sizeof(Ins), cudaMemcpyHostToDevice));
+    mm->d_device = dev;
+    return PM_OK;
+}
+
+}  // namespace
+}  // namespace pm
+
+extern "C" {
+
+pm_status pm_fit_plan_create(const pm_model *const *models, size_t nmodels, const size_t *rows,
+                             const pm_fit_opts *opts, int32_t threads, pm_fit_plan **plan) {
+    if (!models || !rows || !plan || nmodels == 0) return fail(PM_EINVAL, "pm_fit_plan_create: bad argument");
+    if (nmodels > 65535) return fail(PM_EINVAL, "pm_fit_plan_create: at most 65535 models");
+    if (threads != 0 && threads != 64 && threads != 128 && threads != 256)
+        return fail(PM_EINVAL, "pm_fit_plan_create: threads must be 0, 64, 128 or 256");
+    pm_fit_plan *P = new (std::nothrow) pm_fit_plan();
+    if (!P) return fail(PM_ENOMEM, "pm_fit_plan_create: out of memory");
+    pm_status s = check_opts(opts, P->cfg, P->use_p0);
+    if (s) { delete P; return s; }
+    P->threads = threads ? threads : 128;
+    for (size_t k = 0; k < nmodels; k++) {
+        const pm_model *m = models[k];
+        if (!m) { delete P; return fail(PM_EINVAL, "pm_fit_plan_create: model %zu is NULL", k); }
+        if (rows[k] < 1 || rows[k] > (1u << 24)) {
+            delete P;
+            return fail(PM_EINVAL, "pm_fit_plan_create: model %zu needs 1..2^24 rows", k);
+        }
+        P->models.push_back(m);
+        P->rows.push_back(rows[k]);
+        P->xoff.push_back(P->nx);
+        P->poff.push_back(P->np);
+        P->nx += rows[k] * m->features.size();
+        P->nt += rows[k];
+        P->np += m->params.size();
+    }
+    s = plan_build(P);
+    if (s) { delete P; return s; }
+    *plan = P;
+    return PM_OK;
+}
+
+void pm_fit_plan_destroy(pm_fit_plan *plan) { delete plan; }
+
+pm_status pm_fit_plan_run(pm_fit_plan *P, const double *X, const double *t, double *p_inout, pm_fit_report *reports,
+                          void *stream) {
+    if (!P || !t || !p_inout || (P->nx && !X)) return fail(PM_EINVAL, "pm_fit_plan_run: NULL argument");
+    for (size_t k = 0, o = 0; k < P->models.size(); k++)
+        for (size_t r = 0; r < P->rows[k]; r++, o++)
+            if (!finite_pos(t[o])) return fail(PM_EINVAL, "fit: model %zu row %zu: output must be finite and > 0", k, r);
+    for (size_t i = 0; i < P->nx; i++)
+        if (!std::isfinite(X[i])) return fail(PM_EINVAL, "fit: feature value %zu is not finite", i);
+    if (P->use_p0)
+        for (size_t i = 0; i < P->np; i++)
+            if (!std::isfinite(p_inout[i])) return fail(PM_EINVAL, "fit: start point %zu is not finite", i);
+    memcpy(P->hX, X, P->nx * 8);
+    memcpy(P->ht, t, P->nt * 8);
+    memcpy(P->hp, p_inout, P->np * 8);
+    cudaStream_t st = (cudaStream_t)stream;
+    PM_CUDA_TRY(cudaGraphLaunch(P->exec, st));
+    PM_CUDA_TRY(cudaStreamSynchronize(st));
+    memcpy(p_inout, P->hp, P->np * 8);
+    if (reports)
+        for (size_t k = 0; k < P->models.size(); k++) {
+            const double *r = P->hrep + 8 * k;
+            reports[k].status = (int32_t)r[0];
+            reports[k].iterations = (int32_t)r[1];
+            reports[k].rank = (int32_t)r[2];
+            reports[k].linear = (int32_t)r[3];
+            reports[k].residual = r[4];
+            reports[k].lambda = r[5];
+        }
+    return PM_OK;
+}
+
+pm_status pm_fit_batched(const pm_model *const *models, size_t nmodels, const double *X, const double *t,
+                         const size_t *rows, const pm_fit_opts *opts, double *p_inout, pm_fit_report *reports,
+                         void *stream) {
+    pm_fit_plan *P = nullptr;
+    pm_status s = pm_fit_plan_create(models, nmodels, rows, opts, 0, &P);
+    if (s) return s;
+    s = pm_fit_plan_run(P, X, t, p_inout, reports, stream);
+    pm_fit_plan_destroy(P);
+    return s;
+}
+
+pm_status pm_fit(const pm_model *m, const double *X, const double *t, size_t l, const pm_fit_opts *opts,
+                 double *p_inout, pm_fit_report *report) {
+    if (!m || !t || !p_inout) return fail(PM_EINVAL, "pm_fit: NULL argument");
+    pm_fit_report rep{};
+    pm_status s = pm_fit_batched(&m, 1, X, t, &l, opts, p_inout, &rep, nullptr);
+    if (s) return s;
+    if (report) *report = rep;
+    if (rep.status == PM_ERANK) return fail(PM_ERANK, "pm_fit: rank-deficient design (rank %d of %zu)", rep.rank,
+                                            m->params.size());
+    if (rep.status == PM_ENOTCONV) return fail(PM_ENOTCONV, "pm_fit: no convergence in %d iterations", rep.iterations);
+    return (pm_status)rep.status;
+}
+
+pm_status pm_predict(const pm_model *m, const double *p, const double *X, size_t l, double *t_out) {
+    if (!m || !p || !t_out || (l && !X && !m->features.empty())) return fail(PM_EINVAL, "pm_predict: NULL argument");
+    if (l == 0) return PM_OK;
+    const size_t nf = m->features.size(), np = m->params.size();
+    double *dX = nullptr, *dp = nullptr, *dout = nullptr;
+    Ins *dc = nullptr;
+    pm_status s = PM_OK;
+    if (cudaMalloc(&dX, std::max<size_t>(l * nf, 1) * 8) != cudaSuccess || cudaMalloc(&dp, np * 8) != cudaSuccess ||
+        cudaMalloc(&dout, l * 8) != cudaSuccess || cudaMalloc(&dc, m->code.size() * sizeof(Ins)) != cudaSuccess)
+        s = fail(PM_ENOMEM, "pm_predict: device allocation failed");
+    if (!s && nf && cudaMemcpy(dX, X, l * nf * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+        s = fail(PM_ECUDA, "pm_predict: copy failed");
+    if (!s && cudaMemcpy(dp, p, np * 8, cudaMemcpyHostToDevice) != cudaSuccess) s = fail(PM_ECUDA, "pm_predict: copy failed");
+    if (!s && cudaMemcpy(dc, m->code.data(), m->code.size() * sizeof(Ins), cudaMemcpyHostToDevice) != cudaSuccess)
+        s = fail(PM_ECUDA, "pm_predict: copy failed");
+    if (!s) {
+        const unsigned blocks = (unsigned)std::min<size_t>((l + 127) / 128, 1216);
+        k_predict<<<blocks, 128>>>(dc, (int)m->code.size(), (int)nf, dX, l, dp, dout, (int)np);
+        cudaError_t e = cudaGetLastError();
+        if (e == cudaSuccess) e = cudaMemcpy(t_out, dout, l * 8, cudaMemcpyDeviceToHost);
+        if (e != cudaSuccess) s = fail(PM_ECUDA, "pm_predict: %s", cudaGetErrorString(e));
+    }
+    cudaFree(dX);
+    cudaFree(dp);
+    cudaFree(dout);
+    cudaFree(dc);
+    return s;
+}
+
+pm_status pm_residual(const pm_model *m, const float *X, const float *t, size_t l, const double *p, float *r,
+                      void *stream) {
+    if (!m || !t || !p || !r || (!X && !m->features.empty())) return fail(PM_EINVAL, "pm_residual: NULL argument");
+    if (l == 0) return PM_OK;
+    pm_status s = ensure_device_code(m);
+    if (s) return s;
+    const unsigned blocks = (unsigned)std::min<size_t>((l + 127) / 128, 1216);
+    k_residual<<<blocks, 128, 0, (cudaStream_t)stream>>>(m->d_code, (int)m->code.size(), (int)m->params.size(),
+                                                         (int)m->features.size(), X, t, l, p, r);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status pm_residual_vjp(const pm_model *m, const float *X, const float *t, size_t l, const double *p,
+                          const float *rbar, double *pbar, void *stream) {
+    if (!m || !t || !p || !rbar || !pbar || (!X && !m->features.empty()))
+        return fail(PM_EINVAL, "pm_residual_vjp: NULL argument");
+    pm_status s = ensure_device_code(m);
+    if (s) return s;
+    cudaStream_t st = (cudaStream_t)stream;
+    PM_CUDA_TRY(cudaMemsetAsync(pbar, 0, m->params.size() * 8, st));
+    if (l == 0) return PM_OK;
+    const unsigned blocks = (unsigned)std::min<size_t>((l + 255) / 256, 304);
+    k_jac<<<blocks, 256, 0, st>>>(m->d_code, (int)m->code.size(), (int)m->params.size(), (int)m->features.size(), X,
+                                  t, l, p, rbar, pbar, nullptr, 0);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
+pm_status pm_jacobian(const pm_model *m, const float *X, const float *t, size_t l, const double *p, float *J,
+                      void *stream) {
+    if (!m || !t || !p || !J || (!X && !m->features.empty())) return fail(PM_EINVAL, "pm_jacobian: NULL argument");
+    if (l == 0) return PM_OK;
+    pm_status s = ensure_device_code(m);
+    if (s) return s;
+    const unsigned blocks = (unsigned)std::min<size_t>((l + 255) / 256, 1216);
+    k_jac<<<blocks, 256, 0, (cudaStream_t)stream>>>(m->d_code, (int)m->code.size(), (int)m->params.size(),
+                                                     (int)m->features.size(), X, t, l, p, nullptr, nullptr, J, 1);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
+}  // extern "C"

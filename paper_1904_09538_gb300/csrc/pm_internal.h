@@ -1,0 +1,70 @@
+// Internal declarations shared by the translation units of libpm.so.
+#pragma once
+#include <cstdint>
+#include <cstdio>
+#include <string>
+#include <vector>
+
+#include "pm.h"
+
+namespace pm {
+
+// ---- errors -------------------------------------------------------------
+pm_status fail(pm_status s, const char *fmt, ...);
+void clear_error();
+
+#define PM_CUDA_TRY(expr)                                                                   \
+    do {                                                                                    \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return ::pm::fail(PM_ECUDA, "%s: %s (%s:%d)", #expr, cudaGetErrorString(e_),    \
+                              __FILE__, __LINE__);                                          \
+    } while (0)
+
+// ---- kernel registry ------------------------------------------------------
+enum Family { FAM_STREAM, FAM_FMA, FAM_SMEM, FAM_BARRIER, FAM_OVERLAP, FAM_EMPTY, FAM_MM, FAM_DG, FAM_FD };
+
+constexpr int kMaxParams = 8;
+
+struct KernelDef {
+    const char *name;
+    Family fam;
+    int variant;
+    const char *pnames[kMaxParams];  // parameter names in order (nullptr-terminated)
+    double pdefault[kMaxParams];     // NaN = required
+    bool pinteger[kMaxParams];
+};
+
+const KernelDef *kernel_def(int32_t id);
+int32_t kernel_total();
+
+// Parsed kernel parameters (values by position in KernelDef::pnames).
+struct KP {
+    const KernelDef *def = nullptr;
+    double v[kMaxParams] = {0};
+    int64_t i(int k) const { return (int64_t)v[k]; }
+};
+
+pm_status parse_params(int32_t kernel, const pm_param *p, size_t np, KP *out);
+
+// ---- counts (pm_counts.cpp) ---------------------------------------------------
+// Validates the parameters for the family and fills feature records.
+pm_status counts(const KP &kp, std::vector<pm_feature> &out);
+// Validation only (shared by launch paths).
+pm_status validate(const KP &kp);
+
+// ---- buffers and launches (pm_suite.cu, pm_modeled.cu) -------------------------
+struct BufSpec {
+    const char *name;
+    int dtype;
+    int role;
+    uint64_t elems;
+};
+pm_status buffers(const KP &kp, std::vector<BufSpec> &out);
+pm_status launch_suite(const KP &kp, void *const *bufs, void *stream);
+pm_status launch_modeled(const KP &kp, void *const *bufs, void *stream);
+
+// ---- feature records helper --------------------------------------------------
+void canonical_name(pm_feature &f);
+
+}  // namespace pm

@@ -1,0 +1,163 @@
+// pm_launch / pm_run / pm_run_host: stream-ordered launches and the paper's
+// wall-time feature (Section "Other Features": 60 trials averaged, excluding
+// host-device transfer; Section "Results": anomalous ~10x trials excluded).
+#include <algorithm>
+#include <cmath>
+#include <cuda_runtime.h>
+#include <vector>
+
+#include "pm_internal.h"
+
+namespace pm {
+
+static pm_status launch_any(const KP &kp, void *const *bufs, size_t nbufs, void *stream) {
+    pm_status s = validate(kp);
+    if (s) return s;
+    std::vector<BufSpec> spec;
+    if ((s = buffers(kp, spec))) return s;
+    if (nbufs != spec.size())
+        return fail(PM_EINVAL, "%s: %zu buffers passed, %zu needed", kp.def->name, nbufs, spec.size());
+    for (size_t i = 0; i < spec.size(); i++)
+        if (!bufs[i]) return fail(PM_EINVAL, "%s: buffer %zu (%s) is NULL", kp.def->name, i, spec[i].name);
+    switch (kp.def->fam) {
+    case FAM_MM: case FAM_DG: case FAM_FD: return launch_modeled(kp, bufs, stream);
+    default: return launch_suite(kp, bufs, stream);
+    }
+}
+
+static size_t dtype_size(int dt) { return dt == PM_F32 ? 4 : dt == PM_F64 ? 8 : 2; }
+
+struct EventPool {
+    std::vector<cudaEvent_t> ev;
+    ~EventPool() {
+        for (auto e : ev) cudaEventDestroy(e);
+    }
+    pm_status make(size_t n) {
+        ev.resize(n, nullptr);
+        for (size_t i = 0; i < n; i++) PM_CUDA_TRY(cudaEventCreate(&ev[i]));
+        return PM_OK;
+    }
+};
+
+static pm_status timed(const KP &kp, void *const *bufs, size_t nbufs, const pm_run_opts *opts, void *stream,
+                       float *trial_ms, pm_timing *out) {
+    pm_run_opts o{2, 60, 5.0};
+    if (opts) o = *opts;
+    if (o.warmup < 0 || o.trials < 1 || o.trials > 100000)
+        return fail(PM_EINVAL, "pm_run: need warmup >= 0 and 1 <= trials <= 100000");
+    cudaStream_t st = (cudaStream_t)stream;
+    pm_status s;
+    for (int w = 0; w < o.warmup; w++)
+        if ((s = launch_any(kp, bufs, nbufs, stream))) return s;
+    EventPool pool;
+    if ((s = pool.make(2 * (size_t)o.trials))) return s;
+    for (int t = 0; t < o.trials; t++) {
+        PM_CUDA_TRY(cudaEventRecord(pool.ev[2 * t], st));
+        if ((s = launch_any(kp, bufs, nbufs, stream))) return s;
+        PM_CUDA_TRY(cudaEventRecord(pool.ev[2 * t + 1], st));
+    }
+    PM_CUDA_TRY(cudaEventSynchronize(pool.ev[2 * o.trials - 1]));
+    PM_CUDA_TRY(cudaGetLastError());
+    std::vector<float> ms(o.trials);
+    for (int t = 0; t < o.trials; t++) PM_CUDA_TRY(cudaEventElapsedTime(&ms[t], pool.ev[2 * t], pool.ev[2 * t + 1]));
+    if (trial_ms)
+        for (int t = 0; t < o.trials; t++) trial_ms[t] = ms[t];
+    std::vector<float> sorted = ms;
+    std::sort(sorted.begin(), sorted.end());
+    double med = o.trials % 2 ? sorted[o.trials / 2] : 0.5 * (sorted[o.trials / 2 - 1] + sorted[o.trials / 2]);
+    double sum = 0.0, mn = 1e300, mx = 0.0;
+    int kept = 0;
+    for (float v : ms) {
+        if (o.outlier_factor > 0 && v > o.outlier_factor * med) continue;
+        sum += v;
+        mn = std::min(mn, (double)v);
+        mx = std::max(mx, (double)v);
+        kept++;
+    }
+    if (out) {
+        out->mean_ms = sum / kept;
+        out->median_ms = med;
+        out->min_ms = mn;
+        out->max_ms = mx;
+        out->n_trials = o.trials;
+        out->n_dropped = o.trials - kept;
+    }
+    return PM_OK;
+}
+
+}  // namespace pm
+
+using namespace pm;
+
+extern "C" {
+
+pm_status pm_launch(int32_t kernel, const pm_param *p, size_t np, void *const *bufs, size_t nbufs, void *stream) {
+    KP kp;
+    pm_status s = parse_params(kernel, p, np, &kp);
+    if (s) return s;
+    if (nbufs && !bufs) return fail(PM_EINVAL, "pm_launch: bufs is NULL");
+    return launch_any(kp, bufs, nbufs, stream);
+}
+
+pm_status pm_run(int32_t kernel, const pm_param *p, size_t np, void *const *bufs, size_t nbufs,
+                 const pm_run_opts *opts, void *stream, float *trial_ms, pm_timing *out) {
+    KP kp;
+    pm_status s = parse_params(kernel, p, np, &kp);
+    if (s) return s;
+    if (nbufs && !bufs) return fail(PM_EINVAL, "pm_run: bufs is NULL");
+    return timed(kp, bufs, nbufs, opts, stream, trial_ms, out);
+}
+
+pm_status pm_run_host(int32_t kernel, const pm_param *p, size_t np, void *const *host_bufs, size_t nbufs,
+                      const pm_run_opts *opts, void *stream, float *trial_ms, pm_timing *out, double *copy_ms) {
+    KP kp;
+    pm_status s = parse_params(kernel, p, np, &kp);
+    if (s) return s;
+    if ((s = validate(kp))) return s;
+    std::vector<BufSpec> spec;
+    if ((s = buffers(kp, spec))) return s;
+    if (nbufs != spec.size()) return fail(PM_EINVAL, "pm_run_host: %zu buffers passed, %zu needed", nbufs, spec.size());
+    for (size_t i = 0; i < nbufs; i++)
+        if (!host_bufs[i]) return fail(PM_EINVAL, "pm_run_host: host buffer %zu is NULL", i);
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<void *> dev(nbufs, nullptr);
+    cudaEvent_t e[4] = {nullptr, nullptr, nullptr, nullptr};
+    pm_status rc = PM_OK;
+    float c_in = 0, c_out = 0;
+    for (int i = 0; i < 4 && rc == PM_OK; i++)
+        if (cudaEventCreate(&e[i]) != cudaSuccess) rc = fail(PM_ECUDA, "pm_run_host: cudaEventCreate failed");
+    for (size_t i = 0; i < nbufs && rc == PM_OK; i++)
+        if (cudaMallocAsync(&dev[i], spec[i].elems * dtype_size(spec[i].dtype), st) != cudaSuccess)
+            rc = fail(PM_ENOMEM, "pm_run_host: cudaMallocAsync of %s failed", spec[i].name);
+    if (rc == PM_OK) cudaEventRecord(e[0], st);
+    for (size_t i = 0; i < nbufs && rc == PM_OK; i++)
+        if (spec[i].role == PM_IN &&
+            cudaMemcpyAsync(dev[i], host_bufs[i], spec[i].elems * dtype_size(spec[i].dtype), cudaMemcpyHostToDevice,
+                            st) != cudaSuccess)
+            rc = fail(PM_ECUDA, "pm_run_host: host-to-device copy of %s failed", spec[i].name);
+    if (rc == PM_OK) cudaEventRecord(e[1], st);
+    if (rc == PM_OK) rc = timed(kp, dev.data(), nbufs, opts, stream, trial_ms, out);
+    if (rc == PM_OK) cudaEventRecord(e[2], st);
+    for (size_t i = 0; i < nbufs && rc == PM_OK; i++)
+        if (spec[i].role == PM_OUT &&
+            cudaMemcpyAsync(host_bufs[i], dev[i], spec[i].elems * dtype_size(spec[i].dtype), cudaMemcpyDeviceToHost,
+                            st) != cudaSuccess)
+            rc = fail(PM_ECUDA, "pm_run_host: device-to-host copy of %s failed", spec[i].name);
+    if (rc == PM_OK) {
+        cudaEventRecord(e[3], st);
+        if (cudaEventSynchronize(e[3]) != cudaSuccess) rc = fail(PM_ECUDA, "pm_run_host: synchronize failed");
+    }
+    if (rc == PM_OK) {
+        cudaEventElapsedTime(&c_in, e[0], e[1]);
+        cudaEventElapsedTime(&c_out, e[2], e[3]);
+        if (copy_ms) *copy_ms = (double)c_in + (double)c_out;
+    }
+    for (size_t i = 0; i < nbufs; i++)
+        if (dev[i]) cudaFreeAsync(dev[i], st);
+    cudaStreamSynchronize(st);
+    for (int i = 0; i < 4; i++)
+        if (e[i]) cudaEventDestroy(e[i]);
+    return rc;
+}
+
+}  // extern "C"

@@ -1,0 +1,185 @@
+"""Measurement-kernel collection (Section "Parameterized Collection of
+Kernels"): generators carry generator tags and, per argument, a list of
+allowed values; a generator emits one kernel variant per element of the
+Cartesian product of its argument lists.  Filter tags select generators
+(match condition identical / subset / superset (default) / intersect) and
+restrict argument values ("arg:v1,v2").
+
+The default collection is the calibration suite of the GB300 build: stream
+(global memory patterns), arithmetic loops, local-memory shuffle with and
+without per-iteration barriers, barrier, local/global overlap and empty
+kernels, plus the modeled computations and their work-removed twins.
+"""
+import itertools
+
+IDENTICAL, SUBSET, SUPERSET, INTERSECT = "identical", "subset", "superset", "intersect"
+
+SM_COUNT = 152
+RESIDENT = 8 * SM_COUNT   # 256-thread work-groups resident at full occupancy
+
+
+class Generator:
+    def __init__(self, kernel, tags, args, derive=None):
+        self.kernel = kernel
+        self.tags = set(tags)
+        self.args = {k: list(v) for k, v in args.items()}
+        self.derive = derive
+
+    def variants(self, restrict):
+        lists = []
+        for k, vals in self.args.items():
+            if k in restrict:
+                allowed = [v for v in vals if v in restrict[k]]
+                lists.append(allowed)
+            else:
+                lists.append(vals)
+        out = []
+        for combo in itertools.product(*lists):
+            p = dict(zip(self.args, combo))
+            if self.derive:
+                p = self.derive(p)
+                if p is None:
+                    continue
+            out.append((self.kernel, p))
+        return out
+
+
+def _fma_groups(p):
+    # constant total work per dtype: ~2^16 * 256 * RESIDENT operations for
+    # float32, 1/64 of that for float64 (GB300's FP64 rate is far lower)
+    F = p["F"]
+    total = (1 << 16) * RESIDENT if p["dtype"] == 0 else (1 << 10) * RESIDENT
+    p = dict(p)
+    p["G"] = max(SM_COUNT, total // F)
+    return p
+
+
+def _smem_groups(p):
+    p = dict(p)
+    p["G"] = max(SM_COUNT, RESIDENT * (1 << 14) // p["R"])
+    return p
+
+
+def _stream_extra(p):
+    # L in {2, 3} only at stride 1
+    if p["L"] in (2, 3) and p["s"] != 1:
+        return None
+    return p
+
+
+POW = lambda lo, hi, step=1: [1 << e for e in range(lo, hi + 1, step)]  # noqa: E731
+
+GENERATORS = [
+    Generator("stream", ["gmem", "stream", "suite"],
+              {"dtype": [0, 1], "vec": [1], "N": POW(20, 28, 2), "s": [1, 2, 4, 8, 16, 32], "L": [1, 2, 3, 4],
+               "shape": [0]}, _stream_extra),
+    Generator("stream", ["gmem", "stream2d", "suite"],
+              {"dtype": [0], "vec": [0], "N": POW(20, 28, 2), "L": [1, 2, 3, 4], "shape": [1], "W": [2048]}),
+    Generator("fma", ["ops", "flops_pattern", "suite"],
+              {"dtype": [0], "op": [0, 1, 2], "F": POW(10, 16)}, _fma_groups),
+    Generator("fma", ["ops", "flops_pattern", "fp64", "suite"],
+              {"dtype": [1], "op": [2], "F": POW(10, 16)}, _fma_groups),
+    Generator("smem", ["lmem", "suite"], {"R": POW(8, 14), "sync": [0, 1]}, _smem_groups),
+    Generator("barrier", ["sync", "suite"], {"B": POW(4, 14, 2), "G": [RESIDENT]}),
+    Generator("overlap", ["overlap", "suite"], {"m": [0, 1, 2, 4, 8, 12, 16, 24, 32], "N": [1 << 26]}),
+    Generator("empty", ["launch", "suite"], {"G": POW(6, 18)}),
+    Generator("mm_pf", ["matmul_sq", "modeled"], {"n": [256, 384, 512, 640, 768, 896]}),
+    Generator("mm_nopf", ["matmul_sq", "modeled"], {"n": [256, 384, 512, 640, 768, 896]}),
+    Generator("dg_nopf", ["dg", "modeled"], {"Np": [20, 35, 56, 84], "Nel": POW(14, 18), "L0": [16, 32]},
+              lambda p: dict(p, L1=256 // p["L0"])),
+    Generator("dg_dmpf", ["dg", "modeled"], {"Np": [20, 35, 56, 84], "Nel": POW(14, 18), "L0": [16, 32]},
+              lambda p: dict(p, L1=256 // p["L0"])),
+    Generator("fd_tile", ["finite_diff", "modeled"], {"n": POW(10, 14)}),
+    Generator("fd_direct", ["finite_diff", "modeled"], {"n": POW(10, 14)}),
+]
+
+
+def parse_filter(tags):
+    gen_tags, restrict = set(), {}
+    for t in tags:
+        if ":" in t:
+            k, vals = t.split(":", 1)
+            restrict[k] = [int(v) for v in vals.split(",")]
+        else:
+            gen_tags.add(t)
+    return gen_tags, restrict
+
+
+def generate(tags, match=SUPERSET, generators=None):
+    """Kernel variants [(kernel, params)] for filter tags."""
+    gen_tags, restrict = parse_filter(tags)
+    out = []
+    for g in generators or GENERATORS:
+        if match == IDENTICAL:
+            ok = g.tags == gen_tags
+        elif match == SUBSET:
+            ok = g.tags <= gen_tags
+        elif match == SUPERSET:
+            ok = g.tags >= gen_tags
+        else:
+            ok = bool(g.tags & gen_tags)
+        if ok:
+            out.extend(g.variants(restrict))
+    return out
+
+
+def calibration_suite():
+    return generate(["suite"])
+
+
+def algorithmic_bytes(kernel, p):
+    """Bytes a launch must move to/from global memory by its definition."""
+    if kernel == "stream":
+        size = 4 if p.get("dtype", 0) == 0 else 8
+        return (p.get("L", 1) + 1) * p["N"] * size
+    if kernel == "fma":
+        return 2 * p["G"] * 256 * (4 if p.get("dtype", 0) == 0 else 8)
+    if kernel in ("smem", "barrier"):
+        return 2 * p["G"] * 256 * 4
+    if kernel == "overlap":
+        return 2 * p["N"] * 4
+    return 0
+
+
+# ---------------------------------------------------------------- calibration models
+LAUNCH = "p_launch * f_sync_kernel_launch + p_group * f_thread_groups"
+
+
+def family_key(kernel, p):
+    """Which calibration model a suite variant belongs to."""
+    if kernel == "stream":
+        if p.get("shape", 0) == 1:
+            return "stream2d_f32"
+        return "stream_%s_s%d" % ("f32" if p["dtype"] == 0 else "f64", p["s"])
+    if kernel == "fma":
+        return "fma_%s_%s" % ("f32" if p["dtype"] == 0 else "f64", ("add", "mul", "madd")[p["op"]])
+    if kernel == "smem":
+        return "smem_sync%d" % p["sync"]
+    return kernel
+
+
+def family_model(key):
+    """(output feature, expression) of each family's model: the linear model
+    of Section "Models Demonstrated" restricted to the family's features, and
+    the tanh overlap model for the overlap kernel."""
+    if key.startswith("stream"):
+        return LAUNCH + " + p_gmem * f_mem_access_global"
+    if key.startswith("fma"):
+        dt = "float32" if "_f32_" in key else "float64"
+        op = key.rsplit("_", 1)[1]
+        extra = "" if op == "add" else " + p_%s * f_op_%s_%s" % (op, dt, op)
+        return LAUNCH + " + p_add * f_op_%s_add" % dt + extra
+    if key == "smem_sync0":
+        return LAUNCH + " + p_lmem * f_mem_access_local_float32"
+    if key == "smem_sync1":
+        return LAUNCH + " + p_lmem * f_mem_access_local_float32 + p_bar * f_sync_barrier_local * f_thread_groups"
+    if key == "barrier":
+        return LAUNCH + " + p_bar * f_sync_barrier_local * f_thread_groups"
+    if key == "overlap":
+        cg = "(p_gmem * f_mem_access_global_float32)"
+        co = "(p_lmem * f_mem_access_local_float32)"
+        return ("p_launch * f_sync_kernel_launch + %s * (tanh(p_edge * (%s - %s)) + 1) / 2 + "
+                "%s * (tanh(p_edge * (%s - %s)) + 1) / 2" % (cg, cg, co, co, co, cg))
+    if key == "empty":
+        return LAUNCH
+    raise KeyError(key)

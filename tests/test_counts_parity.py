@@ -1,0 +1,156 @@
+"""pm_counts (library closed forms) vs the oracle's brute-force enumeration:
+every record bit-exact, over sizes that span several tiles, ragged tails
+(guarded partial tiles), degenerate sizes, and paper-size values via exact
+quasi-polynomial interpolation.  Host code only -- no GPU needed."""
+import pytest
+
+import paper_1904_09538_gb300 as pm
+from oracle.features import features as ofeatures, feature_value as ofeature_value
+from oracle.quasipoly import extrapolate
+
+
+def _key(r):
+    if r["kind"] == "op":
+        return ("op", r["dtype"], r["op"])
+    if r["kind"] == "mem":
+        return ("mem", r["tag"], r["mem"], r["dir"])
+    return (r["kind"],)
+
+
+def compare(kernel, **params):
+    lib = [r for r in pm.counts(kernel, **params)]
+    orc = [r for r in ofeatures(kernel, **params) if r["kind"] != "grid"]
+    lk = {_key(r): r for r in lib}
+    ok = {_key(r): r for r in orc}
+    assert len(lk) == len(lib) and len(ok) == len(orc)
+    assert sorted(lk) == sorted(ok), (kernel, params, sorted(lk), sorted(ok))
+    for k, o in ok.items():
+        l = lk[k]
+        assert l["name"] == o["name"], (kernel, params, l["name"], o["name"])
+        assert l["count"] == o["count"] and l["gran"] == o["gran"], (kernel, params, k, l, o)
+        if o["kind"] == "op":
+            assert l["count_wi"] == o["count_wi"], (kernel, params, k)
+        if o["kind"] == "mem":
+            for f in ("lstr", "gstr", "loopstr", "accesses", "footprint", "count_wi", "count_sg", "dsize", "dtype"):
+                assert l[f] == o[f], (kernel, params, k, f, l[f], o[f])
+    return lib
+
+
+@pytest.mark.parametrize("dtype,vec,s,L,shape,N,W", [
+    (0, 0, 1, 1, 0, 256 * 8, 16), (0, 0, 2, 2, 0, 256 * 8, 16), (0, 1, 4, 3, 0, 4 * 256 * 16, 16),
+    (1, 0, 8, 4, 0, 256 * 16, 16), (1, 1, 32, 2, 0, 2 * 256 * 64, 16), (0, 0, 1, 4, 1, 32 * 64, 32),
+    (1, 1, 1, 1, 1, 2 * 16 * 48 * 3, 48)])
+def test_stream(dtype, vec, s, L, shape, N, W):
+    compare("stream", dtype=dtype, vec=vec, N=N, s=s, L=L, shape=shape, W=W)
+
+
+@pytest.mark.parametrize("dtype,op,F,G", [(0, 0, 32, 1), (0, 1, 64, 3), (0, 2, 1024, 2), (1, 2, 96, 1), (1, 0, 64, 2)])
+def test_fma(dtype, op, F, G):
+    compare("fma", dtype=dtype, op=op, F=F, G=G)
+
+
+@pytest.mark.parametrize("R,sync,G", [(4, 0, 1), (64, 1, 3), (256, 0, 2)])
+def test_smem(R, sync, G):
+    compare("smem", R=R, sync=sync, G=G)
+
+
+def test_barrier_overlap_empty():
+    compare("barrier", B=0, G=2)
+    compare("barrier", B=17, G=3)
+    for m in (0, 1, 5):
+        compare("overlap", m=m, N=768)
+    compare("empty", G=1)
+    compare("empty", G=77)
+
+
+@pytest.mark.parametrize("kernel", ["mm_pf", "mm_nopf", "mm_pf_a", "mm_pf_b", "mm_nopf_a", "mm_nopf_b"])
+@pytest.mark.parametrize("n", [16, 32, 48, 80])
+def test_mm(kernel, n):
+    compare(kernel, n=n)
+
+
+DG = ["dg_nopf", "dg_dmpf", "dg_nopf_u", "dg_nopf_dm", "dg_dmpf_u", "dg_dmpf_dm", "dg_res"]
+
+
+@pytest.mark.parametrize("kernel", DG)
+@pytest.mark.parametrize("Np,Nel,L0,L1", [(20, 32, 16, 16), (35, 64, 32, 8), (56, 32, 16, 16), (84, 32, 32, 8),
+                                          (1, 16, 16, 16), (7, 32, 32, 8), (16, 16, 16, 16), (33, 32, 32, 8)])
+def test_dg(kernel, Np, Nel, L0, L1):
+    compare(kernel, Np=Np, Nel=Nel, L0=L0, L1=L1)
+
+
+FD = ["fd_tile", "fd_direct", "fd_tile_u", "fd_tile_res", "fd_direct_u", "fd_direct_res"]
+
+
+@pytest.mark.parametrize("kernel", FD)
+@pytest.mark.parametrize("n", [1, 2, 13, 14, 15, 16, 17, 28, 29, 45, 64])
+def test_fd(kernel, n):
+    compare(kernel, n=n)
+
+
+def test_paper_sizes_by_interpolation():
+    # library counts at the configuration sizes equal the oracle's exact
+    # interpolation from brute-force samples on the same residue class
+    def series(kernel, what, **fixed):
+        cache = {}
+
+        def f(x):
+            if x not in cache:
+                p = dict(fixed)
+                p[what[0]] = x
+                recs = ofeatures(kernel, **p)
+                cache[x] = {(r["name"].split("_lstrides")[0] if r["kind"] == "mem" else r["name"]): r["count"]
+                            for r in recs if r["kind"] != "grid"}
+            return cache[x]
+        return f
+
+    def check(kernel, var, target, period, degree, start, **fixed):
+        f = series(kernel, (var,), **fixed)
+        lib = {(r["name"].split("_lstrides")[0] if r["kind"] == "mem" else r["name"]): r["count"]
+               for r in pm.counts(kernel, **dict(fixed, **{var: target}))}
+        for key in f(start):
+            want = extrapolate(lambda x: f(x)[key], target, period, degree, start)
+            assert lib[key] == want, (kernel, key, lib[key], want)
+
+    for n in (256, 768, 896):
+        check("mm_pf", "n", n, 16, 3, 16)
+        check("mm_nopf", "n", n, 16, 3, 16)
+    # stencil tile variant: quasi-polynomial of period 14 in n
+    for n in (1024, 4096):
+        check("fd_tile", "n", n, 14, 2, 14 + n % 14)
+        check("fd_direct", "n", n, 16, 2, 16 + n % 16)
+    # DG: linear in Nel at fixed Np, shape
+    for Np in (20, 35, 56, 84):
+        check("dg_dmpf", "Nel", 1 << 14, 16, 1, 16, Np=Np, L0=16, L1=16)
+        check("dg_nopf", "Nel", 1 << 14, 32, 1, 32, Np=Np, L0=32, L1=8)
+
+
+def test_feature_values_match_oracle():
+    expr = ("p_launch * f_sync_kernel_launch + p_group * f_thread_groups + "
+            "p_bar * f_sync_barrier_local * f_thread_groups + "
+            "p_madd * f_op_float32_madd + p_add * f_op_float32_add + p_mul * f_op_float32_mul + "
+            "p_lmem * f_mem_access_local_float32 + "
+            "p_g * f_mem_access_global_float32_lstrides:{0:1;1:>1}_gstrides:{0:16;1:>16}_afr:1 + "
+            "p_a * f_mem_access_tag:mm-PF-a + p_b * f_mem_access_global_float32_load_gstrides:{0:16}_afr:>1")
+    m = pm.Model("f_wall_time", expr)
+    for kernel, params in (("mm_pf", dict(n=48)), ("mm_nopf", dict(n=32)), ("fd_tile", dict(n=29)),
+                           ("dg_dmpf", dict(Np=35, Nel=64, L0=32, L1=8)), ("stream", dict(N=4096, shape=1, W=32))):
+        row = m.feature_values(kernel, **params)
+        recs = ofeatures(kernel, **params)
+        want = [ofeature_value(f, recs) for f in m.features]
+        assert list(row) == want, (kernel, list(row), want)
+
+
+def test_bad_parameters_rejected():
+    with pytest.raises(pm.PMError):
+        pm.counts("mm_pf", n=17)
+    with pytest.raises(pm.PMError):
+        pm.counts("stream", N=1000)
+    with pytest.raises(pm.PMError):
+        pm.counts("dg_nopf", Np=20, Nel=32, L0=8, L1=32)
+    with pytest.raises(pm.PMError):
+        pm.counts("no_such_kernel")
+    with pytest.raises(pm.PMError):
+        pm.Model("t", "p_a * (f_x")
+    with pytest.raises(pm.PMError):
+        pm.Model("t", "p_a * f_mem_access_float32_global")

@@ -1,0 +1,216 @@
+"""GPU calibration parity: pm_fit / batched plan / autograd kernels / pm_predict
+vs the FP64 oracle (scipy leastsq, column-scaled least squares, symbolic
+derivatives).  Parameter agreement is measured as max_i |p_i - p_i*| / |p_i*|."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import pm_inputs  # noqa: E402
+import paper_1904_09538_gb300 as pm  # noqa: E402
+from paper_1904_09538_gb300 import autograd as pag  # noqa: E402
+from oracle import fit as ofit  # noqa: E402
+from oracle.model import Model as OModel, overlap_expr  # noqa: E402
+
+PTOL = 1e-6
+
+
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+def perr(p, ref):
+    """max_i |p_i - ref_i| / |ref_i| (parameters carry different units)."""
+    ref = np.asarray(ref, dtype=np.float64)
+    return float(np.max(np.abs(np.asarray(p) - ref) / np.abs(ref)))
+
+
+LIN = ("p_launch * f_sync_kernel_launch + p_group * f_thread_groups + p_add * f_op_float32_add + "
+       "p_madd * f_op_float32_madd + p_gmem * f_mem_access_global_float32 + p_lmem * f_mem_access_local_float32")
+OVL = overlap_expr("p_launch * f_sync_kernel_launch + p_group * f_thread_groups",
+                   "p_gmem * f_mem_access_global_float32",
+                   "p_madd * f_op_float32_madd + p_lmem * f_mem_access_local_float32")
+
+
+def design(l, seed, nf=6):
+    """Feature rows: launch = 1, work-groups in [1e2, 1e4], counts in [1e5, 1e7]."""
+    X = pm_inputs.integers((l, nf), seed, 10 ** 5, 10 ** 7).astype(np.float64)
+    X[:, 0] = 1.0
+    X[:, 1] = pm_inputs.integers((l,), seed + 1000, 100, 10 ** 4)
+    return X
+
+
+def synth(expr, X, p_true, sigma, seed):
+    """Outputs of the model at p_true (a name -> value dict), with relative noise."""
+    om = OModel("f_wall_time", expr)
+    F = [dict(zip(om.features, row)) for row in X]
+    t = np.array([om.eval(p_true, f) for f in F])
+    return t * (1 + sigma * pm_inputs.noise((len(t),), seed)), om, F
+
+
+def vec(model, pd):
+    return np.array([pd[n] for n in model.params])
+
+
+P_LIN = dict(p_launch=5e-6, p_group=2e-9, p_add=4e-12, p_madd=3e-12, p_gmem=6e-12, p_lmem=2e-12)
+P_OVL = dict(p_launch=5e-6, p_group=2e-9, p_gmem=6e-12, p_madd=3e-12, p_lmem=2e-12, p_edge=3e4)
+
+
+@pytest.mark.parametrize("sigma", [0.0, 1e-3, 1e-2])
+def test_linear_fit_vs_oracle(sigma):
+    dev()
+    X = design(120, 3)
+    t, om, F = synth(LIN, X, P_LIN, sigma, 4)
+    m = pm.Model("f_wall_time", LIN)
+    assert m.is_linear and m.features == om.features
+    p, rep = m.fit(X, t)
+    po, info = ofit.fit(om, F, t)
+    assert rep["status"] == 0 and rep["linear"] and rep["rank"] == 6
+    assert perr(p, po) <= PTOL, perr(p, po)
+    if sigma == 0:
+        assert perr(p, vec(om, P_LIN)) <= PTOL
+
+
+def test_rank_deficient_matmul_design():
+    # flops, global, local, work-groups on the PF matmul at n = 256..768 are
+    # rank 2 (all columns in span{n^3, n^2}); predictions at n = 896 are unique
+    dev()
+    expr = ("p_f * f_op_float32_madd + p_g * f_mem_access_global_float32 + p_s * f_mem_access_local_float32 + "
+            "p_l * f_thread_groups")
+    m = pm.Model("f_wall_time", expr)
+    om = OModel("f_wall_time", expr)
+    ns = [256, 384, 512, 640, 768]
+    X = np.array([m.feature_values("mm_pf", n=n) for n in ns])
+    t = np.array([1e-12 * n ** 3 + 3e-10 * n ** 2 for n in ns])
+    p, rep = m.fit(X, t)
+    po, info = ofit.fit(om, [dict(zip(om.features, r)) for r in X], t)
+    assert info["rank_deficient"] and rep["status"] == -5 and rep["rank"] == info["rank"] == 2
+    x896 = m.feature_values("mm_pf", n=896)
+    pred = m.predict(p, x896[None, :])[0]
+    pred_o = float(x896 @ po)
+    assert abs(pred / pred_o - 1) <= 1e-6
+    assert perr(p, po) <= 1e-5  # min-norm solutions in the same column-scaled coordinates
+
+
+@pytest.mark.parametrize("sigma,seed", [(0.0, 5), (1e-3, 6), (1e-2, 7)])
+def test_overlap_fit_vs_oracle(sigma, seed):
+    dev()
+    X = design(200, seed, nf=5)
+    t, om, F = synth(OVL, X, P_OVL, sigma, seed + 100)
+    m = pm.Model("f_wall_time", OVL)
+    assert not m.is_linear
+    p0 = vec(om, P_OVL) * (1 + 0.3 * pm_inputs.uniform((6,), seed, dtype=np.float64))
+    p, rep = m.fit(X, t, p0=p0)
+    po, info = ofit.fit(om, F, t, p0=p0)
+    assert rep["status"] == 0, rep
+    assert perr(p, po) <= PTOL, (perr(p, po), p, po)
+
+
+def test_overlap_fit_default_start_point():
+    dev()
+    X = design(150, 9, nf=5)
+    t, om, F = synth(OVL, X, P_OVL, 1e-3, 10)
+    m = pm.Model("f_wall_time", OVL)
+    p, rep = m.fit(X, t)
+    po, _ = ofit.fit(om, F, t)
+    pred = m.predict(p, X)
+    pred_o = ofit.predict(om, po, F)
+    assert np.max(np.abs(pred / pred_o - 1)) <= 1e-5
+
+
+def test_batched_uneven_matches_single_and_oracle():
+    dev()
+    K = 12
+    ls = pm_inputs.row_counts(K, 42)
+    models, Xs, ts, p0s, refs = [], [], [], [], []
+    for k in range(K):
+        expr = LIN if k % 2 == 0 else OVL
+        nf = 6 if k % 2 == 0 else 5
+        ptrue = P_LIN if k % 2 == 0 else P_OVL
+        X = design(int(ls[k]), 200 + k, nf=nf)
+        t, om, F = synth(expr, X, ptrue, 1e-2, 300 + k)
+        p0 = vec(om, ptrue) * 1.2
+        models.append(pm.Model("f_wall_time", expr))
+        Xs.append(X)
+        ts.append(t)
+        p0s.append(p0)
+        refs.append(ofit.fit(om, F, t, p0=p0)[0])
+    for threads in (64, 128, 256):
+        ps, reps = pm.fit_batched(models, Xs, ts, p0s, threads=threads)
+        for k in range(K):
+            assert reps[k]["status"] == 0, (k, reps[k])
+            assert perr(ps[k], refs[k]) <= PTOL, (k, perr(ps[k], refs[k]))
+    single, _ = models[1].fit(Xs[1], ts[1], p0=p0s[1])
+    ps, _ = pm.fit_batched(models, Xs, ts, p0s, threads=128)
+    assert np.array_equal(single, ps[1])
+
+
+def test_autograd_residual_gradient_and_jacobian():
+    d = dev()
+    X = design(64, 51, nf=5)
+    t, om, F = synth(OVL, X, P_OVL, 1e-2, 52)
+    m = pm.Model("f_wall_time", OVL)
+    p = vec(om, P_OVL) * 1.1
+    Xd = torch.from_numpy(X.astype(np.float32)).to(d)
+    td = torch.from_numpy(t.astype(np.float32)).to(d)
+    pd = torch.from_numpy(p).to(d).requires_grad_(True)
+    r = pag.Residual.apply(pd, m, Xd, td)
+    r_or, J_or = ofit.residual_and_jacobian(om, F, t)
+    assert np.max(np.abs(r.detach().cpu().numpy() - r_or(p))) <= 1e-5
+    rbar = pm_inputs.normal((64,), 53)
+    (g,) = torch.autograd.grad(r, pd, grad_outputs=torch.from_numpy(rbar).to(d))
+    J = J_or(p)
+    want = J.T @ rbar.astype(np.float64)
+    scale = np.abs(J).T @ np.abs(rbar)
+    assert np.all(np.abs(g.cpu().numpy() - want) <= 1e-5 * scale)
+    # Jacobian vs FP64 central differences, h = 1e-3 in scaled coordinates q = p / |p|
+    Jg = pag.jacobian(m, Xd, td, pd.detach()).cpu().numpy()
+    for i in range(len(p)):
+        h = 1e-3 * abs(p[i])
+        pp, pm_ = p.copy(), p.copy()
+        pp[i] += h
+        pm_[i] -= h
+        fd = (r_or(pp) - r_or(pm_)) / (2 * h)
+        assert np.all(np.abs(Jg[:, i] - fd) <= 1e-4 * (np.abs(fd).max() + 1e-30)), i
+    # the torch.autograd gradcheck-style consistency: backward == J^T rbar
+    assert np.allclose(g.cpu().numpy(), Jg.T.astype(np.float64) @ rbar, rtol=1e-4, atol=1e-4 * scale.max())
+
+
+def test_autograd_lm_matches_oracle():
+    d = dev()
+    X = design(150, 61, nf=5)
+    t, om, F = synth(OVL, X, P_OVL, 1e-2, 62)
+    m = pm.Model("f_wall_time", OVL)
+    p0 = vec(om, P_OVL) * 1.25
+    Xd = torch.from_numpy(X.astype(np.float32)).to(d)
+    td = torch.from_numpy(t.astype(np.float32)).to(d)
+    p, iters = pag.lm_fit(m, Xd, td, p0)
+    po, _ = ofit.fit(om, F, t, p0=p0)
+    assert perr(p, po) <= 1e-5, perr(p, po)
+
+
+def test_predict_fp64():
+    dev()
+    X = design(50, 71, nf=5)
+    m = pm.Model("f_wall_time", OVL)
+    om = OModel("f_wall_time", OVL)
+    p = vec(om, P_OVL)
+    got = m.predict(p, X)
+    want = ofit.predict(om, p, [dict(zip(om.features, r)) for r in X])
+    assert np.max(np.abs(got / want - 1)) <= 1e-13
+
+
+def test_fit_rejects_bad_data():
+    dev()
+    m = pm.Model("f_wall_time", LIN)
+    X = design(20, 81)
+    t = np.ones(20)
+    t[3] = -1.0
+    with pytest.raises(pm.PMError):
+        m.fit(X, t)
+    t[3] = np.nan
+    with pytest.raises(pm.PMError):
+        m.fit(X, t)

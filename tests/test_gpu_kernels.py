@@ -1,0 +1,241 @@
+"""GPU parity: every kernel's output vs the CPU oracle on the same seeded
+inputs, through the C ABI.  Bit-exact where the kernel's operation order is
+fixed (suite kernels, work-removed twins); within 1e-5 of the FP64
+reference, relative to sum |terms| (condition-aware), for matmul, DG and
+stencil.  Buffers carry guard bands that must stay untouched."""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import pm_inputs  # noqa: E402
+import paper_1904_09538_gb300 as pm  # noqa: E402
+from oracle import refs  # noqa: E402
+
+TOL = 1e-5
+GUARD = 64
+SENT = {np.float32: 1234.5, np.float64: -4321.25}
+
+
+def dev():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return torch.device("cuda:0")
+
+
+class Guarded:
+    """Device buffer with GUARD sentinel elements on both sides."""
+
+    def __init__(self, n, dtype, data=None):
+        tdt = torch.float32 if dtype == np.float32 else torch.float64
+        self.n, self.dtype = n, dtype
+        self.full = torch.full((n + 2 * GUARD,), SENT[dtype], dtype=tdt, device=dev())
+        self.view = self.full[GUARD:GUARD + n]
+        if data is not None:
+            self.view.copy_(torch.from_numpy(np.ascontiguousarray(data).ravel()))
+
+    def check(self):
+        f = self.full.cpu().numpy()
+        assert np.all(f[:GUARD] == SENT[self.dtype]) and np.all(f[GUARD + self.n:] == SENT[self.dtype]), "guard hit"
+
+    def get(self):
+        return self.view.cpu().numpy()
+
+
+def run_kernel(kernel, inputs, **params):
+    """Allocate guarded buffers per pm_kernel_buffers, launch, return outputs."""
+    dev()
+    spec = pm.kernel_buffers(kernel, **params)
+    bufs, it = [], iter(inputs)
+    for b in spec:
+        if b["role"] == "in":
+            bufs.append(Guarded(b["elems"], b["dtype"], next(it)))
+        else:
+            bufs.append(Guarded(b["elems"], b["dtype"]))
+    pm.launch(kernel, [b.view for b in bufs], **params)
+    torch.cuda.synchronize()
+    for b in bufs:
+        b.check()
+    return [b.get() for b, s in zip(bufs, spec) if s["role"] == "out"]
+
+
+@pytest.mark.parametrize("dtype,vec,s,L,shape,W", [
+    (0, 0, 1, 1, 0, 16), (0, 0, 2, 2, 0, 16), (0, 1, 1, 2, 0, 16), (0, 1, 32, 4, 0, 16), (1, 0, 4, 3, 0, 16),
+    (1, 1, 1, 4, 0, 16), (0, 0, 1, 3, 1, 64), (1, 1, 16, 1, 0, 16), (0, 1, 8, 2, 1, 128)])
+def test_stream_bitexact(dtype, vec, s, L, shape, W):
+    N = 1 << 17
+    dt = np.float32 if dtype == 0 else np.float64
+    xs = [pm_inputs.uniform((N,), 40 + a, dtype=dt) for a in range(L)]
+    (out,) = run_kernel("stream", xs, dtype=dtype, vec=vec, N=N, s=s, L=L, shape=shape, W=W)
+    assert np.array_equal(out, refs.stream(xs))
+
+
+@pytest.mark.parametrize("dtype", [0, 1])
+@pytest.mark.parametrize("op", [0, 1, 2])
+@pytest.mark.parametrize("F", [32, 1024, 3200])
+def test_fma_bitexact(dtype, op, F):
+    G = 5
+    dt = np.float32 if dtype == 0 else np.float64
+    seed = pm_inputs.uniform((G * 256,), 7, dtype=dt)
+    (out,) = run_kernel("fma", [seed], dtype=dtype, op=op, F=F, G=G)
+    assert np.array_equal(out, refs.fma(seed, op, F))
+
+
+@pytest.mark.parametrize("kernel,params", [("smem", dict(R=64, sync=0, G=7)), ("smem", dict(R=256, sync=1, G=3)),
+                                           ("barrier", dict(B=0, G=2)), ("barrier", dict(B=33, G=9)),
+                                           ("overlap", dict(m=0, N=2048)), ("overlap", dict(m=12, N=4096))])
+def test_copy_kernels(kernel, params):
+    n = pm.kernel_buffers(kernel, **params)[0]["elems"]
+    x = pm_inputs.uniform((n,), 3)
+    (out,) = run_kernel(kernel, [x], **params)
+    assert np.array_equal(out, x)
+
+
+def test_empty():
+    run_kernel("empty", [], G=4096)
+
+
+def cond_err(out, ref, rabs):
+    return float(np.max(np.abs(out.astype(np.float64) - ref) / np.maximum(rabs, 1e-300)))
+
+
+@pytest.mark.parametrize("kernel", ["mm_pf", "mm_nopf"])
+@pytest.mark.parametrize("n", [16, 48, 128, 768])
+def test_matmul(kernel, n):
+    a, b = pm_inputs.uniform((n, n), 1), pm_inputs.uniform((n, n), 2)
+    (c,) = run_kernel(kernel, [a, b], n=n)
+    ref, rabs = refs.matmul(a, b)
+    assert cond_err(c.reshape(n, n), ref, rabs) <= TOL
+
+
+@pytest.mark.parametrize("kernel", ["mm_pf_a", "mm_pf_b", "mm_nopf_a", "mm_nopf_b"])
+@pytest.mark.parametrize("n", [16, 80])
+def test_matmul_twins_bitexact(kernel, n):
+    x = pm_inputs.uniform((n, n), 5)
+    (d,) = run_kernel(kernel, [x], n=n)
+    assert np.array_equal(d.reshape(n, n), refs.mm_twin(kernel, x))
+
+
+DG_CASES = [(20, 64, 16, 16), (35, 96, 32, 8), (56, 32, 16, 16), (84, 64, 32, 8), (1, 16, 16, 16), (33, 64, 32, 8)]
+
+
+@pytest.mark.parametrize("kernel", ["dg_nopf", "dg_dmpf"])
+@pytest.mark.parametrize("Np,Nel,L0,L1", DG_CASES)
+def test_dg(kernel, Np, Nel, L0, L1):
+    D, u = pm_inputs.normal((3, Np, Np), 11), pm_inputs.normal((Nel, Np), 12)
+    (res,) = run_kernel(kernel, [D, u], Np=Np, Nel=Nel, L0=L0, L1=L1)
+    ref, rabs = refs.dg(D, u)
+    assert cond_err(res.reshape(3, Nel, Np), ref, rabs) <= TOL
+
+
+@pytest.mark.parametrize("kernel", ["dg_nopf_u", "dg_nopf_dm", "dg_dmpf_u", "dg_dmpf_dm"])
+@pytest.mark.parametrize("Np,Nel,L0,L1", DG_CASES[:4])
+def test_dg_twins_bitexact(kernel, Np, Nel, L0, L1):
+    D, u = pm_inputs.normal((3, Np, Np), 13), pm_inputs.normal((Nel, Np), 14)
+    ins = [u] if kernel.endswith("_u") else [D]
+    (d,) = run_kernel(kernel, ins, Np=Np, Nel=Nel, L0=L0, L1=L1)
+    assert np.array_equal(d.reshape(-1, Nel), refs.dg_twin(kernel, D, u, L0, L1))
+
+
+def test_dg_res_twin_writes_zeros():
+    (r,) = run_kernel("dg_res", [], Np=20, Nel=32, L0=16, L1=16)
+    assert np.all(r == 0)
+
+
+@pytest.mark.parametrize("kernel", ["fd_tile", "fd_direct"])
+@pytest.mark.parametrize("n", [1, 13, 14, 29, 100, 1024])
+def test_stencil(kernel, n):
+    u = pm_inputs.uniform((n + 2, n + 2), 21)
+    (r,) = run_kernel(kernel, [u], n=n, c0=-4.0, c1=1.0)
+    ref, rabs = refs.stencil(u, -4.0, 1.0)
+    assert cond_err(r.reshape(n, n), ref, rabs) <= TOL
+
+
+@pytest.mark.parametrize("kernel", ["fd_tile_u", "fd_direct_u"])
+@pytest.mark.parametrize("n", [13, 45, 100])
+def test_stencil_twins_bitexact(kernel, n):
+    u = pm_inputs.uniform((n + 2, n + 2), 22)
+    (d,) = run_kernel(kernel, [u], n=n)
+    want = refs.fd_twin(kernel, u)
+    assert np.array_equal(d.reshape(want.shape), want)
+
+
+@pytest.mark.parametrize("kernel", ["fd_tile_res", "fd_direct_res"])
+def test_stencil_res_twins(kernel):
+    (r,) = run_kernel(kernel, [], n=37)
+    assert np.all(r == 0)
+
+
+# ---------------------------------------------------------------- full sizes, sampled
+def test_stream_full_size_sampled():
+    d = dev()
+    N = 1 << 28
+    L = 2
+    gen = torch.Generator(device=d)
+    gen.manual_seed(77)
+    xs = [torch.rand(N, device=d, generator=gen) * 2 - 1 for _ in range(L)]
+    out = torch.empty(N, device=d)
+    pm.launch("stream", xs + [out], N=N, L=L, vec=1)
+    torch.cuda.synchronize()
+    idx = torch.from_numpy(pm_inputs.integers((4096,), 5, 0, N - 1)).to(d)
+    samples = [x[idx].cpu().numpy() for x in xs]
+    assert np.array_equal(out[idx].cpu().numpy(), refs.stream(samples))
+    del xs, out
+
+
+def test_dg_full_size_sampled():
+    Np, Nel = 84, 1 << 18
+    D, u = pm_inputs.normal((3, Np, Np), 31), pm_inputs.normal((Nel, Np), 32)
+    d = dev()
+    res = torch.empty(3 * Nel * Np, device=d)
+    for kernel, L0, L1 in (("dg_dmpf", 16, 16), ("dg_nopf", 32, 8)):
+        pm.launch(kernel, [torch.from_numpy(D).to(d), torch.from_numpy(u).to(d), res], Np=Np, Nel=Nel, L0=L0, L1=L1)
+        torch.cuda.synchronize()
+        ks = np.unique(pm_inputs.integers((512,), 33, 0, Nel - 1))
+        ref, rabs = refs.dg(D, u[ks])
+        got = res.cpu().numpy().reshape(3, Nel, Np)[:, ks, :]
+        assert cond_err(got, ref, rabs) <= TOL
+
+
+def test_stencil_full_size_sampled():
+    n = 16384
+    d = dev()
+    gen = torch.Generator(device=d)
+    gen.manual_seed(5)
+    u = torch.rand((n + 2) * (n + 2), device=d, generator=gen) * 2 - 1
+    r = torch.empty(n * n, device=d)
+    for kernel in ("fd_tile", "fd_direct"):
+        pm.launch(kernel, [u, r], n=n, c0=-4.0, c1=1.0)
+        torch.cuda.synchronize()
+        for i0 in (0, 7777, n - 9):
+            win = u.view(n + 2, n + 2)[i0:i0 + 11].cpu().numpy()
+            ref, rabs = refs.stencil_rows(win, -4.0, 1.0)
+            got = r.view(n, n)[i0:i0 + 9].cpu().numpy()
+            assert cond_err(got, ref, rabs) <= TOL
+
+
+# ---------------------------------------------------------------- timing entry points
+def test_run_timing_and_host_path():
+    d = dev()
+    N = 1 << 20
+    xs = [pm_inputs.uniform((N,), 60 + a) for a in range(2)]
+    bufs = [torch.from_numpy(x).to(d) for x in xs] + [torch.empty(N, device=d)]
+    tm = pm.run("stream", bufs, warmup=3, trials=60, want_trials=True, N=N, L=2)
+    assert tm["n_trials"] == 60 and tm["mean_ms"] > 0 and len(tm["trials_ms"]) == 60
+    assert tm["min_ms"] <= tm["median_ms"] <= tm["max_ms"]
+    host_out = np.zeros(N, np.float32)
+    th = pm.run_host("stream", xs + [host_out], warmup=1, trials=3, N=N, L=2)
+    assert th["copy_ms"] > 0
+    assert np.array_equal(host_out, refs.stream(xs))
+
+
+def test_launch_errors():
+    d = dev()
+    x = torch.zeros(1024, device=d)
+    with pytest.raises(pm.PMError):
+        pm.launch("stream", [x], N=1024, L=1)               # too few buffers
+    with pytest.raises(pm.PMError):
+        pm.launch("stream", [x, x], N=1000, L=1)            # N not a multiple of 256
+    with pytest.raises(pm.PMError):
+        pm.launch("mm_pf", [x, x, x], n=24)                 # n not a multiple of 16
