@@ -5,10 +5,15 @@
 // scale_features_by_output); Jacobian by reverse-mode differentiation of the
 // model's SSA program (the paper differentiates the model symbolically).
 //
-// Precision: residuals, Jacobians and their reductions (J^T J, J^T r, SSR)
-// run in FP32 with compensated (TwoSum) FP32 accumulation; FP64 is used for
-// the normal-equation solve (Cholesky, or a Jacobi eigen-decomposition for
-// rank-deficient linear designs) and the Levenberg-Marquardt damping update.
+// Precision: everything per row runs on the FP32 pipes.  The Jacobian is
+// plain FP32 (it only steers the iteration); the residual, which fixes the
+// solution, is evaluated in float-float arithmetic (pairs of FP32 with
+// error-free TwoSum / TwoProd transformations) from float-float copies of the
+// features and outputs; J^T J, J^T r and the SSR are accumulated with exact
+// FP32 products (TwoProd) and compensated FP32 sums.  FP64 is used only for
+// the m x m normal-equation solve (Cholesky, or a Jacobi eigen-decomposition
+// for rank-deficient linear designs) and the Levenberg-Marquardt damping
+// update.
 //
 // Batched path: one CTA per model in one persistent kernel launch; a plan
 // captures [H2D copies -> FP64->FP32 conversion -> fit kernel -> D2H copies]
@@ -21,6 +26,7 @@
 #include <new>
 #include <vector>
 
+#include "pm_df.cuh"
 #include "pm_internal.h"
 #include "pm_model.h"
 
@@ -33,7 +39,7 @@ namespace {
 
 constexpr int MP = kMaxParamsFit;               // max parameters
 constexpr int NENT = MP * (MP + 1) / 2 + MP + 1; // A (upper), b, ssr
-constexpr float EPS32 = 5.9604645e-8f;
+constexpr double EPS_DF = 1e-13;  // relative accuracy of a float-float residual (conservative)
 
 struct FitJob {
     const Ins *code;
@@ -42,8 +48,8 @@ struct FitJob {
     int m, nf, l;
     int linear, use_p0;
     unsigned start_mask;
-    const float *X;   // l x nf
-    const float *t;   // l
+    const float2 *X;  // l x nf, (hi, lo) float-float
+    const float2 *t;  // l, (hi, lo)
     double *p;        // m, in/out
     double *rep;      // 8 per job
 };
@@ -95,6 +101,59 @@ __device__ T forward(const Ins *code, int n, const F *frow, const T *par, T *v) 
     return v[n - 1];
 }
 
+// Forward sweep in float-float.
+__device__ df forward_df(const Ins *code, int n, const float2 *frow, const df *par, df *v) {
+    for (int k = 0; k < n; k++) {
+        const Ins in = code[k];
+        df x;
+        switch (in.op) {
+        case OP_FEAT: { const float2 f = frow[in.arg]; x = df{f.x, f.y}; break; }
+        case OP_PAR: x = par[in.arg]; break;
+        case OP_CONST: {
+            const float h = (float)in.c;
+            x = df{h, (float)(in.c - (double)h)};
+            break;
+        }
+        case OP_ADD: x = df_add(v[in.a], v[in.b]); break;
+        case OP_SUB: x = df_sub(v[in.a], v[in.b]); break;
+        case OP_MUL: x = df_mul(v[in.a], v[in.b]); break;
+        case OP_DIV: x = df_div(v[in.a], v[in.b]); break;
+        case OP_NEG: x = df_neg(v[in.a]); break;
+        case OP_TANH: x = df_tanh(v[in.a]); break;
+        case OP_EXP: x = df_exp(v[in.a]); break;
+        case OP_LOG: x = df_log(v[in.a]); break;
+        default: x = df_sqrt(v[in.a]);
+        }
+        v[k] = x;
+    }
+    return v[n - 1];
+}
+
+// Reverse sweep over the high parts of float-float forward values.
+__device__ void reverse_df(const Ins *code, int n, const df *vd, float *adj, float *g, int m) {
+    for (int k = 0; k < n; k++) adj[k] = 0.0f;
+    for (int i = 0; i < m; i++) g[i] = 0.0f;
+    adj[n - 1] = 1.0f;
+    for (int k = n - 1; k >= 0; k--) {
+        const float a = adj[k];
+        if (a == 0.0f) continue;
+        const Ins in = code[k];
+        switch (in.op) {
+        case OP_PAR: g[in.arg] += a; break;
+        case OP_ADD: adj[in.a] += a; adj[in.b] += a; break;
+        case OP_SUB: adj[in.a] += a; adj[in.b] -= a; break;
+        case OP_MUL: adj[in.a] += a * vd[in.b].hi; adj[in.b] += a * vd[in.a].hi; break;
+        case OP_DIV: adj[in.a] += a / vd[in.b].hi; adj[in.b] -= a * vd[k].hi / vd[in.b].hi; break;
+        case OP_NEG: adj[in.a] -= a; break;
+        case OP_TANH: adj[in.a] += a * (1.0f - vd[k].hi * vd[k].hi); break;
+        case OP_EXP: adj[in.a] += a * vd[k].hi; break;
+        case OP_LOG: adj[in.a] += a / vd[in.a].hi; break;
+        case OP_SQRT: adj[in.a] += a * 0.5f / vd[k].hi; break;
+        default: break;
+        }
+    }
+}
+
 // Reverse sweep: g[i] = dv[n-1]/dpar[i] (FP32).
 __device__ void reverse(const Ins *code, int n, const float *v, float *adj, float *g, int m) {
     for (int k = 0; k < n; k++) adj[k] = 0.0f;
@@ -139,10 +198,10 @@ template <int T>
 struct Smem {
     Ins code[kMaxIns];
     float J[T * (MP + 1)];
-    float r[T];
+    float r[T], rl[T];
     double acc[NENT];
     double q[MP], s[MP], dq[MP], qt[MP];
-    float pf[MP];
+    df pd[MP];
     double M[MP][MP + 1], V[MP][MP + 1], rhs[MP], y[MP];
     int idx[MP];
     double red[T / 32];
@@ -156,12 +215,19 @@ __device__ void load_code(Smem<T> &S, const Ins *code, int n) {
     __syncthreads();
 }
 
-// p = s * q (per active parameter) -> FP32 copy for evaluation
+// p = s * q -> float-float copy for evaluation
 template <int T>
 __device__ void set_params(Smem<T> &S, const double *q, int m) {
-    if (threadIdx.x < m) S.pf[threadIdx.x] = (float)(S.s[threadIdx.x] * q[threadIdx.x]);
+    if (threadIdx.x < m) {
+        const double p = S.s[threadIdx.x] * q[threadIdx.x];
+        const float h = (float)p;
+        S.pd[threadIdx.x] = df{h, (float)(p - (double)h)};
+    }
     __syncthreads();
 }
+
+// r_k = 1 - g_k / t_k in float-float
+__device__ __forceinline__ df resid_df(df g, float2 t) { return df_sub(df{1.0f, 0.0f}, df_div(g, df{t.x, t.y})); }
 
 // Assemble over all rows of the job: A = J^T J (upper, if want_A), b = J^T r,
 // ssr = r^T r, with J_ki = -(dg_k/dp_i) s_i / t_k (scaled coordinates q).
@@ -170,24 +236,26 @@ template <int T>
 __device__ void assemble(Smem<T> &S, const FitJob &jb, int n, unsigned mask, bool want_A) {
     const int m = jb.m, tid = threadIdx.x;
     const int nA = m * (m + 1) / 2, nE = nA + m + 1;
-    CSum acc[3];
+    CAcc acc[3];
     for (int u = 0; u < 3; u++) acc[u].init();
-    float v[kMaxIns], adj[kMaxIns], g[MP];
+    df v[kMaxIns];
+    float adj[kMaxIns], g[MP];
     for (int base = 0; base < jb.l; base += T) {
         const int row = base + tid;
-        float rr = 0.0f;
+        df rr = df{0.0f, 0.0f};
         if (row < jb.l) {
-            const float *frow = jb.X + (size_t)row * jb.nf;
-            const float tk = jb.t[row];
-            const float gk = forward<float, float>(S.code, n, frow, S.pf, v);
-            rr = 1.0f - gk / tk;
-            reverse(S.code, n, v, adj, g, m);
+            const float2 *frow = jb.X + (size_t)row * jb.nf;
+            const float2 tk = jb.t[row];
+            const df gk = forward_df(S.code, n, frow, S.pd, v);
+            rr = resid_df(gk, tk);
+            reverse_df(S.code, n, v, adj, g, m);
             for (int i = 0; i < m; i++)
-                S.J[tid * (MP + 1) + i] = ((mask >> i) & 1u) ? -g[i] * (float)S.s[i] / tk : 0.0f;
+                S.J[tid * (MP + 1) + i] = ((mask >> i) & 1u) ? -g[i] * (float)S.s[i] / tk.x : 0.0f;
         } else {
             for (int i = 0; i < m; i++) S.J[tid * (MP + 1) + i] = 0.0f;
         }
-        S.r[tid] = rr;
+        S.r[tid] = rr.hi;
+        S.rl[tid] = rr.lo;
         __syncthreads();
         const int rows = min(T, jb.l - base);
         for (int u = 0; u < 3; u++) {
@@ -199,12 +267,21 @@ __device__ void assemble(Smem<T> &S, const FitJob &jb, int n, unsigned mask, boo
                 int i = 0, rem = e;
                 while (rem >= m - i) { rem -= m - i; i++; }
                 const int j = i + rem;
-                for (int k = 0; k < rows; k++) acc[u].add(S.J[k * (MP + 1) + i] * S.J[k * (MP + 1) + j]);
+                for (int k = 0; k < rows; k++) acc[u].add_prod(S.J[k * (MP + 1) + i], S.J[k * (MP + 1) + j]);
             } else if (e < nA + m) {
                 const int i = e - nA;
-                for (int k = 0; k < rows; k++) acc[u].add(S.J[k * (MP + 1) + i] * S.r[k]);
+                for (int k = 0; k < rows; k++) {
+                    const float ji = S.J[k * (MP + 1) + i];
+                    float p, er;
+                    two_prod(ji, S.r[k], p, er);
+                    acc[u].add(p, __fmaf_rn(ji, S.rl[k], er));
+                }
             } else {
-                for (int k = 0; k < rows; k++) acc[u].add(S.r[k] * S.r[k]);
+                for (int k = 0; k < rows; k++) {
+                    float p, er;
+                    two_prod(S.r[k], S.r[k], p, er);
+                    acc[u].add(p, __fmaf_rn(2.0f * S.r[k], S.rl[k], er));
+                }
             }
         }
         __syncthreads();
@@ -218,16 +295,18 @@ __device__ void assemble(Smem<T> &S, const FitJob &jb, int n, unsigned mask, boo
     __syncthreads();
 }
 
-// SSR only, at parameters S.pf.
+// SSR only, at parameters S.pd (float-float residuals, exact squares).
 template <int T>
 __device__ double ssr_pass(Smem<T> &S, const FitJob &jb, int n) {
-    CSum a;
+    CAcc a;
     a.init();
-    float v[kMaxIns];
+    df v[kMaxIns];
     for (int row = threadIdx.x; row < jb.l; row += T) {
-        const float gk = forward<float, float>(S.code, n, jb.X + (size_t)row * jb.nf, S.pf, v);
-        const float rr = 1.0f - gk / jb.t[row];
-        a.add(rr * rr);
+        const df gk = forward_df(S.code, n, jb.X + (size_t)row * jb.nf, S.pd, v);
+        const df rr = resid_df(gk, jb.t[row]);
+        float p, er;
+        two_prod(rr.hi, rr.hi, p, er);
+        a.add(p, __fmaf_rn(2.0f * rr.hi, rr.lo, er));
     }
     double x = a.value();
     for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
@@ -490,10 +569,10 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
         // median of t (rank selection; ties handled by rank ranges)
         const int k1 = (jb.l - 1) / 2, k2 = jb.l / 2;
         for (int i = tid; i < jb.l; i += T) {
-            const float x = jb.t[i];
+            const float x = jb.t[i].x;
             int lt = 0, eq = 0;
             for (int j = 0; j < jb.l; j++) {
-                const float y = jb.t[j];
+                const float y = jb.t[j].x;
                 lt += y < x;
                 eq += y == x;
             }
@@ -534,8 +613,8 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
     for (int it = 0; it < cfg.max_iter; it++) {
         bool accepted = false;
         double ssr_old = S.ssr;
-        // noise floor of an SSR built from FP32 residuals
-        const double noise = 4.0 * EPS32 * sqrt((double)jb.l * ssr_old) + (double)jb.l * EPS32 * EPS32;
+        // noise floor of an SSR built from float-float residuals
+        const double noise = 4.0 * EPS_DF * sqrt((double)jb.l * ssr_old) + (double)jb.l * EPS_DF * EPS_DF;
         for (int tr = 0; tr < 16; tr++) {
             solve_chol(S, m, S.lambda);
             if (!S.ok) {
@@ -595,9 +674,13 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
     }
 }
 
-__global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, size_t n) {
-    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-        b[i] = (float)a[i];
+// FP64 -> float-float (hi, lo) split of the uploaded features and outputs
+__global__ void k_split(const double *__restrict__ a, float2 *__restrict__ b, size_t n) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double x = a[i];
+        const float h = (float)x;
+        b[i] = make_float2(h, (float)(x - (double)h));
+    }
 }
 
 // ---------------------------------------------------------------- autograd kernels
@@ -700,7 +783,7 @@ struct pm_fit_plan {
     int use_p0 = 0;
     // device
     double *dX64 = nullptr, *dt64 = nullptr, *dp = nullptr, *drep = nullptr;
-    float *dX32 = nullptr, *dt32 = nullptr;
+    float2 *dX32 = nullptr, *dt32 = nullptr;
     Ins *dcode = nullptr;
     FitJob *djobs = nullptr;
     // pinned host staging
@@ -732,9 +815,9 @@ pm_status plan_build(pm_fit_plan *P) {
         code.insert(code.end(), P->models[k]->start_code.begin(), P->models[k]->start_code.end());
     }
     PM_CUDA_TRY(cudaMalloc(&P->dX64, std::max<size_t>(P->nx, 1) * 8));
-    PM_CUDA_TRY(cudaMalloc(&P->dX32, std::max<size_t>(P->nx, 1) * 4));
+    PM_CUDA_TRY(cudaMalloc(&P->dX32, std::max<size_t>(P->nx, 1) * 8));
     PM_CUDA_TRY(cudaMalloc(&P->dt64, P->nt * 8));
-    PM_CUDA_TRY(cudaMalloc(&P->dt32, P->nt * 4));
+    PM_CUDA_TRY(cudaMalloc(&P->dt32, P->nt * 8));
     PM_CUDA_TRY(cudaMalloc(&P->dp, P->np * 8));
     PM_CUDA_TRY(cudaMalloc(&P->drep, K * 8 * 8));
     PM_CUDA_TRY(cudaMalloc(&P->dcode, code.size() * sizeof(Ins)));
@@ -775,11 +858,11 @@ pm_status plan_build(pm_fit_plan *P) {
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->dt64, P->ht, P->nt * 8, cudaMemcpyHostToDevice, P->cap);
     if (e == cudaSuccess) e = cudaMemcpyAsync(P->dp, P->hp, P->np * 8, cudaMemcpyHostToDevice, P->cap);
     if (e == cudaSuccess && P->nx) {
-        k_to_f32<<<152, 256, 0, P->cap>>>(P->dX64, P->dX32, P->nx);
+        k_split<<<152, 256, 0, P->cap>>>(P->dX64, P->dX32, P->nx);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) {
-        k_to_f32<<<152, 256, 0, P->cap>>>(P->dt64, P->dt32, P->nt);
+        k_split<<<152, 256, 0, P->cap>>>(P->dt64, P->dt32, P->nt);
         e = cudaGetLastError();
     }
     if (e == cudaSuccess) s = launch_fit(P->threads, P->djobs, (int)K, P->cfg, P->cap);
