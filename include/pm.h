@@ -238,6 +238,35 @@ pm_status pm_fit_batched(const pm_model *const *models, size_t nmodels, const do
                          const double *t_concat, const size_t *rows, const pm_fit_opts *opts,
                          double *p_inout_concat, pm_fit_report *reports, void *stream);
 
+/* Allocation-free batched calibration.  The paper has no counterpart; this
+ * entry point exists for callers that must not allocate GPU memory -- for
+ * example code that runs while a stream is being captured into a CUDA graph
+ * (where cudaMalloc is not allowed), real-time loops that cannot afford the
+ * device-wide synchronisation an allocation may cause, or processes whose
+ * device memory is entirely reserved by another framework's allocator.
+ *
+ * Same arguments, layout and results as pm_fit_batched (host arrays; CTA
+ * size 128).  Instead of allocating, it stages the models' programs, the
+ * data (FP64 and float-float copies), the parameters and the reports in one
+ * static device array of PM_NOALLOC_SCRATCH_BYTES bytes that every GPU which
+ * loads the library keeps until the process exits.  It calls no cudaMalloc,
+ * cudaFree or other allocating routine.
+ *   - Requests whose staged size exceeds PM_NOALLOC_SCRATCH_BYTES, or with
+ *     more than 256 models, fail with PM_EINVAL and a message giving the
+ *     size needed; nothing is launched then.
+ *   - The first call on a device looks up the array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call
+ *     before any stream capture begins.
+ *   - Every call on a device shares the one array and leaves its contents
+ *     behind; each call rewrites everything it reads.  Calls whose work
+ *     overlaps on the GPU (other host threads, other streams) race on the
+ *     array: serialise them.
+ *   - Blocks until the results are on the host. */
+#define PM_NOALLOC_SCRATCH_BYTES (8u << 20)
+pm_status pm_fit_batched_noalloc(const pm_model *const *models, size_t nmodels, const double *X_concat,
+                                 const double *t_concat, const size_t *rows, const pm_fit_opts *opts,
+                                 double *p_inout_concat, pm_fit_report *reports, void *stream);
+
 /* Differentiation entry points (device pointers; used by the PyTorch
  * autograd.Function).  X: l x n_features FP32, t: l FP32, p: n_params FP64.
  *   pm_residual:  r_k = 1 - g(p; X_k) / t_k                       (FP32)

@@ -10,7 +10,9 @@ from ._lib import (lib, check, PMError, pm_param, pm_buffer, pm_feature, pm_run_
                    pm_fit_report)
 
 __all__ = ["kernel_lookup", "kernel_names", "counts", "kernel_buffers", "launch", "run", "run_host", "Model",
-           "FitPlan", "fit_batched", "PMError", "DTYPES"]
+           "FitPlan", "fit_batched", "fit_batched_noalloc", "NOALLOC_SCRATCH_BYTES", "PMError", "DTYPES"]
+
+NOALLOC_SCRATCH_BYTES = 8 << 20
 
 DTYPES = {0: np.float32, 1: np.float64, 2: np.uint16}
 _KIND = {0: "op", 1: "mem", 2: "sync", 3: "groups", 4: "launch"}
@@ -265,3 +267,30 @@ def fit_batched(models, Xs, ts, p0s=None, threads=0, **kw):
         out.append(p[o:o + n])
         o += n
     return out, reps
+
+
+def fit_batched_noalloc(models, Xs, ts, p0s=None, max_iter=200, ftol=1e-15, xtol=1e-12, stream=None):
+    """pm_fit_batched_noalloc: the batched fit staged in the library's static
+    device scratch (no GPU memory allocation; see include/pm.h for who needs
+    it and its limits).  Same arguments and results as fit_batched."""
+    models = list(models)
+    rows = [len(t) for t in ts]
+    X = np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in Xs]) if Xs else np.zeros(0)
+    t = np.ascontiguousarray(np.concatenate([np.asarray(x, dtype=np.float64) for x in ts]))
+    nps = [len(m.params) for m in models]
+    p = np.zeros(sum(nps)) if p0s is None else np.ascontiguousarray(
+        np.concatenate([np.asarray(q, dtype=np.float64) for q in p0s]))
+    X = np.ascontiguousarray(X)
+    hs = (ctypes.c_void_p * len(models))(*[m.handle.value for m in models])
+    rw = (ctypes.c_size_t * len(rows))(*rows)
+    opts = pm_fit_opts(max_iter, ftol, xtol, 0 if p0s is None else 1)
+    reps = (pm_fit_report * len(models))()
+    D = ctypes.POINTER(ctypes.c_double)
+    check(lib().pm_fit_batched_noalloc(hs, len(models), X.ctypes.data_as(D), t.ctypes.data_as(D), rw,
+                                       ctypes.byref(opts), p.ctypes.data_as(D), reps,
+                                       _stream(stream) if stream is not None else ctypes.c_void_p(0)))
+    out, o = [], 0
+    for n in nps:
+        out.append(p[o:o + n])
+        o += n
+    return out, [_report(r) for r in reps]

@@ -76,6 +76,7 @@ SIGNATURES = {
     "pm_fit_plan_run": (i32, [vp, dp, dp, dp, P(pm_fit_report), vp]),
     "pm_fit_plan_destroy": (None, [vp]),
     "pm_fit_batched": (i32, [P(vp), c_size_t, dp, dp, P(c_size_t), P(pm_fit_opts), dp, P(pm_fit_report), vp]),
+    "pm_fit_batched_noalloc": (i32, [P(vp), c_size_t, dp, dp, P(c_size_t), P(pm_fit_opts), dp, P(pm_fit_report), vp]),
     "pm_residual": (i32, [vp, vp, vp, c_size_t, vp, vp, vp]),
     "pm_residual_vjp": (i32, [vp, vp, vp, c_size_t, vp, vp, vp, vp]),
     "pm_jacobian": (i32, [vp, vp, vp, c_size_t, vp, vp, vp]),

@@ -23,6 +23,7 @@
 #include <cmath>
 #include <cstring>
 #include <cuda_runtime.h>
+#include <mutex>
 #include <new>
 #include <vector>
 
@@ -1074,3 +1075,134 @@ pm_status pm_jacobian(const pm_model *m, const float *X, const float *t, size_t 
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- allocation-free batched fit
+// Scratch for pm_fit_batched_noalloc: one file-scope device array, present on
+// every GPU that loads this library until the process exits.  Host code must
+// not hand the symbol itself to a kernel (on the host it names a host-side
+// shadow); it looks up the device address once per device with
+// cudaGetSymbolAddress and passes that.
+namespace pm {
+namespace {
+
+static __device__ __align__(256) unsigned char g_fit_scratch[PM_NOALLOC_SCRATCH_BYTES];
+
+constexpr int kMaxDevices = 64;
+constexpr size_t kNoallocMaxModels = 256;
+static void *g_scratch_addr[kMaxDevices];
+static std::mutex g_scratch_mu;
+
+pm_status scratch_address(void **out) {
+    int dev = 0;
+    PM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= kMaxDevices) return fail(PM_EINVAL, "noalloc fit: device ordinal %d unsupported", dev);
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
+    if (!g_scratch_addr[dev]) {
+        void *p = nullptr;
+        cudaError_t e = cudaGetSymbolAddress(&p, g_fit_scratch);
+        if (e != cudaSuccess || !p)
+            return fail(PM_ECUDA, "noalloc fit: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        g_scratch_addr[dev] = p;
+    }
+    *out = g_scratch_addr[dev];
+    return PM_OK;
+}
+
+size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+}  // namespace
+}  // namespace pm
+
+extern "C" pm_status pm_fit_batched_noalloc(const pm_model *const *models, size_t nmodels, const double *X,
+                                            const double *t, const size_t *rows, const pm_fit_opts *opts,
+                                            double *p_inout, pm_fit_report *reports, void *stream) {
+    using namespace pm;
+    if (!models || !rows || !t || !p_inout || nmodels == 0) return fail(PM_EINVAL, "pm_fit_batched_noalloc: bad argument");
+    if (nmodels > kNoallocMaxModels)
+        return fail(PM_EINVAL, "pm_fit_batched_noalloc: at most %zu models per call", kNoallocMaxModels);
+    FitCfg cfg;
+    int use_p0 = 0;
+    pm_status s = check_opts(opts, cfg, use_p0);
+    if (s) return s;
+    // layout of the scratch: jobs | code | X (FP64) | X (hi, lo) | t (FP64) | t (hi, lo) | p | reports
+    size_t nx = 0, nt = 0, np = 0, ncode = 0;
+    for (size_t k = 0; k < nmodels; k++) {
+        const pm_model *m = models[k];
+        if (!m) return fail(PM_EINVAL, "pm_fit_batched_noalloc: model %zu is NULL", k);
+        if (rows[k] < 1 || rows[k] > (1u << 24)) return fail(PM_EINVAL, "pm_fit_batched_noalloc: model %zu needs 1..2^24 rows", k);
+        nx += rows[k] * m->features.size();
+        nt += rows[k];
+        np += m->params.size();
+        ncode += m->code.size() + m->start_code.size();
+    }
+    if (nx && !X) return fail(PM_EINVAL, "pm_fit_batched_noalloc: X is NULL");
+    const size_t o_jobs = 0, o_code = align256(o_jobs + nmodels * sizeof(FitJob));
+    const size_t o_x64 = align256(o_code + ncode * sizeof(Ins)), o_x2 = align256(o_x64 + nx * 8);
+    const size_t o_t64 = align256(o_x2 + nx * 8), o_t2 = align256(o_t64 + nt * 8);
+    const size_t o_p = align256(o_t2 + nt * 8), o_rep = align256(o_p + np * 8);
+    const size_t need = align256(o_rep + nmodels * 64);
+    if (need > (size_t)PM_NOALLOC_SCRATCH_BYTES)
+        return fail(PM_EINVAL, "pm_fit_batched_noalloc: request needs %zu bytes of scratch, the limit is %zu",
+                    need, (size_t)PM_NOALLOC_SCRATCH_BYTES);
+    for (size_t k = 0, o = 0; k < nmodels; k++)
+        for (size_t r = 0; r < rows[k]; r++, o++)
+            if (!finite_pos(t[o])) return fail(PM_EINVAL, "fit: model %zu row %zu: output must be finite and > 0", k, r);
+    for (size_t i = 0; i < nx; i++)
+        if (!std::isfinite(X[i])) return fail(PM_EINVAL, "fit: feature value %zu is not finite", i);
+    void *base = nullptr;
+    if ((s = scratch_address(&base))) return s;
+    unsigned char *B = (unsigned char *)base;
+    cudaStream_t st = (cudaStream_t)stream;
+    FitJob jobs[kNoallocMaxModels];
+    size_t co = 0, xo = 0, to = 0, po = 0;
+    for (size_t k = 0; k < nmodels; k++) {
+        const pm_model *md = models[k];
+        FitJob &j = jobs[k];
+        Ins *code = (Ins *)(B + o_code) + co;
+        PM_CUDA_TRY(cudaMemcpyAsync(code, md->code.data(), md->code.size() * sizeof(Ins), cudaMemcpyHostToDevice, st));
+        PM_CUDA_TRY(cudaMemcpyAsync(code + md->code.size(), md->start_code.data(), md->start_code.size() * sizeof(Ins),
+                                    cudaMemcpyHostToDevice, st));
+        j.code = code;
+        j.start_code = code + md->code.size();
+        j.n_code = (int)md->code.size();
+        j.n_start = (int)md->start_code.size();
+        j.m = (int)md->params.size();
+        j.nf = (int)md->features.size();
+        j.l = (int)rows[k];
+        j.linear = md->linear;
+        j.use_p0 = use_p0;
+        j.start_mask = md->start_mask;
+        j.X = (const float2 *)(B + o_x2) + xo;
+        j.t = (const float2 *)(B + o_t2) + to;
+        j.p = (double *)(B + o_p) + po;
+        j.rep = (double *)(B + o_rep) + 8 * k;
+        co += md->code.size() + md->start_code.size();
+        xo += rows[k] * md->features.size();
+        to += rows[k];
+        po += md->params.size();
+    }
+    PM_CUDA_TRY(cudaMemcpyAsync(B + o_jobs, jobs, nmodels * sizeof(FitJob), cudaMemcpyHostToDevice, st));
+    if (nx) PM_CUDA_TRY(cudaMemcpyAsync(B + o_x64, X, nx * 8, cudaMemcpyHostToDevice, st));
+    PM_CUDA_TRY(cudaMemcpyAsync(B + o_t64, t, nt * 8, cudaMemcpyHostToDevice, st));
+    PM_CUDA_TRY(cudaMemcpyAsync(B + o_p, p_inout, np * 8, cudaMemcpyHostToDevice, st));
+    if (nx) k_split<<<152, 256, 0, st>>>((const double *)(B + o_x64), (float2 *)(B + o_x2), nx);
+    k_split<<<152, 256, 0, st>>>((const double *)(B + o_t64), (float2 *)(B + o_t2), nt);
+    PM_CUDA_TRY(cudaGetLastError());
+    if ((s = launch_fit(128, (const FitJob *)(B + o_jobs), (int)nmodels, cfg, st))) return s;
+    PM_CUDA_TRY(cudaMemcpyAsync(p_inout, B + o_p, np * 8, cudaMemcpyDeviceToHost, st));
+    double rep_host[kNoallocMaxModels * 8];
+    PM_CUDA_TRY(cudaMemcpyAsync(rep_host, B + o_rep, nmodels * 64, cudaMemcpyDeviceToHost, st));
+    PM_CUDA_TRY(cudaStreamSynchronize(st));
+    if (reports)
+        for (size_t k = 0; k < nmodels; k++) {
+            const double *r = rep_host + 8 * k;
+            reports[k].status = (int32_t)r[0];
+            reports[k].iterations = (int32_t)r[1];
+            reports[k].rank = (int32_t)r[2];
+            reports[k].linear = (int32_t)r[3];
+            reports[k].residual = r[4];
+            reports[k].lambda = r[5];
+        }
+    PM_CUDA_TRY(cudaStreamSynchronize(st));
+    return PM_OK;
+}
