@@ -43,6 +43,7 @@ def parse():
     ap.add_argument("--no-fit-bench", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--filter", default="suite", help="comma-separated suite filter tags")
+    ap.add_argument("--dump", default=None, help="write per-variant timings of the last step (JSON)")
     return ap.parse_args()
 
 
@@ -181,8 +182,10 @@ def run_ours(args):
     stream = torch.cuda.current_stream()
     launches_per_step = len(prepared) * args.trials + 3 + len(fam_names)
 
+    last_times = {}
+
     def one_step(record):
-        times = {}
+        times = last_times
         for idx, (k, p, bufs, nbytes, inst) in enumerate(prepared):
             tm = pm.run(k, bufs, warmup=0, trials=args.trials, outlier_factor=0.0, **p)
             times[idx] = tm["mean_ms"] * 1e-3
@@ -276,6 +279,10 @@ def run_ours(args):
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,
     }
+    if args.dump and rank == 0:
+        json.dump([{"kernel": k, "params": p, "instance": inst, "mean_s": last_times[i], "bytes": nb,
+                    "GB/s": nb / last_times[i] / 1e9 if last_times[i] > 0 else None}
+                   for i, (k, p, _b, nb, inst) in enumerate(prepared)], open(args.dump, "w"), indent=0)
     if not args.no_e2e:
         line["e2e"] = e2e_measure(pm, S, variants, torch)
     if not args.no_fit_bench:

@@ -140,6 +140,9 @@ typedef struct {
     int32_t warmup;          /* untimed launches first (default 2) */
     int32_t trials;          /* timed launches (default 60, Section "Other Features") */
     double outlier_factor;   /* drop trials > factor * median (default 5; <= 0 keeps all) */
+    int32_t flush_l2;        /* 1: before every trial, overwrite a 256 MiB library-owned buffer (larger
+                                than L2) outside the timed interval, so each trial starts cache-cold.
+                                The buffer is allocated once per device on first use. (default 0) */
 } pm_run_opts;
 
 typedef struct {

@@ -117,10 +117,11 @@ def launch(kernel, bufs, stream=None, **params):
     check(lib().pm_launch(_kid(kernel), arr, n, _ptrs(bufs), len(bufs), _stream(stream)))
 
 
-def run(kernel, bufs, warmup=2, trials=60, outlier_factor=5.0, stream=None, want_trials=False, **params):
+def run(kernel, bufs, warmup=2, trials=60, outlier_factor=5.0, stream=None, want_trials=False, flush_l2=False,
+        **params):
     """Device-timed trials (pm_run).  Returns a timing dict (ms)."""
     arr, n, _keep = _params(params)
-    opts = pm_run_opts(warmup, trials, outlier_factor)
+    opts = pm_run_opts(warmup, trials, outlier_factor, 1 if flush_l2 else 0)
     tm = pm_timing()
     tr = (ctypes.c_float * trials)()
     check(lib().pm_run(_kid(kernel), arr, n, _ptrs(bufs), len(bufs), ctypes.byref(opts), _stream(stream), tr,
@@ -132,7 +133,7 @@ def run(kernel, bufs, warmup=2, trials=60, outlier_factor=5.0, stream=None, want
     return out
 
 
-def run_host(kernel, host_arrays, warmup=2, trials=60, outlier_factor=5.0, stream=None, **params):
+def run_host(kernel, host_arrays, warmup=2, trials=60, outlier_factor=5.0, stream=None, flush_l2=False, **params):
     """pm_run with host (NumPy) buffers: copies in, runs, copies out."""
     arr, n, _keep = _params(params)
     ptrs = (ctypes.c_void_p * max(1, len(host_arrays)))()
@@ -143,7 +144,7 @@ def run_host(kernel, host_arrays, warmup=2, trials=60, outlier_factor=5.0, strea
             if not a.flags["C_CONTIGUOUS"]:
                 raise ValueError("host array %d must be C-contiguous" % i)
             ptrs[i] = a.ctypes.data
-    opts = pm_run_opts(warmup, trials, outlier_factor)
+    opts = pm_run_opts(warmup, trials, outlier_factor, 1 if flush_l2 else 0)
     tm = pm_timing()
     cms = ctypes.c_double()
     check(lib().pm_run_host(_kid(kernel), arr, n, ptrs, len(host_arrays), ctypes.byref(opts), _stream(stream),

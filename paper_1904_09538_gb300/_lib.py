@@ -29,7 +29,8 @@ class pm_feature(ctypes.Structure):
 
 
 class pm_run_opts(ctypes.Structure):
-    _fields_ = [("warmup", ctypes.c_int32), ("trials", ctypes.c_int32), ("outlier_factor", ctypes.c_double)]
+    _fields_ = [("warmup", ctypes.c_int32), ("trials", ctypes.c_int32), ("outlier_factor", ctypes.c_double),
+                ("flush_l2", ctypes.c_int32)]
 
 
 class pm_timing(ctypes.Structure):

@@ -4,6 +4,7 @@
 #include <algorithm>
 #include <cmath>
 #include <cuda_runtime.h>
+#include <mutex>
 #include <vector>
 
 #include "pm_internal.h"
@@ -27,6 +28,37 @@ static pm_status launch_any(const KP &kp, void *const *bufs, size_t nbufs, void 
 
 static size_t dtype_size(int dt) { return dt == PM_F32 ? 4 : dt == PM_F64 ? 8 : 2; }
 
+// L2 flush: overwrite a buffer larger than the 129 MB L2 (one per device).
+constexpr size_t kFlushBytes = 256u << 20;
+static void *g_flush[64];
+static std::mutex g_flush_mu;
+
+__global__ void k_l2_flush(int4 *__restrict__ p, size_t n, int v) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
+        p[i] = make_int4(v, v, v, v);
+}
+
+static pm_status flush_l2(cudaStream_t st) {
+    int dev = 0;
+    PM_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev < 0 || dev >= 64) return fail(PM_EINVAL, "flush_l2: device ordinal %d unsupported", dev);
+    void *buf = nullptr;
+    {
+        std::lock_guard<std::mutex> lock(g_flush_mu);
+        if (!g_flush[dev]) {
+            if (cudaMalloc(&g_flush[dev], kFlushBytes) != cudaSuccess) {
+                g_flush[dev] = nullptr;
+                return fail(PM_ENOMEM, "flush_l2: cannot allocate the %zu-byte flush buffer", kFlushBytes);
+            }
+        }
+        buf = g_flush[dev];
+    }
+    static int counter = 0;
+    k_l2_flush<<<4 * 152, 512, 0, st>>>((int4 *)buf, kFlushBytes / sizeof(int4), ++counter);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
 struct EventPool {
     std::vector<cudaEvent_t> ev;
     ~EventPool() {
@@ -41,7 +73,7 @@ struct EventPool {
 
 static pm_status timed(const KP &kp, void *const *bufs, size_t nbufs, const pm_run_opts *opts, void *stream,
                        float *trial_ms, pm_timing *out) {
-    pm_run_opts o{2, 60, 5.0};
+    pm_run_opts o{2, 60, 5.0, 0};
     if (opts) o = *opts;
     if (o.warmup < 0 || o.trials < 1 || o.trials > 100000)
         return fail(PM_EINVAL, "pm_run: need warmup >= 0 and 1 <= trials <= 100000");
@@ -52,6 +84,7 @@ static pm_status timed(const KP &kp, void *const *bufs, size_t nbufs, const pm_r
     EventPool pool;
     if ((s = pool.make(2 * (size_t)o.trials))) return s;
     for (int t = 0; t < o.trials; t++) {
+        if (o.flush_l2 && (s = flush_l2(st))) return s;
         PM_CUDA_TRY(cudaEventRecord(pool.ev[2 * t], st));
         if ((s = launch_any(kp, bufs, nbufs, stream))) return s;
         PM_CUDA_TRY(cudaEventRecord(pool.ev[2 * t + 1], st));

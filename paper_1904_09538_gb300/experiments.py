@@ -1,0 +1,231 @@
+"""The paper's evaluation on this GPU (Section "Results").
+
+For each computation -- matmul (2 variants), DG differentiation (2 variants x
+2 work-group shapes), five-point stencil (2 variants) -- a model of the form
+of Eq. linear_model or Eq. nonlinear_model is calibrated on a measurement
+kernel set that does NOT contain the modeled kernels (microbenchmarks: the
+arithmetic, local-memory, barrier, overlap, empty and global-memory pattern
+kernels, plus the work-removed twins of the modeled kernels, Algorithm 3),
+then predicts the modeled kernels' times at every size.  Reported: the
+geometric mean and maximum relative error per variant, and how well the
+predictions rank the variants (Spearman and Kendall over all sizes).
+
+Also the illustrative case of Section "Illustrative Example" (configuration
+1): a 4-parameter linear model of the prefetching matmul on n = 256..768,
+predicting n = 896.
+
+Timing: pm_run, `trials` device-timed launches after 2 warm-ups (mean, trials
+above 5x the median dropped).  Inputs are seeded uniform / normal values.
+"""
+import math
+
+import numpy as np
+
+from . import Model, FitPlan, kernel_buffers, run
+from .suite import generate
+
+GENERIC = "p_gen * f_mem_access_global_float32_lstrides:{0:1}_afr:1"
+OVERHEAD = ("p_launch * f_sync_kernel_launch + p_group * f_thread_groups + "
+            "p_bar * f_sync_barrier_local * f_thread_groups")
+ONCHIP = ("p_madd * f_op_float32_madd + p_add * f_op_float32_add + p_mul * f_op_float32_mul + "
+          "p_lmem * f_mem_access_local_float32")
+
+
+def nonlinear(gmem_terms, overhead=OVERHEAD, onchip=ONCHIP):
+    cg = "(%s)" % " + ".join(gmem_terms)
+    co = "(%s)" % onchip
+    return ("%s + %s * (tanh(p_edge * (%s - %s)) + 1) / 2 + %s * (tanh(p_edge * (%s - %s)) + 1) / 2"
+            % (overhead, cg, cg, co, co, co, cg))
+
+
+def linear(gmem_terms, overhead=OVERHEAD, onchip=ONCHIP):
+    return "%s + %s + %s" % (overhead, " + ".join(gmem_terms), onchip)
+
+
+def tagged(tag, name):
+    return "p_%s * f_mem_access_tag:%s" % (name, tag)
+
+
+# microbenchmarks shared by every computation's measurement set (paper Fig. mkernels_common)
+def common_measurements():
+    out = []
+    out += generate(["ops", "dtype:0"])                       # f32 add / mul / madd loops
+    out += generate(["lmem"])                                 # local memory, with and without barriers
+    out += generate(["sync"])                                 # barrier kernel
+    out += generate(["overlap"])                              # local/global overlap
+    out += generate(["launch"])                               # empty kernels
+    out += generate(["stream2d"])                             # unit-stride f32 global pattern (AFR 1)
+    return out
+
+
+def studies():
+    """(name, model expression, measurement kernels, modeled kernels) per computation."""
+    mm_sizes = list(range(512, 4096 + 1, 128))                # 29 sizes
+    mm_twin_sizes = [512, 1024, 1536, 2048, 2560, 3072, 3584, 4096]
+    mm = dict(
+        name="matmul",
+        expr=nonlinear([GENERIC] + [tagged(t, n) for t, n in (("mm-PF-a", "pfa"), ("mm-PF-b", "pfb"),
+                                                              ("mm-noPF-a", "npa"), ("mm-noPF-b", "npb"))]),
+        measure=common_measurements() + [(k, {"n": n}) for k in ("mm_pf_a", "mm_pf_b", "mm_nopf_a", "mm_nopf_b")
+                                         for n in mm_twin_sizes],
+        modeled=[(k, {"n": n}) for k in ("mm_pf", "mm_nopf") for n in mm_sizes],
+    )
+    out = [mm]
+    for L0, L1 in ((16, 16), (32, 8)):
+        sh = "%dx%d" % (L0, L1)
+        tags = [("dg-noPF-u-" + sh, "nu"), ("dg-noPF-dm-" + sh, "ndm"), ("dg-dmPF-u-" + sh, "pu"),
+                ("dg-dmPF-dm-" + sh, "pdm"), ("dg-res-" + sh, "res")]
+        twins = []
+        for k in ("dg_nopf_u", "dg_nopf_dm", "dg_dmpf_u", "dg_dmpf_dm", "dg_res"):
+            for Np in (20, 35, 56, 84):
+                for Nel in (1 << 14, 1 << 16, 1 << 18):
+                    twins.append((k, dict(Np=Np, Nel=Nel, L0=L0, L1=L1)))
+        modeled = [(k, dict(Np=Np, Nel=Nel, L0=L0, L1=L1)) for k in ("dg_nopf", "dg_dmpf")
+                   for Np in (20, 35, 56, 84) for Nel in (1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18)]
+        out.append(dict(name="dg_" + sh, expr=nonlinear([GENERIC] + [tagged(t, n) for t, n in tags]),
+                        measure=common_measurements() + twins, modeled=modeled))
+    fd_sizes = [int(round(1024 * 2 ** (i / 7.0))) for i in range(29)]   # 1024 .. 16384, geometric
+    fd_twins = [(k, {"n": n}) for k in ("fd_tile_u", "fd_tile_res", "fd_direct_u", "fd_direct_res")
+                for n in (1024, 2048, 4096, 8192, 16384)]
+    # the tile variant's result store is a unit-stride AFR-1 pattern, so the
+    # generic feature covers it; only the overlapping tile fetch is tagged
+    out.append(dict(name="fd", expr=linear([GENERIC, tagged("fd-tile-u", "tu")]),
+                    measure=common_measurements() + fd_twins,
+                    modeled=[(k, {"n": n}) for k in ("fd_tile", "fd_direct") for n in fd_sizes]))
+    return out
+
+
+class Buffers:
+    """Device buffers reused across kernels (seeded uniform values in [-1, 1))."""
+
+    def __init__(self, torch, dev, seed=1234):
+        self.torch, self.dev = torch, dev
+        self.gen = torch.Generator(device=dev)
+        self.gen.manual_seed(seed)
+        self.pool = {}
+
+    def get(self, kernel, params):
+        torch = self.torch
+        out = []
+        for i, b in enumerate(kernel_buffers(kernel, **params)):
+            dt = torch.float64 if b["dtype"] == np.float64 else torch.float32
+            key = (i, dt)
+            cur = self.pool.get(key)
+            if cur is None or cur.numel() < b["elems"]:
+                cur = torch.rand(int(b["elems"]), device=self.dev, dtype=dt, generator=self.gen) * 2 - 1
+                self.pool[key] = cur
+            out.append(cur[:b["elems"]])
+        return out
+
+
+def measure(kernels, bufs, trials, flush_l2=True):
+    times = []
+    for k, p in kernels:
+        tm = run(k, bufs.get(k, p), warmup=2, trials=trials, flush_l2=flush_l2, **p)
+        times.append(tm["mean_ms"] * 1e-3)
+    return np.array(times)
+
+
+def spearman(a, b):
+    ra, rb = np.argsort(np.argsort(a)), np.argsort(np.argsort(b))
+    return float(np.corrcoef(ra, rb)[0, 1])
+
+
+def kendall(a, b):
+    n, s = len(a), 0
+    for i in range(n):
+        for j in range(i + 1, n):
+            s += np.sign(a[i] - a[j]) * np.sign(b[i] - b[j])
+    return float(2 * s / (n * (n - 1))) if n > 1 else 1.0
+
+
+def geomean(x):
+    x = np.maximum(np.asarray(x, dtype=np.float64), 1e-300)
+    return float(math.exp(np.mean(np.log(x))))
+
+
+def run_studies(trials=10, names=None, seed=1234, flush_l2=True):
+    """Calibrate each study's model on its measurement set (all studies in one
+    batched fit) and predict its modeled kernels.  Returns a report dict.
+    flush_l2: every timed trial starts with a cold L2 (pm_run flush_l2)."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    bufs = Buffers(torch, dev, seed)
+    sts = [s for s in studies() if names is None or s["name"] in names]
+    models, Xs, ts, info = [], [], [], []
+    for s in sts:
+        m = Model("f_wall_time", s["expr"])
+        Xm = np.stack([m.feature_values(k, **p) for k, p in s["measure"]])
+        tm = measure(s["measure"], bufs, trials, flush_l2)
+        Xp = np.stack([m.feature_values(k, **p) for k, p in s["modeled"]])
+        tp = measure(s["modeled"], bufs, trials, flush_l2)
+        models.append(m)
+        Xs.append(Xm)
+        ts.append(tm)
+        info.append((s, Xp, tp, Xm, tm))
+    plan = FitPlan(models, [len(t) for t in ts])
+    pvec, reps = plan.run(np.concatenate([x.ravel() for x in Xs]), np.concatenate(ts))
+    report, o = {}, 0
+    for m, (s, Xp, tp, Xm, tm), rep in zip(models, info, reps):
+        p = pvec[o:o + len(m.params)]
+        o += len(m.params)
+        pred = m.predict(p, Xp)
+        fitted = m.predict(p, Xm)
+        err = np.abs(pred - tp) / tp
+        per = {}
+        for v in sorted(set(k for k, _ in s["modeled"])):
+            idx = [i for i, (k, _) in enumerate(s["modeled"]) if k == v]
+            per[v] = {"geomean_rel_err": geomean(err[idx]), "max_rel_err": float(err[idx].max()),
+                      "n_sizes": len(idx)}
+        # ranking of variants at equal sizes
+        groups = {}
+        for i, (k, prm) in enumerate(s["modeled"]):
+            key = tuple(sorted((a, b) for a, b in prm.items()))
+            groups.setdefault(key, []).append(i)
+        agree = [int(np.argmin(pred[g]) == np.argmin(tp[g])) for g in groups.values() if len(g) > 1]
+        report[s["name"]] = {
+            "expr": s["expr"], "params": dict(zip(m.params, [float(x) for x in p])), "fit": rep,
+            "n_measure": len(s["measure"]), "n_modeled": len(s["modeled"]),
+            "variants": per, "geomean_rel_err": geomean(err), "max_rel_err": float(err.max()),
+            "spearman": spearman(pred, tp), "kendall": kendall(pred, tp),
+            "fastest_variant_identified": float(np.mean(agree)) if agree else None,
+            "rows": [{"kernel": k, "params": prm, "measured_s": float(a), "predicted_s": float(b)}
+                     for (k, prm), a, b in zip(s["modeled"], tp, pred)],
+            "measure_rows": [{"kernel": k, "params": prm, "measured_s": float(a), "fitted_s": float(b)}
+                             for (k, prm), a, b in zip(s["measure"], tm, fitted)],
+            "flush_l2": flush_l2,
+        }
+    return report
+
+
+def illustrative(trials=20, seed=1234, flush_l2=True):
+    """Configuration 1: t = p_f flops + p_g gmem + p_s smem + p_l work-groups on
+    the prefetching matmul at n = 256..768 (rank-2 design: minimum-norm fit),
+    predict n = 896."""
+    import torch
+    from . import _lib  # noqa: F401
+    dev = torch.device("cuda", torch.cuda.current_device())
+    bufs = Buffers(torch, dev, seed)
+    expr = ("p_f * f_op_float32_madd + p_g * f_mem_access_global_float32 + p_s * f_mem_access_local_float32 + "
+            "p_l * f_thread_groups")
+    m = Model("f_wall_time", expr)
+    fit_n, test_n = [256, 384, 512, 640, 768], [896]
+    X = np.stack([m.feature_values("mm_pf", n=n) for n in fit_n])
+    t = measure([("mm_pf", {"n": n}) for n in fit_n], bufs, trials, flush_l2)
+    p, rep = m.fit(X, t)
+    Xt = np.stack([m.feature_values("mm_pf", n=n) for n in test_n])
+    tt = measure([("mm_pf", {"n": n}) for n in test_n], bufs, trials, flush_l2)
+    pred = m.predict(p, Xt)
+    return {"expr": expr, "fit_sizes": fit_n, "fit_times_s": t.tolist(), "params": p.tolist(), "report": rep,
+            "test_sizes": test_n, "measured_s": tt.tolist(), "predicted_s": pred.tolist(),
+            "rel_err": (np.abs(pred - tt) / tt).tolist()}
+
+
+if __name__ == "__main__":
+    import json
+    import sys
+    flush = "--no-flush" not in sys.argv
+    args = [a for a in sys.argv[1:] if not a.startswith("--")]
+    out = {"illustrative": illustrative(flush_l2=flush), "studies": run_studies(flush_l2=flush)}
+    sys.argv = [sys.argv[0]] + args
+    json.dump(out, open(sys.argv[1], "w") if len(sys.argv) > 1 else sys.stdout, indent=1)
