@@ -57,7 +57,10 @@ typedef struct {
  * DG "dg_nopf", "dg_dmpf" and twins "dg_nopf_u", "dg_nopf_dm", "dg_dmpf_u",
  * "dg_dmpf_dm", "dg_res" (Section "DG"); stencil "fd_tile", "fd_direct" and
  * twins "fd_tile_u", "fd_tile_res", "fd_direct_u", "fd_direct_res"
- * (Section "Finite Differences").  Returns PM_EUNKNOWN_KERNEL for other names. */
+ * (Section "Finite Differences"); autotuning spaces (the paper's use case
+ * of ranking equivalent variants, Section "Assumptions and Limitations"):
+ * "mm_simt" (register-tiled fp32 matmul, parameters n, BM, BN, BK).
+ * Returns PM_EUNKNOWN_KERNEL for other names. */
 pm_status pm_kernel_lookup(const char *name, int32_t *kernel);
 pm_status pm_kernel_count(int32_t *n);
 /* Library-owned, static string. */

@@ -759,6 +759,112 @@ static int setup_fd(ctx *c, int v) {
 }
 
 /* ======================================================================
+ * Register-tiled SIMT matmul family (autotuning space): C = A B, n x n fp32,
+ * 16-byte vector (float32x4) global accesses.  P = {n, BM, BN, BK}.
+ * Work-group L0 x L1 = (BN/8) x (BM/8); each work-item owns an 8 x 8 block
+ * of C (rows 8 lid1 .., columns 8 lid0 ..).  Per k tile (BK wide):
+ *   barrier;
+ *   A tile: rows lid1 + L1 r (r < 8), vector columns c = lid0 + L0 q
+ *           (q < ceil(KC/L0), guard c < KC, KC = BK/4); stored transposed as
+ *           four scalars As[(4c + j) BM + row] (j < 4);
+ *   B tile: rows lid1 + L1 r (r < ceil(BK/L1), guard row < BK), vector
+ *           columns c = lid0 + L0 q (q < 2); stored as one vector Bs[row NC + c];
+ *   barrier;
+ *   kk < BK: two vector loads of As (8 values at kk BM + 8 lid1), two of Bs
+ *           (8 values at kk BN + 8 lid0), 64 multiply-adds.
+ * Finally 8 x 2 vector stores of C.  Requires n divisible by BM, BN, BK.
+ * Index units: float32x4 (vectors) for global and Bs / As vector loads,
+ * float32 for the scalar As stores.
+ * ====================================================================== */
+#define SM_N(c) ((c)->P[0])
+#define SM_BM(c) ((c)->P[1])
+#define SM_BN(c) ((c)->P[2])
+#define SM_BK(c) ((c)->P[3])
+static long long ix_sm_a(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    /* lv = {kt, r, q} */
+    long long n4 = SM_N(c) / 4, KC = SM_BK(c) / 4, L0 = SM_BN(c) / 8, L1 = SM_BM(c) / 8;
+    return n4 * (SM_BM(c) * G1 + L1_ + L1 * lv[1]) + KC * lv[0] + L0_ + L0 * lv[2];
+}
+static long long ix_sm_ast(const ctx *c, const long long *g, const long long *l, const long long *lv, int j) {
+    (void)g;
+    long long L0 = SM_BN(c) / 8, L1 = SM_BM(c) / 8, BM = SM_BM(c);
+    return (4 * (L0_ + L0 * lv[2]) + j) * BM + L1_ + L1 * lv[1];
+}
+static long long ix_sm_ast0(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_ast(c, g, l, lv, 0); }
+static long long ix_sm_ast1(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_ast(c, g, l, lv, 1); }
+static long long ix_sm_ast2(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_ast(c, g, l, lv, 2); }
+static long long ix_sm_ast3(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_ast(c, g, l, lv, 3); }
+static long long ix_sm_b(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long n4 = SM_N(c) / 4, L0 = SM_BN(c) / 8, L1 = SM_BM(c) / 8, NC = SM_BN(c) / 4;
+    return n4 * (SM_BK(c) * lv[0] + L1_ + L1 * lv[1]) + NC * G0 + L0_ + L0 * lv[2];
+}
+static long long ix_sm_bst(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g;
+    long long L0 = SM_BN(c) / 8, L1 = SM_BM(c) / 8, NC = SM_BN(c) / 4;
+    return (L1_ + L1 * lv[1]) * NC + L0_ + L0 * lv[2];
+}
+static long long ix_sm_ald(const ctx *c, const long long *g, const long long *l, const long long *lv, int h) {
+    (void)g; return lv[1] * (SM_BM(c) / 4) + 2 * L1_ + h;
+}
+static long long ix_sm_ald0(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_ald(c, g, l, lv, 0); }
+static long long ix_sm_ald1(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_ald(c, g, l, lv, 1); }
+static long long ix_sm_bld(const ctx *c, const long long *g, const long long *l, const long long *lv, int h) {
+    (void)g; return lv[1] * (SM_BN(c) / 4) + 2 * L0_ + h;
+}
+static long long ix_sm_bld0(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_bld(c, g, l, lv, 0); }
+static long long ix_sm_bld1(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_bld(c, g, l, lv, 1); }
+static long long ix_sm_c(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    /* lv = {i, j} */
+    long long n4 = SM_N(c) / 4, NC = SM_BN(c) / 4;
+    return n4 * (SM_BM(c) * G1 + 8 * L1_ + lv[0]) + NC * G0 + 2 * L0_ + lv[1];
+}
+static void walk_simt(ctx *c) {
+    long long n = SM_N(c), BK = SM_BK(c), KC = BK / 4, L0 = SM_BN(c) / 8, L1 = SM_BM(c) / 8;
+    long long lv[3];
+    long long qa = cdiv(KC, L0), rb = cdiv(BK, L1);
+    for (lv[0] = 0; lv[0] < n / BK; lv[0]++) {
+        BAR(c);
+        for (lv[1] = 0; lv[1] < 8; lv[1]++)
+            for (lv[2] = 0; lv[2] < qa; lv[2]++)
+                if (c->l[0] + L0 * lv[2] < KC) X(c, 0, lv);
+        for (lv[1] = 0; lv[1] < rb; lv[1]++)
+            for (lv[2] = 0; lv[2] < 2; lv[2]++)
+                if (c->l[1] + L1 * lv[1] < BK) X(c, 1, lv);
+        BAR(c);
+        long long kk[2];
+        kk[0] = lv[0];
+        for (kk[1] = 0; kk[1] < BK; kk[1]++) X(c, 2, kk);
+    }
+    for (lv[0] = 0; lv[0] < 8; lv[0]++)
+        for (lv[1] = 0; lv[1] < 2; lv[1]++) X(c, 3, lv);
+}
+static int setup_simt(ctx *c) {
+    long long n = SM_N(c), BM = SM_BM(c), BN = SM_BN(c), BK = SM_BK(c);
+    if (BM < 8 || BN < 8 || BK < 4 || BM % 8 || BN % 8 || BK % 4 || n % BM || n % BN || n % BK || n % 4) return -1;
+    if ((BM / 8) * (BN / 8) > 1024) return -1;
+    c->grid[0] = n / BN; c->grid[1] = n / BM; c->grid[2] = 1;
+    c->wg[0] = BN / 8; c->wg[1] = BM / 8; c->wg[2] = 1;
+    int s0 = add_stmt(c, 3, DT_F32, 0, 0, 0);
+    stmt_site(c, s0, add_site(c, "simt-a", MEM_GLOBAL, DIR_LOAD, "float32x4", 16, ix_sm_a));
+    stmt_site(c, s0, add_site(c, "As_st0", MEM_LOCAL, DIR_STORE, "float32", 4, ix_sm_ast0));
+    stmt_site(c, s0, add_site(c, "As_st1", MEM_LOCAL, DIR_STORE, "float32", 4, ix_sm_ast1));
+    stmt_site(c, s0, add_site(c, "As_st2", MEM_LOCAL, DIR_STORE, "float32", 4, ix_sm_ast2));
+    stmt_site(c, s0, add_site(c, "As_st3", MEM_LOCAL, DIR_STORE, "float32", 4, ix_sm_ast3));
+    int s1 = add_stmt(c, 3, DT_F32, 0, 0, 0);
+    stmt_site(c, s1, add_site(c, "simt-b", MEM_GLOBAL, DIR_LOAD, "float32x4", 16, ix_sm_b));
+    stmt_site(c, s1, add_site(c, "Bs_st", MEM_LOCAL, DIR_STORE, "float32x4", 16, ix_sm_bst));
+    int s2 = add_stmt(c, 2, DT_F32, 0, 0, 64);
+    stmt_site(c, s2, add_site(c, "As_ld0", MEM_LOCAL, DIR_LOAD, "float32x4", 16, ix_sm_ald0));
+    stmt_site(c, s2, add_site(c, "As_ld1", MEM_LOCAL, DIR_LOAD, "float32x4", 16, ix_sm_ald1));
+    stmt_site(c, s2, add_site(c, "Bs_ld0", MEM_LOCAL, DIR_LOAD, "float32x4", 16, ix_sm_bld0));
+    stmt_site(c, s2, add_site(c, "Bs_ld1", MEM_LOCAL, DIR_LOAD, "float32x4", 16, ix_sm_bld1));
+    int s3 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+    stmt_site(c, s3, add_site(c, "simt-c", MEM_GLOBAL, DIR_STORE, "float32x4", 16, ix_sm_c));
+    c->walk = walk_simt;
+    return 0;
+}
+
+/* ======================================================================
  * Public oracle entry: enumerate every (group, sub-group, lane) point.
  * ====================================================================== */
 typedef struct {
@@ -777,6 +883,7 @@ static const struct { const char *name; int fam, v; } KTAB[] = {
     {"dg_dmpf_dm", 7, 5}, {"dg_res", 7, 6},
     {"fd_tile", 8, 0}, {"fd_direct", 8, 1}, {"fd_tile_u", 8, 2}, {"fd_tile_res", 8, 3}, {"fd_direct_u", 8, 4},
     {"fd_direct_res", 8, 5},
+    {"mm_simt", 9, 0},
 };
 
 int oracle_counts(const char *kernel, const long long *P, int nP, orec *out, int cap, int *n_out) {
@@ -796,6 +903,7 @@ int oracle_counts(const char *kernel, const long long *P, int nP, orec *out, int
     case 6: rc = setup_mm(c, v); break;
     case 7: rc = setup_dg(c, v); break;
     case 8: rc = setup_fd(c, v); break;
+    case 9: rc = setup_simt(c); break;
     }
     if (rc) { free(c); return -2; }
     for (int s = 0; s < c->nsite; s++) ks_init(&c->ss[s].foot, 1024);

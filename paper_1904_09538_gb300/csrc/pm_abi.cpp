@@ -33,6 +33,7 @@ static constexpr double REQ = std::numeric_limits<double>::quiet_NaN();
 #define P_MM {"n", nullptr}, {REQ}, {1}
 #define P_DG {"Np", "Nel", "L0", "L1", nullptr}, {REQ, REQ, 16, 16}, {1, 1, 1, 1}
 #define P_FD {"n", "c0", "c1", nullptr}, {REQ, -4.0, 1.0}, {1, 0, 0}
+#define P_SIMT {"n", "BM", "BN", "BK", nullptr}, {REQ, 128, 128, 32}, {1, 1, 1, 1}
 
 static const KernelDef KDEFS[] = {
     {"stream", FAM_STREAM, 0, P_STREAM},
@@ -60,6 +61,7 @@ static const KernelDef KDEFS[] = {
     {"fd_tile_res", FAM_FD, 3, P_FD},
     {"fd_direct_u", FAM_FD, 4, P_FD},
     {"fd_direct_res", FAM_FD, 5, P_FD},
+    {"mm_simt", FAM_SIMT, 0, P_SIMT},
 };
 
 const KernelDef *kernel_def(int32_t id) {

@@ -419,6 +419,48 @@ pm_status counts_fd(const KP &kp, std::vector<pm_feature> &v) {
     return PM_OK;
 }
 
+// ---------------------------------------------------------------- SIMT matmul family
+// Work-group (BN/8) x (BM/8), 8x8 outputs per work-item, k tiles of BK; see
+// pm_tiles.cu for the loop nest.  Vector (float32x4) units for global memory.
+pm_status counts_simt(const KP &kp, std::vector<pm_feature> &v) {
+    i64 n = kp.i(0), BM = kp.i(1), BN = kp.i(2), BK = kp.i(3);
+    i64 L0 = BN / 8, L1 = BM / 8, T = L0 * L1, S = T / 32, KC = BK / 4, NC = BN / 4;
+    i64 G = (n / BN) * (n / BM), K = n / BK, n4 = n / 4;
+    i64 qa = cdiv(KC, L0);
+    u64 aWI = (u64)(G * K * BM * KC), aSG = (u64)(G * S * K * 8 * qa);
+    // B tile rows lid1 + L1 r < BK: a sub-group's first row a decides activity
+    i64 bsg = 0;
+    for (i64 sg = 0; sg < S; sg++) {
+        i64 a = L0 >= 32 ? (32 * sg) / L0 : (32 * sg) / L0;
+        bsg += 2 * cdiv(BK - a, L1);
+    }
+    u64 bWI = (u64)(G * K * BK * NC), bSG = (u64)(G * K * bsg);
+    Out o(v);
+    o.op(0, 2, (u64)(G * T * K * BK * 64), (u64)(G * S * K * BK * 64));
+    auto site = [&](const char *tag, int mem, int dir, const char *dt, int ds, i64 l0, i64 l1, i64 g0, i64 g1,
+                    i64 loop, u64 wi, u64 sg, u64 foot) {
+        Site x{};
+        x.tag = tag; x.mem = mem; x.dir = dir; x.dtype = dt; x.dsize = ds;
+        x.nl = 2; x.l[0] = l0; x.l[1] = l1; x.ng = 2; x.g[0] = g0; x.g[1] = g1; x.loop = loop;
+        x.wi = wi; x.sg = sg; x.foot = foot;
+        o.site(x);
+    };
+    const u64 full = (u64)(n * n / 4);
+    site("simt-a", GL, LD, "float32x4", 16, 1, n4, 0, BM * n4, L0, aWI, aSG, full);
+    static const char *ast[4] = {"As_st0", "As_st1", "As_st2", "As_st3"};
+    for (int j = 0; j < 4; j++) site(ast[j], LO, ST, "float32", 4, 4 * BM, 1, 0, 0, 4 * L0 * BM, aWI, aSG, (u64)(BM * KC));
+    site("simt-b", GL, LD, "float32x4", 16, 1, n4, NC, 0, L0, bWI, bSG, full);
+    site("Bs_st", LO, ST, "float32x4", 16, 1, NC, 0, 0, L0, bWI, bSG, (u64)(BK * NC));
+    const u64 cWI = (u64)(G * T * K * BK), cSG = (u64)(G * S * K * BK);
+    site("As_ld0", LO, LD, "float32x4", 16, 0, 2, 0, 0, BM / 4, cWI, cSG, (u64)(BK * L1));
+    site("As_ld1", LO, LD, "float32x4", 16, 0, 2, 0, 0, BM / 4, cWI, cSG, (u64)(BK * L1));
+    site("Bs_ld0", LO, LD, "float32x4", 16, 2, 0, 0, 0, NC, cWI, cSG, (u64)(BK * L0));
+    site("Bs_ld1", LO, LD, "float32x4", 16, 2, 0, 0, 0, NC, cWI, cSG, (u64)(BK * L0));
+    site("simt-c", GL, ST, "float32x4", 16, 2, 2 * n, NC, BM * n4, 1, (u64)(G * T * 16), (u64)(G * S * 16), full);
+    o.finish((u64)(2 * K), (u64)G);
+    return PM_OK;
+}
+
 bool pow2(i64 x) { return x > 0 && (x & (x - 1)) == 0; }
 
 }  // namespace
@@ -486,6 +528,16 @@ pm_status validate(const KP &kp) {
     case FAM_FD:
         if (kp.i(0) < 1 || kp.i(0) > 46000) return fail(PM_EINVAL, "%s: n must be 1..46000", nm);
         return PM_OK;
+    case FAM_SIMT: {
+        i64 n = kp.i(0), BM = kp.i(1), BN = kp.i(2), BK = kp.i(3);
+        bool okm = BM == 64 || BM == 96 || BM == 128 || BM == 256;
+        bool okn = BN == 64 || BN == 128 || BN == 256;
+        if (!okm || !okn || (BK != 32 && BK != 64))
+            return fail(PM_EINVAL, "%s: tile must have BM in {64,96,128,256}, BN in {64,128,256}, BK in {32,64}", nm);
+        if (n < 1 || n > 32768 || n % BM || n % BN || n % BK)
+            return fail(PM_EINVAL, "%s: n (<= 32768) must be divisible by BM, BN and BK", nm);
+        return PM_OK;
+    }
     }
     return fail(PM_EINVAL, "unknown family");
 }
@@ -503,6 +555,7 @@ pm_status counts(const KP &kp, std::vector<pm_feature> &out) {
     case FAM_MM: return counts_mm(kp, out);
     case FAM_DG: return counts_dg(kp, out);
     case FAM_FD: return counts_fd(kp, out);
+    case FAM_SIMT: return counts_simt(kp, out);
     }
     return fail(PM_EINVAL, "unknown family");
 }
@@ -563,6 +616,13 @@ pm_status buffers(const KP &kp, std::vector<BufSpec> &b) {
         } else {
             b.push_back({"res", PM_F32, PM_OUT, 3 * Nel * Np});
         }
+        break;
+    }
+    case FAM_SIMT: {
+        uint64_t N2 = (uint64_t)kp.i(0) * (uint64_t)kp.i(0);
+        b.push_back({"a", PM_F32, PM_IN, N2});
+        b.push_back({"b", PM_F32, PM_IN, N2});
+        b.push_back({"c", PM_F32, PM_OUT, N2});
         break;
     }
     case FAM_FD: {

@@ -22,6 +22,7 @@ static pm_status launch_any(const KP &kp, void *const *bufs, size_t nbufs, void 
         if (!bufs[i]) return fail(PM_EINVAL, "%s: buffer %zu (%s) is NULL", kp.def->name, i, spec[i].name);
     switch (kp.def->fam) {
     case FAM_MM: case FAM_DG: case FAM_FD: return launch_modeled(kp, bufs, stream);
+    case FAM_SIMT: return launch_tiles(kp, bufs, stream);
     default: return launch_suite(kp, bufs, stream);
     }
 }

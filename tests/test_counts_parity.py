@@ -154,3 +154,10 @@ def test_bad_parameters_rejected():
         pm.Model("t", "p_a * (f_x")
     with pytest.raises(pm.PMError):
         pm.Model("t", "p_a * f_mem_access_float32_global")
+
+
+@pytest.mark.parametrize("n,BM,BN,BK", [(192, 96, 64, 32), (256, 64, 128, 64), (256, 128, 64, 32),
+                                        (512, 256, 128, 32), (256, 128, 256, 64), (256, 256, 256, 32),
+                                        (768, 96, 256, 64), (384, 96, 128, 32), (128, 64, 64, 64)])
+def test_mm_simt(n, BM, BN, BK):
+    compare("mm_simt", n=n, BM=BM, BN=BN, BK=BK)

@@ -239,3 +239,25 @@ def test_launch_errors():
         pm.launch("stream", [x, x], N=1000, L=1)            # N not a multiple of 256
     with pytest.raises(pm.PMError):
         pm.launch("mm_pf", [x, x, x], n=24)                 # n not a multiple of 16
+
+
+# ---------------------------------------------------------------- autotuning families
+_MM768 = {}
+
+
+def _mm768():
+    if not _MM768:
+        n = 768
+        a, b = pm_inputs.uniform((n, n), 91), pm_inputs.uniform((n, n), 92)
+        ref, rabs = refs.matmul(a, b)
+        _MM768.update(a=a, b=b, ref=ref, rabs=rabs)
+    return _MM768
+
+
+@pytest.mark.parametrize("BM", [64, 96, 128, 256])
+@pytest.mark.parametrize("BN", [64, 128, 256])
+@pytest.mark.parametrize("BK", [32, 64])
+def test_mm_simt_all_tiles(BM, BN, BK):
+    d = _mm768()
+    (c,) = run_kernel("mm_simt", [d["a"], d["b"]], n=768, BM=BM, BN=BN, BK=BK)
+    assert cond_err(c.reshape(768, 768), d["ref"], d["rabs"]) <= TOL
