@@ -95,3 +95,10 @@ def tune_fit_threads(models, Xs, ts, p0s=None, candidates=(64, 128, 256), reps=1
         times[th] = (time.perf_counter() - t0) / reps
     best = min(times, key=times.get)
     return best, times
+
+
+if __name__ == "__main__":
+    import json
+    import sys
+    out = {"mm_simt": rank_family()}
+    json.dump(out, open(sys.argv[1], "w") if len(sys.argv) > 1 else sys.stdout, indent=1, default=str)
