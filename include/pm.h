@@ -59,7 +59,9 @@ typedef struct {
  * twins "fd_tile_u", "fd_tile_res", "fd_direct_u", "fd_direct_res"
  * (Section "Finite Differences"); autotuning spaces (the paper's use case
  * of ranking equivalent variants, Section "Assumptions and Limitations"):
- * "mm_simt" (register-tiled fp32 matmul, parameters n, BM, BN, BK).
+ * "mm_simt" (register-tiled fp32 matmul, parameters n, BM, BN, BK); the
+ * added BF16 tensor-core matmul "mm_tc" (C = A Bt^T, bf16 in, fp32 out,
+ * tcgen05/TMEM/TMA, parameter n, a multiple of 256).
  * Returns PM_EUNKNOWN_KERNEL for other names. */
 pm_status pm_kernel_lookup(const char *name, int32_t *kernel);
 pm_status pm_kernel_count(int32_t *n);

@@ -43,7 +43,7 @@
 
 enum { MEM_GLOBAL = 0, MEM_LOCAL = 1 };
 enum { DIR_LOAD = 0, DIR_STORE = 1 };
-enum { DT_F32 = 0, DT_F64 = 1 };
+enum { DT_F32 = 0, DT_F64 = 1, DT_BF16 = 2 };
 
 typedef struct ctx ctx;
 typedef long long (*idx_fn)(const ctx *c, const long long *g, const long long *l, const long long *lv);
@@ -119,7 +119,7 @@ struct ctx {
     long long g[3], l[3];
     /* accumulators */
     site_stat ss[MAXSITE];
-    unsigned long long op_wi[2][3], op_sg[2][3];  /* [dtype][add,mul,madd] */
+    unsigned long long op_wi[3][3], op_sg[3][3];  /* [dtype][add,mul,madd] */
     unsigned long long stmt_sg[MAXSTMT], stmt_wi[MAXSTMT];
     long long bar_cur, bar_min, bar_max;
     kset sgset;              /* distinct statement instances of the current SG */
@@ -865,6 +865,78 @@ static int setup_simt(ctx *c) {
 }
 
 /* ======================================================================
+ * BF16 tensor-core matmul: C = A Bt^T, A and Bt n x n bf16 row-major, C fp32.
+ * P = {n}.  Work-group of 128 work-items (1-D), grid (n/256, n/128), one
+ * 128 x 256 tile of C per work-group.  Work-item 0 copies, per 64-wide k
+ * tile, the 128 x 64 box of A and the 256 x 64 box of Bt (described element
+ * by element); work-item 32 issues four 128 x 256 x 16 multiply-add
+ * instructions per k tile; every work-item stores its C row as 8 x 8
+ * float32x4 vectors; three barriers.
+ * ====================================================================== */
+static long long ix_tc_a(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)l; long long n = c->P[0]; return n * (128 * G1 + lv[1]) + 64 * lv[0] + lv[2];
+}
+static long long ix_tc_b(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)l; long long n = c->P[0]; return n * (256 * G0 + lv[1]) + 64 * lv[0] + lv[2];
+}
+static long long ix_tc_c(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long n = c->P[0]; return (n / 4) * (128 * G1 + L0_) + 64 * G0 + 8 * lv[0] + lv[1];
+}
+static void walk_tc(ctx *c) {
+    long long n = c->P[0], lv[3];
+    BAR(c);
+    if (c->l[0] == 0)
+        for (lv[0] = 0; lv[0] < n / 64; lv[0]++) {
+            for (lv[1] = 0; lv[1] < 128; lv[1]++)
+                for (lv[2] = 0; lv[2] < 64; lv[2]++) X(c, 0, lv);
+            for (lv[1] = 0; lv[1] < 256; lv[1]++)
+                for (lv[2] = 0; lv[2] < 64; lv[2]++) X(c, 1, lv);
+        }
+    if (c->l[0] == 32)
+        for (lv[0] = 0; lv[0] < n / 64; lv[0]++)
+            for (lv[1] = 0; lv[1] < 4; lv[1]++) X(c, 2, lv);
+    for (lv[0] = 0; lv[0] < 8; lv[0]++)
+        for (lv[1] = 0; lv[1] < 8; lv[1]++) X(c, 3, lv);
+    BAR(c);
+    BAR(c);
+}
+static int setup_tc(ctx *c) {
+    long long n = c->P[0];
+    if (n < 256 || n % 256) return -1;
+    c->grid[0] = n / 256; c->grid[1] = n / 128; c->grid[2] = 1;
+    c->wg[0] = 128; c->wg[1] = 1; c->wg[2] = 1;
+    int s0 = add_stmt(c, 3, DT_BF16, 0, 0, 0);
+    stmt_site(c, s0, add_site(c, "tc-a", MEM_GLOBAL, DIR_LOAD, "bfloat16", 2, ix_tc_a));
+    int s1 = add_stmt(c, 3, DT_BF16, 0, 0, 0);
+    stmt_site(c, s1, add_site(c, "tc-b", MEM_GLOBAL, DIR_LOAD, "bfloat16", 2, ix_tc_b));
+    add_stmt(c, 2, DT_BF16, 0, 0, 128 * 256 * 16);
+    int s3 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+    stmt_site(c, s3, add_site(c, "tc-c", MEM_GLOBAL, DIR_STORE, "float32x4", 16, ix_tc_c));
+    c->walk = walk_tc;
+    return 0;
+}
+
+/* FP64 reference of C = A Bt^T over bf16 inputs (uint16 bit patterns) */
+static double bf16_value(unsigned short h) {
+    union { unsigned int u; float f; } v;
+    v.u = (unsigned int)h << 16;
+    return (double)v.f;
+}
+void oracle_mm_tc_ref(long long m, long long n, long long k, const unsigned short *a, const unsigned short *bt,
+                      double *c, double *cabs) {
+    /* a: m x k, bt: n x k, c: m x n */
+    for (long long i = 0; i < m; i++)
+        for (long long j = 0; j < n; j++) {
+            double s = 0.0, sa = 0.0;
+            for (long long q = 0; q < k; q++) {
+                double p = bf16_value(a[k * i + q]) * bf16_value(bt[k * j + q]);
+                s += p; sa += fabs(p);
+            }
+            c[n * i + j] = s; cabs[n * i + j] = sa;
+        }
+}
+
+/* ======================================================================
  * Public oracle entry: enumerate every (group, sub-group, lane) point.
  * ====================================================================== */
 typedef struct {
@@ -884,6 +956,7 @@ static const struct { const char *name; int fam, v; } KTAB[] = {
     {"fd_tile", 8, 0}, {"fd_direct", 8, 1}, {"fd_tile_u", 8, 2}, {"fd_tile_res", 8, 3}, {"fd_direct_u", 8, 4},
     {"fd_direct_res", 8, 5},
     {"mm_simt", 9, 0},
+    {"mm_tc", 10, 0},
 };
 
 int oracle_counts(const char *kernel, const long long *P, int nP, orec *out, int cap, int *n_out) {
@@ -904,6 +977,7 @@ int oracle_counts(const char *kernel, const long long *P, int nP, orec *out, int
     case 7: rc = setup_dg(c, v); break;
     case 8: rc = setup_fd(c, v); break;
     case 9: rc = setup_simt(c); break;
+    case 10: rc = setup_tc(c); break;
     }
     if (rc) { free(c); return -2; }
     for (int s = 0; s < c->nsite; s++) ks_init(&c->ss[s].foot, 1024);
@@ -931,13 +1005,14 @@ int oracle_counts(const char *kernel, const long long *P, int nP, orec *out, int
     int n = 0;
 #define EMIT() do { if (n >= cap) { rc = -4; goto done; } memset(&out[n], 0, sizeof(orec)); } while (0)
     static const char *opn[3] = {"add", "mul", "madd"};
-    for (int dt = 0; dt < 2; dt++)
+    static const char *dtn[3] = {"float32", "float64", "bfloat16"};
+    for (int dt = 0; dt < 3; dt++)
         for (int o = 0; o < 3; o++)
             if (c->op_wi[dt][o]) {
                 EMIT();
                 out[n].kind = 0;
                 strcpy(out[n].name, opn[o]);
-                strcpy(out[n].dtype, dt == 0 ? "float32" : "float64");
+                strcpy(out[n].dtype, dtn[dt]);
                 out[n].wi = c->op_wi[dt][o]; out[n].sg = c->op_sg[dt][o];
                 n++;
             }

@@ -122,7 +122,7 @@ def parse_feature(name):
                 key, val = "mem", f
             elif f in ("load", "store"):
                 key, val = "dir", f
-            elif re.match(r"^float(32|64)(x[0-9]+)?$", f):
+            elif re.match(r"^(float(32|64)(x[0-9]+)?|bfloat16)$", f):
                 key, val = "dtype", f
             elif f.startswith("lstrides:{") and f.endswith("}"):
                 key, val = "lstrides", _parse_strides(f[len("lstrides:{"):-1])

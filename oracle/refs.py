@@ -34,6 +34,8 @@ def _setup():
     L.oracle_dg_twin_ref.argtypes = [ctypes.c_int, ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong,
                                      ctypes.c_longlong, _f32p, _f32p, _f32p]
     L.oracle_fd_twin_ref.argtypes = [ctypes.c_int, ctypes.c_longlong, _f32p, _f32p]
+    _u16p = np.ctypeslib.ndpointer(dtype=np.uint16, flags="C_CONTIGUOUS")
+    L.oracle_mm_tc_ref.argtypes = [ctypes.c_longlong, ctypes.c_longlong, ctypes.c_longlong, _u16p, _u16p, _f64p, _f64p]
     _ready = True
 
 
@@ -63,6 +65,17 @@ def matmul(a, b):
     n = a.shape[0]
     c = np.empty((n, n)); ca = np.empty((n, n))
     lib().oracle_mm_ref(n, np.ascontiguousarray(a, np.float32), np.ascontiguousarray(b, np.float32), c, ca)
+    return c, ca
+
+
+def matmul_bf16_tn(a_bits, bt_bits):
+    """FP64 C = A Bt^T over bf16 inputs given as uint16 bit patterns, and the |.| sums."""
+    _setup()
+    m, k = a_bits.shape
+    n = bt_bits.shape[0]
+    c = np.empty((m, n)); ca = np.empty((m, n))
+    lib().oracle_mm_tc_ref(m, n, k, np.ascontiguousarray(a_bits, np.uint16), np.ascontiguousarray(bt_bits, np.uint16),
+                           c, ca)
     return c, ca
 
 

@@ -62,6 +62,7 @@ static const KernelDef KDEFS[] = {
     {"fd_direct_u", FAM_FD, 4, P_FD},
     {"fd_direct_res", FAM_FD, 5, P_FD},
     {"mm_simt", FAM_SIMT, 0, P_SIMT},
+    {"mm_tc", FAM_TC, 0, P_MM},
 };
 
 const KernelDef *kernel_def(int32_t id) {

@@ -461,6 +461,38 @@ pm_status counts_simt(const KP &kp, std::vector<pm_feature> &v) {
     return PM_OK;
 }
 
+// ---------------------------------------------------------------- tensor-core matmul
+// 128-thread work-group per 128 x 256 tile of C; per 64-wide k tile the
+// elected thread 0 copies a 128x64 box of A and a 256x64 box of Bt (counted
+// element by element, uniform, hence per sub-group) and thread 32 issues four
+// 128x256x16 multiply-add instructions; every work-item stores 64 16-byte
+// vectors of its C row; three barriers.
+pm_status counts_tc(const KP &kp, std::vector<pm_feature> &v) {
+    i64 n = kp.i(0);
+    u64 G = (u64)((n / 256) * (n / 128)), KT = (u64)(n / 64);
+    u64 nn = (u64)(n * n);
+    Out o(v);
+    auto site = [&](const char *tag, int dir, const char *dt, int ds, int nl, i64 l0, i64 g0, i64 g1, i64 loop, u64 wi,
+                    u64 sg, u64 foot) {
+        Site x{};
+        x.tag = tag; x.mem = GL; x.dir = dir; x.dtype = dt; x.dsize = ds;
+        x.nl = nl; x.l[0] = l0; x.ng = 2; x.g[0] = g0; x.g[1] = g1; x.loop = loop;
+        x.wi = wi; x.sg = sg; x.foot = foot;
+        o.site(x);
+    };
+    const u64 ma = G * KT * 128 * 64, mb = G * KT * 256 * 64, mm = G * KT * 4;
+    site("tc-a", LD, "bfloat16", 2, 1, 0, 0, 128 * n, 1, ma, ma, nn);
+    site("tc-b", LD, "bfloat16", 2, 1, 0, 256 * n, 0, 1, mb, mb, nn);
+    site("tc-c", ST, "float32x4", 16, 1, n / 4, 64, 32 * n, 1, G * 128 * 64, G * 4 * 64, nn / 4);
+    pm_feature f = op_rec("bfloat16", "madd", mm * 128 * 256 * 16, mm * 128 * 256 * 16);
+    v.push_back(f);
+    for (auto &x : o.sites) v.push_back(x);
+    v.push_back(simple(PM_FEAT_SYNC, PM_GRAN_WI, 3));
+    v.push_back(simple(PM_FEAT_GROUPS, PM_GRAN_WG, G));
+    v.push_back(simple(PM_FEAT_LAUNCH, PM_GRAN_K, 1));
+    return PM_OK;
+}
+
 bool pow2(i64 x) { return x > 0 && (x & (x - 1)) == 0; }
 
 }  // namespace
@@ -528,6 +560,10 @@ pm_status validate(const KP &kp) {
     case FAM_FD:
         if (kp.i(0) < 1 || kp.i(0) > 46000) return fail(PM_EINVAL, "%s: n must be 1..46000", nm);
         return PM_OK;
+    case FAM_TC:
+        if (kp.i(0) < 256 || kp.i(0) % 256 || kp.i(0) > 32768)
+            return fail(PM_EINVAL, "%s: n must be a multiple of 256 in [256, 32768]", nm);
+        return PM_OK;
     case FAM_SIMT: {
         i64 n = kp.i(0), BM = kp.i(1), BN = kp.i(2), BK = kp.i(3);
         bool okm = BM == 64 || BM == 96 || BM == 128 || BM == 256;
@@ -556,6 +592,7 @@ pm_status counts(const KP &kp, std::vector<pm_feature> &out) {
     case FAM_DG: return counts_dg(kp, out);
     case FAM_FD: return counts_fd(kp, out);
     case FAM_SIMT: return counts_simt(kp, out);
+    case FAM_TC: return counts_tc(kp, out);
     }
     return fail(PM_EINVAL, "unknown family");
 }
@@ -616,6 +653,13 @@ pm_status buffers(const KP &kp, std::vector<BufSpec> &b) {
         } else {
             b.push_back({"res", PM_F32, PM_OUT, 3 * Nel * Np});
         }
+        break;
+    }
+    case FAM_TC: {
+        uint64_t N2 = (uint64_t)kp.i(0) * (uint64_t)kp.i(0);
+        b.push_back({"a", PM_BF16, PM_IN, N2});
+        b.push_back({"bt", PM_BF16, PM_IN, N2});
+        b.push_back({"c", PM_F32, PM_OUT, N2});
         break;
     }
     case FAM_SIMT: {

@@ -22,7 +22,7 @@ void clear_error();
     } while (0)
 
 // ---- kernel registry ------------------------------------------------------
-enum Family { FAM_STREAM, FAM_FMA, FAM_SMEM, FAM_BARRIER, FAM_OVERLAP, FAM_EMPTY, FAM_MM, FAM_DG, FAM_FD, FAM_SIMT };
+enum Family { FAM_STREAM, FAM_FMA, FAM_SMEM, FAM_BARRIER, FAM_OVERLAP, FAM_EMPTY, FAM_MM, FAM_DG, FAM_FD, FAM_SIMT, FAM_TC };
 
 constexpr int kMaxParams = 8;
 
@@ -64,6 +64,8 @@ pm_status buffers(const KP &kp, std::vector<BufSpec> &out);
 pm_status launch_suite(const KP &kp, void *const *bufs, void *stream);
 pm_status launch_modeled(const KP &kp, void *const *bufs, void *stream);
 pm_status launch_tiles(const KP &kp, void *const *bufs, void *stream);
+pm_status launch_tc(const KP &kp, void *const *bufs, void *stream);
+pm_status tc_check_timeout();
 
 // ---- feature records helper --------------------------------------------------
 void canonical_name(pm_feature &f);

@@ -1,0 +1,290 @@
+// BF16-in / FP32-accumulate tensor-core matmul on the 5th-generation tensor
+// cores (tcgen05): C[M x N] = A[M x K] * Bt[N x K]^T, A and Bt row-major
+// (both K-major, the usual tensor-core "TN" layout), C row-major FP32.
+//
+// One CTA of 128 threads computes a 128 x 256 tile of C:
+//   warp 0 lane 0: TMA producer -- per 64-wide k tile, one 128x64 tile of A
+//       and one 256x64 tile of Bt (128-byte swizzle) into a 4-stage shared
+//       memory ring, completion tracked by "full" mbarriers;
+//   warp 1 lane 0: MMA issuer -- four tcgen05.mma (M=128, N=256, K=16) per k
+//       tile accumulating in tensor memory; tcgen05.commit releases the
+//       stage ("empty" mbarrier) and finally signals the accumulator;
+//   warp 2: allocates / frees 256 TMEM columns;
+//   all four warps: epilogue -- tcgen05.ld of their 32 TMEM lanes (= rows),
+//       16-byte stores to C.
+// Every mbarrier wait is bounded; on timeout the kernel sets an error word
+// (read by the host after synchronising), stops issuing work, drains its own
+// copies (bounded), frees its TMEM and returns.
+#include <cuda.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+#include <mutex>
+
+#include "pm_internal.h"
+
+namespace pm {
+
+static __device__ int g_tc_timeout;   // set to 1 by any CTA whose bounded wait ran out
+
+namespace {
+
+constexpr int TM = 128, TN = 256, TK = 64, STAGES = 4;
+constexpr int A_BYTES = TM * TK * 2, B_BYTES = TN * TK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
+constexpr int TMEM_COLS = 256;
+constexpr long long WAIT_LIMIT = 1ll << 26;  // polls of a try_wait before giving up
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
+}
+// bounded wait for the phase with the given parity; false on timeout
+__device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
+    const uint32_t a = smem_u32(bar);
+    for (long long i = 0; i < WAIT_LIMIT; i++) {
+        uint32_t ok;
+        asm volatile(
+            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (ok) return true;
+        if ((i & 1023) == 1023 && *(volatile int *)&g_tc_timeout) return false;
+    }
+    atomicExch(&g_tc_timeout, 1);
+    return false;
+}
+__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
+    asm volatile(
+        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
+        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
+        : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+// Shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1.
+__device__ __forceinline__ uint64_t smem_desc(const void *p) {
+    const uint64_t addr = smem_u32(p);
+    uint64_t d = 0;
+    d |= (addr >> 4) & 0x3FFFull;            // start address, bits 0-13
+    d |= (uint64_t)1 << 16;                  // leading byte offset (unused for this layout), bits 16-29
+    d |= (uint64_t)(1024 >> 4) << 32;        // stride byte offset, bits 32-45
+    d |= (uint64_t)1 << 46;                  // version, bits 46-47
+    d |= (uint64_t)2 << 61;                  // layout: 128-byte swizzle, bits 61-63
+    return d;
+}
+
+// Instruction descriptor, kind::f16: D FP32, A and B BF16, both K-major,
+// N = 256, M = 128.
+constexpr uint32_t IDESC = (1u << 4)            // D format FP32
+                         | (1u << 7)            // A format BF16
+                         | (1u << 10)           // B format BF16
+                         | ((uint32_t)(TN >> 3) << 17)
+                         | ((uint32_t)(TM >> 4) << 24);
+
+__device__ __forceinline__ void mma_bf16(uint32_t d_tmem, uint64_t adesc, uint64_t bdesc, uint32_t accumulate) {
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n}"
+        ::"r"(d_tmem), "l"(adesc), "l"(bdesc), "r"(IDESC), "r"(accumulate)
+        : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint64_t *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+                 : "memory");
+}
+
+struct __align__(8) TcShared {
+    uint64_t full[STAGES], empty[STAGES], accum;
+    uint32_t tmem_base;
+    int issued;   // k tiles whose copies the producer issued
+};
+
+__global__ void __launch_bounds__(128, 1) k_mm_tc(const __grid_constant__ CUtensorMap tmA,
+                                                  const __grid_constant__ CUtensorMap tmB, float *__restrict__ C,
+                                                  int M, int N, int K) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    // 1024-byte aligned ring of stages, then the barriers
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    TcShared *S = (TcShared *)(base + STAGES * STAGE_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int n0 = blockIdx.x * TN, m0 = blockIdx.y * TM;
+    const int KT = K / TK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < STAGES; s++) {
+            mbar_init(&S->full[s], 1);
+            mbar_init(&S->empty[s], 1);
+        }
+        mbar_init(&S->accum, 1);
+        S->issued = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S->tmem_base)),
+                     "r"(TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            // TMA producer
+            for (int kt = 0; kt < KT; kt++) {
+                const int s = kt % STAGES, r = kt / STAGES;
+                if (r > 0 && !mbar_wait(&S->empty[s], (uint32_t)((r - 1) & 1))) break;
+                unsigned char *st = base + s * STAGE_BYTES;
+                mbar_expect_tx(&S->full[s], STAGE_BYTES);
+                tma_load_2d(st, &tmA, &S->full[s], kt * TK, m0);
+                tma_load_2d(st + A_BYTES, &tmB, &S->full[s], kt * TK, n0);
+                S->issued = kt + 1;
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            // MMA issuer
+            for (int kt = 0; kt < KT; kt++) {
+                const int s = kt % STAGES, r = kt / STAGES;
+                if (!mbar_wait(&S->full[s], (uint32_t)(r & 1))) break;
+                tc_fence_after();
+                unsigned char *st = base + s * STAGE_BYTES;
+                const uint64_t ad = smem_desc(st), bd = smem_desc(st + A_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < TK / 16; kk++)   // 16-element k slices: +32 bytes in the start address
+                    mma_bf16(tmem, ad + 2 * kk, bd + 2 * kk, (kt > 0 || kk > 0) ? 1u : 0u);
+                mma_commit(&S->empty[s]);
+            }
+            mma_commit(&S->accum);
+        }
+        __syncwarp();
+    }
+
+    // epilogue: warp w owns TMEM lanes (rows) 32w .. 32w+31
+    const bool ok = mbar_wait(&S->accum, 0);
+    __syncwarp();
+    tc_fence_after();
+    if (ok) {
+        const int row = m0 + warp * 32 + lane;
+        float *crow = C + (size_t)row * N + n0;
+#pragma unroll 1
+        for (int c = 0; c < TN / 32; c++) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(warp * 32) << 16) + (uint32_t)(c * 32);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                  "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+                  "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+                  "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float4 *dst = reinterpret_cast<float4 *>(crow + c * 32);
+#pragma unroll
+            for (int q = 0; q < 8; q++)
+                dst[q] = make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                     __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3]));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && (!ok || *(volatile int *)&g_tc_timeout)) {
+        // drain: every stage's last issued copy must have landed before the
+        // shared memory goes away (bounded waits; the error word is set)
+        const int issued = S->issued;
+        for (int s = 0; s < STAGES && s < issued; s++) {
+            const int last = s + ((issued - 1 - s) / STAGES) * STAGES;
+            const uint32_t a = smem_u32(&S->full[s]);
+            for (long long i = 0; i < WAIT_LIMIT; i++) {
+                uint32_t done;
+                asm volatile(
+                    "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+                    : "=r"(done)
+                    : "r"(a), "r"((uint32_t)((last / STAGES) & 1))
+                    : "memory");
+                if (done) break;
+            }
+        }
+    }
+    __syncthreads();
+    if (warp == 2) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+    }
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+pm_status get_encoder() {
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = (PFN_cuTensorMapEncodeTiled_v12000)fn;
+    });
+    if (!g_encode) return fail(PM_ECUDA, "mm_tc: cuTensorMapEncodeTiled is not available");
+    return PM_OK;
+}
+
+// 2-D bf16 tensor map over a rows x cols row-major matrix, box box_rows x 64,
+// 128-byte swizzle.
+pm_status make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int box_rows) {
+    cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+    cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+    cuuint32_t estr[2] = {1, 1};
+    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(PM_ECUDA, "mm_tc: cuTensorMapEncodeTiled failed (%d)", (int)r);
+    return PM_OK;
+}
+
+}  // namespace
+
+constexpr size_t kTcSmem = (size_t)STAGES * STAGE_BYTES + sizeof(TcShared) + 2048;
+
+pm_status launch_tc(const KP &kp, void *const *b, void *stream) {
+    const int n = (int)kp.i(0);
+    for (int a = 0; a < 3; a++)
+        if ((uintptr_t)b[a] % 16) return fail(PM_EINVAL, "mm_tc: buffer %d must be 16-byte aligned", a);
+    pm_status s = get_encoder();
+    if (s) return s;
+    CUtensorMap ta, tb;
+    if ((s = make_map(&ta, b[0], n, n, TM))) return s;
+    if ((s = make_map(&tb, b[1], n, n, TN))) return s;
+    PM_CUDA_TRY(cudaFuncSetAttribute(k_mm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
+    dim3 grid(n / TN, n / TM);
+    k_mm_tc<<<grid, 128, kTcSmem, (cudaStream_t)stream>>>(ta, tb, (float *)b[2], n, n, n);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
+// After a synchronisation: PM_ETIMEOUT if any CTA's bounded wait ran out
+// since the last check (the word is cleared).
+pm_status tc_check_timeout() {
+    int v = 0, z = 0;
+    PM_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_tc_timeout, sizeof v));
+    if (v) {
+        PM_CUDA_TRY(cudaMemcpyToSymbol(g_tc_timeout, &z, sizeof z));
+        return fail(PM_ETIMEOUT, "mm_tc: a bounded wait gave up (pipeline stalled)");
+    }
+    return PM_OK;
+}
+
+}  // namespace pm

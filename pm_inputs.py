@@ -47,3 +47,14 @@ def noise(shape, seed):
 def row_counts(nmodels, seed, lo=40, hi=400):
     """Uneven measurement-set sizes l_k ~ U{lo..hi}."""
     return integers((nmodels,), seed, lo, hi)
+
+
+def bf16_bits(shape, seed):
+    """Random bfloat16 values as uint16 bit patterns: random sign, exponent
+    field uniform in [118, 126] (magnitudes 2^-9 .. just under 1), random
+    7-bit mantissa."""
+    g = rng(seed)
+    sign = g.integers(0, 2, size=shape, dtype=np.uint16)
+    expo = g.integers(118, 127, size=shape, dtype=np.uint16)
+    mant = g.integers(0, 128, size=shape, dtype=np.uint16)
+    return (sign << 15) | (expo << 7) | mant

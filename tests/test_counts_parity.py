@@ -161,3 +161,8 @@ def test_bad_parameters_rejected():
                                         (768, 96, 256, 64), (384, 96, 128, 32), (128, 64, 64, 64)])
 def test_mm_simt(n, BM, BN, BK):
     compare("mm_simt", n=n, BM=BM, BN=BN, BK=BK)
+
+
+@pytest.mark.parametrize("n", [256, 512])
+def test_mm_tc(n):
+    compare("mm_tc", n=n)
