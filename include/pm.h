@@ -61,7 +61,9 @@ typedef struct {
  * of ranking equivalent variants, Section "Assumptions and Limitations"):
  * "mm_simt" (register-tiled fp32 matmul, parameters n, BM, BN, BK); the
  * added BF16 tensor-core matmul "mm_tc" (C = A Bt^T, bf16 in, fp32 out,
- * tcgen05/TMEM/TMA, parameter n, a multiple of 256).
+ * tcgen05/TMEM/TMA, parameter n, a multiple of 256); the TMA-staged
+ * stencil tile family "fd_block" (parameters n, BX, BY, c0, c1; input u of
+ * (n + 2) rows with row pitch n + 4).
  * Returns PM_EUNKNOWN_KERNEL for other names. */
 pm_status pm_kernel_lookup(const char *name, int32_t *kernel);
 pm_status pm_kernel_count(int32_t *n);

@@ -493,6 +493,38 @@ pm_status counts_tc(const KP &kp, std::vector<pm_feature> &v) {
     return PM_OK;
 }
 
+// ---------------------------------------------------------------- stencil tile family
+// Work-group (BX/4) x BY, input pitch P = n + 4; work-item (0,0) copies the
+// (BY+2) x (BX+4) box element by element (uniform: per sub-group); every
+// work-item loads 14 shared values, computes 4 outputs, stores one vector.
+pm_status counts_fdb(const KP &kp, std::vector<pm_feature> &v) {
+    i64 n = kp.i(0), BX = kp.i(1), BY = kp.i(2), P = n + 4;
+    i64 L0 = BX / 4, L1 = BY, T = L0 * L1, G = (n / BX) * (n / BY), TW = BX + 4;
+    u64 SGw = (u64)((T + 31) / 32);   // sub-groups per work-group
+    Out o(v);
+    const u64 WI = (u64)(G * T), SG = (u64)G * SGw;
+    o.op(0, 0, 12 * WI, 12 * SG);
+    o.op(0, 1, 4 * WI, 4 * SG);
+    o.op(0, 2, 4 * WI, 4 * SG);
+    auto site = [&](const char *tag, int mem, int dir, const char *dt, int ds, i64 l0, i64 l1, i64 g0, i64 g1,
+                    i64 loop, u64 wi, u64 sg, u64 foot) {
+        Site x{};
+        x.tag = tag; x.mem = mem; x.dir = dir; x.dtype = dt; x.dsize = ds;
+        x.nl = 2; x.l[0] = l0; x.l[1] = l1; x.ng = 2; x.g[0] = g0; x.g[1] = g1; x.loop = loop;
+        x.wi = wi; x.sg = sg; x.foot = foot;
+        o.site(x);
+    };
+    const u64 box = (u64)((BY + 2) * (BX + 4)) * (u64)G;
+    site("fdb-u", GL, LD, "float32", 4, 0, 0, BX, BY * P, 1, box, box, (u64)((n + 2) * P));
+    // 14 shared loads: centre row offsets 0..5, north and south rows 1..4
+    static const char *nm[14] = {"t_c0", "t_c1", "t_c2", "t_c3", "t_c4", "t_c5", "t_n1", "t_n2",
+                                 "t_n3", "t_n4", "t_s1", "t_s2", "t_s3", "t_s4"};
+    for (int k = 0; k < 14; k++) site(nm[k], LO, LD, "float32", 4, 4, TW, 0, 0, 0, WI, SG, (u64)(L0 * L1));
+    site("fdb-res", GL, ST, "float32x4", 16, 1, n / 4, L0, BY * n / 4, 0, WI, SG, (u64)(n * n / 4));
+    o.finish(1, (u64)G);
+    return PM_OK;
+}
+
 bool pow2(i64 x) { return x > 0 && (x & (x - 1)) == 0; }
 
 }  // namespace
@@ -560,6 +592,14 @@ pm_status validate(const KP &kp) {
     case FAM_FD:
         if (kp.i(0) < 1 || kp.i(0) > 46000) return fail(PM_EINVAL, "%s: n must be 1..46000", nm);
         return PM_OK;
+    case FAM_FDB: {
+        i64 n = kp.i(0), BX = kp.i(1), BY = kp.i(2);
+        if (BX != 32 && BX != 64 && BX != 128) return fail(PM_EINVAL, "%s: BX must be 32, 64 or 128", nm);
+        if (BY != 4 && BY != 8 && BY != 16 && BY != 32) return fail(PM_EINVAL, "%s: BY must be 4, 8, 16 or 32", nm);
+        if (n < BX || n % BX || n % BY || n > 46000)
+            return fail(PM_EINVAL, "%s: n (<= 46000) must be divisible by BX and BY", nm);
+        return PM_OK;
+    }
     case FAM_TC:
         if (kp.i(0) < 256 || kp.i(0) % 256 || kp.i(0) > 32768)
             return fail(PM_EINVAL, "%s: n must be a multiple of 256 in [256, 32768]", nm);
@@ -593,6 +633,7 @@ pm_status counts(const KP &kp, std::vector<pm_feature> &out) {
     case FAM_FD: return counts_fd(kp, out);
     case FAM_SIMT: return counts_simt(kp, out);
     case FAM_TC: return counts_tc(kp, out);
+    case FAM_FDB: return counts_fdb(kp, out);
     }
     return fail(PM_EINVAL, "unknown family");
 }
@@ -653,6 +694,12 @@ pm_status buffers(const KP &kp, std::vector<BufSpec> &b) {
         } else {
             b.push_back({"res", PM_F32, PM_OUT, 3 * Nel * Np});
         }
+        break;
+    }
+    case FAM_FDB: {
+        uint64_t n = (uint64_t)kp.i(0);
+        b.push_back({"u", PM_F32, PM_IN, (n + 2) * (n + 4)});
+        b.push_back({"res", PM_F32, PM_OUT, n * n});
         break;
     }
     case FAM_TC: {

@@ -22,7 +22,7 @@ void clear_error();
     } while (0)
 
 // ---- kernel registry ------------------------------------------------------
-enum Family { FAM_STREAM, FAM_FMA, FAM_SMEM, FAM_BARRIER, FAM_OVERLAP, FAM_EMPTY, FAM_MM, FAM_DG, FAM_FD, FAM_SIMT, FAM_TC };
+enum Family { FAM_STREAM, FAM_FMA, FAM_SMEM, FAM_BARRIER, FAM_OVERLAP, FAM_EMPTY, FAM_MM, FAM_DG, FAM_FD, FAM_SIMT, FAM_TC, FAM_FDB };
 
 constexpr int kMaxParams = 8;
 
@@ -66,6 +66,11 @@ pm_status launch_modeled(const KP &kp, void *const *bufs, void *stream);
 pm_status launch_tiles(const KP &kp, void *const *bufs, void *stream);
 pm_status launch_tc(const KP &kp, void *const *bufs, void *stream);
 pm_status tc_check_timeout();
+pm_status fdb_check_timeout();
+// 2-D tensor map (TMA descriptor) over a row-major matrix; `map` must point
+// to a CUtensorMap (64-byte aligned, 128 bytes).
+pm_status tensor_map_2d(struct CUtensorMap_st *map, int bf16, const void *ptr, uint64_t cols, uint64_t rows,
+                        uint64_t row_bytes, uint32_t box_cols, uint32_t box_rows, int swizzle128);
 
 // ---- feature records helper --------------------------------------------------
 void canonical_name(pm_feature &f);

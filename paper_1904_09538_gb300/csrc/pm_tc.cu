@@ -21,6 +21,7 @@
 #include <mutex>
 
 #include "pm_internal.h"
+#include "pm_tma.cuh"
 
 namespace pm {
 
@@ -33,36 +34,9 @@ constexpr int A_BYTES = TM * TK * 2, B_BYTES = TN * TK * 2, STAGE_BYTES = A_BYTE
 constexpr int TMEM_COLS = 256;
 constexpr long long WAIT_LIMIT = 1ll << 26;  // polls of a try_wait before giving up
 
-__device__ __forceinline__ uint32_t smem_u32(const void *p) {
-    return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count));
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
-    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes) : "memory");
-}
-// bounded wait for the phase with the given parity; false on timeout
+// bounded wait on this kernel's error word
 __device__ __forceinline__ bool mbar_wait(uint64_t *bar, uint32_t parity) {
-    const uint32_t a = smem_u32(bar);
-    for (long long i = 0; i < WAIT_LIMIT; i++) {
-        uint32_t ok;
-        asm volatile(
-            "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
-            : "=r"(ok)
-            : "r"(a), "r"(parity)
-            : "memory");
-        if (ok) return true;
-        if ((i & 1023) == 1023 && *(volatile int *)&g_tc_timeout) return false;
-    }
-    atomicExch(&g_tc_timeout, 1);
-    return false;
-}
-__device__ __forceinline__ void tma_load_2d(void *dst, const CUtensorMap *map, uint64_t *bar, int x, int y) {
-    asm volatile(
-        "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%3, %4}], [%2];"
-        ::"r"(smem_u32(dst)), "l"((uint64_t)map), "r"(smem_u32(bar)), "r"(x), "r"(y)
-        : "memory");
+    return mbar_wait_bounded(bar, parity, &g_tc_timeout, WAIT_LIMIT);
 }
 __device__ __forceinline__ void tc_fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void tc_fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
@@ -124,7 +98,7 @@ __global__ void __launch_bounds__(128, 1) k_mm_tc(const __grid_constant__ CUtens
         }
         mbar_init(&S->accum, 1);
         S->issued = 0;
-        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        mbar_init_fence();
     }
     if (warp == 2) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S->tmem_base)),
@@ -225,10 +199,12 @@ __global__ void __launch_bounds__(128, 1) k_mm_tc(const __grid_constant__ CUtens
     }
 }
 
-PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
-std::once_flag g_encode_once;
+}  // namespace
 
-pm_status get_encoder() {
+static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+static std::once_flag g_encode_once;
+
+static pm_status get_encoder() {
     std::call_once(g_encode_once, [] {
         void *fn = nullptr;
         cudaDriverEntryPointQueryResult q;
@@ -241,21 +217,21 @@ pm_status get_encoder() {
     return PM_OK;
 }
 
-// 2-D bf16 tensor map over a rows x cols row-major matrix, box box_rows x 64,
-// 128-byte swizzle.
-pm_status make_map(CUtensorMap *map, const void *ptr, int rows, int cols, int box_rows) {
+pm_status tensor_map_2d(CUtensorMap *map, int bf16, const void *ptr, uint64_t cols, uint64_t rows, uint64_t row_bytes,
+                        uint32_t box_cols, uint32_t box_rows, int swizzle128) {
+    pm_status s = get_encoder();
+    if (s) return s;
     cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
-    cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-    cuuint32_t box[2] = {(cuuint32_t)TK, (cuuint32_t)box_rows};
+    cuuint64_t strides[1] = {(cuuint64_t)row_bytes};
+    cuuint32_t box[2] = {box_cols, box_rows};
     cuuint32_t estr[2] = {1, 1};
-    CUresult r = g_encode(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(ptr), dims, strides, box, estr,
-                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
-                          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (r != CUDA_SUCCESS) return fail(PM_ECUDA, "mm_tc: cuTensorMapEncodeTiled failed (%d)", (int)r);
+    CUresult r = g_encode(map, bf16 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16 : CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2,
+                          const_cast<void *>(ptr), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                          swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return fail(PM_ECUDA, "cuTensorMapEncodeTiled failed (%d)", (int)r);
     return PM_OK;
 }
-
-}  // namespace
 
 constexpr size_t kTcSmem = (size_t)STAGES * STAGE_BYTES + sizeof(TcShared) + 2048;
 
@@ -263,11 +239,10 @@ pm_status launch_tc(const KP &kp, void *const *b, void *stream) {
     const int n = (int)kp.i(0);
     for (int a = 0; a < 3; a++)
         if ((uintptr_t)b[a] % 16) return fail(PM_EINVAL, "mm_tc: buffer %d must be 16-byte aligned", a);
-    pm_status s = get_encoder();
-    if (s) return s;
+    pm_status s;
     CUtensorMap ta, tb;
-    if ((s = make_map(&ta, b[0], n, n, TM))) return s;
-    if ((s = make_map(&tb, b[1], n, n, TN))) return s;
+    if ((s = tensor_map_2d(&ta, 1, b[0], n, n, (uint64_t)n * 2, TK, TM, 1))) return s;
+    if ((s = tensor_map_2d(&tb, 1, b[1], n, n, (uint64_t)n * 2, TK, TN, 1))) return s;
     PM_CUDA_TRY(cudaFuncSetAttribute(k_mm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
     dim3 grid(n / TN, n / TM);
     k_mm_tc<<<grid, 128, kTcSmem, (cudaStream_t)stream>>>(ta, tb, (float *)b[2], n, n, n);

@@ -166,3 +166,8 @@ def test_mm_simt(n, BM, BN, BK):
 @pytest.mark.parametrize("n", [256, 512])
 def test_mm_tc(n):
     compare("mm_tc", n=n)
+
+
+@pytest.mark.parametrize("n,BX,BY", [(64, 32, 4), (128, 64, 8), (128, 128, 16), (256, 128, 32), (96, 32, 32)])
+def test_fd_block(n, BX, BY):
+    compare("fd_block", n=n, BX=BX, BY=BY)
