@@ -120,6 +120,18 @@ def kernel_instance(kernel, p):
     return "k_" + kernel
 
 
+def workload_config(variants, trials):
+    """The workload a step covers; identical in both arms."""
+    from paper_1904_09538_gb300 import suite as S
+    bps = sum(S.algorithmic_bytes(k, p) for k, p in variants) * trials
+    return {"workload": "calibration suite (stream, arithmetic, local-memory, barrier, overlap, empty kernels): "
+                        "%d variants, %d timed launches each" % (len(variants), trials),
+            "variants": len(variants), "trials_per_variant": trials,
+            "families": len({S.family_key(k, p) for k, p in variants}), "bytes_per_step": bps,
+            "l2": "inputs larger than L2 (stream arrays up to 2 GiB; step footprint %.0f GB)" % (bps / 1e9),
+            "parallelism": "replicas"}
+
+
 def run_ours(args):
     import numpy as np
     import torch
@@ -266,11 +278,7 @@ def run_ours(args):
         "metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": round(elapsed / args.steps * 1e3, 3), "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-        "config": {"workload": "calibration suite (configs[1]): %d variants, %d timed launches each" %
-                   (len(prepared), args.trials),
-                   "variants": len(prepared), "trials_per_variant": args.trials, "families": len(fam_names),
-                   "bytes_per_step": bytes_per_step, "l2": "inputs larger than L2 (stream arrays up to 2 GiB; "
-                   "step footprint %.0f GB)" % (bytes_per_step / 1e9), "parallelism": "replicas"},
+        "config": workload_config(variants, args.trials),
         "roofline": roofline,
         "best_stream_kernel": {"kernel": best_stream[1], "GB/s": round(best_stream[0], 1),
                                "frac": round(best_stream[0] / peaks["hbm_gbs"], 4)},
@@ -465,7 +473,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
-            "config": {"workload": "calibration suite (configs[1]), bounded sample per step", "variants": len(variants)},
+            "config": workload_config(variants, args.trials),
             "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": last["sample"]},
             "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
