@@ -75,9 +75,11 @@ KERNELS = {
 }
 for _k in ("mm_pf", "mm_nopf", "mm_pf_a", "mm_pf_b", "mm_nopf_a", "mm_nopf_b"):
     KERNELS[_k] = (("n",), (2, 2))
-for _k in ("dg_nopf", "dg_dmpf", "dg_nopf_u", "dg_nopf_dm", "dg_dmpf_u", "dg_dmpf_dm", "dg_res"):
+for _k in ("dg_nopf", "dg_dmpf", "dg_nopf_u", "dg_nopf_dm", "dg_dmpf_u", "dg_dmpf_dm", "dg_res",
+           "dg_upf", "dg_dmpft", "dg_upf_u", "dg_dmpft_u", "dg_dmpft_res"):
     KERNELS[_k] = (("Np", "Nel", "L0", "L1"), (2, 2))
-for _k in ("fd_tile", "fd_direct", "fd_tile_u", "fd_tile_res", "fd_direct_u", "fd_direct_res"):
+for _k in ("fd_tile", "fd_direct", "fd_tile_u", "fd_tile_res", "fd_direct_u", "fd_direct_res",
+           "fd_tile18", "fd_tile18_u", "fd_tile18_res"):
     KERNELS[_k] = (("n",), (2, 2))
 
 KERNELS["mm_simt"] = (("n", "BM", "BN", "BK"), (2, 2))

@@ -476,7 +476,12 @@ static int setup_mm(ctx *c, int v) {
  * lsize1), guard i < Np.  P = {Np, Nel, L0, L1}.
  * variants: 0 noPF, 1 dmPF (D tiles L1 x L0 prefetched to local memory,
  * j split by L0), 2 noPF-u twin, 3 noPF-dm twin, 4 dmPF-u twin,
- * 5 dmPF-dm twin, 6 res twin (store pattern only).
+ * 5 dmPF-dm twin, 6 res twin (store pattern only), 7 uPF (L0 == L1; j
+ * split by L1; per j tile the L0 x L1 tile of u is fetched to local memory,
+ * work-item (lid0, lid1) fetching u[k = L0 gid0 + lid1, j = L1 jo + lid0];
+ * loops j tile, j, m with three accumulators; the local value is read once
+ * per j), 8 dmPF-T (dmPF on the transposed layouts uT[j, k] and
+ * resT[m, i, k]), 9 uPF-u twin, 10 dmPF-T-u twin, 11 dmPF-T-res twin.
  * Twins without a kept store write tgt to tgt_dest[(L1 gid1 + lid1) * Nel + k]
  * (one entry per work-item, every work-item).
  * ====================================================================== */
@@ -507,6 +512,28 @@ static long long ix_dg_u_pf(const ctx *c, const long long *g, const long long *l
 }
 static long long ix_dg_dest(const ctx *c, const long long *g, const long long *l, const long long *lv) {
     (void)lv; return c->P[1] * DG_I(c, g, l) + DG_K(c, g, l);
+}
+/* uPF: lv = {jo, ji, m}; local tile uf[k_in][j_in] with row pitch L1 + 1 */
+static long long ix_dg_upf_fetch(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long Np = c->P[0], L0 = c->P[2], L1 = c->P[3];
+    return Np * (L0 * g[0] + l[1]) + L1 * lv[0] + l[0];
+}
+static long long ix_dg_uf_st(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; (void)lv; return (c->P[3] + 1) * l[1] + l[0];
+}
+static long long ix_dg_uf_ld(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; return (c->P[3] + 1) * l[0] + lv[1];
+}
+static long long ix_dg_upf_D(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long Np = c->P[0], L1 = c->P[3];
+    return Np * Np * lv[2] + Np * DG_I(c, g, l) + L1 * lv[0] + lv[1];
+}
+/* dmPF-T: lv = {m, jo, ji}; uT[j, k] = Nel j + k, resT[m, i, k] = Nel Np m + Nel i + k */
+static long long ix_dg_uT_pf(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long Nel = c->P[1], L0 = c->P[2]; return Nel * (L0 * lv[1] + lv[2]) + DG_K(c, g, l);
+}
+static long long ix_dg_resT(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long Np = c->P[0], Nel = c->P[1]; return Nel * Np * lv[0] + Nel * DG_I(c, g, l) + DG_K(c, g, l);
 }
 static void walk_dg(ctx *c) {
     long long Np = c->P[0], L0 = c->P[2], v = c->D[0], lv[3];
@@ -548,9 +575,51 @@ static void walk_dg(ctx *c) {
                 if (i < Np && L0 * lv[1] + c->l[0] < Np) X(c, 0, lv);
         X(c, 1, NULL);
         break;
-    case 6:
+    case 6: case 11:
         if (i < Np)
             for (lv[0] = 0; lv[0] < 3; lv[0]++) X(c, 0, lv);
+        break;
+    case 7: {
+        long long L1 = c->P[3], njl = cdiv(Np, L1);
+        for (lv[0] = 0; lv[0] < njl; lv[0]++) {
+            BAR(c);
+            if (L1 * lv[0] + c->l[0] < Np) X(c, 0, lv);
+            BAR(c);
+            if (i < Np)
+                for (lv[1] = 0; lv[1] < L1 && L1 * lv[0] + lv[1] < Np; lv[1]++) {
+                    X(c, 1, lv);
+                    for (lv[2] = 0; lv[2] < 3; lv[2]++) X(c, 2, lv);
+                }
+        }
+        if (i < Np)
+            for (lv[0] = 0; lv[0] < 3; lv[0]++) X(c, 3, lv);
+        break; }
+    case 8:
+        for (lv[0] = 0; lv[0] < 3; lv[0]++) {
+            for (lv[1] = 0; lv[1] < nj; lv[1]++) {
+                BAR(c);
+                if (i < Np && L0 * lv[1] + c->l[0] < Np) X(c, 0, lv);
+                BAR(c);
+                if (i < Np)
+                    for (lv[2] = 0; lv[2] < L0; lv[2]++)
+                        if (L0 * lv[1] + lv[2] < Np) X(c, 1, lv);
+            }
+            if (i < Np) X(c, 2, lv);
+        }
+        break;
+    case 9: {
+        long long L1 = c->P[3], njl = cdiv(Np, L1);
+        for (lv[0] = 0; lv[0] < njl; lv[0]++)
+            if (L1 * lv[0] + c->l[0] < Np) X(c, 0, lv);
+        X(c, 1, NULL);
+        break; }
+    case 10:
+        if (i < Np)
+            for (lv[0] = 0; lv[0] < 3; lv[0]++)
+                for (lv[1] = 0; lv[1] < nj; lv[1]++)
+                    for (lv[2] = 0; lv[2] < L0; lv[2]++)
+                        if (L0 * lv[1] + lv[2] < Np) X(c, 0, lv);
+        X(c, 1, NULL);
         break;
     }
 }
@@ -566,6 +635,10 @@ static int setup_dg(ctx *c, int v) {
     snprintf(t_pu, sizeof t_pu, "dg-dmPF-u-%dx%d", (int)L0, (int)L1);
     snprintf(t_pdm, sizeof t_pdm, "dg-dmPF-dm-%dx%d", (int)L0, (int)L1);
     snprintf(t_res, sizeof t_res, "dg-res-%dx%d", (int)L0, (int)L1);
+    char t_uu[48], t_tu[48], t_tres[48];
+    snprintf(t_uu, sizeof t_uu, "dg-uPF-u-%dx%d", (int)L0, (int)L1);
+    snprintf(t_tu, sizeof t_tu, "dg-dmPFT-u-%dx%d", (int)L0, (int)L1);
+    snprintf(t_tres, sizeof t_tres, "dg-dmPFT-res-%dx%d", (int)L0, (int)L1);
     switch (v) {
     case 0: {
         int s0 = add_stmt(c, 2, DT_F32, 0, 0, 1);
@@ -607,6 +680,45 @@ static int setup_dg(ctx *c, int v) {
         int s0 = add_stmt(c, 1, DT_F32, 0, 0, 0);
         stmt_site(c, s0, add_site(c, t_res, MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dg_res));
         break; }
+    case 7: {
+        if (L0 != L1) return -1;
+        int s0 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+        stmt_site(c, s0, add_site(c, t_uu, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dg_upf_fetch));
+        stmt_site(c, s0, add_site(c, "u_fetch_st", MEM_LOCAL, DIR_STORE, "float32", 4, ix_dg_uf_st));
+        int s1 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+        stmt_site(c, s1, add_site(c, "u_fetch_ld", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_dg_uf_ld));
+        int s2 = add_stmt(c, 3, DT_F32, 0, 0, 1);
+        stmt_site(c, s2, add_site(c, t_ndm, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dg_upf_D));
+        int s3 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+        stmt_site(c, s3, add_site(c, t_res, MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dg_res));
+        break; }
+    case 8: {
+        int s0 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+        stmt_site(c, s0, add_site(c, t_pdm, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dg_Dfetch));
+        stmt_site(c, s0, add_site(c, "dm_fetch_st", MEM_LOCAL, DIR_STORE, "float32", 4, ix_dg_Dt_st));
+        int s1 = add_stmt(c, 3, DT_F32, 0, 0, 1);
+        stmt_site(c, s1, add_site(c, "dm_fetch_ld", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_dg_Dt_ld));
+        stmt_site(c, s1, add_site(c, t_tu, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dg_uT_pf));
+        int s2 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+        stmt_site(c, s2, add_site(c, t_tres, MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dg_resT));
+        break; }
+    case 9: {
+        if (L0 != L1) return -1;
+        int s0 = add_stmt(c, 1, DT_F32, 1, 0, 0);
+        stmt_site(c, s0, add_site(c, t_uu, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dg_upf_fetch));
+        int s1 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+        stmt_site(c, s1, add_site(c, "tgt_dest", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dg_dest));
+        break; }
+    case 10: {
+        int s0 = add_stmt(c, 3, DT_F32, 1, 0, 0);
+        stmt_site(c, s0, add_site(c, t_tu, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dg_uT_pf));
+        int s1 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+        stmt_site(c, s1, add_site(c, "tgt_dest", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dg_dest));
+        break; }
+    case 11: {
+        int s0 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+        stmt_site(c, s0, add_site(c, t_tres, MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dg_resT));
+        break; }
     default: return -1;
     }
     c->walk = walk_dg;
@@ -620,33 +732,37 @@ static int setup_dg(ctx *c, int v) {
  * variants: 0 tile (16x16 work-group fetches a 16x16 tile of u to local
  * memory, the 14x14 interior computes, group stride 14), 1 direct (16x16
  * work-group, one output per work-item, five global loads), 2 tile-u twin,
- * 3 tile-res twin, 4 direct-u twin, 5 direct-res twin.
- * Twins without a kept store write to tgt_dest[(16 gid1 + lid1)*(16 G0) + 16 gid0 + lid0].
+ * 3 tile-res twin, 4 direct-u twin, 5 direct-res twin, 6 tile18 (18x18
+ * work-group fetches an 18x18 tile, the 16x16 interior computes, group
+ * stride 16), 7 tile18-u twin, 8 tile18-res twin.
+ * Twins without a kept store write to
+ * tgt_dest[(T gid1 + lid1)*(T G0) + T gid0 + lid0], T the work-group width.
  * ====================================================================== */
 #define FD_W(c) ((c)->P[0] + 2)
+#define FD_T(c) ((c)->D[1])            /* tile (work-group) width: 16 or 18 */
 static long long ix_fd_fetch(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)lv; return FD_W(c) * (14 * G1 + L1_) + 14 * G0 + L0_;
+    (void)lv; long long s = FD_T(c) - 2; return FD_W(c) * (s * G1 + L1_) + s * G0 + L0_;
 }
 static long long ix_fd_tile_st(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)c; (void)g; (void)lv; return 16 * L1_ + L0_;
+    (void)g; (void)lv; return FD_T(c) * L1_ + L0_;
 }
 static long long ix_fd_tC(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)c; (void)g; (void)lv; return 16 * L1_ + L0_;
+    (void)g; (void)lv; return FD_T(c) * L1_ + L0_;
 }
 static long long ix_fd_tN(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)c; (void)g; (void)lv; return 16 * (L1_ - 1) + L0_;
+    (void)g; (void)lv; return FD_T(c) * (L1_ - 1) + L0_;
 }
 static long long ix_fd_tS(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)c; (void)g; (void)lv; return 16 * (L1_ + 1) + L0_;
+    (void)g; (void)lv; return FD_T(c) * (L1_ + 1) + L0_;
 }
 static long long ix_fd_tW(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)c; (void)g; (void)lv; return 16 * L1_ + L0_ - 1;
+    (void)g; (void)lv; return FD_T(c) * L1_ + L0_ - 1;
 }
 static long long ix_fd_tE(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)c; (void)g; (void)lv; return 16 * L1_ + L0_ + 1;
+    (void)g; (void)lv; return FD_T(c) * L1_ + L0_ + 1;
 }
 static long long ix_fd_res_tile(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)lv; return c->P[0] * (14 * G1 + L1_ - 1) + 14 * G0 + L0_ - 1;
+    (void)lv; long long s = FD_T(c) - 2; return c->P[0] * (s * G1 + L1_ - 1) + s * G0 + L0_ - 1;
 }
 #define FD_DI(c, g, l) (16 * (g)[1] + (l)[1])
 #define FD_DJ(c, g, l) (16 * (g)[0] + (l)[0])
@@ -669,20 +785,20 @@ static long long ix_fd_res_direct(const ctx *c, const long long *g, const long l
     (void)lv; return c->P[0] * FD_DI(c, g, l) + FD_DJ(c, g, l);
 }
 static long long ix_fd_dest(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)lv; return 16 * c->grid[0] * (16 * G1 + L1_) + 16 * G0 + L0_;
+    (void)lv; long long T = c->wg[0]; return T * c->grid[0] * (T * G1 + L1_) + T * G0 + L0_;
 }
 static void walk_fd(ctx *c) {
     long long n = c->P[0], W = n + 2, v = c->D[0];
     const long long *g = c->g, *l = c->l;
-    if (v == 0 || v == 2 || v == 3) {
-        long long r = 14 * G1 + L1_, q = 14 * G0 + L0_;
+    if (v == 0 || v == 2 || v == 3 || v >= 6) {
+        long long s = FD_T(c) - 2, r = s * G1 + L1_, q = s * G0 + L0_;
         int fetch = r < W && q < W;
-        int comp = L0_ >= 1 && L0_ <= 14 && L1_ >= 1 && L1_ <= 14 && r - 1 < n && q - 1 < n;
-        if (v == 0) {
+        int comp = L0_ >= 1 && L0_ <= s && L1_ >= 1 && L1_ <= s && r - 1 < n && q - 1 < n;
+        if (v == 0 || v == 6) {
             if (fetch) X(c, 0, NULL);
             BAR(c);
             if (comp) X(c, 1, NULL);
-        } else if (v == 2) {
+        } else if (v == 2 || v == 7) {
             if (fetch) X(c, 0, NULL);
             X(c, 1, NULL);
         } else {
@@ -702,14 +818,16 @@ static int setup_fd(ctx *c, int v) {
     long long n = c->P[0];
     if (n < 1) return -1;
     c->D[0] = v;
-    c->wg[0] = 16; c->wg[1] = 16; c->wg[2] = 1;
-    if (v == 0 || v == 2 || v == 3) { c->grid[0] = cdiv(n, 14); c->grid[1] = cdiv(n, 14); }
+    c->D[1] = v >= 6 ? 18 : 16;
+    c->wg[0] = c->D[1]; c->wg[1] = c->D[1]; c->wg[2] = 1;
+    if (v == 0 || v == 2 || v == 3 || v >= 6) { c->grid[0] = cdiv(n, c->D[1] - 2); c->grid[1] = c->grid[0]; }
     else { c->grid[0] = cdiv(n, 16); c->grid[1] = cdiv(n, 16); }
     c->grid[2] = 1;
+    const char *t_u = v >= 6 ? "fd-tile18-u" : "fd-tile-u", *t_res = v >= 6 ? "fd-tile18-res" : "fd-tile-res";
     switch (v) {
-    case 0: {
+    case 0: case 6: {
         int s0 = add_stmt(c, 0, DT_F32, 0, 0, 0);
-        stmt_site(c, s0, add_site(c, "fd-tile-u", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_fd_fetch));
+        stmt_site(c, s0, add_site(c, t_u, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_fd_fetch));
         stmt_site(c, s0, add_site(c, "u_fetch_st", MEM_LOCAL, DIR_STORE, "float32", 4, ix_fd_tile_st));
         int s1 = add_stmt(c, 0, DT_F32, 3, 1, 1);
         stmt_site(c, s1, add_site(c, "u_fetch_c", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_fd_tC));
@@ -717,7 +835,7 @@ static int setup_fd(ctx *c, int v) {
         stmt_site(c, s1, add_site(c, "u_fetch_s", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_fd_tS));
         stmt_site(c, s1, add_site(c, "u_fetch_w", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_fd_tW));
         stmt_site(c, s1, add_site(c, "u_fetch_e", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_fd_tE));
-        stmt_site(c, s1, add_site(c, "fd-tile-res", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_fd_res_tile));
+        stmt_site(c, s1, add_site(c, t_res, MEM_GLOBAL, DIR_STORE, "float32", 4, ix_fd_res_tile));
         break; }
     case 1: {
         int s0 = add_stmt(c, 0, DT_F32, 3, 1, 1);
@@ -728,15 +846,15 @@ static int setup_fd(ctx *c, int v) {
         stmt_site(c, s0, add_site(c, "u_e", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_fd_uE));
         stmt_site(c, s0, add_site(c, "res", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_fd_res_direct));
         break; }
-    case 2: {
+    case 2: case 7: {
         int s0 = add_stmt(c, 0, DT_F32, 1, 0, 0);
-        stmt_site(c, s0, add_site(c, "fd-tile-u", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_fd_fetch));
+        stmt_site(c, s0, add_site(c, t_u, MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_fd_fetch));
         int s1 = add_stmt(c, 0, DT_F32, 0, 0, 0);
         stmt_site(c, s1, add_site(c, "tgt_dest", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_fd_dest));
         break; }
-    case 3: {
+    case 3: case 8: {
         int s0 = add_stmt(c, 0, DT_F32, 0, 0, 0);
-        stmt_site(c, s0, add_site(c, "fd-tile-res", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_fd_res_tile));
+        stmt_site(c, s0, add_site(c, t_res, MEM_GLOBAL, DIR_STORE, "float32", 4, ix_fd_res_tile));
         break; }
     case 4: {
         static const char *nm[5] = {"u_c", "u_n", "u_s", "u_w", "u_e"};
@@ -1007,7 +1125,8 @@ static const struct { const char *name; int fam, v; } KTAB[] = {
     {"dg_nopf", 7, 0}, {"dg_dmpf", 7, 1}, {"dg_nopf_u", 7, 2}, {"dg_nopf_dm", 7, 3}, {"dg_dmpf_u", 7, 4},
     {"dg_dmpf_dm", 7, 5}, {"dg_res", 7, 6},
     {"fd_tile", 8, 0}, {"fd_direct", 8, 1}, {"fd_tile_u", 8, 2}, {"fd_tile_res", 8, 3}, {"fd_direct_u", 8, 4},
-    {"fd_direct_res", 8, 5},
+    {"fd_direct_res", 8, 5}, {"fd_tile18", 8, 6}, {"fd_tile18_u", 8, 7}, {"fd_tile18_res", 8, 8},
+    {"dg_upf", 7, 7}, {"dg_dmpft", 7, 8}, {"dg_upf_u", 7, 9}, {"dg_dmpft_u", 7, 10}, {"dg_dmpft_res", 7, 11},
     {"mm_simt", 9, 0},
     {"mm_tc", 10, 0},
     {"fd_block", 11, 0},
@@ -1219,13 +1338,18 @@ void oracle_mm_twin_ref(int v, long long n, const float *x, float *dest) {
 
 void oracle_dg_twin_ref(int v, long long Np, long long Nel, long long L0, long long L1, const float *D,
                         const float *u, float *dest) {
-    /* v: 2 noPF-u, 3 noPF-dm, 4 dmPF-u, 5 dmPF-dm; dest rows = ceil(Np/L1)*L1, cols = Nel */
-    long long rows = cdiv(Np, L1) * L1, nj = cdiv(Np, L0);
+    /* v: 2 noPF-u, 3 noPF-dm, 4 dmPF-u, 5 dmPF-dm, 9 uPF-u, 10 dmPF-T-u (u given
+     * as uT[j, k]); dest rows = ceil(Np/L1)*L1, cols = Nel */
+    long long rows = cdiv(Np, L1) * L1, nj = cdiv(Np, L0), njl = cdiv(Np, L1);
     for (long long i = 0; i < rows; i++)
         for (long long k = 0; k < Nel; k++) {
             float t = 0.0f;
             long long l0 = k % L0;
+            if (v == 9)   /* every work-item fetches, whatever its row i */
+                for (long long jo = 0; jo < njl; jo++)
+                    if (L1 * jo + l0 < Np) t = t + u[Np * (L0 * (k / L0) + i % L1) + L1 * jo + l0];
             if (i < Np) for (long long m = 0; m < 3; m++) {
+                if (v == 10) for (long long j = 0; j < Np; j++) t = t + u[Nel * j + k];
                 if (v == 2 || v == 4) for (long long j = 0; j < Np; j++) t = t + u[Np * k + j];
                 if (v == 3) for (long long j = 0; j < Np; j++) t = t + D[Np * Np * m + Np * i + j];
                 if (v == 5) for (long long jo = 0; jo < nj; jo++)
@@ -1237,16 +1361,17 @@ void oracle_dg_twin_ref(int v, long long Np, long long Nel, long long L0, long l
 
 void oracle_fd_twin_ref(int v, long long n, const float *u, float *dest) {
     /* v: 2 tile-u (dest is (16*G1) x (16*G0), G = ceil(n/14)),
+     *    7 tile18-u (dest is (18*G1) x (18*G0), G = ceil(n/16)),
      *    4 direct-u (dest is (16*G1) x (16*G0), G = ceil(n/16)) */
     long long W = n + 2;
-    if (v == 2) {
-        long long G = cdiv(n, 14), cols = 16 * G;
+    if (v == 2 || v == 7) {
+        long long T = v == 2 ? 16 : 18, G = cdiv(n, T - 2), cols = T * G;
         for (long long gi = 0; gi < G; gi++) for (long long gj = 0; gj < G; gj++)
-        for (long long l1 = 0; l1 < 16; l1++) for (long long l0 = 0; l0 < 16; l0++) {
-            long long r = 14 * gi + l1, q = 14 * gj + l0;
+        for (long long l1 = 0; l1 < T; l1++) for (long long l0 = 0; l0 < T; l0++) {
+            long long r = (T - 2) * gi + l1, q = (T - 2) * gj + l0;
             float t = 0.0f;
             if (r < W && q < W) t = t + u[W * r + q];
-            dest[cols * (16 * gi + l1) + 16 * gj + l0] = t;
+            dest[cols * (T * gi + l1) + T * gj + l0] = t;
         }
     } else {
         long long G = cdiv(n, 16), cols = 16 * G;

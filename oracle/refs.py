@@ -104,8 +104,8 @@ def stencil_rows(u, c0, c1):
 
 
 _MM_V = {"mm_pf_a": 2, "mm_pf_b": 3, "mm_nopf_a": 4, "mm_nopf_b": 5}
-_DG_V = {"dg_nopf_u": 2, "dg_nopf_dm": 3, "dg_dmpf_u": 4, "dg_dmpf_dm": 5}
-_FD_V = {"fd_tile_u": 2, "fd_direct_u": 4}
+_DG_V = {"dg_nopf_u": 2, "dg_nopf_dm": 3, "dg_dmpf_u": 4, "dg_dmpf_dm": 5, "dg_upf_u": 9, "dg_dmpft_u": 10}
+_FD_V = {"fd_tile_u": 2, "fd_direct_u": 4, "fd_tile18_u": 7}
 
 
 def mm_twin(kernel, x):
@@ -117,8 +117,10 @@ def mm_twin(kernel, x):
 
 
 def dg_twin(kernel, D, u, L0, L1):
+    """Twin output in the kernel's own layout (dg_dmpft_u reads u as uT[j, k])."""
     _setup()
-    Np, Nel = D.shape[1], u.shape[0]
+    Np = D.shape[1]
+    Nel = u.shape[1] if kernel == "dg_dmpft_u" else u.shape[0]
     rows = -(-Np // L1) * L1
     dest = np.empty((rows, Nel), np.float32)
     lib().oracle_dg_twin_ref(_DG_V[kernel], Np, Nel, L0, L1, np.ascontiguousarray(D, np.float32),
@@ -130,6 +132,7 @@ def fd_twin(kernel, u):
     _setup()
     n = u.shape[0] - 2
     G = -(-n // (14 if kernel == "fd_tile_u" else 16))
-    dest = np.empty((16 * G, 16 * G), np.float32)
+    T = 18 if kernel == "fd_tile18_u" else 16
+    dest = np.empty((T * G, T * G), np.float32)
     lib().oracle_fd_twin_ref(_FD_V[kernel], n, np.ascontiguousarray(u, np.float32), dest)
     return dest

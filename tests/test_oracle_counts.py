@@ -162,6 +162,73 @@ def test_dg_closed_forms(Np, Nel, L0, L1):
         assert single(fs, "groups") == (Nel // L0) * (-(-Np // L1))
 
 
+@pytest.mark.parametrize("Np,Nel,L0,L1", [(20, 64, 16, 16), (35, 32, 16, 16), (84, 32, 16, 16), (7, 16, 16, 16)])
+def test_dg_upf_closed_forms(Np, Nel, L0, L1):
+    # uPF (Section "DG"): j split by lsize1, u tile prefetched per j tile,
+    # loops j tile -> j -> m with one accumulator per m
+    fs = features("dg_upf", Np=Np, Nel=Nel, L0=L0, L1=L1)
+    G1 = -(-Np // L1)
+    assert op(fs, "float32", "madd", wi=True) == 3 * Nel * Np * Np
+    u = by_tag(fs, "dg-uPF-u-16x16")
+    # every u element fetched once per i-group, lid(0) runs along j (stride 1)
+    assert u["count_wi"] == G1 * Nel * Np and u["footprint"] == Nel * Np
+    assert u["lstr"] == (1, Np) and u["gstr"] == (L0 * Np, 0) and u["loopstr"] == L1
+    d = by_tag(fs, "dg-noPF-dm-16x16")     # same pattern as noPF's D, shared twin
+    assert d["lstr"][0] == 0 and d["gran"] == "SG" and d["count_wi"] == 3 * Nel * Np * Np
+    assert d["loopstr"] == Np * Np           # m innermost
+    loc = {f["tag"]: f for f in fs if f["kind"] == "mem" and f["mem"] == "local"}
+    assert loc["u_fetch_st"]["count_wi"] == u["count_wi"]
+    assert loc["u_fetch_ld"]["count_wi"] == Nel * Np * Np      # read once per (k, i, j)
+    res = by_tag(fs, "dg-res-16x16")
+    assert res["count"] == res["footprint"] == 3 * Nel * Np
+    assert single(fs, "sync") == 2 * G1
+    with pytest.raises(Exception):
+        features("dg_upf", Np=Np, Nel=64, L0=32, L1=8)
+
+
+@pytest.mark.parametrize("Np,Nel,L0,L1", [(20, 64, 16, 16), (35, 64, 32, 8), (56, 32, 16, 16)])
+def test_dg_dmpft_closed_forms(Np, Nel, L0, L1):
+    # dmPF-T: dmPF on transposed u and res, lid(0) stride 1 for both
+    sh = "%dx%d" % (L0, L1)
+    t = features("dg_dmpft", Np=Np, Nel=Nel, L0=L0, L1=L1)
+    d = features("dg_dmpf", Np=Np, Nel=Nel, L0=L0, L1=L1)
+    assert op(t, "float32", "madd", wi=True) == op(d, "float32", "madd", wi=True) == 3 * Nel * Np * Np
+    u = by_tag(t, "dg-dmPFT-u-" + sh)
+    assert u["lstr"] == (1, 0) and u["gstr"] == (L0, 0) and u["loopstr"] == Nel
+    assert u["count_wi"] == 3 * Nel * Np * Np and u["footprint"] == Nel * Np
+    r = by_tag(t, "dg-dmPFT-res-" + sh)
+    assert r["lstr"] == (1, Nel) and r["count"] == r["footprint"] == 3 * Nel * Np
+    for tag in ("dg-dmPF-dm-" + sh,):
+        a, b = by_tag(t, tag), by_tag(d, tag)
+        assert (a["count"], a["lstr"], a["gstr"], a["footprint"]) == (b["count"], b["lstr"], b["gstr"], b["footprint"])
+    assert single(t, "sync") == single(d, "sync")
+
+
+@pytest.mark.parametrize("n", [16, 20, 33, 48])
+def test_fd_tile18_closed_forms(n):
+    # 18x18 work-groups fetch 18x18 tiles, the 16x16 interior computes:
+    # gid(0) stride 16 (Section "Finite Differences")
+    W = n + 2
+    t = features("fd_tile18", n=n)
+    assert op(t, "float32", "madd", wi=True) == n * n
+    assert op(t, "float32", "add", wi=True) == 3 * n * n
+    u = by_tag(t, "fd-tile18-u")
+    assert u["footprint"] == W * W and u["lstr"] == (1, W) and u["gstr"] == (16, 16 * W)
+    G = -(-n // 16)
+    per_axis = sum(min(18, W - 16 * g) for g in range(G))
+    assert u["count"] == per_axis * per_axis
+    if n % 16 == 0:
+        assert u["count"] == 324 * G * G          # one fetch per thread of every group
+    r = by_tag(t, "fd-tile18-res")
+    assert r["count"] == r["footprint"] == n * n and r["gstr"] == (16, 16 * n)
+    loc = [f for f in t if f["kind"] == "mem" and f["mem"] == "local"]
+    assert sum(f["count_wi"] for f in loc if f["dir"] == "load") == 5 * n * n
+    assert single(t, "sync") == 1 and single(t, "groups") == G * G
+    # 18x18 = 324 threads: 10 full sub-groups and one of 4 lanes per group
+    if n % 16 == 0:
+        assert by_tag(t, "u_fetch_st")["count"] == 11 * G * G
+
+
 @pytest.mark.parametrize("n", [14, 20, 33, 48])
 def test_fd_closed_forms(n):
     W = n + 2

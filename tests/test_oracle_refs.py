@@ -117,7 +117,22 @@ def test_dg_twin_ones(kernel, Np, L0, L1):
     assert np.all(dest[Np:] == 0)
 
 
-@pytest.mark.parametrize("kernel", ["fd_tile_u", "fd_direct_u"])
+@pytest.mark.parametrize("kernel", ["dg_upf_u", "dg_dmpft_u"])
+@pytest.mark.parametrize("Np", [20, 35])
+def test_dg_new_twin_ones(kernel, Np):
+    Nel, L0, L1 = 64, 16, 16
+    D = np.ones((3, Np, Np), np.float32)
+    u = np.ones((Np, Nel) if kernel == "dg_dmpft_u" else (Nel, Np), np.float32)
+    dest = refs.dg_twin(kernel, D, u, L0, L1)
+    assert dest.sum() == _loads_per_wi(kernel, Np=Np, Nel=Nel, L0=L0, L1=L1)
+    if kernel == "dg_upf_u":     # the u fetch is not guarded by the row i
+        l0 = np.arange(Nel) % L0
+        assert np.all(dest == (-(-(Np - l0) // L1))[None, :])   # j tiles in which lane l0 fetches
+    else:
+        assert np.all(dest[:Np] == 3 * Np) and np.all(dest[Np:] == 0)
+
+
+@pytest.mark.parametrize("kernel", ["fd_tile_u", "fd_direct_u", "fd_tile18_u"])
 def test_fd_twin_ones(kernel):
     n = 37
     dest = refs.fd_twin(kernel, np.ones((n + 2, n + 2), np.float32))
