@@ -54,10 +54,14 @@ typedef struct {
  * "barrier", "overlap", "empty" (Section "Measurement Kernel Design");
  * matmul "mm_pf", "mm_nopf" and the work-removed twins "mm_pf_a", "mm_pf_b",
  * "mm_nopf_a", "mm_nopf_b" (Section "Matrix Multiplication", Algorithm 3);
- * DG "dg_nopf", "dg_dmpf" and twins "dg_nopf_u", "dg_nopf_dm", "dg_dmpf_u",
- * "dg_dmpf_dm", "dg_res" (Section "DG"); stencil "fd_tile", "fd_direct" and
- * twins "fd_tile_u", "fd_tile_res", "fd_direct_u", "fd_direct_res"
- * (Section "Finite Differences"); autotuning spaces (the paper's use case
+ * DG "dg_nopf", "dg_upf", "dg_dmpf", "dg_dmpft" and twins "dg_nopf_u",
+ * "dg_nopf_dm", "dg_dmpf_u", "dg_dmpf_dm", "dg_res", "dg_upf_u", "dg_dmpft_u",
+ * "dg_dmpft_res" (Section "DG"; dg_upf needs L0 == L1; dg_dmpft and its twins
+ * read u as uT[j, k] (Np x Nel) and write res as resT[m, i, k]); stencil
+ * "fd_tile" (16x16 work-group, 14x14 interior), "fd_tile18" (18x18
+ * work-group, 16x16 interior), "fd_direct" and twins "fd_tile_u",
+ * "fd_tile_res", "fd_tile18_u", "fd_tile18_res", "fd_direct_u",
+ * "fd_direct_res" (Section "Finite Differences"); autotuning spaces (the paper's use case
  * of ranking equivalent variants, Section "Assumptions and Limitations"):
  * "mm_simt" (register-tiled fp32 matmul, parameters n, BM, BN, BK); the
  * added BF16 tensor-core matmul "mm_tc" (C = A Bt^T, bf16 in, fp32 out,

@@ -65,6 +65,14 @@ static const KernelDef KDEFS[] = {
     {"mm_simt", FAM_SIMT, 0, P_SIMT},
     {"mm_tc", FAM_TC, 0, P_MM},
     {"fd_block", FAM_FDB, 0, P_FDB},
+    {"fd_tile18", FAM_FD, 6, P_FD},
+    {"fd_tile18_u", FAM_FD, 7, P_FD},
+    {"fd_tile18_res", FAM_FD, 8, P_FD},
+    {"dg_upf", FAM_DG, 7, P_DG},
+    {"dg_dmpft", FAM_DG, 8, P_DG},
+    {"dg_upf_u", FAM_DG, 9, P_DG},
+    {"dg_dmpft_u", FAM_DG, 10, P_DG},
+    {"dg_dmpft_res", FAM_DG, 11, P_DG},
 };
 
 const KernelDef *kernel_def(int32_t id) {

@@ -271,7 +271,10 @@ pm_status counts_dg(const KP &kp, std::vector<pm_feature> &v) {
     u64 WIa = (u64)(Nel * Np);                   // active work-items
     u64 Np2 = (u64)(Np * Np);
     u64 WIall = (u64)(G0 * G1 * L0 * L1), SGall = (u64)(G0 * G1 * (L0 * L1 / 32));
-    char t_nu[32], t_ndm[32], t_pu[32], t_pdm[32], t_res[32];
+    char t_nu[32], t_ndm[32], t_pu[32], t_pdm[32], t_res[32], t_uu[32], t_tu[32], t_tres[32];
+    snprintf(t_uu, sizeof t_uu, "dg-uPF-u-%dx%d", (int)L0, (int)L1);
+    snprintf(t_tu, sizeof t_tu, "dg-dmPFT-u-%dx%d", (int)L0, (int)L1);
+    snprintf(t_tres, sizeof t_tres, "dg-dmPFT-res-%dx%d", (int)L0, (int)L1);
     snprintf(t_nu, sizeof t_nu, "dg-noPF-u-%dx%d", (int)L0, (int)L1);
     snprintf(t_ndm, sizeof t_ndm, "dg-noPF-dm-%dx%d", (int)L0, (int)L1);
     snprintf(t_pu, sizeof t_pu, "dg-dmPF-u-%dx%d", (int)L0, (int)L1);
@@ -345,6 +348,50 @@ pm_status counts_dg(const KP &kp, std::vector<pm_feature> &v) {
         res_site();
         o.finish(0, (u64)(G0 * G1));
         break;
+    case 7: case 9: {
+        // uPF (L0 == L1): per j tile every work-item (any row) with
+        // L1 jo + lid0 < Np fetches u[Np (L0 gid0 + lid1) + L1 jo + lid0];
+        // summed over the tiles that is L1 Np per group, and every sub-group
+        // has an active lane (lid0 = 0) in every tile.
+        i64 njl = cdiv(Np, L1);
+        u64 uWI = (u64)(G0 * G1 * L1 * Np), uSG = (u64)(G0 * G1 * (L0 * L1 / 32) * njl);
+        u64 ufoot = (u64)(L0 * std::min(L1, Np));
+        if (var == 7) {
+            o.op(0, 2, WIa * inner, SGa * inner);
+            site(t_uu, GL, LD, 1, Np, L0 * Np, 0, L1, uWI, uSG, (u64)(Nel * Np));
+            site("u_fetch_st", LO, ST, 1, L1 + 1, 0, 0, 0, uWI, uSG, ufoot);
+            site("u_fetch_ld", LO, LD, L1 + 1, 0, 0, 0, 1, WIa * (u64)Np, SGa * (u64)Np, ufoot);
+            site(t_ndm, GL, LD, 0, Np, 0, L1 * Np, Np * Np, WIa * inner, SGa * inner, 3 * Np2);
+            res_site();
+            o.finish(2 * (u64)njl, (u64)(G0 * G1));
+        } else {
+            o.op(0, 0, uWI, uSG);
+            site(t_uu, GL, LD, 1, Np, L0 * Np, 0, L1, uWI, uSG, (u64)(Nel * Np));
+            dest_site();
+            o.finish(0, (u64)(G0 * G1));
+        }
+        break;
+    }
+    case 8:
+        // dmPF-T: dmPF on uT[j, k] = Nel j + k and resT[m, i, k] = Nel Np m + Nel i + k
+        o.op(0, 2, WIa * inner, SGa * inner);
+        site(t_pdm, GL, LD, 1, Np, 0, L1 * Np, L0, fWI, fSG, 3 * Np2);
+        site("dm_fetch_st", LO, ST, 1, L0, 0, 0, 0, fWI, fSG, tileFoot);
+        site("dm_fetch_ld", LO, LD, 0, L0, 0, 0, 1, WIa * inner, SGa * inner, tileFoot);
+        site(t_tu, GL, LD, 1, 0, L0, 0, Nel, WIa * inner, SGa * inner, (u64)(Nel * Np));
+        site(t_tres, GL, ST, 1, Nel, L0, L1 * Nel, Nel * Np, WIa * 3, SGa * 3, (u64)(3 * Nel * Np));
+        o.finish(6 * (u64)nj, (u64)(G0 * G1));
+        break;
+    case 10:
+        o.op(0, 0, WIa * inner, SGa * inner);
+        site(t_tu, GL, LD, 1, 0, L0, 0, Nel, WIa * inner, SGa * inner, (u64)(Nel * Np));
+        dest_site();
+        o.finish(0, (u64)(G0 * G1));
+        break;
+    case 11:
+        site(t_tres, GL, ST, 1, Nel, L0, L1 * Nel, Nel * Np, WIa * 3, SGa * 3, (u64)(3 * Nel * Np));
+        o.finish(0, (u64)(G0 * G1));
+        break;
     }
     return PM_OK;
 }
@@ -362,7 +409,61 @@ pm_status counts_fd(const KP &kp, std::vector<pm_feature> &v) {
         o.site(s);
     };
     u64 N2 = (u64)(n * n);
-    if (var == 0 || var == 2 || var == 3) {
+    if (var >= 6) {
+        // 18x18 work-group (tid = lid0 + 18 lid1), tile origin 16 gid; the
+        // active lanes of a statement form a rectangle per group, whose extent
+        // depends only on whether the group is the last one along each axis.
+        const i64 T = 18, S = 16, G = cdiv(n, S);
+        auto sg_rect = [&](i64 x0, i64 x1, i64 y0, i64 y1) {
+            u64 c = 0;
+            for (i64 q = 0; q * 32 < T * T; q++) {
+                bool any = false;
+                for (i64 t = 32 * q; t < std::min(32 * q + 32, T * T) && !any; t++)
+                    any = t % T >= x0 && t % T < x1 && t / T >= y0 && t / T < y1;
+                c += any;
+            }
+            return c;
+        };
+        // per-axis extents: fetch rows min(T, W - S g), computing rows min(S, n - S g)
+        i64 fe[2] = {std::min(T, W), std::min(T, W - S * (G - 1))};
+        i64 ce[2] = {std::min(S, n), std::min(S, n - S * (G - 1))};
+        u64 cnt[2] = {(u64)(G - 1), 1};   // groups 0..G-2 are full, group G-1 is the last
+        u64 fWI = 0, fSG = 0, cSG = 0;
+        for (int a = 0; a < 2; a++)
+            for (int b = 0; b < 2; b++) {
+                u64 m = cnt[a] * cnt[b];
+                if (!m) continue;
+                fWI += m * (u64)(fe[a] * fe[b]);
+                fSG += m * sg_rect(0, fe[a], 0, fe[b]);
+                cSG += m * sg_rect(1, 1 + ce[a], 1, 1 + ce[b]);
+            }
+        if (G == 1) {   // the only group is the last one: recount without the "full" class
+            fWI = (u64)(fe[1] * fe[1]);
+            fSG = sg_rect(0, fe[1], 0, fe[1]);
+            cSG = sg_rect(1, 1 + ce[1], 1, 1 + ce[1]);
+        }
+        u64 tf = (u64)(std::min(T, W) * std::min(T, W)), cf = (u64)(std::min(S, n) * std::min(S, n));
+        if (var == 6) {
+            o.op(0, 0, 3 * N2, 3 * cSG);
+            o.op(0, 1, N2, cSG);
+            o.op(0, 2, N2, cSG);
+            site("fd-tile18-u", GL, LD, 1, W, S, S * W, fWI, fSG, (u64)(W * W));
+            site("u_fetch_st", LO, ST, 1, T, 0, 0, fWI, fSG, tf);
+            static const char *nm[5] = {"u_fetch_c", "u_fetch_n", "u_fetch_s", "u_fetch_w", "u_fetch_e"};
+            for (int k = 0; k < 5; k++) site(nm[k], LO, LD, 1, T, 0, 0, N2, cSG, cf);
+            site("fd-tile18-res", GL, ST, 1, n, S, S * n, N2, cSG, N2);
+            o.finish(1, (u64)(G * G));
+        } else if (var == 7) {
+            o.op(0, 0, fWI, fSG);
+            site("fd-tile18-u", GL, LD, 1, W, S, S * W, fWI, fSG, (u64)(W * W));
+            u64 all = (u64)(T * T * G * G), allSG = (u64)(cdiv(T * T, 32) * G * G);
+            site("tgt_dest", GL, ST, 1, T * G, T, T * T * G, all, allSG, all);
+            o.finish(0, (u64)(G * G));
+        } else {
+            site("fd-tile18-res", GL, ST, 1, n, S, S * n, N2, cSG, N2);
+            o.finish(0, (u64)(G * G));
+        }
+    } else if (var == 0 || var == 2 || var == 3) {
         // 16x16 work-group, tile origin 14*gid; a sub-group is rows {2q, 2q+1}.
         i64 G = cdiv(n, 14);
         u64 S = 0, Qf = 0, Qc = 0;
@@ -587,6 +688,8 @@ pm_status validate(const KP &kp) {
         if (Np < 1 || Np > 512) return fail(PM_EINVAL, "%s: Np must be 1..512", nm);
         if (Nel < L0 || Nel % L0 || Nel > (1LL << 24))
             return fail(PM_EINVAL, "%s: Nel must be a positive multiple of L0 (<= 2^24)", nm);
+        if ((kp.def->variant == 7 || kp.def->variant == 9) && L0 != L1)
+            return fail(PM_EINVAL, "%s: the u-prefetch variant needs a square work-group (16, 16)", nm);
         return PM_OK;
     }
     case FAM_FD:
@@ -681,11 +784,11 @@ pm_status buffers(const KP &kp, std::vector<BufSpec> &b) {
     case FAM_DG: {
         uint64_t Np = (uint64_t)kp.i(0), Nel = (uint64_t)kp.i(1), L1 = (uint64_t)kp.i(3);
         uint64_t rows = (uint64_t)cdiv((i64)Np, (i64)L1) * L1;
-        if (var <= 1) {
+        if (var <= 1 || var == 7 || var == 8) {   // dmPF-T: u as uT[j, k], res as resT[m, i, k]
             b.push_back({"diff_mat", PM_F32, PM_IN, 3 * Np * Np});
             b.push_back({"u", PM_F32, PM_IN, Nel * Np});
             b.push_back({"res", PM_F32, PM_OUT, 3 * Nel * Np});
-        } else if (var == 2 || var == 4) {
+        } else if (var == 2 || var == 4 || var == 9 || var == 10) {
             b.push_back({"u", PM_F32, PM_IN, Nel * Np});
             b.push_back({"tgt_dest", PM_F32, PM_OUT, rows * Nel});
         } else if (var == 3 || var == 5) {
@@ -719,13 +822,13 @@ pm_status buffers(const KP &kp, std::vector<BufSpec> &b) {
     case FAM_FD: {
         uint64_t n = (uint64_t)kp.i(0), W = n + 2;
         uint64_t Gt = (uint64_t)cdiv((i64)n, 14), Gd = (uint64_t)cdiv((i64)n, 16);
-        if (var == 0 || var == 1) {
+        if (var == 0 || var == 1 || var == 6) {
             b.push_back({"u", PM_F32, PM_IN, W * W});
             b.push_back({"res", PM_F32, PM_OUT, n * n});
-        } else if (var == 2 || var == 4) {
-            uint64_t G = var == 2 ? Gt : Gd;
+        } else if (var == 2 || var == 4 || var == 7) {
+            uint64_t G = var == 2 ? Gt : Gd, T = var == 7 ? 18 : 16;
             b.push_back({"u", PM_F32, PM_IN, W * W});
-            b.push_back({"tgt_dest", PM_F32, PM_OUT, 256 * G * G});
+            b.push_back({"tgt_dest", PM_F32, PM_OUT, T * T * G * G});
         } else {
             b.push_back({"res", PM_F32, PM_OUT, n * n});
         }

@@ -13,10 +13,18 @@
 //       noPF: j loop over global memory.
 //       dmPF: j split by L0; per (m, j tile) the L1 x L0 tile of D is staged
 //             in shared memory between two barriers.
+//       uPF (square work-groups): j split by L1; per j tile the L0 x L1
+//             tile of u is staged in shared memory (work-item (lid0, lid1)
+//             fetches u[L0 gid0 + lid1, L1 jo + lid0], lid0 along j), loops
+//             j tile -> j -> m with three accumulators.
+//       dmPF-T: dmPF on the transposed layouts uT[j, k] and resT[m, i, k],
+//             so lid0 (k) has stride 1 in both.
 //   stencil (Section "Finite Differences"):
 //     res[i,j] = c0 u[i+1,j+1] + c1 (u[i,j+1] + u[i+2,j+1] + u[i+1,j] + u[i+1,j+2]).
 //       tile:   16x16 work-group stages a 16x16 tile (origin 14 gid) in shared
 //               memory; the 14x14 interior computes.
+//       tile18: 18x18 work-group stages an 18x18 tile (origin 16 gid); the
+//               16x16 interior computes.
 //       direct: 16x16 work-group, one output per work-item, 5 global loads.
 //   Twins keep the loop nest and the kept global accesses, replace arithmetic
 //   by tgt = tgt + load, keep the stores (writing tgt), and otherwise write tgt
@@ -137,7 +145,71 @@ __global__ void __launch_bounds__(L0 *L1) k_dg_dmpf(const float *__restrict__ D,
     }
 }
 
-// variant: 2 noPF-u, 3 noPF-dm, 4 dmPF-u, 5 dmPF-dm, 6 res
+template <int L>
+__global__ void __launch_bounds__(L *L) k_dg_upf(const float *__restrict__ D, const float *__restrict__ u,
+                                                float *__restrict__ res, int Np, int Nel) {
+    __shared__ float uf[L][L + 1];   // uf[k_in][j_in]
+    const int l0 = threadIdx.x, l1 = threadIdx.y;
+    const int k = L * blockIdx.x + l0, i = L * blockIdx.y + l1;
+    const int nj = (Np + L - 1) / L;
+    const size_t NN = (size_t)Np * Np;
+    const float *urow = u + (size_t)Np * (L * blockIdx.x + l1);
+    const float *Di = D + (size_t)Np * i;
+    float a0 = 0.0f, a1 = 0.0f, a2 = 0.0f;
+    for (int jo = 0; jo < nj; jo++) {
+        __syncthreads();
+        if (L * jo + l0 < Np) uf[l1][l0] = urow[L * jo + l0];
+        __syncthreads();
+        if (i < Np) {
+            const int jn = min(L, Np - L * jo);
+            for (int ji = 0; ji < jn; ji++) {
+                const float x = uf[l0][ji];
+                const int j = L * jo + ji;
+                a0 = __fmaf_rn(Di[j], x, a0);
+                a1 = __fmaf_rn(Di[NN + j], x, a1);
+                a2 = __fmaf_rn(Di[2 * NN + j], x, a2);
+            }
+        }
+    }
+    if (i < Np) {
+        const size_t o = (size_t)Np * k + i, M = (size_t)Nel * Np;
+        res[o] = a0;
+        res[M + o] = a1;
+        res[2 * M + o] = a2;
+    }
+}
+
+template <int L0, int L1>
+__global__ void __launch_bounds__(L0 *L1) k_dg_dmpft(const float *__restrict__ D, const float *__restrict__ uT,
+                                                     float *__restrict__ resT, int Np, int Nel) {
+    __shared__ float Dt[L1 * L0];
+    const int l0 = threadIdx.x, l1 = threadIdx.y;
+    const int k = L0 * blockIdx.x + l0, i = L1 * blockIdx.y + l1;
+    const int nj = (Np + L0 - 1) / L0;
+    const float *uk = uT + k;
+    for (int m = 0; m < 3; m++) {
+        float acc = 0.0f;
+        for (int jo = 0; jo < nj; jo++) {
+            __syncthreads();
+            if (i < Np && L0 * jo + l0 < Np) Dt[L0 * l1 + l0] = D[(size_t)Np * Np * m + (size_t)Np * i + L0 * jo + l0];
+            __syncthreads();
+            if (i < Np) {
+                const int jn = min(L0, Np - L0 * jo);
+                const float *uj = uk + (size_t)Nel * L0 * jo;
+                if (jn == L0) {
+#pragma unroll
+                    for (int ji = 0; ji < L0; ji++) acc = __fmaf_rn(Dt[L0 * l1 + ji], uj[(size_t)Nel * ji], acc);
+                } else {
+                    for (int ji = 0; ji < jn; ji++) acc = __fmaf_rn(Dt[L0 * l1 + ji], uj[(size_t)Nel * ji], acc);
+                }
+            }
+        }
+        if (i < Np) resT[(size_t)Nel * Np * m + (size_t)Nel * i + k] = acc;
+    }
+}
+
+// variant: 2 noPF-u, 3 noPF-dm, 4 dmPF-u, 5 dmPF-dm, 6 res, 9 uPF-u,
+// 10 dmPF-T-u (reads uT), 11 dmPF-T-res (writes resT)
 template <int L0, int L1, int V>
 __global__ void __launch_bounds__(L0 *L1) k_dg_twin(const float *__restrict__ D, const float *__restrict__ u,
                                                     float *__restrict__ out, int Np, int Nel) {
@@ -149,6 +221,24 @@ __global__ void __launch_bounds__(L0 *L1) k_dg_twin(const float *__restrict__ D,
         if (i < Np)
             for (int m = 0; m < 3; m++) out[(size_t)Nel * Np * m + (size_t)Np * k + i] = t;
         return;
+    }
+    if (V == 11) {
+        if (i < Np)
+            for (int m = 0; m < 3; m++) out[(size_t)Nel * Np * m + (size_t)Nel * i + k] = t;
+        return;
+    }
+    if (V == 9) {   // every work-item fetches, whatever its row
+        const float *urow = u + (size_t)Np * (L0 * blockIdx.x + l1);
+        const int njl = (Np + L1 - 1) / L1;
+        for (int jo = 0; jo < njl; jo++)
+            if (L1 * jo + l0 < Np) t = __fadd_rn(t, urow[L1 * jo + l0]);
+    }
+    if (V == 10) {
+        if (i < Np)
+            for (int m = 0; m < 3; m++)
+                for (int jo = 0; jo < nj; jo++)
+                    for (int ji = 0; ji < L0; ji++)
+                        if (L0 * jo + ji < Np) t = __fadd_rn(t, u[(size_t)Nel * (L0 * jo + ji) + k]);
     }
     if (V == 2 || V == 4) {
         if (i < Np)
@@ -187,8 +277,23 @@ pm_status launch_dg_t(int var, void *const *b, int Np, int Nel, cudaStream_t st)
         if (var == 3) k_dg_twin<L0, L1, 3><<<grid, blk, 0, st>>>(D, u, o, Np, Nel);
         else k_dg_twin<L0, L1, 5><<<grid, blk, 0, st>>>(D, u, o, Np, Nel);
         break;
-    default:
+    case 6:
         k_dg_twin<L0, L1, 6><<<grid, blk, 0, st>>>(D, u, (float *)b[0], Np, Nel);
+        break;
+    case 7:
+        if constexpr (L0 == L1)
+            k_dg_upf<L0><<<grid, blk, 0, st>>>((const float *)b[0], (const float *)b[1], (float *)b[2], Np, Nel);
+        else
+            return fail(PM_EINVAL, "dg_upf needs a square work-group");
+        break;
+    case 8: k_dg_dmpft<L0, L1><<<grid, blk, 0, st>>>((const float *)b[0], (const float *)b[1], (float *)b[2], Np, Nel); break;
+    case 9: case 10:
+        u = (const float *)b[0]; o = (float *)b[1];
+        if (var == 9) k_dg_twin<L0, L1, 9><<<grid, blk, 0, st>>>(D, u, o, Np, Nel);
+        else k_dg_twin<L0, L1, 10><<<grid, blk, 0, st>>>(D, u, o, Np, Nel);
+        break;
+    default:
+        k_dg_twin<L0, L1, 11><<<grid, blk, 0, st>>>(D, u, (float *)b[0], Np, Nel);
     }
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
@@ -207,15 +312,17 @@ __device__ __forceinline__ float fd_combine(float c0, float c1, float C, float N
     return __fmaf_rn(c0, C, __fmul_rn(c1, s));
 }
 
-__global__ void __launch_bounds__(256) k_fd_tile(const float *__restrict__ u, float *__restrict__ res, int n,
+// T x T work-group, tile origin (T - 2) gid, interior (T - 2) x (T - 2)
+template <int T>
+__global__ void __launch_bounds__(T *T) k_fd_tile(const float *__restrict__ u, float *__restrict__ res, int n,
                                                  float c0, float c1) {
-    __shared__ float t[16][16];
+    __shared__ float t[T][T];
     const int l0 = threadIdx.x, l1 = threadIdx.y;
     const int W = n + 2;
-    const int r = 14 * blockIdx.y + l1, q = 14 * blockIdx.x + l0;
+    const int r = (T - 2) * blockIdx.y + l1, q = (T - 2) * blockIdx.x + l0;
     if (r < W && q < W) t[l1][l0] = u[(size_t)W * r + q];
     __syncthreads();
-    if (l0 >= 1 && l0 <= 14 && l1 >= 1 && l1 <= 14 && r - 1 < n && q - 1 < n)
+    if (l0 >= 1 && l0 <= T - 2 && l1 >= 1 && l1 <= T - 2 && r - 1 < n && q - 1 < n)
         res[(size_t)n * (r - 1) + (q - 1)] =
             fd_combine(c0, c1, t[l1][l0], t[l1 - 1][l0], t[l1 + 1][l0], t[l1][l0 - 1], t[l1][l0 + 1]);
 }
@@ -229,18 +336,19 @@ __global__ void __launch_bounds__(256) k_fd_direct(const float *__restrict__ u, 
     res[(size_t)n * i + j] = fd_combine(c0, c1, p[W + 1], p[1], p[2 * W + 1], p[W], p[W + 2]);
 }
 
-// variant 2 tile-u, 3 tile-res, 4 direct-u, 5 direct-res
-template <int V>
-__global__ void __launch_bounds__(256) k_fd_twin(const float *__restrict__ u, float *__restrict__ out, int n) {
+// variant 2 tile-u, 3 tile-res, 4 direct-u, 5 direct-res; T the work-group
+// width of the tile variants (16 or 18)
+template <int V, int T>
+__global__ void __launch_bounds__(T *T) k_fd_twin(const float *__restrict__ u, float *__restrict__ out, int n) {
     const int l0 = threadIdx.x, l1 = threadIdx.y;
     const int W = n + 2;
     float t = 0.0f;
     if (V == 2 || V == 3) {
-        const int r = 14 * blockIdx.y + l1, q = 14 * blockIdx.x + l0;
+        const int r = (T - 2) * blockIdx.y + l1, q = (T - 2) * blockIdx.x + l0;
         if (V == 2) {
             if (r < W && q < W) t = __fadd_rn(t, u[(size_t)W * r + q]);
-            out[(size_t)16 * gridDim.x * (16 * blockIdx.y + l1) + 16 * blockIdx.x + l0] = t;
-        } else if (l0 >= 1 && l0 <= 14 && l1 >= 1 && l1 <= 14 && r - 1 < n && q - 1 < n) {
+            out[(size_t)T * gridDim.x * (T * blockIdx.y + l1) + T * blockIdx.x + l0] = t;
+        } else if (l0 >= 1 && l0 <= T - 2 && l1 >= 1 && l1 <= T - 2 && r - 1 < n && q - 1 < n) {
             out[(size_t)n * (r - 1) + (q - 1)] = t;
         }
     } else {
@@ -267,14 +375,18 @@ pm_status launch_fd(const KP &kp, void *const *b, cudaStream_t st) {
     float c0 = (float)kp.v[1], c1 = (float)kp.v[2];
     int var = kp.def->variant;
     int G = (var == 0 || var == 2 || var == 3) ? (n + 13) / 14 : (n + 15) / 16;
-    dim3 grid(G, G), blk(16, 16);
+    const int T = var >= 6 ? 18 : 16;
+    dim3 grid(G, G), blk(T, T);
     switch (var) {
-    case 0: k_fd_tile<<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n, c0, c1); break;
+    case 0: k_fd_tile<16><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n, c0, c1); break;
     case 1: k_fd_direct<<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n, c0, c1); break;
-    case 2: k_fd_twin<2><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n); break;
-    case 3: k_fd_twin<3><<<grid, blk, 0, st>>>(nullptr, (float *)b[0], n); break;
-    case 4: k_fd_twin<4><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n); break;
-    default: k_fd_twin<5><<<grid, blk, 0, st>>>(nullptr, (float *)b[0], n); break;
+    case 2: k_fd_twin<2, 16><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n); break;
+    case 3: k_fd_twin<3, 16><<<grid, blk, 0, st>>>(nullptr, (float *)b[0], n); break;
+    case 4: k_fd_twin<4, 16><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n); break;
+    case 5: k_fd_twin<5, 16><<<grid, blk, 0, st>>>(nullptr, (float *)b[0], n); break;
+    case 6: k_fd_tile<18><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n, c0, c1); break;
+    case 7: k_fd_twin<2, 18><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n); break;
+    default: k_fd_twin<3, 18><<<grid, blk, 0, st>>>(nullptr, (float *)b[0], n); break;
     }
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;

@@ -1,7 +1,8 @@
 """The paper's evaluation on this GPU (Section "Results").
 
-For each computation -- matmul (2 variants), DG differentiation (2 variants x
-2 work-group shapes), five-point stencil (2 variants) -- a model of the form
+For each computation -- matmul (2 variants), DG differentiation (noPF, uPF,
+dmPF, dmPF-T with 16x16 work-groups; noPF, dmPF, dmPF-T with 32x8), five-point
+stencil (16x16 and 18x18 tiles, direct loads) -- a model of the form
 of Eq. linear_model or Eq. nonlinear_model is calibrated on a measurement
 kernel set that does NOT contain the modeled kernels (microbenchmarks: the
 arithmetic, local-memory, barrier, overlap, empty and global-memory pattern
@@ -73,25 +74,35 @@ def studies():
     out = [mm]
     for L0, L1 in ((16, 16), (32, 8)):
         sh = "%dx%d" % (L0, L1)
+        # uPF's D loads share noPF's pattern and twin; dmPF-T's D fetch shares
+        # dmPF's; dmPF-T's unit-stride AFR-1 result store is covered by the
+        # generic feature (a tag on it would count it twice)
         tags = [("dg-noPF-u-" + sh, "nu"), ("dg-noPF-dm-" + sh, "ndm"), ("dg-dmPF-u-" + sh, "pu"),
-                ("dg-dmPF-dm-" + sh, "pdm"), ("dg-res-" + sh, "res")]
+                ("dg-dmPF-dm-" + sh, "pdm"), ("dg-res-" + sh, "res"), ("dg-dmPFT-u-" + sh, "tu")]
+        twin_k = ["dg_nopf_u", "dg_nopf_dm", "dg_dmpf_u", "dg_dmpf_dm", "dg_res", "dg_dmpft_u", "dg_dmpft_res"]
+        variants = ["dg_nopf", "dg_dmpf", "dg_dmpft"]
+        if L0 == L1:   # the u-prefetch variant needs a square work-group
+            tags.append(("dg-uPF-u-" + sh, "uu"))
+            twin_k.append("dg_upf_u")
+            variants.insert(1, "dg_upf")
         twins = []
-        for k in ("dg_nopf_u", "dg_nopf_dm", "dg_dmpf_u", "dg_dmpf_dm", "dg_res"):
+        for k in twin_k:
             for Np in (20, 35, 56, 84):
                 for Nel in (1 << 14, 1 << 16, 1 << 18):
                     twins.append((k, dict(Np=Np, Nel=Nel, L0=L0, L1=L1)))
-        modeled = [(k, dict(Np=Np, Nel=Nel, L0=L0, L1=L1)) for k in ("dg_nopf", "dg_dmpf")
+        modeled = [(k, dict(Np=Np, Nel=Nel, L0=L0, L1=L1)) for k in variants
                    for Np in (20, 35, 56, 84) for Nel in (1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18)]
         out.append(dict(name="dg_" + sh, expr=nonlinear([GENERIC] + [tagged(t, n) for t, n in tags]),
                         measure=common_measurements() + twins, modeled=modeled))
     fd_sizes = [int(round(1024 * 2 ** (i / 7.0))) for i in range(29)]   # 1024 .. 16384, geometric
-    fd_twins = [(k, {"n": n}) for k in ("fd_tile_u", "fd_tile_res", "fd_direct_u", "fd_direct_res")
+    fd_twins = [(k, {"n": n}) for k in ("fd_tile_u", "fd_tile_res", "fd_direct_u", "fd_direct_res",
+                                        "fd_tile18_u", "fd_tile18_res")
                 for n in (1024, 2048, 4096, 8192, 16384)]
-    # the tile variant's result store is a unit-stride AFR-1 pattern, so the
-    # generic feature covers it; only the overlapping tile fetch is tagged
-    out.append(dict(name="fd", expr=linear([GENERIC, tagged("fd-tile-u", "tu")]),
+    # the tile variants' result stores are unit-stride AFR-1 patterns, so the
+    # generic feature covers them; only the overlapping tile fetches are tagged
+    out.append(dict(name="fd", expr=linear([GENERIC, tagged("fd-tile-u", "tu"), tagged("fd-tile18-u", "t18u")]),
                     measure=common_measurements() + fd_twins,
-                    modeled=[(k, {"n": n}) for k in ("fd_tile", "fd_direct") for n in fd_sizes]))
+                    modeled=[(k, {"n": n}) for k in ("fd_tile", "fd_tile18", "fd_direct") for n in fd_sizes]))
     return out
 
 

@@ -69,21 +69,28 @@ def test_mm(kernel, n):
     compare(kernel, n=n)
 
 
-DG = ["dg_nopf", "dg_dmpf", "dg_nopf_u", "dg_nopf_dm", "dg_dmpf_u", "dg_dmpf_dm", "dg_res"]
+DG = ["dg_nopf", "dg_dmpf", "dg_nopf_u", "dg_nopf_dm", "dg_dmpf_u", "dg_dmpf_dm", "dg_res",
+      "dg_dmpft", "dg_dmpft_u", "dg_dmpft_res", "dg_upf", "dg_upf_u"]
 
 
 @pytest.mark.parametrize("kernel", DG)
 @pytest.mark.parametrize("Np,Nel,L0,L1", [(20, 32, 16, 16), (35, 64, 32, 8), (56, 32, 16, 16), (84, 32, 32, 8),
-                                          (1, 16, 16, 16), (7, 32, 32, 8), (16, 16, 16, 16), (33, 32, 32, 8)])
+                                          (1, 16, 16, 16), (7, 32, 32, 8), (16, 16, 16, 16), (33, 32, 32, 8),
+                                          (84, 48, 16, 16), (17, 16, 16, 16)])
 def test_dg(kernel, Np, Nel, L0, L1):
+    if kernel.startswith("dg_upf") and L0 != L1:
+        with pytest.raises(pm.PMError):
+            pm.counts(kernel, Np=Np, Nel=Nel, L0=L0, L1=L1)
+        return
     compare(kernel, Np=Np, Nel=Nel, L0=L0, L1=L1)
 
 
-FD = ["fd_tile", "fd_direct", "fd_tile_u", "fd_tile_res", "fd_direct_u", "fd_direct_res"]
+FD = ["fd_tile", "fd_direct", "fd_tile_u", "fd_tile_res", "fd_direct_u", "fd_direct_res",
+      "fd_tile18", "fd_tile18_u", "fd_tile18_res"]
 
 
 @pytest.mark.parametrize("kernel", FD)
-@pytest.mark.parametrize("n", [1, 2, 13, 14, 15, 16, 17, 28, 29, 45, 64])
+@pytest.mark.parametrize("n", [1, 2, 13, 14, 15, 16, 17, 28, 29, 31, 32, 33, 45, 64])
 def test_fd(kernel, n):
     compare(kernel, n=n)
 
@@ -119,10 +126,15 @@ def test_paper_sizes_by_interpolation():
     for n in (1024, 4096):
         check("fd_tile", "n", n, 14, 2, 14 + n % 14)
         check("fd_direct", "n", n, 16, 2, 16 + n % 16)
+        check("fd_tile18", "n", n, 16, 2, 16 + n % 16)
+    for n in (1000, 16383):
+        check("fd_tile18", "n", n, 16, 2, 16 + n % 16)
     # DG: linear in Nel at fixed Np, shape
     for Np in (20, 35, 56, 84):
         check("dg_dmpf", "Nel", 1 << 14, 16, 1, 16, Np=Np, L0=16, L1=16)
         check("dg_nopf", "Nel", 1 << 14, 32, 1, 32, Np=Np, L0=32, L1=8)
+        check("dg_upf", "Nel", 1 << 14, 16, 1, 16, Np=Np, L0=16, L1=16)
+        check("dg_dmpft", "Nel", 1 << 14, 32, 1, 32, Np=Np, L0=32, L1=8)
 
 
 def test_feature_values_match_oracle():

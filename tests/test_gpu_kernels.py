@@ -141,10 +141,38 @@ def test_dg_twins_bitexact(kernel, Np, Nel, L0, L1):
 def test_dg_res_twin_writes_zeros():
     (r,) = run_kernel("dg_res", [], Np=20, Nel=32, L0=16, L1=16)
     assert np.all(r == 0)
+    (r,) = run_kernel("dg_dmpft_res", [], Np=35, Nel=64, L0=32, L1=8)
+    assert np.all(r == 0)
 
 
-@pytest.mark.parametrize("kernel", ["fd_tile", "fd_direct"])
-@pytest.mark.parametrize("n", [1, 13, 14, 29, 100, 1024])
+@pytest.mark.parametrize("Np,Nel,L0,L1", [c for c in DG_CASES if c[2] == c[3]] + [(84, 48, 16, 16), (17, 16, 16, 16)])
+def test_dg_upf(Np, Nel, L0, L1):
+    D, u = pm_inputs.normal((3, Np, Np), 15), pm_inputs.normal((Nel, Np), 16)
+    (res,) = run_kernel("dg_upf", [D, u], Np=Np, Nel=Nel, L0=L0, L1=L1)
+    ref, rabs = refs.dg(D, u)
+    assert cond_err(res.reshape(3, Nel, Np), ref, rabs) <= TOL
+
+
+@pytest.mark.parametrize("Np,Nel,L0,L1", DG_CASES)
+def test_dg_dmpft(Np, Nel, L0, L1):
+    # transposed layouts: the kernel reads uT[j, k] and writes resT[m, i, k]
+    D, u = pm_inputs.normal((3, Np, Np), 17), pm_inputs.normal((Nel, Np), 18)
+    (resT,) = run_kernel("dg_dmpft", [D, np.ascontiguousarray(u.T)], Np=Np, Nel=Nel, L0=L0, L1=L1)
+    ref, rabs = refs.dg(D, u)
+    assert cond_err(resT.reshape(3, Np, Nel).transpose(0, 2, 1), ref, rabs) <= TOL
+
+
+@pytest.mark.parametrize("kernel", ["dg_upf_u", "dg_dmpft_u"])
+@pytest.mark.parametrize("Np,Nel", [(20, 64), (84, 64), (35, 32)])
+def test_dg_new_twins_bitexact(kernel, Np, Nel):
+    D, u = pm_inputs.normal((3, Np, Np), 19), pm_inputs.normal((Nel, Np), 20)
+    uk = np.ascontiguousarray(u.T) if kernel == "dg_dmpft_u" else u
+    (d,) = run_kernel(kernel, [uk], Np=Np, Nel=Nel, L0=16, L1=16)
+    assert np.array_equal(d.reshape(-1, Nel), refs.dg_twin(kernel, D, uk, 16, 16))
+
+
+@pytest.mark.parametrize("kernel", ["fd_tile", "fd_direct", "fd_tile18"])
+@pytest.mark.parametrize("n", [1, 13, 14, 16, 29, 100, 1024])
 def test_stencil(kernel, n):
     u = pm_inputs.uniform((n + 2, n + 2), 21)
     (r,) = run_kernel(kernel, [u], n=n, c0=-4.0, c1=1.0)
@@ -152,7 +180,7 @@ def test_stencil(kernel, n):
     assert cond_err(r.reshape(n, n), ref, rabs) <= TOL
 
 
-@pytest.mark.parametrize("kernel", ["fd_tile_u", "fd_direct_u"])
+@pytest.mark.parametrize("kernel", ["fd_tile_u", "fd_direct_u", "fd_tile18_u"])
 @pytest.mark.parametrize("n", [13, 45, 100])
 def test_stencil_twins_bitexact(kernel, n):
     u = pm_inputs.uniform((n + 2, n + 2), 22)
@@ -161,7 +189,7 @@ def test_stencil_twins_bitexact(kernel, n):
     assert np.array_equal(d.reshape(want.shape), want)
 
 
-@pytest.mark.parametrize("kernel", ["fd_tile_res", "fd_direct_res"])
+@pytest.mark.parametrize("kernel", ["fd_tile_res", "fd_direct_res", "fd_tile18_res"])
 def test_stencil_res_twins(kernel):
     (r,) = run_kernel(kernel, [], n=37)
     assert np.all(r == 0)
@@ -189,12 +217,14 @@ def test_dg_full_size_sampled():
     D, u = pm_inputs.normal((3, Np, Np), 31), pm_inputs.normal((Nel, Np), 32)
     d = dev()
     res = torch.empty(3 * Nel * Np, device=d)
-    for kernel, L0, L1 in (("dg_dmpf", 16, 16), ("dg_nopf", 32, 8)):
-        pm.launch(kernel, [torch.from_numpy(D).to(d), torch.from_numpy(u).to(d), res], Np=Np, Nel=Nel, L0=L0, L1=L1)
+    for kernel, L0, L1 in (("dg_dmpf", 16, 16), ("dg_nopf", 32, 8), ("dg_upf", 16, 16), ("dg_dmpft", 32, 8)):
+        uk = np.ascontiguousarray(u.T) if kernel == "dg_dmpft" else u
+        pm.launch(kernel, [torch.from_numpy(D).to(d), torch.from_numpy(uk).to(d), res], Np=Np, Nel=Nel, L0=L0, L1=L1)
         torch.cuda.synchronize()
         ks = np.unique(pm_inputs.integers((512,), 33, 0, Nel - 1))
         ref, rabs = refs.dg(D, u[ks])
-        got = res.cpu().numpy().reshape(3, Nel, Np)[:, ks, :]
+        full = res.cpu().numpy()
+        got = (full.reshape(3, Np, Nel).transpose(0, 2, 1) if kernel == "dg_dmpft" else full.reshape(3, Nel, Np))[:, ks, :]
         assert cond_err(got, ref, rabs) <= TOL
 
 
@@ -205,7 +235,7 @@ def test_stencil_full_size_sampled():
     gen.manual_seed(5)
     u = torch.rand((n + 2) * (n + 2), device=d, generator=gen) * 2 - 1
     r = torch.empty(n * n, device=d)
-    for kernel in ("fd_tile", "fd_direct"):
+    for kernel in ("fd_tile", "fd_direct", "fd_tile18"):
         pm.launch(kernel, [u, r], n=n, c0=-4.0, c1=1.0)
         torch.cuda.synchronize()
         for i0 in (0, 7777, n - 9):
