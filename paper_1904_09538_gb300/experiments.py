@@ -106,6 +106,36 @@ def studies():
     return out
 
 
+def sweep_studies():
+    """The cross-variant sweep: 8 modeled variants (prefetching fp32 matmul,
+    BF16 tensor-core matmul, DG noPF / uPF / dmPF / dmPF-T with 16x16
+    work-groups, stencil 16x16 tile and direct) at ~30 sizes each.  Every
+    third size is held out; each variant's model is calibrated on the
+    microbenchmarks (plus its computation's twins) and the variant's own other
+    sizes -- the paper's "few extra on-line calibration runs" -- and predicts
+    the held-out sizes."""
+    base = {s["name"]: s for s in studies()}
+    # the A and B tile loads both scale as n^3 at a fixed tile shape, so one
+    # bf16 load feature carries them
+    tc_expr = nonlinear(["p_gbf * f_mem_access_global_bfloat16", tagged("tc-c", "tcc")],
+                        overhead="p_launch * f_sync_kernel_launch + p_group * f_thread_groups",
+                        onchip="p_tc * f_op_bfloat16_madd")
+    nels = sorted({int(round(2 ** (14 + 4 * i / 7.0) / 32)) * 32 for i in range(8)})
+    dg_sizes = [dict(Np=Np, Nel=Nel, L0=16, L1=16) for Np in (20, 35, 56, 84) for Nel in nels]
+    plan = [("mm_pf", "matmul", None, [{"n": n} for n in range(512, 4096 + 1, 128)]),
+            ("mm_tc", None, tc_expr, [{"n": n} for n in range(1024, 8192 + 1, 256)])]
+    plan += [(k, "dg_16x16", None, dg_sizes) for k in ("dg_nopf", "dg_upf", "dg_dmpf", "dg_dmpft")]
+    plan += [(k, "fd", None, [{"n": int(round(1024 * 2 ** (i / 7.0)))} for i in range(29)])
+             for k in ("fd_tile", "fd_direct")]
+    out = []
+    for k, parent, expr, sizes in plan:
+        fit = [(k, p) for i, p in enumerate(sizes) if i % 3 != 2]
+        held = [(k, p) for i, p in enumerate(sizes) if i % 3 == 2]
+        measure = (base[parent]["measure"] if parent else common_measurements()) + fit
+        out.append(dict(name="sweep_" + k, expr=expr or base[parent]["expr"], measure=measure, modeled=held))
+    return out
+
+
 class Buffers:
     """Device buffers reused across kernels (seeded uniform values in [-1, 1))."""
 
@@ -155,21 +185,30 @@ def geomean(x):
     return float(math.exp(np.mean(np.log(x))))
 
 
-def run_studies(trials=10, names=None, seed=1234, flush_l2=True):
+def run_studies(trials=10, names=None, seed=1234, flush_l2=True, study_list=None):
     """Calibrate each study's model on its measurement set (all studies in one
     batched fit) and predict its modeled kernels.  Returns a report dict.
-    flush_l2: every timed trial starts with a cold L2 (pm_run flush_l2)."""
+    flush_l2: every timed trial starts with a cold L2 (pm_run flush_l2).
+    A kernel instance shared by several studies is timed once."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     bufs = Buffers(torch, dev, seed)
-    sts = [s for s in studies() if names is None or s["name"] in names]
+    sts = [s for s in (study_list if study_list is not None else studies()) if names is None or s["name"] in names]
+    cache = {}
+
+    def timed(kernels):
+        todo = [(k, p) for k, p in kernels if (k, tuple(sorted(p.items()))) not in cache]
+        for (k, p), t in zip(todo, measure(todo, bufs, trials, flush_l2) if todo else []):
+            cache[(k, tuple(sorted(p.items())))] = t
+        return np.array([cache[(k, tuple(sorted(p.items())))] for k, p in kernels])
+
     models, Xs, ts, info = [], [], [], []
     for s in sts:
         m = Model("f_wall_time", s["expr"])
         Xm = np.stack([m.feature_values(k, **p) for k, p in s["measure"]])
-        tm = measure(s["measure"], bufs, trials, flush_l2)
+        tm = timed(s["measure"])
         Xp = np.stack([m.feature_values(k, **p) for k, p in s["modeled"]])
-        tp = measure(s["modeled"], bufs, trials, flush_l2)
+        tp = timed(s["modeled"])
         models.append(m)
         Xs.append(Xm)
         ts.append(tm)
@@ -237,6 +276,7 @@ if __name__ == "__main__":
     import sys
     flush = "--no-flush" not in sys.argv
     args = [a for a in sys.argv[1:] if not a.startswith("--")]
-    out = {"illustrative": illustrative(flush_l2=flush), "studies": run_studies(flush_l2=flush)}
+    out = {"illustrative": illustrative(flush_l2=flush), "studies": run_studies(flush_l2=flush),
+           "sweep": run_studies(flush_l2=flush, study_list=sweep_studies())}
     sys.argv = [sys.argv[0]] + args
     json.dump(out, open(sys.argv[1], "w") if len(sys.argv) > 1 else sys.stdout, indent=1)
