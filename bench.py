@@ -264,7 +264,7 @@ def run_ours(args):
         try:
             tj = json.load(open(tpath))
             ent = tj.get(dom)
-            if ent and ent.get("source_sha") == source_sha():
+            if ent and ent.get("source_sha") == source_sha(ent.get("source", "pm_suite.cu")):
                 traffic = ent["dram_bytes_per_launch"]
         except Exception:
             traffic = None
@@ -303,12 +303,11 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def source_sha():
+def source_sha(f="pm_suite.cu"):
+    """Hash of the source file that defines a kernel: a recorded DRAM traffic
+    figure is valid only while that file is unchanged."""
     import hashlib
-    h = hashlib.sha256()
-    for f in ("pm_suite.cu", "pm_modeled.cu"):
-        h.update(open(os.path.join(ROOT, "paper_1904_09538_gb300", "csrc", f), "rb").read())
-    return h.hexdigest()[:16]
+    return hashlib.sha256(open(os.path.join(ROOT, "paper_1904_09538_gb300", "csrc", f), "rb").read()).hexdigest()[:16]
 
 
 def e2e_measure(pm, S, variants, torch):

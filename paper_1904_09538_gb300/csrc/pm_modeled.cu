@@ -233,17 +233,28 @@ __global__ void __launch_bounds__(L0 *L1) k_dg_twin(const float *__restrict__ D,
         for (int jo = 0; jo < njl; jo++)
             if (L1 * jo + l0 < Np) t = __fadd_rn(t, urow[L1 * jo + l0]);
     }
-    if (V == 10) {
-        if (i < Np)
-            for (int m = 0; m < 3; m++)
-                for (int jo = 0; jo < nj; jo++)
-                    for (int ji = 0; ji < L0; ji++)
-                        if (L0 * jo + ji < Np) t = __fadd_rn(t, u[(size_t)Nel * (L0 * jo + ji) + k]);
-    }
-    if (V == 2 || V == 4) {
+
+    if (V == 2) {
         if (i < Np)
             for (int m = 0; m < 3; m++)
                 for (int j = 0; j < Np; j++) t = __fadd_rn(t, u[(size_t)Np * k + j]);
+    }
+    if (V == 4 || V == 10) {
+        // the parent's j loop shape (full tiles unrolled) keeps its memory-level parallelism
+        const float *uk = V == 4 ? u + (size_t)Np * k : u + k;
+        const size_t js = V == 4 ? 1 : (size_t)Nel;
+        if (i < Np)
+            for (int m = 0; m < 3; m++)
+                for (int jo = 0; jo < nj; jo++) {
+                    const int jn = min(L0, Np - L0 * jo);
+                    const float *uj = uk + js * L0 * jo;
+                    if (jn == L0) {
+#pragma unroll
+                        for (int ji = 0; ji < L0; ji++) t = __fadd_rn(t, uj[js * ji]);
+                    } else {
+                        for (int ji = 0; ji < jn; ji++) t = __fadd_rn(t, uj[js * ji]);
+                    }
+                }
     }
     if (V == 3) {
         if (i < Np)
