@@ -138,6 +138,28 @@ typedef struct {
 pm_status pm_counts(int32_t kernel, const pm_param *p, size_t np,
                     pm_feature *out, size_t cap, size_t *n_out);
 
+/* Compiled resources and launch shape of one kernel instance, for an
+ * autotuner's pruning step (the paper's use of a model as a heuristic that
+ * narrows the variants worth timing, Section "Assumptions and Limitations"):
+ * a variant that spills registers to local memory or cannot keep a CTA
+ * resident is not worth timing. */
+typedef struct {
+    int32_t regs_per_thread;
+    int32_t local_bytes_per_thread;  /* stack / register spill */
+    int32_t static_smem_bytes;
+    int32_t dynamic_smem_bytes;      /* of this launch */
+    int32_t threads_per_block;       /* of this launch */
+    int32_t max_threads_per_block;   /* of the compiled kernel */
+    int32_t blocks_per_sm;           /* resident CTAs per SM at this launch shape (0: cannot run) */
+    int32_t sm_count;
+    uint64_t grid_blocks;
+} pm_resources;
+
+/* Fill *out for `kernel` at parameters p on the current device, without
+ * launching it and without touching device memory.  Needs a CUDA device;
+ * PM_ECUDA without one. */
+pm_status pm_kernel_resources(int32_t kernel, const pm_param *p, size_t np, pm_resources *out);
+
 /* ---------------------------------------------------------------- running */
 
 /* Enqueue one launch of `kernel` on `stream`.  bufs: device pointers in the

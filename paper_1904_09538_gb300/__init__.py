@@ -111,6 +111,15 @@ def _stream(stream):
     return ctypes.c_void_p(stream)
 
 
+def resources(kernel, **params):
+    """Compiled resources and launch shape of a kernel instance
+    (pm_kernel_resources; needs a CUDA device, launches nothing)."""
+    arr, n, _keep = _params(params)
+    r = _lib.pm_resources()
+    check(lib().pm_kernel_resources(_kid(kernel), arr, n, ctypes.byref(r)))
+    return {f: int(getattr(r, f)) for f, _ in r._fields_}
+
+
 def launch(kernel, bufs, stream=None, **params):
     """Enqueue one launch (device buffers in pm_kernel_buffers order)."""
     arr, n, _keep = _params(params)

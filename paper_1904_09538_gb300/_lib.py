@@ -28,6 +28,13 @@ class pm_feature(ctypes.Structure):
                 ("accesses", ctypes.c_uint64), ("footprint", ctypes.c_uint64)]
 
 
+class pm_resources(ctypes.Structure):
+    _fields_ = [("regs_per_thread", ctypes.c_int32), ("local_bytes_per_thread", ctypes.c_int32),
+                ("static_smem_bytes", ctypes.c_int32), ("dynamic_smem_bytes", ctypes.c_int32),
+                ("threads_per_block", ctypes.c_int32), ("max_threads_per_block", ctypes.c_int32),
+                ("blocks_per_sm", ctypes.c_int32), ("sm_count", ctypes.c_int32), ("grid_blocks", ctypes.c_uint64)]
+
+
 class pm_run_opts(ctypes.Structure):
     _fields_ = [("warmup", ctypes.c_int32), ("trials", ctypes.c_int32), ("outlier_factor", ctypes.c_double),
                 ("flush_l2", ctypes.c_int32)]
@@ -63,6 +70,7 @@ SIGNATURES = {
     "pm_kernel_buffers": (i32, [i32, P(pm_param), c_size_t, P(pm_buffer), c_size_t, P(c_size_t)]),
     "pm_counts": (i32, [i32, P(pm_param), c_size_t, P(pm_feature), c_size_t, P(c_size_t)]),
     "pm_launch": (i32, [i32, P(pm_param), c_size_t, P(vp), c_size_t, vp]),
+    "pm_kernel_resources": (i32, [i32, P(pm_param), c_size_t, P(pm_resources)]),
     "pm_run": (i32, [i32, P(pm_param), c_size_t, P(vp), c_size_t, P(pm_run_opts), vp, fp, P(pm_timing)]),
     "pm_run_host": (i32, [i32, P(pm_param), c_size_t, P(vp), c_size_t, P(pm_run_opts), vp, fp, P(pm_timing), dp]),
     "pm_model_create": (i32, [ctypes.c_char_p, ctypes.c_char_p, P(vp)]),

@@ -61,6 +61,27 @@ struct BufSpec {
     uint64_t elems;
 };
 pm_status buffers(const KP &kp, std::vector<BufSpec> &out);
+// Launch query: while a LaunchQuery is installed on the calling thread, the
+// launch helpers record the kernel they would launch (attributes, occupancy,
+// launch shape) instead of launching it.  Used by pm_kernel_resources.
+struct LaunchQuery {
+    pm_resources *out;
+    int hits;
+    pm_status status;
+};
+extern thread_local LaunchQuery *g_launch_query;
+// Returns true when the launch must be skipped (a query is installed).
+bool launch_query_hook(const void *fn, unsigned gx, unsigned gy, unsigned gz, unsigned bx, unsigned by, unsigned bz,
+                       size_t smem);
+
+#ifdef __CUDACC__
+template <typename... P, typename... A>
+inline void launch_k(void (*k)(P...), dim3 g, dim3 b, size_t smem, cudaStream_t st, A... a) {
+    if (launch_query_hook((const void *)k, g.x, g.y, g.z, b.x, b.y, b.z, smem)) return;
+    k<<<g, b, smem, st>>>(static_cast<P>(a)...);
+}
+#endif
+
 pm_status launch_suite(const KP &kp, void *const *bufs, void *stream);
 pm_status launch_modeled(const KP &kp, void *const *bufs, void *stream);
 pm_status launch_tiles(const KP &kp, void *const *bufs, void *stream);

@@ -91,12 +91,12 @@ pm_status launch_mm(const KP &kp, void *const *b, cudaStream_t st) {
     int n = (int)kp.i(0);
     dim3 grid(n / 16, n / 16), blk(16, 16);
     switch (kp.def->variant) {
-    case 0: k_mm_pf<<<grid, blk, 0, st>>>((const float *)b[0], (const float *)b[1], (float *)b[2], n); break;
-    case 1: k_mm_nopf<<<grid, blk, 0, st>>>((const float *)b[0], (const float *)b[1], (float *)b[2], n); break;
-    case 2: k_mm_twin<2><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n); break;
-    case 3: k_mm_twin<3><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n); break;
-    case 4: k_mm_twin<4><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n); break;
-    default: k_mm_twin<5><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n); break;
+    case 0: launch_k(k_mm_pf, grid, blk, 0, st, (const float *)b[0], (const float *)b[1], (float *)b[2], n); break;
+    case 1: launch_k(k_mm_nopf, grid, blk, 0, st, (const float *)b[0], (const float *)b[1], (float *)b[2], n); break;
+    case 2: launch_k(k_mm_twin<2>, grid, blk, 0, st, (const float *)b[0], (float *)b[1], n); break;
+    case 3: launch_k(k_mm_twin<3>, grid, blk, 0, st, (const float *)b[0], (float *)b[1], n); break;
+    case 4: launch_k(k_mm_twin<4>, grid, blk, 0, st, (const float *)b[0], (float *)b[1], n); break;
+    default: launch_k(k_mm_twin<5>, grid, blk, 0, st, (const float *)b[0], (float *)b[1], n); break;
     }
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
@@ -276,35 +276,35 @@ pm_status launch_dg_t(int var, void *const *b, int Np, int Nel, cudaStream_t st)
     const float *D = nullptr, *u = nullptr;
     float *o = nullptr;
     switch (var) {
-    case 0: k_dg_nopf<L0, L1><<<grid, blk, 0, st>>>((const float *)b[0], (const float *)b[1], (float *)b[2], Np, Nel); break;
-    case 1: k_dg_dmpf<L0, L1><<<grid, blk, 0, st>>>((const float *)b[0], (const float *)b[1], (float *)b[2], Np, Nel); break;
+    case 0: launch_k(k_dg_nopf<L0, L1>, grid, blk, 0, st, (const float *)b[0], (const float *)b[1], (float *)b[2], Np, Nel); break;
+    case 1: launch_k(k_dg_dmpf<L0, L1>, grid, blk, 0, st, (const float *)b[0], (const float *)b[1], (float *)b[2], Np, Nel); break;
     case 2: case 4:
         u = (const float *)b[0]; o = (float *)b[1];
-        if (var == 2) k_dg_twin<L0, L1, 2><<<grid, blk, 0, st>>>(D, u, o, Np, Nel);
-        else k_dg_twin<L0, L1, 4><<<grid, blk, 0, st>>>(D, u, o, Np, Nel);
+        if (var == 2) launch_k(k_dg_twin<L0, L1, 2>, grid, blk, 0, st, D, u, o, Np, Nel);
+        else launch_k(k_dg_twin<L0, L1, 4>, grid, blk, 0, st, D, u, o, Np, Nel);
         break;
     case 3: case 5:
         D = (const float *)b[0]; o = (float *)b[1];
-        if (var == 3) k_dg_twin<L0, L1, 3><<<grid, blk, 0, st>>>(D, u, o, Np, Nel);
-        else k_dg_twin<L0, L1, 5><<<grid, blk, 0, st>>>(D, u, o, Np, Nel);
+        if (var == 3) launch_k(k_dg_twin<L0, L1, 3>, grid, blk, 0, st, D, u, o, Np, Nel);
+        else launch_k(k_dg_twin<L0, L1, 5>, grid, blk, 0, st, D, u, o, Np, Nel);
         break;
     case 6:
-        k_dg_twin<L0, L1, 6><<<grid, blk, 0, st>>>(D, u, (float *)b[0], Np, Nel);
+        launch_k(k_dg_twin<L0, L1, 6>, grid, blk, 0, st, D, u, (float *)b[0], Np, Nel);
         break;
     case 7:
         if constexpr (L0 == L1)
-            k_dg_upf<L0><<<grid, blk, 0, st>>>((const float *)b[0], (const float *)b[1], (float *)b[2], Np, Nel);
+            launch_k(k_dg_upf<L0>, grid, blk, 0, st, (const float *)b[0], (const float *)b[1], (float *)b[2], Np, Nel);
         else
             return fail(PM_EINVAL, "dg_upf needs a square work-group");
         break;
-    case 8: k_dg_dmpft<L0, L1><<<grid, blk, 0, st>>>((const float *)b[0], (const float *)b[1], (float *)b[2], Np, Nel); break;
+    case 8: launch_k(k_dg_dmpft<L0, L1>, grid, blk, 0, st, (const float *)b[0], (const float *)b[1], (float *)b[2], Np, Nel); break;
     case 9: case 10:
         u = (const float *)b[0]; o = (float *)b[1];
-        if (var == 9) k_dg_twin<L0, L1, 9><<<grid, blk, 0, st>>>(D, u, o, Np, Nel);
-        else k_dg_twin<L0, L1, 10><<<grid, blk, 0, st>>>(D, u, o, Np, Nel);
+        if (var == 9) launch_k(k_dg_twin<L0, L1, 9>, grid, blk, 0, st, D, u, o, Np, Nel);
+        else launch_k(k_dg_twin<L0, L1, 10>, grid, blk, 0, st, D, u, o, Np, Nel);
         break;
     default:
-        k_dg_twin<L0, L1, 11><<<grid, blk, 0, st>>>(D, u, (float *)b[0], Np, Nel);
+        launch_k(k_dg_twin<L0, L1, 11>, grid, blk, 0, st, D, u, (float *)b[0], Np, Nel);
     }
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
@@ -389,15 +389,15 @@ pm_status launch_fd(const KP &kp, void *const *b, cudaStream_t st) {
     const int T = var >= 6 ? 18 : 16;
     dim3 grid(G, G), blk(T, T);
     switch (var) {
-    case 0: k_fd_tile<16><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n, c0, c1); break;
-    case 1: k_fd_direct<<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n, c0, c1); break;
-    case 2: k_fd_twin<2, 16><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n); break;
-    case 3: k_fd_twin<3, 16><<<grid, blk, 0, st>>>(nullptr, (float *)b[0], n); break;
-    case 4: k_fd_twin<4, 16><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n); break;
-    case 5: k_fd_twin<5, 16><<<grid, blk, 0, st>>>(nullptr, (float *)b[0], n); break;
-    case 6: k_fd_tile<18><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n, c0, c1); break;
-    case 7: k_fd_twin<2, 18><<<grid, blk, 0, st>>>((const float *)b[0], (float *)b[1], n); break;
-    default: k_fd_twin<3, 18><<<grid, blk, 0, st>>>(nullptr, (float *)b[0], n); break;
+    case 0: launch_k(k_fd_tile<16>, grid, blk, 0, st, (const float *)b[0], (float *)b[1], n, c0, c1); break;
+    case 1: launch_k(k_fd_direct, grid, blk, 0, st, (const float *)b[0], (float *)b[1], n, c0, c1); break;
+    case 2: launch_k(k_fd_twin<2, 16>, grid, blk, 0, st, (const float *)b[0], (float *)b[1], n); break;
+    case 3: launch_k(k_fd_twin<3, 16>, grid, blk, 0, st, nullptr, (float *)b[0], n); break;
+    case 4: launch_k(k_fd_twin<4, 16>, grid, blk, 0, st, (const float *)b[0], (float *)b[1], n); break;
+    case 5: launch_k(k_fd_twin<5, 16>, grid, blk, 0, st, nullptr, (float *)b[0], n); break;
+    case 6: launch_k(k_fd_tile<18>, grid, blk, 0, st, (const float *)b[0], (float *)b[1], n, c0, c1); break;
+    case 7: launch_k(k_fd_twin<2, 18>, grid, blk, 0, st, (const float *)b[0], (float *)b[1], n); break;
+    default: launch_k(k_fd_twin<3, 18>, grid, blk, 0, st, nullptr, (float *)b[0], n); break;
     }
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;

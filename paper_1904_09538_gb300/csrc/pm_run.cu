@@ -30,6 +30,36 @@ static pm_status launch_any(const KP &kp, void *const *bufs, size_t nbufs, void 
 
 static size_t dtype_size(int dt) { return dt == PM_F32 ? 4 : dt == PM_F64 ? 8 : 2; }
 
+thread_local LaunchQuery *g_launch_query = nullptr;
+
+bool launch_query_hook(const void *fn, unsigned gx, unsigned gy, unsigned gz, unsigned bx, unsigned by, unsigned bz,
+                       size_t smem) {
+    LaunchQuery *q = g_launch_query;
+    if (!q) return false;
+    q->hits++;
+    cudaFuncAttributes a;
+    int dev = 0, sms = 0, nb = 0;
+    const int threads = (int)(bx * by * bz);
+    if (cudaFuncGetAttributes(&a, fn) != cudaSuccess || cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, fn, threads, smem) != cudaSuccess) {
+        cudaGetLastError();
+        q->status = fail(PM_ECUDA, "pm_kernel_resources: attribute query failed");
+        return true;
+    }
+    pm_resources *o = q->out;
+    o->regs_per_thread = a.numRegs;
+    o->local_bytes_per_thread = (int32_t)a.localSizeBytes;
+    o->static_smem_bytes = (int32_t)a.sharedSizeBytes;
+    o->dynamic_smem_bytes = (int32_t)smem;
+    o->threads_per_block = threads;
+    o->max_threads_per_block = a.maxThreadsPerBlock;
+    o->blocks_per_sm = nb;
+    o->sm_count = sms;
+    o->grid_blocks = (uint64_t)gx * gy * gz;
+    return true;
+}
+
 // L2 flush: overwrite a buffer larger than the 129 MB L2 (one per device).
 constexpr size_t kFlushBytes = 256u << 20;
 static void *g_flush[64];
@@ -127,6 +157,28 @@ static pm_status timed(const KP &kp, void *const *bufs, size_t nbufs, const pm_r
 using namespace pm;
 
 extern "C" {
+
+pm_status pm_kernel_resources(int32_t kernel, const pm_param *p, size_t np, pm_resources *out) {
+    KP kp;
+    pm_status s = parse_params(kernel, p, np, &kp);
+    if (s) return s;
+    if (!out) return fail(PM_EINVAL, "pm_kernel_resources: out is NULL");
+    if ((s = validate(kp))) return s;
+    std::vector<BufSpec> spec;
+    if ((s = buffers(kp, spec))) return s;
+    // placeholder addresses: aligned, never dereferenced (the launch is skipped)
+    std::vector<void *> fake(spec.size());
+    for (size_t i = 0; i < fake.size(); i++) fake[i] = (void *)(uintptr_t)((i + 1) << 20);
+    *out = pm_resources{};
+    LaunchQuery q{out, 0, PM_OK};
+    g_launch_query = &q;
+    s = launch_any(kp, fake.data(), fake.size(), nullptr);
+    g_launch_query = nullptr;
+    if (s) return s;
+    if (q.status) return q.status;
+    if (q.hits != 1) return fail(PM_EINVAL, "pm_kernel_resources: %s issued %d launches", kp.def->name, q.hits);
+    return PM_OK;
+}
 
 pm_status pm_launch(int32_t kernel, const pm_param *p, size_t np, void *const *bufs, size_t nbufs, void *stream) {
     KP kp;

@@ -63,10 +63,10 @@ pm_status launch_stream_t(int L, void *const *b, int arg, int G0, unsigned grid,
     T *o = (T *)b[L];
     dim3 blk = SHAPE == 0 ? dim3(256) : dim3(16, 16);
     switch (L) {
-    case 1: k_stream<T, 1, SHAPE><<<grid, blk, 0, st>>>(i0, i1, i2, i3, o, arg, G0); break;
-    case 2: k_stream<T, 2, SHAPE><<<grid, blk, 0, st>>>(i0, i1, i2, i3, o, arg, G0); break;
-    case 3: k_stream<T, 3, SHAPE><<<grid, blk, 0, st>>>(i0, i1, i2, i3, o, arg, G0); break;
-    default: k_stream<T, 4, SHAPE><<<grid, blk, 0, st>>>(i0, i1, i2, i3, o, arg, G0); break;
+    case 1: launch_k(k_stream<T, 1, SHAPE>, grid, blk, 0, st, i0, i1, i2, i3, o, arg, G0); break;
+    case 2: launch_k(k_stream<T, 2, SHAPE>, grid, blk, 0, st, i0, i1, i2, i3, o, arg, G0); break;
+    case 3: launch_k(k_stream<T, 3, SHAPE>, grid, blk, 0, st, i0, i1, i2, i3, o, arg, G0); break;
+    default: launch_k(k_stream<T, 4, SHAPE>, grid, blk, 0, st, i0, i1, i2, i3, o, arg, G0); break;
     }
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
@@ -143,9 +143,9 @@ __global__ void __launch_bounds__(256) k_fma(const T *__restrict__ seed, T *__re
 
 template <typename T>
 pm_status launch_fma_t(int op, const void *seed, void *out, int rounds, unsigned G, cudaStream_t st) {
-    if (op == 0) k_fma<T, 0><<<G, 256, 0, st>>>((const T *)seed, (T *)out, rounds);
-    else if (op == 1) k_fma<T, 1><<<G, 256, 0, st>>>((const T *)seed, (T *)out, rounds);
-    else k_fma<T, 2><<<G, 256, 0, st>>>((const T *)seed, (T *)out, rounds);
+    if (op == 0) launch_k(k_fma<T, 0>, G, 256, 0, st, (const T *)seed, (T *)out, rounds);
+    else if (op == 1) launch_k(k_fma<T, 1>, G, 256, 0, st, (const T *)seed, (T *)out, rounds);
+    else launch_k(k_fma<T, 2>, G, 256, 0, st, (const T *)seed, (T *)out, rounds);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
 }
@@ -209,18 +209,18 @@ pm_status launch_suite(const KP &kp, void *const *b, void *stream) {
     case FAM_SMEM: {
         int iters = (int)(kp.i(0) / 4);
         unsigned G = (unsigned)kp.i(2);
-        if (kp.i(1)) k_smem<1><<<G, 256, 0, st>>>((const float *)b[0], (float *)b[1], iters);
-        else k_smem<0><<<G, 256, 0, st>>>((const float *)b[0], (float *)b[1], iters);
+        if (kp.i(1)) launch_k(k_smem<1>, G, 256, 0, st, (const float *)b[0], (float *)b[1], iters);
+        else launch_k(k_smem<0>, G, 256, 0, st, (const float *)b[0], (float *)b[1], iters);
         break;
     }
     case FAM_BARRIER:
-        k_barrier<<<(unsigned)kp.i(1), 256, 0, st>>>((const float *)b[0], (float *)b[1], (int)kp.i(0));
+        launch_k(k_barrier, (unsigned)kp.i(1), 256, 0, st, (const float *)b[0], (float *)b[1], (int)kp.i(0));
         break;
     case FAM_OVERLAP:
-        k_overlap<<<(unsigned)(kp.i(1) / 256), 256, 0, st>>>((const float *)b[0], (float *)b[1], (int)kp.i(0));
+        launch_k(k_overlap, (unsigned)(kp.i(1) / 256), 256, 0, st, (const float *)b[0], (float *)b[1], (int)kp.i(0));
         break;
     case FAM_EMPTY:
-        k_empty<<<(unsigned)kp.i(0), 256, 0, st>>>();
+        launch_k(k_empty, (unsigned)kp.i(0), 256, 0, st);
         break;
     default:
         return fail(PM_EINVAL, "not a suite kernel");

@@ -245,7 +245,7 @@ pm_status launch_tc(const KP &kp, void *const *b, void *stream) {
     if ((s = tensor_map_2d(&tb, 1, b[1], n, n, (uint64_t)n * 2, TK, TN, 1))) return s;
     PM_CUDA_TRY(cudaFuncSetAttribute(k_mm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
     dim3 grid(n / TN, n / TM);
-    k_mm_tc<<<grid, 128, kTcSmem, (cudaStream_t)stream>>>(ta, tb, (float *)b[2], n, n, n);
+    launch_k(k_mm_tc, grid, 128, kTcSmem, (cudaStream_t)stream, ta, tb, (float *)b[2], n, n, n);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
 }

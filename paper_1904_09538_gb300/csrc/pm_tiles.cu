@@ -107,7 +107,7 @@ pm_status launch_simt_t(void *const *b, int n, cudaStream_t st) {
     auto fn = k_mm_simt<BM, BN, BK>;
     PM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(n / BN, n / BM), blk(BN / 8, BM / 8);
-    fn<<<grid, blk, smem, st>>>((const float4 *)b[0], (const float4 *)b[1], (float4 *)b[2], n);
+    launch_k(fn, grid, blk, smem, st, (const float4 *)b[0], (const float4 *)b[1], (float4 *)b[2], n);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
 }
@@ -175,7 +175,7 @@ pm_status launch_fdb_t(void *const *b, int n, float c0, float c1, cudaStream_t s
     pm_status s = tensor_map_2d(&tm, 0, b[0], P, (uint64_t)n + 2, P * sizeof(float), TW, TH, 0);
     if (s) return s;
     dim3 grid(n / BX, n / BY), blk(BX / 4, BY);
-    k_fd_block<BX, BY><<<grid, blk, smem, st>>>(tm, (float *)b[1], n, c0, c1);
+    launch_k(k_fd_block<BX, BY>, grid, blk, smem, st, tm, (float *)b[1], n, c0, c1);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
 }
