@@ -65,7 +65,9 @@ typedef struct {
  * of ranking equivalent variants, Section "Assumptions and Limitations"):
  * "mm_simt" (register-tiled fp32 matmul, parameters n, BM, BN, BK); the
  * added BF16 tensor-core matmul "mm_tc" (C = A Bt^T, bf16 in, fp32 out,
- * tcgen05/TMEM/TMA, parameter n, a multiple of 256); the TMA-staged
+ * tcgen05/TMEM/TMA, parameter n, a multiple of 256, and pipe: 0 = 4-stage
+ * ring with one CTA per SM, 1 (default) = 2-stage ring with two CTAs per SM;
+ * the counts do not depend on pipe); the TMA-staged
  * stencil tile family "fd_block" (parameters n, BX, BY, c0, c1; input u of
  * (n + 2) rows with row pitch n + 4).
  * Returns PM_EUNKNOWN_KERNEL for other names. */

@@ -34,6 +34,7 @@ static constexpr double REQ = std::numeric_limits<double>::quiet_NaN();
 #define P_DG {"Np", "Nel", "L0", "L1", nullptr}, {REQ, REQ, 16, 16}, {1, 1, 1, 1}
 #define P_FD {"n", "c0", "c1", nullptr}, {REQ, -4.0, 1.0}, {1, 0, 0}
 #define P_SIMT {"n", "BM", "BN", "BK", nullptr}, {REQ, 128, 128, 32}, {1, 1, 1, 1}
+#define P_TC {"n", "pipe", nullptr}, {REQ, 1}, {1, 1}
 #define P_FDB {"n", "BX", "BY", "c0", "c1", nullptr}, {REQ, 64, 8, -4.0, 1.0}, {1, 1, 1, 0, 0}
 
 static const KernelDef KDEFS[] = {
@@ -63,7 +64,7 @@ static const KernelDef KDEFS[] = {
     {"fd_direct_u", FAM_FD, 4, P_FD},
     {"fd_direct_res", FAM_FD, 5, P_FD},
     {"mm_simt", FAM_SIMT, 0, P_SIMT},
-    {"mm_tc", FAM_TC, 0, P_MM},
+    {"mm_tc", FAM_TC, 0, P_TC},
     {"fd_block", FAM_FDB, 0, P_FDB},
     {"fd_tile18", FAM_FD, 6, P_FD},
     {"fd_tile18_u", FAM_FD, 7, P_FD},

@@ -4,14 +4,19 @@
 //
 // One CTA of 128 threads computes a 128 x 256 tile of C:
 //   warp 0 lane 0: TMA producer -- per 64-wide k tile, one 128x64 tile of A
-//       and one 256x64 tile of Bt (128-byte swizzle) into a 4-stage shared
-//       memory ring, completion tracked by "full" mbarriers;
+//       and one 256x64 tile of Bt (128-byte swizzle) into a shared-memory
+//       ring of STAGES stages, completion tracked by "full" mbarriers;
 //   warp 1 lane 0: MMA issuer -- four tcgen05.mma (M=128, N=256, K=16) per k
 //       tile accumulating in tensor memory; tcgen05.commit releases the
 //       stage ("empty" mbarrier) and finally signals the accumulator;
 //   warp 2: allocates / frees 256 TMEM columns;
 //   all four warps: epilogue -- tcgen05.ld of their 32 TMEM lanes (= rows),
 //       16-byte stores to C.
+// Two pipeline shapes: 4 stages with one CTA per SM, or 2 stages with two
+// CTAs per SM (2 x 256 TMEM columns), where one CTA's epilogue overlaps the
+// other's main loop.  CTAs are numbered in groups of 16 tile rows sharing a
+// sweep over the tile columns, so that concurrently resident CTAs reuse the
+// same A and Bt tiles from L2.
 // Every mbarrier wait is bounded; on timeout the kernel sets an error word
 // (read by the host after synchronising), stops issuing work, drains its own
 // copies (bounded), frees its TMEM and returns.
@@ -29,7 +34,7 @@ static __device__ int g_tc_timeout;   // set to 1 by any CTA whose bounded wait 
 
 namespace {
 
-constexpr int TM = 128, TN = 256, TK = 64, STAGES = 4;
+constexpr int TM = 128, TN = 256, TK = 64, GROUP_M = 16;
 constexpr int A_BYTES = TM * TK * 2, B_BYTES = TN * TK * 2, STAGE_BYTES = A_BYTES + B_BYTES;
 constexpr int TMEM_COLS = 256;
 constexpr long long WAIT_LIMIT = 1ll << 26;  // polls of a try_wait before giving up
@@ -74,21 +79,30 @@ __device__ __forceinline__ void mma_commit(uint64_t *bar) {
                  : "memory");
 }
 
+template <int STAGES>
 struct __align__(8) TcShared {
     uint64_t full[STAGES], empty[STAGES], accum;
     uint32_t tmem_base;
     int issued;   // k tiles whose copies the producer issued
 };
 
-__global__ void __launch_bounds__(128, 1) k_mm_tc(const __grid_constant__ CUtensorMap tmA,
-                                                  const __grid_constant__ CUtensorMap tmB, float *__restrict__ C,
-                                                  int M, int N, int K) {
+template <int STAGES>
+constexpr size_t tc_smem() { return (size_t)STAGES * STAGE_BYTES + sizeof(TcShared<STAGES>) + 2048; }
+
+template <int STAGES, int MINB>
+__global__ void __launch_bounds__(128, MINB) k_mm_tc(const __grid_constant__ CUtensorMap tmA,
+                                                     const __grid_constant__ CUtensorMap tmB, float *__restrict__ C,
+                                                     int M, int N, int K) {
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     // 1024-byte aligned ring of stages, then the barriers
     unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
-    TcShared *S = (TcShared *)(base + STAGES * STAGE_BYTES);
+    TcShared<STAGES> *S = (TcShared<STAGES> *)(base + STAGES * STAGE_BYTES);
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int n0 = blockIdx.x * TN, m0 = blockIdx.y * TM;
+    // CTA -> tile: groups of GROUP_M tile rows, column-major inside a group
+    const int ntm = M / TM, ntn = N / TN, per_group = GROUP_M * ntn;
+    const int t = blockIdx.x, grp = t / per_group, first = grp * GROUP_M;
+    const int gsz = min(ntm - first, GROUP_M), r = t - grp * per_group;
+    const int m0 = (first + r % gsz) * TM, n0 = (r / gsz) * TN;
     const int KT = K / TK;
 
     if (threadIdx.x == 0) {
@@ -233,21 +247,28 @@ pm_status tensor_map_2d(CUtensorMap *map, int bf16, const void *ptr, uint64_t co
     return PM_OK;
 }
 
-constexpr size_t kTcSmem = (size_t)STAGES * STAGE_BYTES + sizeof(TcShared) + 2048;
+template <int STAGES, int MINB>
+pm_status launch_tc_t(const CUtensorMap &ta, const CUtensorMap &tb, float *c, int n, cudaStream_t st) {
+    constexpr size_t smem = tc_smem<STAGES>();
+    static_assert(MINB * (smem + 1024) <= 228 * 1024, "resident CTAs exceed shared memory");
+    static_assert(MINB * 256 <= 512, "resident CTAs exceed tensor memory");
+    auto fn = k_mm_tc<STAGES, MINB>;
+    PM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    launch_k(fn, (unsigned)((n / TN) * (n / TM)), 128, smem, st, ta, tb, c, n, n, n);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
 
 pm_status launch_tc(const KP &kp, void *const *b, void *stream) {
-    const int n = (int)kp.i(0);
+    const int n = (int)kp.i(0), pipe = (int)kp.i(1);
     for (int a = 0; a < 3; a++)
         if ((uintptr_t)b[a] % 16) return fail(PM_EINVAL, "mm_tc: buffer %d must be 16-byte aligned", a);
     pm_status s;
     CUtensorMap ta, tb;
     if ((s = tensor_map_2d(&ta, 1, b[0], n, n, (uint64_t)n * 2, TK, TM, 1))) return s;
     if ((s = tensor_map_2d(&tb, 1, b[1], n, n, (uint64_t)n * 2, TK, TN, 1))) return s;
-    PM_CUDA_TRY(cudaFuncSetAttribute(k_mm_tc, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kTcSmem));
-    dim3 grid(n / TN, n / TM);
-    launch_k(k_mm_tc, grid, 128, kTcSmem, (cudaStream_t)stream, ta, tb, (float *)b[2], n, n, n);
-    PM_CUDA_TRY(cudaGetLastError());
-    return PM_OK;
+    if (pipe == 0) return launch_tc_t<4, 1>(ta, tb, (float *)b[2], n, (cudaStream_t)stream);
+    return launch_tc_t<2, 2>(ta, tb, (float *)b[2], n, (cudaStream_t)stream);
 }
 
 // After a synchronisation: PM_ETIMEOUT if any CTA's bounded wait ran out

@@ -20,23 +20,37 @@ def dev():
     return torch.device("cuda:0")
 
 
-def run_tc(n, seed):
+def run_tc(n, seed, pipe=1):
     d = dev()
     a = pm_inputs.bf16_bits((n, n), seed)
     bt = pm_inputs.bf16_bits((n, n), seed + 1)
     ta = torch.from_numpy(a.view(np.int16)).to(d)
     tb = torch.from_numpy(bt.view(np.int16)).to(d)
     c = torch.full((n * n,), 7.5, device=d)
-    pm.launch("mm_tc", [ta, tb, c], n=n)
+    pm.launch("mm_tc", [ta, tb, c], n=n, pipe=pipe)
     torch.cuda.synchronize()
     return a, bt, c.cpu().numpy().reshape(n, n)
 
 
+@pytest.mark.parametrize("pipe", [0, 1])
 @pytest.mark.parametrize("n", [256, 512, 1024])
-def test_mm_tc_matches_oracle(n):
-    a, bt, c = run_tc(n, 40 + n)
+def test_mm_tc_matches_oracle(n, pipe):
+    a, bt, c = run_tc(n, 40 + n, pipe)
     ref, rabs = refs.matmul_bf16_tn(a, bt)
     err = np.abs(c.astype(np.float64) - ref) / rabs
+    assert err.max() <= TOL, err.max()
+
+
+@pytest.mark.parametrize("pipe", [0, 1])
+@pytest.mark.parametrize("n", [2304, 4352])
+def test_mm_tc_partial_tile_groups(n, pipe):
+    # 18 and 34 tile rows: the last group of 16 tile rows is partial; every
+    # output row block must still be computed exactly once (sampled rows,
+    # one from each tile row, all columns)
+    a, bt, c = run_tc(n, 60 + n, pipe)
+    rows = np.arange(0, n, 128) + pm_inputs.integers((n // 128,), 61, 0, 127)
+    ref, rabs = refs.matmul_bf16_tn(a[rows], bt)
+    err = np.abs(c[rows].astype(np.float64) - ref) / rabs
     assert err.max() <= TOL, err.max()
 
 
