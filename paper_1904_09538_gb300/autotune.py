@@ -64,7 +64,7 @@ def _time(kernel, variants, bufs, trials, flush_l2=True):
     return np.array(out)
 
 
-def rank_family(kernel="mm_simt", shapes=None, calib_sizes=(1536, 2304), target=7680, trials=5, seed=7,
+def rank_family(kernel="mm_simt", shapes=None, calib_sizes=(3072, 4608), target=7680, trials=5, seed=7,
                 expr=SIMT_MODEL, flops_per_n3=2.0, bytes_fn=None):
     import torch
     shapes = shapes or SIMT_SHAPES

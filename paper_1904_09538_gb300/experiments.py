@@ -63,10 +63,11 @@ def studies():
     """(name, model expression, measurement kernels, modeled kernels) per computation."""
     mm_sizes = list(range(512, 4096 + 1, 128))                # 29 sizes
     mm_twin_sizes = [512, 1024, 1536, 2048, 2560, 3072, 3584, 4096]
+    mm_gm = [GENERIC] + [tagged(t, n) for t, n in (("mm-PF-a", "pfa"), ("mm-PF-b", "pfb"),
+                                                   ("mm-noPF-a", "npa"), ("mm-noPF-b", "npb"))]
     mm = dict(
-        name="matmul",
-        expr=nonlinear([GENERIC] + [tagged(t, n) for t, n in (("mm-PF-a", "pfa"), ("mm-PF-b", "pfb"),
-                                                              ("mm-noPF-a", "npa"), ("mm-noPF-b", "npb"))]),
+        name="matmul", gmem=mm_gm,
+        expr=nonlinear(mm_gm),
         measure=common_measurements() + [(k, {"n": n}) for k in ("mm_pf_a", "mm_pf_b", "mm_nopf_a", "mm_nopf_b")
                                          for n in mm_twin_sizes],
         modeled=[(k, {"n": n}) for k in ("mm_pf", "mm_nopf") for n in mm_sizes],
@@ -92,7 +93,8 @@ def studies():
                     twins.append((k, dict(Np=Np, Nel=Nel, L0=L0, L1=L1)))
         modeled = [(k, dict(Np=Np, Nel=Nel, L0=L0, L1=L1)) for k in variants
                    for Np in (20, 35, 56, 84) for Nel in (1 << 14, 1 << 15, 1 << 16, 1 << 17, 1 << 18)]
-        out.append(dict(name="dg_" + sh, expr=nonlinear([GENERIC] + [tagged(t, n) for t, n in tags]),
+        gm = [GENERIC] + [tagged(t, n) for t, n in tags]
+        out.append(dict(name="dg_" + sh, gmem=gm, expr=nonlinear(gm),
                         measure=common_measurements() + twins, modeled=modeled))
     fd_sizes = [int(round(1024 * 2 ** (i / 7.0))) for i in range(29)]   # 1024 .. 16384, geometric
     fd_twins = [(k, {"n": n}) for k in ("fd_tile_u", "fd_tile_res", "fd_direct_u", "fd_direct_res",
@@ -100,7 +102,8 @@ def studies():
                 for n in (1024, 2048, 4096, 8192, 16384)]
     # the tile variants' result stores are unit-stride AFR-1 patterns, so the
     # generic feature covers them; only the overlapping tile fetches are tagged
-    out.append(dict(name="fd", expr=linear([GENERIC, tagged("fd-tile-u", "tu"), tagged("fd-tile18-u", "t18u")]),
+    fd_gm = [GENERIC, tagged("fd-tile-u", "tu"), tagged("fd-tile18-u", "t18u")]
+    out.append(dict(name="fd", gmem=fd_gm, expr=linear(fd_gm),
                     measure=common_measurements() + fd_twins,
                     modeled=[(k, {"n": n}) for k in ("fd_tile", "fd_tile18", "fd_direct") for n in fd_sizes]))
     return out
@@ -248,6 +251,71 @@ def run_studies(trials=10, names=None, seed=1234, flush_l2=True, study_list=None
     return report
 
 
+def diagnostics(trials=10, seed=1234, flush_l2=True):
+    """The paper's diagnostic experiments on this GPU.
+
+    ab_ratio (Section "Data Motion Features", Table ab_pattern): average cost
+    per load of the prefetching matmul's b fetch pattern over its a pattern,
+    from the two work-removed twins at n = 2048 .. 3584, where overhead is
+    negligible (time / tagged loads).
+
+    madd_only (Section "Illustrative Example"): p_madd calibrated on the madd
+    throughput kernels alone, as a FLOP/s rate against the FP32 peak, and the
+    share of the prefetching matmul's time it accounts for.
+
+    overlap (Section "Modeling Overlap"): per modeled variant, the sum of the
+    separately calibrated costs (linear model: twins for global memory,
+    microbenchmarks for on-chip work) over the measured time -- near 1 means
+    no overlap, well above 1 means hidden on-chip cost -- and the geomean
+    error of the linear and the tanh-overlap model calibrated on the same
+    measurement set."""
+    import torch
+    dev = torch.device("cuda", torch.cuda.current_device())
+    bufs = Buffers(torch, dev, seed)
+    out = {}
+    # -- a vs b pattern
+    rows = []
+    for n in range(2048, 3584 + 1, 256):
+        per = {}
+        for k, tag in (("mm_pf_a", "mm-PF-a"), ("mm_pf_b", "mm-PF-b")):
+            loads = Model("t", "p * f_mem_access_tag:%s" % tag).feature_values(k, n=n)[0]
+            per[k] = measure([(k, {"n": n})], bufs, trials, flush_l2)[0] / loads
+        rows.append({"n": n, "a_s_per_load": per["mm_pf_a"], "b_s_per_load": per["mm_pf_b"],
+                     "b_over_a": per["mm_pf_b"] / per["mm_pf_a"]})
+    out["ab_ratio"] = {"rows": rows, "mean_b_over_a": float(np.mean([r["b_over_a"] for r in rows]))}
+    # -- madd-only calibration
+    m = Model("f_wall_time", "p_launch * f_sync_kernel_launch + p_madd * f_op_float32_madd")
+    cal = generate(["flops_pattern", "dtype:0", "op:2"])
+    X = np.stack([m.feature_values(k, **p) for k, p in cal])
+    t = measure(cal, bufs, trials, flush_l2)
+    p, rep = m.fit(X, t)
+    sizes = [512, 1024, 1536, 2048, 3072, 4096]
+    tm = measure([("mm_pf", {"n": n}) for n in sizes], bufs, trials, flush_l2)
+    share = [float(p[1] * m.feature_values("mm_pf", n=n)[1] / tt) for n, tt in zip(sizes, tm)]
+    out["madd_only"] = {"p_madd_s_per_subgroup_op": float(p[1]), "rate_flops": 64.0 / float(p[1]),
+                        "fit": rep, "mm_pf_sizes": sizes, "mm_pf_madd_share": share}
+    # -- overlap analysis, linear vs tanh-overlap on the same measurement sets
+    res = {}
+    for st in studies():
+        if st["name"] == "dg_32x8":
+            continue
+        gm = st["gmem"]
+        exprs = {"linear": linear(gm), "nonlinear": nonlinear(gm)}
+        rep_s = run_studies(trials, seed=seed, flush_l2=flush_l2,
+                            study_list=[dict(st, name=st["name"] + "_" + kind, expr=e) for kind, e in exprs.items()])
+        per = {}
+        lin = rep_s[st["name"] + "_linear"]
+        non = rep_s[st["name"] + "_nonlinear"]
+        for v in lin["variants"]:
+            ratio = [r["predicted_s"] / r["measured_s"] for r in lin["rows"] if r["kernel"] == v]
+            per[v] = {"separate_costs_over_measured": geomean(ratio),
+                      "linear_geomean_err": lin["variants"][v]["geomean_rel_err"],
+                      "nonlinear_geomean_err": non["variants"][v]["geomean_rel_err"]}
+        res[st["name"]] = per
+    out["overlap"] = res
+    return out
+
+
 def illustrative(trials=20, seed=1234, flush_l2=True):
     """Configuration 1: t = p_f flops + p_g gmem + p_s smem + p_l work-groups on
     the prefetching matmul at n = 256..768 (rank-2 design: minimum-norm fit),
@@ -277,6 +345,7 @@ if __name__ == "__main__":
     flush = "--no-flush" not in sys.argv
     args = [a for a in sys.argv[1:] if not a.startswith("--")]
     out = {"illustrative": illustrative(flush_l2=flush), "studies": run_studies(flush_l2=flush),
-           "sweep": run_studies(flush_l2=flush, study_list=sweep_studies())}
+           "sweep": run_studies(flush_l2=flush, study_list=sweep_studies()),
+           "diagnostics": diagnostics(flush_l2=flush)}
     sys.argv = [sys.argv[0]] + args
     json.dump(out, open(sys.argv[1], "w") if len(sys.argv) > 1 else sys.stdout, indent=1)

@@ -89,8 +89,17 @@ GENERATORS = [
               lambda p: dict(p, L1=256 // p["L0"])),
     Generator("dg_dmpf", ["dg", "modeled"], {"Np": [20, 35, 56, 84], "Nel": POW(14, 18), "L0": [16, 32]},
               lambda p: dict(p, L1=256 // p["L0"])),
+    Generator("dg_upf", ["dg", "modeled"], {"Np": [20, 35, 56, 84], "Nel": POW(14, 18), "L0": [16]},
+              lambda p: dict(p, L1=16)),
+    Generator("dg_dmpft", ["dg", "modeled"], {"Np": [20, 35, 56, 84], "Nel": POW(14, 18), "L0": [16, 32]},
+              lambda p: dict(p, L1=256 // p["L0"])),
     Generator("fd_tile", ["finite_diff", "modeled"], {"n": POW(10, 14)}),
+    Generator("fd_tile18", ["finite_diff", "modeled"], {"n": POW(10, 14)}),
     Generator("fd_direct", ["finite_diff", "modeled"], {"n": POW(10, 14)}),
+    Generator("mm_tc", ["matmul_tc", "modeled"], {"n": POW(10, 14)}),
+    Generator("mm_simt", ["matmul_tiles", "autotune"],
+              {"n": [7680], "BM": [64, 96, 128, 256], "BN": [64, 128, 256], "BK": [32, 64]}),
+    Generator("fd_block", ["stencil_tiles", "autotune"], {"n": [16384], "BX": [32, 64, 128], "BY": [4, 8, 16, 32]}),
 ]
 
 
