@@ -264,7 +264,7 @@ def run_ours(args):
         try:
             tj = json.load(open(tpath))
             ent = tj.get(dom)
-            if ent and ent.get("source_sha") == source_sha(ent.get("source", "pm_suite.cu")):
+            if ent and ent.get("source_sha") == source_sha(ent.get("source", "pm_suite.cu"), dom.split("<")[0]):
                 traffic = ent["dram_bytes_per_launch"]
         except Exception:
             traffic = None
@@ -303,11 +303,24 @@ def run_ours(args):
         dist.destroy_process_group()
 
 
-def source_sha(f="pm_suite.cu"):
-    """Hash of the source file that defines a kernel: a recorded DRAM traffic
-    figure is valid only while that file is unchanged."""
+def source_sha(f="pm_suite.cu", kernel="k_stream"):
+    """Hash of a kernel's definition (from its __global__ line to the closing
+    brace of its body): a recorded DRAM traffic figure is valid only while
+    that definition is unchanged."""
     import hashlib
-    return hashlib.sha256(open(os.path.join(ROOT, "paper_1904_09538_gb300", "csrc", f), "rb").read()).hexdigest()[:16]
+    import re
+    src = open(os.path.join(ROOT, "paper_1904_09538_gb300", "csrc", f)).read()
+    m = re.search(r"__global__[^;{]*\b%s\s*\(" % re.escape(kernel), src)
+    if not m:
+        return None
+    i = src.index("{", m.end())
+    depth, j = 0, i
+    while j < len(src):
+        depth += {"{": 1, "}": -1}.get(src[j], 0)
+        j += 1
+        if depth == 0:
+            break
+    return hashlib.sha256(src[m.start():j].encode()).hexdigest()[:16]
 
 
 def e2e_measure(pm, S, variants, torch):
@@ -390,10 +403,14 @@ def fit_throughput(pm, torch, dev):
     for _ in range(reps_n):
         pb, reps = plan.run(Xc, tc, pc)
     dt_b = (time.perf_counter() - t0) / reps_n
-    # plain per-model fits on a subset (time per model)
+    # plain per-model fits on a subset (time per model), after one untimed
+    # fit that pays the one-time library initialisation of the small solves
     sub = list(range(0, K, 8)) + list(range(1, K, 8))
     errs = []
     o = np.cumsum([0] + [len(p) for p in p0s])
+    pag.lm_fit(models[0], torch.from_numpy(Xs[0].astype(np.float32)).to(dev),
+               torch.from_numpy(ts[0].astype(np.float32)).to(dev), p0s[0])
+    torch.cuda.synchronize()
     t0 = time.perf_counter()
     for k in sub:
         Xd = torch.from_numpy(Xs[k].astype(np.float32)).to(dev)

@@ -91,7 +91,7 @@ def lm_fit(model, X, t, p0, max_iter=200, xtol=1e-12):
         J = jacobian(model, X, t, p.detach())
         A = torch.stack([_jtv(model, X, t, p.detach(), J[:, i]) for i in range(J.shape[1])], dim=1)
         Sd = s
-        return float((r.double() ** 2).sum()), b * Sd, A * Sd[:, None] * Sd[None, :]
+        return float((r.detach().double() ** 2).sum()), b * Sd, A * Sd[:, None] * Sd[None, :]
 
     ssr, b, A = ssr_b_A(q)
     for it in range(1, max_iter + 1):

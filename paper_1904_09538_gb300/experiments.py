@@ -278,21 +278,23 @@ def diagnostics(trials=10, seed=1234, flush_l2=True):
     for n in range(2048, 3584 + 1, 256):
         per = {}
         for k, tag in (("mm_pf_a", "mm-PF-a"), ("mm_pf_b", "mm-PF-b")):
-            loads = Model("t", "p * f_mem_access_tag:%s" % tag).feature_values(k, n=n)[0]
+            loads = Model("f_wall_time", "p_x * f_mem_access_tag:%s" % tag).feature_values(k, n=n)[0]
             per[k] = measure([(k, {"n": n})], bufs, trials, flush_l2)[0] / loads
         rows.append({"n": n, "a_s_per_load": per["mm_pf_a"], "b_s_per_load": per["mm_pf_b"],
                      "b_over_a": per["mm_pf_b"] / per["mm_pf_a"]})
     out["ab_ratio"] = {"rows": rows, "mean_b_over_a": float(np.mean([r["b_over_a"] for r in rows]))}
     # -- madd-only calibration
-    m = Model("f_wall_time", "p_launch * f_sync_kernel_launch + p_madd * f_op_float32_madd")
+    # the madd kernels are sized to a similar total time, so a launch term
+    # would be collinear with the madd count: p_madd alone
+    m = Model("f_wall_time", "p_madd * f_op_float32_madd")
     cal = generate(["flops_pattern", "dtype:0", "op:2"])
     X = np.stack([m.feature_values(k, **p) for k, p in cal])
     t = measure(cal, bufs, trials, flush_l2)
     p, rep = m.fit(X, t)
     sizes = [512, 1024, 1536, 2048, 3072, 4096]
     tm = measure([("mm_pf", {"n": n}) for n in sizes], bufs, trials, flush_l2)
-    share = [float(p[1] * m.feature_values("mm_pf", n=n)[1] / tt) for n, tt in zip(sizes, tm)]
-    out["madd_only"] = {"p_madd_s_per_subgroup_op": float(p[1]), "rate_flops": 64.0 / float(p[1]),
+    share = [float(p[0] * m.feature_values("mm_pf", n=n)[0] / tt) for n, tt in zip(sizes, tm)]
+    out["madd_only"] = {"p_madd_s_per_subgroup_op": float(p[0]), "rate_flops": 64.0 / float(p[0]),
                         "fit": rep, "mm_pf_sizes": sizes, "mm_pf_madd_share": share}
     # -- overlap analysis, linear vs tanh-overlap on the same measurement sets
     res = {}
