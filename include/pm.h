@@ -196,8 +196,13 @@ pm_status pm_run(int32_t kernel, const pm_param *p, size_t np,
 
 /* pm_run with HOST buffers: copies inputs host->device, runs as pm_run, and
  * copies outputs device->host, all on `stream`; device memory is allocated
- * with cudaMallocAsync and freed before returning.  *copy_ms (nullable)
- * receives the total time of the copies. */
+ * with cudaMallocAsync and freed before returning.  The first call on a device
+ * raises the release threshold of that device's default memory pool to the
+ * maximum, so freed staging memory stays reserved for later calls (and for
+ * any other cudaMallocAsync user of that pool) instead of being unmapped at
+ * every synchronisation.  Pinned host buffers copy at the link rate; pageable
+ * ones are staged by the driver.  *copy_ms (nullable) receives the total time
+ * of the copies. */
 pm_status pm_run_host(int32_t kernel, const pm_param *p, size_t np,
                       void *const *host_bufs, size_t nbufs, const pm_run_opts *opts,
                       void *stream, float *trial_ms, pm_timing *out, double *copy_ms);
