@@ -19,6 +19,7 @@ Timing: pm_run, `trials` device-timed launches after 2 warm-ups (mean, trials
 above 5x the median dropped).  Inputs are seeded uniform / normal values.
 """
 import math
+import re
 
 import numpy as np
 
@@ -37,6 +38,17 @@ def nonlinear(gmem_terms, overhead=OVERHEAD, onchip=ONCHIP):
     co = "(%s)" % onchip
     return ("%s + %s * (tanh(p_edge * (%s - %s)) + 1) / 2 + %s * (tanh(p_edge * (%s - %s)) + 1) / 2"
             % (overhead, cg, cg, co, co, co, cg))
+
+
+def partial(gmem_terms, overhead=OVERHEAD, onchip=ONCHIP):
+    """Eq. nonlinear_model with one more parameter, p_part, for partial overlap
+    (the variation of Eq. tanh the paper suggests): the smaller of the two
+    cost groups is added with weight p_part (0: full overlap, 1: none)."""
+    cg = "(%s)" % " + ".join(gmem_terms)
+    co = "(%s)" % onchip
+    hi = "%s * (tanh(p_edge * (%s - %s)) + 1) / 2 + %s * (tanh(p_edge * (%s - %s)) + 1) / 2" % (cg, cg, co, co, co, cg)
+    lo = "%s * (tanh(p_edge * (%s - %s)) + 1) / 2 + %s * (tanh(p_edge * (%s - %s)) + 1) / 2" % (cg, co, cg, co, cg, co)
+    return "%s + %s + p_part * (%s)" % (overhead, hi, lo)
 
 
 def linear(gmem_terms, overhead=OVERHEAD, onchip=ONCHIP):
@@ -267,8 +279,8 @@ def diagnostics(trials=10, seed=1234, flush_l2=True):
     separately calibrated costs (linear model: twins for global memory,
     microbenchmarks for on-chip work) over the measured time -- near 1 means
     no overlap, well above 1 means hidden on-chip cost -- and the geomean
-    error of the linear and the tanh-overlap model calibrated on the same
-    measurement set."""
+    error of the linear, the tanh-overlap and the partial-overlap model
+    calibrated on the same measurement set."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     bufs = Buffers(torch, dev, seed)
@@ -299,20 +311,21 @@ def diagnostics(trials=10, seed=1234, flush_l2=True):
     # -- overlap analysis, linear vs tanh-overlap on the same measurement sets
     res = {}
     for st in studies():
-        if st["name"] == "dg_32x8":
-            continue
         gm = st["gmem"]
-        exprs = {"linear": linear(gm), "nonlinear": nonlinear(gm)}
+        exprs = {"linear": linear(gm), "nonlinear": nonlinear(gm), "partial": partial(gm)}
+        if len(set(re.findall(r"\bp_\w+", exprs["partial"]))) > 16:   # the fit's parameter limit
+            del exprs["partial"]
         rep_s = run_studies(trials, seed=seed, flush_l2=flush_l2,
                             study_list=[dict(st, name=st["name"] + "_" + kind, expr=e) for kind, e in exprs.items()])
         per = {}
         lin = rep_s[st["name"] + "_linear"]
-        non = rep_s[st["name"] + "_nonlinear"]
         for v in lin["variants"]:
             ratio = [r["predicted_s"] / r["measured_s"] for r in lin["rows"] if r["kernel"] == v]
-            per[v] = {"separate_costs_over_measured": geomean(ratio),
-                      "linear_geomean_err": lin["variants"][v]["geomean_rel_err"],
-                      "nonlinear_geomean_err": non["variants"][v]["geomean_rel_err"]}
+            per[v] = {"separate_costs_over_measured": geomean(ratio)}
+            for kind in exprs:
+                per[v][kind + "_geomean_err"] = rep_s[st["name"] + "_" + kind]["variants"][v]["geomean_rel_err"]
+        if "partial" in exprs:
+            per["p_part"] = rep_s[st["name"] + "_partial"]["params"]["p_part"]
         res[st["name"]] = per
     out["overlap"] = res
     return out
