@@ -57,6 +57,10 @@ def lib():
         _lib.oracle_counts.argtypes = [ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong), ctypes.c_int,
                                        ctypes.POINTER(_Orec), ctypes.c_int, ctypes.POINTER(ctypes.c_int)]
         _lib.oracle_counts.restype = ctypes.c_int
+        _lib.oracle_counts_twin.argtypes = [ctypes.c_char_p, ctypes.c_char_p, ctypes.POINTER(ctypes.c_longlong),
+                                            ctypes.c_int, ctypes.POINTER(_Orec), ctypes.c_int,
+                                            ctypes.POINTER(ctypes.c_int)]
+        _lib.oracle_counts_twin.restype = ctypes.c_int
         _lib.oracle_count_example.argtypes = [ctypes.c_longlong, ctypes.c_longlong]
         _lib.oracle_count_example.restype = ctypes.c_longlong
         assert _lib.oracle_sizeof_orec() == ctypes.sizeof(_Orec)
@@ -97,8 +101,10 @@ def dims(kernel, params):
     return KERNELS[kernel][1]
 
 
-def raw_counts(kernel, **params):
-    """Enumerate the loop domain of `kernel`; returns a list of record dicts."""
+def raw_counts(kernel, remove=None, **params):
+    """Enumerate the loop domain of `kernel`; returns a list of record dicts.
+    remove: global-access tags for work removal (Algorithm 3): the counts are
+    then those of the twin derived from `kernel`'s descriptor."""
     names = KERNELS[kernel][0]
     vals = []
     for nm in names:
@@ -110,7 +116,11 @@ def raw_counts(kernel, **params):
     cap = 256
     out = (_Orec * cap)()
     n = ctypes.c_int(0)
-    rc = lib().oracle_counts(kernel.encode(), arr, len(vals), out, cap, ctypes.byref(n))
+    if remove is None:
+        rc = lib().oracle_counts(kernel.encode(), arr, len(vals), out, cap, ctypes.byref(n))
+    else:
+        rc = lib().oracle_counts_twin(kernel.encode(), "|".join(remove).encode(), arr, len(vals), out, cap,
+                                      ctypes.byref(n))
     if rc != 0:
         raise ValueError("oracle_counts(%s, %r) failed: %d" % (kernel, params, rc))
     recs = []

@@ -124,6 +124,9 @@ struct ctx {
     long long bar_cur, bar_min, bar_max;
     kset sgset;              /* distinct statement instances of the current SG */
     int err;
+    /* work removal (Algorithm 3): parent statement -> its twin statements */
+    int twin, tdest;
+    int tmap_n[MAXSTMT], tmap[MAXSTMT][8];
 };
 
 static int add_site(ctx *c, const char *tag, int mem, int dir, const char *dtype, int dsize, idx_fn f) {
@@ -142,8 +145,14 @@ static int add_stmt(ctx *c, int nloop, int dt, int nadd, int nmul, int nmadd) {
 }
 static void stmt_site(ctx *c, int st, int site) { stmt_t *s = &c->stmt[st]; s->site[s->nsite++] = site; }
 
-/* one executed statement instance of the current work-item */
+static void X_exec(ctx *c, int st, const long long *lv);
+/* one executed statement instance of the current work-item; in work-removal
+ * mode the parent statement is replaced by the statements derived from it */
 static void X(ctx *c, int st, const long long *lv) {
+    if (!c->twin) { X_exec(c, st, lv); return; }
+    for (int k = 0; k < c->tmap_n[st]; k++) X_exec(c, c->tmap[st][k], lv);
+}
+static void X_exec(ctx *c, int st, const long long *lv) {
     const stmt_t *S = &c->stmt[st];
     long long key = st;
     for (int i = 0; i < S->nloop; i++) {
@@ -191,7 +200,7 @@ static void X(ctx *c, int st, const long long *lv) {
         }
     }
 }
-static void BAR(ctx *c) { c->bar_cur++; }
+static void BAR(ctx *c) { if (!c->twin) c->bar_cur++; }   /* work removal drops barriers with the local memory */
 
 /* ---------------------------------------------------------------- helpers */
 #define G0 (g[0])
@@ -1119,6 +1128,55 @@ typedef struct {
     unsigned long long wi, sg, footprint;
 } orec;
 
+/* ======================================================================
+ * Work removal (Algorithm 3) on a parent descriptor: every statement is
+ * replaced by one "tgt = tgt + load" statement (one add) per global load it
+ * contains that is not in the removal set, and by "store = tgt" for a kept
+ * global store, at the same loop point and under the same guards; local
+ * memory accesses, arithmetic and barriers go.  If no global store is kept,
+ * every work-item finally writes tgt to its own entry of tgt_dest
+ * (row-major over the global index space).
+ * ====================================================================== */
+static long long ix_tgt_dest(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)lv;
+    const long long L0 = c->wg[0], L1 = c->wg[1], L2 = c->wg[2];
+    return ((g[2] * L2 + l[2]) * (c->grid[1] * L1) + g[1] * L1 + l[1]) * (c->grid[0] * L0) + g[0] * L0 + l[0];
+}
+static int make_twin(ctx *c, const char *remove) {
+    /* remove: tags separated by '|' */
+    const int nst = c->nstmt;
+    int kept_store = 0, first_dt = -1;
+    const char *dname = "float32";
+    int dsize = 4;
+    for (int st = 0; st < nst; st++) {
+        stmt_t S = c->stmt[st];
+        c->tmap_n[st] = 0;
+        for (int a = 0; a < S.nsite; a++) {
+            const site_t *x = &c->site[S.site[a]];
+            if (x->mem != MEM_GLOBAL) continue;
+            char key[64];
+            snprintf(key, sizeof key, "|%s|", x->tag);
+            char all[1024];
+            snprintf(all, sizeof all, "|%s|", remove);
+            if (strstr(all, key)) continue;
+            if (c->nstmt >= MAXSTMT || c->tmap_n[st] >= 8) return -1;
+            int t = add_stmt(c, S.nloop, S.dt, x->dir == DIR_LOAD ? 1 : 0, 0, 0);
+            stmt_site(c, t, S.site[a]);
+            c->tmap[st][c->tmap_n[st]++] = t;
+            if (x->dir == DIR_STORE) kept_store = 1;
+            else if (first_dt < 0) { first_dt = S.dt; dname = x->dtype; dsize = x->dsize; }
+        }
+    }
+    c->tdest = -1;
+    if (!kept_store) {
+        if (c->nstmt >= MAXSTMT || c->nsite >= MAXSITE) return -1;
+        c->tdest = add_stmt(c, 0, first_dt < 0 ? DT_F32 : first_dt, 0, 0, 0);
+        stmt_site(c, c->tdest, add_site(c, "tgt_dest", MEM_GLOBAL, DIR_STORE, dname, dsize, ix_tgt_dest));
+    }
+    c->twin = 1;
+    return 0;
+}
+
 static const struct { const char *name; int fam, v; } KTAB[] = {
     {"stream", 0, 0}, {"fma", 1, 0}, {"smem", 2, 0}, {"barrier", 3, 0}, {"overlap", 4, 0}, {"empty", 5, 0},
     {"mm_pf", 6, 0}, {"mm_nopf", 6, 1}, {"mm_pf_a", 6, 2}, {"mm_pf_b", 6, 3}, {"mm_nopf_a", 6, 4}, {"mm_nopf_b", 6, 5},
@@ -1132,7 +1190,19 @@ static const struct { const char *name; int fam, v; } KTAB[] = {
     {"fd_block", 11, 0},
 };
 
+static int counts_impl(const char *kernel, const char *remove, const long long *P, int nP, orec *out, int cap,
+                       int *n_out);
 int oracle_counts(const char *kernel, const long long *P, int nP, orec *out, int cap, int *n_out) {
+    return counts_impl(kernel, NULL, P, nP, out, cap, n_out);
+}
+/* counts of the work-removed twin of `kernel` (Algorithm 3), global accesses
+ * whose tags are listed in `remove` ('|'-separated) removed */
+int oracle_counts_twin(const char *kernel, const char *remove, const long long *P, int nP, orec *out, int cap,
+                       int *n_out) {
+    return counts_impl(kernel, remove ? remove : "", P, nP, out, cap, n_out);
+}
+static int counts_impl(const char *kernel, const char *remove, const long long *P, int nP, orec *out, int cap,
+                       int *n_out) {
     ctx *c = (ctx *)calloc(1, sizeof(ctx));
     int fam = -1, v = 0, rc = 0;
     for (size_t i = 0; i < sizeof KTAB / sizeof KTAB[0]; i++)
@@ -1154,6 +1224,7 @@ int oracle_counts(const char *kernel, const long long *P, int nP, orec *out, int
     case 11: rc = setup_fdb(c); break;
     }
     if (rc) { free(c); return -2; }
+    if (remove && make_twin(c, remove)) { free(c); return -5; }
     for (int s = 0; s < c->nsite; s++) ks_init(&c->ss[s].foot, 1024);
     ks_init(&c->sgset, 1024);
     c->bar_min = -1; c->bar_max = -1;
@@ -1170,6 +1241,7 @@ int oracle_counts(const char *kernel, const long long *P, int nP, orec *out, int
                 c->l[0] = t % L0; c->l[1] = (t / L0) % L1; c->l[2] = t / (L0 * L1);
                 c->bar_cur = 0;
                 c->walk(c);
+                if (c->twin && c->tdest >= 0) X_exec(c, c->tdest, NULL);
                 if (c->bar_min < 0 || c->bar_cur < c->bar_min) c->bar_min = c->bar_cur;
                 if (c->bar_cur > c->bar_max) c->bar_max = c->bar_cur;
             }

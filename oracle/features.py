@@ -28,13 +28,15 @@ def _afr_str(acc, foot):
     return str(f.numerator) if f.denominator == 1 else "%d/%d" % (f.numerator, f.denominator)
 
 
-def features(kernel, **params):
+def features(kernel, remove=None, **params):
     """Feature records of one kernel instance, from brute-force enumeration.
 
     Each record: name, count (at its granularity), gran, and for memory
     accesses the pattern fields (tag, mem, dtype, dir, lstr, gstr, afr).
+    remove: global-access tags; the records are then those of the
+    work-removed twin derived from this kernel's descriptor (Algorithm 3).
     """
-    recs = raw_counts(kernel, **params)
+    recs = raw_counts(kernel, remove=remove, **params)
     wdim, gdim = dims(kernel, params)
     out = []
     for r in recs:
