@@ -242,14 +242,14 @@ def run_ours(args):
     if world > 1:
         dist.barrier()
     clk = clocks.stop()
-    elapsed = t_start.elapsed_time(t_end) * 1e-3
-    if world > 1:
-        tt = torch.tensor([elapsed], device=dev)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        elapsed = float(tt.item())
+    from paper_1904_09538_gb300 import replicas
     bytes_per_step = sum(x[3] for x in prepared) * args.trials
-    total_bytes = bytes_per_step * args.steps * world
-    value = total_bytes / elapsed / 1e9
+    value, elapsed = replicas.job_throughput(bytes_per_step * args.steps, t_start.elapsed_time(t_end) * 1e-3,
+                                             dist, dev)
+    value /= 1e9
+    geo_rank = math.exp(sum(math.log(max(e, 1e-12)) for e in all_errs) / len(all_errs)) if all_errs else None
+    rank_reports = replicas.gather_reports({"rank": rank, "heldout_geomean": geo_rank,
+                                            "fit_status": sorted(set(fit_status))}, dist)
 
     # roofline of the dominant kernel instantiation (largest share of device time)
     per = {}
@@ -290,6 +290,8 @@ def run_ours(args):
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,
     }
+    if world > 1:
+        line["ranks"] = rank_reports
     if args.dump and rank == 0:
         json.dump([{"kernel": k, "params": p, "instance": inst, "mean_s": last_times[i], "bytes": nb,
                     "GB/s": nb / last_times[i] / 1e9 if last_times[i] > 0 else None}
