@@ -309,6 +309,16 @@ static void walk_smem(ctx *c) {
     }
     X(c, 3, NULL);          /* out[gtid] = s[lid0] */
 }
+static void walk_smem2d(ctx *c) {
+    long long lv[1];
+    X(c, 0, NULL);
+    BAR(c);
+    for (lv[0] = 0; lv[0] < c->P[0] / 4; lv[0]++) {
+        X(c, 1, lv);
+        X(c, 2, lv);
+    }
+    X(c, 3, NULL);
+}
 static int setup_smem(ctx *c) {
     long long R = c->P[0], sync = c->P[1], G = c->P[2];
     if (R < 4 || R % 4 || sync < 0 || sync > 1 || G < 1) return -1;
@@ -327,6 +337,42 @@ static int setup_smem(ctx *c) {
     stmt_site(c, s3, add_site(c, "s_fin", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_lA));
     stmt_site(c, s3, add_site(c, "out", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_lin));
     c->walk = walk_smem;
+    return 0;
+}
+
+/* 2-D local memory shuffle kernel (local accesses with a lid(1) stride, the
+ * pattern of the stencil tiles' local memory).  P = {R, T, G}.  T x T
+ * work-groups, local index a = T lid1 + lid0: each work-item stores its
+ * element at slot a, passes a barrier, moves it between slots a and T^2 + a
+ * R/2 times (R local accesses in the loop), and writes it to global memory
+ * at G0-major offset T^2 gid0 + a. */
+static long long ix_l2A(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; (void)lv; return c->P[1] * L1_ + L0_;
+}
+static long long ix_l2B(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; (void)lv; long long T = c->P[1]; return T * T + T * L1_ + L0_;
+}
+static long long ix_l2g(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)lv; long long T = c->P[1]; return T * T * G0 + T * L1_ + L0_;
+}
+static int setup_smem2d(ctx *c) {
+    long long R = c->P[0], T = c->P[1], G = c->P[2];
+    if (R < 4 || R % 4 || (T != 16 && T != 18) || G < 1) return -1;
+    c->grid[0] = G; c->grid[1] = 1; c->grid[2] = 1;
+    c->wg[0] = T; c->wg[1] = T; c->wg[2] = 1;
+    int s0 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+    stmt_site(c, s0, add_site(c, "in", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_l2g));
+    stmt_site(c, s0, add_site(c, "s_init", MEM_LOCAL, DIR_STORE, "float32", 4, ix_l2A));
+    int s1 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+    stmt_site(c, s1, add_site(c, "s_ldA", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_l2A));
+    stmt_site(c, s1, add_site(c, "s_stB", MEM_LOCAL, DIR_STORE, "float32", 4, ix_l2B));
+    int s2 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+    stmt_site(c, s2, add_site(c, "s_ldB", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_l2B));
+    stmt_site(c, s2, add_site(c, "s_stA", MEM_LOCAL, DIR_STORE, "float32", 4, ix_l2A));
+    int s3 = add_stmt(c, 0, DT_F32, 0, 0, 0);
+    stmt_site(c, s3, add_site(c, "s_fin", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_l2A));
+    stmt_site(c, s3, add_site(c, "out", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_l2g));
+    c->walk = walk_smem2d;
     return 0;
 }
 
@@ -1188,6 +1234,7 @@ static const struct { const char *name; int fam, v; } KTAB[] = {
     {"mm_simt", 9, 0},
     {"mm_tc", 10, 0},
     {"fd_block", 11, 0},
+    {"smem2d", 12, 0},
 };
 
 static int counts_impl(const char *kernel, const char *remove, const long long *P, int nP, orec *out, int cap,
@@ -1222,6 +1269,7 @@ static int counts_impl(const char *kernel, const char *remove, const long long *
     case 9: rc = setup_simt(c); break;
     case 10: rc = setup_tc(c); break;
     case 11: rc = setup_fdb(c); break;
+    case 12: rc = setup_smem2d(c); break;
     }
     if (rc) { free(c); return -2; }
     if (remove && make_twin(c, remove)) { free(c); return -5; }

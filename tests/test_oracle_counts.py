@@ -299,3 +299,21 @@ def test_smem_and_barrier_counts(R, sync):
     e = features("empty", G=64)
     assert single(e, "groups") == 64 and single(e, "launch") == 1
     assert [f for f in e if f["kind"] == "mem"] == []
+
+
+@pytest.mark.parametrize("T", [16, 18])
+@pytest.mark.parametrize("R,G", [(4, 1), (64, 3)])
+def test_smem2d_counts(T, R, G):
+    # 2-D local shuffle: R local accesses per work-item in the loop, lid(1)
+    # stride T; a T x T work-group has ceil(T^2 / 32) sub-groups
+    fs = features("smem2d", R=R, T=T, G=G)
+    loc = [f for f in fs if f["kind"] == "mem" and f["mem"] == "local"]
+    assert sum(f["count_wi"] for f in loc) == G * T * T * (R + 2)
+    sgs = G * (-(-T * T // 32))
+    for f in loc:
+        assert f["lstr"] == (1, T) and f["gran"] == "SG"
+        assert f["count"] == sgs * (R // 4 if f["tag"] in ("s_ldA", "s_stB", "s_ldB", "s_stA") else 1)
+        assert f["footprint"] == T * T
+    g = by_tag(fs, "in")
+    assert g["count"] == g["footprint"] == G * T * T and g["lstr"] == (1, T) and g["gstr"] == (T * T,)
+    assert single(fs, "sync") == 1 and single(fs, "groups") == G
