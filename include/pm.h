@@ -51,7 +51,10 @@ typedef struct {
 /* ---------------------------------------------------------------- kernels */
 
 /* Kernel registry.  Names: the calibration suite "stream", "fma", "smem",
- * "barrier", "overlap", "empty" (Section "Measurement Kernel Design");
+ * "barrier", "overlap", "empty" (Section "Measurement Kernel Design"), and
+ * "smem2d" (local accesses with a lid(1) stride T = 16 or 18 in T x T
+ * work-groups, parameters R, T, G: the local-memory pattern of the stencil
+ * tiles, for models that split local-memory features by stride);
  * matmul "mm_pf", "mm_nopf" and the work-removed twins "mm_pf_a", "mm_pf_b",
  * "mm_nopf_a", "mm_nopf_b" (Section "Matrix Multiplication", Algorithm 3);
  * DG "dg_nopf", "dg_upf", "dg_dmpf", "dg_dmpft" and twins "dg_nopf_u",

@@ -175,6 +175,38 @@ pm_status counts_smem(const KP &kp, std::vector<pm_feature> &v) {
     return PM_OK;
 }
 
+// 2-D local shuffle: T x T work-group, local index T lid1 + lid0, all lanes
+// active, ceil(T^2 / 32) sub-groups per group.
+pm_status counts_smem2d(const KP &kp, std::vector<pm_feature> &v) {
+    i64 R = kp.i(0), T = kp.i(1), G = kp.i(2);
+    u64 W = (u64)(G * T * T), S = (u64)(G * ((T * T + 31) / 32)), it = (u64)(R / 4), TT = (u64)(T * T);
+    Out o(v);
+    auto gsite = [&](const char *tag, int dir) {
+        Site s{};
+        s.tag = tag; s.mem = GL; s.dir = dir; s.dtype = "float32"; s.dsize = 4;
+        s.nl = 2; s.l[0] = 1; s.l[1] = T; s.ng = 1; s.g[0] = T * T;
+        s.wi = W; s.sg = S; s.foot = W;
+        return s;
+    };
+    auto lsite = [&](const char *tag, int dir, u64 reps, i64 loop) {
+        Site s{};
+        s.tag = tag; s.mem = LO; s.dir = dir; s.dtype = "float32"; s.dsize = 4;
+        s.nl = 2; s.l[0] = 1; s.l[1] = T; s.ng = 1; s.g[0] = 0; s.loop = loop;
+        s.wi = W * reps; s.sg = S * reps; s.foot = TT;
+        return s;
+    };
+    o.site(gsite("in", LD));
+    o.site(lsite("s_init", ST, 1, 0));
+    o.site(lsite("s_ldA", LD, it, 0));
+    o.site(lsite("s_stB", ST, it, 0));
+    o.site(lsite("s_ldB", LD, it, 0));
+    o.site(lsite("s_stA", ST, it, 0));
+    o.site(lsite("s_fin", LD, 1, 0));
+    o.site(gsite("out", ST));
+    o.finish(1, (u64)G);
+    return PM_OK;
+}
+
 pm_status counts_barrier(const KP &kp, std::vector<pm_feature> &v) {
     i64 B = kp.i(0), G = kp.i(1);
     u64 T = (u64)G * 256;
@@ -665,6 +697,12 @@ pm_status validate(const KP &kp) {
         if (kp.i(1) < 0 || kp.i(1) > 1) return fail(PM_EINVAL, "%s: sync must be 0 or 1", nm);
         if (kp.i(2) < 1 || kp.i(2) > (1LL << 23)) return fail(PM_EINVAL, "%s: G must be 1..2^23", nm);
         return PM_OK;
+    case FAM_SMEM2D:
+        if (kp.i(0) < 4 || kp.i(0) % 4 || kp.i(0) > (1LL << 30))
+            return fail(PM_EINVAL, "%s: R must be a positive multiple of 4", nm);
+        if (kp.i(1) != 16 && kp.i(1) != 18) return fail(PM_EINVAL, "%s: T must be 16 or 18", nm);
+        if (kp.i(2) < 1 || kp.i(2) > (1LL << 23)) return fail(PM_EINVAL, "%s: G must be 1..2^23", nm);
+        return PM_OK;
     case FAM_BARRIER:
         if (kp.i(0) < 0 || kp.i(0) > (1LL << 30)) return fail(PM_EINVAL, "%s: B must be >= 0", nm);
         if (kp.i(1) < 1 || kp.i(1) > (1LL << 23)) return fail(PM_EINVAL, "%s: G must be 1..2^23", nm);
@@ -730,6 +768,7 @@ pm_status counts(const KP &kp, std::vector<pm_feature> &out) {
     case FAM_STREAM: return counts_stream(kp, out);
     case FAM_FMA: return counts_fma(kp, out);
     case FAM_SMEM: return counts_smem(kp, out);
+    case FAM_SMEM2D: return counts_smem2d(kp, out);
     case FAM_BARRIER: return counts_barrier(kp, out);
     case FAM_OVERLAP: return counts_overlap(kp, out);
     case FAM_EMPTY: return counts_empty(kp, out);
@@ -758,6 +797,12 @@ pm_status buffers(const KP &kp, std::vector<BufSpec> &b) {
         uint64_t T = (uint64_t)kp.i(3) * 256;
         b.push_back({"seed", (int)kp.i(0), PM_IN, T});
         b.push_back({"out", (int)kp.i(0), PM_OUT, T});
+        break;
+    }
+    case FAM_SMEM2D: {
+        uint64_t n = (uint64_t)kp.i(2) * (uint64_t)kp.i(1) * (uint64_t)kp.i(1);
+        b.push_back({"in", PM_F32, PM_IN, n});
+        b.push_back({"out", PM_F32, PM_OUT, n});
         break;
     }
     case FAM_SMEM: case FAM_BARRIER: {

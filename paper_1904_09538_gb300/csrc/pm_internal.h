@@ -22,7 +22,8 @@ void clear_error();
     } while (0)
 
 // ---- kernel registry ------------------------------------------------------
-enum Family { FAM_STREAM, FAM_FMA, FAM_SMEM, FAM_BARRIER, FAM_OVERLAP, FAM_EMPTY, FAM_MM, FAM_DG, FAM_FD, FAM_SIMT, FAM_TC, FAM_FDB };
+enum Family { FAM_STREAM, FAM_FMA, FAM_SMEM, FAM_BARRIER, FAM_OVERLAP, FAM_EMPTY, FAM_MM, FAM_DG, FAM_FD, FAM_SIMT, FAM_TC, FAM_FDB,
+              FAM_SMEM2D };
 
 constexpr int kMaxParams = 8;
 

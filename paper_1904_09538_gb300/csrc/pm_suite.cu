@@ -170,6 +170,23 @@ __global__ void __launch_bounds__(256) k_smem(const float *__restrict__ in, floa
     out[gt] = s[l0];
 }
 
+// 2-D variant: T x T work-group, local index a = T lid1 + lid0, slots a and
+// T^2 + a; one barrier after the initial store.
+template <int T>
+__global__ void __launch_bounds__(T *T) k_smem2d(const float *__restrict__ in, float *__restrict__ out, int iters) {
+    __shared__ float sm[2 * T * T];
+    volatile float *s = sm;
+    const int a = T * threadIdx.y + threadIdx.x;
+    const size_t gt = (size_t)blockIdx.x * (T * T) + a;
+    s[a] = in[gt];
+    __syncthreads();
+    for (int r = 0; r < iters; r++) {
+        s[T * T + a] = s[a];
+        s[a] = s[T * T + a];
+    }
+    out[gt] = s[a];
+}
+
 __global__ void __launch_bounds__(256) k_barrier(const float *__restrict__ in, float *__restrict__ out, int B) {
     const size_t gt = (size_t)blockIdx.x * 256 + threadIdx.x;
     const float v = in[gt];
@@ -211,6 +228,13 @@ pm_status launch_suite(const KP &kp, void *const *b, void *stream) {
         unsigned G = (unsigned)kp.i(2);
         if (kp.i(1)) launch_k(k_smem<1>, G, 256, 0, st, (const float *)b[0], (float *)b[1], iters);
         else launch_k(k_smem<0>, G, 256, 0, st, (const float *)b[0], (float *)b[1], iters);
+        break;
+    }
+    case FAM_SMEM2D: {
+        int iters = (int)(kp.i(0) / 4);
+        unsigned G = (unsigned)kp.i(2);
+        if (kp.i(1) == 16) launch_k(k_smem2d<16>, G, dim3(16, 16), 0, st, (const float *)b[0], (float *)b[1], iters);
+        else launch_k(k_smem2d<18>, G, dim3(18, 18), 0, st, (const float *)b[0], (float *)b[1], iters);
         break;
     }
     case FAM_BARRIER:

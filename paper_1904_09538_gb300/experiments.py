@@ -328,6 +328,28 @@ def diagnostics(trials=10, seed=1234, flush_l2=True):
             per["p_part"] = rep_s[st["name"] + "_partial"]["params"]["p_part"]
         res[st["name"]] = per
     out["overlap"] = res
+    # -- local memory split by lid(1) stride (Section "Finite Differences"): the
+    # 16x16 and 18x18 stencil tiles differ in the lid(1) stride of their local
+    # accesses; calibrate a per-stride correction on the 2-D local kernels
+    fd = [st for st in studies() if st["name"] == "fd"][0]
+    l2d = generate(["lmem2d"])
+    split_onchip = ONCHIP + " + p_l18 * f_mem_access_local_float32_lstrides:{1:18}"
+    sts = [dict(fd, name="fd_single_lmem", expr=linear(fd["gmem"]), measure=fd["measure"] + l2d),
+           dict(fd, name="fd_split_lmem", expr=linear(fd["gmem"], onchip=split_onchip), measure=fd["measure"] + l2d)]
+    rep_s = run_studies(trials, seed=seed, flush_l2=flush_l2, study_list=sts)
+    per_access = {}
+    for T in (16, 18):
+        rows = [(k, p) for k, p in l2d if p["T"] == T]
+        ml = Model("f_wall_time", "p_l * f_mem_access_local_float32")
+        X = np.stack([ml.feature_values(k, **p) for k, p in rows])
+        t = measure(rows, bufs, trials, flush_l2)
+        per_access["T%d" % T] = float(np.median(t / X[:, 0]))
+    out["split_lmem"] = {
+        "s_per_subgroup_local_access": per_access,
+        "single": {v: r["geomean_rel_err"] for v, r in rep_s["fd_single_lmem"]["variants"].items()},
+        "split": {v: r["geomean_rel_err"] for v, r in rep_s["fd_split_lmem"]["variants"].items()},
+        "p_lmem": rep_s["fd_split_lmem"]["params"]["p_lmem"], "p_l18": rep_s["fd_split_lmem"]["params"]["p_l18"],
+        "fastest_identified": {k: rep_s[k]["fastest_variant_identified"] for k in rep_s}}
     return out
 
 

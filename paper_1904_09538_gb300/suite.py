@@ -60,6 +60,13 @@ def _smem_groups(p):
     return p
 
 
+def _smem2d_groups(p):
+    # the 1-D kernel's sizing: R x G constant, at least one work-group per SM
+    p = dict(p)
+    p["G"] = max(SM_COUNT, RESIDENT * (1 << 14) // p["R"])
+    return p
+
+
 def _stream_extra(p):
     # L in {2, 3} only at stride 1
     if p["L"] in (2, 3) and p["s"] != 1:
@@ -81,6 +88,7 @@ GENERATORS = [
               {"dtype": [1], "op": [2], "F": POW(10, 16)}, _fma_groups),
     Generator("smem", ["lmem", "suite"], {"R": POW(8, 14), "sync": [0, 1]}, _smem_groups),
     Generator("barrier", ["sync", "suite"], {"B": POW(4, 14, 2), "G": [RESIDENT]}),
+    Generator("smem2d", ["lmem2d"], {"R": POW(8, 14), "T": [16, 18]}, _smem2d_groups),
     Generator("overlap", ["overlap", "suite"], {"m": [0, 1, 2, 4, 8, 12, 16, 24, 32], "N": [1 << 26]}),
     Generator("empty", ["launch", "suite"], {"G": POW(6, 18)}),
     Generator("mm_pf", ["matmul_sq", "modeled"], {"n": [256, 384, 512, 640, 768, 896]}),

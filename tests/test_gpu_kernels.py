@@ -314,3 +314,11 @@ def test_kernel_resources_report_launch_shape():
     assert r["threads_per_block"] == 256 and r["regs_per_thread"] > 0
     r = pm.resources("mm_tc", n=512)
     assert r["threads_per_block"] == 128 and r["grid_blocks"] == (512 // 256) * (512 // 128)
+
+
+@pytest.mark.parametrize("T", [16, 18])
+def test_smem2d_moves_values_exactly(T):
+    G = 7
+    x = pm_inputs.uniform((G * T * T,), 81)
+    (r,) = run_kernel("smem2d", [x], R=64, T=T, G=G)
+    assert np.array_equal(r, x)
