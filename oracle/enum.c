@@ -1110,31 +1110,35 @@ void oracle_mm_tc_ref(long long m, long long n, long long k, const unsigned shor
 }
 
 /* ======================================================================
- * Stencil tile family (TMA-staged): P = {n, BX, BY}; input rows of pitch
- * n + 4; work-group (BX/4) x BY, grid (n/BX, n/BY).  Work-item (0,0) copies
+ * Stencil tile family (TMA-staged): P = {n, BX, BY, V}; input rows of pitch
+ * n + 4; work-group (BX/V) x BY, grid (n/BX, n/BY).  Work-item (0,0) copies
  * the (BY+2) x (BX+4) box at (row BY gid1, column BX gid0) element by
- * element; one barrier; every work-item loads 14 shared values (centre row
- * offsets 0..5, north and south rows 1..4 relative to 4 lid0), computes 4
- * outputs (3 add + 1 mul + 1 madd each) and stores one float32x4 vector.
+ * element; one barrier; every work-item then loads its V + 2 centre-row
+ * values (columns V lid0 + q, q = 0..V+1), and for q = 1..V its north and
+ * south values with one output each (3 add + 1 mul + 1 madd), and stores its
+ * V outputs as V/4 float32x4 vectors.
  * ====================================================================== */
 #define FB_BX(c) ((c)->P[1])
 #define FB_BY(c) ((c)->P[2])
+#define FB_V(c) ((c)->P[3])
 static long long ix_fb_u(const ctx *c, const long long *g, const long long *l, const long long *lv) {
     (void)l; long long P = c->P[0] + 4; return P * (FB_BY(c) * G1 + lv[0]) + FB_BX(c) * G0 + lv[1];
 }
 static long long fb_t(const ctx *c, const long long *l, long long row, long long col) {
-    return (FB_BX(c) + 4) * (L1_ + row) + 4 * L0_ + col;
+    return (FB_BX(c) + 4) * (L1_ + row) + FB_V(c) * L0_ + col;
 }
-#define FB_SITE(name, row, col) \
-    static long long name(const ctx *c, const long long *g, const long long *l, const long long *lv) { \
-        (void)g; (void)lv; return fb_t(c, l, row, col); }
-FB_SITE(ix_fb_c0, 1, 0) FB_SITE(ix_fb_c1, 1, 1) FB_SITE(ix_fb_c2, 1, 2) FB_SITE(ix_fb_c3, 1, 3)
-FB_SITE(ix_fb_c4, 1, 4) FB_SITE(ix_fb_c5, 1, 5) FB_SITE(ix_fb_n1, 0, 1) FB_SITE(ix_fb_n2, 0, 2)
-FB_SITE(ix_fb_n3, 0, 3) FB_SITE(ix_fb_n4, 0, 4) FB_SITE(ix_fb_s1, 2, 1) FB_SITE(ix_fb_s2, 2, 2)
-FB_SITE(ix_fb_s3, 2, 3) FB_SITE(ix_fb_s4, 2, 4)
+static long long ix_fb_c(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; return fb_t(c, l, 1, lv[0]);
+}
+static long long ix_fb_n(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; return fb_t(c, l, 0, lv[0]);
+}
+static long long ix_fb_s(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; return fb_t(c, l, 2, lv[0]);
+}
 static long long ix_fb_res(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)lv; long long n = c->P[0];
-    return (n / 4) * (FB_BY(c) * G1 + L1_) + (FB_BX(c) / 4) * G0 + L0_;
+    long long n = c->P[0];
+    return (n / 4) * (FB_BY(c) * G1 + L1_) + (FB_BX(c) / 4) * G0 + (FB_V(c) / 4) * L0_ + lv[0];
 }
 static void walk_fdb(ctx *c) {
     long long lv[2];
@@ -1142,22 +1146,24 @@ static void walk_fdb(ctx *c) {
         for (lv[0] = 0; lv[0] < FB_BY(c) + 2; lv[0]++)
             for (lv[1] = 0; lv[1] < FB_BX(c) + 4; lv[1]++) X(c, 0, lv);
     BAR(c);
-    X(c, 1, NULL);
+    for (lv[0] = 0; lv[0] < FB_V(c) + 2; lv[0]++) X(c, 1, lv);
+    for (lv[0] = 1; lv[0] <= FB_V(c); lv[0]++) X(c, 2, lv);
+    for (lv[0] = 0; lv[0] < FB_V(c) / 4; lv[0]++) X(c, 3, lv);
 }
 static int setup_fdb(ctx *c) {
-    long long n = c->P[0], BX = c->P[1], BY = c->P[2];
-    if (BX < 4 || BX % 4 || BY < 1 || n % BX || n % BY || n % 4) return -1;
+    long long n = c->P[0], BX = c->P[1], BY = c->P[2], V = c->P[3];
+    if ((V != 4 && V != 8) || BX < V || BX % V || BY < 1 || n % BX || n % BY || n % 4) return -1;
     c->grid[0] = n / BX; c->grid[1] = n / BY; c->grid[2] = 1;
-    c->wg[0] = BX / 4; c->wg[1] = BY; c->wg[2] = 1;
+    c->wg[0] = BX / V; c->wg[1] = BY; c->wg[2] = 1;
     int s0 = add_stmt(c, 2, DT_F32, 0, 0, 0);
     stmt_site(c, s0, add_site(c, "fdb-u", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_fb_u));
-    int s1 = add_stmt(c, 0, DT_F32, 12, 4, 4);
-    static const char *nm[14] = {"t_c0", "t_c1", "t_c2", "t_c3", "t_c4", "t_c5", "t_n1", "t_n2",
-                                 "t_n3", "t_n4", "t_s1", "t_s2", "t_s3", "t_s4"};
-    idx_fn fs[14] = {ix_fb_c0, ix_fb_c1, ix_fb_c2, ix_fb_c3, ix_fb_c4, ix_fb_c5, ix_fb_n1, ix_fb_n2,
-                     ix_fb_n3, ix_fb_n4, ix_fb_s1, ix_fb_s2, ix_fb_s3, ix_fb_s4};
-    for (int k = 0; k < 14; k++) stmt_site(c, s1, add_site(c, nm[k], MEM_LOCAL, DIR_LOAD, "float32", 4, fs[k]));
-    stmt_site(c, s1, add_site(c, "fdb-res", MEM_GLOBAL, DIR_STORE, "float32x4", 16, ix_fb_res));
+    int s1 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+    stmt_site(c, s1, add_site(c, "t_c", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_fb_c));
+    int s2 = add_stmt(c, 1, DT_F32, 3, 1, 1);
+    stmt_site(c, s2, add_site(c, "t_n", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_fb_n));
+    stmt_site(c, s2, add_site(c, "t_s", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_fb_s));
+    int s3 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+    stmt_site(c, s3, add_site(c, "fdb-res", MEM_GLOBAL, DIR_STORE, "float32x4", 16, ix_fb_res));
     c->walk = walk_fdb;
     return 0;
 }

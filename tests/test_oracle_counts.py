@@ -317,3 +317,22 @@ def test_smem2d_counts(T, R, G):
     g = by_tag(fs, "in")
     assert g["count"] == g["footprint"] == G * T * T and g["lstr"] == (1, T) and g["gstr"] == (T * T,)
     assert single(fs, "sync") == 1 and single(fs, "groups") == G
+
+
+@pytest.mark.parametrize("V", [4, 8])
+@pytest.mark.parametrize("n,BX,BY", [(64, 32, 4), (128, 64, 8), (96, 32, 32)])
+def test_fd_block_counts(n, BX, BY, V):
+    # TMA stencil tile: every output computed once (3 add + 1 mul + 1 madd),
+    # the box (BY+2) x (BX+4) copied once per group, 3V + 2 shared loads and
+    # V/4 vector stores per work-item
+    fs = features("fd_block", n=n, BX=BX, BY=BY, V=V)
+    assert op(fs, "float32", "add", wi=True) == 3 * n * n and op(fs, "float32", "madd", wi=True) == n * n
+    G = (n // BX) * (n // BY)
+    u = by_tag(fs, "fdb-u")
+    assert u["count_wi"] == G * (BY + 2) * (BX + 4) and u["lstr"] == (0, 0) and u["footprint"] == (n + 2) * (n + 4)
+    wi = G * (BX // V) * BY
+    assert by_tag(fs, "t_c")["count_wi"] == wi * (V + 2) and by_tag(fs, "t_n")["count_wi"] == wi * V
+    assert by_tag(fs, "t_c")["footprint"] == BY * (BX + 2) and by_tag(fs, "t_s")["footprint"] == BY * BX
+    r = by_tag(fs, "fdb-res")
+    assert r["count"] == r["footprint"] == n * n // 4 and r["lstr"] == (V // 4, n // 4)
+    assert single(fs, "sync") == 1 and single(fs, "groups") == G
