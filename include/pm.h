@@ -71,8 +71,8 @@ typedef struct {
  * tcgen05/TMEM/TMA, parameter n, a multiple of 256, and pipe: 0 = 4-stage
  * ring with one CTA per SM, 1 (default) = 2-stage ring with two CTAs per SM;
  * the counts do not depend on pipe); the TMA-staged
- * stencil tile family "fd_block" (parameters n, BX, BY, c0, c1; input u of
- * (n + 2) rows with row pitch n + 4).
+ * stencil tile family "fd_block" (parameters n, BX, BY, c0, c1, V = 4 or 8
+ * outputs per work-item; input u of (n + 2) rows with row pitch n + 4).
  * Returns PM_EUNKNOWN_KERNEL for other names. */
 pm_status pm_kernel_lookup(const char *name, int32_t *kernel);
 pm_status pm_kernel_count(int32_t *n);

@@ -36,7 +36,7 @@ static constexpr double REQ = std::numeric_limits<double>::quiet_NaN();
 #define P_SIMT {"n", "BM", "BN", "BK", nullptr}, {REQ, 128, 128, 32}, {1, 1, 1, 1}
 #define P_SMEM2D {"R", "T", "G", nullptr}, {REQ, 16, REQ}, {1, 1, 1}
 #define P_TC {"n", "pipe", nullptr}, {REQ, 1}, {1, 1}
-#define P_FDB {"n", "BX", "BY", "c0", "c1", nullptr}, {REQ, 64, 8, -4.0, 1.0}, {1, 1, 1, 0, 0}
+#define P_FDB {"n", "BX", "BY", "c0", "c1", "V", nullptr}, {REQ, 64, 8, -4.0, 1.0, 4}, {1, 1, 1, 0, 0, 1}
 
 static const KernelDef KDEFS[] = {
     {"stream", FAM_STREAM, 0, P_STREAM},

@@ -631,14 +631,14 @@ pm_status counts_tc(const KP &kp, std::vector<pm_feature> &v) {
 // (BY+2) x (BX+4) box element by element (uniform: per sub-group); every
 // work-item loads 14 shared values, computes 4 outputs, stores one vector.
 pm_status counts_fdb(const KP &kp, std::vector<pm_feature> &v) {
-    i64 n = kp.i(0), BX = kp.i(1), BY = kp.i(2), P = n + 4;
-    i64 L0 = BX / 4, L1 = BY, T = L0 * L1, G = (n / BX) * (n / BY), TW = BX + 4;
+    i64 n = kp.i(0), BX = kp.i(1), BY = kp.i(2), V = kp.i(5), P = n + 4;
+    i64 L0 = BX / V, L1 = BY, T = L0 * L1, G = (n / BX) * (n / BY), TW = BX + 4;
     u64 SGw = (u64)((T + 31) / 32);   // sub-groups per work-group
     Out o(v);
     const u64 WI = (u64)(G * T), SG = (u64)G * SGw;
-    o.op(0, 0, 12 * WI, 12 * SG);
-    o.op(0, 1, 4 * WI, 4 * SG);
-    o.op(0, 2, 4 * WI, 4 * SG);
+    o.op(0, 0, 3 * V * WI, 3 * V * SG);
+    o.op(0, 1, V * WI, V * SG);
+    o.op(0, 2, V * WI, V * SG);
     auto site = [&](const char *tag, int mem, int dir, const char *dt, int ds, i64 l0, i64 l1, i64 g0, i64 g1,
                     i64 loop, u64 wi, u64 sg, u64 foot) {
         Site x{};
@@ -649,11 +649,12 @@ pm_status counts_fdb(const KP &kp, std::vector<pm_feature> &v) {
     };
     const u64 box = (u64)((BY + 2) * (BX + 4)) * (u64)G;
     site("fdb-u", GL, LD, "float32", 4, 0, 0, BX, BY * P, 1, box, box, (u64)((n + 2) * P));
-    // 14 shared loads: centre row offsets 0..5, north and south rows 1..4
-    static const char *nm[14] = {"t_c0", "t_c1", "t_c2", "t_c3", "t_c4", "t_c5", "t_n1", "t_n2",
-                                 "t_n3", "t_n4", "t_s1", "t_s2", "t_s3", "t_s4"};
-    for (int k = 0; k < 14; k++) site(nm[k], LO, LD, "float32", 4, 4, TW, 0, 0, 0, WI, SG, (u64)(L0 * L1));
-    site("fdb-res", GL, ST, "float32x4", 16, 1, n / 4, L0, BY * n / 4, 0, WI, SG, (u64)(n * n / 4));
+    // shared loads: centre row columns V lid0 + 0..V+1, north and south rows V lid0 + 1..V
+    site("t_c", LO, LD, "float32", 4, V, TW, 0, 0, 1, WI * (V + 2), SG * (V + 2), (u64)(BY * (BX + 2)));
+    site("t_n", LO, LD, "float32", 4, V, TW, 0, 0, 1, WI * V, SG * V, (u64)(BY * BX));
+    site("t_s", LO, LD, "float32", 4, V, TW, 0, 0, 1, WI * V, SG * V, (u64)(BY * BX));
+    site("fdb-res", GL, ST, "float32x4", 16, V / 4, n / 4, BX / 4, BY * n / 4, 1, WI * (V / 4), SG * (V / 4),
+         (u64)(n * n / 4));
     o.finish(1, (u64)G);
     return PM_OK;
 }
@@ -736,6 +737,7 @@ pm_status validate(const KP &kp) {
     case FAM_FDB: {
         i64 n = kp.i(0), BX = kp.i(1), BY = kp.i(2);
         if (BX != 32 && BX != 64 && BX != 128) return fail(PM_EINVAL, "%s: BX must be 32, 64 or 128", nm);
+        if (kp.i(5) != 4 && kp.i(5) != 8) return fail(PM_EINVAL, "%s: V must be 4 or 8", nm);
         if (BY != 4 && BY != 8 && BY != 16 && BY != 32) return fail(PM_EINVAL, "%s: BY must be 4, 8, 16 or 32", nm);
         if (n < BX || n % BX || n % BY || n > 46000)
             return fail(PM_EINVAL, "%s: n (<= 46000) must be divisible by BX and BY", nm);

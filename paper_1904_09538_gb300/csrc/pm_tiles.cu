@@ -13,14 +13,16 @@
 //   16 vector stores of C.
 // The shared-memory tiles take (BM + BN) * BK * 4 bytes (up to 128 KiB).
 //
-// Stencil tile family "fd_block" (12 shapes BX x BY): the five-point stencil
-// on an input with a padded row pitch P = n + 4 (16-byte multiple, as TMA
-// requires), one BY x BX output tile per work-group of (BX/4) x BY
-// work-items.  Work-item (0, 0) copies the (BY + 2) x (BX + 4) input box into
-// shared memory with one TMA load (mbarrier completion, bounded wait); after a
-// barrier every work-item computes 4 consecutive outputs from 14 shared-memory
-// values (3 adds, 1 multiply, 1 multiply-add each) and stores them as one
-// 16-byte vector.
+// Stencil tile family "fd_block" (12 shapes BX x BY, V = 4 or 8 outputs per
+// work-item): the five-point stencil on an input with a padded row pitch
+// P = n + 4 (16-byte multiple, as TMA requires), one BY x BX output tile per
+// work-group of (BX/V) x BY work-items.  Work-item (0, 0) copies the
+// (BY + 2) x (BX + 4) input box into shared memory with one TMA load
+// (mbarrier completion, bounded wait); after a barrier every work-item reads
+// V + 2 centre-row and 2V north/south values, computes V consecutive outputs
+// (3 adds, 1 multiply, 1 multiply-add each) and stores them as V/4 16-byte
+// vectors.  V = 8 halves the threads per tile, so twice as many tiles (and
+// TMA copies in flight) fit on an SM.
 #include <cuda.h>
 #include <cuda_runtime.h>
 
@@ -129,8 +131,8 @@ pm_status launch_simt_bn(int BN, int BK, void *const *b, int n, cudaStream_t st)
 // ---------------------------------------------------------------- stencil tile family
 static __device__ int g_fdb_timeout;
 
-template <int BX, int BY>
-__global__ void __launch_bounds__((BX / 4) * BY) k_fd_block(const __grid_constant__ CUtensorMap tmU,
+template <int BX, int BY, int V>
+__global__ void __launch_bounds__((BX / V) * BY) k_fd_block(const __grid_constant__ CUtensorMap tmU,
                                                          float *__restrict__ res, int n, float c0, float c1) {
     constexpr int TW = BX + 4, TH = BY + 2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
@@ -150,23 +152,22 @@ __global__ void __launch_bounds__((BX / 4) * BY) k_fd_block(const __grid_constan
     bool ok = mbar_wait_bounded(bar, 0, &g_fdb_timeout, 1ll << 26);
     if (!ok && leader) mbar_wait_bounded(bar, 0, &g_fdb_timeout, 1ll << 26);   // drain our own copy
     if (!ok) return;
-    const float *r0 = T + ly * TW + 4 * lx;       // north row
+    const float *r0 = T + ly * TW + V * lx;       // north row
     const float *r1 = r0 + TW;                    // centre row
     const float *r2 = r1 + TW;                    // south row
-    const float m0 = r1[0], m1 = r1[1], m2 = r1[2], m3 = r1[3], m4 = r1[4], m5 = r1[5];
-    const float n1 = r0[1], n2 = r0[2], n3 = r0[3], n4 = r0[4];
-    const float s1 = r2[1], s2 = r2[2], s3 = r2[3], s4 = r2[4];
-    float o[4];
-    const float cc[4] = {m1, m2, m3, m4}, nn[4] = {n1, n2, n3, n4}, ss[4] = {s1, s2, s3, s4};
-    const float ww[4] = {m0, m1, m2, m3}, ee[4] = {m2, m3, m4, m5};
+    float m[V + 2], o[V];
 #pragma unroll
-    for (int q = 0; q < 4; q++)
-        o[q] = __fmaf_rn(c0, cc[q], __fmul_rn(c1, __fadd_rn(__fadd_rn(__fadd_rn(nn[q], ss[q]), ww[q]), ee[q])));
+    for (int q = 0; q < V + 2; q++) m[q] = r1[q];
+#pragma unroll
+    for (int q = 1; q <= V; q++)
+        o[q - 1] = __fmaf_rn(c0, m[q], __fmul_rn(c1, __fadd_rn(__fadd_rn(__fadd_rn(r0[q], r2[q]), m[q - 1]), m[q + 1])));
     const size_t row = (size_t)BY * blockIdx.y + ly;
-    reinterpret_cast<float4 *>(res)[row * (n / 4) + (size_t)(BX / 4) * blockIdx.x + lx] = make_float4(o[0], o[1], o[2], o[3]);
+    float4 *dst = reinterpret_cast<float4 *>(res) + row * (n / 4) + (size_t)(BX / 4) * blockIdx.x + (V / 4) * lx;
+#pragma unroll
+    for (int h = 0; h < V / 4; h++) dst[h] = make_float4(o[4 * h], o[4 * h + 1], o[4 * h + 2], o[4 * h + 3]);
 }
 
-template <int BX, int BY>
+template <int BX, int BY, int V>
 pm_status launch_fdb_t(void *const *b, int n, float c0, float c1, cudaStream_t st) {
     constexpr int TW = BX + 4, TH = BY + 2;
     const size_t smem = 128 + (size_t)TW * TH * sizeof(float) + 32;
@@ -174,19 +175,28 @@ pm_status launch_fdb_t(void *const *b, int n, float c0, float c1, cudaStream_t s
     const uint64_t P = (uint64_t)n + 4;
     pm_status s = tensor_map_2d(&tm, 0, b[0], P, (uint64_t)n + 2, P * sizeof(float), TW, TH, 0);
     if (s) return s;
-    dim3 grid(n / BX, n / BY), blk(BX / 4, BY);
-    launch_k(k_fd_block<BX, BY>, grid, blk, smem, st, tm, (float *)b[1], n, c0, c1);
+    dim3 grid(n / BX, n / BY), blk(BX / V, BY);
+    launch_k(k_fd_block<BX, BY, V>, grid, blk, smem, st, tm, (float *)b[1], n, c0, c1);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
 }
 
-template <int BX>
+template <int BX, int V>
 pm_status launch_fdb_by(int BY, void *const *b, int n, float c0, float c1, cudaStream_t st) {
     switch (BY) {
-    case 4: return launch_fdb_t<BX, 4>(b, n, c0, c1, st);
-    case 8: return launch_fdb_t<BX, 8>(b, n, c0, c1, st);
-    case 16: return launch_fdb_t<BX, 16>(b, n, c0, c1, st);
-    default: return launch_fdb_t<BX, 32>(b, n, c0, c1, st);
+    case 4: return launch_fdb_t<BX, 4, V>(b, n, c0, c1, st);
+    case 8: return launch_fdb_t<BX, 8, V>(b, n, c0, c1, st);
+    case 16: return launch_fdb_t<BX, 16, V>(b, n, c0, c1, st);
+    default: return launch_fdb_t<BX, 32, V>(b, n, c0, c1, st);
+    }
+}
+
+template <int V>
+pm_status launch_fdb_v(int BX, int BY, void *const *b, int n, float c0, float c1, cudaStream_t st) {
+    switch (BX) {
+    case 32: return launch_fdb_by<32, V>(BY, b, n, c0, c1, st);
+    case 64: return launch_fdb_by<64, V>(BY, b, n, c0, c1, st);
+    default: return launch_fdb_by<128, V>(BY, b, n, c0, c1, st);
     }
 }
 
@@ -205,15 +215,12 @@ pm_status fdb_check_timeout() {
 pm_status launch_tiles(const KP &kp, void *const *b, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if (kp.def->fam == FAM_FDB) {
-        const int n = (int)kp.i(0), BX = (int)kp.i(1), BY = (int)kp.i(2);
+        const int n = (int)kp.i(0), BX = (int)kp.i(1), BY = (int)kp.i(2), V = (int)kp.i(5);
         const float c0 = (float)kp.v[3], c1 = (float)kp.v[4];
         for (int a = 0; a < 2; a++)
             if ((uintptr_t)b[a] % 16) return fail(PM_EINVAL, "fd_block: buffer %d must be 16-byte aligned", a);
-        switch (BX) {
-        case 32: return launch_fdb_by<32>(BY, b, n, c0, c1, st);
-        case 64: return launch_fdb_by<64>(BY, b, n, c0, c1, st);
-        default: return launch_fdb_by<128>(BY, b, n, c0, c1, st);
-        }
+        if (V == 8) return launch_fdb_v<8>(BX, BY, b, n, c0, c1, st);
+        return launch_fdb_v<4>(BX, BY, b, n, c0, c1, st);
     }
     if (kp.def->fam != FAM_SIMT) return fail(PM_EINVAL, "not a tile-family kernel");
     const int n = (int)kp.i(0), BM = (int)kp.i(1), BN = (int)kp.i(2), BK = (int)kp.i(3);

@@ -180,9 +180,10 @@ def test_mm_tc(n):
     compare("mm_tc", n=n)
 
 
+@pytest.mark.parametrize("V", [4, 8])
 @pytest.mark.parametrize("n,BX,BY", [(64, 32, 4), (128, 64, 8), (128, 128, 16), (256, 128, 32), (96, 32, 32)])
-def test_fd_block(n, BX, BY):
-    compare("fd_block", n=n, BX=BX, BY=BY)
+def test_fd_block(n, BX, BY, V):
+    compare("fd_block", n=n, BX=BX, BY=BY, V=V)
 
 
 @pytest.mark.parametrize("R,T,G", [(4, 16, 1), (64, 18, 3), (256, 16, 5), (8, 18, 1)])

@@ -293,12 +293,13 @@ def test_mm_simt_all_tiles(BM, BN, BK):
     assert cond_err(c.reshape(768, 768), d["ref"], d["rabs"]) <= TOL
 
 
+@pytest.mark.parametrize("V", [4, 8])
 @pytest.mark.parametrize("BX", [32, 64, 128])
 @pytest.mark.parametrize("BY", [4, 8, 16, 32])
-def test_fd_block_all_tiles(BX, BY):
+def test_fd_block_all_tiles(BX, BY, V):
     n = 256
     u = pm_inputs.uniform((n + 2, n + 4), 71)      # row pitch n + 4; columns n+2, n+3 are padding
-    (r,) = run_kernel("fd_block", [u], n=n, BX=BX, BY=BY, c0=-4.0, c1=1.0)
+    (r,) = run_kernel("fd_block", [u], n=n, BX=BX, BY=BY, V=V, c0=-4.0, c1=1.0)
     ref, rabs = refs.stencil(np.ascontiguousarray(u[:, :n + 2]), -4.0, 1.0)
     assert cond_err(r.reshape(n, n), ref, rabs) <= TOL
 
