@@ -38,7 +38,8 @@ SIMT_MODEL = (
     "p_lv * f_mem_access_local_float32x4) - (p_gv * f_mem_access_global_float32x4))) + 1) / 2")
 
 
-STENCIL_SHAPES = [dict(BX=bx, BY=by) for bx in (32, 64, 128) for by in (4, 8, 16, 32)]
+# 8 outputs per work-item: the faster work-item shape for every tile with at most 2^19 tiles at n = 16384
+STENCIL_SHAPES = [dict(BX=bx, BY=by, V=8) for bx in (32, 64, 128) for by in (4, 8, 16, 32)]
 
 # linear model of Section "Finite Differences" on the tile family's features
 STENCIL_MODEL = ("p_launch * f_sync_kernel_launch + p_group * f_thread_groups + "
