@@ -112,7 +112,7 @@ def rank_family(kernel="mm_simt", shapes=None, calib_sizes=(3072, 4608), target=
     }
 
 
-def rank_stencil(target=16384, calib_sizes=(2048, 4096), trials=5, seed=7):
+def rank_stencil(target=16384, calib_sizes=(4096, 8192), trials=5, seed=7):
     """The 12 stencil tile shapes (BX x BY outputs per CTA) at n = 16384."""
     return rank_family("fd_block", STENCIL_SHAPES, calib_sizes, target, trials, seed, STENCIL_MODEL,
                        bytes_fn=lambda n: 4.0 * ((n + 2) * (n + 4) + n * n))
