@@ -210,6 +210,30 @@ pm_status pm_run_host(int32_t kernel, const pm_param *p, size_t np,
                       void *const *host_bufs, size_t nbufs, const pm_run_opts *opts,
                       void *stream, float *trial_ms, pm_timing *out, double *copy_ms);
 
+/* One kernel instance of a host-buffer batch: parameters and host buffers
+ * as for pm_run_host. */
+typedef struct {
+    int32_t kernel;
+    const pm_param *p;
+    size_t np;
+    void *const *host_bufs;
+    size_t nbufs;
+} pm_host_job;
+
+/* pm_run_host over a list of kernel instances, pipelined over the two copy
+ * directions of the host link: while job i's outputs travel device->host,
+ * job i+1's inputs travel host->device (two internal copy streams).  Kernels
+ * never overlap a copy, so each job's device timing is as in pm_run_host:
+ * job i+1's launches wait for its inputs and for job i's output copy.  When
+ * an output buffer of job i overlaps an input buffer of job i+1 in host
+ * memory, that pair of copies is serialised instead.  Device staging comes
+ * from the default memory pool (see pm_run_host).  out: njobs timings;
+ * copy_ms (nullable): time from the first input copy's start to the last
+ * output copy's end minus the kernels' time; on error the failing job's
+ * index is in the message and later jobs are not run. */
+pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_opts *opts, void *stream,
+                            pm_timing *out, double *copy_ms);
+
 /* ---------------------------------------------------------------- models */
 
 typedef struct pm_model pm_model;

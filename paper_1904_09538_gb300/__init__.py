@@ -162,6 +162,33 @@ def run_host(kernel, host_arrays, warmup=2, trials=60, outlier_factor=5.0, strea
                 n_dropped=tm.n_dropped, copy_ms=cms.value)
 
 
+def run_host_batch(jobs, warmup=0, trials=1, outlier_factor=5.0, stream=None, flush_l2=False):
+    """pm_run_host over a list of (kernel, host_arrays, params) jobs with the
+    output copy of each job overlapping the input copy of the next.  Returns
+    (list of timing dicts, copy_ms)."""
+    keep = []
+    arr = (_lib.pm_host_job * max(1, len(jobs)))()
+    for i, (kernel, host_arrays, params) in enumerate(jobs):
+        parr, n, k = _params(params)
+        ptrs = (ctypes.c_void_p * max(1, len(host_arrays)))()
+        for b, a in enumerate(host_arrays):
+            if hasattr(a, "data_ptr"):
+                ptrs[b] = a.data_ptr()
+            else:
+                if not a.flags["C_CONTIGUOUS"]:
+                    raise ValueError("job %d host array %d must be C-contiguous" % (i, b))
+                ptrs[b] = a.ctypes.data
+        keep += [parr, k, ptrs]
+        arr[i] = _lib.pm_host_job(_kid(kernel), ctypes.cast(parr, ctypes.c_void_p), n,
+                                  ctypes.cast(ptrs, ctypes.c_void_p), len(host_arrays))
+    opts = pm_run_opts(warmup, trials, outlier_factor, 1 if flush_l2 else 0)
+    tms = (pm_timing * max(1, len(jobs)))()
+    cms = ctypes.c_double()
+    check(lib().pm_run_host_batch(arr, len(jobs), ctypes.byref(opts), _stream(stream), tms, ctypes.byref(cms)))
+    return [dict(mean_ms=t.mean_ms, median_ms=t.median_ms, min_ms=t.min_ms, n_trials=t.n_trials,
+                 n_dropped=t.n_dropped) for t in tms[:len(jobs)]], cms.value
+
+
 def _opts(max_iter=200, ftol=1e-15, xtol=1e-12, p0=None):
     return pm_fit_opts(max_iter, ftol, xtol, 0 if p0 is None else 1)
 

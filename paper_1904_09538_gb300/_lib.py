@@ -35,6 +35,11 @@ class pm_resources(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("sm_count", ctypes.c_int32), ("grid_blocks", ctypes.c_uint64)]
 
 
+class pm_host_job(ctypes.Structure):
+    _fields_ = [("kernel", ctypes.c_int32), ("p", ctypes.c_void_p), ("np", ctypes.c_size_t),
+                ("host_bufs", ctypes.c_void_p), ("nbufs", ctypes.c_size_t)]
+
+
 class pm_run_opts(ctypes.Structure):
     _fields_ = [("warmup", ctypes.c_int32), ("trials", ctypes.c_int32), ("outlier_factor", ctypes.c_double),
                 ("flush_l2", ctypes.c_int32)]
@@ -73,6 +78,7 @@ SIGNATURES = {
     "pm_kernel_resources": (i32, [i32, P(pm_param), c_size_t, P(pm_resources)]),
     "pm_run": (i32, [i32, P(pm_param), c_size_t, P(vp), c_size_t, P(pm_run_opts), vp, fp, P(pm_timing)]),
     "pm_run_host": (i32, [i32, P(pm_param), c_size_t, P(vp), c_size_t, P(pm_run_opts), vp, fp, P(pm_timing), dp]),
+    "pm_run_host_batch": (i32, [P(pm_host_job), c_size_t, P(pm_run_opts), vp, P(pm_timing), dp]),
     "pm_model_create": (i32, [ctypes.c_char_p, ctypes.c_char_p, P(vp)]),
     "pm_model_destroy": (None, [vp]),
     "pm_model_info": (i32, [vp, P(c_size_t), P(c_size_t)]),

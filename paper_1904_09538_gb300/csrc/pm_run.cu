@@ -5,6 +5,7 @@
 #include <cmath>
 #include <cuda_runtime.h>
 #include <mutex>
+#include <string>
 #include <vector>
 
 #include "pm_internal.h"
@@ -265,6 +266,114 @@ pm_status pm_run_host(int32_t kernel, const pm_param *p, size_t np, void *const 
     cudaStreamSynchronize(st);
     for (int i = 0; i < 4; i++)
         if (e[i]) cudaEventDestroy(e[i]);
+    return rc;
+}
+
+pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_opts *opts, void *stream,
+                            pm_timing *out, double *copy_ms) {
+    if (njobs && (!jobs || !out)) return fail(PM_EINVAL, "pm_run_host_batch: jobs or out is NULL");
+    pm_status s;
+    if ((s = retain_staging_pool())) return s;
+    cudaStream_t cs = (cudaStream_t)stream;
+    struct Job {
+        KP kp;
+        std::vector<BufSpec> spec;
+        std::vector<void *> dev;
+    };
+    std::vector<Job> J(njobs);
+    for (size_t i = 0; i < njobs; i++) {
+        const pm_host_job &h = jobs[i];
+        if ((s = parse_params(h.kernel, h.p, h.np, &J[i].kp))) return s;
+        if ((s = validate(J[i].kp))) return s;
+        if ((s = buffers(J[i].kp, J[i].spec))) return s;
+        if (h.nbufs != J[i].spec.size())
+            return fail(PM_EINVAL, "pm_run_host_batch: job %zu: %zu buffers passed, %zu needed", i, h.nbufs,
+                        J[i].spec.size());
+        for (size_t b = 0; b < h.nbufs; b++)
+            if (!h.host_bufs || !h.host_bufs[b]) return fail(PM_EINVAL, "pm_run_host_batch: job %zu buffer %zu is NULL", i, b);
+    }
+    // does an output of job i overlap an input of job i + 1 in host memory?
+    auto clash = [&](size_t i) {
+        for (size_t a = 0; a < J[i].spec.size(); a++) {
+            if (J[i].spec[a].role != PM_OUT) continue;
+            const char *o0 = (const char *)jobs[i].host_bufs[a];
+            const char *o1 = o0 + J[i].spec[a].elems * dtype_size(J[i].spec[a].dtype);
+            for (size_t b = 0; b < J[i + 1].spec.size(); b++) {
+                if (J[i + 1].spec[b].role != PM_IN) continue;
+                const char *i0 = (const char *)jobs[i + 1].host_bufs[b];
+                const char *i1 = i0 + J[i + 1].spec[b].elems * dtype_size(J[i + 1].spec[b].dtype);
+                if (o0 < i1 && i0 < o1) return true;
+            }
+        }
+        return false;
+    };
+    cudaStream_t up = nullptr, down = nullptr;
+    EventPool ev;   // per job: inputs copied, kernels done, outputs copied
+    pm_status rc = PM_OK;
+    if (cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking) != cudaSuccess)
+        rc = fail(PM_ECUDA, "pm_run_host_batch: stream creation failed");
+    if (rc == PM_OK) rc = ev.make(3 * njobs + 2);
+    double kernels_ms = 0.0;
+    for (size_t i = 0; i < njobs && rc == PM_OK; i++) {
+        Job &j = J[i];
+        cudaEvent_t e_in = ev.ev[3 * i], e_k = ev.ev[3 * i + 1], e_out = ev.ev[3 * i + 2];
+        j.dev.assign(j.spec.size(), nullptr);
+        if (i > 0) {
+            // inputs of job i after job i-1's kernels (and after its output copy if they alias)
+            cudaStreamWaitEvent(up, ev.ev[3 * (i - 1) + 1], 0);
+            if (clash(i - 1)) cudaStreamWaitEvent(up, ev.ev[3 * (i - 1) + 2], 0);
+        }
+        if (i == 0) cudaEventRecord(ev.ev[3 * njobs], up);
+        for (size_t b = 0; b < j.spec.size() && rc == PM_OK; b++) {
+            const size_t bytes = j.spec[b].elems * dtype_size(j.spec[b].dtype);
+            if (cudaMallocAsync(&j.dev[b], bytes, up) != cudaSuccess)
+                rc = fail(PM_ENOMEM, "pm_run_host_batch: job %zu: allocation of %s failed", i, j.spec[b].name);
+            else if (j.spec[b].role == PM_IN &&
+                     cudaMemcpyAsync(j.dev[b], jobs[i].host_bufs[b], bytes, cudaMemcpyHostToDevice, up) != cudaSuccess)
+                rc = fail(PM_ECUDA, "pm_run_host_batch: job %zu: host-to-device copy failed", i);
+        }
+        if (rc != PM_OK) break;
+        cudaEventRecord(e_in, up);
+        cudaStreamWaitEvent(cs, e_in, 0);
+        if (i > 0) cudaStreamWaitEvent(cs, ev.ev[3 * (i - 1) + 2], 0);   // no kernel under a copy
+        pm_timing t{};
+        rc = timed(j.kp, j.dev.data(), j.dev.size(), opts, stream, nullptr, &t);
+        if (rc != PM_OK) {
+            const std::string why = pm_last_error();
+            fail(rc, "pm_run_host_batch: job %zu (%s): %s", i, j.kp.def->name, why.c_str());
+            break;
+        }
+        out[i] = t;
+        kernels_ms += t.mean_ms * t.n_trials;
+        cudaEventRecord(e_k, cs);
+        cudaStreamWaitEvent(down, e_k, 0);
+        for (size_t b = 0; b < j.spec.size() && rc == PM_OK; b++)
+            if (j.spec[b].role == PM_OUT &&
+                cudaMemcpyAsync(jobs[i].host_bufs[b], j.dev[b], j.spec[b].elems * dtype_size(j.spec[b].dtype),
+                                cudaMemcpyDeviceToHost, down) != cudaSuccess)
+                rc = fail(PM_ECUDA, "pm_run_host_batch: job %zu: device-to-host copy failed", i);
+        cudaEventRecord(e_out, down);
+        for (void *d : j.dev)
+            if (d) cudaFreeAsync(d, down);
+        j.dev.clear();
+    }
+    if (up) cudaStreamSynchronize(up);
+    if (down) {
+        if (rc == PM_OK && njobs) cudaEventRecord(ev.ev[3 * njobs + 1], down);
+        cudaStreamSynchronize(down);
+    }
+    cudaStreamSynchronize(cs);
+    for (auto &j : J)   // buffers of a job that failed before its output copy
+        for (void *d : j.dev)
+            if (d) cudaFree(d);
+    if (rc == PM_OK && copy_ms && njobs) {
+        float total = 0;
+        cudaEventElapsedTime(&total, ev.ev[3 * njobs], ev.ev[3 * njobs + 1]);
+        *copy_ms = std::max(0.0, (double)total - kernels_ms);
+    }
+    if (up) cudaStreamDestroy(up);
+    if (down) cudaStreamDestroy(down);
     return rc;
 }
 

@@ -323,3 +323,21 @@ def test_smem2d_moves_values_exactly(T):
     x = pm_inputs.uniform((G * T * T,), 81)
     (r,) = run_kernel("smem2d", [x], R=64, T=T, G=G)
     assert np.array_equal(r, x)
+
+
+def test_run_host_batch_pipelines_and_orders_aliased_buffers():
+    dev()
+    N = 1 << 20
+    x0, x1 = pm_inputs.uniform((N,), 91), pm_inputs.uniform((N,), 92)
+    o0 = np.zeros(N, np.float32)
+    o1 = np.zeros(N, np.float32)
+    y = [pm_inputs.uniform((N,), 93 + a) for a in range(4)]
+    o2 = np.zeros(N, np.float32)
+    jobs = [("stream", [x0, x1, o0], dict(N=N, L=2, vec=1)),
+            ("stream", [o0, o1], dict(N=N, L=1, vec=1)),        # reads job 0's output: copies serialised
+            ("stream", y + [o2], dict(N=N, L=4, vec=1))]
+    tms, copy_ms = pm.run_host_batch(jobs, warmup=1, trials=3)
+    want = refs.stream([x0, x1])
+    assert np.array_equal(o0, want) and np.array_equal(o1, want)
+    assert np.array_equal(o2, refs.stream(y))
+    assert len(tms) == 3 and all(t["n_trials"] == 3 and t["mean_ms"] > 0 for t in tms) and copy_ms > 0
