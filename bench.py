@@ -329,46 +329,48 @@ def source_sha(f="pm_suite.cu", kernel="k_stream"):
 
 
 def e2e_measure(pm, S, variants, torch, trials, fit_and_predict):
-    """Same step through the public API with host buffers: per variant
-    pm_run_host (host->device copies of its inputs, `trials` timed launches,
-    device->host copy of its output; pinned host buffers), then the batched
-    calibration and the held-out predictions from host arrays.  One step."""
+    """Same step through the public API with host buffers: pm_run_host_batch
+    over every variant (pinned host buffers; per variant the host-to-device
+    copies of its inputs, its `trials` timed launches, the device-to-host
+    copy of its output, the output copy of one variant overlapping the input
+    copy of the next), then the batched calibration and the held-out
+    predictions from host arrays.  One step."""
     import numpy as np
     need = 1
     for k, p in variants:
         for b in pm.kernel_buffers(k, **p):
             need = max(need, b["elems"] * np.dtype(b["dtype"]).itemsize)
-    host = [torch.empty(need, dtype=torch.uint8, pin_memory=True) for _ in range(5)]
+    ins = [torch.empty(need, dtype=torch.uint8, pin_memory=True) for _ in range(4)]
+    outs = [torch.empty(need, dtype=torch.uint8, pin_memory=True) for _ in range(2)]   # alternate between jobs
+    for a in ins + outs:   # values in [-1, 1) as float32 bit patterns are fine for every kernel here
+        a.numpy().view(np.float32)[:] = 0.5
     h2d = d2h = 0
     nbytes = 0
-    prepared = []
-    for k, p in variants:
-        arrs = []
-        for i, b in enumerate(pm.kernel_buffers(k, **p)):
-            a = host[i].numpy().view(b["dtype"])[:b["elems"]]
+    jobs = []
+    for j, (k, p) in enumerate(variants):
+        arrs, ii = [], 0
+        for b in pm.kernel_buffers(k, **p):
             if b["role"] == "in":
+                a = ins[ii].numpy().view(b["dtype"])[:b["elems"]]
+                ii += 1
                 h2d += a.nbytes
             else:
+                a = outs[j % 2].numpy().view(b["dtype"])[:b["elems"]]
                 d2h += a.nbytes
             arrs.append(a)
-        prepared.append((k, p, arrs))
+        jobs.append((k, arrs, p))
         nbytes += S.algorithmic_bytes(k, p) * trials
-    for a in host:   # values in [-1, 1) as float32 bit patterns are fine for every kernel here
-        a.numpy().view(np.float32)[:] = 0.5
     # untimed warm-up: the largest variant sizes the reserved staging pool
-    big = max(prepared, key=lambda x: sum(a.nbytes for a in x[2]))
-    for k, p, arrs in prepared[:3] + [big]:
-        pm.run_host(k, arrs, warmup=0, trials=1, **p)
+    big = max(jobs, key=lambda x: sum(a.nbytes for a in x[1]))
+    pm.run_host_batch(jobs[:3] + [big, big], warmup=0, trials=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
-    times = {}
-    for i, (k, p, arrs) in enumerate(prepared):
-        times[i] = pm.run_host(k, arrs, warmup=0, trials=trials, outlier_factor=0.0, **p)["mean_ms"] * 1e-3
-    fit_and_predict(times)
+    tms, copy_ms = pm.run_host_batch(jobs, warmup=0, trials=trials, outlier_factor=0.0)
+    fit_and_predict({i: t["mean_ms"] * 1e-3 for i, t in enumerate(tms)})
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
     return {"value": round(nbytes / dt / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 2)}
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 2), "copy_ms": round(copy_ms, 1)}
 
 
 def fit_throughput(pm, torch, dev):
