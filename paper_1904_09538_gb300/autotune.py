@@ -104,6 +104,9 @@ def rank_family(kernel="mm_simt", shapes=None, calib_sizes=(3072, 4608), target=
         "best_predicted": kt[best_pred], "best_measured": kt[best_meas],
         "best_hit": best_pred == best_meas, "best_in_predicted_top3": best_meas in top3,
         "slowdown_of_predicted_best": float(meas[best_pred] / best_all),
+        # the model as a pruning heuristic: time only its k best predictions, keep the fastest
+        "slowdown_after_timing_predicted_top_k": {str(k): float(meas[np.argsort(pred)[:k]].min() / best_all)
+                                                  for k in (1, 3, 5) if k <= len(pred)},
         "best_measured_rate": rate(best_all), "rate_unit": "TFLOP/s" if bytes_fn is None else "GB/s",
         "geomean_rel_err": float(math.exp(np.mean(np.log(np.abs(pred - meas) / meas)))),
         "calibration_seconds": calib_s, "exhaustive_seconds": meas_s,
