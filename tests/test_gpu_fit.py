@@ -214,3 +214,37 @@ def test_fit_rejects_bad_data():
     t[3] = np.nan
     with pytest.raises(pm.PMError):
         m.fit(X, t)
+
+
+def test_fit_rejects_empty_data():
+    dev()
+    m = pm.Model("f_wall_time", LIN)
+    with pytest.raises(pm.PMError):
+        m.fit(np.zeros((0, 6)), np.zeros(0))
+
+
+def test_fewer_rows_than_parameters_interpolates_with_min_norm():
+    # l = 3 < m = 6: rank-deficient, the minimum-norm solution reproduces every row
+    dev()
+    X = design(3, 131)
+    t, om, F = synth(LIN, X, P_LIN, 0.0, 132)
+    m = pm.Model("f_wall_time", LIN)
+    p, rep = m.fit(X, t)
+    assert rep["status"] == -5 and rep["rank"] == 3
+    assert np.max(np.abs(m.predict(p, X) / t - 1)) <= 1e-9
+    po, _ = ofit.fit(om, F, t)      # the oracle's minimum-norm solution in the same coordinates
+    assert np.max(np.abs(m.predict(po, X) / t - 1)) <= 1e-9
+
+
+def test_batched_single_row_and_single_parameter_models():
+    dev()
+    one = pm.Model("f_wall_time", "p_madd * f_op_float32_madd")
+    lin = pm.Model("f_wall_time", LIN)
+    X1 = np.array([[4.0e6]])
+    t1 = np.array([1.2e-5])
+    X2 = design(40, 141)
+    t2, _, _ = synth(LIN, X2, P_LIN, 0.0, 142)
+    plan = pm.FitPlan([one, lin], [1, 40])
+    p, reps = plan.run(np.concatenate([X1.ravel(), X2.ravel()]), np.concatenate([t1, t2]))
+    assert reps[0]["status"] == 0 and abs(p[0] * 4.0e6 / 1.2e-5 - 1) <= 1e-12
+    assert reps[1]["status"] == 0 and perr(p[1:], vec(lin, P_LIN)) <= 1e-8
