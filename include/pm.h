@@ -69,8 +69,11 @@ typedef struct {
  * "mm_simt" (register-tiled fp32 matmul, parameters n, BM, BN, BK); the
  * added BF16 tensor-core matmul "mm_tc" (C = A Bt^T, bf16 in, fp32 out,
  * tcgen05/TMEM/TMA, parameter n, a multiple of 256, and pipe: 0 = 4-stage
- * ring with one CTA per SM, 1 (default) = 2-stage ring with two CTAs per SM;
- * the counts do not depend on pipe); the TMA-staged
+ * ring with one CTA per SM, 1 (default) = 2-stage ring with two CTAs per SM,
+ * 2 = persistent (one CTA per SM walking the tiles, 4-stage ring, two TMEM
+ * accumulators so one tile's epilogue overlaps the next tile's main loop);
+ * the counts describe the decomposition into 128 x 256 tiles and do not
+ * depend on pipe); the TMA-staged
  * stencil tile family "fd_block" (parameters n, BX, BY, c0, c1, V = 4 or 8
  * outputs per work-item; input u of (n + 2) rows with row pitch n + 4).
  * Returns PM_EUNKNOWN_KERNEL for other names. */

@@ -746,8 +746,9 @@ pm_status validate(const KP &kp) {
     case FAM_TC:
         if (kp.i(0) < 256 || kp.i(0) % 256 || kp.i(0) > 32768)
             return fail(PM_EINVAL, "%s: n must be a multiple of 256 in [256, 32768]", nm);
-        if (kp.i(1) != 0 && kp.i(1) != 1)
-            return fail(PM_EINVAL, "%s: pipe must be 0 (4 stages, 1 CTA/SM) or 1 (2 stages, 2 CTAs/SM)", nm);
+        if (kp.i(1) < 0 || kp.i(1) > 2)
+            return fail(PM_EINVAL, "%s: pipe must be 0 (4 stages, 1 CTA/SM), 1 (2 stages, 2 CTAs/SM) or 2 (persistent)",
+                        nm);
         return PM_OK;
     case FAM_SIMT: {
         i64 n = kp.i(0), BM = kp.i(1), BN = kp.i(2), BK = kp.i(3);

@@ -20,6 +20,7 @@
 // Every mbarrier wait is bounded; on timeout the kernel sets an error word
 // (read by the host after synchronising), stops issuing work, drains its own
 // copies (bounded), frees its TMEM and returns.
+#include <algorithm>
 #include <cuda.h>
 #include <cuda_runtime.h>
 #include <cudaTypedefs.h>
@@ -213,6 +214,167 @@ __global__ void __launch_bounds__(128, MINB) k_mm_tc(const __grid_constant__ CUt
     }
 }
 
+// ---------------------------------------------------------------- persistent
+// One CTA of 192 threads per SM walks the tiles t = blockIdx.x, +gridDim.x,
+// ... (same CTA -> tile numbering as above): warp 0 lane 0 produces into a
+// 4-stage ring that runs on across tiles, warp 1 lane 0 issues the MMAs into
+// one of two TMEM accumulators (2 x 256 columns), and warps 2-5 drain the
+// other accumulator (warp w reads TMEM lanes 32 (w mod 4) ...), so a tile's
+// epilogue overlaps the next tile's main loop.  Accumulator b is handed over
+// by tfull[b] (MMA commit) and returned by tempty[b] (one arrival per
+// epilogue warp).  The tile <-> logical work-group correspondence is the
+// same bijection as above, so the counts of the logical decomposition hold;
+// only the CTA schedule differs.
+constexpr int PST = 4;
+struct __align__(8) TcPersist {
+    uint64_t full[PST], empty[PST], tfull[2], tempty[2], done;
+    uint32_t tmem_base;
+    int issued;
+};
+constexpr size_t kPersistSmem = (size_t)PST * STAGE_BYTES + sizeof(TcPersist) + 2048;
+
+__device__ __forceinline__ void tile_origin(int t, int ntm, int ntn, int &m0, int &n0) {
+    const int per_group = GROUP_M * ntn, grp = t / per_group, first = grp * GROUP_M;
+    const int gsz = min(ntm - first, GROUP_M), r = t - grp * per_group;
+    m0 = (first + r % gsz) * TM;
+    n0 = (r / gsz) * TN;
+}
+
+__global__ void __launch_bounds__(192, 1) k_mm_tc_persist(const __grid_constant__ CUtensorMap tmA,
+                                                          const __grid_constant__ CUtensorMap tmB,
+                                                          float *__restrict__ C, int M, int N, int K) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    TcPersist *S = (TcPersist *)(base + PST * STAGE_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int ntm = M / TM, ntn = N / TN, tiles = ntm * ntn, KT = K / TK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < PST; s++) {
+            mbar_init(&S->full[s], 1);
+            mbar_init(&S->empty[s], 1);
+        }
+        for (int b = 0; b < 2; b++) {
+            mbar_init(&S->tfull[b], 1);
+            mbar_init(&S->tempty[b], 4);
+        }
+        mbar_init(&S->done, 1);
+        S->issued = 0;
+        mbar_init_fence();
+    }
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S->tmem_base)),
+                     "r"(2 * TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            int it = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x) {
+                int m0, n0;
+                tile_origin(t, ntm, ntn, m0, n0);
+                for (int kt = 0; kt < KT; kt++, it++) {
+                    const int s = it % PST, r = it / PST;
+                    if (r > 0 && !mbar_wait(&S->empty[s], (uint32_t)((r - 1) & 1))) { ok = false; break; }
+                    unsigned char *st = base + s * STAGE_BYTES;
+                    mbar_expect_tx(&S->full[s], STAGE_BYTES);
+                    tma_load_2d(st, &tmA, &S->full[s], kt * TK, m0);
+                    tma_load_2d(st + A_BYTES, &tmB, &S->full[s], kt * TK, n0);
+                    S->issued = it + 1;
+                }
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            int it = 0, lt = 0;
+            bool ok = true;
+            for (int t = blockIdx.x; t < tiles && ok; t += gridDim.x, lt++) {
+                const int b = lt & 1, u = lt >> 1;
+                if (u > 0 && !mbar_wait(&S->tempty[b], (uint32_t)((u - 1) & 1))) break;
+                tc_fence_after();
+                const uint32_t d = tmem + (uint32_t)(b * TMEM_COLS);
+                for (int kt = 0; kt < KT; kt++, it++) {
+                    const int s = it % PST, r = it / PST;
+                    if (!mbar_wait(&S->full[s], (uint32_t)(r & 1))) { ok = false; break; }
+                    tc_fence_after();
+                    unsigned char *st = base + s * STAGE_BYTES;
+                    const uint64_t ad = smem_desc(st), bd = smem_desc(st + A_BYTES);
+#pragma unroll
+                    for (int kk = 0; kk < TK / 16; kk++)
+                        mma_bf16(d, ad + 2 * kk, bd + 2 * kk, (kt > 0 || kk > 0) ? 1u : 0u);
+                    mma_commit(&S->empty[s]);
+                }
+                if (ok) mma_commit(&S->tfull[b]);
+            }
+            mma_commit(&S->done);   // arrives once every MMA this thread issued has completed
+        }
+        __syncwarp();
+    } else {
+        const int q = warp & 3;   // TMEM lane quarter this warp may read
+        int lt = 0;
+        for (int t = blockIdx.x; t < tiles; t += gridDim.x, lt++) {
+            const int b = lt & 1, u = lt >> 1;
+            const bool got = mbar_wait(&S->tfull[b], (uint32_t)(u & 1));
+            if (!__all_sync(0xffffffffu, got)) break;
+            tc_fence_after();
+            int m0, n0;
+            tile_origin(t, ntm, ntn, m0, n0);
+            float *crow = C + (size_t)(m0 + q * 32 + lane) * N + n0;
+#pragma unroll 1
+            for (int c = 0; c < TN / 32; c++) {
+                uint32_t v[32];
+                const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(b * TMEM_COLS + c * 32);
+                asm volatile(
+                    "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, "
+                    "%13, %14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, "
+                    "[%32];"
+                    : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                      "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]),
+                      "=r"(v[15]), "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]),
+                      "=r"(v[22]), "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]),
+                      "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
+                    : "r"(taddr));
+                asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+                float4 *dst = reinterpret_cast<float4 *>(crow + c * 32);
+#pragma unroll
+                for (int k = 0; k < 8; k++)
+                    dst[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
+                                         __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3]));
+            }
+            tc_fence_before();
+            __syncwarp();
+            if (lane == 0) mbar_arrive(&S->tempty[b]);
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && *(volatile int *)&g_tc_timeout) {
+        // drain: every stage's last issued copy must land before the shared memory goes away
+        const int issued = S->issued;
+        for (int s = 0; s < PST && s < issued; s++) {
+            const int last = s + ((issued - 1 - s) / PST) * PST;
+            for (long long i = 0; i < WAIT_LIMIT; i++)
+                if (mbar_try(&S->full[s], (uint32_t)((last / PST) & 1))) break;
+        }
+    }
+    __syncthreads();
+    if (warp == 1) {
+        mbar_wait(&S->done, 0);   // no MMA may still write the accumulators being released
+        __syncwarp();
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS)
+                     : "memory");
+    }
+}
+
 }  // namespace
 
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -268,7 +430,17 @@ pm_status launch_tc(const KP &kp, void *const *b, void *stream) {
     if ((s = tensor_map_2d(&ta, 1, b[0], n, n, (uint64_t)n * 2, TK, TM, 1))) return s;
     if ((s = tensor_map_2d(&tb, 1, b[1], n, n, (uint64_t)n * 2, TK, TN, 1))) return s;
     if (pipe == 0) return launch_tc_t<4, 1>(ta, tb, (float *)b[2], n, (cudaStream_t)stream);
-    return launch_tc_t<2, 2>(ta, tb, (float *)b[2], n, (cudaStream_t)stream);
+    if (pipe == 1) return launch_tc_t<2, 2>(ta, tb, (float *)b[2], n, (cudaStream_t)stream);
+    // persistent: one CTA per SM (at most one per tile)
+    int dev = 0, sms = 0;
+    PM_CUDA_TRY(cudaGetDevice(&dev));
+    PM_CUDA_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    const int tiles = (n / TN) * (n / TM);
+    PM_CUDA_TRY(cudaFuncSetAttribute(k_mm_tc_persist, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kPersistSmem));
+    launch_k(k_mm_tc_persist, (unsigned)std::min(tiles, sms), 192, kPersistSmem, (cudaStream_t)stream, ta, tb,
+             (float *)b[2], n, n, n);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
 }
 
 // After a synchronisation: PM_ETIMEOUT if any CTA's bounded wait ran out

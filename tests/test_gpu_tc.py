@@ -32,7 +32,7 @@ def run_tc(n, seed, pipe=1):
     return a, bt, c.cpu().numpy().reshape(n, n)
 
 
-@pytest.mark.parametrize("pipe", [0, 1])
+@pytest.mark.parametrize("pipe", [0, 1, 2])
 @pytest.mark.parametrize("n", [256, 512, 1024])
 def test_mm_tc_matches_oracle(n, pipe):
     a, bt, c = run_tc(n, 40 + n, pipe)
@@ -41,7 +41,7 @@ def test_mm_tc_matches_oracle(n, pipe):
     assert err.max() <= TOL, err.max()
 
 
-@pytest.mark.parametrize("pipe", [0, 1])
+@pytest.mark.parametrize("pipe", [0, 1, 2])
 @pytest.mark.parametrize("n", [2304, 4352])
 def test_mm_tc_partial_tile_groups(n, pipe):
     # 18 and 34 tile rows: the last group of 16 tile rows is partial; every
