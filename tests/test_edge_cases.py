@@ -60,7 +60,7 @@ def test_counts_cap_protocol():
 
 
 @pytest.mark.parametrize("kernel,params", [
-    ("mm_pf", dict(n=0)), ("mm_pf", dict(n=17)), ("mm_tc", dict(n=384)), ("mm_tc", dict(n=512, pipe=2)),
+    ("mm_pf", dict(n=0)), ("mm_pf", dict(n=17)), ("mm_tc", dict(n=384)), ("mm_tc", dict(n=512, pipe=3)),
     ("fd_block", dict(n=100, BX=64, BY=8)), ("fd_block", dict(n=256, BX=64, BY=8, V=2)),
     ("fd_tile", dict(n=0)), ("dg_upf", dict(Np=20, Nel=32, L0=32, L1=8)), ("dg_nopf", dict(Np=0, Nel=32)),
     ("smem2d", dict(R=8, T=17, G=1)), ("stream", dict(N=1000)), ("stream", dict(N=1 << 20, s=3)),
