@@ -146,6 +146,40 @@ typedef struct {
 pm_status pm_counts(int32_t kernel, const pm_param *p, size_t np,
                     pm_feature *out, size_t cap, size_t *n_out);
 
+/* Size parameter over which pm_counts_desc extrapolates: counts are
+ * quasi-polynomials in it of the given period and degree bound. */
+typedef struct {
+    const char *name;
+    int32_t period;
+    int32_t degree;
+} pm_interp;
+
+/* Exact features of a kernel given as a text description of its affine loop
+ * nest instead of a registry name (Algorithm 1 and Algorithm 2 over a
+ * user's kernel; the paper counts such kernels with a polyhedral library,
+ * Section "Gathering Kernel Statistics").  Format, one item per line, '#'
+ * starts a comment:
+ *   params <name>...                      size parameters
+ *   grid <e0> [<e1> [<e2>]]               work-group counts per axis
+ *   group <e0> [<e1> [<e2>]]              work-items per group per axis
+ *   stmt | barrier                        a statement / a local barrier, then:
+ *     loop <var> <lo> <hi>                loop (hi exclusive), outermost first
+ *     guard <expr>                        executes only where expr >= 0
+ *     ops <float32|float64|bfloat16> <add> <mul> <madd>
+ *     access <tag> <global|local> <load|store> <dtype> <bytes> <index expr>
+ * Expressions: integers, parameters, g0 g1 g2 l0 l1 l2 (group and local
+ * ids), the statement's loop variables, + - * / (floor) % min(,) max(,) and
+ * parentheses; index expressions must be affine in the ids and loop
+ * variables.  Records and granularities are those of pm_counts; tags must be
+ * unique (a model can name a tag only if it contains no '_').  With interp
+ * (nullable), each listed parameter
+ * is extrapolated exactly from degree + 2 enumerated sizes of its residue
+ * class (PM_EINVAL if the extra sample contradicts the degree bound);
+ * without it every loop point is enumerated (at most 2^31 statement
+ * instances).  Pure host computation; *n_out and PM_ECAP as pm_counts. */
+pm_status pm_counts_desc(const char *description, const pm_param *p, size_t np, const pm_interp *interp,
+                         size_t ninterp, pm_feature *out, size_t cap, size_t *n_out);
+
 /* Compiled resources and launch shape of one kernel instance, for an
  * autotuner's pruning step (the paper's use of a model as a heuristic that
  * narrows the variants worth timing, Section "Assumptions and Limitations"):

@@ -49,15 +49,9 @@ def _kid(kernel):
     return kernel if isinstance(kernel, int) else kernel_lookup(kernel)
 
 
-def counts(kernel, **params):
-    """Exact feature records (pm_counts) as dicts."""
-    arr, n, _keep = _params(params)
-    cap = 64
-    out = (pm_feature * cap)()
-    nout = ctypes.c_size_t()
-    check(lib().pm_counts(_kid(kernel), arr, n, out, cap, ctypes.byref(nout)))
+def _records(out, count):
     recs = []
-    for i in range(nout.value):
+    for i in range(count):
         f = out[i]
         r = dict(name=f.name.decode(), kind=_KIND[f.kind], gran=_GRAN[f.gran], count=f.count)
         if f.kind == 0:
@@ -69,6 +63,38 @@ def counts(kernel, **params):
                      footprint=f.footprint, count_wi=f.count_wi, count_sg=f.count_sg)
         recs.append(r)
     return recs
+
+
+def counts(kernel, **params):
+    """Exact feature records (pm_counts) as dicts."""
+    out, n = _counts_raw(kernel, **params)
+    return _records(out, n)
+
+
+def _counts_desc_raw(description, interp=None, **params):
+    arr, n, _keep = _params(params)
+    interp = interp or {}
+    names = [k.encode() for k in interp]
+    ip = (_lib.pm_interp * max(1, len(interp)))()
+    for i, (k, (period, degree)) in enumerate(interp.items()):
+        ip[i] = _lib.pm_interp(names[i], int(period), int(degree))
+    cap = 64
+    while True:
+        out = (pm_feature * cap)()
+        nout = ctypes.c_size_t()
+        st = lib().pm_counts_desc(description.encode(), arr, n, ip, len(interp), out, cap, ctypes.byref(nout))
+        if st == -9 and nout.value > cap:
+            cap = nout.value
+            continue
+        check(st)
+        return out, nout.value
+
+
+def counts_desc(description, interp=None, **params):
+    """Exact feature records of a kernel given as a loop-nest description
+    (pm_counts_desc).  interp: {parameter: (period, degree bound)} for sizes
+    too large to enumerate."""
+    return _records(*_counts_desc_raw(description, interp, **params))
 
 
 def _counts_raw(kernel, **params):
@@ -229,6 +255,13 @@ class Model:
     @property
     def handle(self):
         return self._h
+
+    def feature_values_desc(self, description, interp=None, **params):
+        """One design-matrix row on a kernel given as a loop-nest description."""
+        feats, n = _counts_desc_raw(description, interp, **params)
+        row = (ctypes.c_double * max(1, len(self.features)))()
+        check(lib().pm_feature_values(self._h, feats, n, row))
+        return np.array(row[:len(self.features)], dtype=np.float64)
 
     def feature_values(self, kernel, **params):
         """One design-matrix row: this model's features on kernel(params)."""

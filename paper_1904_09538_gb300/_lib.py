@@ -35,6 +35,10 @@ class pm_resources(ctypes.Structure):
                 ("blocks_per_sm", ctypes.c_int32), ("sm_count", ctypes.c_int32), ("grid_blocks", ctypes.c_uint64)]
 
 
+class pm_interp(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char_p), ("period", ctypes.c_int32), ("degree", ctypes.c_int32)]
+
+
 class pm_host_job(ctypes.Structure):
     _fields_ = [("kernel", ctypes.c_int32), ("p", ctypes.c_void_p), ("np", ctypes.c_size_t),
                 ("host_bufs", ctypes.c_void_p), ("nbufs", ctypes.c_size_t)]
@@ -74,6 +78,8 @@ SIGNATURES = {
     "pm_kernel_name": (i32, [i32, P(ctypes.c_char_p)]),
     "pm_kernel_buffers": (i32, [i32, P(pm_param), c_size_t, P(pm_buffer), c_size_t, P(c_size_t)]),
     "pm_counts": (i32, [i32, P(pm_param), c_size_t, P(pm_feature), c_size_t, P(c_size_t)]),
+    "pm_counts_desc": (i32, [ctypes.c_char_p, P(pm_param), c_size_t, P(pm_interp), c_size_t, P(pm_feature), c_size_t,
+                             P(c_size_t)]),
     "pm_launch": (i32, [i32, P(pm_param), c_size_t, P(vp), c_size_t, vp]),
     "pm_kernel_resources": (i32, [i32, P(pm_param), c_size_t, P(pm_resources)]),
     "pm_run": (i32, [i32, P(pm_param), c_size_t, P(vp), c_size_t, P(pm_run_opts), vp, fp, P(pm_timing)]),
