@@ -1,0 +1,67 @@
+"""Time the batched calibration: python -m paper_1904_09538_gb300.fitbench
+[--models K] [--reps R] [--threads T]
+
+K models (alternately linear and tanh-overlap, 40..400 rows each, seeded
+synthetic features and model-plus-noise outputs) fitted in one batched plan
+(one persistent launch in a CUDA graph), R timed replays.  Prints one JSON
+line: fits per second, milliseconds per replay, status counts."""
+import json
+import sys
+import time
+
+import numpy as np
+
+
+def main(argv):
+    import torch
+    import pm_inputs
+    from . import Model, FitPlan
+    from .suite import LAUNCH
+    K, reps, threads = 64, 10, 128
+    it = iter(argv)
+    for a in it:
+        if a == "--models":
+            K = int(next(it))
+        elif a == "--reps":
+            reps = int(next(it))
+        elif a == "--threads":
+            threads = int(next(it))
+    lin = LAUNCH + " + p_add * f_op_float32_add + p_madd * f_op_float32_madd + p_gmem * f_mem_access_global_float32"
+    cg = "(p_gmem * f_mem_access_global_float32)"
+    co = "(p_madd * f_op_float32_madd + p_lmem * f_mem_access_local_float32)"
+    ovl = (LAUNCH + " + %s * (tanh(p_edge * (%s - %s)) + 1) / 2 + %s * (tanh(p_edge * (%s - %s)) + 1) / 2"
+           % (cg, cg, co, co, co, cg))
+    truth = {"p_launch": 5e-6, "p_group": 2e-9, "p_add": 4e-12, "p_madd": 3e-12, "p_gmem": 6e-12, "p_lmem": 2e-12,
+             "p_edge": 3e4}
+    ls = pm_inputs.row_counts(K, 4242)
+    models, Xs, ts, p0s = [], [], [], []
+    for k in range(K):
+        m = Model("f_wall_time", lin if k % 2 == 0 else ovl)
+        l = int(ls[k])
+        X = pm_inputs.integers((l, len(m.features)), 9000 + k, 10 ** 5, 10 ** 7).astype(np.float64)
+        X[:, 0] = 1.0
+        X[:, 1] = pm_inputs.integers((l,), 9500 + k, 100, 10 ** 4)
+        pt = np.array([truth[n] for n in m.params])
+        models.append(m)
+        Xs.append(X)
+        ts.append(m.predict(pt, X) * (1 + 1e-2 * pm_inputs.noise((l,), 9900 + k)))
+        p0s.append(pt * 1.2)
+    plan = FitPlan(models, [len(t) for t in ts], p0_given=True, threads=threads)
+    Xc = np.concatenate([x.ravel() for x in Xs])
+    tc = np.concatenate(ts)
+    pc = np.concatenate(p0s)
+    plan.run(Xc, tc, pc)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(reps):
+        _, out = plan.run(Xc, tc, pc)
+    dt = (time.perf_counter() - t0) / reps
+    st = [r["status"] for r in out]
+    print(json.dumps({"models": K, "rows": [int(ls.min()), int(ls.max())], "threads": threads,
+                      "ms_per_batch": dt * 1e3, "fits_per_s": K / dt,
+                      "iterations_max": max(r["iterations"] for r in out),
+                      "statuses": {str(s): st.count(s) for s in sorted(set(st))}}))
+
+
+if __name__ == "__main__":
+    main(sys.argv[1:])
