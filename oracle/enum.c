@@ -935,7 +935,8 @@ static int setup_fd(ctx *c, int v) {
  * Register-tiled SIMT matmul family (autotuning space): C = A B, n x n fp32,
  * 16-byte vector (float32x4) global accesses.  P = {n, BM, BN, BK}.
  * Work-group L0 x L1 = (BN/8) x (BM/8); each work-item owns an 8 x 8 block
- * of C (rows 8 lid1 .., columns 8 lid0 ..).  Per k tile (BK wide):
+ * of C (rows 8 lid1 .., vector columns lid0 and L0 + lid0).  Per k tile
+ * (BK wide):
  *   barrier;
  *   A tile: rows lid1 + L1 r (r < 8), vector columns c = lid0 + L0 q
  *           (q < ceil(KC/L0), guard c < KC, KC = BK/4); stored transposed as
@@ -944,8 +945,9 @@ static int setup_fd(ctx *c, int v) {
  *           columns c = lid0 + L0 q (q < 2); stored as one vector Bs[row NC + c];
  *   barrier;
  *   kk < BK: two vector loads of As (8 values at kk BM + 8 lid1), two of Bs
- *           (8 values at kk BN + 8 lid0), 64 multiply-adds.
- * Finally 8 x 2 vector stores of C.  Requires n divisible by BM, BN, BK.
+ *           (vectors lid0 and L0 + lid0 of row kk), 64 multiply-adds.
+ * Finally 8 x 2 vector stores of C (rows 8 lid1 + i, vector columns
+ * NC gid0 + lid0 + L0 j).  Requires n divisible by BM, BN, BK.
  * Index units: float32x4 (vectors) for global and Bs / As vector loads,
  * float32 for the scalar As stores.
  * ====================================================================== */
@@ -982,14 +984,14 @@ static long long ix_sm_ald(const ctx *c, const long long *g, const long long *l,
 static long long ix_sm_ald0(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_ald(c, g, l, lv, 0); }
 static long long ix_sm_ald1(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_ald(c, g, l, lv, 1); }
 static long long ix_sm_bld(const ctx *c, const long long *g, const long long *l, const long long *lv, int h) {
-    (void)g; return lv[1] * (SM_BN(c) / 4) + 2 * L0_ + h;
+    (void)g; return lv[1] * (SM_BN(c) / 4) + L0_ + (SM_BN(c) / 8) * h;
 }
 static long long ix_sm_bld0(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_bld(c, g, l, lv, 0); }
 static long long ix_sm_bld1(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_bld(c, g, l, lv, 1); }
 static long long ix_sm_c(const ctx *c, const long long *g, const long long *l, const long long *lv) {
     /* lv = {i, j} */
     long long n4 = SM_N(c) / 4, NC = SM_BN(c) / 4;
-    return n4 * (SM_BM(c) * G1 + 8 * L1_ + lv[0]) + NC * G0 + 2 * L0_ + lv[1];
+    return n4 * (SM_BM(c) * G1 + 8 * L1_ + lv[0]) + NC * G0 + L0_ + (SM_BN(c) / 8) * lv[1];
 }
 static void walk_simt(ctx *c) {
     long long n = SM_N(c), BK = SM_BK(c), KC = BK / 4, L0 = SM_BN(c) / 8, L1 = SM_BM(c) / 8;

@@ -336,3 +336,19 @@ def test_fd_block_counts(n, BX, BY, V):
     r = by_tag(fs, "fdb-res")
     assert r["count"] == r["footprint"] == n * n // 4 and r["lstr"] == (V // 4, n // 4)
     assert single(fs, "sync") == 1 and single(fs, "groups") == G
+
+
+@pytest.mark.parametrize("n,BM,BN,BK", [(192, 96, 64, 32), (256, 128, 64, 64), (256, 64, 128, 32)])
+def test_simt_closed_forms(n, BM, BN, BK):
+    # register-tiled matmul: n^3 multiply-adds, A read n/BN times and B n/BM
+    # times (16-byte vectors), every C vector stored once; the B fragment is
+    # read as vectors lid0 and L0 + lid0 (lid(0) stride 1)
+    fs = features("mm_simt", n=n, BM=BM, BN=BN, BK=BK)
+    assert op(fs, "float32", "madd", wi=True) == n ** 3
+    assert by_tag(fs, "simt-a")["count_wi"] == n ** 3 // (4 * BN)
+    assert by_tag(fs, "simt-b")["count_wi"] == n ** 3 // (4 * BM)
+    c = by_tag(fs, "simt-c")
+    assert c["count_wi"] == c["footprint"] == n * n // 4 and c["lstr"][0] == 1 and c["loopstr"] == BN // 8
+    for t in ("Bs_ld0", "Bs_ld1"):
+        assert by_tag(fs, t)["lstr"] == (1, 0)
+    assert single(fs, "sync") == 2 * (n // BK)
