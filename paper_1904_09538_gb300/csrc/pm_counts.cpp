@@ -587,9 +587,9 @@ pm_status counts_simt(const KP &kp, std::vector<pm_feature> &v) {
     const u64 cWI = (u64)(G * T * K * BK), cSG = (u64)(G * S * K * BK);
     site("As_ld0", LO, LD, "float32x4", 16, 0, 2, 0, 0, BM / 4, cWI, cSG, (u64)(BK * L1));
     site("As_ld1", LO, LD, "float32x4", 16, 0, 2, 0, 0, BM / 4, cWI, cSG, (u64)(BK * L1));
-    site("Bs_ld0", LO, LD, "float32x4", 16, 2, 0, 0, 0, NC, cWI, cSG, (u64)(BK * L0));
-    site("Bs_ld1", LO, LD, "float32x4", 16, 2, 0, 0, 0, NC, cWI, cSG, (u64)(BK * L0));
-    site("simt-c", GL, ST, "float32x4", 16, 2, 2 * n, NC, BM * n4, 1, (u64)(G * T * 16), (u64)(G * S * 16), full);
+    site("Bs_ld0", LO, LD, "float32x4", 16, 1, 0, 0, 0, NC, cWI, cSG, (u64)(BK * L0));
+    site("Bs_ld1", LO, LD, "float32x4", 16, 1, 0, 0, 0, NC, cWI, cSG, (u64)(BK * L0));
+    site("simt-c", GL, ST, "float32x4", 16, 1, 2 * n, NC, BM * n4, L0, (u64)(G * T * 16), (u64)(G * S * 16), full);
     o.finish((u64)(2 * K), (u64)G);
     return PM_OK;
 }

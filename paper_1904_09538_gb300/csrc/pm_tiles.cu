@@ -1,6 +1,7 @@
 // Autotuning spaces: the register-tiled SIMT fp32 matmul family (24 tile
 // shapes).  Loop nest (the one pm_counts counts), work-group (BN/8) x (BM/8),
-// every work-item owns an 8 x 8 block of C:
+// every work-item owns 8 rows (8 lid1 + i) x 2 column vectors (lid0 and
+// L0 + lid0, L0 = BN/8) of C:
 //   per k tile of width BK:
 //     barrier;
 //     A tile, rows lid1 + L1 r (r < 8), vector columns lid0 + L0 q (< BK/4),
@@ -8,8 +9,10 @@
 //     B tile, rows lid1 + L1 r (< BK), vector columns lid0 + L0 q (q < 2),
 //       one 16-byte load and one 16-byte shared store each;
 //     barrier;
-//     for kk < BK: two 16-byte shared loads of A (8 rows), two of B (8
-//       columns), 64 fused multiply-adds;
+//     for kk < BK: two 16-byte shared loads of A (8 rows), two of B
+//       (vectors lid0 and L0 + lid0 of row kk, so the 16-byte words of
+//       consecutive threads are adjacent and the loads are bank-conflict
+//       free), 64 fused multiply-adds;
 //   16 vector stores of C.
 // The shared-memory tiles take (BM + BN) * BK * 4 bytes (up to 128 KiB).
 //
@@ -83,8 +86,9 @@ __global__ void __launch_bounds__((BM / 8) * (BN / 8)) k_mm_simt(const float4 *_
         for (int kk = 0; kk < BK; kk++) {
             const float4 a0 = reinterpret_cast<const float4 *>(As)[kk * (BM / 4) + 2 * l1];
             const float4 a1 = reinterpret_cast<const float4 *>(As)[kk * (BM / 4) + 2 * l1 + 1];
-            const float4 b0 = reinterpret_cast<const float4 *>(Bs)[kk * NC + 2 * l0];
-            const float4 b1 = reinterpret_cast<const float4 *>(Bs)[kk * NC + 2 * l0 + 1];
+            // vectors lid0 and L0 + lid0: consecutive threads read consecutive 16-byte words
+            const float4 b0 = reinterpret_cast<const float4 *>(Bs)[kk * NC + l0];
+            const float4 b1 = reinterpret_cast<const float4 *>(Bs)[kk * NC + L0 + l0];
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
             const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
 #pragma unroll
@@ -98,7 +102,7 @@ __global__ void __launch_bounds__((BM / 8) * (BN / 8)) k_mm_simt(const float4 *_
         const size_t row = arow0 + 8 * l1 + i;
 #pragma unroll
         for (int h = 0; h < 2; h++)
-            C4[n4 * row + (size_t)NC * blockIdx.x + 2 * l0 + h] =
+            C4[n4 * row + (size_t)NC * blockIdx.x + l0 + L0 * h] =
                 make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
     }
 }
