@@ -940,11 +940,12 @@ static int setup_fd(ctx *c, int v) {
  *   barrier;
  *   A tile: rows lid1 + L1 r (r < 8), vector columns c = lid0 + L0 q
  *           (q < ceil(KC/L0), guard c < KC, KC = BK/4); stored transposed as
- *           four scalars As[(4c + j) BM + row] (j < 4);
+ *           four scalars As[(4c + j) (BM + 4) + row] (j < 4; rows padded by 4
+ *           so that the 8 columns of a warp fall on 4 banks, not 1);
  *   B tile: rows lid1 + L1 r (r < ceil(BK/L1), guard row < BK), vector
  *           columns c = lid0 + L0 q (q < 2); stored as one vector Bs[row NC + c];
  *   barrier;
- *   kk < BK: two vector loads of As (8 values at kk BM + 8 lid1), two of Bs
+ *   kk < BK: two vector loads of As (8 values at kk (BM + 4) + 8 lid1), two of Bs
  *           (vectors lid0 and L0 + lid0 of row kk), 64 multiply-adds.
  * Finally 8 x 2 vector stores of C (rows 8 lid1 + i, vector columns
  * NC gid0 + lid0 + L0 j).  Requires n divisible by BM, BN, BK.
@@ -962,8 +963,8 @@ static long long ix_sm_a(const ctx *c, const long long *g, const long long *l, c
 }
 static long long ix_sm_ast(const ctx *c, const long long *g, const long long *l, const long long *lv, int j) {
     (void)g;
-    long long L0 = SM_BN(c) / 8, L1 = SM_BM(c) / 8, BM = SM_BM(c);
-    return (4 * (L0_ + L0 * lv[2]) + j) * BM + L1_ + L1 * lv[1];
+    long long L0 = SM_BN(c) / 8, L1 = SM_BM(c) / 8, BMP = SM_BM(c) + 4;
+    return (4 * (L0_ + L0 * lv[2]) + j) * BMP + L1_ + L1 * lv[1];
 }
 static long long ix_sm_ast0(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_ast(c, g, l, lv, 0); }
 static long long ix_sm_ast1(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_ast(c, g, l, lv, 1); }
@@ -979,7 +980,7 @@ static long long ix_sm_bst(const ctx *c, const long long *g, const long long *l,
     return (L1_ + L1 * lv[1]) * NC + L0_ + L0 * lv[2];
 }
 static long long ix_sm_ald(const ctx *c, const long long *g, const long long *l, const long long *lv, int h) {
-    (void)g; return lv[1] * (SM_BM(c) / 4) + 2 * L1_ + h;
+    (void)g; return lv[1] * ((SM_BM(c) + 4) / 4) + 2 * L1_ + h;
 }
 static long long ix_sm_ald0(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_ald(c, g, l, lv, 0); }
 static long long ix_sm_ald1(const ctx *c, const long long *g, const long long *l, const long long *lv) { return ix_sm_ald(c, g, l, lv, 1); }
