@@ -581,12 +581,13 @@ pm_status counts_simt(const KP &kp, std::vector<pm_feature> &v) {
     const u64 full = (u64)(n * n / 4);
     site("simt-a", GL, LD, "float32x4", 16, 1, n4, 0, BM * n4, L0, aWI, aSG, full);
     static const char *ast[4] = {"As_st0", "As_st1", "As_st2", "As_st3"};
-    for (int j = 0; j < 4; j++) site(ast[j], LO, ST, "float32", 4, 4 * BM, 1, 0, 0, 4 * L0 * BM, aWI, aSG, (u64)(BM * KC));
+    const i64 BMP = BM + 4;   // padded row of the transposed A tile
+    for (int j = 0; j < 4; j++) site(ast[j], LO, ST, "float32", 4, 4 * BMP, 1, 0, 0, 4 * L0 * BMP, aWI, aSG, (u64)(BM * KC));
     site("simt-b", GL, LD, "float32x4", 16, 1, n4, NC, 0, L0, bWI, bSG, full);
     site("Bs_st", LO, ST, "float32x4", 16, 1, NC, 0, 0, L0, bWI, bSG, (u64)(BK * NC));
     const u64 cWI = (u64)(G * T * K * BK), cSG = (u64)(G * S * K * BK);
-    site("As_ld0", LO, LD, "float32x4", 16, 0, 2, 0, 0, BM / 4, cWI, cSG, (u64)(BK * L1));
-    site("As_ld1", LO, LD, "float32x4", 16, 0, 2, 0, 0, BM / 4, cWI, cSG, (u64)(BK * L1));
+    site("As_ld0", LO, LD, "float32x4", 16, 0, 2, 0, 0, BMP / 4, cWI, cSG, (u64)(BK * L1));
+    site("As_ld1", LO, LD, "float32x4", 16, 0, 2, 0, 0, BMP / 4, cWI, cSG, (u64)(BK * L1));
     site("Bs_ld0", LO, LD, "float32x4", 16, 1, 0, 0, 0, NC, cWI, cSG, (u64)(BK * L0));
     site("Bs_ld1", LO, LD, "float32x4", 16, 1, 0, 0, 0, NC, cWI, cSG, (u64)(BK * L0));
     site("simt-c", GL, ST, "float32x4", 16, 1, 2 * n, NC, BM * n4, L0, (u64)(G * T * 16), (u64)(G * S * 16), full);

@@ -5,7 +5,8 @@
 //   per k tile of width BK:
 //     barrier;
 //     A tile, rows lid1 + L1 r (r < 8), vector columns lid0 + L0 q (< BK/4),
-//       one 16-byte load each, stored transposed (k-major) as four floats;
+//       one 16-byte load each, stored transposed (k-major, rows padded to
+//       BM + 4 floats) as four floats;
 //     B tile, rows lid1 + L1 r (< BK), vector columns lid0 + L0 q (q < 2),
 //       one 16-byte load and one 16-byte shared store each;
 //     barrier;
@@ -14,7 +15,7 @@
 //       consecutive threads are adjacent and the loads are bank-conflict
 //       free), 64 fused multiply-adds;
 //   16 vector stores of C.
-// The shared-memory tiles take (BM + BN) * BK * 4 bytes (up to 128 KiB).
+// The shared-memory tiles take (BM + 4 + BN) * BK * 4 bytes (up to 129 KiB).
 //
 // Stencil tile family "fd_block" (12 shapes BX x BY, V = 4 or 8 outputs per
 // work-item): the five-point stencil on an input with a padded row pitch
@@ -40,9 +41,10 @@ __global__ void __launch_bounds__((BM / 8) * (BN / 8)) k_mm_simt(const float4 *_
                                                               float4 *__restrict__ C4, int n) {
     constexpr int L0 = BN / 8, L1 = BM / 8, KC = BK / 4, NC = BN / 4;
     constexpr int QA = (KC + L0 - 1) / L0, RB = (BK + L1 - 1) / L1;
+    constexpr int BMP = BM + 4;       // padded row: a warp's 8 transposed-store columns hit 4 banks, not 1
     extern __shared__ __align__(16) float smem[];
-    float *As = smem;                 // [BK][BM]
-    float *Bs = smem + BK * BM;       // [BK][BN]
+    float *As = smem;                 // [BK][BMP]
+    float *Bs = smem + BK * BMP;      // [BK][BN]
     const int l0 = threadIdx.x, l1 = threadIdx.y;
     const size_t n4 = (size_t)n / 4;
     const size_t arow0 = (size_t)BM * blockIdx.y;
@@ -62,10 +64,10 @@ __global__ void __launch_bounds__((BM / 8) * (BN / 8)) k_mm_simt(const float4 *_
                 const int c = l0 + L0 * q;
                 if (c < KC) {
                     const float4 v = A4[n4 * (arow0 + row) + (size_t)KC * kt + c];
-                    As[(4 * c + 0) * BM + row] = v.x;
-                    As[(4 * c + 1) * BM + row] = v.y;
-                    As[(4 * c + 2) * BM + row] = v.z;
-                    As[(4 * c + 3) * BM + row] = v.w;
+                    As[(4 * c + 0) * BMP + row] = v.x;
+                    As[(4 * c + 1) * BMP + row] = v.y;
+                    As[(4 * c + 2) * BMP + row] = v.z;
+                    As[(4 * c + 3) * BMP + row] = v.w;
                 }
             }
         }
@@ -84,8 +86,8 @@ __global__ void __launch_bounds__((BM / 8) * (BN / 8)) k_mm_simt(const float4 *_
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < BK; kk++) {
-            const float4 a0 = reinterpret_cast<const float4 *>(As)[kk * (BM / 4) + 2 * l1];
-            const float4 a1 = reinterpret_cast<const float4 *>(As)[kk * (BM / 4) + 2 * l1 + 1];
+            const float4 a0 = reinterpret_cast<const float4 *>(As)[kk * (BMP / 4) + 2 * l1];
+            const float4 a1 = reinterpret_cast<const float4 *>(As)[kk * (BMP / 4) + 2 * l1 + 1];
             // vectors lid0 and L0 + lid0: consecutive threads read consecutive 16-byte words
             const float4 b0 = reinterpret_cast<const float4 *>(Bs)[kk * NC + l0];
             const float4 b1 = reinterpret_cast<const float4 *>(Bs)[kk * NC + L0 + l0];
@@ -109,7 +111,7 @@ __global__ void __launch_bounds__((BM / 8) * (BN / 8)) k_mm_simt(const float4 *_
 
 template <int BM, int BN, int BK>
 pm_status launch_simt_t(void *const *b, int n, cudaStream_t st) {
-    constexpr size_t smem = (size_t)(BM + BN) * BK * sizeof(float);
+    constexpr size_t smem = (size_t)(BM + 4 + BN) * BK * sizeof(float);
     auto fn = k_mm_simt<BM, BN, BK>;
     PM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
     dim3 grid(n / BN, n / BM), blk(BN / 8, BM / 8);

@@ -308,7 +308,7 @@ def test_kernel_resources_report_launch_shape():
     dev()
     r = pm.resources("mm_simt", n=768, BM=128, BN=64, BK=32)
     assert r["threads_per_block"] == (128 // 8) * (64 // 8) and r["grid_blocks"] == (768 // 64) * (768 // 128)
-    assert r["dynamic_smem_bytes"] == (128 + 64) * 32 * 4 and r["blocks_per_sm"] >= 1 and r["sm_count"] > 0
+    assert r["dynamic_smem_bytes"] == (128 + 4 + 64) * 32 * 4 and r["blocks_per_sm"] >= 1 and r["sm_count"] > 0
     r = pm.resources("fd_block", n=1024, BX=64, BY=8)
     assert r["threads_per_block"] == 16 * 8 and r["grid_blocks"] == (1024 // 64) * (1024 // 8)
     r = pm.resources("stream", N=1 << 20, L=2, vec=1)
