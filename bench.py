@@ -328,6 +328,21 @@ def source_sha(f="pm_suite.cu", kernel="k_stream"):
     return hashlib.sha256(src[m.start():j].encode()).hexdigest()[:16]
 
 
+def gpu_local_cpus(torch, dev_index):
+    """Host CPUs local to the GPU's PCI device (Linux sysfs), or None."""
+    try:
+        pr = torch.cuda.get_device_properties(dev_index)
+        bus = "%04x:%02x:%02x.0" % (getattr(pr, "pci_domain_id"), getattr(pr, "pci_bus_id"), getattr(pr, "pci_device_id"))
+        text = open("/sys/bus/pci/devices/%s/local_cpulist" % bus).read().strip()
+        cpus = set()
+        for part in text.split(","):
+            a, _, b = part.partition("-")
+            cpus.update(range(int(a), int(b or a) + 1))
+        return cpus & os.sched_getaffinity(0) or None
+    except Exception:
+        return None
+
+
 def e2e_measure(pm, S, variants, torch, trials, fit_and_predict):
     """Same step through the public API with host buffers: pm_run_host_batch
     over every variant (pinned host buffers; per variant the host-to-device
@@ -336,6 +351,12 @@ def e2e_measure(pm, S, variants, torch, trials, fit_and_predict):
     copy of the next), then the batched calibration and the held-out
     predictions from host arrays.  One step."""
     import numpy as np
+    # staging buffers on the host memory next to the GPU: run (and first-touch
+    # the pinned pages) on the GPU's local CPUs
+    saved = os.sched_getaffinity(0)
+    local = gpu_local_cpus(torch, torch.cuda.current_device())
+    if local:
+        os.sched_setaffinity(0, local)
     need = 1
     for k, p in variants:
         for b in pm.kernel_buffers(k, **p):
@@ -369,8 +390,10 @@ def e2e_measure(pm, S, variants, torch, trials, fit_and_predict):
     fit_and_predict({i: t["mean_ms"] * 1e-3 for i, t in enumerate(tms)})
     torch.cuda.synchronize()
     dt = time.perf_counter() - t0
+    os.sched_setaffinity(0, saved)
     return {"value": round(nbytes / dt / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 2), "copy_ms": round(copy_ms, 1)}
+            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 2), "copy_ms": round(copy_ms, 1),
+            "host_cpus": len(local) if local else None}
 
 
 def fit_throughput(pm, torch, dev):
