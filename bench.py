@@ -401,31 +401,10 @@ def fit_throughput(pm, torch, dev):
     launch in a CUDA graph) vs the plain per-model fit (host-driven LM through
     the autograd.Function), same data, same start points."""
     import numpy as np
-    import pm_inputs
     from paper_1904_09538_gb300 import autograd as pag
-    from paper_1904_09538_gb300.suite import LAUNCH
+    from paper_1904_09538_gb300.fitbench import problem
     K = 64
-    ls = pm_inputs.row_counts(K, 4242)
-    lin = LAUNCH + " + p_add * f_op_float32_add + p_madd * f_op_float32_madd + p_gmem * f_mem_access_global_float32"
-    cg = "(p_gmem * f_mem_access_global_float32)"
-    co = "(p_madd * f_op_float32_madd + p_lmem * f_mem_access_local_float32)"
-    ovl = (LAUNCH + " + %s * (tanh(p_edge * (%s - %s)) + 1) / 2 + %s * (tanh(p_edge * (%s - %s)) + 1) / 2"
-           % (cg, cg, co, co, co, cg))
-    truth = {"p_launch": 5e-6, "p_group": 2e-9, "p_add": 4e-12, "p_madd": 3e-12, "p_gmem": 6e-12, "p_lmem": 2e-12,
-             "p_edge": 3e4}
-    models, Xs, ts, p0s = [], [], [], []
-    for k in range(K):
-        m = pm.Model("f_wall_time", lin if k % 2 == 0 else ovl)
-        l = int(ls[k])
-        X = pm_inputs.integers((l, len(m.features)), 9000 + k, 10 ** 5, 10 ** 7).astype(np.float64)
-        X[:, 0] = 1.0
-        X[:, 1] = pm_inputs.integers((l,), 9500 + k, 100, 10 ** 4)
-        pt = np.array([truth[n] for n in m.params])
-        t = m.predict(pt, X) * (1 + 1e-2 * pm_inputs.noise((l,), 9900 + k))
-        models.append(m)
-        Xs.append(X)
-        ts.append(t)
-        p0s.append(pt * 1.2)
+    models, Xs, ts, p0s, ls = problem(K)
     plan = pm.FitPlan(models, [len(t) for t in ts], p0_given=True)
     Xc = np.concatenate([x.ravel() for x in Xs])
     tc = np.concatenate(ts)

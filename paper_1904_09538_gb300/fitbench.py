@@ -12,20 +12,12 @@ import time
 import numpy as np
 
 
-def main(argv):
-    import torch
+def problem(K):
+    """K seeded calibration problems: (models, feature matrices, outputs,
+    start points = 1.2 x the parameters the outputs were made with)."""
     import pm_inputs
-    from . import Model, FitPlan
+    from . import Model
     from .suite import LAUNCH
-    K, reps, threads = 64, 10, 128
-    it = iter(argv)
-    for a in it:
-        if a == "--models":
-            K = int(next(it))
-        elif a == "--reps":
-            reps = int(next(it))
-        elif a == "--threads":
-            threads = int(next(it))
     lin = LAUNCH + " + p_add * f_op_float32_add + p_madd * f_op_float32_madd + p_gmem * f_mem_access_global_float32"
     cg = "(p_gmem * f_mem_access_global_float32)"
     co = "(p_madd * f_op_float32_madd + p_lmem * f_mem_access_local_float32)"
@@ -46,6 +38,22 @@ def main(argv):
         Xs.append(X)
         ts.append(m.predict(pt, X) * (1 + 1e-2 * pm_inputs.noise((l,), 9900 + k)))
         p0s.append(pt * 1.2)
+    return models, Xs, ts, p0s, ls
+
+
+def main(argv):
+    import torch
+    from . import FitPlan
+    K, reps, threads = 64, 10, 128
+    it = iter(argv)
+    for a in it:
+        if a == "--models":
+            K = int(next(it))
+        elif a == "--reps":
+            reps = int(next(it))
+        elif a == "--threads":
+            threads = int(next(it))
+    models, Xs, ts, p0s, ls = problem(K)
     plan = FitPlan(models, [len(t) for t in ts], p0_given=True, threads=threads)
     Xc = np.concatenate([x.ravel() for x in Xs])
     tc = np.concatenate(ts)
