@@ -403,9 +403,12 @@ def fit_throughput(pm, torch, dev):
     import numpy as np
     from paper_1904_09538_gb300 import autograd as pag
     from paper_1904_09538_gb300.fitbench import problem
+    from paper_1904_09538_gb300.autotune import tune_fit_threads
     K = 64
     models, Xs, ts, p0s, ls = problem(K)
-    plan = pm.FitPlan(models, [len(t) for t in ts], p0_given=True)
+    # the autotuner picks the fit kernel's CTA size for this batch
+    threads, tune_times = tune_fit_threads(models, Xs, ts, p0s, candidates=(64, 128, 256), reps=5)
+    plan = pm.FitPlan(models, [len(t) for t in ts], p0_given=True, threads=threads)
     Xc = np.concatenate([x.ravel() for x in Xs])
     tc = np.concatenate(ts)
     pc = np.concatenate(p0s)
@@ -433,7 +436,9 @@ def fit_throughput(pm, torch, dev):
         errs.append(float(np.max(np.abs(pp - ref) / np.abs(ref))))
     torch.cuda.synchronize()
     dt_p = (time.perf_counter() - t0) / len(sub)
-    return {"models": K, "rows": [int(ls.min()), int(ls.max())], "fits_per_s_batched": round(K / dt_b, 1),
+    return {"models": K, "rows": [int(ls.min()), int(ls.max())], "cta_threads": threads,
+            "tuned_ms": {str(k): round(v * 1e3, 3) for k, v in tune_times.items()},
+            "fits_per_s_batched": round(K / dt_b, 1),
             "fits_per_s_plain": round(1.0 / dt_p, 2), "speedup": round((K / dt_b) * dt_p, 1),
             "batched_ms": round(dt_b * 1e3, 3), "plain_ms_per_model": round(dt_p * 1e3, 2),
             "max_param_rel_diff_plain_vs_batched": max(errs),
