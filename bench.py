@@ -300,6 +300,8 @@ def run_ours(args):
         line["e2e"] = e2e_measure(pm, S, variants, torch, args.trials, fit_and_predict)
     if not args.no_fit_bench:
         line["fit"] = fit_throughput(pm, torch, dev)
+        if rank == 0 and world == 1 and not args.no_cpu:
+            line["fit"]["oracle_cpu"] = oracle_fit_rate()
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(variants, seconds=12.0)
     if rank == 0:
@@ -443,6 +445,31 @@ def fit_throughput(pm, torch, dev):
             "batched_ms": round(dt_b * 1e3, 3), "plain_ms_per_model": round(dt_p * 1e3, 2),
             "max_param_rel_diff_plain_vs_batched": max(errs),
             "statuses": {str(s): [r["status"] for r in reps].count(s) for s in set(r["status"] for r in reps)}}
+
+
+def oracle_fit_rate(seconds=5.0):
+    """The oracle's FP64 fits (SciPy Levenberg-Marquardt / least squares) on
+    the same 64 calibration problems, one host core, as many as fit in about
+    `seconds`: fits per second, for context beside the GPU fits."""
+    import numpy as np
+    import pm_inputs
+    from oracle import fit as ofit
+    from oracle.model import Model as OModel
+    from paper_1904_09538_gb300.fitbench import LIN, OVL, TRUTH, features
+    oms = [OModel("f_wall_time", LIN if k % 2 == 0 else OVL) for k in range(64)]
+    Xs, _ = features(64, lambda k: len(oms[k].features))
+    done, t0 = 0, time.perf_counter()
+    for k in range(64):
+        om = oms[k]
+        F = [dict(zip(om.features, row)) for row in Xs[k]]
+        t = np.array([om.eval(TRUTH, f) for f in F]) * (1 + 1e-2 * pm_inputs.noise((len(F),), 9900 + k))
+        p0 = np.array([TRUTH[n] for n in om.params]) * 1.2
+        ofit.fit(om, F, t, p0=p0)
+        done += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    dt = time.perf_counter() - t0
+    return {"fits_per_s": round(done / dt, 2), "fits": done, "cores": 1, "kind": "oracle"}
 
 
 def cpu_baseline(variants, seconds=12.0):

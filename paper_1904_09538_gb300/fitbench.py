@@ -12,31 +12,42 @@ import time
 import numpy as np
 
 
+LAUNCH = "p_launch * f_sync_kernel_launch + p_group * f_thread_groups"
+LIN = LAUNCH + " + p_add * f_op_float32_add + p_madd * f_op_float32_madd + p_gmem * f_mem_access_global_float32"
+_CG = "(p_gmem * f_mem_access_global_float32)"
+_CO = "(p_madd * f_op_float32_madd + p_lmem * f_mem_access_local_float32)"
+OVL = (LAUNCH + " + %s * (tanh(p_edge * (%s - %s)) + 1) / 2 + %s * (tanh(p_edge * (%s - %s)) + 1) / 2"
+       % (_CG, _CG, _CO, _CO, _CO, _CG))
+TRUTH = {"p_launch": 5e-6, "p_group": 2e-9, "p_add": 4e-12, "p_madd": 3e-12, "p_gmem": 6e-12, "p_lmem": 2e-12,
+         "p_edge": 3e4}
+
+
+def features(K, nfeat):
+    """Seeded feature matrices of K problems (launch = 1, work-groups in
+    [1e2, 1e4], other counts in [1e5, 1e7]) and their row counts."""
+    import pm_inputs
+    ls = pm_inputs.row_counts(K, 4242)
+    Xs = []
+    for k in range(K):
+        l = int(ls[k])
+        X = pm_inputs.integers((l, nfeat(k)), 9000 + k, 10 ** 5, 10 ** 7).astype(np.float64)
+        X[:, 0] = 1.0
+        X[:, 1] = pm_inputs.integers((l,), 9500 + k, 100, 10 ** 4)
+        Xs.append(X)
+    return Xs, ls
+
+
 def problem(K):
     """K seeded calibration problems: (models, feature matrices, outputs,
     start points = 1.2 x the parameters the outputs were made with)."""
     import pm_inputs
     from . import Model
-    from .suite import LAUNCH
-    lin = LAUNCH + " + p_add * f_op_float32_add + p_madd * f_op_float32_madd + p_gmem * f_mem_access_global_float32"
-    cg = "(p_gmem * f_mem_access_global_float32)"
-    co = "(p_madd * f_op_float32_madd + p_lmem * f_mem_access_local_float32)"
-    ovl = (LAUNCH + " + %s * (tanh(p_edge * (%s - %s)) + 1) / 2 + %s * (tanh(p_edge * (%s - %s)) + 1) / 2"
-           % (cg, cg, co, co, co, cg))
-    truth = {"p_launch": 5e-6, "p_group": 2e-9, "p_add": 4e-12, "p_madd": 3e-12, "p_gmem": 6e-12, "p_lmem": 2e-12,
-             "p_edge": 3e4}
-    ls = pm_inputs.row_counts(K, 4242)
-    models, Xs, ts, p0s = [], [], [], []
-    for k in range(K):
-        m = Model("f_wall_time", lin if k % 2 == 0 else ovl)
-        l = int(ls[k])
-        X = pm_inputs.integers((l, len(m.features)), 9000 + k, 10 ** 5, 10 ** 7).astype(np.float64)
-        X[:, 0] = 1.0
-        X[:, 1] = pm_inputs.integers((l,), 9500 + k, 100, 10 ** 4)
-        pt = np.array([truth[n] for n in m.params])
-        models.append(m)
-        Xs.append(X)
-        ts.append(m.predict(pt, X) * (1 + 1e-2 * pm_inputs.noise((l,), 9900 + k)))
+    models = [Model("f_wall_time", LIN if k % 2 == 0 else OVL) for k in range(K)]
+    Xs, ls = features(K, lambda k: len(models[k].features))
+    ts, p0s = [], []
+    for k, (m, X) in enumerate(zip(models, Xs)):
+        pt = np.array([TRUTH[n] for n in m.params])
+        ts.append(m.predict(pt, X) * (1 + 1e-2 * pm_inputs.noise((len(X),), 9900 + k)))
         p0s.append(pt * 1.2)
     return models, Xs, ts, p0s, ls
 
