@@ -24,7 +24,7 @@ import re
 import numpy as np
 
 from . import Model, FitPlan, kernel_buffers, run
-from .suite import generate
+from .suite import LAUNCH, generate
 
 GENERIC = "p_gen * f_mem_access_global_float32_lstrides:{0:1}_afr:1"
 OVERHEAD = ("p_launch * f_sync_kernel_launch + p_group * f_thread_groups + "
@@ -295,18 +295,19 @@ def diagnostics(trials=10, seed=1234, flush_l2=True):
         rows.append({"n": n, "a_s_per_load": per["mm_pf_a"], "b_s_per_load": per["mm_pf_b"],
                      "b_over_a": per["mm_pf_b"] / per["mm_pf_a"]})
     out["ab_ratio"] = {"rows": rows, "mean_b_over_a": float(np.mean([r["b_over_a"] for r in rows]))}
-    # -- madd-only calibration
-    # the madd kernels are sized to a similar total time, so a launch term
-    # would be collinear with the madd count: p_madd alone
-    m = Model("f_wall_time", "p_madd * f_op_float32_madd")
+    # -- madd-only calibration: launch, work-group and madd costs on the madd
+    # throughput kernels alone (their sizes vary total work and its split)
+    m = Model("f_wall_time", LAUNCH + " + p_madd * f_op_float32_madd")
     cal = generate(["flops_pattern", "dtype:0", "op:2"])
     X = np.stack([m.feature_values(k, **p) for k, p in cal])
     t = measure(cal, bufs, trials, flush_l2)
     p, rep = m.fit(X, t)
     sizes = [512, 1024, 1536, 2048, 3072, 4096]
     tm = measure([("mm_pf", {"n": n}) for n in sizes], bufs, trials, flush_l2)
-    share = [float(p[0] * m.feature_values("mm_pf", n=n)[0] / tt) for n, tt in zip(sizes, tm)]
-    out["madd_only"] = {"p_madd_s_per_subgroup_op": float(p[0]), "rate_flops": 64.0 / float(p[0]),
+    im = m.params.index("p_madd")
+    fm = m.features.index("f_op_float32_madd")
+    share = [float(p[im] * m.feature_values("mm_pf", n=n)[fm] / tt) for n, tt in zip(sizes, tm)]
+    out["madd_only"] = {"p_madd_s_per_subgroup_op": float(p[im]), "rate_flops": 64.0 / float(p[im]),
                         "fit": rep, "mm_pf_sizes": sizes, "mm_pf_madd_share": share}
     # -- overlap analysis, linear vs tanh-overlap on the same measurement sets
     res = {}

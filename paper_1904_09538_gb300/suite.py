@@ -44,20 +44,48 @@ class Generator:
         return out
 
 
+def _half_on_odd(x):
+    # 1 for even powers of two, 1/2 for odd ones: neighbouring variants then
+    # differ in total work as well as in its split into work-groups, so the
+    # per-operation and per-work-group costs are separately identifiable
+    return 2 if (x.bit_length() - 1) % 2 else 1
+
+
 def _fma_groups(p):
-    # constant total work per dtype: ~2^16 * 256 * RESIDENT operations for
-    # float32, 1/64 of that for float64 (GB300's FP64 rate is far lower)
+    # total work per dtype ~2^16 * 256 * RESIDENT operations for float32
+    # (halved on every other F), 1/64 of that for float64 (GB300's FP64 rate
+    # is far lower)
     F = p["F"]
     total = (1 << 16) * RESIDENT if p["dtype"] == 0 else (1 << 10) * RESIDENT
     p = dict(p)
-    p["G"] = max(SM_COUNT, total // F)
+    p["G"] = max(SM_COUNT, total // F // _half_on_odd(F))
     return p
 
 
 def _smem_groups(p):
     p = dict(p)
-    p["G"] = max(SM_COUNT, RESIDENT * (1 << 14) // p["R"])
+    p["G"] = max(SM_COUNT, RESIDENT * (1 << 14) // p["R"] // _half_on_odd(p["R"]))
     return p
+
+
+def _barrier_groups(p):
+    # B runs over even powers of two: alternate a full and a half wave of
+    # work-groups so the launch and per-work-group costs separate
+    p = dict(p)
+    e = p["B"].bit_length() - 1
+    p["G"] = RESIDENT // (1 + (e // 2) % 2)
+    return p
+
+
+def _overlap_size(p):
+    # alternate the global footprint with m so the global and local costs
+    # are not both fixed multiples of the launch
+    p = dict(p)
+    p["N"] = (1 << 26) // (1 + _OVERLAP_M.index(p["m"]) % 2)
+    return p
+
+
+_OVERLAP_M = [0, 1, 2, 4, 8, 12, 16, 24, 32]
 
 
 def _smem2d_groups(p):
@@ -87,9 +115,9 @@ GENERATORS = [
     Generator("fma", ["ops", "flops_pattern", "fp64", "suite"],
               {"dtype": [1], "op": [2], "F": POW(10, 16)}, _fma_groups),
     Generator("smem", ["lmem", "suite"], {"R": POW(8, 14), "sync": [0, 1]}, _smem_groups),
-    Generator("barrier", ["sync", "suite"], {"B": POW(4, 14, 2), "G": [RESIDENT]}),
+    Generator("barrier", ["sync", "suite"], {"B": POW(4, 14, 2)}, _barrier_groups),
     Generator("smem2d", ["lmem2d"], {"R": POW(8, 14), "T": [16, 18]}, _smem2d_groups),
-    Generator("overlap", ["overlap", "suite"], {"m": [0, 1, 2, 4, 8, 12, 16, 24, 32], "N": [1 << 26]}),
+    Generator("overlap", ["overlap", "suite"], {"m": _OVERLAP_M}, _overlap_size),
     Generator("empty", ["launch", "suite"], {"G": POW(6, 18)}),
     Generator("mm_pf", ["matmul_sq", "modeled"], {"n": [256, 384, 512, 640, 768, 896]}),
     Generator("mm_nopf", ["matmul_sq", "modeled"], {"n": [256, 384, 512, 640, 768, 896]}),
@@ -182,14 +210,17 @@ def family_model(key):
     if key.startswith("stream"):
         return LAUNCH + " + p_gmem * f_mem_access_global"
     if key.startswith("fma"):
+        # the mul / madd loops end in a reduction of a fixed number of adds
+        # per work-group: that cost is part of p_group, not a separate term
         dt = "float32" if "_f32_" in key else "float64"
         op = key.rsplit("_", 1)[1]
-        extra = "" if op == "add" else " + p_%s * f_op_%s_%s" % (op, dt, op)
-        return LAUNCH + " + p_add * f_op_%s_add" % dt + extra
+        return LAUNCH + " + p_%s * f_op_%s_%s" % (op, dt, op)
     if key == "smem_sync0":
         return LAUNCH + " + p_lmem * f_mem_access_local_float32"
     if key == "smem_sync1":
-        return LAUNCH + " + p_lmem * f_mem_access_local_float32 + p_bar * f_sync_barrier_local * f_thread_groups"
+        # one barrier per fixed number of local accesses: the barrier cost is
+        # folded into p_lmem (the barrier kernel calibrates p_bar on its own)
+        return LAUNCH + " + p_lmem * f_mem_access_local_float32"
     if key == "barrier":
         return LAUNCH + " + p_bar * f_sync_barrier_local * f_thread_groups"
     if key == "overlap":
