@@ -196,6 +196,8 @@ def run_ours(args):
 
     last_times = {}
 
+    fitted = {}
+
     def fit_and_predict(times):
         # calibrate every family model on its fitting rows in one batched launch
         tfit = np.array([times[i] for f in fam_names for i in fit_rows[f]])
@@ -204,6 +206,7 @@ def run_ours(args):
         o, errs = 0, []
         for f, npar in zip(fam_names, plan.nparams):
             pf = pvec[o:o + npar]
+            fitted[f] = dict(zip(models[f].params, (float(x) for x in pf)))
             o += npar
             if held[f]:
                 Xh = np.stack([rows[i] for i in held[f]])
@@ -290,6 +293,8 @@ def run_ours(args):
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,
     }
+    line["calibrated"] = calibrated_rates(fitted, torch.cuda.get_device_properties(dev).multi_processor_count,
+                                          clk.get("sm_mhz"))
     if world > 1:
         line["ranks"] = rank_reports
     if args.dump and rank == 0:
@@ -308,6 +313,43 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def calibrated_rates(fitted, sm_count, sm_mhz):
+    """The suite families' fitted per-unit costs as rates (the conversions of
+    the paper's Table mm_param_vals), against the peaks they estimate.
+    A sub-group op is 32 lanes (a madd is 2 flops), a sub-group local access
+    moves 32 x 4 bytes, a stream access one 16-byte vector per work-item.
+    FP32 peak = SMs x 128 lanes x 2 x clock; shared memory = SMs x 128 B x
+    clock, at the sampled median SM clock (2070 MHz if none was sampled)."""
+    clk = (sm_mhz or 2070.0) * 1e6
+    fp32_peak, smem_peak = sm_count * 128 * 2 * clk, sm_count * 128 * clk
+
+    def rate(fam, par, units):
+        v = fitted.get(fam, {}).get(par)
+        return units / v if v and v > 0 else None
+
+    out = {"sm_mhz": round(clk / 1e6, 1), "fp32_peak_tflops": round(fp32_peak / 1e12, 2),
+           "smem_peak_tbs": round(smem_peak / 1e12, 2)}
+    for key, fam, par, units in (("f32_madd_tflops", "fma_f32_madd", "p_madd", 64),
+                                 ("f32_mul_tflops", "fma_f32_mul", "p_mul", 32),
+                                 ("f32_add_tflops", "fma_f32_add", "p_add", 32),
+                                 ("f64_madd_tflops", "fma_f64_madd", "p_madd", 64),
+                                 ("lmem_tbs", "smem_sync0", "p_lmem", 128),
+                                 ("lmem_sync_tbs", "smem_sync1", "p_lmem", 128),
+                                 ("gmem_f32_s1_gbs", "stream_f32_s1", "p_gmem", 16),
+                                 ("gmem_f64_s1_gbs", "stream_f64_s1", "p_gmem", 16)):
+        r = rate(fam, par, units)
+        out[key] = round(r / (1e9 if key.endswith("gbs") else 1e12), 3) if r else None
+    if out["f32_madd_tflops"]:
+        out["f32_madd_frac"] = round(out["f32_madd_tflops"] * 1e12 / fp32_peak, 4)
+    if out["lmem_tbs"]:
+        out["lmem_frac"] = round(out["lmem_tbs"] * 1e12 / smem_peak, 4)
+    emp, bar = fitted.get("empty", {}), fitted.get("barrier", {})
+    out["launch_us"] = round(emp["p_launch"] * 1e6, 3) if "p_launch" in emp else None
+    out["group_ns"] = round(emp["p_group"] * 1e9, 4) if "p_group" in emp else None
+    out["barrier_ns_per_group"] = round(bar["p_bar"] * 1e9, 4) if "p_bar" in bar else None
+    return out
 
 
 def source_sha(f="pm_suite.cu", kernel="k_stream"):

@@ -1,0 +1,105 @@
+"""Host-side logic of bench.py and the suite's fit designs (no GPU)."""
+import importlib.util
+import os
+import sys
+
+import numpy as np
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bench():
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    mod = importlib.util.module_from_spec(spec)
+    argv = sys.argv
+    sys.argv = ["bench.py"]
+    try:
+        spec.loader.exec_module(mod)
+    finally:
+        sys.argv = argv
+    return mod
+
+
+def test_calibrated_rates_units(bench):
+    # per-unit costs made from known rates come back as those rates
+    fitted = {"fma_f32_madd": {"p_madd": 64 / 72e12}, "fma_f32_add": {"p_add": 32 / 40e12},
+              "fma_f64_madd": {"p_madd": 64 / 1.2e12}, "smem_sync0": {"p_lmem": 128 / 30e12},
+              "stream_f64_s1": {"p_gmem": 16 / 7000e9}, "empty": {"p_launch": 2e-6, "p_group": 1e-9},
+              "barrier": {"p_bar": 5e-9}}
+    r = bench.calibrated_rates(fitted, 152, 2070.0)
+    assert r["fp32_peak_tflops"] == pytest.approx(152 * 256 * 2.07e9 / 1e12, rel=1e-3)
+    assert r["smem_peak_tbs"] == pytest.approx(152 * 128 * 2.07e9 / 1e12, rel=1e-3)
+    assert r["f32_madd_tflops"] == pytest.approx(72.0)
+    assert r["f32_add_tflops"] == pytest.approx(40.0)
+    assert r["f64_madd_tflops"] == pytest.approx(1.2)
+    assert r["lmem_tbs"] == pytest.approx(30.0)
+    assert r["gmem_f64_s1_gbs"] == pytest.approx(7000.0)
+    assert r["f32_madd_frac"] == pytest.approx(72.0 / r["fp32_peak_tflops"], rel=1e-3)
+    assert r["launch_us"] == pytest.approx(2.0) and r["group_ns"] == pytest.approx(1.0)
+    assert r["barrier_ns_per_group"] == pytest.approx(5.0)
+    # missing families and non-positive costs give null, not a division error
+    assert r["f32_mul_tflops"] is None and r["gmem_f32_s1_gbs"] is None
+    assert bench.calibrated_rates({"fma_f32_madd": {"p_madd": -1.0}}, 152, None)["f32_madd_tflops"] is None
+
+
+def test_clock_sampler_parses_reasons(bench):
+    class _Proc:
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    cs = bench.ClockSampler(0)
+    cs.proc = _Proc()
+    cs.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "0, 1980, 2070, 1390.0, 0x4, Not Active, Not Active, Not Active, Active",
+                "0, 2010, 2070, 1200.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+                "garbage line"]
+    out = bench.ClockSampler.stop(cs)
+    assert out["sm_mhz"] == 2010 and out["sm_max_mhz"] == 2070 and out["samples"] == 3
+    assert out["reasons"] == ["sw_power_cap"]
+
+
+def test_kernel_instance_names(bench):
+    assert bench.kernel_instance("stream", dict(dtype=1, vec=1, L=4, shape=0)) == "k_stream<double2,4,0>"
+    assert bench.kernel_instance("stream", dict(dtype=0, vec=0, L=2, shape=1)) == "k_stream<float,2,1>"
+    assert bench.kernel_instance("fma", dict(dtype=1, op=2)) == "k_fma<double,2>"
+    assert bench.kernel_instance("smem", dict(sync=1)) == "k_smem<1>"
+    assert bench.kernel_instance("barrier", dict(B=4)) == "k_barrier"
+
+
+def test_source_sha_tracks_one_definition(bench):
+    a = bench.source_sha("pm_suite.cu", "k_stream")
+    assert a is not None and len(a) == 16 and a == bench.source_sha("pm_suite.cu", "k_stream")
+    assert a != bench.source_sha("pm_suite.cu", "k_fma")
+    assert bench.source_sha("pm_suite.cu", "k_no_such_kernel") is None
+
+
+def test_workload_config_counts_bytes(bench):
+    from paper_1904_09538_gb300 import suite as S
+    variants = S.generate(["suite"])
+    cfg = bench.workload_config(variants, 3)
+    assert cfg["variants"] == len(variants) == 230
+    assert cfg["bytes_per_step"] == 3 * sum(S.algorithmic_bytes(k, p) for k, p in variants)
+    assert cfg["families"] == 22 and cfg["bytes_per_step"] > 100 * 129e6   # far above L2
+
+
+def test_every_suite_family_design_is_full_rank():
+    # each family model is identifiable from its fitting rows (every third
+    # variant is held out): no feature column is a combination of the others
+    import paper_1904_09538_gb300 as pm
+    from paper_1904_09538_gb300 import suite as S
+    variants = S.generate(["suite"])
+    fams = {}
+    for idx, (k, p) in enumerate(variants):
+        fams.setdefault(S.family_key(k, p), []).append(idx)
+    for f, idxs in fams.items():
+        m = pm.Model("f_wall_time", S.family_model(f))
+        fit = [i for j, i in enumerate(idxs) if j % 3 != 2]
+        X = np.stack([m.feature_values(variants[i][0], **variants[i][1]) for i in fit])
+        Xs = X / np.abs(X).max(axis=0)
+        assert np.linalg.matrix_rank(Xs) == X.shape[1], f
+        assert np.linalg.cond(Xs) < 1e3, f
