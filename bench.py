@@ -514,45 +514,56 @@ def oracle_fit_rate(seconds=5.0):
     return {"fits_per_s": round(done / dt, 2), "fits": done, "cores": 1, "kind": "oracle"}
 
 
-def cpu_baseline(variants, seconds=12.0):
+_CPU_INPUTS = {}
+
+
+def cpu_baseline(variants, seconds=12.0, scale=16):
     """The oracle's plain CPU reference kernels on a bounded sample of the
-    same suite: every memory-moving variant scaled down by a common factor
-    until the pass costs about `seconds` of one host core."""
+    same suite: every stream variant at N/`scale` (arrays still larger than a
+    host's last-level cache at the larger N), every arithmetic variant at
+    1/(64 `scale`) of its work-items, each oracle call repeated until the pass
+    costs about `seconds` of one host core.  Inputs are made once per array
+    and kept across calls; only the oracle calls are timed."""
     import numpy as np
     import pm_inputs
     from oracle import refs
-    from paper_1904_09538_gb300 import suite as S
 
-    # time only the oracle calls
-    def timed(scale):
+    def inp(n, seed, dt):
+        key = (n, seed, np.dtype(dt).str)
+        if key not in _CPU_INPUTS:
+            _CPU_INPUTS[key] = pm_inputs.uniform((n,), seed, dtype=dt)
+        return _CPU_INPUTS[key]
+
+    def one_pass(reps):
         total_b, total_t = 0, 0.0
         for k, p in variants:
+            dt = np.float32 if p.get("dtype", 0) == 0 else np.float64
             if k == "stream":
                 N = max(256, p["N"] // scale)
-                dt = np.float32 if p.get("dtype", 0) == 0 else np.float64
-                xs = [pm_inputs.uniform((N,), 5 + a, dtype=dt) for a in range(p.get("L", 1))]
+                xs = [inp(N, 5 + a, dt) for a in range(p.get("L", 1))]
                 t1 = time.perf_counter()
-                refs.stream(xs)
+                for _ in range(reps):
+                    refs.stream(xs)
                 total_t += time.perf_counter() - t1
-                total_b += (p.get("L", 1) + 1) * N * np.dtype(dt).itemsize
+                total_b += reps * (p.get("L", 1) + 1) * N * np.dtype(dt).itemsize
             elif k == "fma":
                 T = max(256, p["G"] * 256 // (scale * 64))
-                dt = np.float32 if p.get("dtype", 0) == 0 else np.float64
-                u = pm_inputs.uniform((T,), 9, dtype=dt)
+                u = inp(T, 9, dt)
                 t1 = time.perf_counter()
-                refs.fma(u, p["op"], p["F"])
+                for _ in range(reps):
+                    refs.fma(u, p["op"], p["F"])
                 total_t += time.perf_counter() - t1
-                total_b += 2 * T * np.dtype(dt).itemsize
+                total_b += reps * 2 * T * np.dtype(dt).itemsize
         return total_b, total_t
 
-    scale = 4096
-    b, t = timed(scale)
-    if t > 0:
-        scale = max(1, int(scale * t / seconds))
-        b, t = timed(scale)
+    b, t = one_pass(1)
+    reps = max(1, math.ceil(seconds / t)) if t > 0 else 1
+    if reps > 1:
+        b, t = one_pass(reps)
     return {"value": round(b / t / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
-            "sample": "every stream variant at N/%d and every arithmetic variant at 1/%d of its work-items "
-                      "(oracle C reference, one host core, %.1f s)" % (scale, scale * 64, t)}
+            "sample": "every stream variant at N/%d and every arithmetic variant at 1/%d of its work-items, "
+                      "each oracle call %d times (oracle C reference, one host core, %.1f s)"
+                      % (scale, scale * 64, reps, t)}
 
 
 # ---------------------------------------------------------------- reference arm
