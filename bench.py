@@ -196,7 +196,7 @@ def run_ours(args):
 
     last_times = {}
 
-    fitted = {}
+    fitted, fam_errs = {}, {}
 
     def fit_and_predict(times):
         # calibrate every family model on its fitting rows in one batched launch
@@ -204,6 +204,7 @@ def run_ours(args):
         pvec, reps = plan.run(Xfit, tfit)
         # predict the held-out rows
         o, errs = 0, []
+        fam_errs.clear()
         for f, npar in zip(fam_names, plan.nparams):
             pf = pvec[o:o + npar]
             fitted[f] = dict(zip(models[f].params, (float(x) for x in pf)))
@@ -212,7 +213,9 @@ def run_ours(args):
                 Xh = np.stack([rows[i] for i in held[f]])
                 pred = models[f].predict(pf, Xh)
                 meas = np.array([times[i] for i in held[f]])
-                errs.extend(list(np.abs(pred - meas) / meas))
+                e = list(np.abs(pred - meas) / meas)
+                errs.extend(e)
+                fam_errs[f] = e
         return errs, reps
 
     def one_step(record):
@@ -288,7 +291,8 @@ def run_ours(args):
         "roofline": roofline,
         "best_stream_kernel": {"kernel": best_stream[1], "GB/s": round(best_stream[0], 1),
                                "frac": round(best_stream[0] / peaks["hbm_gbs"], 4)},
-        "heldout_pred_rel_err": {"geomean": geo, "max": max(all_errs) if all_errs else None, "n": len(all_errs)},
+        "heldout_pred_rel_err": {"geomean": geo, "max": max(all_errs) if all_errs else None, "n": len(all_errs),
+                                 "max_by_family_last_step": {f: round(max(e), 4) for f, e in sorted(fam_errs.items())}},
         "fit_status_counts": {str(s): fit_status.count(s) for s in sorted(set(fit_status))},
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,

@@ -73,7 +73,9 @@ typedef struct {
  * 2 = persistent (one CTA per SM walking the tiles, 4-stage ring, two TMEM
  * accumulators so one tile's epilogue overlaps the next tile's main loop);
  * the counts describe the decomposition into 128 x 256 tiles and do not
- * depend on pipe); the TMA-staged
+ * depend on pipe) and its 256 x 256-tile form "mm_tc256" (parameter n, a
+ * multiple of 256: 256-thread work-groups, two 128-row accumulators in 512
+ * TMEM columns sharing each Bt box, 3-stage ring, one CTA per SM); the TMA-staged
  * stencil tile family "fd_block" (parameters n, BX, BY, c0, c1, V = 4 or 8
  * outputs per work-item; input u of (n + 2) rows with row pitch n + 4).
  * Returns PM_EUNKNOWN_KERNEL for other names. */

@@ -1092,6 +1092,51 @@ static int setup_tc(ctx *c) {
     return 0;
 }
 
+/* 256 x 256 tile variant: a 256-work-item group per tile; work-item 0
+ * copies a 256x64 box of A and a 256x64 box of Bt per 64-wide k tile,
+ * work-item 32 issues eight 128x256x16 multiply-adds per k tile (two row
+ * halves sharing the Bt box), work-item t stores row t of the tile (64
+ * 16-byte vectors); three barriers. */
+static long long ix_tcw_a(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)l; long long n = c->P[0]; return n * (256 * G1 + lv[1]) + 64 * lv[0] + lv[2];
+}
+static long long ix_tcw_c(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long n = c->P[0]; return (n / 4) * (256 * G1 + L0_) + 64 * G0 + 8 * lv[0] + lv[1];
+}
+static void walk_tcw(ctx *c) {
+    long long n = c->P[0], lv[3];
+    BAR(c);
+    if (c->l[0] == 0)
+        for (lv[0] = 0; lv[0] < n / 64; lv[0]++) {
+            for (lv[1] = 0; lv[1] < 256; lv[1]++)
+                for (lv[2] = 0; lv[2] < 64; lv[2]++) X(c, 0, lv);
+            for (lv[1] = 0; lv[1] < 256; lv[1]++)
+                for (lv[2] = 0; lv[2] < 64; lv[2]++) X(c, 1, lv);
+        }
+    if (c->l[0] == 32)
+        for (lv[0] = 0; lv[0] < n / 64; lv[0]++)
+            for (lv[1] = 0; lv[1] < 8; lv[1]++) X(c, 2, lv);
+    for (lv[0] = 0; lv[0] < 8; lv[0]++)
+        for (lv[1] = 0; lv[1] < 8; lv[1]++) X(c, 3, lv);
+    BAR(c);
+    BAR(c);
+}
+static int setup_tcw(ctx *c) {
+    long long n = c->P[0];
+    if (n < 256 || n % 256) return -1;
+    c->grid[0] = n / 256; c->grid[1] = n / 256; c->grid[2] = 1;
+    c->wg[0] = 256; c->wg[1] = 1; c->wg[2] = 1;
+    int s0 = add_stmt(c, 3, DT_BF16, 0, 0, 0);
+    stmt_site(c, s0, add_site(c, "tc-a", MEM_GLOBAL, DIR_LOAD, "bfloat16", 2, ix_tcw_a));
+    int s1 = add_stmt(c, 3, DT_BF16, 0, 0, 0);
+    stmt_site(c, s1, add_site(c, "tc-b", MEM_GLOBAL, DIR_LOAD, "bfloat16", 2, ix_tc_b));
+    add_stmt(c, 2, DT_BF16, 0, 0, 128 * 256 * 16);
+    int s3 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+    stmt_site(c, s3, add_site(c, "tc-c", MEM_GLOBAL, DIR_STORE, "float32x4", 16, ix_tcw_c));
+    c->walk = walk_tcw;
+    return 0;
+}
+
 /* FP64 reference of C = A Bt^T over bf16 inputs (uint16 bit patterns) */
 static double bf16_value(unsigned short h) {
     union { unsigned int u; float f; } v;
@@ -1244,6 +1289,7 @@ static const struct { const char *name; int fam, v; } KTAB[] = {
     {"mm_tc", 10, 0},
     {"fd_block", 11, 0},
     {"smem2d", 12, 0},
+    {"mm_tc256", 10, 1},
 };
 
 static int counts_impl(const char *kernel, const char *remove, const long long *P, int nP, orec *out, int cap,
@@ -1276,7 +1322,7 @@ static int counts_impl(const char *kernel, const char *remove, const long long *
     case 7: rc = setup_dg(c, v); break;
     case 8: rc = setup_fd(c, v); break;
     case 9: rc = setup_simt(c); break;
-    case 10: rc = setup_tc(c); break;
+    case 10: rc = v ? setup_tcw(c) : setup_tc(c); break;
     case 11: rc = setup_fdb(c); break;
     case 12: rc = setup_smem2d(c); break;
     }

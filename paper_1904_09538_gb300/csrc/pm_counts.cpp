@@ -596,14 +596,15 @@ pm_status counts_simt(const KP &kp, std::vector<pm_feature> &v) {
 }
 
 // ---------------------------------------------------------------- tensor-core matmul
-// 128-thread work-group per 128 x 256 tile of C; per 64-wide k tile the
-// elected thread 0 copies a 128x64 box of A and a 256x64 box of Bt (counted
-// element by element, uniform, hence per sub-group) and thread 32 issues four
-// 128x256x16 multiply-add instructions; every work-item stores 64 16-byte
-// vectors of its C row; three barriers.
+// R-thread work-group per R x 256 tile of C (R = 128 for mm_tc, 256 for
+// mm_tc256); per 64-wide k tile the elected thread 0 copies an Rx64 box of A
+// and a 256x64 box of Bt (counted element by element, uniform, hence per
+// sub-group) and thread 32 issues R/32 128x256x16 multiply-add instructions
+// (R/128 row halves x 4 k slices); every work-item stores 64 16-byte vectors
+// of its C row; three barriers.
 pm_status counts_tc(const KP &kp, std::vector<pm_feature> &v) {
-    i64 n = kp.i(0);
-    u64 G = (u64)((n / 256) * (n / 128)), KT = (u64)(n / 64);
+    i64 n = kp.i(0), R = kp.def->variant ? 256 : 128;
+    u64 G = (u64)((n / 256) * (n / R)), KT = (u64)(n / 64);
     u64 nn = (u64)(n * n);
     Out o(v);
     auto site = [&](const char *tag, int dir, const char *dt, int ds, int nl, i64 l0, i64 g0, i64 g1, i64 loop, u64 wi,
@@ -614,10 +615,10 @@ pm_status counts_tc(const KP &kp, std::vector<pm_feature> &v) {
         x.wi = wi; x.sg = sg; x.foot = foot;
         o.site(x);
     };
-    const u64 ma = G * KT * 128 * 64, mb = G * KT * 256 * 64, mm = G * KT * 4;
-    site("tc-a", LD, "bfloat16", 2, 1, 0, 0, 128 * n, 1, ma, ma, nn);
+    const u64 ma = G * KT * (u64)R * 64, mb = G * KT * 256 * 64, mm = G * KT * (u64)(R / 32);
+    site("tc-a", LD, "bfloat16", 2, 1, 0, 0, R * n, 1, ma, ma, nn);
     site("tc-b", LD, "bfloat16", 2, 1, 0, 256 * n, 0, 1, mb, mb, nn);
-    site("tc-c", ST, "float32x4", 16, 1, n / 4, 64, 32 * n, 1, G * 128 * 64, G * 4 * 64, nn / 4);
+    site("tc-c", ST, "float32x4", 16, 1, n / 4, 64, R * n / 4, 1, G * (u64)R * 64, G * (u64)(R / 32) * 64, nn / 4);
     pm_feature f = op_rec("bfloat16", "madd", mm * 128 * 256 * 16, mm * 128 * 256 * 16);
     v.push_back(f);
     for (auto &x : o.sites) v.push_back(x);
@@ -688,7 +689,7 @@ pm_status validate(const KP &kp) {
     }
     case FAM_FMA:
         if (kp.i(0) < 0 || kp.i(0) > 1) return fail(PM_EINVAL, "%s: dtype must be 0 or 1", nm);
-        if (kp.i(1) < 0 || kp.i(1) > 2) return fail(PM_EINVAL, "%s: op must be 0 (add), 1 (mul), 2 (madd)", nm);
+        if (kp.def->variant == 0 && (kp.i(1) < 0 || kp.i(1) > 2)) return fail(PM_EINVAL, "%s: op must be 0 (add), 1 (mul), 2 (madd)", nm);
         if (kp.i(2) < 32 || kp.i(2) % 32 || kp.i(2) > (1LL << 30))
             return fail(PM_EINVAL, "%s: F must be a positive multiple of 32", nm);
         if (kp.i(3) < 1 || kp.i(3) > (1LL << 23)) return fail(PM_EINVAL, "%s: G must be 1..2^23", nm);
@@ -747,7 +748,7 @@ pm_status validate(const KP &kp) {
     case FAM_TC:
         if (kp.i(0) < 256 || kp.i(0) % 256 || kp.i(0) > 32768)
             return fail(PM_EINVAL, "%s: n must be a multiple of 256 in [256, 32768]", nm);
-        if (kp.i(1) < 0 || kp.i(1) > 2)
+        if (kp.def->variant == 0 && (kp.i(1) < 0 || kp.i(1) > 2))
             return fail(PM_EINVAL, "%s: pipe must be 0 (4 stages, 1 CTA/SM), 1 (2 stages, 2 CTAs/SM) or 2 (persistent)",
                         nm);
         return PM_OK;

@@ -375,6 +375,140 @@ __global__ void __launch_bounds__(192, 1) k_mm_tc_persist(const __grid_constant_
     }
 }
 
+// ---------------------------------------------------------------- 256 x 256 tiles
+// One CTA of 256 threads per 256 x 256 tile of C (one CTA per SM): per
+// 64-wide k tile one 256x64 box of A and one 256x64 box of Bt (64 KB per
+// stage, 3 stages) and eight MMAs -- the two 128-row halves of the A box
+// against the same Bt box, four k slices each -- into two accumulators of
+// 256 TMEM columns.  Per flop this moves two thirds of the operand bytes of
+// the 128 x 256 tile.  Epilogue: warps w and w + 4 drain TMEM lanes
+// 32 (w mod 4) ... of accumulator 0 and 1, i.e. work-item t stores row t.
+constexpr int WM = 256, W_STAGES = 3, GROUP_W = 8;
+constexpr int WA_BYTES = WM * TK * 2, W_STAGE_BYTES = WA_BYTES + B_BYTES;
+struct __align__(8) TcWide {
+    uint64_t full[W_STAGES], empty[W_STAGES], accum;
+    uint32_t tmem_base;
+    int issued;
+};
+constexpr size_t kWideSmem = (size_t)W_STAGES * W_STAGE_BYTES + sizeof(TcWide) + 2048;
+static_assert(kWideSmem <= 227 * 1024, "wide tile ring exceeds shared memory");
+static_assert(2 * kWideSmem > 228 * 1024, "one wide CTA per SM: the 512 TMEM columns are not shared");
+
+__global__ void __launch_bounds__(256, 1) k_mm_tc_w(const __grid_constant__ CUtensorMap tmA,
+                                                    const __grid_constant__ CUtensorMap tmB, float *__restrict__ C,
+                                                    int M, int N, int K) {
+    extern __shared__ __align__(1024) unsigned char smem_raw[];
+    unsigned char *base = (unsigned char *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+    TcWide *S = (TcWide *)(base + W_STAGES * W_STAGE_BYTES);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    // CTA -> tile: groups of GROUP_W tile rows, column-major inside a group
+    const int ntm = M / WM, ntn = N / TN, per_group = GROUP_W * ntn;
+    const int t = blockIdx.x, grp = t / per_group, first = grp * GROUP_W;
+    const int gsz = min(ntm - first, GROUP_W), r = t - grp * per_group;
+    const int m0 = (first + r % gsz) * WM, n0 = (r / gsz) * TN;
+    const int KT = K / TK;
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < W_STAGES; s++) {
+            mbar_init(&S->full[s], 1);
+            mbar_init(&S->empty[s], 1);
+        }
+        mbar_init(&S->accum, 1);
+        S->issued = 0;
+        mbar_init_fence();
+    }
+    if (warp == 2) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&S->tmem_base)),
+                     "r"(2 * TMEM_COLS)
+                     : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+        tc_fence_before();
+    }
+    __syncthreads();
+    tc_fence_after();
+    const uint32_t tmem = S->tmem_base;
+
+    if (warp == 0) {
+        if (lane == 0) {
+            for (int kt = 0; kt < KT; kt++) {
+                const int s = kt % W_STAGES, r = kt / W_STAGES;
+                if (r > 0 && !mbar_wait(&S->empty[s], (uint32_t)((r - 1) & 1))) break;
+                unsigned char *st = base + s * W_STAGE_BYTES;
+                mbar_expect_tx(&S->full[s], W_STAGE_BYTES);
+                tma_load_2d(st, &tmA, &S->full[s], kt * TK, m0);
+                tma_load_2d(st + WA_BYTES, &tmB, &S->full[s], kt * TK, n0);
+                S->issued = kt + 1;
+            }
+        }
+        __syncwarp();
+    } else if (warp == 1) {
+        if (lane == 0) {
+            for (int kt = 0; kt < KT; kt++) {
+                const int s = kt % W_STAGES, r = kt / W_STAGES;
+                if (!mbar_wait(&S->full[s], (uint32_t)(r & 1))) break;
+                tc_fence_after();
+                unsigned char *st = base + s * W_STAGE_BYTES;
+                // rows 128..255 of the A box start 128 rows x 128 bytes in
+                const uint64_t a0 = smem_desc(st), a1 = smem_desc(st + WA_BYTES / 2), bd = smem_desc(st + WA_BYTES);
+#pragma unroll
+                for (int kk = 0; kk < TK / 16; kk++) {
+                    const uint32_t acc = (kt > 0 || kk > 0) ? 1u : 0u;
+                    mma_bf16(tmem, a0 + 2 * kk, bd + 2 * kk, acc);
+                    mma_bf16(tmem + (uint32_t)TMEM_COLS, a1 + 2 * kk, bd + 2 * kk, acc);
+                }
+                mma_commit(&S->empty[s]);
+            }
+            mma_commit(&S->accum);
+        }
+        __syncwarp();
+    }
+
+    const bool ok = mbar_wait(&S->accum, 0);
+    __syncwarp();
+    tc_fence_after();
+    if (ok) {
+        const int h = warp >> 2, q = warp & 3;
+        float *crow = C + (size_t)(m0 + h * 128 + q * 32 + lane) * N + n0;
+#pragma unroll 1
+        for (int c = 0; c < TN / 32; c++) {
+            uint32_t v[32];
+            const uint32_t taddr = tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)(h * TMEM_COLS + c * 32);
+            asm volatile(
+                "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, "
+                "%14, %15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+                : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+                  "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
+                  "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]),
+                  "=r"(v[23]), "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]),
+                  "=r"(v[30]), "=r"(v[31])
+                : "r"(taddr));
+            asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+            float4 *dst = reinterpret_cast<float4 *>(crow + c * 32);
+#pragma unroll
+            for (int k = 0; k < 8; k++)
+                dst[k] = make_float4(__uint_as_float(v[4 * k]), __uint_as_float(v[4 * k + 1]),
+                                     __uint_as_float(v[4 * k + 2]), __uint_as_float(v[4 * k + 3]));
+        }
+    }
+    tc_fence_before();
+    __syncthreads();
+    if (threadIdx.x == 0 && (!ok || *(volatile int *)&g_tc_timeout)) {
+        // drain: every stage's last issued copy must land before the shared memory goes away
+        const int issued = S->issued;
+        for (int s = 0; s < W_STAGES && s < issued; s++) {
+            const int last = s + ((issued - 1 - s) / W_STAGES) * W_STAGES;
+            for (long long i = 0; i < WAIT_LIMIT; i++)
+                if (mbar_try(&S->full[s], (uint32_t)((last / W_STAGES) & 1))) break;
+        }
+    }
+    __syncthreads();
+    if (warp == 2) {
+        tc_fence_after();
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * TMEM_COLS)
+                     : "memory");
+    }
+}
+
 }  // namespace
 
 static PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
@@ -427,6 +561,15 @@ pm_status launch_tc(const KP &kp, void *const *b, void *stream) {
         if ((uintptr_t)b[a] % 16) return fail(PM_EINVAL, "mm_tc: buffer %d must be 16-byte aligned", a);
     pm_status s;
     CUtensorMap ta, tb;
+    if (kp.def->variant == 1) {
+        if ((s = tensor_map_2d(&ta, 1, b[0], n, n, (uint64_t)n * 2, TK, WM, 1))) return s;
+        if ((s = tensor_map_2d(&tb, 1, b[1], n, n, (uint64_t)n * 2, TK, TN, 1))) return s;
+        PM_CUDA_TRY(cudaFuncSetAttribute(k_mm_tc_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kWideSmem));
+        launch_k(k_mm_tc_w, (unsigned)((n / TN) * (n / WM)), 256, kWideSmem, (cudaStream_t)stream, ta, tb,
+                 (float *)b[2], n, n, n);
+        PM_CUDA_TRY(cudaGetLastError());
+        return PM_OK;
+    }
     if ((s = tensor_map_2d(&ta, 1, b[0], n, n, (uint64_t)n * 2, TK, TM, 1))) return s;
     if ((s = tensor_map_2d(&tb, 1, b[1], n, n, (uint64_t)n * 2, TK, TN, 1))) return s;
     if (pipe == 0) return launch_tc_t<4, 1>(ta, tb, (float *)b[2], n, (cudaStream_t)stream);

@@ -69,11 +69,13 @@ def _smem_groups(p):
 
 
 def _barrier_groups(p):
-    # B runs over even powers of two: alternate a full and a half wave of
-    # work-groups so the launch and per-work-group costs separate
+    # B runs over even powers of two: alternate one and two full waves of
+    # work-groups so the launch and per-work-group costs separate (a partial
+    # wave would change the per-barrier cost: fewer resident groups hide
+    # less of each barrier's latency)
     p = dict(p)
     e = p["B"].bit_length() - 1
-    p["G"] = RESIDENT // (1 + (e // 2) % 2)
+    p["G"] = RESIDENT * (1 + (e // 2) % 2)
     return p
 
 

@@ -180,6 +180,11 @@ def test_mm_tc(n):
     compare("mm_tc", n=n)
 
 
+@pytest.mark.parametrize("n", [256, 512, 768])
+def test_mm_tc256(n):
+    compare("mm_tc256", n=n)
+
+
 @pytest.mark.parametrize("V", [4, 8])
 @pytest.mark.parametrize("n,BX,BY", [(64, 32, 4), (128, 64, 8), (128, 128, 16), (256, 128, 32), (96, 32, 32)])
 def test_fd_block(n, BX, BY, V):
