@@ -122,13 +122,15 @@ def studies():
 
 
 def sweep_studies():
-    """The cross-variant sweep: 8 modeled variants (prefetching fp32 matmul,
-    BF16 tensor-core matmul, DG noPF / uPF / dmPF / dmPF-T with 16x16
-    work-groups, stencil 16x16 tile and direct) at ~30 sizes each.  Every
-    third size is held out; each variant's model is calibrated on the
-    microbenchmarks (plus its computation's twins) and the variant's own other
-    sizes -- the paper's "few extra on-line calibration runs" -- and predicts
-    the held-out sizes."""
+    """The cross-variant sweep: 9 modeled variants (prefetching fp32 matmul,
+    BF16 tensor-core matmul with 128 x 256 and 256 x 256 tiles, DG noPF /
+    uPF / dmPF / dmPF-T with 16x16 work-groups, stencil 16x16 tile and
+    direct) at ~30 sizes each.  Every third size is held out; each variant's
+    model is calibrated on the microbenchmarks (plus its computation's twins)
+    and the variant's own other sizes -- the paper's "few extra on-line
+    calibration runs" -- and predicts the held-out sizes.  A tenth study
+    calibrates one model on both tensor-core tiles and ranks them at the
+    held-out sizes."""
     base = {s["name"]: s for s in studies()}
     # the A and B tile loads both scale as n^3 at a fixed tile shape, so one
     # bf16 load feature carries them
@@ -137,8 +139,9 @@ def sweep_studies():
                         onchip="p_tc * f_op_bfloat16_madd")
     nels = sorted({int(round(2 ** (14 + 4 * i / 7.0) / 32)) * 32 for i in range(8)})
     dg_sizes = [dict(Np=Np, Nel=Nel, L0=16, L1=16) for Np in (20, 35, 56, 84) for Nel in nels]
+    tc_sizes = [{"n": n} for n in range(1024, 8192 + 1, 256)]
     plan = [("mm_pf", "matmul", None, [{"n": n} for n in range(512, 4096 + 1, 128)]),
-            ("mm_tc", None, tc_expr, [{"n": n} for n in range(1024, 8192 + 1, 256)])]
+            ("mm_tc", None, tc_expr, tc_sizes), ("mm_tc256", None, tc_expr, tc_sizes)]
     plan += [(k, "dg_16x16", None, dg_sizes) for k in ("dg_nopf", "dg_upf", "dg_dmpf", "dg_dmpft")]
     plan += [(k, "fd", None, [{"n": int(round(1024 * 2 ** (i / 7.0)))} for i in range(29)])
              for k in ("fd_tile", "fd_direct")]
@@ -148,6 +151,13 @@ def sweep_studies():
         held = [(k, p) for i, p in enumerate(sizes) if i % 3 == 2]
         measure = (base[parent]["measure"] if parent else common_measurements()) + fit
         out.append(dict(name="sweep_" + k, expr=expr or base[parent]["expr"], measure=measure, modeled=held))
+    # both tensor-core tile shapes in one calibration: their bf16 loads per
+    # multiply-add differ (3/256 and 2/256), which separates the load and
+    # tensor-op costs; the held-out sizes then rank the two tiles
+    tcs = ("mm_tc", "mm_tc256")
+    out.append(dict(name="sweep_tc_tiles", expr=tc_expr,
+                    measure=common_measurements() + [(k, p) for k in tcs for i, p in enumerate(tc_sizes) if i % 3 != 2],
+                    modeled=[(k, p) for k in tcs for i, p in enumerate(tc_sizes) if i % 3 == 2]))
     return out
 
 

@@ -80,10 +80,11 @@ def _barrier_groups(p):
 
 
 def _overlap_size(p):
-    # alternate the global footprint with m so the global and local costs
-    # are not both fixed multiples of the launch
+    # alternate the global footprint with m (2^26 and 2^27 floats per array,
+    # both above the L2 size) so the global and local costs are not both
+    # fixed multiples of the launch
     p = dict(p)
-    p["N"] = (1 << 26) // (1 + _OVERLAP_M.index(p["m"]) % 2)
+    p["N"] = (1 << 26) * (1 + _OVERLAP_M.index(p["m"]) % 2)
     return p
 
 
@@ -135,6 +136,7 @@ GENERATORS = [
     Generator("fd_tile18", ["finite_diff", "modeled"], {"n": POW(10, 14)}),
     Generator("fd_direct", ["finite_diff", "modeled"], {"n": POW(10, 14)}),
     Generator("mm_tc", ["matmul_tc", "modeled"], {"n": POW(10, 14)}),
+    Generator("mm_tc256", ["matmul_tc", "modeled"], {"n": POW(10, 14)}),
     Generator("mm_simt", ["matmul_tiles", "autotune"],
               {"n": [7680], "BM": [64, 96, 128, 256], "BN": [64, 128, 256], "BK": [32, 64]}),
     Generator("fd_block", ["stencil_tiles", "autotune"], {"n": [16384], "BX": [32, 64, 128], "BY": [4, 8, 16, 32]}),

@@ -103,3 +103,22 @@ def test_every_suite_family_design_is_full_rank():
         Xs = X / np.abs(X).max(axis=0)
         assert np.linalg.matrix_rank(Xs) == X.shape[1], f
         assert np.linalg.cond(Xs) < 1e3, f
+
+
+def test_tensor_core_tiles_separate_load_and_mma_costs():
+    # at one tile shape the bf16 loads are a fixed multiple of the tensor
+    # multiply-adds (3/256 for 128 x 256 tiles, 2/256 for 256 x 256), so only
+    # a calibration over both shapes identifies both costs
+    import paper_1904_09538_gb300 as pm
+    from paper_1904_09538_gb300.experiments import sweep_studies
+    st = [s for s in sweep_studies() if s["name"] == "sweep_tc_tiles"][0]
+    m = pm.Model("f_wall_time", st["expr"])
+    cols = [m.features.index("f_mem_access_global_bfloat16"), m.features.index("f_op_bfloat16_madd")]
+    rows = {k: np.stack([m.feature_values(k, **p)[cols] for kk, p in st["measure"] if kk == k])
+            for k in ("mm_tc", "mm_tc256")}
+    for k, ratio in (("mm_tc", 3 / 256), ("mm_tc256", 2 / 256)):
+        assert np.allclose(rows[k][:, 0] / rows[k][:, 1], ratio)
+        assert np.linalg.matrix_rank(rows[k] / rows[k].max(axis=0)) == 1
+    both = np.concatenate([rows["mm_tc"], rows["mm_tc256"]])
+    assert np.linalg.matrix_rank(both / both.max(axis=0)) == 2
+    assert {k for k, _ in st["modeled"]} == {"mm_tc", "mm_tc256"}
