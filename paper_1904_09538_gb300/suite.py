@@ -16,6 +16,9 @@ IDENTICAL, SUBSET, SUPERSET, INTERSECT = "identical", "subset", "superset", "int
 
 SM_COUNT = 152
 RESIDENT = 8 * SM_COUNT   # 256-thread work-groups resident at full occupancy
+FMA_F32_PER_SM = 6        # k_fma<float> holds 32 accumulators: 37-39 registers -> 6 CTAs of 256 per SM
+FMA_F64_PER_SM = 3        # k_fma<double>: 70-72 registers -> 3 CTAs of 256 per SM
+L2_BYTES = 129 * 10 ** 6
 
 
 class Generator:
@@ -54,11 +57,20 @@ def _half_on_odd(x):
 def _fma_groups(p):
     # total work per dtype ~2^16 * 256 * RESIDENT operations for float32
     # (halved on every other F), 1/64 of that for float64 (GB300's FP64 rate
-    # is far lower)
+    # is far lower).  float32 grids are whole waves of FMA_F32_PER_SM CTAs per
+    # SM: a last round of 2-4 CTAs per SM is placed unevenly across the SMs
+    # and runs up to 25 % longer than its share of the work, which no count
+    # feature sees.  The float64 loop saturates its pipe at one CTA per SM, so
+    # below one wave it runs whole CTAs per SM.
     F = p["F"]
-    total = (1 << 16) * RESIDENT if p["dtype"] == 0 else (1 << 10) * RESIDENT
     p = dict(p)
-    p["G"] = max(SM_COUNT, total // F // _half_on_odd(F))
+    if p["dtype"] == 0:
+        wave = FMA_F32_PER_SM * SM_COUNT
+        p["G"] = wave * max(1, round((1 << 16) * RESIDENT / F / _half_on_odd(F) / wave))
+    else:
+        wave = FMA_F64_PER_SM * SM_COUNT
+        g = (1 << 10) * RESIDENT / F / _half_on_odd(F)
+        p["G"] = wave * round(g / wave) if g >= wave else SM_COUNT * max(1, round(g / SM_COUNT))
     return p
 
 
@@ -174,6 +186,13 @@ def generate(tags, match=SUPERSET, generators=None):
 
 def calibration_suite():
     return generate(["suite"])
+
+
+def cache_resident(kernel, p):
+    """Stream variants whose footprint is below twice the L2 size: repeated
+    trials would find their arrays in L2, so they are timed from a flushed L2
+    (the features count DRAM-bound accesses)."""
+    return kernel == "stream" and algorithmic_bytes(kernel, p) < 2 * L2_BYTES
 
 
 def algorithmic_bytes(kernel, p):

@@ -317,6 +317,23 @@ def test_kernel_resources_report_launch_shape():
     assert r["threads_per_block"] == 128 and r["grid_blocks"] == (512 // 256) * (512 // 128)
 
 
+def test_suite_wave_sizes_match_residency():
+    # the arithmetic suite sizes its grids in whole waves of the resident
+    # CTAs per SM; the compiled kernels must have that residency
+    from paper_1904_09538_gb300 import suite as S
+    dev()
+    for op in (0, 1, 2):
+        r = pm.resources("fma", dtype=0, op=op, F=1024, G=912)
+        assert r["blocks_per_sm"] == S.FMA_F32_PER_SM and r["sm_count"] == S.SM_COUNT, r
+    r = pm.resources("fma", dtype=1, op=2, F=1024, G=456)
+    assert r["blocks_per_sm"] == S.FMA_F64_PER_SM, r
+    for k, p in S.generate(["ops"]):
+        per_sm = S.FMA_F32_PER_SM if p["dtype"] == 0 else S.FMA_F64_PER_SM
+        assert p["G"] % (per_sm * S.SM_COUNT) == 0 or p["G"] < per_sm * S.SM_COUNT, p
+    for k, p in S.generate(["lmem"]) + S.generate(["sync"]):
+        assert pm.resources(k, **p)["blocks_per_sm"] == S.RESIDENT // S.SM_COUNT, (k, p)
+
+
 @pytest.mark.parametrize("T", [16, 18])
 def test_smem2d_moves_values_exactly(T):
     G = 7
