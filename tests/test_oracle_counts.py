@@ -352,3 +352,21 @@ def test_simt_closed_forms(n, BM, BN, BK):
     for t in ("Bs_ld0", "Bs_ld1"):
         assert by_tag(fs, t)["lstr"] == (1, 0)
     assert single(fs, "sync") == 2 * (n // BK)
+
+
+@pytest.mark.parametrize("kernel,R", [("mm_tc", 128), ("mm_tc256", 256)])
+@pytest.mark.parametrize("n", [256, 512])
+def test_tensor_core_closed_forms(kernel, R, n):
+    # R x 256 tiles: n^3 bf16 multiply-adds; A read once per tile column
+    # (n/256 times), Bt once per tile row (n/R times), by one elected thread
+    # (uniform, lid(0) stride 0); every 16-byte C vector stored once, each
+    # work-item writing one row (lid(0) stride n/4 vectors)
+    fs = features(kernel, n=n)
+    assert op(fs, "bfloat16", "madd", wi=True) == n ** 3
+    a, b = by_tag(fs, "tc-a"), by_tag(fs, "tc-b")
+    assert a["count_wi"] == a["count"] == n ** 3 // 256 and a["footprint"] == n * n and a["lstr"][0] == 0
+    assert b["count_wi"] == n ** 3 // R and b["footprint"] == n * n
+    c = by_tag(fs, "tc-c")
+    assert c["count_wi"] == c["footprint"] == n * n // 4 and c["lstr"][0] == n // 4
+    assert c["count"] == c["count_wi"]   # non-uniform global access: counted per work-item
+    assert single(fs, "groups") == (n // 256) * (n // R) and single(fs, "sync") == 3
