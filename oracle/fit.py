@@ -176,3 +176,14 @@ def geomean(values):
     """Geometric mean (the 'Mean' rows of the paper's accuracy tables)."""
     v = np.asarray(values, dtype=np.float64)
     return float(math.exp(np.mean(np.log(v))))
+
+
+def fit_rows(job):
+    """fit() of a model given by its expression on a feature matrix:
+    job = (expression, feature names, rows (l x nf), t, p0).  A plain
+    function of plain data, so that a process pool can run it.  Returns
+    (p_vec, info)."""
+    from .model import Model
+    expr, names, rows, t, p0 = job
+    m = Model("f_wall_time", expr)
+    return fit(m, [dict(zip(names, r)) for r in rows], t, p0=p0)

@@ -177,3 +177,18 @@ def test_model_features_from_counts():
     vals = {name: feature_value(name, fs) for name in m.features}
     assert vals == {"f_sync_kernel_launch": 1, "f_thread_groups": 4, "f_mem_access_tag:c": 1024,
                     "f_op_float32_madd": 1024}
+
+
+def test_fit_rows_is_fit_on_plain_data():
+    # the process-pool entry point: the same fit from (expression, names,
+    # matrix) as from the model and row dicts; exact recovery without noise
+    expr = "p_a * f_x + p_b * f_y + p_c"
+    m = Model("f_wall_time", expr)
+    X = pm_inputs.integers((30, 2), 77, 1, 1000).astype(np.float64)
+    truth = {"p_a": 3e-9, "p_b": 5e-10, "p_c": 2e-6}
+    F = [dict(zip(m.features, r)) for r in X]
+    t = np.array([m.eval(truth, f) for f in F])
+    p1, _ = ofit.fit(m, F, t)
+    p2, _ = ofit.fit_rows((expr, list(m.features), X, t, None))
+    assert np.array_equal(p1, p2)
+    assert np.allclose(p2, [truth[n] for n in m.params], rtol=1e-10, atol=0)
