@@ -434,6 +434,19 @@ def e2e_measure(pm, S, variants, torch, trials, fit_and_predict):
             arrs.append(a)
         jobs.append((k, arrs, p))
         nbytes += S.algorithmic_bytes(k, p) * trials
+    # this box's link rates (pinned 1 GiB copies, untimed), for reading copy_ms
+    link = {}
+    dbuf = torch.empty(1 << 30, dtype=torch.uint8, device=torch.cuda.current_device())
+    hbuf = ins[0][:1 << 30] if need >= 1 << 30 else torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
+    for name, dst, src in (("h2d_gbs", dbuf, hbuf), ("d2h_gbs", hbuf, dbuf)):
+        dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(3):
+            dst.copy_(src, non_blocking=True)
+        torch.cuda.synchronize()
+        link[name] = round(3 * (1 << 30) / (time.perf_counter() - t1) / 1e9, 1)
+    del dbuf
     # untimed warm-up: the largest variant sizes the reserved staging pool
     big = max(jobs, key=lambda x: sum(a.nbytes for a in x[1]))
     pm.run_host_batch(jobs[:3] + [big, big], warmup=0, trials=1)
@@ -446,6 +459,7 @@ def e2e_measure(pm, S, variants, torch, trials, fit_and_predict):
     os.sched_setaffinity(0, saved)
     return {"value": round(nbytes / dt / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 2), "copy_ms": round(copy_ms, 1),
+            "link": dict(link, copies_at_link_rate_ms=round((h2d / link["h2d_gbs"] + d2h / link["d2h_gbs"]) / 1e6, 1)),
             "host_cpus": len(local) if local else None}
 
 
