@@ -24,6 +24,10 @@ def test_matmul_counts_at_largest_size():
     t = pm.counts("mm_tc", n=n)
     assert rec(t, "f_op_bfloat16_madd")["count"] == n ** 3           # one work-item issues 128x256x16 per instruction
     assert rec(t, "f_thread_groups")["count"] == (n // 256) * (n // 128)
+    w = pm.counts("mm_tc256", n=n)
+    assert rec(w, "f_op_bfloat16_madd")["count"] == n ** 3
+    assert rec(w, "f_thread_groups")["count"] == (n // 256) ** 2
+    assert rec(w, "f_mem_access_tag:tc-b")["count"] == n ** 3 // 256
 
 
 @pytest.mark.parametrize("kernel", ["fd_tile", "fd_tile18", "fd_direct"])
@@ -61,6 +65,7 @@ def test_counts_cap_protocol():
 
 @pytest.mark.parametrize("kernel,params", [
     ("mm_pf", dict(n=0)), ("mm_pf", dict(n=17)), ("mm_tc", dict(n=384)), ("mm_tc", dict(n=512, pipe=3)),
+    ("mm_tc256", dict(n=384)), ("mm_tc256", dict(n=32768 + 256)),
     ("fd_block", dict(n=100, BX=64, BY=8)), ("fd_block", dict(n=256, BX=64, BY=8, V=2)),
     ("fd_tile", dict(n=0)), ("dg_upf", dict(Np=20, Nel=32, L0=32, L1=8)), ("dg_nopf", dict(Np=0, Nel=32)),
     ("smem2d", dict(R=8, T=17, G=1)), ("stream", dict(N=1000)), ("stream", dict(N=1 << 20, s=3)),

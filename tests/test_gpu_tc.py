@@ -117,3 +117,21 @@ def test_mm_tc256_resources():
     assert r["threads_per_block"] == 256 and r["blocks_per_sm"] == 1
     assert r["grid_blocks"] == (8192 // 256) ** 2
     assert r["local_bytes_per_thread"] == 0
+
+
+@pytest.mark.parametrize("kernel", ["mm_tc", "mm_tc256"])
+def test_tc_large_size_sampled(kernel):
+    # n = 16384 (1 GiB of fp32 output): eight sampled rows, every column
+    d = dev()
+    n = 16384
+    a = pm_inputs.bf16_bits((n, n), 23)
+    bt = pm_inputs.bf16_bits((n, n), 24)
+    ta = torch.from_numpy(a.view(np.int16)).to(d)
+    tb = torch.from_numpy(bt.view(np.int16)).to(d)
+    c = torch.empty(n * n, device=d)
+    pm.launch(kernel, [ta, tb, c], n=n)
+    torch.cuda.synchronize()
+    rows = np.unique(pm_inputs.integers((8,), 25, 0, n - 1))
+    ref, rabs = refs.matmul_bf16_tn(a[rows], bt)
+    got = c.view(n, n)[torch.from_numpy(rows).to(d)].cpu().numpy()
+    assert np.max(np.abs(got - ref) / rabs) <= TOL
