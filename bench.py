@@ -474,7 +474,7 @@ def fit_throughput(pm, torch, dev):
     K = 64
     models, Xs, ts, p0s, ls = problem(K)
     # the autotuner picks the fit kernel's CTA size for this batch
-    threads, tune_times = tune_fit_threads(models, Xs, ts, p0s, candidates=(64, 128, 256), reps=5)
+    threads, tune_times = tune_fit_threads(models, Xs, ts, p0s, candidates=(64, 128, 256, 512), reps=5)
     plan = pm.FitPlan(models, [len(t) for t in ts], p0_given=True, threads=threads)
     Xc = np.concatenate([x.ravel() for x in Xs])
     tc = np.concatenate(ts)

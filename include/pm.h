@@ -329,7 +329,7 @@ pm_status pm_fit(const pm_model *m, const double *X, const double *t, size_t l,
  * persistent kernel launch, one CTA per model, replayed from a CUDA graph).
  * A plan fixes the models and row counts; it owns device and pinned host
  * staging buffers (allocated at creation) and the captured graph.
- *   threads: CTA size of the fit kernel (64, 128 or 256; 0 = 128).
+ *   threads: CTA size of the fit kernel (64, 128, 256 or 512; 0 = 128).
  * pm_fit_plan_run: X_concat holds, model after model, rows[k] x
  * n_features(k) FP64 values (row-major); t_concat the outputs; p_inout_concat
  * n_params(k) values per model (start points if opts->use_p0); reports one

@@ -121,7 +121,7 @@ def rank_stencil(target=16384, calib_sizes=(4096, 8192), trials=5, seed=7):
                        bytes_fn=lambda n: 4.0 * ((n + 2) * (n + 4) + n * n))
 
 
-def tune_fit_threads(models, Xs, ts, p0s=None, candidates=(64, 128, 256), reps=10):
+def tune_fit_threads(models, Xs, ts, p0s=None, candidates=(64, 128, 256, 512), reps=10):
     """Time the batched calibration plan at each CTA size; return the fastest
     and all timings (seconds per plan run)."""
     X = np.concatenate([np.asarray(x, dtype=np.float64).ravel() for x in Xs])

@@ -58,12 +58,18 @@ __device__ __forceinline__ df df_mulf(df x, float b) {
     quick_two_sum(p, e, p, e);
     return df{p, e};
 }
+// Long division with three quotient digits.  Each digit only needs to be
+// close (the exact remainder r = x - y q carries its error into the next
+// one), so they come from one reciprocal of y.hi (approximate, a few ulp):
+// after q1 the remainder is ~2^-22 |x|, after q2 ~2^-44, and q3 brings the
+// result to float-float accuracy.
 __device__ __forceinline__ df df_div(df x, df y) {
-    const float q1 = __fdiv_rn(x.hi, y.hi);
+    const float ry = __fdividef(1.0f, y.hi);
+    const float q1 = __fmul_rn(x.hi, ry);
     df r = df_sub(x, df_mulf(y, q1));
-    const float q2 = __fdiv_rn(r.hi, y.hi);
+    const float q2 = __fmul_rn(r.hi, ry);
     r = df_sub(r, df_mulf(y, q2));
-    const float q3 = __fdiv_rn(r.hi, y.hi);
+    const float q3 = __fmul_rn(r.hi, ry);
     float s, e;
     quick_two_sum(q1, q2, s, e);
     return df_add(df{s, e}, df{q3, 0.0f});
@@ -89,13 +95,16 @@ __device__ __forceinline__ df df_expm1(df x) {
     const float k = rintf(__fmul_rn(x.hi, 1.44269502162933349609375f));
     df r = df_sub(x, df_mulf(LN2, k));
     r = df{__fmul_rn(r.hi, 0.0625f), __fmul_rn(r.lo, 0.0625f)};
-    // Horner on r (1 + r/2 (1 + r/3 (... (1 + r/8))))
-    df p = df{1.0f, 0.0f};
-    for (int i = 8; i >= 2; i--) {
-        p = df_mul(p, r);
-        p = df_div(p, df{(float)i, 0.0f});
-        p = df_add(p, df{1.0f, 0.0f});
-    }
+    // Horner on r: sum_{k<8} r^k / (k+1)!, the coefficients as float-float
+    // constants (hi + lo of 1/(k+1)! to 2^-49 relative)
+    df p = df{0x1.a01a02p-16f, -0x1.7f97fap-42f};                        // 1/8!
+    p = df_add(df_mul(p, r), df{0x1.a01a02p-13f, -0x1.7f97fap-39f});       // 1/7!
+    p = df_add(df_mul(p, r), df{0x1.6c16c2p-10f, -0x1.27d27ep-35f});       // 1/6!
+    p = df_add(df_mul(p, r), df{0x1.111112p-7f, -0x1.dddddep-32f});        // 1/5!
+    p = df_add(df_mul(p, r), df{0x1.555556p-5f, -0x1.555556p-30f});        // 1/4!
+    p = df_add(df_mul(p, r), df{0x1.555556p-3f, -0x1.555556p-28f});        // 1/3!
+    p = df_add(df_mul(p, r), df{0.5f, 0.0f});                              // 1/2!
+    p = df_add(df_mul(p, r), df{1.0f, 0.0f});                              // 1/1!
     df s = df_mul(p, r);  // e^(r/16) - 1
     for (int i = 0; i < 4; i++) s = df_add(df_mulf(s, 2.0f), df_mul(s, s));
     if (k == 0.0f) return s;
@@ -146,6 +155,22 @@ struct CAcc {
         add(p, e);
     }
     __device__ double value() const { return (double)s + (double)c; }
+    // the sum as a float-float value (no FP64 arithmetic)
+    __device__ df sum() const {
+        float h, l;
+        two_sum(s, c, h, l);
+        return df{h, l};
+    }
 };
+
+// Sum of a float-float value over the 32 lanes of a warp (butterfly; every
+// lane receives the same result, df_add being symmetric in its operands).
+__device__ __forceinline__ df warp_sum(df x) {
+    for (int o = 16; o; o >>= 1) {
+        const df y = df{__shfl_xor_sync(0xffffffffu, x.hi, o), __shfl_xor_sync(0xffffffffu, x.lo, o)};
+        x = df_add(x, y);
+    }
+    return x;
+}
 
 }  // namespace pm

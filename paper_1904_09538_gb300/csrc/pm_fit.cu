@@ -102,19 +102,16 @@ __device__ T forward(const Ins *code, int n, const F *frow, const T *par, T *v) 
     return v[n - 1];
 }
 
-// Forward sweep in float-float.
-__device__ df forward_df(const Ins *code, int n, const float2 *frow, const df *par, df *v) {
+// Forward sweep in float-float; cst[k] holds instruction k's constant as a
+// float-float value (converted once per program load, not per row).
+__device__ df forward_df(const Ins *code, const df *cst, int n, const float2 *frow, const df *par, df *v) {
     for (int k = 0; k < n; k++) {
         const Ins in = code[k];
         df x;
         switch (in.op) {
         case OP_FEAT: { const float2 f = frow[in.arg]; x = df{f.x, f.y}; break; }
         case OP_PAR: x = par[in.arg]; break;
-        case OP_CONST: {
-            const float h = (float)in.c;
-            x = df{h, (float)(in.c - (double)h)};
-            break;
-        }
+        case OP_CONST: x = cst[k]; break;
         case OP_ADD: x = df_add(v[in.a], v[in.b]); break;
         case OP_SUB: x = df_sub(v[in.a], v[in.b]); break;
         case OP_MUL: x = df_mul(v[in.a], v[in.b]); break;
@@ -198,21 +195,32 @@ struct CSum {
 template <int T>
 struct Smem {
     Ins code[kMaxIns];
+    df cst[kMaxIns];   // constants of `code` in float-float
     float J[T * (MP + 1)];
     float r[T], rl[T];
     double acc[NENT];
+    df accf[NENT];    // the same entries in float-float (the fast solve reads these)
     double q[MP], s[MP], dq[MP], qt[MP];
     df pd[MP];
+    float sf[MP];      // S.s in FP32 (the Jacobian's column scales), set with the parameters
     double M[MP][MP + 1], V[MP][MP + 1], rhs[MP], y[MP];
     int idx[MP];
-    double red[T / 32];
-    double ssr, ssr_new, pred, lambda, med[2];
+    df Mf[MP][MP + 1], rhsf[MP], dinvf[MP];
+    df redf[T / 32];
+    df part[T];       // per row-group partial sums of the assembled entries
+    double ssr, ssr_new, pred, lambda, med[2], noise;
+    int stop;
     int nact, ok, rankdef, rank;
 };
 
 template <int T>
 __device__ void load_code(Smem<T> &S, const Ins *code, int n) {
-    for (int k = threadIdx.x; k < n; k += T) S.code[k] = code[k];
+    for (int k = threadIdx.x; k < n; k += T) {
+        const Ins in = code[k];
+        S.code[k] = in;
+        const float h = (float)in.c;
+        S.cst[k] = df{h, (float)(in.c - (double)h)};
+    }
     __syncthreads();
 }
 
@@ -221,6 +229,7 @@ template <int T>
 __device__ void set_params(Smem<T> &S, const double *q, int m) {
     if (threadIdx.x < m) {
         const double p = S.s[threadIdx.x] * q[threadIdx.x];
+        S.sf[threadIdx.x] = (float)S.s[threadIdx.x];
         const float h = (float)p;
         S.pd[threadIdx.x] = df{h, (float)(p - (double)h)};
     }
@@ -230,13 +239,46 @@ __device__ void set_params(Smem<T> &S, const double *q, int m) {
 // r_k = 1 - g_k / t_k in float-float
 __device__ __forceinline__ df resid_df(df g, float2 t) { return df_sub(df{1.0f, 0.0f}, df_div(g, df{t.x, t.y})); }
 
+// Entry e of the assembled system over rows k = k0, k0 + step, ... < rows of
+// the staged block: A_ij (e < nA, row-major upper triangle), b_i, or the SSR.
+template <int T>
+__device__ __forceinline__ void add_entry(const Smem<T> &S, CAcc &a, int e, int m, int nA, int k0, int step,
+                                          int rows) {
+    if (e < nA) {
+        int i = 0, rem = e;
+        while (rem >= m - i) { rem -= m - i; i++; }
+        const int j = i + rem;
+        for (int k = k0; k < rows; k += step) a.add_prod(S.J[k * (MP + 1) + i], S.J[k * (MP + 1) + j]);
+    } else if (e < nA + m) {
+        const int i = e - nA;
+        for (int k = k0; k < rows; k += step) {
+            const float ji = S.J[k * (MP + 1) + i];
+            float p, er;
+            two_prod(ji, S.r[k], p, er);
+            a.add(p, __fmaf_rn(ji, S.rl[k], er));
+        }
+    } else {
+        for (int k = k0; k < rows; k += step) {
+            float p, er;
+            two_prod(S.r[k], S.r[k], p, er);
+            a.add(p, __fmaf_rn(2.0f * S.r[k], S.rl[k], er));
+        }
+    }
+}
+
 // Assemble over all rows of the job: A = J^T J (upper, if want_A), b = J^T r,
 // ssr = r^T r, with J_ki = -(dg_k/dp_i) s_i / t_k (scaled coordinates q).
-// Parameters outside `mask` get a zero column.
+// Parameters outside `mask` get a zero column.  With nE entries and
+// 2 nE <= T, each entry is summed by G = T / nE threads over interleaved
+// rows (compensated FP32 sums, one per thread across all row blocks), and
+// the G partial sums are added in FP64 in a fixed order; otherwise each
+// thread sums whole entries.
 template <int T>
 __device__ void assemble(Smem<T> &S, const FitJob &jb, int n, unsigned mask, bool want_A) {
     const int m = jb.m, tid = threadIdx.x;
     const int nA = m * (m + 1) / 2, nE = nA + m + 1;
+    const int G = 2 * nE <= T ? T / nE : 1;
+    const int ge = tid % nE, gg = tid / nE;   // grouped mode: entry, row group
     CAcc acc[3];
     for (int u = 0; u < 3; u++) acc[u].init();
     df v[kMaxIns];
@@ -247,11 +289,12 @@ __device__ void assemble(Smem<T> &S, const FitJob &jb, int n, unsigned mask, boo
         if (row < jb.l) {
             const float2 *frow = jb.X + (size_t)row * jb.nf;
             const float2 tk = jb.t[row];
-            const df gk = forward_df(S.code, n, frow, S.pd, v);
+            const df gk = forward_df(S.code, S.cst, n, frow, S.pd, v);
             rr = resid_df(gk, tk);
             reverse_df(S.code, n, v, adj, g, m);
+            const float rt = __frcp_rn(tk.x);
             for (int i = 0; i < m; i++)
-                S.J[tid * (MP + 1) + i] = ((mask >> i) & 1u) ? -g[i] * (float)S.s[i] / tk.x : 0.0f;
+                S.J[tid * (MP + 1) + i] = ((mask >> i) & 1u) ? -g[i] * S.sf[i] * rt : 0.0f;
         } else {
             for (int i = 0; i < m; i++) S.J[tid * (MP + 1) + i] = 0.0f;
         }
@@ -259,37 +302,35 @@ __device__ void assemble(Smem<T> &S, const FitJob &jb, int n, unsigned mask, boo
         S.rl[tid] = rr.lo;
         __syncthreads();
         const int rows = min(T, jb.l - base);
-        for (int u = 0; u < 3; u++) {
-            const int e = tid + u * T;
-            if (e >= nE) break;
-            if (e < nA) {
-                if (!want_A) continue;
-                // e -> (i, j), i <= j, row-major upper triangle
-                int i = 0, rem = e;
-                while (rem >= m - i) { rem -= m - i; i++; }
-                const int j = i + rem;
-                for (int k = 0; k < rows; k++) acc[u].add_prod(S.J[k * (MP + 1) + i], S.J[k * (MP + 1) + j]);
-            } else if (e < nA + m) {
-                const int i = e - nA;
-                for (int k = 0; k < rows; k++) {
-                    const float ji = S.J[k * (MP + 1) + i];
-                    float p, er;
-                    two_prod(ji, S.r[k], p, er);
-                    acc[u].add(p, __fmaf_rn(ji, S.rl[k], er));
-                }
-            } else {
-                for (int k = 0; k < rows; k++) {
-                    float p, er;
-                    two_prod(S.r[k], S.r[k], p, er);
-                    acc[u].add(p, __fmaf_rn(2.0f * S.r[k], S.rl[k], er));
-                }
+        if (G > 1) {
+            if (gg < G && (want_A || ge >= nA)) add_entry(S, acc[0], ge, m, nA, gg, G, rows);
+        } else {
+            for (int u = 0; u < 3; u++) {
+                const int e = tid + u * T;
+                if (e >= nE) break;
+                if (e < nA && !want_A) continue;
+                add_entry(S, acc[u], e, m, nA, 0, 1, rows);
             }
         }
         __syncthreads();
     }
-    for (int u = 0; u < 3; u++) {
-        const int e = tid + u * T;
-        if (e < nE && (want_A || e >= nA)) S.acc[e] = acc[u].value();
+    if (G > 1) {
+        if (gg < G) S.part[gg * nE + ge] = acc[0].sum();
+        __syncthreads();
+        if (tid < nE && (want_A || tid >= nA)) {
+            df x = S.part[tid];
+            for (int g2 = 1; g2 < G; g2++) x = df_add(x, S.part[g2 * nE + tid]);
+            S.accf[tid] = x;
+            S.acc[tid] = (double)x.hi + (double)x.lo;
+        }
+    } else {
+        for (int u = 0; u < 3; u++) {
+            const int e = tid + u * T;
+            if (e < nE && (want_A || e >= nA)) {
+                S.accf[e] = acc[u].sum();
+                S.acc[e] = (double)S.accf[e].hi + (double)S.accf[e].lo;
+            }
+        }
     }
     __syncthreads();
     if (tid == 0) S.ssr = S.acc[nE - 1];
@@ -303,20 +344,19 @@ __device__ double ssr_pass(Smem<T> &S, const FitJob &jb, int n) {
     a.init();
     df v[kMaxIns];
     for (int row = threadIdx.x; row < jb.l; row += T) {
-        const df gk = forward_df(S.code, n, jb.X + (size_t)row * jb.nf, S.pd, v);
+        const df gk = forward_df(S.code, S.cst, n, jb.X + (size_t)row * jb.nf, S.pd, v);
         const df rr = resid_df(gk, jb.t[row]);
         float p, er;
         two_prod(rr.hi, rr.hi, p, er);
         a.add(p, __fmaf_rn(2.0f * rr.hi, rr.lo, er));
     }
-    double x = a.value();
-    for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-    if ((threadIdx.x & 31) == 0) S.red[threadIdx.x >> 5] = x;
+    df x = warp_sum(a.sum());
+    if ((threadIdx.x & 31) == 0) S.redf[threadIdx.x >> 5] = x;
     __syncthreads();
-    double tot = 0.0;
-    for (int w = 0; w < T / 32; w++) tot += S.red[w];
+    df tot = S.redf[0];
+    for (int w = 1; w < T / 32; w++) tot = df_add(tot, S.redf[w]);
     __syncthreads();
-    return tot;
+    return (double)tot.hi + (double)tot.lo;
 }
 
 __device__ __forceinline__ double A_at(const double *acc, int m, int i, int j) {
@@ -324,70 +364,92 @@ __device__ __forceinline__ double A_at(const double *acc, int m, int i, int j) {
     return acc[i * m - i * (i - 1) / 2 + (j - i)];
 }
 
+__device__ __forceinline__ df A_atf(const df *acc, int m, int i, int j) {
+    if (i > j) { const int t = i; i = j; j = t; }
+    return acc[i * m - i * (i - 1) / 2 + (j - i)];
+}
+
 // Warp 0: solve (Ahat + lambda I) y = -bhat on the active set, Ahat the
-// unit-diagonal scaling of A; dq = y / sqrt(diag A).  S.ok = 0 when a
+// unit-diagonal scaling of A; dq = y / sqrt(diag A).  Float-float arithmetic
+// on the FP32 pipes (GB300's FP64 pipe retires about two lanes per clock
+// per SM; the LM step is refined by the iteration itself).  S.ok = 0 when a
 // pivot is not positive (relative 1e-10).  Also S.pred = predicted SSR
 // decrease -(2 dq.b + dq^T A dq).
 template <int T>
 __device__ void solve_chol(Smem<T> &S, int m, double lambda) {
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x, n = S.nact;
-        const double *acc = S.acc;
+        const df *acc = S.accf;
         const int nA = m * (m + 1) / 2;
-        if (lane < n) {
-            const int gi = S.idx[lane];
-            const double di = sqrt(A_at(acc, m, gi, gi));
-            for (int c = 0; c < n; c++) {
-                const int gj = S.idx[c];
-                const double dj = sqrt(A_at(acc, m, gj, gj));
-                S.M[lane][c] = A_at(acc, m, gi, gj) / (di * dj) + (c == lane ? lambda : 0.0);
-            }
-            S.rhs[lane] = -acc[nA + gi] / di;
-        }
+        const float lh = (float)lambda;
+        const df lam = df{lh, (float)(lambda - (double)lh)};
+        df dinv = df{0.0f, 0.0f};
+        if (lane < n) dinv = df_div(df{1.0f, 0.0f}, df_sqrt(A_atf(acc, m, S.idx[lane], S.idx[lane])));
+        if (lane < MP) S.dinvf[lane] = dinv;
         if (lane == 0) S.ok = 1;
         __syncwarp();
-        for (int k = 0; k < n; k++) {
-            if (lane == 0) {
-                const double d = S.M[k][k];
-                if (!(d > 1e-10)) S.ok = 0;
-                S.M[k][k] = sqrt(fmax(d, 1e-300));
+        if (lane < n) {
+            const int gi = S.idx[lane];
+            for (int c = 0; c < n; c++) {
+                df x = df_mul(df_mul(A_atf(acc, m, gi, S.idx[c]), dinv), S.dinvf[c]);
+                if (c == lane) x = df_add(x, lam);
+                S.Mf[lane][c] = x;
             }
+            S.rhsf[lane] = df_neg(df_mul(acc[nA + gi], dinv));
+        }
+        __syncwarp();
+        // Cholesky, lower factor in place
+        for (int k = 0; k < n; k++) {
+            const df d = S.Mf[k][k];
+            if (lane == 0 && !(d.hi > 1e-10f)) S.ok = 0;
+            const df piv = df_sqrt(d.hi > 1e-30f ? d : df{1e-30f, 0.0f});
+            if (lane > k && lane < n) S.Mf[lane][k] = df_div(S.Mf[lane][k], piv);
             __syncwarp();
-            if (lane > k && lane < n) S.M[lane][k] /= S.M[k][k];
-            __syncwarp();
-            if (lane > k && lane < n)
-                for (int j = k + 1; j <= lane; j++) S.M[lane][j] -= S.M[lane][k] * S.M[j][k];
+            if (lane == k) S.Mf[k][k] = piv;
+            if (lane > k && lane < n) {
+                const df lk = S.Mf[lane][k];
+                for (int j = k + 1; j <= lane; j++) S.Mf[lane][j] = df_sub(S.Mf[lane][j], df_mul(lk, S.Mf[j][k]));
+            }
             __syncwarp();
         }
         // forward: L z = rhs
         for (int k = 0; k < n; k++) {
-            if (lane == 0) S.rhs[k] /= S.M[k][k];
+            if (lane == k) S.rhsf[k] = df_div(S.rhsf[k], S.Mf[k][k]);
             __syncwarp();
-            if (lane > k && lane < n) S.rhs[lane] -= S.M[lane][k] * S.rhs[k];
+            if (lane > k && lane < n) S.rhsf[lane] = df_sub(S.rhsf[lane], df_mul(S.Mf[lane][k], S.rhsf[k]));
             __syncwarp();
         }
         // backward: L^T y = z
         for (int k = n - 1; k >= 0; k--) {
-            if (lane == 0) S.rhs[k] /= S.M[k][k];
+            if (lane == k) S.rhsf[k] = df_div(S.rhsf[k], S.Mf[k][k]);
             __syncwarp();
-            if (lane < k) S.rhs[lane] -= S.M[k][lane] * S.rhs[k];
+            if (lane < k) S.rhsf[lane] = df_sub(S.rhsf[lane], df_mul(S.Mf[k][lane], S.rhsf[k]));
             __syncwarp();
         }
+        // dq in every parameter slot (zero outside the active set)
+        df dql = df{0.0f, 0.0f};
+        int gl = -1;
+        if (lane < n) {
+            gl = S.idx[lane];
+            dql = df_mul(S.rhsf[lane], dinv);
+        }
+        __syncwarp();
         if (lane < m) S.dq[lane] = 0.0;
         __syncwarp();
-        if (lane < n) {
-            const int gi = S.idx[lane];
-            S.dq[gi] = S.rhs[lane] / sqrt(A_at(acc, m, gi, gi));
-        }
+        if (gl >= 0) S.dq[gl] = (double)dql.hi + (double)dql.lo;
+        // predicted decrease: lane i adds dq_i (2 b_i + sum_j A_ij dq_j)
+        if (lane < MP) S.dinvf[lane] = df{0.0f, 0.0f};
         __syncwarp();
-        if (lane == 0) {
-            double db = 0.0, dAd = 0.0;
-            for (int i = 0; i < m; i++) {
-                db += S.dq[i] * acc[nA + i];
-                for (int j = 0; j < m; j++) dAd += S.dq[i] * A_at(acc, m, i, j) * S.dq[j];
-            }
-            S.pred = -(2.0 * db + dAd);
+        if (gl >= 0) S.dinvf[gl] = dql;   // dq by parameter index, float-float
+        __syncwarp();
+        df t = df{0.0f, 0.0f};
+        if (lane < m) {
+            df w = df_add(acc[nA + lane], acc[nA + lane]);
+            for (int j = 0; j < m; j++) w = df_add(w, df_mul(A_atf(acc, m, lane, j), S.dinvf[j]));
+            t = df_mul(S.dinvf[lane], w);
         }
+        t = warp_sum(t);
+        if (lane == 0) S.pred = -((double)t.hi + (double)t.lo);
     }
     __syncthreads();
 }
@@ -613,9 +675,12 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
     bool converged = false;
     for (int it = 0; it < cfg.max_iter; it++) {
         bool accepted = false;
-        double ssr_old = S.ssr;
-        // noise floor of an SSR built from float-float residuals
-        const double noise = 4.0 * EPS_DF * sqrt((double)jb.l * ssr_old) + (double)jb.l * EPS_DF * EPS_DF;
+        const double ssr_old = S.ssr;
+        // noise floor of an SSR built from float-float residuals (one thread:
+        // FP64 work on every warp costs the whole CTA)
+        if (tid == 0) S.noise = 4.0 * EPS_DF * sqrt((double)jb.l * ssr_old) + (double)jb.l * EPS_DF * EPS_DF;
+        __syncthreads();
+        const double noise = S.noise;
         for (int tr = 0; tr < 16; tr++) {
             solve_chol(S, m, S.lambda);
             if (!S.ok) {
@@ -641,14 +706,14 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
             converged = true;  // no decrease possible above the noise floor
             break;
         }
-        double dn = 0.0, qn = 0.0;
-        for (int i = 0; i < m; i++) {
-            dn += S.dq[i] * S.dq[i];
-            qn += S.qt[i] * S.qt[i];
+        if (tid == 0) {
+            double dn = 0.0, qn = 0.0;
+            for (int i = 0; i < m; i++) {
+                dn += S.dq[i] * S.dq[i];
+                qn += S.qt[i] * S.qt[i];
+            }
+            S.stop = sqrt(dn) <= cfg.xtol * (sqrt(qn) + cfg.xtol) || S.pred <= noise;
         }
-        dn = sqrt(dn);
-        qn = sqrt(qn);
-        const double pred = S.pred;
         __syncthreads();
         if (tid < m) S.q[tid] = S.qt[tid];
         if (tid == 0) S.lambda = fmax(S.lambda * 0.1, 1e-12);
@@ -657,8 +722,9 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
         set_params(S, S.q, m);
         assemble(S, jb, jb.n_code, all, true);
         set_active(S, m, all);
-        if (dn <= cfg.xtol * (qn + cfg.xtol) || pred <= noise ||
-            (ssr_old - S.ssr) <= cfg.ftol * ssr_old) {
+        if (tid == 0) S.stop = S.stop || (ssr_old - S.ssr) <= cfg.ftol * ssr_old;
+        __syncthreads();
+        if (S.stop) {
             converged = true;
             break;
         }
@@ -764,6 +830,7 @@ pm_status launch_fit(int threads, const FitJob *jobs, int njobs, FitCfg cfg, cud
     switch (threads) {
     case 64: return launch_fit_t<64>(jobs, njobs, cfg, st);
     case 256: return launch_fit_t<256>(jobs, njobs, cfg, st);
+    case 512: return launch_fit_t<512>(jobs, njobs, cfg, st);
     default: return launch_fit_t<128>(jobs, njobs, cfg, st);
     }
 }
@@ -918,8 +985,8 @@ pm_status pm_fit_plan_create(const pm_model *const *models, size_t nmodels, cons
                              const pm_fit_opts *opts, int32_t threads, pm_fit_plan **plan) {
     if (!models || !rows || !plan || nmodels == 0) return fail(PM_EINVAL, "pm_fit_plan_create: bad argument");
     if (nmodels > 65535) return fail(PM_EINVAL, "pm_fit_plan_create: at most 65535 models");
-    if (threads != 0 && threads != 64 && threads != 128 && threads != 256)
-        return fail(PM_EINVAL, "pm_fit_plan_create: threads must be 0, 64, 128 or 256");
+    if (threads != 0 && threads != 64 && threads != 128 && threads != 256 && threads != 512)
+        return fail(PM_EINVAL, "pm_fit_plan_create: threads must be 0, 64, 128, 256 or 512");
     pm_fit_plan *P = new (std::nothrow) pm_fit_plan();
     if (!P) return fail(PM_ENOMEM, "pm_fit_plan_create: out of memory");
     pm_status s = check_opts(opts, P->cfg, P->use_p0);
@@ -951,16 +1018,25 @@ void pm_fit_plan_destroy(pm_fit_plan *plan) { delete plan; }
 pm_status pm_fit_plan_run(pm_fit_plan *P, const double *X, const double *t, double *p_inout, pm_fit_report *reports,
                           void *stream) {
     if (!P || !t || !p_inout || (P->nx && !X)) return fail(PM_EINVAL, "pm_fit_plan_run: NULL argument");
+    // validate while copying into the pinned staging buffers (one pass)
     for (size_t k = 0, o = 0; k < P->models.size(); k++)
-        for (size_t r = 0; r < P->rows[k]; r++, o++)
-            if (!finite_pos(t[o])) return fail(PM_EINVAL, "fit: model %zu row %zu: output must be finite and > 0", k, r);
-    for (size_t i = 0; i < P->nx; i++)
-        if (!std::isfinite(X[i])) return fail(PM_EINVAL, "fit: feature value %zu is not finite", i);
+        for (size_t r = 0; r < P->rows[k]; r++, o++) {
+            const double v = t[o];
+            if (!finite_pos(v)) return fail(PM_EINVAL, "fit: model %zu row %zu: output must be finite and > 0", k, r);
+            P->ht[o] = v;
+        }
+    bool bad = false;
+    for (size_t i = 0; i < P->nx; i++) {
+        const double v = X[i];
+        bad |= !std::isfinite(v);
+        P->hX[i] = v;
+    }
+    if (bad)
+        for (size_t i = 0; i < P->nx; i++)
+            if (!std::isfinite(X[i])) return fail(PM_EINVAL, "fit: feature value %zu is not finite", i);
     if (P->use_p0)
         for (size_t i = 0; i < P->np; i++)
             if (!std::isfinite(p_inout[i])) return fail(PM_EINVAL, "fit: start point %zu is not finite", i);
-    memcpy(P->hX, X, P->nx * 8);
-    memcpy(P->ht, t, P->nt * 8);
     memcpy(P->hp, p_inout, P->np * 8);
     cudaStream_t st = (cudaStream_t)stream;
     PM_CUDA_TRY(cudaGraphLaunch(P->exec, st));

@@ -138,7 +138,7 @@ def test_batched_uneven_matches_single_and_oracle():
         ts.append(t)
         p0s.append(p0)
         refs.append(ofit.fit(om, F, t, p0=p0)[0])
-    for threads in (64, 128, 256):
+    for threads in (64, 128, 256, 512):
         ps, reps = pm.fit_batched(models, Xs, ts, p0s, threads=threads)
         for k in range(K):
             assert reps[k]["status"] == 0, (k, reps[k])
