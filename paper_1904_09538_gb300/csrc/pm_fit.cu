@@ -374,7 +374,7 @@ __device__ __forceinline__ df A_atf(const df *acc, int m, int i, int j) {
 // on the FP32 pipes (GB300's FP64 pipe retires about two lanes per clock
 // per SM; the LM step is refined by the iteration itself).  S.ok = 0 when a
 // pivot is not positive (relative 1e-10).  Also S.pred = predicted SSR
-// decrease -(2 dq.b + dq^T A dq).
+// decrease -(2 dq.b + dq^T A dq), evaluated as -dq.b + lambda dq^T D dq.
 template <int T>
 __device__ void solve_chol(Smem<T> &S, int m, double lambda) {
     if (threadIdx.x < 32) {
@@ -437,19 +437,18 @@ __device__ void solve_chol(Smem<T> &S, int m, double lambda) {
         if (lane < m) S.dq[lane] = 0.0;
         __syncwarp();
         if (gl >= 0) S.dq[gl] = (double)dql.hi + (double)dql.lo;
-        // predicted decrease: lane i adds dq_i (2 b_i + sum_j A_ij dq_j)
-        if (lane < MP) S.dinvf[lane] = df{0.0f, 0.0f};
-        __syncwarp();
-        if (gl >= 0) S.dinvf[gl] = dql;   // dq by parameter index, float-float
-        __syncwarp();
+        // predicted decrease -(2 dq.b + dq^T A dq).  With (A + lambda D) dq = -b
+        // (D = diag A) it equals -dq.b + lambda dq^T D dq, in the scaled
+        // coordinates -y.bhat + lambda y.y: two non-negative terms, free of
+        // the cancellation the first form suffers near convergence.
         df t = df{0.0f, 0.0f};
-        if (lane < m) {
-            df w = df_add(acc[nA + lane], acc[nA + lane]);
-            for (int j = 0; j < m; j++) w = df_add(w, df_mul(A_atf(acc, m, lane, j), S.dinvf[j]));
-            t = df_mul(S.dinvf[lane], w);
+        if (lane < n) {
+            const df y = S.rhsf[lane];
+            const df bh = df_mul(acc[nA + gl], dinv);
+            t = df_sub(df_mul(lam, df_mul(y, y)), df_mul(y, bh));
         }
         t = warp_sum(t);
-        if (lane == 0) S.pred = -((double)t.hi + (double)t.lo);
+        if (lane == 0) S.pred = (double)t.hi + (double)t.lo;
     }
     __syncthreads();
 }
