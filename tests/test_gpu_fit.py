@@ -248,3 +248,30 @@ def test_batched_single_row_and_single_parameter_models():
     p, reps = plan.run(np.concatenate([X1.ravel(), X2.ravel()]), np.concatenate([t1, t2]))
     assert reps[0]["status"] == 0 and abs(p[0] * 4.0e6 / 1.2e-5 - 1) <= 1e-12
     assert reps[1]["status"] == 0 and perr(p[1:], vec(lin, P_LIN)) <= 1e-8
+
+
+OVL_BIG = overlap_expr(
+    "p_launch * f_sync_kernel_launch + p_group * f_thread_groups + p_bar * f_sync_barrier_local",
+    "p_g1 * f_mem_access_global_float32 + p_g2 * f_mem_access_global_float64",
+    "p_madd * f_op_float32_madd + p_add * f_op_float32_add + p_lmem * f_mem_access_local_float32")
+P_BIG = dict(p_launch=5e-6, p_group=2e-9, p_bar=1e-10, p_g1=6e-12, p_g2=9e-12, p_madd=3e-12, p_add=2e-12,
+             p_lmem=2e-12, p_edge=3e4)
+
+
+@pytest.mark.parametrize("threads", [128, 512])
+@pytest.mark.parametrize("sigma,seed", [(1e-2, 31), (3e-2, 32)])
+def test_large_overlap_model_converges(sigma, seed, threads):
+    # nine parameters, noisy outputs, default start point: the LM must stop
+    # on its own criteria (status 0, not the iteration limit) and predict
+    # like the FP64 oracle
+    dev()
+    X = design(300, seed, nf=8)
+    t, om, F = synth(OVL_BIG, X, P_BIG, sigma, seed + 100)
+    m = pm.Model("f_wall_time", OVL_BIG)
+    assert m.features == om.features and len(m.params) == 9
+    ps, reps = pm.fit_batched([m], [X], [t], threads=threads)
+    assert reps[0]["status"] == 0 and reps[0]["iterations"] < 200, reps[0]
+    po, _ = ofit.fit(om, F, t)
+    pred = m.predict(ps[0], X)
+    pred_o = ofit.predict(om, po, F)
+    assert np.max(np.abs(pred / pred_o - 1)) <= 1e-5
