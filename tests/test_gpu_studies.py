@@ -1,0 +1,44 @@
+"""End-to-end calibration parity on GB300 timings: a reduced matmul study
+(the paper's measurement kernels plus the matmul twins, tanh overlap model,
+Section "Matrix Multiplication") is timed and calibrated by the library;
+the oracle refits the same measured rows and must reach the same optimum."""
+import math
+
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import paper_1904_09538_gb300 as pm  # noqa: E402
+from paper_1904_09538_gb300 import experiments as E  # noqa: E402
+from oracle import fit as ofit  # noqa: E402
+from oracle.model import Model as OModel  # noqa: E402
+
+
+def test_matmul_study_calibration_matches_oracle():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    mm = [s for s in E.studies() if s["name"] == "matmul"][0]
+    twins = [(k, p) for k, p in mm["measure"] if k.startswith("mm_") and p["n"] in (1024, 2048, 3072, 4096)]
+    common = [(k, p) for k, p in mm["measure"] if not k.startswith("mm_")]
+    st = dict(mm, name="mm_small", measure=common + twins,
+              modeled=[(k, {"n": n}) for k in ("mm_pf", "mm_nopf") for n in (1536, 2560, 3584)])
+    rep = E.run_studies(trials=5, study_list=[st])["mm_small"]
+    assert rep["fit"]["status"] == 0, rep["fit"]
+    m = pm.Model("f_wall_time", st["expr"])
+    om = OModel("f_wall_time", st["expr"])
+    rows = rep["measure_rows"]
+    X = np.stack([m.feature_values(r["kernel"], **r["params"]) for r in rows])
+    t = np.array([r["measured_s"] for r in rows])
+    F = [dict(zip(om.features, x)) for x in X]
+    po, _ = ofit.fit(om, F, t)
+    ssr_o = float(np.sum((1 - np.array(ofit.predict(om, po, F)) / t) ** 2))
+    ssr_g = float(np.sum((1 - np.array([r["fitted_s"] for r in rows]) / t) ** 2))
+    assert abs(ssr_g / ssr_o - 1) <= 1e-4, (ssr_g, ssr_o)
+    # predictions of the held-out matmul sizes from the two calibrations
+    Xp = np.stack([m.feature_values(r["kernel"], **r["params"]) for r in rep["rows"]])
+    pred_o = np.array(ofit.predict(om, po, [dict(zip(om.features, x)) for x in Xp]))
+    pred_g = np.array([r["predicted_s"] for r in rep["rows"]])
+    assert np.max(np.abs(pred_g / pred_o - 1)) <= 1e-3
+    assert math.isfinite(rep["geomean_rel_err"])
