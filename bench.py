@@ -331,24 +331,26 @@ def calibrated_rates(fitted, sm_count, sm_mhz):
     moves 32 x 4 bytes, a stream access one 16-byte vector per work-item.
     FP32 peak = SMs x 128 lanes x 2 x clock; shared memory = SMs x 128 B x
     clock, at the sampled median SM clock (2070 MHz if none was sampled)."""
+    from paper_1904_09538_gb300.report import rate as unit_rate
     clk = (sm_mhz or 2070.0) * 1e6
     fp32_peak, smem_peak = sm_count * 128 * 2 * clk, sm_count * 128 * clk
 
-    def rate(fam, par, units):
+    def rate(fam, par, gran, per_wi):
         v = fitted.get(fam, {}).get(par)
-        return units / v if v and v > 0 else None
+        return None if v is None else unit_rate(v, gran, per_wi)
 
     out = {"sm_mhz": round(clk / 1e6, 1), "fp32_peak_tflops": round(fp32_peak / 1e12, 2),
            "smem_peak_tbs": round(smem_peak / 1e12, 2)}
-    for key, fam, par, units in (("f32_madd_tflops", "fma_f32_madd", "p_madd", 64),
-                                 ("f32_mul_tflops", "fma_f32_mul", "p_mul", 32),
-                                 ("f32_add_tflops", "fma_f32_add", "p_add", 32),
-                                 ("f64_madd_tflops", "fma_f64_madd", "p_madd", 64),
-                                 ("lmem_tbs", "smem_sync0", "p_lmem", 128),
-                                 ("lmem_sync_tbs", "smem_sync1", "p_lmem", 128),
-                                 ("gmem_f32_s1_gbs", "stream_f32_s1", "p_gmem", 16),
-                                 ("gmem_f64_s1_gbs", "stream_f64_s1", "p_gmem", 16)):
-        r = rate(fam, par, units)
+    # (key, family, parameter, counting granularity, flops or bytes per work-item)
+    for key, fam, par, gran, per_wi in (("f32_madd_tflops", "fma_f32_madd", "p_madd", "SG", 2),
+                                        ("f32_mul_tflops", "fma_f32_mul", "p_mul", "SG", 1),
+                                        ("f32_add_tflops", "fma_f32_add", "p_add", "SG", 1),
+                                        ("f64_madd_tflops", "fma_f64_madd", "p_madd", "SG", 2),
+                                        ("lmem_tbs", "smem_sync0", "p_lmem", "SG", 4),
+                                        ("lmem_sync_tbs", "smem_sync1", "p_lmem", "SG", 4),
+                                        ("gmem_f32_s1_gbs", "stream_f32_s1", "p_gmem", "WI", 16),
+                                        ("gmem_f64_s1_gbs", "stream_f64_s1", "p_gmem", "WI", 16)):
+        r = rate(fam, par, gran, per_wi)
         out[key] = round(r / (1e9 if key.endswith("gbs") else 1e12), 3) if r else None
     if out["f32_madd_tflops"]:
         out["f32_madd_frac"] = round(out["f32_madd_tflops"] * 1e12 / fp32_peak, 4)

@@ -122,3 +122,23 @@ def test_tensor_core_tiles_separate_load_and_mma_costs():
     both = np.concatenate([rows["mm_tc"], rows["mm_tc256"]])
     assert np.linalg.matrix_rank(both / both.max(axis=0)) == 2
     assert {k for k, _ in st["modeled"]} == {"mm_tc", "mm_tc256"}
+
+
+def _sig(x, digits=2):
+    return float("%.*g" % (digits, x))
+
+
+def test_rates_reproduce_paper_table_mm_param_vals():
+    # Table mm_param_vals: each printed rate follows from the printed
+    # parameter, its counting granularity and the work per work-item
+    import json
+    from paper_1904_09538_gb300.report import rate
+    g = json.load(open(os.path.join(ROOT, "tests", "golden", "paper_tables.json")))["mm_param_vals"]
+    assert len(g["rows"]) == 9
+    for row in g["rows"]:
+        work = row.get("flops_per_op", row.get("bytes"))
+        r = rate(row["param"], row["mcg"], work)
+        assert _sig(r) == _sig(row["rate"]), (row, r)
+    assert rate(0.0, "SG", 1) is None
+    with pytest.raises(ValueError):
+        rate(1e-12, "WG", 1)
