@@ -397,6 +397,15 @@ pm_status pm_predict(const pm_model *m, const double *p, const double *X, size_t
 /* Thread-local, library-owned message of the last failure ("" if none). */
 const char *pm_last_error(void);
 
+/* Test hook (failure injection on the host, no GPU involvement): after
+ * pm_test_fail_allocation(n) with n >= 1, the n-th next device or pinned-host
+ * allocation the library attempts on the calling thread fails with PM_ENOMEM
+ * before any CUDA call is made; n = 0 disarms it.  Every entry point that
+ * allocates releases what it had allocated and returns PM_ENOMEM.  Genuine
+ * out-of-memory errors from CUDA also map to PM_ENOMEM.  PM_EINVAL for
+ * n < 0. */
+pm_status pm_test_fail_allocation(int32_t n);
+
 #ifdef __cplusplus
 }
 #endif

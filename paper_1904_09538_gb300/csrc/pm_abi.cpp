@@ -20,6 +20,14 @@ pm_status fail(pm_status s, const char *fmt, ...) {
 }
 void clear_error() { g_err[0] = 0; }
 
+// allocation failure injection (pm_test_fail_allocation): countdown per thread
+static thread_local int g_fail_alloc = 0;
+void set_fail_allocation(int n) { g_fail_alloc = n; }
+bool alloc_fault_injected() {
+    if (g_fail_alloc <= 0) return false;
+    return --g_fail_alloc == 0;
+}
+
 static constexpr double REQ = std::numeric_limits<double>::quiet_NaN();
 
 // Parameter lists of each kernel family.  Integer unless noted.
@@ -155,6 +163,12 @@ void canonical_name(pm_feature &f) {
 using namespace pm;
 
 extern "C" {
+
+pm_status pm_test_fail_allocation(int32_t n) {
+    if (n < 0) return pm::fail(PM_EINVAL, "pm_test_fail_allocation: n must be >= 0");
+    pm::set_fail_allocation(n);
+    return PM_OK;
+}
 
 const char *pm_last_error(void) { return g_err; }
 

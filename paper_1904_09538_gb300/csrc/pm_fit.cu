@@ -881,18 +881,18 @@ pm_status plan_build(pm_fit_plan *P) {
         soff[k] = code.size();
         code.insert(code.end(), P->models[k]->start_code.begin(), P->models[k]->start_code.end());
     }
-    PM_CUDA_TRY(cudaMalloc(&P->dX64, std::max<size_t>(P->nx, 1) * 8));
-    PM_CUDA_TRY(cudaMalloc(&P->dX32, std::max<size_t>(P->nx, 1) * 8));
-    PM_CUDA_TRY(cudaMalloc(&P->dt64, P->nt * 8));
-    PM_CUDA_TRY(cudaMalloc(&P->dt32, P->nt * 8));
-    PM_CUDA_TRY(cudaMalloc(&P->dp, P->np * 8));
-    PM_CUDA_TRY(cudaMalloc(&P->drep, K * 8 * 8));
-    PM_CUDA_TRY(cudaMalloc(&P->dcode, code.size() * sizeof(Ins)));
-    PM_CUDA_TRY(cudaMalloc(&P->djobs, K * sizeof(FitJob)));
-    PM_CUDA_TRY(cudaMallocHost(&P->hX, std::max<size_t>(P->nx, 1) * 8));
-    PM_CUDA_TRY(cudaMallocHost(&P->ht, P->nt * 8));
-    PM_CUDA_TRY(cudaMallocHost(&P->hp, P->np * 8));
-    PM_CUDA_TRY(cudaMallocHost(&P->hrep, K * 8 * 8));
+    PM_ALLOC_TRY(cudaMalloc(&P->dX64, std::max<size_t>(P->nx, 1) * 8));
+    PM_ALLOC_TRY(cudaMalloc(&P->dX32, std::max<size_t>(P->nx, 1) * 8));
+    PM_ALLOC_TRY(cudaMalloc(&P->dt64, P->nt * 8));
+    PM_ALLOC_TRY(cudaMalloc(&P->dt32, P->nt * 8));
+    PM_ALLOC_TRY(cudaMalloc(&P->dp, P->np * 8));
+    PM_ALLOC_TRY(cudaMalloc(&P->drep, K * 8 * 8));
+    PM_ALLOC_TRY(cudaMalloc(&P->dcode, code.size() * sizeof(Ins)));
+    PM_ALLOC_TRY(cudaMalloc(&P->djobs, K * sizeof(FitJob)));
+    PM_ALLOC_TRY(cudaMallocHost(&P->hX, std::max<size_t>(P->nx, 1) * 8));
+    PM_ALLOC_TRY(cudaMallocHost(&P->ht, P->nt * 8));
+    PM_ALLOC_TRY(cudaMallocHost(&P->hp, P->np * 8));
+    PM_ALLOC_TRY(cudaMallocHost(&P->hrep, K * 8 * 8));
     std::vector<FitJob> jobs(K);
     size_t toff = 0;
     for (size_t k = 0; k < K; k++) {
@@ -969,7 +969,7 @@ pm_status ensure_device_code(const pm_model *m) {
         cudaFree(mm->d_code);
         mm->d_code = nullptr;
     }
-    PM_CUDA_TRY(cudaMalloc(&mm->d_code, m->code.size() * sizeof(Ins)));
+    PM_ALLOC_TRY(cudaMalloc(&mm->d_code, m->code.size() * sizeof(Ins)));
     PM_CUDA_TRY(cudaMemcpy(mm->d_code, m->code.data(), m->code.size() * sizeof(Ins), cudaMemcpyHostToDevice));
     mm->d_device = dev;
     return PM_OK;
@@ -1085,8 +1085,9 @@ pm_status pm_predict(const pm_model *m, const double *p, const double *X, size_t
     double *dX = nullptr, *dp = nullptr, *dout = nullptr;
     Ins *dc = nullptr;
     pm_status s = PM_OK;
-    if (cudaMalloc(&dX, std::max<size_t>(l * nf, 1) * 8) != cudaSuccess || cudaMalloc(&dp, np * 8) != cudaSuccess ||
-        cudaMalloc(&dout, l * 8) != cudaSuccess || cudaMalloc(&dc, m->code.size() * sizeof(Ins)) != cudaSuccess)
+    auto alloc = [](void **p, size_t b) { return !alloc_fault_injected() && cudaMalloc(p, b) == cudaSuccess; };
+    if (!alloc((void **)&dX, std::max<size_t>(l * nf, 1) * 8) || !alloc((void **)&dp, np * 8) ||
+        !alloc((void **)&dout, l * 8) || !alloc((void **)&dc, m->code.size() * sizeof(Ins)))
         s = fail(PM_ENOMEM, "pm_predict: device allocation failed");
     if (!s && nf && cudaMemcpy(dX, X, l * nf * 8, cudaMemcpyHostToDevice) != cudaSuccess)
         s = fail(PM_ECUDA, "pm_predict: copy failed");

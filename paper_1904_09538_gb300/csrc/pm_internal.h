@@ -12,6 +12,20 @@ namespace pm {
 // ---- errors -------------------------------------------------------------
 pm_status fail(pm_status s, const char *fmt, ...);
 void clear_error();
+bool alloc_fault_injected();   // pm_test_fail_allocation countdown (true: fail this allocation)
+void set_fail_allocation(int n);
+
+// An allocation: PM_ENOMEM when it is refused for lack of memory (or a test
+// injected the failure, see pm_test_fail_allocation), PM_ECUDA otherwise.
+#define PM_ALLOC_TRY(expr)                                                                  \
+    do {                                                                                    \
+        if (::pm::alloc_fault_injected())                                                   \
+            return ::pm::fail(PM_ENOMEM, "%s: allocation failed (injected)", #expr);        \
+        cudaError_t e_ = (expr);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return ::pm::fail(e_ == cudaErrorMemoryAllocation ? PM_ENOMEM : PM_ECUDA, "%s: %s (%s:%d)", \
+                              #expr, cudaGetErrorString(e_), __FILE__, __LINE__);           \
+    } while (0)
 
 #define PM_CUDA_TRY(expr)                                                                   \
     do {                                                                                    \

@@ -97,7 +97,7 @@ static pm_status flush_l2(cudaStream_t st) {
     {
         std::lock_guard<std::mutex> lock(g_flush_mu);
         if (!g_flush[dev]) {
-            if (cudaMalloc(&g_flush[dev], kFlushBytes) != cudaSuccess) {
+            if (alloc_fault_injected() || cudaMalloc(&g_flush[dev], kFlushBytes) != cudaSuccess) {
                 g_flush[dev] = nullptr;
                 return fail(PM_ENOMEM, "flush_l2: cannot allocate the %zu-byte flush buffer", kFlushBytes);
             }
@@ -236,7 +236,7 @@ pm_status pm_run_host(int32_t kernel, const pm_param *p, size_t np, void *const 
     for (int i = 0; i < 4 && rc == PM_OK; i++)
         if (cudaEventCreate(&e[i]) != cudaSuccess) rc = fail(PM_ECUDA, "pm_run_host: cudaEventCreate failed");
     for (size_t i = 0; i < nbufs && rc == PM_OK; i++)
-        if (cudaMallocAsync(&dev[i], spec[i].elems * dtype_size(spec[i].dtype), st) != cudaSuccess)
+        if (alloc_fault_injected() || cudaMallocAsync(&dev[i], spec[i].elems * dtype_size(spec[i].dtype), st) != cudaSuccess)
             rc = fail(PM_ENOMEM, "pm_run_host: cudaMallocAsync of %s failed", spec[i].name);
     if (rc == PM_OK) cudaEventRecord(e[0], st);
     for (size_t i = 0; i < nbufs && rc == PM_OK; i++)
@@ -327,7 +327,7 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
         if (i == 0) cudaEventRecord(ev.ev[3 * njobs], up);
         for (size_t b = 0; b < j.spec.size() && rc == PM_OK; b++) {
             const size_t bytes = j.spec[b].elems * dtype_size(j.spec[b].dtype);
-            if (cudaMallocAsync(&j.dev[b], bytes, up) != cudaSuccess)
+            if (alloc_fault_injected() || cudaMallocAsync(&j.dev[b], bytes, up) != cudaSuccess)
                 rc = fail(PM_ENOMEM, "pm_run_host_batch: job %zu: allocation of %s failed", i, j.spec[b].name);
             else if (j.spec[b].role == PM_IN &&
                      cudaMemcpyAsync(j.dev[b], jobs[i].host_bufs[b], bytes, cudaMemcpyHostToDevice, up) != cudaSuccess)

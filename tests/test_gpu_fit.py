@@ -276,3 +276,36 @@ def test_large_overlap_model_converges(sigma, seed, threads):
     pred = m.predict(ps[0], X)
     pred_o = ofit.predict(om, po, F)
     assert np.max(np.abs(pred / pred_o - 1)) <= 1e-5
+
+
+def test_injected_allocation_failures_return_enomem():
+    # pm_test_fail_allocation makes the n-th next allocation fail on the host
+    # (no GPU fault): each entry point that allocates reports PM_ENOMEM,
+    # releases what it had, and works again once the hook is disarmed
+    dev()
+    L = pm.lib()
+    m = pm.Model("f_wall_time", LIN)
+    X = design(40, 71)
+    t, _, _ = synth(LIN, X, P_LIN, 0.0, 72)
+    try:
+        for n in (1, 4, 9):              # a fit plan allocates 12 staging buffers
+            assert L.pm_test_fail_allocation(n) == 0
+            with pytest.raises(pm.PMError) as ei:
+                pm.FitPlan([m], [len(t)])
+            assert ei.value.status == -2, ei.value
+        assert L.pm_test_fail_allocation(2) == 0
+        with pytest.raises(pm.PMError) as ei:
+            m.predict(vec(OModel("f_wall_time", LIN), P_LIN), X)
+        assert ei.value.status == -2
+        host = [np.ones(1 << 16, dtype=np.float32) for _ in range(2)]
+        assert L.pm_test_fail_allocation(1) == 0
+        with pytest.raises(pm.PMError) as ei:
+            pm.run_host("stream", host, warmup=0, trials=1, N=1 << 16)
+        assert ei.value.status == -2
+        assert L.pm_test_fail_allocation(-1) == -1
+    finally:
+        L.pm_test_fail_allocation(0)
+    p, rep = m.fit(X, t)
+    assert rep["status"] == 0 and perr(p, vec(OModel("f_wall_time", LIN), P_LIN)) <= PTOL
+    out = pm.run_host("stream", host, warmup=0, trials=1, N=1 << 16)
+    assert out["n_trials"] == 1 and np.array_equal(host[1], host[0])
