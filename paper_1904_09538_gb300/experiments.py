@@ -210,21 +210,38 @@ def geomean(x):
     return float(math.exp(np.mean(np.log(x))))
 
 
-def run_studies(trials=10, names=None, seed=1234, flush_l2=True, study_list=None):
+def run_studies(trials=10, names=None, seed=1234, flush_l2=True, study_list=None, cache_path=None):
     """Calibrate each study's model on its measurement set (all studies in one
     batched fit) and predict its modeled kernels.  Returns a report dict.
     flush_l2: every timed trial starts with a cold L2 (pm_run flush_l2).
-    A kernel instance shared by several studies is timed once."""
+    A kernel instance shared by several studies is timed once.
+    cache_path: a JSON timing cache (timings.TimingCache) read before timing
+    and saved after every batch, so an interrupted run resumes."""
     import torch
+    from .timings import TimingCache, device_identity
     dev = torch.device("cuda", torch.cuda.current_device())
     bufs = Buffers(torch, dev, seed)
     sts = [s for s in (study_list if study_list is not None else studies()) if names is None or s["name"] in names]
     cache = {}
+    tc = TimingCache(cache_path, device_identity(torch, dev.index)) if cache_path else None
 
     def timed(kernels):
         todo = [(k, p) for k, p in kernels if (k, tuple(sorted(p.items()))) not in cache]
+        if tc is not None:
+            rest = []
+            for k, p in todo:
+                v = tc.get(k, p, trials, flush_l2)
+                if v is None:
+                    rest.append((k, p))
+                else:
+                    cache[(k, tuple(sorted(p.items())))] = v
+            todo = rest
         for (k, p), t in zip(todo, measure(todo, bufs, trials, flush_l2) if todo else []):
             cache[(k, tuple(sorted(p.items())))] = t
+            if tc is not None:
+                tc.put(k, p, trials, flush_l2, t)
+        if tc is not None and todo:
+            tc.save()
         return np.array([cache[(k, tuple(sorted(p.items())))] for k, p in kernels])
 
     models, Xs, ts, info = [], [], [], []
@@ -270,10 +287,12 @@ def run_studies(trials=10, names=None, seed=1234, flush_l2=True, study_list=None
                              for (k, prm), a, b in zip(s["measure"], tm, fitted)],
             "flush_l2": flush_l2,
         }
+        if tc is not None:
+            report[s["name"]]["timing_cache"] = {"path": cache_path, "hits": tc.hits, "stored": tc.stored}
     return report
 
 
-def diagnostics(trials=10, seed=1234, flush_l2=True):
+def diagnostics(trials=10, seed=1234, flush_l2=True, cache_path=None):
     """The paper's diagnostic experiments on this GPU.
 
     ab_ratio (Section "Data Motion Features", Table ab_pattern): average cost
@@ -326,7 +345,7 @@ def diagnostics(trials=10, seed=1234, flush_l2=True):
         exprs = {"linear": linear(gm), "nonlinear": nonlinear(gm), "partial": partial(gm)}
         if len(set(re.findall(r"\bp_\w+", exprs["partial"]))) > 16:   # the fit's parameter limit
             del exprs["partial"]
-        rep_s = run_studies(trials, seed=seed, flush_l2=flush_l2,
+        rep_s = run_studies(trials, seed=seed, flush_l2=flush_l2, cache_path=cache_path,
                             study_list=[dict(st, name=st["name"] + "_" + kind, expr=e) for kind, e in exprs.items()])
         per = {}
         lin = rep_s[st["name"] + "_linear"]
@@ -347,7 +366,7 @@ def diagnostics(trials=10, seed=1234, flush_l2=True):
     split_onchip = ONCHIP + " + p_l18 * f_mem_access_local_float32_lstrides:{1:18}"
     sts = [dict(fd, name="fd_single_lmem", expr=linear(fd["gmem"]), measure=fd["measure"] + l2d),
            dict(fd, name="fd_split_lmem", expr=linear(fd["gmem"], onchip=split_onchip), measure=fd["measure"] + l2d)]
-    rep_s = run_studies(trials, seed=seed, flush_l2=flush_l2, study_list=sts)
+    rep_s = run_studies(trials, seed=seed, flush_l2=flush_l2, cache_path=cache_path, study_list=sts)
     per_access = {}
     for T in (16, 18):
         rows = [(k, p) for k, p in l2d if p["T"] == T]
@@ -391,9 +410,10 @@ if __name__ == "__main__":
     import json
     import sys
     flush = "--no-flush" not in sys.argv
+    cache = next((a.split("=", 1)[1] for a in sys.argv[1:] if a.startswith("--cache=")), None)
     args = [a for a in sys.argv[1:] if not a.startswith("--")]
-    out = {"illustrative": illustrative(flush_l2=flush), "studies": run_studies(flush_l2=flush),
-           "sweep": run_studies(flush_l2=flush, study_list=sweep_studies()),
-           "diagnostics": diagnostics(flush_l2=flush)}
+    out = {"illustrative": illustrative(flush_l2=flush), "studies": run_studies(flush_l2=flush, cache_path=cache),
+           "sweep": run_studies(flush_l2=flush, study_list=sweep_studies(), cache_path=cache),
+           "diagnostics": diagnostics(flush_l2=flush, cache_path=cache)}
     sys.argv = [sys.argv[0]] + args
     json.dump(out, open(sys.argv[1], "w") if len(sys.argv) > 1 else sys.stdout, indent=1)

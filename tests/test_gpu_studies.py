@@ -42,3 +42,23 @@ def test_matmul_study_calibration_matches_oracle():
     pred_g = np.array([r["predicted_s"] for r in rep["rows"]])
     assert np.max(np.abs(pred_g / pred_o - 1)) <= 1e-3
     assert math.isfinite(rep["geomean_rel_err"])
+
+
+def test_study_resumes_from_timing_cache(tmp_path):
+    # a second run with the same cache times nothing and calibrates to the
+    # same parameters from the cached times
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    fd = [s for s in E.studies() if s["name"] == "fd"][0]
+    common = [(k, p) for k, p in fd["measure"] if k in ("stream", "fma", "empty")]
+    twins = [(k, p) for k, p in fd["measure"] if k.startswith("fd_") and p["n"] <= 4096]
+    st = dict(fd, name="fd_small", measure=common + twins,
+              modeled=[(k, {"n": n}) for k in ("fd_tile", "fd_direct") for n in (1536, 3072)])
+    path = str(tmp_path / "timings.json")
+    r1 = E.run_studies(trials=3, study_list=[st], cache_path=path)["fd_small"]
+    r2 = E.run_studies(trials=3, study_list=[st], cache_path=path)["fd_small"]
+    n = len({(k, tuple(sorted(p.items()))) for k, p in st["measure"] + st["modeled"]})
+    assert r1["timing_cache"]["stored"] == n and r1["timing_cache"]["hits"] == 0
+    assert r2["timing_cache"]["stored"] == 0 and r2["timing_cache"]["hits"] == n
+    assert [r["measured_s"] for r in r1["rows"]] == [r["measured_s"] for r in r2["rows"]]
+    assert r1["params"] == r2["params"]
