@@ -311,6 +311,11 @@ typedef struct {
     int32_t linear;          /* 1 linear least squares, 0 Levenberg-Marquardt */
     double residual;         /* || 1 - g(p; f_k)/t_k ||_2 at the solution */
     double lambda;           /* final LM damping */
+    double cond;             /* condition estimate of the unit-diagonal normal matrix J^T J at the
+                                solution over the active parameters: (largest / smallest Cholesky
+                                pivot)^2, a lower bound of its 2-norm condition number; the
+                                eigenvalue ratio where the factorisation fails; +inf when rank-
+                                deficient */
 } pm_fit_report;
 
 /* Calibrate one model (Section "Computing Model Parameters") on l rows:

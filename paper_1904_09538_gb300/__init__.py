@@ -221,7 +221,7 @@ def _opts(max_iter=200, ftol=1e-15, xtol=1e-12, p0=None):
 
 def _report(r):
     return dict(status=r.status, iterations=r.iterations, rank=r.rank, linear=bool(r.linear), residual=r.residual,
-                lambda_=r.lambda_)
+                lambda_=r.lambda_, cond=r.cond)
 
 
 class Model:

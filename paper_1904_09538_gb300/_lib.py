@@ -61,7 +61,8 @@ class pm_fit_opts(ctypes.Structure):
 
 class pm_fit_report(ctypes.Structure):
     _fields_ = [("status", ctypes.c_int32), ("iterations", ctypes.c_int32), ("rank", ctypes.c_int32),
-                ("linear", ctypes.c_int32), ("residual", ctypes.c_double), ("lambda_", ctypes.c_double)]
+                ("linear", ctypes.c_int32), ("residual", ctypes.c_double), ("lambda_", ctypes.c_double),
+                ("cond", ctypes.c_double)]
 
 
 P = ctypes.POINTER

@@ -208,7 +208,7 @@ struct Smem {
     df Mf[MP][MP + 1], rhsf[MP], dinvf[MP];
     df redf[T / 32];
     df part[T];       // per row-group partial sums of the assembled entries
-    double ssr, ssr_new, pred, lambda, med[2], noise;
+    double ssr, ssr_new, pred, lambda, med[2], noise, cond;
     int stop;
     int nact, ok, rankdef, rank;
 };
@@ -557,6 +557,45 @@ __device__ void set_active(Smem<T> &S, int m, unsigned mask) {
     __syncthreads();
 }
 
+// Condition estimate of the unit-diagonal normal matrix at the current
+// assembly (lambda = 0): (max / min Cholesky pivot)^2, or the eigenvalue
+// ratio when the factorisation fails (+inf if rank-deficient).  Overwrites
+// the last step (S.dq, S.pred).
+template <int T>
+__device__ void cond_estimate(Smem<T> &S, int m) {
+    solve_chol(S, m, 0.0);
+    if (threadIdx.x < 32) {
+        const int lane = threadIdx.x, n = S.nact;
+        float mx = 0.0f, mn = 3.0e38f;
+        if (lane < n) {
+            mx = S.Mf[lane][lane].hi;
+            mn = mx;
+        }
+        for (int o = 16; o; o >>= 1) {
+            mx = fmaxf(mx, __shfl_xor_sync(0xffffffffu, mx, o));
+            mn = fminf(mn, __shfl_xor_sync(0xffffffffu, mn, o));
+        }
+        if (lane == 0) {
+            const double r = (double)mx / (double)mn;
+            S.cond = n == 0 ? 1.0 : (S.ok ? r * r : -1.0);
+        }
+    }
+    __syncthreads();
+    if (S.cond < 0.0) {
+        eigen(S, m);
+        if (threadIdx.x == 0) {
+            double emax = 0.0, emin = INFINITY;
+            for (int i = 0; i < S.nact; i++)
+                if (S.y[i] > 0.0) {
+                    emax = fmax(emax, S.y[i]);
+                    emin = fmin(emin, S.y[i]);
+                }
+            S.cond = S.rank < S.nact ? INFINITY : emax / emin;
+        }
+        __syncthreads();
+    }
+}
+
 // Linear least squares on `code` for the parameters in mask; S.s must be set.
 // Result (scaled) in S.q; S.rank, S.rankdef set.
 template <int T>
@@ -611,6 +650,8 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
         load_code(S, jb.code, jb.n_code);
         linear_fit(S, jb, jb.n_code, all);
         if (tid < m) jb.p[tid] = S.q[tid] * S.s[tid];
+        set_active(S, m, all);
+        cond_estimate(S, m);
         if (tid == 0) {
             jb.rep[0] = S.rankdef ? PM_ERANK : PM_OK;
             jb.rep[1] = 1;
@@ -618,6 +659,7 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
             jb.rep[3] = 1;
             jb.rep[4] = sqrt(S.ssr);
             jb.rep[5] = 0.0;
+            jb.rep[6] = S.cond;
         }
         return;
     }
@@ -730,6 +772,7 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
     }
     if (!converged) status = PM_ENOTCONV;
     if (tid < m) jb.p[tid] = S.q[tid] * S.s[tid];
+    cond_estimate(S, m);
     if (tid == 0) {
         jb.rep[0] = status;
         jb.rep[1] = iters;
@@ -737,6 +780,7 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
         jb.rep[3] = 0;
         jb.rep[4] = sqrt(S.ssr);
         jb.rep[5] = S.lambda;
+        jb.rep[6] = S.cond;
     }
 }
 
@@ -1050,6 +1094,7 @@ pm_status pm_fit_plan_run(pm_fit_plan *P, const double *X, const double *t, doub
             reports[k].linear = (int32_t)r[3];
             reports[k].residual = r[4];
             reports[k].lambda = r[5];
+            reports[k].cond = r[6];
         }
     return PM_OK;
 }
@@ -1278,6 +1323,7 @@ extern "C" pm_status pm_fit_batched_noalloc(const pm_model *const *models, size_
             reports[k].linear = (int32_t)r[3];
             reports[k].residual = r[4];
             reports[k].lambda = r[5];
+            reports[k].cond = r[6];
         }
     PM_CUDA_TRY(cudaStreamSynchronize(st));
     return PM_OK;

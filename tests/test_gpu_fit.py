@@ -309,3 +309,29 @@ def test_injected_allocation_failures_return_enomem():
     assert rep["status"] == 0 and perr(p, vec(OModel("f_wall_time", LIN), P_LIN)) <= PTOL
     out = pm.run_host("stream", host, warmup=0, trials=1, N=1 << 16)
     assert out["n_trials"] == 1 and np.array_equal(host[1], host[0])
+
+
+def test_fit_report_condition_estimate():
+    # (max/min Cholesky pivot)^2 of the unit-diagonal normal matrix: a lower
+    # bound of its 2-norm condition number, within a small factor of it here;
+    # +inf for the rank-deficient matmul design
+    dev()
+    X = design(120, 81)
+    t, om, F = synth(LIN, X, P_LIN, 1e-3, 82)
+    m = pm.Model("f_wall_time", LIN)
+    p, rep = m.fit(X, t)
+    A = X / t[:, None]
+    N = A.T @ A
+    d = np.sqrt(np.diag(N))
+    kappa = np.linalg.cond(N / np.outer(d, d))
+    assert 1.0 <= rep["cond"] <= kappa * (1 + 1e-6) and rep["cond"] >= kappa / 100, (rep["cond"], kappa)
+    ps, reps = pm.fit_batched([pm.Model("f_wall_time", OVL)], [design(150, 83, nf=5)],
+                              [synth(OVL, design(150, 83, nf=5), P_OVL, 1e-3, 84)[0]], threads=128)
+    assert np.isfinite(reps[0]["cond"]) and reps[0]["cond"] >= 1.0
+    expr = ("p_f * f_op_float32_madd + p_g * f_mem_access_global_float32 + p_s * f_mem_access_local_float32 + "
+            "p_l * f_thread_groups")
+    mm = pm.Model("f_wall_time", expr)
+    Xm = np.array([mm.feature_values("mm_pf", n=n) for n in (256, 384, 512, 640, 768)])
+    tm = np.array([1e-12 * n ** 3 + 3e-10 * n ** 2 for n in (256, 384, 512, 640, 768)])
+    _, reps = pm.fit_batched([mm], [Xm], [tm])
+    assert reps[0]["status"] == -5 and reps[0]["cond"] == float("inf")
