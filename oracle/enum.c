@@ -1217,6 +1217,91 @@ static int setup_fdb(ctx *c) {
 }
 
 /* ======================================================================
+ * DG tile (GB300 form of the DG derivative): P = {Np, Nel}.  The product
+ * res[m, k, i] = sum_j D[m, i, j] u[k, j] as one matrix product over 128
+ * elements per work-group: 16 x 16 work-group, grid ceil(Nel / 128).
+ * Columns (m, i) are laid out c = m NPP + i with NPP = 16 ceil(Np / 16)
+ * (each m block padded to a multiple of 16; W = 3 NPP columns).
+ *  - D staging: for m < 3, column block ib, row block jb: work-item
+ *    (lid0, lid1) handles i = lid1 + 16 ib, j = lid0 + 16 jb (j < Np): it
+ *    loads D[m, i, j] and stores it to Dt[j][c] (row pitch W + 1) when
+ *    i < Np, and stores 0 there when i >= Np;
+ *  - u tile: work-item (0,0) copies the tile's rows (k0 .. k0 + rows - 1,
+ *    rows = min(128, Nel - k0)) element by element (one bulk copy);
+ *  - one barrier;
+ *  - for every j < Np: each work-item loads Us[lid1 + 16 a][j] (a < 8) and
+ *    Dt[j][lid0 + 16 b] (b < 3 NPP / 16) and does 8 x 3 NPP / 16 madds;
+ *  - it stores res[m, k0 + lid1 + 16 a, lid0 + 16 ib] for k < Nel, i < Np.
+ * ====================================================================== */
+#define DT_NB(c) (cdiv((c)->P[0], 16))
+#define DT_W(c) (48 * DT_NB(c))
+static long long ix_dt_D(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; long long Np = c->P[0]; return lv[0] * Np * Np + (L1_ + 16 * lv[1]) * Np + L0_ + 16 * lv[2];
+}
+static long long ix_dt_Dt(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; return (L0_ + 16 * lv[2]) * (DT_W(c) + 1) + lv[0] * 16 * DT_NB(c) + L1_ + 16 * lv[1];
+}
+static long long ix_dt_u(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)l; return 128 * c->P[0] * G0 + lv[0];
+}
+static long long ix_dt_Us(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; return (L1_ + 16 * lv[1]) * c->P[0] + lv[0];
+}
+static long long ix_dt_Dl(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; return lv[0] * (DT_W(c) + 1) + L0_ + 16 * lv[1];
+}
+static long long ix_dt_res(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long Np = c->P[0], Nel = c->P[1];
+    return lv[0] * Nel * Np + (128 * G0 + L1_ + 16 * lv[2]) * Np + L0_ + 16 * lv[1];
+}
+static void walk_dgt(ctx *c) {
+    long long Np = c->P[0], Nel = c->P[1], NB = DT_NB(c), lv[3];
+    long long k0 = 128 * c->g[0], rows = Nel - k0 < 128 ? Nel - k0 : 128;
+    for (lv[0] = 0; lv[0] < 3; lv[0]++)
+        for (lv[1] = 0; lv[1] < NB; lv[1]++)
+            for (lv[2] = 0; lv[2] < NB; lv[2]++) {
+                if (c->l[0] + 16 * lv[2] >= Np) continue;
+                X(c, c->l[1] + 16 * lv[1] < Np ? 0 : 1, lv);
+            }
+    if (c->l[0] == 0 && c->l[1] == 0)
+        for (lv[0] = 0; lv[0] < rows * Np; lv[0]++) X(c, 2, lv);
+    BAR(c);
+    for (lv[0] = 0; lv[0] < Np; lv[0]++) {
+        for (lv[1] = 0; lv[1] < 8; lv[1]++) X(c, 3, lv);
+        for (lv[1] = 0; lv[1] < 3 * NB; lv[1]++) X(c, 4, lv);
+        for (lv[1] = 0; lv[1] < 8; lv[1]++)
+            for (lv[2] = 0; lv[2] < 3 * NB; lv[2]++) X(c, 5, lv);
+    }
+    for (lv[0] = 0; lv[0] < 3; lv[0]++)
+        for (lv[1] = 0; lv[1] < NB; lv[1]++)
+            for (lv[2] = 0; lv[2] < 8; lv[2]++)
+                if (k0 + c->l[1] + 16 * lv[2] < Nel && c->l[0] + 16 * lv[1] < Np) X(c, 6, lv);
+}
+static int setup_dgt(ctx *c) {
+    long long Np = c->P[0], Nel = c->P[1];
+    if (Np < 1 || Np > 96 || Nel < 4 || Nel % 4) return -1;
+    c->grid[0] = cdiv(Nel, 128); c->grid[1] = 1; c->grid[2] = 1;
+    c->wg[0] = 16; c->wg[1] = 16; c->wg[2] = 1;
+    int sDt = add_site(c, "dgt-Dt", MEM_LOCAL, DIR_STORE, "float32", 4, ix_dt_Dt);
+    int s0 = add_stmt(c, 3, DT_F32, 0, 0, 0);
+    stmt_site(c, s0, add_site(c, "dgt-D", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dt_D));
+    stmt_site(c, s0, sDt);
+    int s1 = add_stmt(c, 3, DT_F32, 0, 0, 0);
+    stmt_site(c, s1, sDt);
+    int s2 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+    stmt_site(c, s2, add_site(c, "dgt-u", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dt_u));
+    int s3 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+    stmt_site(c, s3, add_site(c, "dgt-Us", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_dt_Us));
+    int s4 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+    stmt_site(c, s4, add_site(c, "dgt-Dl", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_dt_Dl));
+    add_stmt(c, 3, DT_F32, 0, 0, 1);
+    int s6 = add_stmt(c, 3, DT_F32, 0, 0, 0);
+    stmt_site(c, s6, add_site(c, "dgt-res", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dt_res));
+    c->walk = walk_dgt;
+    return 0;
+}
+
+/* ======================================================================
  * Public oracle entry: enumerate every (group, sub-group, lane) point.
  * ====================================================================== */
 typedef struct {
@@ -1290,6 +1375,7 @@ static const struct { const char *name; int fam, v; } KTAB[] = {
     {"fd_block", 11, 0},
     {"smem2d", 12, 0},
     {"mm_tc256", 10, 1},
+    {"dg_tile", 13, 0},
 };
 
 static int counts_impl(const char *kernel, const char *remove, const long long *P, int nP, orec *out, int cap,
@@ -1325,6 +1411,7 @@ static int counts_impl(const char *kernel, const char *remove, const long long *
     case 10: rc = v ? setup_tcw(c) : setup_tc(c); break;
     case 11: rc = setup_fdb(c); break;
     case 12: rc = setup_smem2d(c); break;
+    case 13: rc = setup_dgt(c); break;
     }
     if (rc) { free(c); return -2; }
     if (remove && make_twin(c, remove)) { free(c); return -5; }

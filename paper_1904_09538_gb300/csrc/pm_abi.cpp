@@ -45,6 +45,7 @@ static constexpr double REQ = std::numeric_limits<double>::quiet_NaN();
 #define P_SMEM2D {"R", "T", "G", nullptr}, {REQ, 16, REQ}, {1, 1, 1}
 #define P_TC {"n", "pipe", nullptr}, {REQ, 1}, {1, 1}
 #define P_TCW {"n", nullptr}, {REQ}, {1}
+#define P_DGT {"Np", "Nel", nullptr}, {REQ, REQ}, {1, 1}
 #define P_FDB {"n", "BX", "BY", "c0", "c1", "V", nullptr}, {REQ, 64, 8, -4.0, 1.0, 4}, {1, 1, 1, 0, 0, 1}
 
 static const KernelDef KDEFS[] = {
@@ -86,6 +87,7 @@ static const KernelDef KDEFS[] = {
     {"dg_dmpft_res", FAM_DG, 11, P_DG},
     {"smem2d", FAM_SMEM2D, 0, P_SMEM2D},
     {"mm_tc256", FAM_TC, 1, P_TCW},
+    {"dg_tile", FAM_DGT, 0, P_DGT},
 };
 
 const KernelDef *kernel_def(int32_t id) {

@@ -661,6 +661,54 @@ pm_status counts_fdb(const KP &kp, std::vector<pm_feature> &v) {
     return PM_OK;
 }
 
+// ---------------------------------------------------------------- DG tile
+// 16 x 16 work-group per 128 elements; columns (m, i) at c = m NPP + i with
+// NPP = 16 NB, NB = ceil(Np / 16), W = 3 NPP.  Work-item (x, y) stages
+// D[m, y + 16 ib, x + 16 jb] into Dt[j][c] (zero for the padding rows
+// i >= Np), work-item (0, 0) copies the u tile (one bulk copy, counted per
+// element), one barrier, then per j: 8 loads of Us[y + 16 a][j], 3 NB loads
+// of Dt[j][x + 16 b], 8 x 3 NB madds; stores res[m, k0 + y + 16 a, x + 16 ib].
+// A sub-group is lanes (x, y) with y in {2 w, 2 w + 1}.
+pm_status counts_dgt(const KP &kp, std::vector<pm_feature> &v) {
+    const i64 Np = kp.i(0), Nel = kp.i(1), NB = cdiv(Np, 16), W = 48 * NB;
+    const i64 G = cdiv(Nel, 128), Gfull = Nel / 128, rlast = Nel % 128;
+    const u64 WI = (u64)G * 256, SG = (u64)G * 8;
+    Out o(v);
+    o.op(0, 2, WI * (u64)(24 * NB * Np), SG * (u64)(24 * NB * Np));
+    // sub-groups with some row y + 16 ib below / at or above Np, per column block
+    u64 sg_in = 0, sg_pad = 0;
+    for (i64 ib = 0; ib < NB; ib++)
+        for (i64 w = 0; w < 8; w++) {
+            sg_in += (2 * w + 16 * ib < Np);
+            sg_pad += (2 * w + 1 + 16 * ib >= Np);
+        }
+    // sub-groups storing results at row step a of a tile with r rows
+    auto sg_rows = [](i64 r) {
+        u64 n = 0;
+        for (i64 a = 0; a < 8; a++)
+            for (i64 w = 0; w < 8; w++) n += (2 * w + 16 * a < r);
+        return n;
+    };
+    auto site = [&](const char *tag, int mem, int dir, i64 l0, i64 l1, i64 g0, i64 loop, u64 wi, u64 sg, u64 foot) {
+        Site x{};
+        x.tag = tag; x.mem = mem; x.dir = dir; x.dtype = "float32"; x.dsize = 4;
+        x.nl = 2; x.l[0] = l0; x.l[1] = l1; x.ng = 1; x.g[0] = g0; x.loop = loop;
+        x.wi = wi; x.sg = sg; x.foot = foot;
+        o.site(x);
+    };
+    const u64 uG = (u64)G, uNp = (u64)Np;
+    site("dgt-D", GL, LD, 1, Np, 0, 16, uG * 3 * uNp * uNp, uG * 3 * (u64)NB * sg_in, 3 * uNp * uNp);
+    site("dgt-Dt", LO, ST, W + 1, 1, 0, 16 * (W + 1), uG * 3 * (u64)(16 * NB) * uNp,
+         uG * 3 * (u64)NB * (sg_in + sg_pad), (u64)W * uNp);
+    site("dgt-u", GL, LD, 0, 0, 128 * Np, 1, (u64)Nel * uNp, (u64)Nel * uNp, (u64)Nel * uNp);
+    site("dgt-Us", LO, LD, 0, Np, 0, 16 * Np, WI * 8 * uNp, SG * 8 * uNp, 128 * uNp);
+    site("dgt-Dl", LO, LD, 1, 0, 0, 16, WI * 3 * (u64)NB * uNp, SG * 3 * (u64)NB * uNp, (u64)W * uNp);
+    site("dgt-res", GL, ST, 1, Np, 128 * Np, 16 * Np, 3 * (u64)Nel * uNp,
+         3 * (u64)NB * ((u64)Gfull * 64 + (rlast ? sg_rows(rlast) : 0)), 3 * (u64)Nel * uNp);
+    o.finish(1, uG);
+    return PM_OK;
+}
+
 bool pow2(i64 x) { return x > 0 && (x & (x - 1)) == 0; }
 
 }  // namespace
@@ -736,6 +784,11 @@ pm_status validate(const KP &kp) {
     case FAM_FD:
         if (kp.i(0) < 1 || kp.i(0) > 46000) return fail(PM_EINVAL, "%s: n must be 1..46000", nm);
         return PM_OK;
+    case FAM_DGT:
+        if (kp.i(0) < 1 || kp.i(0) > 96) return fail(PM_EINVAL, "%s: Np must be 1..96", nm);
+        if (kp.i(1) < 4 || kp.i(1) % 4 || kp.i(1) > (1LL << 24))
+            return fail(PM_EINVAL, "%s: Nel must be a positive multiple of 4 (<= 2^24)", nm);
+        return PM_OK;
     case FAM_FDB: {
         i64 n = kp.i(0), BX = kp.i(1), BY = kp.i(2);
         if (BX != 32 && BX != 64 && BX != 128) return fail(PM_EINVAL, "%s: BX must be 32, 64 or 128", nm);
@@ -783,6 +836,7 @@ pm_status counts(const KP &kp, std::vector<pm_feature> &out) {
     case FAM_SIMT: return counts_simt(kp, out);
     case FAM_TC: return counts_tc(kp, out);
     case FAM_FDB: return counts_fdb(kp, out);
+    case FAM_DGT: return counts_dgt(kp, out);
     }
     return fail(PM_EINVAL, "unknown family");
 }
@@ -849,6 +903,13 @@ pm_status buffers(const KP &kp, std::vector<BufSpec> &b) {
         } else {
             b.push_back({"res", PM_F32, PM_OUT, 3 * Nel * Np});
         }
+        break;
+    }
+    case FAM_DGT: {
+        uint64_t Np = (uint64_t)kp.i(0), Nel = (uint64_t)kp.i(1);
+        b.push_back({"diff_mat", PM_F32, PM_IN, 3 * Np * Np});
+        b.push_back({"u", PM_F32, PM_IN, Nel * Np});
+        b.push_back({"res", PM_F32, PM_OUT, 3 * Nel * Np});
         break;
     }
     case FAM_FDB: {

@@ -37,7 +37,7 @@ void set_fail_allocation(int n);
 
 // ---- kernel registry ------------------------------------------------------
 enum Family { FAM_STREAM, FAM_FMA, FAM_SMEM, FAM_BARRIER, FAM_OVERLAP, FAM_EMPTY, FAM_MM, FAM_DG, FAM_FD, FAM_SIMT, FAM_TC, FAM_FDB,
-              FAM_SMEM2D };
+              FAM_SMEM2D, FAM_DGT };
 
 constexpr int kMaxParams = 8;
 
@@ -103,6 +103,7 @@ pm_status launch_tiles(const KP &kp, void *const *bufs, void *stream);
 pm_status launch_tc(const KP &kp, void *const *bufs, void *stream);
 pm_status tc_check_timeout();
 pm_status fdb_check_timeout();
+pm_status dgt_check_timeout();
 // 2-D tensor map (TMA descriptor) over a row-major matrix; `map` must point
 // to a CUtensorMap (64-byte aligned, 128 bytes).
 pm_status tensor_map_2d(struct CUtensorMap_st *map, int bf16, const void *ptr, uint64_t cols, uint64_t rows,

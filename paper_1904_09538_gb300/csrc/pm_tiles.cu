@@ -206,7 +206,118 @@ pm_status launch_fdb_v(int BX, int BY, void *const *b, int n, float c0, float c1
     }
 }
 
+// ---------------------------------------------------------------- DG tile
+// res[m, k, i] = sum_j D[m, i, j] u[k, j] for 128 elements k per CTA, as one
+// product C (128 x 3 NPP) = U (128 x Np) Dt, the m blocks of Dt padded to
+// NPP = 16 NB columns (zero rows of D beyond Np).  CTA 16 x 16: thread
+// (x, y) accumulates rows y + 16 a (a < 8) and columns x + 16 b (b < 3 NB)
+// in registers.  The u tile (contiguous, rows x Np floats) arrives by one
+// bulk copy on the TMA engine while the threads stage D transposed into
+// shared memory (row pitch W + 1: conflict-free stores and loads); one
+// barrier; the mbarrier wait is bounded (error word, no stores on timeout).
+static __device__ int g_dgt_timeout;
+
+template <int NB>
+constexpr size_t dgt_smem(int Np) {
+    return 16 + (size_t)128 * Np * 4 + (((size_t)Np * (48 * NB + 1) + 1) & ~(size_t)1) * 4 + 8;
+}
+
+template <int NB>
+__global__ void __launch_bounds__(256, NB <= 2 ? 3 : 1) k_dg_tile(const float *__restrict__ D, const float *__restrict__ u,
+                                                 float *__restrict__ res, int Np, int Nel) {
+    constexpr int W = 48 * NB, NC = 3 * NB;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    float *Us = reinterpret_cast<float *>((((uintptr_t)smem_raw + 15) & ~(uintptr_t)15));
+    float *Dt = Us + 128 * Np;
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Dt + (((size_t)Np * (W + 1) + 1) & ~(size_t)1));
+    const int x = threadIdx.x, y = threadIdx.y;
+    const bool leader = x == 0 && y == 0;
+    const long long k0 = 128LL * blockIdx.x;
+    const int rows = (int)min(128LL, (long long)Nel - k0);
+    if (leader) {
+        mbar_init(bar, 1);
+        mbar_init_fence();
+        const uint32_t bytes = (uint32_t)rows * (uint32_t)Np * 4u;
+        mbar_expect_tx(bar, bytes);
+        bulk_load(Us, u + k0 * Np, bytes, bar);
+    }
+    // all of a thread's D loads of one m block in flight before its stores
+#pragma unroll
+    for (int m = 0; m < 3; m++) {
+        float dv[NB][NB];
+#pragma unroll
+        for (int ib = 0; ib < NB; ib++)
+#pragma unroll
+            for (int jb = 0; jb < NB; jb++) {
+                const int i = y + 16 * ib, j = x + 16 * jb;
+                dv[ib][jb] = (i < Np && j < Np) ? __ldg(D + (m * Np + i) * Np + j) : 0.0f;
+            }
+#pragma unroll
+        for (int ib = 0; ib < NB; ib++)
+#pragma unroll
+            for (int jb = 0; jb < NB; jb++) {
+                const int j = x + 16 * jb;
+                if (j < Np) Dt[j * (W + 1) + m * 16 * NB + y + 16 * ib] = dv[ib][jb];
+            }
+    }
+    __syncthreads();
+    const bool ok = mbar_wait_bounded(bar, 0, &g_dgt_timeout, 1ll << 26);
+    if (!ok && leader) mbar_wait_bounded(bar, 0, &g_dgt_timeout, 1ll << 26);   // drain our own copy
+    if (!ok) return;
+    float acc[8][NC];
+#pragma unroll
+    for (int a = 0; a < 8; a++)
+#pragma unroll
+        for (int b = 0; b < NC; b++) acc[a][b] = 0.0f;
+    const float *ur = Us + y * Np;
+    const float *dr = Dt + x;
+#pragma unroll 2
+    for (int j = 0; j < Np; j++) {
+        float av[8], bv[NC];
+#pragma unroll
+        for (int a = 0; a < 8; a++) av[a] = ur[16 * a * Np + j];
+#pragma unroll
+        for (int b = 0; b < NC; b++) bv[b] = dr[j * (W + 1) + 16 * b];
+#pragma unroll
+        for (int a = 0; a < 8; a++)
+#pragma unroll
+            for (int b = 0; b < NC; b++) acc[a][b] = __fmaf_rn(av[a], bv[b], acc[a][b]);
+    }
+#pragma unroll
+    for (int m = 0; m < 3; m++)
+#pragma unroll
+        for (int ib = 0; ib < NB; ib++) {
+            const int i = x + 16 * ib;
+            if (i >= Np) continue;
+#pragma unroll
+            for (int a = 0; a < 8; a++) {
+                const long long k = k0 + y + 16 * a;
+                if (k < Nel) res[((long long)m * Nel + k) * Np + i] = acc[a][m * NB + ib];
+            }
+        }
+}
+
+template <int NB>
+pm_status launch_dgt_t(void *const *b, int Np, int Nel, cudaStream_t st) {
+    const size_t smem = dgt_smem<NB>(Np);
+    PM_CUDA_TRY(cudaFuncSetAttribute(k_dg_tile<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    launch_k(k_dg_tile<NB>, (unsigned)((Nel + 127) / 128), dim3(16, 16), smem, st, (const float *)b[0],
+             (const float *)b[1], (float *)b[2], Np, Nel);
+    PM_CUDA_TRY(cudaGetLastError());
+    return PM_OK;
+}
+
 }  // namespace
+
+pm_status dgt_check_timeout() {
+    int v = 0, z = 0;
+    PM_CUDA_TRY(cudaMemcpyFromSymbol(&v, g_dgt_timeout, sizeof v));
+    if (v) {
+        PM_CUDA_TRY(cudaMemcpyToSymbol(g_dgt_timeout, &z, sizeof z));
+        return fail(PM_ETIMEOUT, "dg_tile: a bounded wait gave up");
+    }
+    return PM_OK;
+}
 
 pm_status fdb_check_timeout() {
     int v = 0, z = 0;
@@ -220,6 +331,18 @@ pm_status fdb_check_timeout() {
 
 pm_status launch_tiles(const KP &kp, void *const *b, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
+    if (kp.def->fam == FAM_DGT) {
+        const int Np = (int)kp.i(0), Nel = (int)kp.i(1);
+        if ((uintptr_t)b[1] % 16) return fail(PM_EINVAL, "dg_tile: u must be 16-byte aligned");
+        switch ((Np + 15) / 16) {
+        case 1: return launch_dgt_t<1>(b, Np, Nel, st);
+        case 2: return launch_dgt_t<2>(b, Np, Nel, st);
+        case 3: return launch_dgt_t<3>(b, Np, Nel, st);
+        case 4: return launch_dgt_t<4>(b, Np, Nel, st);
+        case 5: return launch_dgt_t<5>(b, Np, Nel, st);
+        default: return launch_dgt_t<6>(b, Np, Nel, st);
+        }
+    }
     if (kp.def->fam == FAM_FDB) {
         const int n = (int)kp.i(0), BX = (int)kp.i(1), BY = (int)kp.i(2), V = (int)kp.i(5);
         const float c0 = (float)kp.v[3], c1 = (float)kp.v[4];

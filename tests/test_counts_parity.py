@@ -194,3 +194,9 @@ def test_fd_block(n, BX, BY, V):
 @pytest.mark.parametrize("R,T,G", [(4, 16, 1), (64, 18, 3), (256, 16, 5), (8, 18, 1)])
 def test_smem2d(R, T, G):
     compare("smem2d", R=R, T=T, G=G)
+
+
+@pytest.mark.parametrize("Np,Nel", [(20, 132), (35, 256), (56, 4), (84, 260), (1, 8), (16, 128), (17, 132),
+                                    (96, 136)])
+def test_dg_tile(Np, Nel):
+    compare("dg_tile", Np=Np, Nel=Nel)

@@ -358,3 +358,36 @@ def test_run_host_batch_pipelines_and_orders_aliased_buffers():
     assert np.array_equal(o0, want) and np.array_equal(o1, want)
     assert np.array_equal(o2, refs.stream(y))
     assert len(tms) == 3 and all(t["n_trials"] == 3 and t["mean_ms"] > 0 for t in tms) and copy_ms > 0
+
+
+# DG tile (128 elements per CTA, D staged transposed in shared memory, the
+# u tile by one bulk copy): ragged Np (column padding) and ragged Nel (last
+# tile of 4..124 elements), guard bands checked by run_kernel
+@pytest.mark.parametrize("Np,Nel", [(20, 132), (35, 256), (56, 4), (84, 260), (1, 8), (17, 132), (96, 136),
+                                    (84, 1024), (16, 384)])
+def test_dg_tile(Np, Nel):
+    D, u = pm_inputs.normal((3, Np, Np), 21), pm_inputs.normal((Nel, Np), 22)
+    (res,) = run_kernel("dg_tile", [D, u], Np=Np, Nel=Nel)
+    ref, rabs = refs.dg(D, u)
+    assert cond_err(res.reshape(3, Nel, Np), ref, rabs) <= TOL
+
+
+@pytest.mark.parametrize("Np", [20, 35, 56, 84])
+def test_dg_tile_full_size_sampled_and_timed(Np):
+    Nel = 1 << 18
+    D, u = pm_inputs.normal((3, Np, Np), 41), pm_inputs.normal((Nel, Np), 42)
+    d = dev()
+    res = torch.empty(3 * Nel * Np, device=d)
+    bufs = [torch.from_numpy(D).to(d), torch.from_numpy(u).to(d), res]
+    tm = pm.run("dg_tile", bufs, warmup=2, trials=5, Np=Np, Nel=Nel)
+    ks = np.unique(pm_inputs.integers((512,), 43, 0, Nel - 1))
+    ref, rabs = refs.dg(D, u[ks])
+    got = res.cpu().numpy().reshape(3, Nel, Np)[:, ks, :]
+    assert cond_err(got, ref, rabs) <= TOL and tm["mean_ms"] > 0
+
+
+def test_dg_tile_resources():
+    dev()
+    r = pm.resources("dg_tile", Np=84, Nel=1 << 18)
+    assert r["threads_per_block"] == 256 and r["grid_blocks"] == (1 << 18) // 128 and r["local_bytes_per_thread"] == 0
+    assert r["dynamic_smem_bytes"] >= (128 * 84 + 84 * 289) * 4

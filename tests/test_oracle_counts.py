@@ -370,3 +370,25 @@ def test_tensor_core_closed_forms(kernel, R, n):
     assert c["count_wi"] == c["footprint"] == n * n // 4 and c["lstr"][0] == n // 4
     assert c["count"] == c["count_wi"]   # non-uniform global access: counted per work-item
     assert single(fs, "groups") == (n // 256) * (n // R) and single(fs, "sync") == 3
+
+
+@pytest.mark.parametrize("Np,Nel", [(20, 132), (35, 256), (84, 128), (17, 4)])
+def test_dg_tile_closed_forms(Np, Nel):
+    # the DG product through 128-element tiles: every D element loaded once
+    # per work-group, every u element once (one bulk copy, uniform), every
+    # result stored once; padded columns and rows of a partial tile add
+    # multiply-adds (8 x 3 NB per j per work-item), never stores
+    fs = features("dg_tile", Np=Np, Nel=Nel)
+    G, NB = -(-Nel // 128), -(-Np // 16)
+    assert op(fs, "float32", "madd", wi=True) == G * 256 * 8 * 3 * NB * Np >= 3 * Nel * Np * Np
+    if Np % 16 == 0 and Nel % 128 == 0:
+        assert op(fs, "float32", "madd", wi=True) == 3 * Nel * Np * Np
+    d = by_tag(fs, "dgt-D")
+    assert d["count_wi"] == G * 3 * Np * Np and d["footprint"] == 3 * Np * Np and d["lstr"] == (1, Np)
+    uu = by_tag(fs, "dgt-u")
+    assert uu["count_wi"] == uu["count"] == uu["footprint"] == Nel * Np and uu["lstr"] == (0, 0)
+    r = by_tag(fs, "dgt-res")
+    assert r["count_wi"] == r["footprint"] == 3 * Nel * Np and r["lstr"] == (1, Np) and r["gstr"] == (128 * Np,)
+    assert by_tag(fs, "dgt-Us")["count_wi"] == G * 256 * 8 * Np
+    assert by_tag(fs, "dgt-Dl")["count_wi"] == G * 256 * 3 * NB * Np
+    assert single(fs, "sync") == 1 and single(fs, "groups") == G
