@@ -75,7 +75,10 @@ typedef struct {
  * the counts describe the decomposition into 128 x 256 tiles and do not
  * depend on pipe) and its 256 x 256-tile form "mm_tc256" (parameter n, a
  * multiple of 256: 256-thread work-groups, two 128-row accumulators in 512
- * TMEM columns sharing each Bt box, 3-stage ring, one CTA per SM); the TMA-staged
+ * TMEM columns sharing each Bt box, 3-stage ring, one CTA per SM); the DG
+ * tile form "dg_tile" (parameters Np <= 96 and Nel, a multiple of 4; buffers
+ * diff_mat, u, res as for dg_nopf; 16 x 16 work-groups of 128 elements, D
+ * staged transposed in shared memory, u tiles by one bulk TMA copy); the TMA-staged
  * stencil tile family "fd_block" (parameters n, BX, BY, c0, c1, V = 4 or 8
  * outputs per work-item; input u of (n + 2) rows with row pitch n + 4).
  * Returns PM_EUNKNOWN_KERNEL for other names. */
