@@ -122,10 +122,10 @@ def studies():
 
 
 def sweep_studies():
-    """The cross-variant sweep: 9 modeled variants (prefetching fp32 matmul,
+    """The cross-variant sweep: 10 modeled variants (prefetching fp32 matmul,
     BF16 tensor-core matmul with 128 x 256 and 256 x 256 tiles, DG noPF /
-    uPF / dmPF / dmPF-T with 16x16 work-groups, stencil 16x16 tile and
-    direct) at ~30 sizes each.  Every third size is held out; each variant's
+    uPF / dmPF / dmPF-T with 16x16 work-groups and the DG tile form, stencil
+    16x16 tile and direct) at ~30 sizes each.  Every third size is held out; each variant's
     model is calibrated on the microbenchmarks (plus its computation's twins)
     and the variant's own other sizes -- the paper's "few extra on-line
     calibration runs" -- and predicts the held-out sizes.  A tenth study
@@ -143,6 +143,7 @@ def sweep_studies():
     plan = [("mm_pf", "matmul", None, [{"n": n} for n in range(512, 4096 + 1, 128)]),
             ("mm_tc", None, tc_expr, tc_sizes), ("mm_tc256", None, tc_expr, tc_sizes)]
     plan += [(k, "dg_16x16", None, dg_sizes) for k in ("dg_nopf", "dg_upf", "dg_dmpf", "dg_dmpft")]
+    plan += [("dg_tile", "dg_16x16", None, [dict(Np=Np, Nel=Nel) for Np in (20, 35, 56, 84) for Nel in nels])]
     plan += [(k, "fd", None, [{"n": int(round(1024 * 2 ** (i / 7.0)))} for i in range(29)])
              for k in ("fd_tile", "fd_direct")]
     out = []
