@@ -89,7 +89,7 @@ for _k in ("fd_tile", "fd_direct", "fd_tile_u", "fd_tile_res", "fd_direct_u", "f
 KERNELS["mm_simt"] = (("n", "BM", "BN", "BK"), (2, 2))
 KERNELS["mm_tc"] = (("n",), (1, 2))
 KERNELS["mm_tc256"] = (("n",), (1, 2))
-KERNELS["dg_tile"] = (("Np", "Nel"), (2, 1))
+KERNELS["dg_tile"] = (("Np", "Nel"), (2, 2))
 KERNELS["fd_block"] = (("n", "BX", "BY", "V"), (2, 2))
 KERNELS["smem2d"] = (("R", "T", "G"), (2, 1))
 

@@ -1217,86 +1217,122 @@ static int setup_fdb(ctx *c) {
 }
 
 /* ======================================================================
- * DG tile (GB300 form of the DG derivative): P = {Np, Nel}.  The product
- * res[m, k, i] = sum_j D[m, i, j] u[k, j] as one matrix product over 128
- * elements per work-group: 16 x 16 work-group, grid ceil(Nel / 128).
- * Columns (m, i) are laid out c = m NPP + i with NPP = 16 ceil(Np / 16)
- * (each m block padded to a multiple of 16; W = 3 NPP columns).
- *  - D staging: for m < 3, column block ib, row block jb: work-item
- *    (lid0, lid1) handles i = lid1 + 16 ib, j = lid0 + 16 jb (j < Np): it
- *    loads D[m, i, j] and stores it to Dt[j][c] (row pitch W + 1) when
- *    i < Np, and stores 0 there when i >= Np;
- *  - u tile: work-item (0,0) copies the tile's rows (k0 .. k0 + rows - 1,
- *    rows = min(128, Nel - k0)) element by element (one bulk copy);
- *  - one barrier;
- *  - for every j < Np: each work-item loads Us[lid1 + 16 a][j] (a < 8) and
- *    Dt[j][lid0 + 16 b] (b < 3 NPP / 16) and does 8 x 3 NPP / 16 madds;
- *  - it stores res[m, k0 + lid1 + 16 a, lid0 + 16 ib] for k < Nel, i < Np.
+ * DG tile (GB300 form of the DG derivative): P = {Np, Nel}.  For one m
+ * (gid0 < 3) and 128 elements (gid1): res[m, k, i] = sum_j D[m, i, j]
+ * u[k, j] as one matrix product; 16 x 16 work-group, grid (3, ceil(Nel /
+ * 128)).  Rows i are padded to NPP = 16 NB (NB = ceil(Np / 16)) with zeros,
+ * j runs over Q = ceil(Np / 4) chunks of four (16-byte vectors), zero beyond
+ * Np; Dt row pitch PD floats (PD >= 4 Q, PD % 32 == 4).
+ *  - D staging: for row block ib < NB and chunk block qb: work-item
+ *    (lid0, lid1) handles i = lid1 + 16 ib and chunk q = lid0 + 16 qb < Q;
+ *    for i < Np it loads D[m, i, 4q .. 4q+3] (one 16-byte vector when
+ *    Np % 4 == 0, else the j < Np elements one by one); it stores the chunk
+ *    to Dt[i][q] (one 16-byte vector);
+ *  - u tile: work-item (0,0) copies the tile's rows (one bulk copy, counted
+ *    per element); one barrier; when Np % 4 != 0 every work-item then
+ *    re-lays the 128 rows out with pitch 4 Q (row r = lid1 + 16 rb, chunk
+ *    q = lid0 + 16 qb < Q: element loads j < Np, one vector store) and a
+ *    second barrier follows;
+ *  - for every chunk q < Q: vector loads Us[lid1 + 16 a][q] (a < 8) and
+ *    Dt[lid0 + 16 b][q] (b < NB), 4 x 8 x NB madds;
+ *  - stores res[m, k0 + lid1 + 16 a, lid0 + 16 b] for k < Nel, i < Np.
  * ====================================================================== */
 #define DT_NB(c) (cdiv((c)->P[0], 16))
-#define DT_W(c) (48 * DT_NB(c))
+#define DT_Q(c) (cdiv((c)->P[0], 4))
+static long long dt_pd(const ctx *c) { long long p = 4 * DT_Q(c); while (p % 32 != 4) p++; return p; }
 static long long ix_dt_D(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)g; long long Np = c->P[0]; return lv[0] * Np * Np + (L1_ + 16 * lv[1]) * Np + L0_ + 16 * lv[2];
+    long long Np = c->P[0];
+    return G0 * Np * Np + (L1_ + 16 * lv[0]) * Np + 4 * (L0_ + 16 * lv[1]) + lv[2];
+}
+static long long ix_dt_D4(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long Np = c->P[0];
+    return (G0 * Np * Np + (L1_ + 16 * lv[0]) * Np) / 4 + L0_ + 16 * lv[1];
 }
 static long long ix_dt_Dt(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)g; return (L0_ + 16 * lv[2]) * (DT_W(c) + 1) + lv[0] * 16 * DT_NB(c) + L1_ + 16 * lv[1];
+    (void)g; return (L1_ + 16 * lv[0]) * (dt_pd(c) / 4) + L0_ + 16 * lv[1];
 }
 static long long ix_dt_u(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)l; return 128 * c->P[0] * G0 + lv[0];
+    (void)l; return 128 * c->P[0] * G1 + lv[0];
+}
+static long long ix_dt_R(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; return (L1_ + 16 * lv[0]) * c->P[0] + 4 * (L0_ + 16 * lv[1]) + lv[2];
+}
+static long long ix_dt_Ur(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; return (L1_ + 16 * lv[0]) * DT_Q(c) + L0_ + 16 * lv[1];
 }
 static long long ix_dt_Us(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)g; return (L1_ + 16 * lv[1]) * c->P[0] + lv[0];
+    (void)g; return (L1_ + 16 * lv[1]) * DT_Q(c) + lv[0];
 }
 static long long ix_dt_Dl(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)g; return lv[0] * (DT_W(c) + 1) + L0_ + 16 * lv[1];
+    (void)g; return (L0_ + 16 * lv[1]) * (dt_pd(c) / 4) + lv[0];
 }
 static long long ix_dt_res(const ctx *c, const long long *g, const long long *l, const long long *lv) {
     long long Np = c->P[0], Nel = c->P[1];
-    return lv[0] * Nel * Np + (128 * G0 + L1_ + 16 * lv[2]) * Np + L0_ + 16 * lv[1];
+    return G0 * Nel * Np + (128 * G1 + L1_ + 16 * lv[1]) * Np + L0_ + 16 * lv[0];
 }
+/* statements: 0 D vector load, 1 D element load, 2 Dt store, 3 u copy,
+ * 4 raw-row element load, 5 re-laid row store, 6 Us load, 7 Dt load,
+ * 8 madd, 9 res store */
 static void walk_dgt(ctx *c) {
-    long long Np = c->P[0], Nel = c->P[1], NB = DT_NB(c), lv[3];
-    long long k0 = 128 * c->g[0], rows = Nel - k0 < 128 ? Nel - k0 : 128;
-    for (lv[0] = 0; lv[0] < 3; lv[0]++)
-        for (lv[1] = 0; lv[1] < NB; lv[1]++)
-            for (lv[2] = 0; lv[2] < NB; lv[2]++) {
-                if (c->l[0] + 16 * lv[2] >= Np) continue;
-                X(c, c->l[1] + 16 * lv[1] < Np ? 0 : 1, lv);
+    long long Np = c->P[0], Nel = c->P[1], NB = DT_NB(c), Q = DT_Q(c), lv[3];
+    long long k0 = 128 * c->g[1], rows = Nel - k0 < 128 ? Nel - k0 : 128;
+    for (lv[0] = 0; lv[0] < NB; lv[0]++)
+        for (lv[1] = 0; lv[1] < cdiv(Q, 16); lv[1]++) {
+            long long q = c->l[0] + 16 * lv[1], i = c->l[1] + 16 * lv[0];
+            if (q >= Q) continue;
+            if (i < Np) {
+                if (Np % 4 == 0) { lv[2] = 0; X(c, 0, lv); }
+                else for (lv[2] = 0; lv[2] < 4; lv[2]++) if (4 * q + lv[2] < Np) X(c, 1, lv);
             }
+            X(c, 2, lv);
+        }
     if (c->l[0] == 0 && c->l[1] == 0)
-        for (lv[0] = 0; lv[0] < rows * Np; lv[0]++) X(c, 2, lv);
+        for (lv[0] = 0; lv[0] < rows * Np; lv[0]++) X(c, 3, lv);
     BAR(c);
-    for (lv[0] = 0; lv[0] < Np; lv[0]++) {
-        for (lv[1] = 0; lv[1] < 8; lv[1]++) X(c, 3, lv);
-        for (lv[1] = 0; lv[1] < 3 * NB; lv[1]++) X(c, 4, lv);
-        for (lv[1] = 0; lv[1] < 8; lv[1]++)
-            for (lv[2] = 0; lv[2] < 3 * NB; lv[2]++) X(c, 5, lv);
+    if (Np % 4) {
+        for (lv[0] = 0; lv[0] < 8; lv[0]++)
+            for (lv[1] = 0; lv[1] < cdiv(Q, 16); lv[1]++) {
+                long long q = c->l[0] + 16 * lv[1];
+                if (q >= Q) continue;
+                for (lv[2] = 0; lv[2] < 4; lv[2]++) if (4 * q + lv[2] < Np) X(c, 4, lv);
+                X(c, 5, lv);
+            }
+        BAR(c);
     }
-    for (lv[0] = 0; lv[0] < 3; lv[0]++)
-        for (lv[1] = 0; lv[1] < NB; lv[1]++)
-            for (lv[2] = 0; lv[2] < 8; lv[2]++)
-                if (k0 + c->l[1] + 16 * lv[2] < Nel && c->l[0] + 16 * lv[1] < Np) X(c, 6, lv);
+    for (lv[0] = 0; lv[0] < Q; lv[0]++) {
+        for (lv[1] = 0; lv[1] < 8; lv[1]++) X(c, 6, lv);
+        for (lv[1] = 0; lv[1] < NB; lv[1]++) X(c, 7, lv);
+        for (lv[1] = 0; lv[1] < 8; lv[1]++)
+            for (lv[2] = 0; lv[2] < NB; lv[2]++) X(c, 8, lv);
+    }
+    for (lv[0] = 0; lv[0] < NB; lv[0]++)
+        for (lv[1] = 0; lv[1] < 8; lv[1]++)
+            if (k0 + c->l[1] + 16 * lv[1] < Nel && c->l[0] + 16 * lv[0] < Np) X(c, 9, lv);
 }
 static int setup_dgt(ctx *c) {
     long long Np = c->P[0], Nel = c->P[1];
-    if (Np < 1 || Np > 96 || Nel < 4 || Nel % 4) return -1;
-    c->grid[0] = cdiv(Nel, 128); c->grid[1] = 1; c->grid[2] = 1;
+    if (Np < 1 || Np > 96 || Nel < 4 || Nel % 4 || Nel > 65535LL * 128) return -1;
+    c->grid[0] = 3; c->grid[1] = cdiv(Nel, 128); c->grid[2] = 1;
     c->wg[0] = 16; c->wg[1] = 16; c->wg[2] = 1;
-    int sDt = add_site(c, "dgt-Dt", MEM_LOCAL, DIR_STORE, "float32", 4, ix_dt_Dt);
-    int s0 = add_stmt(c, 3, DT_F32, 0, 0, 0);
-    stmt_site(c, s0, add_site(c, "dgt-D", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dt_D));
-    stmt_site(c, s0, sDt);
+    int s0 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+    stmt_site(c, s0, add_site(c, "dgt-D", MEM_GLOBAL, DIR_LOAD, "float32x4", 16, ix_dt_D4));
     int s1 = add_stmt(c, 3, DT_F32, 0, 0, 0);
-    stmt_site(c, s1, sDt);
-    int s2 = add_stmt(c, 1, DT_F32, 0, 0, 0);
-    stmt_site(c, s2, add_site(c, "dgt-u", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dt_u));
-    int s3 = add_stmt(c, 2, DT_F32, 0, 0, 0);
-    stmt_site(c, s3, add_site(c, "dgt-Us", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_dt_Us));
-    int s4 = add_stmt(c, 2, DT_F32, 0, 0, 0);
-    stmt_site(c, s4, add_site(c, "dgt-Dl", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_dt_Dl));
-    add_stmt(c, 3, DT_F32, 0, 0, 1);
-    int s6 = add_stmt(c, 3, DT_F32, 0, 0, 0);
-    stmt_site(c, s6, add_site(c, "dgt-res", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dt_res));
+    stmt_site(c, s1, add_site(c, "dgt-D", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dt_D));
+    int s2 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+    stmt_site(c, s2, add_site(c, "dgt-Dt", MEM_LOCAL, DIR_STORE, "float32x4", 16, ix_dt_Dt));
+    int s3 = add_stmt(c, 1, DT_F32, 0, 0, 0);
+    stmt_site(c, s3, add_site(c, "dgt-u", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dt_u));
+    int s4 = add_stmt(c, 3, DT_F32, 0, 0, 0);
+    stmt_site(c, s4, add_site(c, "dgt-R", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_dt_R));
+    int s5 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+    stmt_site(c, s5, add_site(c, "dgt-Ur", MEM_LOCAL, DIR_STORE, "float32x4", 16, ix_dt_Ur));
+    int s6 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+    stmt_site(c, s6, add_site(c, "dgt-Us", MEM_LOCAL, DIR_LOAD, "float32x4", 16, ix_dt_Us));
+    int s7 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+    stmt_site(c, s7, add_site(c, "dgt-Dl", MEM_LOCAL, DIR_LOAD, "float32x4", 16, ix_dt_Dl));
+    add_stmt(c, 3, DT_F32, 0, 0, 4);
+    int s9 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+    stmt_site(c, s9, add_site(c, "dgt-res", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dt_res));
     c->walk = walk_dgt;
     return 0;
 }

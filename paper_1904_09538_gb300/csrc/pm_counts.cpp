@@ -662,50 +662,64 @@ pm_status counts_fdb(const KP &kp, std::vector<pm_feature> &v) {
 }
 
 // ---------------------------------------------------------------- DG tile
-// 16 x 16 work-group per 128 elements; columns (m, i) at c = m NPP + i with
-// NPP = 16 NB, NB = ceil(Np / 16), W = 3 NPP.  Work-item (x, y) stages
-// D[m, y + 16 ib, x + 16 jb] into Dt[j][c] (zero for the padding rows
-// i >= Np), work-item (0, 0) copies the u tile (one bulk copy, counted per
-// element), one barrier, then per j: 8 loads of Us[y + 16 a][j], 3 NB loads
-// of Dt[j][x + 16 b], 8 x 3 NB madds; stores res[m, k0 + y + 16 a, x + 16 ib].
-// A sub-group is lanes (x, y) with y in {2 w, 2 w + 1}.
+// 16 x 16 work-group per (m, 128 elements), grid (3, ceil(Nel / 128)); rows
+// i padded to NPP = 16 NB (NB = ceil(Np / 16)), j in Q = ceil(Np / 4)
+// chunks of four (16-byte vectors), Dt row pitch PD (PD >= 4 Q, PD % 32 ==
+// 4).  Work-item (x, y): D staging for row i = y + 16 ib and chunk
+// q = x + 16 qb < Q -- a vector load of D[m, i, 4q ..] when Np % 4 == 0
+// (else the j < Np elements one by one) for i < Np, a vector store to
+// Dt[i][q]; work-item (0, 0) copies the u tile (one bulk copy, counted per
+// element); when Np % 4 != 0 the 128 rows are re-laid out with pitch 4 Q
+// (element loads, vector stores) behind a second barrier; then per chunk: 8
+// vector loads of Us[y + 16 a][q], NB of Dt[x + 16 b][q], 4 x 8 x NB madds;
+// stores res[m, k0 + y + 16 a, x + 16 b].  A sub-group is lanes (x, y) with
+// y in {2 w, 2 w + 1}.
 pm_status counts_dgt(const KP &kp, std::vector<pm_feature> &v) {
-    const i64 Np = kp.i(0), Nel = kp.i(1), NB = cdiv(Np, 16), W = 48 * NB;
-    const i64 G = cdiv(Nel, 128), Gfull = Nel / 128, rlast = Nel % 128;
-    const u64 WI = (u64)G * 256, SG = (u64)G * 8;
+    const i64 Np = kp.i(0), Nel = kp.i(1), NB = cdiv(Np, 16), Q = cdiv(Np, 4), QB = cdiv(Q, 16);
+    i64 PD = 4 * Q;
+    while (PD % 32 != 4) PD++;
+    const bool v4 = Np % 4 == 0;
+    const i64 T = cdiv(Nel, 128), Tfull = Nel / 128, rlast = Nel % 128, G = 3 * T;
+    const u64 uG = (u64)G, uNp = (u64)Np, uQ = (u64)Q, uNB = (u64)NB, uQB = (u64)QB;
     Out o(v);
-    o.op(0, 2, WI * (u64)(24 * NB * Np), SG * (u64)(24 * NB * Np));
-    // sub-groups with some row y + 16 ib below / at or above Np, per column block
-    u64 sg_in = 0, sg_pad = 0;
+    o.op(0, 2, uG * 256 * 32 * uNB * uQ, uG * 8 * 32 * uNB * uQ);
+    // sub-groups with a row y + 16 ib < Np, summed over the row blocks ib
+    u64 sg_in = 0;
     for (i64 ib = 0; ib < NB; ib++)
-        for (i64 w = 0; w < 8; w++) {
-            sg_in += (2 * w + 16 * ib < Np);
-            sg_pad += (2 * w + 1 + 16 * ib >= Np);
-        }
-    // sub-groups storing results at row step a of a tile with r rows
+        for (i64 w = 0; w < 8; w++) sg_in += (2 * w + 16 * ib < Np);
+    // (chunk block, element) pairs with an element j < Np in some lane
+    u64 qe = 0;
+    for (i64 qb = 0; qb < QB; qb++)
+        for (i64 e = 0; e < 4; e++) qe += (64 * qb + e < Np);
     auto sg_rows = [](i64 r) {
         u64 n = 0;
         for (i64 a = 0; a < 8; a++)
             for (i64 w = 0; w < 8; w++) n += (2 * w + 16 * a < r);
         return n;
     };
-    auto site = [&](const char *tag, int mem, int dir, i64 l0, i64 l1, i64 g0, i64 loop, u64 wi, u64 sg, u64 foot) {
+    auto site = [&](const char *tag, int mem, int dir, bool vec, i64 l0, i64 l1, i64 g0, i64 g1, i64 loop, u64 wi,
+                    u64 sg, u64 foot) {
         Site x{};
-        x.tag = tag; x.mem = mem; x.dir = dir; x.dtype = "float32"; x.dsize = 4;
-        x.nl = 2; x.l[0] = l0; x.l[1] = l1; x.ng = 1; x.g[0] = g0; x.loop = loop;
+        x.tag = tag; x.mem = mem; x.dir = dir; x.dtype = vec ? "float32x4" : "float32"; x.dsize = vec ? 16 : 4;
+        x.nl = 2; x.l[0] = l0; x.l[1] = l1; x.ng = 2; x.g[0] = g0; x.g[1] = g1; x.loop = loop;
         x.wi = wi; x.sg = sg; x.foot = foot;
         o.site(x);
     };
-    const u64 uG = (u64)G, uNp = (u64)Np;
-    site("dgt-D", GL, LD, 1, Np, 0, 16, uG * 3 * uNp * uNp, uG * 3 * (u64)NB * sg_in, 3 * uNp * uNp);
-    site("dgt-Dt", LO, ST, W + 1, 1, 0, 16 * (W + 1), uG * 3 * (u64)(16 * NB) * uNp,
-         uG * 3 * (u64)NB * (sg_in + sg_pad), (u64)W * uNp);
-    site("dgt-u", GL, LD, 0, 0, 128 * Np, 1, (u64)Nel * uNp, (u64)Nel * uNp, (u64)Nel * uNp);
-    site("dgt-Us", LO, LD, 0, Np, 0, 16 * Np, WI * 8 * uNp, SG * 8 * uNp, 128 * uNp);
-    site("dgt-Dl", LO, LD, 1, 0, 0, 16, WI * 3 * (u64)NB * uNp, SG * 3 * (u64)NB * uNp, (u64)W * uNp);
-    site("dgt-res", GL, ST, 1, Np, 128 * Np, 16 * Np, 3 * (u64)Nel * uNp,
-         3 * (u64)NB * ((u64)Gfull * 64 + (rlast ? sg_rows(rlast) : 0)), 3 * (u64)Nel * uNp);
-    o.finish(1, uG);
+    if (v4)
+        site("dgt-D", GL, LD, true, 1, Np / 4, Np * Np / 4, 0, 16, uG * uNp * uQ, uG * uQB * sg_in, 3 * uNp * uQ);
+    else
+        site("dgt-D", GL, LD, false, 4, Np, Np * Np, 0, 1, uG * uNp * uNp, uG * sg_in * qe, 3 * uNp * uNp);
+    site("dgt-Dt", LO, ST, true, 1, PD / 4, 0, 0, 16, uG * 16 * uNB * uQ, uG * 8 * uNB * uQB, 16 * uNB * uQ);
+    site("dgt-u", GL, LD, false, 0, 0, 0, 128 * Np, 1, 3 * (u64)Nel * uNp, 3 * (u64)Nel * uNp, (u64)Nel * uNp);
+    if (!v4) {
+        site("dgt-R", LO, LD, false, 4, Np, 0, 0, 1, uG * 128 * uNp, uG * 64 * qe, 128 * uNp);
+        site("dgt-Ur", LO, ST, true, 1, Q, 0, 0, 16, uG * 128 * uQ, uG * 64 * uQB, 128 * uQ);
+    }
+    site("dgt-Us", LO, LD, true, 0, Q, 0, 0, 16 * Q, uG * 256 * 8 * uQ, uG * 64 * uQ, 128 * uQ);
+    site("dgt-Dl", LO, LD, true, PD / 4, 0, 0, 0, 4 * PD, uG * 256 * uNB * uQ, uG * 8 * uNB * uQ, 16 * uNB * uQ);
+    site("dgt-res", GL, ST, false, 1, Np, Nel * Np, 128 * Np, 16 * Np, 3 * (u64)Nel * uNp,
+         3 * uNB * ((u64)Tfull * 64 + (rlast ? sg_rows(rlast) : 0)), 3 * (u64)Nel * uNp);
+    o.finish(v4 ? 1 : 2, uG);
     return PM_OK;
 }
 
@@ -786,8 +800,8 @@ pm_status validate(const KP &kp) {
         return PM_OK;
     case FAM_DGT:
         if (kp.i(0) < 1 || kp.i(0) > 96) return fail(PM_EINVAL, "%s: Np must be 1..96", nm);
-        if (kp.i(1) < 4 || kp.i(1) % 4 || kp.i(1) > (1LL << 24))
-            return fail(PM_EINVAL, "%s: Nel must be a positive multiple of 4 (<= 2^24)", nm);
+        if (kp.i(1) < 4 || kp.i(1) % 4 || kp.i(1) > 65535LL * 128)
+            return fail(PM_EINVAL, "%s: Nel must be a positive multiple of 4 (<= 65535 x 128)", nm);
         return PM_OK;
     case FAM_FDB: {
         i64 n = kp.i(0), BX = kp.i(1), BY = kp.i(2);

@@ -207,101 +207,144 @@ pm_status launch_fdb_v(int BX, int BY, void *const *b, int n, float c0, float c1
 }
 
 // ---------------------------------------------------------------- DG tile
-// res[m, k, i] = sum_j D[m, i, j] u[k, j] for 128 elements k per CTA, as one
-// product C (128 x 3 NPP) = U (128 x Np) Dt, the m blocks of Dt padded to
-// NPP = 16 NB columns (zero rows of D beyond Np).  CTA 16 x 16: thread
-// (x, y) accumulates rows y + 16 a (a < 8) and columns x + 16 b (b < 3 NB)
-// in registers.  The u tile (contiguous, rows x Np floats) arrives by one
-// bulk copy on the TMA engine while the threads stage D transposed into
-// shared memory (row pitch W + 1: conflict-free stores and loads); one
-// barrier; the mbarrier wait is bounded (error word, no stores on timeout).
+// res[m, k, i] = sum_j D[m, i, j] u[k, j] for one m (blockIdx.x < 3) and
+// 128 elements k (blockIdx.y) per CTA, as one product C (128 x NPP) =
+// U (128 x Np4) Dt^T: Dt's rows padded to NPP = 16 NB with zeros, j padded
+// to Np4 = 4 Q with zeros, row pitch PD (PD % 32 == 4: conflict-free
+// 16-byte loads across 16 rows).  CTA 16 x 16: thread (x, y) accumulates
+// rows y + 16 a (a < 8) and columns x + 16 b (b < NB) in registers,
+// reading 16-byte vectors of u and D (four j per load).  The three CTAs of
+// a tile are adjacent in launch order, so the tile is read from HBM once.
+// The u tile (contiguous, rows x Np floats) arrives by one bulk copy on the
+// TMA engine while the threads stage D with 16-byte loads and stores; when
+// Np % 4 != 0 the rows are then re-laid out with pitch Np4 behind a second
+// barrier.  Small register tiles keep two or more CTAs per SM, so one CTA's
+// staging and stores overlap another's multiply-adds.  The mbarrier wait is
+// bounded (error word; a thread that gives up still passes the second
+// barrier and stores nothing).
 static __device__ int g_dgt_timeout;
 
-template <int NB>
-constexpr size_t dgt_smem(int Np) {
-    return 16 + (size_t)128 * Np * 4 + (((size_t)Np * (48 * NB + 1) + 1) & ~(size_t)1) * 4 + 8;
+__host__ __device__ constexpr int dgt_pd(int Q) { return 4 * Q + ((36 - (4 * Q) % 32) % 32); }
+
+size_t dgt_smem(int Np) {
+    const int Q = (Np + 3) / 4, NB = (Np + 15) / 16;
+    return 16 + (size_t)128 * 4 * Q * 4 + (Np % 4 ? (size_t)128 * Np * 4 : 0) + (size_t)16 * NB * dgt_pd(Q) * 4 + 8;
 }
 
 template <int NB>
-__global__ void __launch_bounds__(256, NB <= 2 ? 3 : 1) k_dg_tile(const float *__restrict__ D, const float *__restrict__ u,
-                                                 float *__restrict__ res, int Np, int Nel) {
-    constexpr int W = 48 * NB, NC = 3 * NB;
+__global__ void __launch_bounds__(256, NB <= 3 ? 3 : 2) k_dg_tile(const float *__restrict__ D,
+                                                                  const float *__restrict__ u,
+                                                                  float *__restrict__ res, int Np, int Nel) {
+    const int Q = (Np + 3) / 4, QB = (Q + 15) / 16, PD = dgt_pd(Q), P4 = PD / 4;
+    const bool v4 = (Np & 3) == 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
     float *Us = reinterpret_cast<float *>((((uintptr_t)smem_raw + 15) & ~(uintptr_t)15));
-    float *Dt = Us + 128 * Np;
-    uint64_t *bar = reinterpret_cast<uint64_t *>(Dt + (((size_t)Np * (W + 1) + 1) & ~(size_t)1));
-    const int x = threadIdx.x, y = threadIdx.y;
+    float *R = Us + 128 * 4 * Q;                    // raw rows (Np % 4 != 0 only)
+    float *Dt = R + (v4 ? 0 : 128 * Np);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Dt + 16 * NB * PD);
+    const int x = threadIdx.x, y = threadIdx.y, m = blockIdx.x;
     const bool leader = x == 0 && y == 0;
-    const long long k0 = 128LL * blockIdx.x;
+    const long long k0 = 128LL * blockIdx.y;
     const int rows = (int)min(128LL, (long long)Nel - k0);
     if (leader) {
         mbar_init(bar, 1);
         mbar_init_fence();
         const uint32_t bytes = (uint32_t)rows * (uint32_t)Np * 4u;
         mbar_expect_tx(bar, bytes);
-        bulk_load(Us, u + k0 * Np, bytes, bar);
+        bulk_load(v4 ? Us : R, u + k0 * Np, bytes, bar);
     }
-    // all of a thread's D loads of one m block in flight before its stores
-#pragma unroll
-    for (int m = 0; m < 3; m++) {
-        float dv[NB][NB];
+    // D staging: all of a thread's loads in flight before its stores
+    {
+        float4 dv[NB][2];
 #pragma unroll
         for (int ib = 0; ib < NB; ib++)
 #pragma unroll
-            for (int jb = 0; jb < NB; jb++) {
-                const int i = y + 16 * ib, j = x + 16 * jb;
-                dv[ib][jb] = (i < Np && j < Np) ? __ldg(D + (m * Np + i) * Np + j) : 0.0f;
+            for (int qb = 0; qb < 2; qb++) {
+                const int i = y + 16 * ib, q = x + 16 * qb;
+                float4 d = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
+                if (qb < QB && q < Q && i < Np) {
+                    const float *src = D + (m * Np + i) * Np + 4 * q;
+                    if (v4) {
+                        d = __ldg(reinterpret_cast<const float4 *>(src));
+                    } else {
+                        d.x = __ldg(src);
+                        if (4 * q + 1 < Np) d.y = __ldg(src + 1);
+                        if (4 * q + 2 < Np) d.z = __ldg(src + 2);
+                        if (4 * q + 3 < Np) d.w = __ldg(src + 3);
+                    }
+                }
+                dv[ib][qb] = d;
             }
 #pragma unroll
         for (int ib = 0; ib < NB; ib++)
 #pragma unroll
-            for (int jb = 0; jb < NB; jb++) {
-                const int j = x + 16 * jb;
-                if (j < Np) Dt[j * (W + 1) + m * 16 * NB + y + 16 * ib] = dv[ib][jb];
+            for (int qb = 0; qb < 2; qb++) {
+                const int q = x + 16 * qb;
+                if (qb < QB && q < Q) reinterpret_cast<float4 *>(Dt + (y + 16 * ib) * PD)[q] = dv[ib][qb];
             }
     }
     __syncthreads();
     const bool ok = mbar_wait_bounded(bar, 0, &g_dgt_timeout, 1ll << 26);
     if (!ok && leader) mbar_wait_bounded(bar, 0, &g_dgt_timeout, 1ll << 26);   // drain our own copy
+    if (!v4) {
+        if (ok)
+#pragma unroll
+            for (int rb = 0; rb < 8; rb++)
+                for (int qb = 0; qb < QB; qb++) {
+                    const int r = y + 16 * rb, q = x + 16 * qb;
+                    if (q >= Q) continue;
+                    const float *src = R + r * Np + 4 * q;
+                    float4 t = make_float4(src[0], 0.0f, 0.0f, 0.0f);
+                    if (4 * q + 1 < Np) t.y = src[1];
+                    if (4 * q + 2 < Np) t.z = src[2];
+                    if (4 * q + 3 < Np) t.w = src[3];
+                    reinterpret_cast<float4 *>(Us + r * 4 * Q)[q] = t;
+                }
+        __syncthreads();
+    }
     if (!ok) return;
-    float acc[8][NC];
+    float acc[8][NB];
 #pragma unroll
     for (int a = 0; a < 8; a++)
 #pragma unroll
-        for (int b = 0; b < NC; b++) acc[a][b] = 0.0f;
-    const float *ur = Us + y * Np;
-    const float *dr = Dt + x;
-#pragma unroll 2
-    for (int j = 0; j < Np; j++) {
-        float av[8], bv[NC];
+        for (int b = 0; b < NB; b++) acc[a][b] = 0.0f;
+    const float4 *U4 = reinterpret_cast<const float4 *>(Us) + y * Q;
+    const float4 *D4 = reinterpret_cast<const float4 *>(Dt) + x * P4;
+#pragma unroll 1
+    for (int q = 0; q < Q; q++) {
+        float4 av[8];
 #pragma unroll
-        for (int a = 0; a < 8; a++) av[a] = ur[16 * a * Np + j];
+        for (int a = 0; a < 8; a++) av[a] = U4[16 * a * Q + q];
 #pragma unroll
-        for (int b = 0; b < NC; b++) bv[b] = dr[j * (W + 1) + 16 * b];
-#pragma unroll
-        for (int a = 0; a < 8; a++)
-#pragma unroll
-            for (int b = 0; b < NC; b++) acc[a][b] = __fmaf_rn(av[a], bv[b], acc[a][b]);
-    }
-#pragma unroll
-    for (int m = 0; m < 3; m++)
-#pragma unroll
-        for (int ib = 0; ib < NB; ib++) {
-            const int i = x + 16 * ib;
-            if (i >= Np) continue;
+        for (int b = 0; b < NB; b++) {
+            const float4 bv = D4[16 * b * P4 + q];
 #pragma unroll
             for (int a = 0; a < 8; a++) {
-                const long long k = k0 + y + 16 * a;
-                if (k < Nel) res[((long long)m * Nel + k) * Np + i] = acc[a][m * NB + ib];
+                float t = __fmaf_rn(av[a].x, bv.x, acc[a][b]);
+                t = __fmaf_rn(av[a].y, bv.y, t);
+                t = __fmaf_rn(av[a].z, bv.z, t);
+                acc[a][b] = __fmaf_rn(av[a].w, bv.w, t);
             }
         }
+    }
+    float *out = res + (long long)m * Nel * Np;
+#pragma unroll
+    for (int b = 0; b < NB; b++) {
+        const int i = x + 16 * b;
+        if (i >= Np) continue;
+#pragma unroll
+        for (int a = 0; a < 8; a++) {
+            const long long k = k0 + y + 16 * a;
+            if (k < Nel) out[k * Np + i] = acc[a][b];
+        }
+    }
 }
 
 template <int NB>
 pm_status launch_dgt_t(void *const *b, int Np, int Nel, cudaStream_t st) {
-    const size_t smem = dgt_smem<NB>(Np);
+    const size_t smem = dgt_smem(Np);
     PM_CUDA_TRY(cudaFuncSetAttribute(k_dg_tile<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    launch_k(k_dg_tile<NB>, (unsigned)((Nel + 127) / 128), dim3(16, 16), smem, st, (const float *)b[0],
+    launch_k(k_dg_tile<NB>, dim3(3, (unsigned)((Nel + 127) / 128)), dim3(16, 16), smem, st, (const float *)b[0],
              (const float *)b[1], (float *)b[2], Np, Nel);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
@@ -333,7 +376,8 @@ pm_status launch_tiles(const KP &kp, void *const *b, void *stream) {
     cudaStream_t st = (cudaStream_t)stream;
     if (kp.def->fam == FAM_DGT) {
         const int Np = (int)kp.i(0), Nel = (int)kp.i(1);
-        if ((uintptr_t)b[1] % 16) return fail(PM_EINVAL, "dg_tile: u must be 16-byte aligned");
+        for (int a = 0; a < 2; a++)
+            if ((uintptr_t)b[a] % 16) return fail(PM_EINVAL, "dg_tile: buffer %d must be 16-byte aligned", a);
         switch ((Np + 15) / 16) {
         case 1: return launch_dgt_t<1>(b, Np, Nel, st);
         case 2: return launch_dgt_t<2>(b, Np, Nel, st);

@@ -374,21 +374,32 @@ def test_tensor_core_closed_forms(kernel, R, n):
 
 @pytest.mark.parametrize("Np,Nel", [(20, 132), (35, 256), (84, 128), (17, 4)])
 def test_dg_tile_closed_forms(Np, Nel):
-    # the DG product through 128-element tiles: every D element loaded once
-    # per work-group, every u element once (one bulk copy, uniform), every
-    # result stored once; padded columns and rows of a partial tile add
-    # multiply-adds (8 x 3 NB per j per work-item), never stores
+    # the DG product, one work-group per (m, 128 elements), j in 16-byte
+    # chunks: every D row block of its m loaded once per work-group (as
+    # vectors when Np % 4 == 0), every u element once per m (one bulk copy,
+    # uniform), every result stored once; padded rows, padded j and rows of a
+    # partial tile add multiply-adds (4 x 8 x NB per chunk per work-item),
+    # never stores
     fs = features("dg_tile", Np=Np, Nel=Nel)
-    G, NB = -(-Nel // 128), -(-Np // 16)
-    assert op(fs, "float32", "madd", wi=True) == G * 256 * 8 * 3 * NB * Np >= 3 * Nel * Np * Np
+    T, NB, Q = -(-Nel // 128), -(-Np // 16), -(-Np // 4)
+    G = 3 * T
+    assert op(fs, "float32", "madd", wi=True) == G * 256 * 8 * NB * 4 * Q >= 3 * Nel * Np * Np
     if Np % 16 == 0 and Nel % 128 == 0:
         assert op(fs, "float32", "madd", wi=True) == 3 * Nel * Np * Np
     d = by_tag(fs, "dgt-D")
-    assert d["count_wi"] == G * 3 * Np * Np and d["footprint"] == 3 * Np * Np and d["lstr"] == (1, Np)
+    if Np % 4 == 0:
+        assert d["dtype"] == "float32x4" and d["count_wi"] == G * Np * Np // 4 and d["lstr"] == (1, Np // 4)
+        assert d["footprint"] == 3 * Np * Np // 4 and d["gstr"] == (Np * Np // 4, 0)
+    else:
+        assert d["dtype"] == "float32" and d["count_wi"] == G * Np * Np and d["lstr"] == (4, Np)
+        assert d["footprint"] == 3 * Np * Np and d["gstr"] == (Np * Np, 0)
     uu = by_tag(fs, "dgt-u")
-    assert uu["count_wi"] == uu["count"] == uu["footprint"] == Nel * Np and uu["lstr"] == (0, 0)
+    assert uu["count_wi"] == uu["count"] == 3 * Nel * Np and uu["footprint"] == Nel * Np and uu["lstr"] == (0, 0)
     r = by_tag(fs, "dgt-res")
-    assert r["count_wi"] == r["footprint"] == 3 * Nel * Np and r["lstr"] == (1, Np) and r["gstr"] == (128 * Np,)
-    assert by_tag(fs, "dgt-Us")["count_wi"] == G * 256 * 8 * Np
-    assert by_tag(fs, "dgt-Dl")["count_wi"] == G * 256 * 3 * NB * Np
-    assert single(fs, "sync") == 1 and single(fs, "groups") == G
+    assert r["count_wi"] == r["footprint"] == 3 * Nel * Np and r["lstr"] == (1, Np)
+    assert r["gstr"] == (Nel * Np, 128 * Np)
+    assert by_tag(fs, "dgt-Us")["count_wi"] == G * 256 * 8 * Q
+    assert by_tag(fs, "dgt-Dl")["count_wi"] == G * 256 * NB * Q
+    pd = by_tag(fs, "dgt-Dl")["lstr"][0] * 4
+    assert pd % 32 == 4 and pd >= 4 * Q
+    assert single(fs, "sync") == (1 if Np % 4 == 0 else 2) and single(fs, "groups") == G
