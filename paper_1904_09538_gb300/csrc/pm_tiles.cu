@@ -231,10 +231,12 @@ size_t dgt_smem(int Np) {
     return 16 + (size_t)128 * 4 * Q * 4 + (Np % 4 ? (size_t)128 * Np * 4 : 0) + (size_t)16 * NB * dgt_pd(Q) * 4 + 8;
 }
 
-template <int NB>
+// NPC: Np fixed at compile time (the paper's sizes), 0 = taken from the argument
+template <int NB, int NPC>
 __global__ void __launch_bounds__(256, NB <= 3 ? 3 : 2) k_dg_tile(const float *__restrict__ D,
                                                                   const float *__restrict__ u,
-                                                                  float *__restrict__ res, int Np, int Nel) {
+                                                                  float *__restrict__ res, int np_arg, int Nel) {
+    const int Np = NPC ? NPC : np_arg;
     const int Q = (Np + 3) / 4, QB = (Q + 15) / 16, PD = dgt_pd(Q), P4 = PD / 4;
     const bool v4 = (Np & 3) == 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -310,7 +312,7 @@ __global__ void __launch_bounds__(256, NB <= 3 ? 3 : 2) k_dg_tile(const float *_
         for (int b = 0; b < NB; b++) acc[a][b] = 0.0f;
     const float4 *U4 = reinterpret_cast<const float4 *>(Us) + y * Q;
     const float4 *D4 = reinterpret_cast<const float4 *>(Dt) + x * P4;
-#pragma unroll 1
+#pragma unroll(NPC ? 3 : 1)
     for (int q = 0; q < Q; q++) {
         float4 av[8];
 #pragma unroll
@@ -340,11 +342,12 @@ __global__ void __launch_bounds__(256, NB <= 3 ? 3 : 2) k_dg_tile(const float *_
     }
 }
 
-template <int NB>
+template <int NB, int NPC>
 pm_status launch_dgt_t(void *const *b, int Np, int Nel, cudaStream_t st) {
     const size_t smem = dgt_smem(Np);
-    PM_CUDA_TRY(cudaFuncSetAttribute(k_dg_tile<NB>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    launch_k(k_dg_tile<NB>, dim3(3, (unsigned)((Nel + 127) / 128)), dim3(16, 16), smem, st, (const float *)b[0],
+    auto fn = k_dg_tile<NB, NPC>;
+    PM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    launch_k(fn, dim3(3, (unsigned)((Nel + 127) / 128)), dim3(16, 16), smem, st, (const float *)b[0],
              (const float *)b[1], (float *)b[2], Np, Nel);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
@@ -378,13 +381,20 @@ pm_status launch_tiles(const KP &kp, void *const *b, void *stream) {
         const int Np = (int)kp.i(0), Nel = (int)kp.i(1);
         for (int a = 0; a < 2; a++)
             if ((uintptr_t)b[a] % 16) return fail(PM_EINVAL, "dg_tile: buffer %d must be 16-byte aligned", a);
+        switch (Np) {   // the paper's node counts, specialised
+        case 20: return launch_dgt_t<2, 20>(b, Np, Nel, st);
+        case 35: return launch_dgt_t<3, 35>(b, Np, Nel, st);
+        case 56: return launch_dgt_t<4, 56>(b, Np, Nel, st);
+        case 84: return launch_dgt_t<6, 84>(b, Np, Nel, st);
+        default: break;
+        }
         switch ((Np + 15) / 16) {
-        case 1: return launch_dgt_t<1>(b, Np, Nel, st);
-        case 2: return launch_dgt_t<2>(b, Np, Nel, st);
-        case 3: return launch_dgt_t<3>(b, Np, Nel, st);
-        case 4: return launch_dgt_t<4>(b, Np, Nel, st);
-        case 5: return launch_dgt_t<5>(b, Np, Nel, st);
-        default: return launch_dgt_t<6>(b, Np, Nel, st);
+        case 1: return launch_dgt_t<1, 0>(b, Np, Nel, st);
+        case 2: return launch_dgt_t<2, 0>(b, Np, Nel, st);
+        case 3: return launch_dgt_t<3, 0>(b, Np, Nel, st);
+        case 4: return launch_dgt_t<4, 0>(b, Np, Nel, st);
+        case 5: return launch_dgt_t<5, 0>(b, Np, Nel, st);
+        default: return launch_dgt_t<6, 0>(b, Np, Nel, st);
         }
     }
     if (kp.def->fam == FAM_FDB) {
