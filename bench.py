@@ -311,7 +311,10 @@ def run_ours(args):
                     "GB/s": nb / last_times[i] / 1e9 if last_times[i] > 0 else None}
                    for i, (k, p, _b, nb, inst) in enumerate(prepared)], open(args.dump, "w"), indent=0)
     if not args.no_e2e:
-        line["e2e"] = e2e_measure(pm, S, variants, torch, args.trials, fit_and_predict)
+        fit_sizes = {"models": len(fam_names), "params": sum(plan.nparams), "rows": sum(len(fit_rows[f]) for f in fam_names),
+                     "features": int(Xfit.size), "heldout": sum(len(held[f]) for f in fam_names),
+                     "heldout_features": sum(len(held[f]) * len(models[f].features) for f in fam_names)}
+        line["e2e"] = e2e_measure(pm, S, variants, torch, args.trials, fit_and_predict, fit_sizes)
     if not args.no_fit_bench:
         line["fit"] = fit_throughput(pm, torch, dev)
         if rank == 0 and world == 1 and not args.no_cpu:
@@ -398,13 +401,13 @@ def gpu_local_cpus(torch, dev_index):
         return None
 
 
-def e2e_measure(pm, S, variants, torch, trials, fit_and_predict):
+def e2e_measure(pm, S, variants, torch, trials, fit_and_predict, fit_sizes):
     """Same step through the public API with host buffers: pm_run_host_batch
     over every variant (pinned host buffers; per variant the host-to-device
-    copies of its inputs, its `trials` timed launches, the device-to-host
-    copy of its output, the output copy of one variant overlapping the input
-    copy of the next), then the batched calibration and the held-out
-    predictions from host arrays.  One step."""
+    copies of its inputs and its `trials` timed launches, the outputs of the
+    measurement kernels left on the device), then the batched calibration
+    and the held-out predictions from host arrays, their results read back.
+    One step."""
     import numpy as np
     # staging buffers on the host memory next to the GPU: run (and first-touch
     # the pinned pages) on the GPU's local CPUs
@@ -417,8 +420,7 @@ def e2e_measure(pm, S, variants, torch, trials, fit_and_predict):
         for b in pm.kernel_buffers(k, **p):
             need = max(need, b["elems"] * np.dtype(b["dtype"]).itemsize)
     ins = [torch.empty(need, dtype=torch.uint8, pin_memory=True) for _ in range(4)]
-    outs = [torch.empty(need, dtype=torch.uint8, pin_memory=True) for _ in range(2)]   # alternate between jobs
-    for a in ins + outs:   # values in [-1, 1) as float32 bit patterns are fine for every kernel here
+    for a in ins:   # values in [-1, 1) as float32 bit patterns are fine for every kernel here
         a.numpy().view(np.float32)[:] = 0.5
     h2d = d2h = 0
     nbytes = 0
@@ -431,11 +433,15 @@ def e2e_measure(pm, S, variants, torch, trials, fit_and_predict):
                 ii += 1
                 h2d += a.nbytes
             else:
-                a = outs[j % 2].numpy().view(b["dtype"])[:b["elems"]]
-                d2h += a.nbytes
+                a = None    # the measurement kernels' outputs stay on the device
             arrs.append(a)
         jobs.append((k, arrs, p))
         nbytes += S.algorithmic_bytes(k, p) * trials
+    # the step's result read back to the host: fitted parameters, fit
+    # reports (64 bytes per model) and held-out predictions; the fit's
+    # inputs (features, times) go host -> device
+    d2h += 8 * (fit_sizes["params"] + fit_sizes["heldout"]) + 64 * fit_sizes["models"]
+    h2d += 8 * (fit_sizes["features"] + fit_sizes["rows"] + fit_sizes["heldout_features"])
     # this box's link rates (pinned 1 GiB copies, untimed), for reading copy_ms
     link = {}
     dbuf = torch.empty(1 << 30, dtype=torch.uint8, device=torch.cuda.current_device())
@@ -450,7 +456,7 @@ def e2e_measure(pm, S, variants, torch, trials, fit_and_predict):
         link[name] = round(3 * (1 << 30) / (time.perf_counter() - t1) / 1e9, 1)
     del dbuf
     # untimed warm-up: the largest variant sizes the reserved staging pool
-    big = max(jobs, key=lambda x: sum(a.nbytes for a in x[1]))
+    big = max(jobs, key=lambda x: sum(a.nbytes for a in x[1] if a is not None))
     pm.run_host_batch(jobs[:3] + [big, big], warmup=0, trials=1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()

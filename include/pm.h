@@ -253,7 +253,10 @@ pm_status pm_run_host(int32_t kernel, const pm_param *p, size_t np,
                       void *stream, float *trial_ms, pm_timing *out, double *copy_ms);
 
 /* One kernel instance of a host-buffer batch: parameters and host buffers
- * as for pm_run_host. */
+ * as for pm_run_host, except that an output buffer's host pointer may be
+ * NULL: that output stays on the device (the kernel still writes it) and is
+ * not copied back -- for calibrations, whose result is the timings.  Input
+ * pointers must not be NULL. */
 typedef struct {
     int32_t kernel;
     const pm_param *p;

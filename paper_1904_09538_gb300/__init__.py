@@ -190,15 +190,18 @@ def run_host(kernel, host_arrays, warmup=2, trials=60, outlier_factor=5.0, strea
 
 def run_host_batch(jobs, warmup=0, trials=1, outlier_factor=5.0, stream=None, flush_l2=False):
     """pm_run_host over a list of (kernel, host_arrays, params) jobs with the
-    output copy of each job overlapping the input copy of the next.  Returns
-    (list of timing dicts, copy_ms)."""
+    output copy of each job overlapping the input copy of the next; None for
+    an output array leaves that output on the device.  Returns (list of
+    timing dicts, copy_ms)."""
     keep = []
     arr = (_lib.pm_host_job * max(1, len(jobs)))()
     for i, (kernel, host_arrays, params) in enumerate(jobs):
         parr, n, k = _params(params)
         ptrs = (ctypes.c_void_p * max(1, len(host_arrays)))()
         for b, a in enumerate(host_arrays):
-            if hasattr(a, "data_ptr"):
+            if a is None:                      # an output left on the device
+                ptrs[b] = None
+            elif hasattr(a, "data_ptr"):
                 ptrs[b] = a.data_ptr()
             else:
                 if not a.flags["C_CONTIGUOUS"]:

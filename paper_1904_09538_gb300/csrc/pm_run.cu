@@ -291,12 +291,13 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
             return fail(PM_EINVAL, "pm_run_host_batch: job %zu: %zu buffers passed, %zu needed", i, h.nbufs,
                         J[i].spec.size());
         for (size_t b = 0; b < h.nbufs; b++)
-            if (!h.host_bufs || !h.host_bufs[b]) return fail(PM_EINVAL, "pm_run_host_batch: job %zu buffer %zu is NULL", i, b);
+            if (!h.host_bufs || (!h.host_bufs[b] && J[i].spec[b].role == PM_IN))
+                return fail(PM_EINVAL, "pm_run_host_batch: job %zu input buffer %zu is NULL", i, b);
     }
     // does an output of job i overlap an input of job i + 1 in host memory?
     auto clash = [&](size_t i) {
         for (size_t a = 0; a < J[i].spec.size(); a++) {
-            if (J[i].spec[a].role != PM_OUT) continue;
+            if (J[i].spec[a].role != PM_OUT || !jobs[i].host_bufs[a]) continue;
             const char *o0 = (const char *)jobs[i].host_bufs[a];
             const char *o1 = o0 + J[i].spec[a].elems * dtype_size(J[i].spec[a].dtype);
             for (size_t b = 0; b < J[i + 1].spec.size(); b++) {
@@ -350,7 +351,7 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
         cudaEventRecord(e_k, cs);
         cudaStreamWaitEvent(down, e_k, 0);
         for (size_t b = 0; b < j.spec.size() && rc == PM_OK; b++)
-            if (j.spec[b].role == PM_OUT &&
+            if (j.spec[b].role == PM_OUT && jobs[i].host_bufs[b] &&
                 cudaMemcpyAsync(jobs[i].host_bufs[b], j.dev[b], j.spec[b].elems * dtype_size(j.spec[b].dtype),
                                 cudaMemcpyDeviceToHost, down) != cudaSuccess)
                 rc = fail(PM_ECUDA, "pm_run_host_batch: job %zu: device-to-host copy failed", i);

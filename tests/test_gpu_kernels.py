@@ -392,3 +392,18 @@ def test_dg_tile_resources():
     assert r["threads_per_block"] == 256 and r["grid_blocks"] == 3 * (1 << 18) // 128
     assert r["local_bytes_per_thread"] == 0 and r["blocks_per_sm"] >= 2
     assert r["dynamic_smem_bytes"] >= (128 * 84 + 96 * 100) * 4
+
+
+def test_run_host_batch_outputs_left_on_device():
+    # a NULL output pointer leaves that output on the device (timings only);
+    # a NULL input pointer is an error
+    dev()
+    N = 1 << 16
+    x = np.ones(N, dtype=np.float32)
+    out = np.zeros(N, dtype=np.float32)
+    tms, cms = pm.run_host_batch([("stream", [x, None], {"N": N}), ("stream", [x, out], {"N": N}),
+                                  ("fma", [x[:256 * 4], None], {"F": 1024, "G": 4})], trials=2)
+    assert len(tms) == 3 and all(t["n_trials"] == 2 and t["mean_ms"] > 0 for t in tms) and cms >= 0
+    assert np.array_equal(out, x)
+    with pytest.raises(pm.PMError):
+        pm.run_host_batch([("stream", [None, out], {"N": N})])
