@@ -125,7 +125,8 @@ def workload_config(variants, trials):
     from paper_1904_09538_gb300 import suite as S
     bps = sum(S.algorithmic_bytes(k, p) for k, p in variants) * trials
     return {"workload": "calibration suite (stream, arithmetic, local-memory, barrier, overlap, empty kernels): "
-                        "%d variants, %d timed launches each" % (len(variants), trials),
+                        "%d variants, %d timed launches each (%d for the empty kernels)" % (len(variants), trials,
+                                                                                              10 * trials),
             "variants": len(variants), "trials_per_variant": trials,
             "families": len({S.family_key(k, p) for k, p in variants}), "bytes_per_step": bps,
             "l2": "stream variants under 2x L2 (%d) timed from a flushed L2, the others larger than L2 (arrays "
@@ -195,9 +196,12 @@ def run_ours(args):
 
     stream = torch.cuda.current_stream()
     flushed = [S.cache_resident(k, p) for k, p in variants]
+    # the empty kernels last a few microseconds: ten times the trials keep
+    # their event-timing jitter out of the calibration
+    ntrials = [args.trials * (10 if k == "empty" else 1) for k, p in variants]
     # variant launches, one L2-flush launch per trial of the cache-resident
     # variants, the batched fit's graph (3 kernels) and one predict per family
-    launches_per_step = (len(prepared) + sum(flushed)) * args.trials + 3 + len(fam_names)
+    launches_per_step = sum(ntrials) + sum(t for t, f in zip(ntrials, flushed) if f) + 3 + len(fam_names)
 
     last_times = {}
 
@@ -226,10 +230,10 @@ def run_ours(args):
     def one_step(record):
         times = last_times
         for idx, (k, p, bufs, nbytes, inst) in enumerate(prepared):
-            tm = pm.run(k, bufs, warmup=0, trials=args.trials, outlier_factor=0.0, flush_l2=flushed[idx], **p)
+            tm = pm.run(k, bufs, warmup=0, trials=ntrials[idx], outlier_factor=0.0, flush_l2=flushed[idx], **p)
             times[idx] = tm["mean_ms"] * 1e-3
             if record is not None:
-                record.append((inst, nbytes, tm["mean_ms"] * args.trials, args.trials))
+                record.append((inst, nbytes, tm["mean_ms"] * ntrials[idx], ntrials[idx]))
         return fit_and_predict(times)
 
     for _ in range(args.warmup):
