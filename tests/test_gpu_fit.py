@@ -335,3 +335,29 @@ def test_fit_report_condition_estimate():
     tm = np.array([1e-12 * n ** 3 + 3e-10 * n ** 2 for n in (256, 384, 512, 640, 768)])
     _, reps = pm.fit_batched([mm], [Xm], [tm])
     assert reps[0]["status"] == -5 and reps[0]["cond"] == float("inf")
+
+
+@pytest.mark.parametrize("eps", [1e-3, 1e-4])
+def test_ill_conditioned_linear_fit_matches_qr_oracle(eps):
+    # two nearly collinear columns (condition number of the column-scaled
+    # design ~1/eps): the library solves the normal equations in float-float
+    # with iterative refinement, the oracle uses FP64 QR; they must agree
+    dev()
+    X = design(200, 91, nf=4)
+    X[:, 3] = X[:, 2] * (1 + eps * pm_inputs.uniform((200,), 92, dtype=np.float64))
+    expr = "p_a * f_sync_kernel_launch + p_b * f_thread_groups + p_c * f_op_float32_add + p_d * f_op_float32_mul"
+    om = OModel("f_wall_time", expr)
+    F = [dict(zip(om.features, r)) for r in X]
+    ptrue = {"p_a": 5e-6, "p_b": 2e-9, "p_c": 3e-12, "p_d": 4e-12}
+    t = np.array([om.eval(ptrue, f) for f in F]) * (1 + 1e-3 * pm_inputs.noise((200,), 93))
+    m = pm.Model("f_wall_time", expr)
+    assert m.features == om.features
+    p, rep = m.fit(X, t)
+    po, info = ofit.fit(om, F, t)
+    assert rep["status"] == 0 and not info["rank_deficient"]
+    A = X / t[:, None]
+    An = A / np.linalg.norm(A, axis=0)
+    kappa = np.linalg.cond(An)
+    assert kappa > 0.1 / eps, kappa
+    assert rep["cond"] <= kappa ** 2 * (1 + 1e-6)
+    assert perr(p, po) <= 1e-6, (perr(p, po), kappa)
