@@ -177,6 +177,38 @@ __device__ void reverse(const Ins *code, int n, const float *v, float *adj, floa
     }
 }
 
+// Reverse sweep in float-float (adjoints and derivatives as hi + lo): the
+// exact Jacobian of a linear model's direct solve.
+__device__ void reverse_dd(const Ins *code, int n, const df *vd, df *adj, df *g, int m) {
+    for (int k = 0; k < n; k++) adj[k] = df{0.0f, 0.0f};
+    for (int i = 0; i < m; i++) g[i] = df{0.0f, 0.0f};
+    adj[n - 1] = df{1.0f, 0.0f};
+    for (int k = n - 1; k >= 0; k--) {
+        const df a = adj[k];
+        if (a.hi == 0.0f && a.lo == 0.0f) continue;
+        const Ins in = code[k];
+        switch (in.op) {
+        case OP_PAR: g[in.arg] = df_add(g[in.arg], a); break;
+        case OP_ADD: adj[in.a] = df_add(adj[in.a], a); adj[in.b] = df_add(adj[in.b], a); break;
+        case OP_SUB: adj[in.a] = df_add(adj[in.a], a); adj[in.b] = df_sub(adj[in.b], a); break;
+        case OP_MUL:
+            adj[in.a] = df_add(adj[in.a], df_mul(a, vd[in.b]));
+            adj[in.b] = df_add(adj[in.b], df_mul(a, vd[in.a]));
+            break;
+        case OP_DIV:
+            adj[in.a] = df_add(adj[in.a], df_div(a, vd[in.b]));
+            adj[in.b] = df_sub(adj[in.b], df_div(df_mul(a, vd[k]), vd[in.b]));
+            break;
+        case OP_NEG: adj[in.a] = df_sub(adj[in.a], a); break;
+        case OP_TANH: adj[in.a] = df_add(adj[in.a], df_mul(a, df_sub(df{1.0f, 0.0f}, df_mul(vd[k], vd[k])))); break;
+        case OP_EXP: adj[in.a] = df_add(adj[in.a], df_mul(a, vd[k])); break;
+        case OP_LOG: adj[in.a] = df_add(adj[in.a], df_div(a, vd[in.a])); break;
+        case OP_SQRT: adj[in.a] = df_add(adj[in.a], df_div(df_mulf(a, 0.5f), vd[k])); break;
+        default: break;
+        }
+    }
+}
+
 // Compensated FP32 sum (TwoSum error-free transformation).
 struct CSum {
     float s, c;
@@ -197,12 +229,14 @@ struct Smem {
     Ins code[kMaxIns];
     df cst[kMaxIns];   // constants of `code` in float-float
     float J[T * (MP + 1)];
+    float Jl[T * (MP + 1)];   // low parts of J (direct linear solves only)
     float r[T], rl[T];
     double acc[NENT];
     df accf[NENT];    // the same entries in float-float (the fast solve reads these)
     double q[MP], s[MP], dq[MP], qt[MP];
     df pd[MP];
     float sf[MP];      // S.s in FP32 (the Jacobian's column scales), set with the parameters
+    df sdf[MP];        // S.s in float-float
     double M[MP][MP + 1], V[MP][MP + 1], rhs[MP], y[MP];
     int idx[MP];
     df Mf[MP][MP + 1], rhsf[MP], dinvf[MP];
@@ -230,6 +264,8 @@ __device__ void set_params(Smem<T> &S, const double *q, int m) {
     if (threadIdx.x < m) {
         const double p = S.s[threadIdx.x] * q[threadIdx.x];
         S.sf[threadIdx.x] = (float)S.s[threadIdx.x];
+        const float sh = (float)S.s[threadIdx.x];
+        S.sdf[threadIdx.x] = df{sh, (float)(S.s[threadIdx.x] - (double)sh)};
         const float h = (float)p;
         S.pd[threadIdx.x] = df{h, (float)(p - (double)h)};
     }
@@ -241,21 +277,35 @@ __device__ __forceinline__ df resid_df(df g, float2 t) { return df_sub(df{1.0f, 
 
 // Entry e of the assembled system over rows k = k0, k0 + step, ... < rows of
 // the staged block: A_ij (e < nA, row-major upper triangle), b_i, or the SSR.
-template <int T>
+// EXACT: J carries low parts (S.Jl) and the products include the cross
+// terms hi lo + lo hi.
+template <int T, bool EXACT>
 __device__ __forceinline__ void add_entry(const Smem<T> &S, CAcc &a, int e, int m, int nA, int k0, int step,
                                           int rows) {
     if (e < nA) {
         int i = 0, rem = e;
         while (rem >= m - i) { rem -= m - i; i++; }
         const int j = i + rem;
-        for (int k = k0; k < rows; k += step) a.add_prod(S.J[k * (MP + 1) + i], S.J[k * (MP + 1) + j]);
+        for (int k = k0; k < rows; k += step) {
+            if (EXACT) {
+                const float hi = S.J[k * (MP + 1) + i], hj = S.J[k * (MP + 1) + j];
+                float p, er;
+                two_prod(hi, hj, p, er);
+                er = __fmaf_rn(hi, S.Jl[k * (MP + 1) + j], er);
+                a.add(p, __fmaf_rn(S.Jl[k * (MP + 1) + i], hj, er));
+            } else {
+                a.add_prod(S.J[k * (MP + 1) + i], S.J[k * (MP + 1) + j]);
+            }
+        }
     } else if (e < nA + m) {
         const int i = e - nA;
         for (int k = k0; k < rows; k += step) {
             const float ji = S.J[k * (MP + 1) + i];
             float p, er;
             two_prod(ji, S.r[k], p, er);
-            a.add(p, __fmaf_rn(ji, S.rl[k], er));
+            er = __fmaf_rn(ji, S.rl[k], er);
+            if (EXACT) er = __fmaf_rn(S.Jl[k * (MP + 1) + i], S.r[k], er);
+            a.add(p, er);
         }
     } else {
         for (int k = k0; k < rows; k += step) {
@@ -273,7 +323,7 @@ __device__ __forceinline__ void add_entry(const Smem<T> &S, CAcc &a, int e, int 
 // rows (compensated FP32 sums, one per thread across all row blocks), and
 // the G partial sums are added in FP64 in a fixed order; otherwise each
 // thread sums whole entries.
-template <int T>
+template <int T, bool EXACT = false>
 __device__ void assemble(Smem<T> &S, const FitJob &jb, int n, unsigned mask, bool want_A) {
     const int m = jb.m, tid = threadIdx.x;
     const int nA = m * (m + 1) / 2, nE = nA + m + 1;
@@ -291,25 +341,39 @@ __device__ void assemble(Smem<T> &S, const FitJob &jb, int n, unsigned mask, boo
             const float2 tk = jb.t[row];
             const df gk = forward_df(S.code, S.cst, n, frow, S.pd, v);
             rr = resid_df(gk, tk);
-            reverse_df(S.code, n, v, adj, g, m);
-            const float rt = __frcp_rn(tk.x);
-            for (int i = 0; i < m; i++)
-                S.J[tid * (MP + 1) + i] = ((mask >> i) & 1u) ? -g[i] * S.sf[i] * rt : 0.0f;
+            if (EXACT) {
+                df adjd[kMaxIns], gd[MP];
+                reverse_dd(S.code, n, v, adjd, gd, m);
+                const df tdf = df{tk.x, tk.y};
+                for (int i = 0; i < m; i++) {
+                    const df jv = ((mask >> i) & 1u) ? df_neg(df_div(df_mul(gd[i], S.sdf[i]), tdf)) : df{0.0f, 0.0f};
+                    S.J[tid * (MP + 1) + i] = jv.hi;
+                    S.Jl[tid * (MP + 1) + i] = jv.lo;
+                }
+            } else {
+                reverse_df(S.code, n, v, adj, g, m);
+                const float rt = __frcp_rn(tk.x);
+                for (int i = 0; i < m; i++)
+                    S.J[tid * (MP + 1) + i] = ((mask >> i) & 1u) ? -g[i] * S.sf[i] * rt : 0.0f;
+            }
         } else {
-            for (int i = 0; i < m; i++) S.J[tid * (MP + 1) + i] = 0.0f;
+            for (int i = 0; i < m; i++) {
+                S.J[tid * (MP + 1) + i] = 0.0f;
+                if (EXACT) S.Jl[tid * (MP + 1) + i] = 0.0f;
+            }
         }
         S.r[tid] = rr.hi;
         S.rl[tid] = rr.lo;
         __syncthreads();
         const int rows = min(T, jb.l - base);
         if (G > 1) {
-            if (gg < G && (want_A || ge >= nA)) add_entry(S, acc[0], ge, m, nA, gg, G, rows);
+            if (gg < G && (want_A || ge >= nA)) add_entry<T, EXACT>(S, acc[0], ge, m, nA, gg, G, rows);
         } else {
             for (int u = 0; u < 3; u++) {
                 const int e = tid + u * T;
                 if (e >= nE) break;
                 if (e < nA && !want_A) continue;
-                add_entry(S, acc[u], e, m, nA, 0, 1, rows);
+                add_entry<T, EXACT>(S, acc[u], e, m, nA, 0, 1, rows);
             }
         }
         __syncthreads();
@@ -604,7 +668,7 @@ __device__ void linear_fit(Smem<T> &S, const FitJob &jb, int n, unsigned mask) {
     if (threadIdx.x < m) S.q[threadIdx.x] = 0.0;
     __syncthreads();
     set_params(S, S.q, m);
-    assemble(S, jb, n, mask, true);
+    assemble<T, true>(S, jb, n, mask, true);
     set_active(S, m, mask);
     solve_chol(S, m, 0.0);
     const bool pinv = !S.ok;
@@ -617,7 +681,7 @@ __device__ void linear_fit(Smem<T> &S, const FitJob &jb, int n, unsigned mask) {
     for (int it = 0; it < 3; it++) {  // solve, then iterative refinement (b at the new q)
         if (it > 0) {
             set_params(S, S.q, m);
-            assemble(S, jb, n, mask, false);
+            assemble<T, true>(S, jb, n, mask, false);
             if (pinv) solve_pinv(S, m);
             else {
                 // A unchanged (linear): reuse the factorisation by re-solving
