@@ -405,13 +405,13 @@ def gpu_local_cpus(torch, dev_index):
         return None
 
 
-def e2e_measure(pm, S, variants, torch, trials, fit_and_predict, fit_sizes):
+def e2e_measure(pm, S, variants, torch, trials, fit_and_predict, fit_sizes, steps=3):
     """Same step through the public API with host buffers: pm_run_host_batch
     over every variant (pinned host buffers; per variant the host-to-device
     copies of its inputs and its `trials` timed launches, the outputs of the
     measurement kernels left on the device), then the batched calibration
     and the held-out predictions from host arrays, their results read back.
-    One step."""
+    `steps` steps, timed on the host clock."""
     import numpy as np
     # staging buffers on the host memory next to the GPU: run (and first-touch
     # the pinned pages) on the GPU's local CPUs
@@ -463,14 +463,21 @@ def e2e_measure(pm, S, variants, torch, trials, fit_and_predict, fit_sizes):
     big = max(jobs, key=lambda x: sum(a.nbytes for a in x[1] if a is not None))
     pm.run_host_batch(jobs[:3] + [big, big], warmup=0, trials=1)
     torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    tms, copy_ms = pm.run_host_batch(jobs, warmup=0, trials=trials, outlier_factor=0.0)
-    fit_and_predict({i: t["mean_ms"] * 1e-3 for i, t in enumerate(tms)})
-    torch.cuda.synchronize()
-    dt = time.perf_counter() - t0
+    # `steps` timed steps (the host link is shared with the machine's other
+    # GPUs, so one step is a thin sample): aggregate throughput, each step kept
+    step_ms, copy_list = [], []
+    for _ in range(steps):
+        t0 = time.perf_counter()
+        tms, copy_ms = pm.run_host_batch(jobs, warmup=0, trials=trials, outlier_factor=0.0)
+        fit_and_predict({i: t["mean_ms"] * 1e-3 for i, t in enumerate(tms)})
+        torch.cuda.synchronize()
+        step_ms.append((time.perf_counter() - t0) * 1e3)
+        copy_list.append(copy_ms)
     os.sched_setaffinity(0, saved)
-    return {"value": round(nbytes / dt / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
-            "d2h_bytes_per_step": int(d2h), "ms_per_step": round(dt * 1e3, 2), "copy_ms": round(copy_ms, 1),
+    dt = sum(step_ms) * 1e-3
+    return {"value": round(steps * nbytes / dt / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps, "ms_per_step": round(dt * 1e3 / steps, 2),
+            "step_ms": [round(x, 1) for x in step_ms], "copy_ms": [round(x, 1) for x in copy_list],
             "link": dict(link, copies_at_link_rate_ms=round((h2d / link["h2d_gbs"] + d2h / link["d2h_gbs"]) / 1e6, 1)),
             "host_cpus": len(local) if local else None}
 
