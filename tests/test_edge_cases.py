@@ -66,6 +66,8 @@ def test_counts_cap_protocol():
 @pytest.mark.parametrize("kernel,params", [
     ("mm_pf", dict(n=0)), ("mm_pf", dict(n=17)), ("mm_tc", dict(n=384)), ("mm_tc", dict(n=512, pipe=3)),
     ("mm_tc256", dict(n=384)), ("mm_tc256", dict(n=32768 + 256)),
+    ("dg_tile", dict(Np=20, Nel=130)), ("dg_tile", dict(Np=97, Nel=128)), ("dg_tile", dict(Np=20, Nel=65536 * 128)),
+    ("dg_tile", dict(Np=0, Nel=128)),
     ("fd_block", dict(n=100, BX=64, BY=8)), ("fd_block", dict(n=256, BX=64, BY=8, V=2)),
     ("fd_tile", dict(n=0)), ("dg_upf", dict(Np=20, Nel=32, L0=32, L1=8)), ("dg_nopf", dict(Np=0, Nel=32)),
     ("smem2d", dict(R=8, T=17, G=1)), ("stream", dict(N=1000)), ("stream", dict(N=1 << 20, s=3)),
@@ -82,3 +84,13 @@ def test_missing_and_unknown_parameters_rejected():
         pm.counts("mm_pf", n=64, bogus=1)
     with pytest.raises(pm.PMError):
         pm.counts("mm_pf", n=64.5)          # integer parameter
+
+
+def test_dg_tile_counts_at_largest_size():
+    # 65535 tiles of 128 elements, Np = 96: the closed forms do not overflow
+    Np, Nel = 96, 65535 * 128
+    r = pm.counts("dg_tile", Np=Np, Nel=Nel)
+    assert rec(r, "f_op_float32_madd")["count_wi"] == 3 * Nel * Np * Np     # Np % 16 == 0, no padding
+    assert rec(r, "f_mem_access_tag:dgt-res")["count"] == 3 * Nel * Np
+    assert rec(r, "f_mem_access_tag:dgt-u")["count"] == 3 * Nel * Np
+    assert rec(r, "f_thread_groups")["count"] == 3 * 65535
