@@ -234,6 +234,7 @@ struct Smem {
     double acc[NENT];
     df accf[NENT];    // the same entries in float-float (the fast solve reads these)
     double q[MP], s[MP], dq[MP], qt[MP];
+    double dmax[MP];   // largest diag(J^T J) seen by the LM so far (its damping scale)
     df pd[MP];
     float sf[MP];      // S.s in FP32 (the Jacobian's column scales), set with the parameters
     df sdf[MP];        // S.s in float-float
@@ -433,22 +434,32 @@ __device__ __forceinline__ df A_atf(const df *acc, int m, int i, int j) {
     return acc[i * m - i * (i - 1) / 2 + (j - i)];
 }
 
-// Warp 0: solve (Ahat + lambda I) y = -bhat on the active set, Ahat the
-// unit-diagonal scaling of A; dq = y / sqrt(diag A).  Float-float arithmetic
-// on the FP32 pipes (GB300's FP64 pipe retires about two lanes per clock
-// per SM; the LM step is refined by the iteration itself).  S.ok = 0 when a
-// pivot is not positive (relative 1e-10).  Also S.pred = predicted SSR
-// decrease -(2 dq.b + dq^T A dq), evaluated as -dq.b + lambda dq^T D dq.
+// Warp 0: solve (A + lambda E) dq = -b on the active set, E = diag(dmax)
+// (the largest diag A seen by the LM, Moré's scaling; unused at lambda = 0),
+// as (Ahat + lambda E / diag A) y = -bhat with Ahat the unit-diagonal scaling
+// of A and dq = y / sqrt(diag A).  Float-float arithmetic on the FP32 pipes
+// (GB300's FP64 pipe retires about two lanes per clock per SM; the LM step
+// is refined by the iteration itself).  S.ok = 0 when a pivot is not
+// positive (relative 1e-10).  Also S.pred = predicted SSR decrease
+// -(2 dq.b + dq^T A dq), evaluated as -dq.b + lambda dq^T E dq.
 template <int T>
 __device__ void solve_chol(Smem<T> &S, int m, double lambda) {
     if (threadIdx.x < 32) {
         const int lane = threadIdx.x, n = S.nact;
         const df *acc = S.accf;
         const int nA = m * (m + 1) / 2;
-        const float lh = (float)lambda;
-        const df lam = df{lh, (float)(lambda - (double)lh)};
         df dinv = df{0.0f, 0.0f};
         if (lane < n) dinv = df_div(df{1.0f, 0.0f}, df_sqrt(A_atf(acc, m, S.idx[lane], S.idx[lane])));
+        // damping lambda * dmax_i on the diagonal of A (Moré's scaling: the
+        // largest diagonal entry met so far), lambda * dmax_i / A_ii once the
+        // rows are scaled to a unit diagonal
+        double lam_d = 0.0;
+        if (lane < n && lambda != 0.0) {
+            const int gi = S.idx[lane];
+            lam_d = lambda * fmax(S.dmax[gi] / A_at(S.acc, m, gi, gi), 1.0);
+        }
+        const float lh = (float)lam_d;
+        const df lam = df{lh, (float)(lam_d - (double)lh)};
         if (lane < MP) S.dinvf[lane] = dinv;
         if (lane == 0) S.ok = 1;
         __syncwarp();
@@ -501,10 +512,11 @@ __device__ void solve_chol(Smem<T> &S, int m, double lambda) {
         if (lane < m) S.dq[lane] = 0.0;
         __syncwarp();
         if (gl >= 0) S.dq[gl] = (double)dql.hi + (double)dql.lo;
-        // predicted decrease -(2 dq.b + dq^T A dq).  With (A + lambda D) dq = -b
-        // (D = diag A) it equals -dq.b + lambda dq^T D dq, in the scaled
-        // coordinates -y.bhat + lambda y.y: two non-negative terms, free of
-        // the cancellation the first form suffers near convergence.
+        // predicted decrease -(2 dq.b + dq^T A dq).  With (A + lambda E) dq = -b
+        // (E = diag dmax) it equals -dq.b + lambda dq^T E dq, in the scaled
+        // coordinates -y.bhat + sum_i lam_i y_i^2 (lam_i the damping on row i
+        // above): non-negative terms, free of the cancellation the first form
+        // suffers near convergence.
         df t = df{0.0f, 0.0f};
         if (lane < n) {
             const df y = S.rhsf[lane];
@@ -777,6 +789,8 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
     set_params(S, S.q, m);
     assemble(S, jb, jb.n_code, all, true);
     set_active(S, m, all);
+    if (tid < m) S.dmax[tid] = A_at(S.acc, m, tid, tid);
+    __syncthreads();
     bool converged = false;
     for (int it = 0; it < cfg.max_iter; it++) {
         bool accepted = false;
@@ -827,6 +841,7 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
         set_params(S, S.q, m);
         assemble(S, jb, jb.n_code, all, true);
         set_active(S, m, all);
+        if (tid < m) S.dmax[tid] = fmax(S.dmax[tid], A_at(S.acc, m, tid, tid));
         if (tid == 0) S.stop = S.stop || (ssr_old - S.ssr) <= cfg.ftol * ssr_old;
         __syncthreads();
         if (S.stop) {

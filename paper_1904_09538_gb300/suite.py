@@ -227,10 +227,27 @@ def family_key(kernel, p):
     return kernel
 
 
+def overlap_model(partial=True):
+    """Model of the local/global overlap kernel (Section "Modeling Operation
+    Overlap"): launch cost plus the tanh-weighted larger of the global and
+    local costs (Eq. overlap_differentiable).  With partial=True the
+    tanh-weighted smaller of the two is added with weight p_part, one of the
+    variations with an extra parameter that the section proposes for partial
+    overlap (p_part = 0: the smaller cost hidden entirely, 1: not at all)."""
+    cg = "(p_gmem * f_mem_access_global_float32)"
+    co = "(p_lmem * f_mem_access_local_float32)"
+    sw = "%s * (tanh(p_edge * (%s - %s)) + 1) / 2 + %s * (tanh(p_edge * (%s - %s)) + 1) / 2"
+    expr = "p_launch * f_sync_kernel_launch + " + sw % (cg, cg, co, co, co, cg)
+    if partial:
+        expr += " + p_part * (%s)" % (sw % (cg, co, cg, co, cg, co))
+    return expr
+
+
 def family_model(key):
     """(output feature, expression) of each family's model: the linear model
     of Section "Models Demonstrated" restricted to the family's features, and
-    the tanh overlap model for the overlap kernel."""
+    the partial-overlap variant of the tanh overlap model for the overlap
+    kernel."""
     if key.startswith("stream"):
         return LAUNCH + " + p_gmem * f_mem_access_global"
     if key.startswith("fma"):
@@ -248,10 +265,7 @@ def family_model(key):
     if key == "barrier":
         return LAUNCH + " + p_bar * f_sync_barrier_local * f_thread_groups"
     if key == "overlap":
-        cg = "(p_gmem * f_mem_access_global_float32)"
-        co = "(p_lmem * f_mem_access_local_float32)"
-        return ("p_launch * f_sync_kernel_launch + %s * (tanh(p_edge * (%s - %s)) + 1) / 2 + "
-                "%s * (tanh(p_edge * (%s - %s)) + 1) / 2" % (cg, cg, co, co, co, cg))
+        return overlap_model(partial=True)
     if key == "empty":
         return LAUNCH
     raise KeyError(key)

@@ -142,3 +142,28 @@ def test_rates_reproduce_paper_table_mm_param_vals():
     assert rate(0.0, "SG", 1) is None
     with pytest.raises(ValueError):
         rate(1e-12, "WG", 1)
+
+
+def test_overlap_family_model_limits():
+    # the partial-overlap model reduces to Eq. overlap_max as p_edge grows
+    # (p_part = 0: max of the two costs), to the linear sum of both costs
+    # with p_part = 1, and equals the tanh model of the section at p_part = 0
+    from oracle.model import Model as OModel, overlap_expr
+    from paper_1904_09538_gb300 import suite as S
+    assert S.family_model("overlap") == S.overlap_model(partial=True)
+    part = OModel("f_wall_time", S.overlap_model(partial=True))
+    tanh = OModel("f_wall_time", S.overlap_model(partial=False))
+    ref = OModel("f_wall_time", overlap_expr("p_launch * f_sync_kernel_launch",
+                                             "p_gmem * f_mem_access_global_float32",
+                                             "p_lmem * f_mem_access_local_float32"))
+    assert set(part.params) == set(tanh.params) | {"p_part"}
+    for m_ratio in (0.25, 0.9, 1.1, 4.0):
+        f = {"f_sync_kernel_launch": 1.0, "f_mem_access_global_float32": 2e6,
+             "f_mem_access_local_float32": 2e6 * m_ratio}
+        p = {"p_launch": 5e-6, "p_gmem": 3e-12, "p_lmem": 3e-12, "p_edge": 1e9}
+        cg, co = 6e-6, 6e-6 * m_ratio
+        assert tanh.eval(p, f) == pytest.approx(ref.eval(p, f), rel=1e-15)
+        assert part.eval(dict(p, p_part=0.0), f) == pytest.approx(tanh.eval(p, f), rel=1e-15)
+        assert part.eval(dict(p, p_part=0.0), f) == pytest.approx(5e-6 + max(cg, co), rel=1e-9)
+        assert part.eval(dict(p, p_part=1.0), f) == pytest.approx(5e-6 + cg + co, rel=1e-9)
+        assert part.eval(dict(p, p_part=0.5), f) == pytest.approx(5e-6 + max(cg, co) + min(cg, co) / 2, rel=1e-9)

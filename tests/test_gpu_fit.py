@@ -361,3 +361,31 @@ def test_ill_conditioned_linear_fit_matches_qr_oracle(eps):
     assert kappa > 0.1 / eps, kappa
     assert rep["cond"] <= kappa ** 2 * (1 + 1e-6)
     assert perr(p, po) <= 1e-6, (perr(p, po), kappa)
+
+
+@pytest.mark.parametrize("p_edge,sigma,seed", [(1e5, 1e-2, 41), (1e7, 1e-2, 42), (1e5, 0.0, 43)])
+def test_partial_overlap_model_default_start(p_edge, sigma, seed):
+    # the suite's overlap-kernel model with the partial-overlap weight p_part
+    # (a product of parameters, so its start-point column vanishes at the
+    # origin and it starts from the clamp): features of the overlap kernel
+    # for m = 0..32 local load-store pairs at two array sizes, outputs from
+    # a generating point with 40 % of the smaller cost not hidden; the fit
+    # from the default start must reach the oracle's optimum
+    dev()
+    from paper_1904_09538_gb300 import suite as S
+    expr = S.overlap_model(partial=True)
+    m = pm.Model("f_wall_time", expr)
+    X = np.stack([m.feature_values("overlap", m=mm, N=N) for mm in range(33) for N in (2 ** 26, 2 ** 27)])
+    truth = dict(p_launch=1.2e-5, p_gmem=1.2e-12, p_lmem=3e-12, p_edge=p_edge, p_part=0.4)
+    t, om, F = synth(expr, X, truth, sigma, seed)
+    assert m.features == om.features
+    p, rep = m.fit(X, t)
+    assert rep["status"] == 0 and rep["iterations"] < 200, rep
+    po, _ = ofit.fit(om, F, t)
+    pred = m.predict(p, X)
+    pred_o = ofit.predict(om, po, F)
+    assert np.max(np.abs(pred / pred_o - 1)) <= 1e-5
+    i = m.params.index("p_part")
+    assert abs(p[i] - po[om.params.index("p_part")]) <= 1e-3
+    if sigma == 0.0:
+        assert abs(p[i] - 0.4) <= 1e-3
