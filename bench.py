@@ -233,7 +233,7 @@ def run_ours(args):
             tm = pm.run(k, bufs, warmup=0, trials=ntrials[idx], outlier_factor=0.0, flush_l2=flushed[idx], **p)
             times[idx] = tm["mean_ms"] * 1e-3
             if record is not None:
-                record.append((inst, nbytes, tm["mean_ms"] * ntrials[idx], ntrials[idx]))
+                record.append((idx, inst, nbytes, tm["mean_ms"] * ntrials[idx], ntrials[idx]))
         return fit_and_predict(times)
 
     for _ in range(args.warmup):
@@ -268,7 +268,7 @@ def run_ours(args):
 
     # roofline of the dominant kernel instantiation (largest share of device time)
     per = {}
-    for inst, nbytes, ms, n in record:
+    for _, inst, nbytes, ms, n in record:
         a = per.setdefault(inst, [0.0, 0.0, 0])
         a[0] += nbytes * n
         a[1] += ms
@@ -306,8 +306,15 @@ def run_ours(args):
         "clocks": clk,
         "gpu_launches": launches_per_step * args.steps,
     }
-    line["calibrated"] = calibrated_rates(fitted, torch.cuda.get_device_properties(dev).multi_processor_count,
-                                          clk.get("sm_mhz"))
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    line["calibrated"] = calibrated_rates(fitted, sm_count, clk.get("sm_mhz"))
+    # per-variant roofline fractions from the mean launch time over the timed steps
+    tsum, nsum = [0.0] * len(variants), [0] * len(variants)
+    for idx, _, _, ms, n in record:
+        tsum[idx] += ms
+        nsum[idx] += n
+    mean_s = [tsum[i] / nsum[i] * 1e-3 if nsum[i] else None for i in range(len(variants))]
+    line["suite_roofline"] = suite_roofline(variants, mean_s, peaks["hbm_gbs"], sm_count, clk.get("sm_mhz"))
     if world > 1:
         line["ranks"] = rank_reports
     if args.dump and rank == 0:
@@ -329,6 +336,66 @@ def run_ours(args):
         print(json.dumps(line))
     if world > 1:
         dist.destroy_process_group()
+
+
+def variant_work(kernel, p):
+    """(algorithmic bytes, flops, local-memory bytes) of one suite launch:
+    bytes by the kernel's definition; flops and local bytes from its exact
+    counts (a madd is 2 flops, a local access moves 4 bytes per work-item)."""
+    import paper_1904_09538_gb300 as pm
+    from paper_1904_09538_gb300 import suite as S
+    flops = lbytes = 0
+    if kernel in ("fma", "smem"):
+        for f in pm.counts(kernel, **p):
+            if f["kind"] == "op":
+                flops += f["count_wi"] * (2 if f["op"] == "madd" else 1)
+            elif f["kind"] == "mem" and f["mem"] == "local":
+                lbytes += f["count_wi"] * f["dsize"]
+    return S.algorithmic_bytes(kernel, p), flops, lbytes
+
+
+def suite_roofline(variants, mean_s, hbm_gbs, sm_count, sm_mhz, l2_bytes=None):
+    """Per-variant fractions of the roofline that bounds each suite kernel,
+    from its mean launch time: stream variants of at least 4x the L2 size
+    against the measured HBM copy rate (smaller ones are partly served by
+    L2 and claim nothing), by lid(0) stride; FP32 arithmetic loops against
+    SMs x 128 lanes x clock operations (x2 flops for madd); local-memory
+    loops against SMs x 128 bytes x clock.  FP64 loops are reported as
+    TFLOP/s (no peak is assumed for GB300's FP64 pipe)."""
+    from paper_1904_09538_gb300 import suite as S
+    l2 = l2_bytes or S.L2_BYTES
+    clk = (sm_mhz or 2070.0) * 1e6
+    lanes = sm_count * 128 * clk
+
+    def summary(fr):
+        fr = sorted(fr)
+        return {"n": len(fr), "min": round(fr[0], 4), "median": round(fr[len(fr) // 2], 4),
+                "max": round(fr[-1], 4)} if fr else None
+
+    stream, fma, f64, smem = {}, {}, [], {}
+    for (k, p), t in zip(variants, mean_s):
+        if t is None or t <= 0:
+            continue
+        nbytes, flops, lbytes = variant_work(k, p)
+        if k == "stream" and nbytes >= 4 * l2:
+            key = "2d" if p.get("shape", 0) == 1 else "s%d" % p["s"]
+            stream.setdefault(key, []).append(nbytes / t / 1e9 / hbm_gbs)
+        elif k == "fma" and p["dtype"] == 0:
+            op = ("add", "mul", "madd")[p["op"]]
+            fma.setdefault(op, []).append(flops / t / (lanes * (2 if op == "madd" else 1)))
+        elif k == "fma":
+            f64.append(flops / t / 1e12)
+        elif k == "smem":
+            smem.setdefault("sync%d" % p["sync"], []).append(lbytes / t / lanes)
+    allf = [x for v in stream.values() for x in v]
+    return {
+        "sm_mhz": round(clk / 1e6, 1),
+        "stream_ge_4x_l2": {"variants": len(allf), "at_least_0.8": sum(x >= 0.8 for x in allf),
+                            "by_stride": {k: summary(v) for k, v in sorted(stream.items())}},
+        "fma_f32_vs_pipe": {k: summary(v) for k, v in sorted(fma.items())},
+        "fma_f64_madd_tflops": summary(f64),
+        "smem_vs_bandwidth": {k: summary(v) for k, v in sorted(smem.items())},
+    }
 
 
 def calibrated_rates(fitted, sm_count, sm_mhz):
@@ -568,7 +635,7 @@ def oracle_fit_rate(seconds=5.0):
         allc = n_all / (time.perf_counter() - t1)
     return {"fits_per_s": round(one, 2), "fits": done, "cores": 1, "kind": "oracle",
             "all_cores": {"fits_per_s": round(allc, 2), "fits": n_all, "cores": cores,
-                          "machine": platform.machine()}}
+                          "machine": platform.machine(), "cpu": cpu_model()}}
 
 
 _CPU_INPUTS = {}
@@ -625,12 +692,32 @@ def cpu_baseline(variants, seconds=12.0, scale=16):
     with ThreadPoolExecutor(cores) as ex:
         ba = sum(ex.map(lambda kp: one_pass([kp], reps)[0], variants))
     ta = time.perf_counter() - t1
-    return {"value": round(b / t / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle",
+    return {"value": round(b / t / 1e9, 3), "unit": "GB/s", "cores": 1, "kind": "oracle", "cpu": cpu_model(),
             "sample": "every stream variant at N/%d and every arithmetic variant at 1/%d of its work-items, "
                       "each oracle call %d times (oracle C reference, one host core, %.1f s)"
                       % (scale, scale * 64, reps, t),
             "all_cores": {"value": round(ba / ta / 1e9, 3), "cores": cores,
                           "sample": "the same calls over a %d-thread pool, %.1f s wall" % (cores, ta)}}
+
+
+def cpu_model():
+    """The host CPU's model name (lscpu's "Model name", else /proc/cpuinfo's
+    "model name", else the machine type)."""
+    import platform
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for ln in out.splitlines():
+            if ln.strip().lower().startswith("model name:"):
+                return ln.split(":", 1)[1].strip()
+    except Exception:
+        pass
+    try:
+        for ln in open("/proc/cpuinfo"):
+            if ln.lower().startswith("model name"):
+                return ln.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return platform.machine()
 
 
 # ---------------------------------------------------------------- reference arm
@@ -655,8 +742,8 @@ def run_reference(args):
             "warmup": args.warmup, "ms_per_step": round(el / args.steps * 1e3, 1), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f32/f64", "data": "synthetic",
             "config": workload_config(variants, args.trials),
-            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "sample": last["sample"],
-                             "all_cores": last["all_cores"]},
+            "cpu_baseline": {"value": v, "unit": "GB/s", "cores": 1, "kind": "oracle", "cpu": last["cpu"],
+                             "sample": last["sample"], "all_cores": last["all_cores"]},
             "e2e": {"value": v, "unit": "GB/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 

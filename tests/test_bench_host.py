@@ -167,3 +167,43 @@ def test_overlap_family_model_limits():
         assert part.eval(dict(p, p_part=0.0), f) == pytest.approx(5e-6 + max(cg, co), rel=1e-9)
         assert part.eval(dict(p, p_part=1.0), f) == pytest.approx(5e-6 + cg + co, rel=1e-9)
         assert part.eval(dict(p, p_part=0.5), f) == pytest.approx(5e-6 + max(cg, co) + min(cg, co) / 2, rel=1e-9)
+
+
+def test_suite_roofline_fractions(bench):
+    # times built from known rates come back as those fractions of the peaks
+    from paper_1904_09538_gb300 import suite as S
+    variants = S.generate(["suite"])
+    hbm, sms, mhz = 7000.0, 152, 2000.0
+    lanes = sms * 128 * mhz * 1e6
+    times = []
+    for k, p in variants:
+        nbytes, flops, lbytes = bench.variant_work(k, p)
+        if k == "stream":
+            times.append(nbytes / (0.9 * hbm * 1e9))
+        elif k == "fma" and p["dtype"] == 0:
+            times.append(flops / (0.75 * lanes * (2 if p["op"] == 2 else 1)))
+        elif k == "fma":
+            times.append(flops / 1.1e12)
+        elif k == "smem":
+            times.append(lbytes / (0.5 * lanes))
+        else:
+            times.append(1e-3)
+    r = bench.suite_roofline(variants, times, hbm, sms, mhz)
+    big = [p for k, p in variants if k == "stream" and S.algorithmic_bytes(k, p) >= 4 * S.L2_BYTES]
+    assert r["stream_ge_4x_l2"]["variants"] == len(big) > 0
+    assert r["stream_ge_4x_l2"]["at_least_0.8"] == len(big)
+    for v in r["stream_ge_4x_l2"]["by_stride"].values():
+        assert v["min"] == v["max"] == 0.9
+    assert set(r["fma_f32_vs_pipe"]) == {"add", "mul", "madd"}
+    assert all(v["median"] == 0.75 for v in r["fma_f32_vs_pipe"].values())
+    assert r["fma_f64_madd_tflops"]["median"] == 1.1
+    assert set(r["smem_vs_bandwidth"]) == {"sync0", "sync1"}
+    assert all(v["median"] == 0.5 for v in r["smem_vs_bandwidth"].values())
+    # a madd variant's flops are 2 per madd from its exact counts
+    k, p = [(k, p) for k, p in variants if k == "fma" and p["op"] == 2 and p["dtype"] == 0][0]
+    assert bench.variant_work(k, p)[1] >= 2 * p["F"] * p["G"] * 256
+
+
+def test_cpu_model_is_named(bench):
+    name = bench.cpu_model()
+    assert isinstance(name, str) and name
