@@ -207,3 +207,18 @@ def test_suite_roofline_fractions(bench):
 def test_cpu_model_is_named(bench):
     name = bench.cpu_model()
     assert isinstance(name, str) and name
+
+
+def test_overlap_model_choice_rules():
+    # the overlap test: separately calibrated costs about equal to the
+    # measured time -> linear; well above it -> nonlinear
+    from paper_1904_09538_gb300.experiments import choose_by_residual, choose_overlap_model
+    assert choose_overlap_model(0.92) == "linear"
+    assert choose_overlap_model(1.05) == "linear"
+    assert choose_overlap_model(1.10) == "linear"
+    assert choose_overlap_model(1.18) == "nonlinear"
+    assert choose_overlap_model(1.18, margin=0.2) == "linear"
+    assert choose_by_residual({"linear": 0.9, "nonlinear": 0.87, "partial": 0.5}) == "nonlinear"
+    assert choose_by_residual({"linear": 0.8, "nonlinear": 0.87}) == "linear"
+    assert choose_by_residual({"linear": None, "nonlinear": 0.87}) == "nonlinear"
+    assert choose_by_residual({}) is None
