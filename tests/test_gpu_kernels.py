@@ -407,3 +407,49 @@ def test_run_host_batch_outputs_left_on_device():
     assert np.array_equal(out, x)
     with pytest.raises(pm.PMError):
         pm.run_host_batch([("stream", [None, out], {"N": N})])
+
+
+# ---------------------------------------------------------------- the timed suite, every variant at its size
+def test_every_suite_variant_at_timed_size_sampled():
+    # each of the calibration suite's variants in the size and launch shape the
+    # suite is timed in (arrays up to 2^28 elements), inputs ~U[-1, 1] from a
+    # seeded device generator, outputs poisoned with NaN first: 2048 sampled
+    # outputs per variant must equal the oracle's bit for bit (an element the
+    # kernel never wrote stays NaN and fails)
+    from paper_1904_09538_gb300 import suite as S
+    d = dev()
+    gen = torch.Generator(device=d)
+    checked = 0
+    for vi, (k, p) in enumerate(S.generate(["suite"])):
+        gen.manual_seed(1000 + vi)
+        spec = pm.kernel_buffers(k, **p)
+        bufs = []
+        for b in spec:
+            tdt = torch.float32 if b["dtype"] == np.float32 else torch.float64
+            if b["role"] == "in":
+                bufs.append(torch.rand(b["elems"], device=d, dtype=tdt, generator=gen) * 2 - 1)
+            else:
+                bufs.append(torch.full((b["elems"],), float("nan"), device=d, dtype=tdt))
+        pm.launch(k, bufs, **p)
+        torch.cuda.synchronize()
+        ins = [t for t, b in zip(bufs, spec) if b["role"] == "in"]
+        outs = [t for t, b in zip(bufs, spec) if b["role"] == "out"]
+        if k == "empty":
+            assert not outs
+            continue
+        (out,) = outs
+        n = out.numel()
+        idx_np = np.unique(pm_inputs.integers((2048,), 2000 + vi, 0, n - 1))
+        idx = torch.from_numpy(idx_np).to(d)
+        got = out[idx].cpu().numpy()
+        samples = [x[idx].cpu().numpy() for x in ins]
+        if k == "stream":
+            want = refs.stream(samples)
+        elif k == "fma":
+            want = refs.fma(samples[0], p["op"], p["F"])
+        else:   # local-memory shuffle, barrier and overlap kernels move each value back to its place
+            want = samples[0]
+        assert np.array_equal(got, want), (k, p)
+        checked += 1
+        del bufs, ins, outs, out
+    assert checked == 230 - 13   # every variant but the 13 empty kernels has an output
