@@ -68,6 +68,16 @@ def matmul(a, b):
     return c, ca
 
 
+def matmul_rows(a_rows, b):
+    """FP64 rows of C = A B for the given rows of A (r x n) and all of B
+    (n x n), with sum_k |a_ik b_kj|: the same definition as matmul, for
+    sampled rows of a product too large to form whole (one FP64 matrix
+    product per quantity)."""
+    a64 = np.asarray(a_rows, dtype=np.float32).astype(np.float64)
+    b64 = np.asarray(b, dtype=np.float32).astype(np.float64)
+    return a64 @ b64, np.abs(a64) @ np.abs(b64)
+
+
 def matmul_bf16_tn(a_bits, bt_bits):
     """FP64 C = A Bt^T over bf16 inputs given as uint16 bit patterns, and the |.| sums."""
     _setup()

@@ -453,3 +453,48 @@ def test_every_suite_variant_at_timed_size_sampled():
         checked += 1
         del bufs, ins, outs, out
     assert checked == 230 - 13   # every variant but the 13 empty kernels has an output
+
+
+# ---------------------------------------------------------------- matmuls at their sweep sizes, sampled rows
+def _mm_sampled(kernel, n, seed, **params):
+    d = dev()
+    a, b = pm_inputs.uniform((n, n), seed), pm_inputs.uniform((n, n), seed + 1)
+    c = torch.full((n * n,), float("nan"), device=d)
+    pm.launch(kernel, [torch.from_numpy(a).to(d), torch.from_numpy(b).to(d), c], n=n, **params)
+    torch.cuda.synchronize()
+    # one sampled row in each of 16 bands of the rows, all columns
+    rows = np.arange(0, n, n // 16) + pm_inputs.integers((16,), seed + 2, 0, n // 16 - 1)
+    ref, rabs = refs.matmul_rows(a[rows], b)
+    got = c.view(n, n)[torch.from_numpy(rows).to(d)].cpu().numpy()
+    return cond_err(got, ref, rabs)
+
+
+@pytest.mark.parametrize("kernel", ["mm_pf", "mm_nopf"])
+def test_matmul_largest_sweep_size_sampled(kernel):
+    # n = 4096, the largest size of the matmul study and sweep
+    assert _mm_sampled(kernel, 4096, 90) <= TOL
+
+
+@pytest.mark.parametrize("BM,BN,BK", [(128, 128, 32), (96, 256, 64), (64, 64, 32)])
+def test_mm_simt_autotune_size_sampled(BM, BN, BK):
+    # n = 7680, the size the SIMT tile shapes are ranked at
+    assert _mm_sampled("mm_simt", 7680, 95, BM=BM, BN=BN, BK=BK) <= TOL
+
+
+@pytest.mark.parametrize("BX,BY,V", [(32, 16, 8), (128, 32, 8), (64, 4, 4)])
+def test_fd_block_ranking_size_sampled(BX, BY, V):
+    # n = 16384, the size the stencil tile shapes are ranked at (row pitch
+    # n + 4 as in the ranking); three row windows, one at each edge band
+    n = 16384
+    d = dev()
+    gen = torch.Generator(device=d)
+    gen.manual_seed(9)
+    u = torch.rand((n + 2) * (n + 4), device=d, generator=gen) * 2 - 1
+    r = torch.full((n * n,), float("nan"), device=d)
+    pm.launch("fd_block", [u, r], n=n, BX=BX, BY=BY, V=V, c0=-4.0, c1=1.0)
+    torch.cuda.synchronize()
+    for i0 in (0, 8191, n - 9):
+        win = u.view(n + 2, n + 4)[i0:i0 + 11, :n + 2].cpu().numpy()
+        ref, rabs = refs.stencil_rows(np.ascontiguousarray(win), -4.0, 1.0)
+        got = r.view(n, n)[i0:i0 + 9].cpu().numpy()
+        assert cond_err(got, ref, rabs) <= TOL

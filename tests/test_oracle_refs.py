@@ -65,6 +65,22 @@ def test_matmul_reference():
     assert np.array_equal(c_id, a.astype(np.float64))
 
 
+def test_matmul_rows_agrees_with_full_product():
+    # rows of the product from the FP64 matrix product equal the same rows of
+    # the C reference's triple loop; the identity gives A's rows back exactly
+    n = 40
+    a = pm_inputs.uniform((n, n), 11)
+    b = pm_inputs.uniform((n, n), 12)
+    c, ca = refs.matmul(a, b)
+    rows = np.array([0, 7, 39])
+    cr, car = refs.matmul_rows(a[rows], b)
+    assert cr.shape == (3, n)
+    assert np.max(np.abs(cr - c[rows])) <= 1e-13 * np.max(ca)
+    assert np.allclose(car, ca[rows], rtol=1e-13)
+    ci, _ = refs.matmul_rows(a[rows], np.eye(n, dtype=np.float32))
+    assert np.array_equal(ci, a[rows].astype(np.float64))
+
+
 def test_dg_reference():
     Np, Nel = 20, 40
     D = pm_inputs.normal((3, Np, Np), 3)
