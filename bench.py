@@ -474,11 +474,13 @@ def gpu_local_cpus(torch, dev_index):
 
 def e2e_measure(pm, S, variants, torch, trials, fit_and_predict, fit_sizes, steps=3):
     """Same step through the public API with host buffers: pm_run_host_batch
-    over every variant (pinned host buffers; per variant the host-to-device
-    copies of its inputs and its `trials` timed launches, the outputs of the
-    measurement kernels left on the device), then the batched calibration
-    and the held-out predictions from host arrays, their results read back.
-    `steps` steps, timed on the host clock."""
+    over every variant (inputs in four pinned host buffers, each variant
+    reading a prefix of them, so each buffer is one shared region that the
+    batch copies to the device once per step; per variant its `trials`
+    timed launches, the outputs of the measurement kernels left on the
+    device), then the batched calibration and the held-out predictions from
+    host arrays, their results read back.  `steps` steps, timed on the host
+    clock; the copied bytes are the library's own count."""
     import numpy as np
     # staging buffers on the host memory next to the GPU: run (and first-touch
     # the pinned pages) on the GPU's local CPUs
@@ -493,7 +495,6 @@ def e2e_measure(pm, S, variants, torch, trials, fit_and_predict, fit_sizes, step
     ins = [torch.empty(need, dtype=torch.uint8, pin_memory=True) for _ in range(4)]
     for a in ins:   # values in [-1, 1) as float32 bit patterns are fine for every kernel here
         a.numpy().view(np.float32)[:] = 0.5
-    h2d = d2h = 0
     nbytes = 0
     jobs = []
     for j, (k, p) in enumerate(variants):
@@ -502,12 +503,12 @@ def e2e_measure(pm, S, variants, torch, trials, fit_and_predict, fit_sizes, step
             if b["role"] == "in":
                 a = ins[ii].numpy().view(b["dtype"])[:b["elems"]]
                 ii += 1
-                h2d += a.nbytes
             else:
                 a = None    # the measurement kernels' outputs stay on the device
             arrs.append(a)
         jobs.append((k, arrs, p))
         nbytes += S.algorithmic_bytes(k, p) * trials
+    h2d, d2h = pm.run_host_batch_bytes(jobs)
     # the step's result read back to the host: fitted parameters, fit
     # reports (64 bytes per model) and held-out predictions; the fit's
     # inputs (features, times) go host -> device

@@ -271,13 +271,25 @@ typedef struct {
  * never overlap a copy, so each job's device timing is as in pm_run_host:
  * job i+1's launches wait for its inputs and for job i's output copy.  When
  * an output buffer of job i overlaps an input buffer of job i+1 in host
- * memory, that pair of copies is serialised instead.  Device staging comes
- * from the default memory pool (see pm_run_host).  out: njobs timings;
- * copy_ms (nullable): time from the first input copy's start to the last
- * output copy's end minus the kernels' time; on error the failing job's
- * index is in the message and later jobs are not run. */
+ * memory, that pair of copies is serialised instead.  Input buffers that
+ * start at the same host address in several jobs are one shared region: it
+ * is copied once, by its first reader, at the largest extent any reader
+ * reads, and freed after its last reader's kernels (every kernel only reads
+ * its inputs).  A region that any host output buffer of the batch overlaps
+ * is not shared (its host contents may change during the batch); each of
+ * its readers copies it.  Device staging comes from the default memory pool
+ * (see pm_run_host).  out: njobs timings; copy_ms (nullable): time from the
+ * first input copy's start to the last output copy's end minus the
+ * kernels' time; on error the failing job's index is in the message and
+ * later jobs are not run. */
 pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_opts *opts, void *stream,
                             pm_timing *out, double *copy_ms);
+
+/* The bytes pm_run_host_batch would copy for these jobs (host only, no GPU
+ * work): host->device (shared regions once, at their largest extent) and
+ * device->host (outputs with a non-NULL host pointer).  Either output
+ * pointer may be NULL.  Same validation and errors as pm_run_host_batch. */
+pm_status pm_run_host_batch_bytes(const pm_host_job *jobs, size_t njobs, uint64_t *h2d_bytes, uint64_t *d2h_bytes);
 
 /* ---------------------------------------------------------------- models */
 

@@ -188,11 +188,7 @@ def run_host(kernel, host_arrays, warmup=2, trials=60, outlier_factor=5.0, strea
                 n_dropped=tm.n_dropped, copy_ms=cms.value)
 
 
-def run_host_batch(jobs, warmup=0, trials=1, outlier_factor=5.0, stream=None, flush_l2=False):
-    """pm_run_host over a list of (kernel, host_arrays, params) jobs with the
-    output copy of each job overlapping the input copy of the next; None for
-    an output array leaves that output on the device.  Returns (list of
-    timing dicts, copy_ms)."""
+def _host_jobs(jobs):
     keep = []
     arr = (_lib.pm_host_job * max(1, len(jobs)))()
     for i, (kernel, host_arrays, params) in enumerate(jobs):
@@ -210,12 +206,31 @@ def run_host_batch(jobs, warmup=0, trials=1, outlier_factor=5.0, stream=None, fl
         keep += [parr, k, ptrs]
         arr[i] = _lib.pm_host_job(_kid(kernel), ctypes.cast(parr, ctypes.c_void_p), n,
                                   ctypes.cast(ptrs, ctypes.c_void_p), len(host_arrays))
+    return arr, keep
+
+
+def run_host_batch(jobs, warmup=0, trials=1, outlier_factor=5.0, stream=None, flush_l2=False):
+    """pm_run_host over a list of (kernel, host_arrays, params) jobs with the
+    output copy of each job overlapping the input copy of the next; None for
+    an output array leaves that output on the device; an input region that
+    several jobs read from the same host address is copied once.  Returns
+    (list of timing dicts, copy_ms)."""
+    arr, keep = _host_jobs(jobs)
     opts = pm_run_opts(warmup, trials, outlier_factor, 1 if flush_l2 else 0)
     tms = (pm_timing * max(1, len(jobs)))()
     cms = ctypes.c_double()
     check(lib().pm_run_host_batch(arr, len(jobs), ctypes.byref(opts), _stream(stream), tms, ctypes.byref(cms)))
     return [dict(mean_ms=t.mean_ms, median_ms=t.median_ms, min_ms=t.min_ms, n_trials=t.n_trials,
                  n_dropped=t.n_dropped) for t in tms[:len(jobs)]], cms.value
+
+
+def run_host_batch_bytes(jobs):
+    """(host->device, device->host) bytes run_host_batch copies for these
+    jobs (shared input regions counted once).  Host only."""
+    arr, keep = _host_jobs(jobs)
+    h2d, d2h = ctypes.c_uint64(), ctypes.c_uint64()
+    check(lib().pm_run_host_batch_bytes(arr, len(jobs), ctypes.byref(h2d), ctypes.byref(d2h)))
+    return int(h2d.value), int(d2h.value)
 
 
 def _opts(max_iter=200, ftol=1e-15, xtol=1e-12, p0=None):

@@ -270,40 +270,131 @@ pm_status pm_run_host(int32_t kernel, const pm_param *p, size_t np, void *const 
     return rc;
 }
 
-pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_opts *opts, void *stream,
-                            pm_timing *out, double *copy_ms) {
-    if (njobs && (!jobs || !out)) return fail(PM_EINVAL, "pm_run_host_batch: jobs or out is NULL");
+}  // extern "C"
+
+namespace {
+
+struct BatchJob {
+    KP kp;
+    std::vector<BufSpec> spec;
+    std::vector<void *> dev;
+    std::vector<int> shared;   // per buffer: index into the shared inputs, or -1
+};
+
+// An input region several jobs of a batch read: every input buffer that
+// starts at the same host address.  It is copied once, at the largest extent
+// any of its readers reads, and freed after its last reader's kernels.
+struct SharedIn {
+    const char *host;
+    size_t bytes;
+    size_t last;
+    int readers;
+    void *dev;
+};
+
+size_t buf_bytes(const BufSpec &b) { return b.elems * dtype_size(b.dtype); }
+
+pm_status batch_plan(const char *who, const pm_host_job *jobs, size_t njobs, std::vector<BatchJob> &J,
+                     std::vector<SharedIn> &sh) {
+    if (njobs && !jobs) return fail(PM_EINVAL, "%s: jobs is NULL", who);
+    J.assign(njobs, BatchJob{});
     pm_status s;
-    if ((s = retain_staging_pool())) return s;
-    cudaStream_t cs = (cudaStream_t)stream;
-    struct Job {
-        KP kp;
-        std::vector<BufSpec> spec;
-        std::vector<void *> dev;
-    };
-    std::vector<Job> J(njobs);
     for (size_t i = 0; i < njobs; i++) {
         const pm_host_job &h = jobs[i];
         if ((s = parse_params(h.kernel, h.p, h.np, &J[i].kp))) return s;
         if ((s = validate(J[i].kp))) return s;
         if ((s = buffers(J[i].kp, J[i].spec))) return s;
         if (h.nbufs != J[i].spec.size())
-            return fail(PM_EINVAL, "pm_run_host_batch: job %zu: %zu buffers passed, %zu needed", i, h.nbufs,
-                        J[i].spec.size());
+            return fail(PM_EINVAL, "%s: job %zu: %zu buffers passed, %zu needed", who, i, h.nbufs, J[i].spec.size());
         for (size_t b = 0; b < h.nbufs; b++)
             if (!h.host_bufs || (!h.host_bufs[b] && J[i].spec[b].role == PM_IN))
-                return fail(PM_EINVAL, "pm_run_host_batch: job %zu input buffer %zu is NULL", i, b);
+                return fail(PM_EINVAL, "%s: job %zu input buffer %zu is NULL", who, i, b);
     }
+    // group the inputs by host start address
+    sh.clear();
+    for (size_t i = 0; i < njobs; i++) {
+        J[i].shared.assign(J[i].spec.size(), -1);
+        for (size_t b = 0; b < J[i].spec.size(); b++) {
+            if (J[i].spec[b].role != PM_IN) continue;
+            const char *h = (const char *)jobs[i].host_bufs[b];
+            int k = -1;
+            for (size_t e = 0; e < sh.size(); e++)
+                if (sh[e].host == h) k = (int)e;
+            if (k < 0) {
+                sh.push_back(SharedIn{h, 0, i, 0, nullptr});
+                k = (int)sh.size() - 1;
+            }
+            sh[k].bytes = std::max(sh[k].bytes, buf_bytes(J[i].spec[b]));
+            sh[k].last = i;
+            sh[k].readers++;
+            J[i].shared[b] = k;
+        }
+    }
+    // a region with one reader, or one that any host output of the batch
+    // overlaps (its host data may change during the batch), is not shared
+    std::vector<bool> keep(sh.size());
+    for (size_t e = 0; e < sh.size(); e++) {
+        keep[e] = sh[e].readers > 1;
+        for (size_t i = 0; i < njobs && keep[e]; i++)
+            for (size_t b = 0; b < J[i].spec.size(); b++) {
+                if (J[i].spec[b].role != PM_OUT || !jobs[i].host_bufs[b]) continue;
+                const char *o0 = (const char *)jobs[i].host_bufs[b], *o1 = o0 + buf_bytes(J[i].spec[b]);
+                if (o0 < sh[e].host + sh[e].bytes && sh[e].host < o1) keep[e] = false;
+            }
+    }
+    std::vector<int> renum(sh.size(), -1);
+    std::vector<SharedIn> kept;
+    for (size_t e = 0; e < sh.size(); e++)
+        if (keep[e]) {
+            renum[e] = (int)kept.size();
+            kept.push_back(sh[e]);
+        }
+    sh.swap(kept);
+    for (auto &j : J)
+        for (int &k : j.shared) k = k >= 0 ? renum[k] : -1;
+    return PM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+pm_status pm_run_host_batch_bytes(const pm_host_job *jobs, size_t njobs, uint64_t *h2d_bytes, uint64_t *d2h_bytes) {
+    std::vector<BatchJob> J;
+    std::vector<SharedIn> sh;
+    pm_status s = batch_plan("pm_run_host_batch_bytes", jobs, njobs, J, sh);
+    if (s) return s;
+    uint64_t in = 0, out = 0;
+    for (const SharedIn &e : sh) in += e.bytes;
+    for (size_t i = 0; i < njobs; i++)
+        for (size_t b = 0; b < J[i].spec.size(); b++) {
+            if (J[i].spec[b].role == PM_IN && J[i].shared[b] < 0) in += buf_bytes(J[i].spec[b]);
+            if (J[i].spec[b].role == PM_OUT && jobs[i].host_bufs[b]) out += buf_bytes(J[i].spec[b]);
+        }
+    if (h2d_bytes) *h2d_bytes = in;
+    if (d2h_bytes) *d2h_bytes = out;
+    return PM_OK;
+}
+
+pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_opts *opts, void *stream,
+                            pm_timing *out, double *copy_ms) {
+    if (njobs && (!jobs || !out)) return fail(PM_EINVAL, "pm_run_host_batch: jobs or out is NULL");
+    std::vector<BatchJob> J;
+    std::vector<SharedIn> sh;
+    pm_status s = batch_plan("pm_run_host_batch", jobs, njobs, J, sh);
+    if (s) return s;
+    if ((s = retain_staging_pool())) return s;
+    cudaStream_t cs = (cudaStream_t)stream;
     // does an output of job i overlap an input of job i + 1 in host memory?
     auto clash = [&](size_t i) {
         for (size_t a = 0; a < J[i].spec.size(); a++) {
             if (J[i].spec[a].role != PM_OUT || !jobs[i].host_bufs[a]) continue;
             const char *o0 = (const char *)jobs[i].host_bufs[a];
-            const char *o1 = o0 + J[i].spec[a].elems * dtype_size(J[i].spec[a].dtype);
+            const char *o1 = o0 + buf_bytes(J[i].spec[a]);
             for (size_t b = 0; b < J[i + 1].spec.size(); b++) {
                 if (J[i + 1].spec[b].role != PM_IN) continue;
                 const char *i0 = (const char *)jobs[i + 1].host_bufs[b];
-                const char *i1 = i0 + J[i + 1].spec[b].elems * dtype_size(J[i + 1].spec[b].dtype);
+                const char *i1 = i0 + buf_bytes(J[i + 1].spec[b]);
                 if (o0 < i1 && i0 < o1) return true;
             }
         }
@@ -318,7 +409,7 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
     if (rc == PM_OK) rc = ev.make(3 * njobs + 2);
     double kernels_ms = 0.0;
     for (size_t i = 0; i < njobs && rc == PM_OK; i++) {
-        Job &j = J[i];
+        BatchJob &j = J[i];
         cudaEvent_t e_in = ev.ev[3 * i], e_k = ev.ev[3 * i + 1], e_out = ev.ev[3 * i + 2];
         j.dev.assign(j.spec.size(), nullptr);
         if (i > 0) {
@@ -327,20 +418,37 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
             if (clash(i - 1)) cudaStreamWaitEvent(up, ev.ev[3 * (i - 1) + 2], 0);
         }
         if (i == 0) cudaEventRecord(ev.ev[3 * njobs], up);
+        std::vector<void *> bufs(j.spec.size(), nullptr);
         for (size_t b = 0; b < j.spec.size() && rc == PM_OK; b++) {
-            const size_t bytes = j.spec[b].elems * dtype_size(j.spec[b].dtype);
-            if (alloc_fault_injected() || cudaMallocAsync(&j.dev[b], bytes, up) != cudaSuccess)
+            const int k = j.shared[b];
+            if (k >= 0) {   // a shared input: copied by its first reader only
+                SharedIn &e = sh[k];
+                if (!e.dev) {
+                    if (alloc_fault_injected() || cudaMallocAsync(&e.dev, e.bytes, up) != cudaSuccess) {
+                        e.dev = nullptr;
+                        rc = fail(PM_ENOMEM, "pm_run_host_batch: job %zu: allocation of shared %s failed", i,
+                                  j.spec[b].name);
+                    } else if (cudaMemcpyAsync(e.dev, e.host, e.bytes, cudaMemcpyHostToDevice, up) != cudaSuccess)
+                        rc = fail(PM_ECUDA, "pm_run_host_batch: job %zu: host-to-device copy failed", i);
+                }
+                bufs[b] = e.dev;
+                continue;
+            }
+            const size_t bytes = buf_bytes(j.spec[b]);
+            if (alloc_fault_injected() || cudaMallocAsync(&j.dev[b], bytes, up) != cudaSuccess) {
+                j.dev[b] = nullptr;
                 rc = fail(PM_ENOMEM, "pm_run_host_batch: job %zu: allocation of %s failed", i, j.spec[b].name);
-            else if (j.spec[b].role == PM_IN &&
-                     cudaMemcpyAsync(j.dev[b], jobs[i].host_bufs[b], bytes, cudaMemcpyHostToDevice, up) != cudaSuccess)
+            } else if (j.spec[b].role == PM_IN &&
+                       cudaMemcpyAsync(j.dev[b], jobs[i].host_bufs[b], bytes, cudaMemcpyHostToDevice, up) != cudaSuccess)
                 rc = fail(PM_ECUDA, "pm_run_host_batch: job %zu: host-to-device copy failed", i);
+            bufs[b] = j.dev[b];
         }
         if (rc != PM_OK) break;
         cudaEventRecord(e_in, up);
         cudaStreamWaitEvent(cs, e_in, 0);
         if (i > 0) cudaStreamWaitEvent(cs, ev.ev[3 * (i - 1) + 2], 0);   // no kernel under a copy
         pm_timing t{};
-        rc = timed(j.kp, j.dev.data(), j.dev.size(), opts, stream, nullptr, &t);
+        rc = timed(j.kp, bufs.data(), bufs.size(), opts, stream, nullptr, &t);
         if (rc != PM_OK) {
             const std::string why = pm_last_error();
             fail(rc, "pm_run_host_batch: job %zu (%s): %s", i, j.kp.def->name, why.c_str());
@@ -352,13 +460,18 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
         cudaStreamWaitEvent(down, e_k, 0);
         for (size_t b = 0; b < j.spec.size() && rc == PM_OK; b++)
             if (j.spec[b].role == PM_OUT && jobs[i].host_bufs[b] &&
-                cudaMemcpyAsync(jobs[i].host_bufs[b], j.dev[b], j.spec[b].elems * dtype_size(j.spec[b].dtype),
-                                cudaMemcpyDeviceToHost, down) != cudaSuccess)
+                cudaMemcpyAsync(jobs[i].host_bufs[b], j.dev[b], buf_bytes(j.spec[b]), cudaMemcpyDeviceToHost, down) !=
+                    cudaSuccess)
                 rc = fail(PM_ECUDA, "pm_run_host_batch: job %zu: device-to-host copy failed", i);
         cudaEventRecord(e_out, down);
         for (void *d : j.dev)
             if (d) cudaFreeAsync(d, down);
         j.dev.clear();
+        for (SharedIn &e : sh)   // shared inputs whose last reader has run
+            if (e.last == i && e.dev) {
+                cudaFreeAsync(e.dev, down);
+                e.dev = nullptr;
+            }
     }
     if (up) cudaStreamSynchronize(up);
     if (down) {
@@ -369,6 +482,8 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
     for (auto &j : J)   // buffers of a job that failed before its output copy
         for (void *d : j.dev)
             if (d) cudaFree(d);
+    for (SharedIn &e : sh)   // shared inputs of a batch that stopped early
+        if (e.dev) cudaFree(e.dev);
     if (rc == PM_OK && copy_ms && njobs) {
         float total = 0;
         cudaEventElapsedTime(&total, ev.ev[3 * njobs], ev.ev[3 * njobs + 1]);

@@ -360,6 +360,34 @@ def test_run_host_batch_pipelines_and_orders_aliased_buffers():
     assert len(tms) == 3 and all(t["n_trials"] == 3 and t["mean_ms"] > 0 for t in tms) and copy_ms > 0
 
 
+def test_run_host_batch_shared_input_regions():
+    # several jobs read prefixes of the same host buffers (shared regions,
+    # copied once); a region that an earlier job's output writes is not
+    # shared, and its readers see the written values
+    dev()
+    N = 1 << 18
+    X, Y = pm_inputs.uniform((4 * N,), 101), pm_inputs.uniform((4 * N,), 102)
+    P = pm_inputs.uniform((N,), 103)
+    Z = np.zeros(2 * N, np.float32)
+    oa, ob, oc, o1, o2 = (np.zeros(n, np.float32) for n in (N, 2 * N, 2 * N, N, N))
+    jobs = [("stream", [X[:N], Y[:N], oa], dict(N=N, L=2, vec=1)),
+            ("stream", [X[:2 * N], ob], dict(N=2 * N, L=1, vec=1)),
+            ("stream", [X[:4 * N], None], dict(N=4 * N, L=1, vec=1)),     # output left on the device
+            ("stream", [Y[:2 * N], X[:2 * N], oc], dict(N=2 * N, L=2, vec=0)),
+            ("stream", [P, Z[:N]], dict(N=N, L=1, vec=1)),               # writes the host region read next
+            ("stream", [Z[:N], o1], dict(N=N, L=1, vec=1)),
+            ("stream", [Z[:N], o2], dict(N=N, L=1, vec=0))]
+    h2d, d2h = pm.run_host_batch_bytes(jobs)
+    # X once (4N), Y once (2N), P, and Z[:N] twice (not shared)
+    assert h2d == 4 * (4 * N + 2 * N + N + 2 * N) and d2h == 4 * (N + 2 * N + 2 * N + N + N + N)
+    tms, copy_ms = pm.run_host_batch(jobs, warmup=1, trials=2)
+    assert np.array_equal(oa, refs.stream([X[:N], Y[:N]]))
+    assert np.array_equal(ob, X[:2 * N])
+    assert np.array_equal(oc, refs.stream([Y[:2 * N], X[:2 * N]]))
+    assert np.array_equal(Z[:N], P) and np.array_equal(o1, P) and np.array_equal(o2, P)
+    assert len(tms) == 7 and all(t["n_trials"] == 2 for t in tms) and copy_ms > 0
+
+
 # DG tile (128 elements per CTA, D staged transposed in shared memory, the
 # u tile by one bulk copy): ragged Np (column padding) and ragged Nel (last
 # tile of 4..124 elements), guard bands checked by run_kernel
