@@ -17,8 +17,11 @@ Readings of the paper taken here where it is silent or ambiguous:
     max(l, m) * eps * sigma_max) is below m the minimum-norm solution in the
     column-scaled coordinates is returned with rank_deficient = True;
   * the LM start point, when not given, is the linear fit of the model with
-    every tanh switch replaced by 1/2 (negative entries clamped to
-    1e-3 * max |p|), and p_edge0 = 10 / median(t);
+    every tanh switch replaced by 1/2, and p_edge0 = 10 / median(t); a
+    coefficient that comes out non-positive is replaced by
+    1e-3 * sum_k t_k / sum_k |h_ki| (h_i its column of that linear design),
+    so that its term carries about 0.1 % of the outputs -- or, if the column
+    is zero (a parameter that only multiplies others), by 1e-3 * max |p|;
   * LM iterates in scaled coordinates q = p / |p0| (the minimiser does not
     depend on the coordinates).
 
@@ -100,7 +103,9 @@ def residual_and_jacobian(model, F, t):
 
 def start_point(model, F, t):
     """Start point: linear fit with every tanh(...) replaced by 0 (so each
-    s_hat is 1/2), negatives clamped, p_edge0 = 10 / median(t)."""
+    s_hat is 1/2); a non-positive coefficient becomes 1e-3 * sum(t) /
+    sum |its column| (1e-3 * max |p| for a zero column); p_edge0 = 10 /
+    median(t)."""
     lin = Model(model.out_feature, _strip_tanh(model.expr))
     t = np.asarray(t, dtype=np.float64)
     p = {}
@@ -108,8 +113,10 @@ def start_point(model, F, t):
         H = linear_design(lin, F)
         pl, _ = fit_linear(H, t)
         big = max(1e-300, float(np.max(np.abs(pl))))
-        for name, v in zip(lin.params, pl):
-            p[name] = v if v > 0 else 1e-3 * big
+        tsum = float(np.sum(t))
+        for i, (name, v) in enumerate(zip(lin.params, pl)):
+            cs = float(np.sum(np.abs(H[:, i])))
+            p[name] = v if v > 0 else (1e-3 * tsum / cs if cs > 0 else 1e-3 * big)
     for name in model.params:
         if name not in p:
             p[name] = 10.0 / float(np.median(t))

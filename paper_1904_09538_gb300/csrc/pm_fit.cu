@@ -242,6 +242,7 @@ struct Smem {
     int idx[MP];
     df Mf[MP][MP + 1], rhsf[MP], dinvf[MP];
     df redf[T / 32];
+    float redc[T / 32][MP + 1];   // per-warp column sums of the start design (and of t)
     df part[T];       // per row-group partial sums of the assembled entries
     double ssr, ssr_new, pred, lambda, med[2], noise, cond;
     int stop;
@@ -711,6 +712,41 @@ __device__ void linear_fit(Smem<T> &S, const FitJob &jb, int n, unsigned mask) {
     __syncthreads();
 }
 
+// Start-point column sums: S.redc[w][i] (i < m) = sum of |d g_start / d p_i|
+// at the origin over warp w's rows, S.redc[w][m] = sum of t over them (the
+// start code is loaded and S.s = 1).  Used to replace a non-positive start
+// coefficient by 1e-3 * sum t / sum |h_i|.
+template <int T>
+__device__ void start_column_sums(Smem<T> &S, const FitJob &jb, int n) {
+    const int m = jb.m, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    if (tid < m) S.qt[tid] = 0.0;
+    __syncthreads();
+    set_params(S, S.qt, m);
+    float cs[MP], ts = 0.0f;
+#pragma unroll
+    for (int i = 0; i < MP; i++) cs[i] = 0.0f;
+    df v[kMaxIns];
+    float adj[kMaxIns], g[MP];
+    for (int row = tid; row < jb.l; row += T) {
+        forward_df(S.code, S.cst, n, jb.X + (size_t)row * jb.nf, S.pd, v);
+        reverse_df(S.code, n, v, adj, g, m);
+#pragma unroll
+        for (int i = 0; i < MP; i++)
+            if (i < m) cs[i] += fabsf(g[i]);
+        ts += jb.t[row].x;
+    }
+#pragma unroll
+    for (int i = 0; i < MP; i++) {
+        if (i >= m) break;
+        float x = cs[i];
+        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
+        if (lane == 0) S.redc[warp][i] = x;
+    }
+    for (int o = 16; o; o >>= 1) ts += __shfl_xor_sync(0xffffffffu, ts, o);
+    if (lane == 0) S.redc[warp][m] = ts;
+    __syncthreads();
+}
+
 template <int T>
 __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitCfg cfg) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -760,15 +796,30 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
             if (lt <= k2 && k2 < lt + eq) S.med[1] = x;
         }
         __syncthreads();
+        // a non-positive start coefficient: its term set to carry about 0.1 %
+        // of the outputs, 1e-3 * sum t / sum |h_i|; a column that vanishes at
+        // the origin (a parameter that only multiplies others): 1e-3 * max |p|
+        bool clamp = false;
+        for (int i = 0; i < m; i++) clamp |= ((jb.start_mask >> i) & 1u) && !(S.q[i] > 0.0);
+        if (clamp) start_column_sums(S, jb, jb.n_start);
         if (tid == 0) {
             double big = 0.0;
             for (int i = 0; i < m; i++)
                 if ((jb.start_mask >> i) & 1u) big = fmax(big, fabs(S.q[i]));
             big = fmax(big, 1e-300);
+            double tsum = 0.0;
+            if (clamp)
+                for (int w = 0; w < T / 32; w++) tsum += (double)S.redc[w][m];
             const double pe = 10.0 / (0.5 * (S.med[0] + S.med[1]));
             for (int i = 0; i < m; i++) {
-                if ((jb.start_mask >> i) & 1u) S.q[i] = S.q[i] > 0.0 ? S.q[i] : 1e-3 * big;
-                else S.q[i] = pe;
+                if ((jb.start_mask >> i) & 1u) {
+                    if (S.q[i] > 0.0) continue;
+                    double cs = 0.0;
+                    for (int w = 0; w < T / 32; w++) cs += (double)S.redc[w][i];
+                    S.q[i] = cs > 0.0 ? 1e-3 * tsum / cs : 1e-3 * big;
+                } else {
+                    S.q[i] = pe;
+                }
             }
         }
         __syncthreads();

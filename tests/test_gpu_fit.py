@@ -278,6 +278,25 @@ def test_large_overlap_model_converges(sigma, seed, threads):
     assert np.max(np.abs(pred / pred_o - 1)) <= 1e-5
 
 
+@pytest.mark.parametrize("sigma,seed", [(1e-2, 31), (3e-2, 32)])
+def test_large_overlap_model_default_start(sigma, seed):
+    # the same nine-parameter problems from the default start point, where
+    # three coefficients of the start's linear fit come out negative and are
+    # replaced by 1e-3 sum(t) / sum |their column|: both fits stop at the
+    # same optimum
+    dev()
+    X = design(300, seed, nf=8)
+    t, om, F = synth(OVL_BIG, X, P_BIG, sigma, seed + 100)
+    m = pm.Model("f_wall_time", OVL_BIG)
+    p, rep = m.fit(X, t)
+    assert rep["status"] == 0 and rep["iterations"] < 200, rep
+    po, info = ofit.fit(om, F, t)
+    pred = m.predict(p, X)
+    pred_o = ofit.predict(om, po, F)
+    assert np.max(np.abs(pred / pred_o - 1)) <= 1e-5
+    assert rep["residual"] ** 2 <= info["residual"] ** 2 * (1 + 1e-6)
+
+
 def test_injected_allocation_failures_return_enomem():
     # pm_test_fail_allocation makes the n-th next allocation fail on the host
     # (no GPU fault): each entry point that allocates reports PM_ENOMEM,
