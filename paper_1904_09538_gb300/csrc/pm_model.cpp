@@ -394,7 +394,6 @@ pm_status pm_model_create(const char *out_feature, const char *expr, pm_model **
         }
     }
     mm->linear = homog(mm->code) == 1;
-    mm->start_linear = homog(mm->start_code) == 1;
     for (const Ins &in : mm->start_code)
         if (in.op == OP_PAR) mm->start_mask |= 1u << in.arg;
     *m = mm;

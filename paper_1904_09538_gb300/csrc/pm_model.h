@@ -44,7 +44,6 @@ struct pm_model {
     std::vector<pm::Ins> code;   // SSA program, last instruction is the result
     bool linear = false;         // g is homogeneous linear in the parameters
     std::vector<pm::Ins> start_code;  // same expression with tanh(.) -> 0 (start point)
-    bool start_linear = false;
     unsigned start_mask = 0;     // parameters that occur in start_code
     // device copy of `code` for the differentiation entry points (lazy)
     pm::Ins *d_code = nullptr;
