@@ -551,7 +551,7 @@ def e2e_measure(pm, S, variants, torch, trials, fit_and_predict, fit_sizes, step
 
 
 def fit_throughput(pm, torch, dev):
-    """Batched calibration (64 models, uneven 40..400 rows, one persistent
+    """Batched calibration (64 models of 4..12 parameters, uneven 40..400 rows, one persistent
     launch in a CUDA graph) vs the plain per-model fit (host-driven LM through
     the autograd.Function), same data, same start points."""
     import numpy as np
@@ -611,8 +611,8 @@ def oracle_fit_rate(seconds=5.0):
     import pm_inputs
     from oracle import fit as ofit
     from oracle.model import Model as OModel
-    from paper_1904_09538_gb300.fitbench import LIN, OVL, TRUTH, features
-    oms = [OModel("f_wall_time", LIN if k % 2 == 0 else OVL) for k in range(64)]
+    from paper_1904_09538_gb300.fitbench import TRUTH, features, model_expr
+    oms = [OModel("f_wall_time", model_expr(k)) for k in range(64)]
     Xs, _ = features(64, lambda k: len(oms[k].features))
     jobs = []
     for k, om in enumerate(oms):

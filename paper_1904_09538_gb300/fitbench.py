@@ -1,7 +1,7 @@
 """Time the batched calibration: python -m paper_1904_09538_gb300.fitbench
 [--models K] [--reps R] [--threads T]
 
-K models (alternately linear and tanh-overlap, 40..400 rows each, seeded
+K models (alternately linear and tanh-overlap, 4..12 parameters, 40..400 rows each, seeded
 synthetic features and model-plus-noise outputs) fitted in one batched plan
 (one persistent launch in a CUDA graph), R timed replays.  Prints one JSON
 line: fits per second, milliseconds per replay, status counts."""
@@ -13,13 +13,37 @@ import numpy as np
 
 
 LAUNCH = "p_launch * f_sync_kernel_launch + p_group * f_thread_groups"
-LIN = LAUNCH + " + p_add * f_op_float32_add + p_madd * f_op_float32_madd + p_gmem * f_mem_access_global_float32"
-_CG = "(p_gmem * f_mem_access_global_float32)"
-_CO = "(p_madd * f_op_float32_madd + p_lmem * f_mem_access_local_float32)"
-OVL = (LAUNCH + " + %s * (tanh(p_edge * (%s - %s)) + 1) / 2 + %s * (tanh(p_edge * (%s - %s)) + 1) / 2"
-       % (_CG, _CG, _CO, _CO, _CO, _CG))
+# (parameter, feature) terms the models draw from: global-memory terms and
+# on-chip terms (arithmetic, local memory)
+GMEM = [("p_gmem", "f_mem_access_global_float32"), ("p_g64", "f_mem_access_global_float64"),
+        ("p_gld", "f_mem_access_global_float32_load"), ("p_gst", "f_mem_access_global_float32_store"),
+        ("p_g16", "f_mem_access_global_bfloat16")]
+ONCHIP = [("p_madd", "f_op_float32_madd"), ("p_lmem", "f_mem_access_local_float32"), ("p_add", "f_op_float32_add"),
+          ("p_mul", "f_op_float32_mul"), ("p_d64", "f_op_float64_madd")]
 TRUTH = {"p_launch": 5e-6, "p_group": 2e-9, "p_add": 4e-12, "p_madd": 3e-12, "p_gmem": 6e-12, "p_lmem": 2e-12,
+         "p_mul": 5e-12, "p_g64": 9e-12, "p_gld": 5e-12, "p_gst": 7e-12, "p_g16": 4e-12, "p_d64": 2e-11,
          "p_edge": 3e4}
+
+
+def _sum(terms):
+    return " + ".join("%s * %s" % t for t in terms)
+
+
+def model_expr(k):
+    """Expression of problem k: even k a linear model with 4..12 parameters
+    (launch and work-group terms plus 2..10 cost terms), odd k a tanh-overlap
+    model (Section "Modeling Operation Overlap") with 5..12 parameters
+    (launch, work-group, p_edge, and 2..9 terms split between the global and
+    the on-chip cost), the parameter count cycling with k."""
+    if k % 2 == 0:
+        m = 4 + (k // 2) % 9
+        return LAUNCH + " + " + _sum((GMEM + ONCHIP)[:m - 2])
+    m = 5 + (k // 2) % 8
+    n = m - 3
+    cg = "(%s)" % _sum(GMEM[:(n + 1) // 2])
+    co = "(%s)" % _sum(ONCHIP[:n // 2])
+    return (LAUNCH + " + %s * (tanh(p_edge * (%s - %s)) + 1) / 2 + %s * (tanh(p_edge * (%s - %s)) + 1) / 2"
+            % (cg, cg, co, co, co, cg))
 
 
 def features(K, nfeat):
@@ -42,7 +66,7 @@ def problem(K):
     start points = 1.2 x the parameters the outputs were made with)."""
     import pm_inputs
     from . import Model
-    models = [Model("f_wall_time", LIN if k % 2 == 0 else OVL) for k in range(K)]
+    models = [Model("f_wall_time", model_expr(k)) for k in range(K)]
     Xs, ls = features(K, lambda k: len(models[k].features))
     ts, p0s = [], []
     for k, (m, X) in enumerate(zip(models, Xs)):

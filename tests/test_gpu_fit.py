@@ -408,3 +408,24 @@ def test_partial_overlap_model_default_start(p_edge, sigma, seed):
     assert abs(p[i] - po[om.params.index("p_part")]) <= 1e-3
     if sigma == 0.0:
         assert abs(p[i] - 0.4) <= 1e-3
+
+
+def test_fit_workload_batched_matches_oracle():
+    # the batched-fit workload the bench times: 64 models of 4..12
+    # parameters (linear and tanh-overlap), 40..400 rows, one batched plan;
+    # every fit converges and predicts what the oracle's fit predicts
+    dev()
+    from paper_1904_09538_gb300.fitbench import problem
+    models, Xs, ts, p0s, ls = problem(64)
+    assert {len(m.params) for m in models} == set(range(4, 13))
+    ps, reps = pm.fit_batched(models, Xs, ts, p0s)
+    assert all(r["status"] == 0 for r in reps), [r["status"] for r in reps]
+    worst = 0.0
+    for m, X, t, p0, p in zip(models, Xs, ts, p0s, ps):
+        om = OModel("f_wall_time", m.expr)
+        F = [dict(zip(om.features, row)) for row in X]
+        po, _ = ofit.fit(om, F, t, p0=p0)
+        pred = m.predict(p, X)
+        pred_o = np.asarray(ofit.predict(om, po, F))
+        worst = max(worst, float(np.max(np.abs(pred / pred_o - 1))))
+    assert worst <= 1e-5, worst
