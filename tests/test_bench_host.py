@@ -222,3 +222,10 @@ def test_overlap_model_choice_rules():
     assert choose_by_residual({"linear": 0.8, "nonlinear": 0.87}) == "linear"
     assert choose_by_residual({"linear": None, "nonlinear": 0.87}) == "nonlinear"
     assert choose_by_residual({}) is None
+
+
+def test_experiments_cli_rejects_unknown_part():
+    import subprocess
+    r = subprocess.run([sys.executable, "-m", "paper_1904_09538_gb300.experiments", "--only=bogus"],
+                       cwd=ROOT, capture_output=True, text=True, timeout=120)
+    assert r.returncode != 0 and "unknown part 'bogus'" in r.stderr
