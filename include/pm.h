@@ -321,6 +321,15 @@ typedef struct {
     double xtol;             /* stop when |dq| <= xtol (|q| + xtol) in scaled coordinates (default 1e-12) */
     int32_t use_p0;          /* 1: p_inout holds the start point; 0: library start point */
 } pm_fit_opts;
+/* The library start point (Section "Computing Model Parameters" leaves it
+ * open): the linear least-squares fit of the model with every tanh(.)
+ * replaced by 0 (each switch at 1/2); a coefficient that comes out <= 0
+ * becomes 1e-3 * sum_k t_k / sum_k |h_ki| (h_i its column of that linear
+ * design at the origin), or 1e-3 * max |p| when that column is zero; every
+ * parameter absent from that design (p_edge) starts at 10 / median(t).  The
+ * LM then damps by lambda * dmax_i on the diagonal of J^T J (dmax_i the
+ * largest value met so far), lambda from 1e-3, /10 on an accepted step, x10
+ * on a rejected one (at most 16 per iteration). */
 
 typedef struct {
     int32_t status;          /* pm_status of this fit */
