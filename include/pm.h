@@ -316,7 +316,8 @@ pm_status pm_model_is_linear(const pm_model *m, int32_t *linear);
 pm_status pm_feature_values(const pm_model *m, const pm_feature *feats, size_t nfeat, double *row_out);
 
 typedef struct {
-    int32_t max_iter;        /* LM iteration cap (default 200) */
+    int32_t max_iter;        /* LM iteration cap (default 200); 0: no iteration, a nonlinear
+                                fit returns its start point with PM_ENOTCONV */
     double ftol;             /* stop when relative SSR decrease < ftol (default 1e-15) */
     double xtol;             /* stop when |dq| <= xtol (|q| + xtol) in scaled coordinates (default 1e-12) */
     int32_t use_p0;          /* 1: p_inout holds the start point; 0: library start point */

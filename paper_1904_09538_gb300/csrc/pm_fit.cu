@@ -1134,7 +1134,7 @@ pm_status check_opts(const pm_fit_opts *o, FitCfg &cfg, int &use_p0) {
     cfg.xtol = 1e-12;
     use_p0 = 0;
     if (o) {
-        if (o->max_iter < 1 || o->max_iter > 100000) return fail(PM_EINVAL, "fit: max_iter must be 1..100000");
+        if (o->max_iter < 0 || o->max_iter > 100000) return fail(PM_EINVAL, "fit: max_iter must be 0..100000");
         if (!(o->ftol >= 0) || !(o->xtol >= 0)) return fail(PM_EINVAL, "fit: ftol and xtol must be >= 0");
         cfg.max_iter = o->max_iter;
         cfg.ftol = o->ftol;

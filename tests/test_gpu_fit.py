@@ -467,3 +467,36 @@ def test_fit_workload_batched_matches_oracle():
         pred_o = np.asarray(ofit.predict(om, po, F))
         worst = max(worst, float(np.max(np.abs(pred / pred_o - 1))))
     assert worst <= 1e-5, worst
+
+
+def test_start_point_matches_oracle():
+    # max_iter = 0 returns the library start point: the linear fit with every
+    # tanh switch at 1/2, non-positive coefficients replaced by 1e-3 sum(t) /
+    # sum |column| (1e-3 max |p| for a zero column), p_edge = 10 / median(t);
+    # cases: no replacement, three replaced (the nine-parameter model), and a
+    # column zero at the origin (p_part of the partial-overlap model)
+    dev()
+    from paper_1904_09538_gb300 import suite as S
+    cases = []
+    X = design(150, 9, nf=5)
+    cases.append((OVL, X, synth(OVL, X, P_OVL, 1e-3, 10)[0]))
+    X = design(300, 31, nf=8)
+    cases.append((OVL_BIG, X, synth(OVL_BIG, X, P_BIG, 1e-2, 131)[0]))
+    expr = S.overlap_model(partial=True)
+    mp = pm.Model("f_wall_time", expr)
+    X = np.stack([mp.feature_values("overlap", m=mm, N=N) for mm in range(33) for N in (2 ** 26, 2 ** 27)])
+    truth = dict(p_launch=1.2e-5, p_gmem=1.2e-12, p_lmem=3e-12, p_edge=1e5, p_part=0.4)
+    cases.append((expr, X, synth(expr, X, truth, 1e-2, 41)[0]))
+    replaced = []
+    for expr, X, t in cases:
+        m = pm.Model("f_wall_time", expr)
+        om = OModel("f_wall_time", expr)
+        F = [dict(zip(om.features, row)) for row in X]
+        p, rep = m.fit(X, t, max_iter=0)
+        assert rep["status"] == -4 and rep["iterations"] == 0
+        po = ofit.start_point(om, F, t)
+        assert perr(p, po) <= 1e-5, (expr[:40], perr(p, po), p, po)
+        lin = OModel("f_wall_time", ofit._strip_tanh(expr))
+        pl, _ = ofit.fit_linear(ofit.linear_design(lin, F), t)
+        replaced.append(int(np.sum(pl <= 0)))
+    assert replaced[0] == 0 and replaced[1] == 3 and replaced[2] >= 1
