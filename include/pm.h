@@ -326,7 +326,8 @@ typedef struct {
  * open): the linear least-squares fit of the model with every tanh(.)
  * replaced by 0 (each switch at 1/2); a coefficient that comes out <= 0
  * becomes 1e-3 * sum_k t_k / sum_k |h_ki| (h_i its column of that linear
- * design at the origin), or 1e-3 * max |p| when that column is zero; every
+ * design at the origin; for a column zero there, its column at the point
+ * reached so far, and 1e-3 * max |p| if that is zero too); every
  * parameter absent from that design (p_edge) starts at 10 / median(t).  The
  * LM then damps by lambda * dmax_i on the diagonal of J^T J (dmax_i the
  * largest value met so far), lambda from 1e-3, /10 on an accepted step, x10

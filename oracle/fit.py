@@ -20,8 +20,10 @@ Readings of the paper taken here where it is silent or ambiguous:
     every tanh switch replaced by 1/2, and p_edge0 = 10 / median(t); a
     coefficient that comes out non-positive is replaced by
     1e-3 * sum_k t_k / sum_k |h_ki| (h_i its column of that linear design),
-    so that its term carries about 0.1 % of the outputs -- or, if the column
-    is zero (a parameter that only multiplies others), by 1e-3 * max |p|;
+    so that its term carries about 0.1 % of the outputs; for a column that
+    is zero at the origin (a parameter that only multiplies others) the same
+    rule uses its column at the point reached so far (1e-3 * max |p| if that
+    is zero too);
   * LM iterates in scaled coordinates q = p / |p0| (the minimiser does not
     depend on the coordinates).
 
@@ -104,8 +106,9 @@ def residual_and_jacobian(model, F, t):
 def start_point(model, F, t):
     """Start point: linear fit with every tanh(...) replaced by 0 (so each
     s_hat is 1/2); a non-positive coefficient becomes 1e-3 * sum(t) /
-    sum |its column| (1e-3 * max |p| for a zero column); p_edge0 = 10 /
-    median(t)."""
+    sum |its column| (for a column zero at the origin, its column at the
+    point reached so far; 1e-3 * max |p| if that is zero too); p_edge0 =
+    10 / median(t)."""
     lin = Model(model.out_feature, _strip_tanh(model.expr))
     t = np.asarray(t, dtype=np.float64)
     p = {}
@@ -114,9 +117,26 @@ def start_point(model, F, t):
         pl, _ = fit_linear(H, t)
         big = max(1e-300, float(np.max(np.abs(pl))))
         tsum = float(np.sum(t))
+        zero = []
         for i, (name, v) in enumerate(zip(lin.params, pl)):
             cs = float(np.sum(np.abs(H[:, i])))
-            p[name] = v if v > 0 else (1e-3 * tsum / cs if cs > 0 else 1e-3 * big)
+            if v > 0:
+                p[name] = v
+            elif cs > 0:
+                p[name] = 1e-3 * tsum / cs
+            else:
+                p[name] = 0.0
+                zero.append(i)
+        if zero:
+            # a column that vanishes at the origin (a parameter that only
+            # multiplies others): the same rule on its column at the point
+            # reached so far (those parameters at 0)
+            q = dict(p)
+            cz = np.zeros(len(lin.params))
+            for f in F:
+                cz += np.abs(np.asarray(lin.grad(q, f)[1]))
+            for i in zero:
+                p[lin.params[i]] = 1e-3 * tsum / cz[i] if cz[i] > 0 else 1e-3 * big
     for name in model.params:
         if name not in p:
             p[name] = 10.0 / float(np.median(t))

@@ -253,6 +253,8 @@ struct Smem {
     df Mf[MP][MP + 1], rhsf[MP], dinvf[MP];
     df redf[T / 32];
     float redc[T / 32][MP + 1];   // per-warp column sums of the start design (and of t)
+    double sbig;                  // start point: max |p| of its linear fit
+    unsigned zmask;               // start point: parameters whose column is zero at the origin
     df part[T];       // per row-group partial sums of the assembled entries
     double ssr, ssr_new, pred, lambda, med[2], noise, cond;
     int stop;
@@ -723,15 +725,13 @@ __device__ void linear_fit(Smem<T> &S, const FitJob &jb, int n, unsigned mask) {
 }
 
 // Start-point column sums: S.redc[w][i] (i < m) = sum of |d g_start / d p_i|
-// at the origin over warp w's rows, S.redc[w][m] = sum of t over them (the
-// start code is loaded and S.s = 1).  Used to replace a non-positive start
-// coefficient by 1e-3 * sum t / sum |h_i|.
+// at the point `at` over warp w's rows, S.redc[w][m] = sum of t over them
+// (the start code is loaded and S.s = 1).  Used to replace a non-positive
+// start coefficient by 1e-3 * sum t / sum |h_i|.
 template <int T>
-__device__ void start_column_sums(Smem<T> &S, const FitJob &jb, int n) {
+__device__ void start_column_sums(Smem<T> &S, const FitJob &jb, int n, const double *at) {
     const int m = jb.m, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    if (tid < m) S.qt[tid] = 0.0;
-    __syncthreads();
-    set_params(S, S.qt, m);
+    set_params(S, at, m);
     float cs[MP], ts = 0.0f;
 #pragma unroll
     for (int i = 0; i < MP; i++) cs[i] = 0.0f;
@@ -807,11 +807,17 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
         }
         __syncthreads();
         // a non-positive start coefficient: its term set to carry about 0.1 %
-        // of the outputs, 1e-3 * sum t / sum |h_i|; a column that vanishes at
-        // the origin (a parameter that only multiplies others): 1e-3 * max |p|
+        // of the outputs, 1e-3 * sum t / sum |h_i| (h_i its column at the
+        // origin); a column that vanishes there (a parameter that only
+        // multiplies others): the same rule on its column at the point
+        // reached so far, 1e-3 * max |p| if that vanishes too
         bool clamp = false;
         for (int i = 0; i < m; i++) clamp |= ((jb.start_mask >> i) & 1u) && !(S.q[i] > 0.0);
-        if (clamp) start_column_sums(S, jb, jb.n_start);
+        if (clamp) {
+            if (tid < m) S.qt[tid] = 0.0;
+            __syncthreads();
+            start_column_sums(S, jb, jb.n_start, S.qt);
+        }
         if (tid == 0) {
             double big = 0.0;
             for (int i = 0; i < m; i++)
@@ -821,18 +827,40 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
             if (clamp)
                 for (int w = 0; w < T / 32; w++) tsum += (double)S.redc[w][m];
             const double pe = 10.0 / (0.5 * (S.med[0] + S.med[1]));
+            unsigned zm = 0u;
             for (int i = 0; i < m; i++) {
                 if ((jb.start_mask >> i) & 1u) {
                     if (S.q[i] > 0.0) continue;
                     double cs = 0.0;
                     for (int w = 0; w < T / 32; w++) cs += (double)S.redc[w][i];
-                    S.q[i] = cs > 0.0 ? 1e-3 * tsum / cs : 1e-3 * big;
+                    if (cs > 0.0) {
+                        S.q[i] = 1e-3 * tsum / cs;
+                    } else {
+                        S.q[i] = 0.0;
+                        zm |= 1u << i;
+                    }
                 } else {
                     S.q[i] = pe;
                 }
             }
+            S.zmask = zm;
+            S.sbig = big;
         }
         __syncthreads();
+        if (S.zmask) {
+            start_column_sums(S, jb, jb.n_start, S.q);
+            if (tid == 0) {
+                double tsum = 0.0;
+                for (int w = 0; w < T / 32; w++) tsum += (double)S.redc[w][m];
+                for (int i = 0; i < m; i++) {
+                    if (!((S.zmask >> i) & 1u)) continue;
+                    double cs = 0.0;
+                    for (int w = 0; w < T / 32; w++) cs += (double)S.redc[w][i];
+                    S.q[i] = cs > 0.0 ? 1e-3 * tsum / cs : 1e-3 * S.sbig;
+                }
+            }
+            __syncthreads();
+        }
     } else {
         if (tid < m) S.q[tid] = jb.p[tid];
         __syncthreads();

@@ -197,13 +197,14 @@ def test_fit_rows_is_fit_on_plain_data():
 def test_start_point_rules():
     # linear fit of the model with every tanh switch at 1/2: exact here for
     # p_a; p_b comes out negative and becomes 1e-3 sum(t) / sum |f_y|; p_c
-    # only multiplies p_a (its column is zero at the origin) and becomes
-    # 1e-3 max |p|; p_edge starts at 10 / median(t)
+    # only multiplies p_a (its column is zero at the origin): the same rule on
+    # its column at the point reached so far, p_a * f_z; p_edge starts at
+    # 10 / median(t)
     m = Model("t", "p_a * f_x + p_b * f_y + p_c * p_a * f_z + tanh(p_edge * f_x) * 0")
     F = [{"f_x": float(x), "f_y": float(y), "f_z": 1.0} for x, y in ((1, 5), (2, 1), (3, 7), (4, 2))]
     t = np.array([1e-6 * f["f_x"] - 1e-9 * f["f_y"] for f in F])
     p0 = dict(zip(m.params, ofit.start_point(m, F, t)))
     assert p0["p_a"] == pytest.approx(1e-6, rel=1e-9)
     assert p0["p_b"] == pytest.approx(1e-3 * t.sum() / 15.0, rel=1e-12)
-    assert p0["p_c"] == pytest.approx(1e-3 * 1e-6, rel=1e-9)
+    assert p0["p_c"] == pytest.approx(1e-3 * t.sum() / (4 * p0["p_a"]), rel=1e-9)
     assert p0["p_edge"] == pytest.approx(10.0 / np.median(t), rel=1e-12)
