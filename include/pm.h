@@ -185,6 +185,7 @@ typedef struct {
 pm_status pm_counts_desc(const char *description, const pm_param *p, size_t np, const pm_interp *interp,
                          size_t ninterp, pm_feature *out, size_t cap, size_t *n_out);
 
+
 /* Compiled resources and launch shape of one kernel instance, for an
  * autotuner's pruning step (the paper's use of a model as a heuristic that
  * narrows the variants worth timing, Section "Assumptions and Limitations"):
@@ -331,7 +332,14 @@ typedef struct {
  * parameter absent from that design (p_edge) starts at 10 / median(t).  The
  * LM then damps by lambda * dmax_i on the diagonal of J^T J (dmax_i the
  * largest value met so far), lambda from 1e-3, /10 on an accepted step, x10
- * on a rejected one (at most 16 per iteration). */
+ * on a rejected one (at most 16 per iteration; 16 rejections end the fit).
+ * A trial is accepted when its SSR is not larger, or when its predicted
+ * decrease is below the SSR's noise floor (4e-13 sqrt(l SSR): float-float
+ * residuals), where only the gradient can still direct the step.  The fit
+ * stops when |dq| <= xtol (|q| + xtol); when such unverifiable steps have
+ * become negligible (max |dq_i| <= 1e-9 max(max |q_i|, 1)) or four of them
+ * came in a row; or when a measurable relative SSR decrease is below
+ * ftol. */
 
 typedef struct {
     int32_t status;          /* pm_status of this fit */
@@ -351,8 +359,11 @@ typedef struct {
  * X is l x n_features row-major (host, FP64 feature values), t the l output
  * values (host).  Minimises sum_k (1 - g(p; X_k)/t_k)^2 (relative error,
  * scale_features_by_output).  Linear-in-p models: column-scaled least
- * squares (FP64 solve on the GPU); otherwise Levenberg-Marquardt on the GPU
- * (FP32 residual and Jacobian, FP64 normal-equation solve and damping).
+ * squares (normal equations in float-float with iterative refinement on the
+ * GPU); otherwise Levenberg-Marquardt on the GPU (float-float residuals and
+ * FP32 Jacobian on the FP32 pipes, J^T J and J^T r accumulated with exact
+ * products and compensated sums, the damped normal equations solved in
+ * float-float, damping and stopping decisions in FP64).
  * p_inout: n_params doubles (start point if opts->use_p0, result out).
  * Returns PM_ERANK (minimum-norm solution written) or PM_ENOTCONV (best
  * iterate written) where applicable. */
@@ -382,47 +393,99 @@ pm_status pm_fit_batched(const pm_model *const *models, size_t nmodels, const do
                          double *p_inout_concat, pm_fit_report *reports, void *stream);
 
 /* Allocation-free batched calibration.  The paper has no counterpart; this
- * entry point exists for callers that must not allocate GPU memory -- for
- * example code that runs while a stream is being captured into a CUDA graph
- * (where cudaMalloc is not allowed), real-time loops that cannot afford the
- * device-wide synchronisation an allocation may cause, or processes whose
- * device memory is entirely reserved by another framework's allocator.
+ * entry point exists for callers that must not allocate GPU memory: a
+ * process whose device memory is entirely reserved by another framework's
+ * pooling allocator (a cudaMalloc there fails or evicts the pool's cache),
+ * or a latency-critical loop that cannot afford the device-wide
+ * synchronisation that cudaMalloc and cudaFree may cause.
  *
  * Same arguments, layout and results as pm_fit_batched (host arrays; CTA
  * size 128).  Instead of allocating, it stages the models' programs, the
  * data (FP64 and float-float copies), the parameters and the reports in one
  * static device array of PM_NOALLOC_SCRATCH_BYTES bytes that every GPU which
  * loads the library keeps until the process exits.  It calls no cudaMalloc,
- * cudaFree or other allocating routine.
+ * cudaFree or other allocating routine, and no host allocator either (the
+ * job table is built in a static host array).
  *   - Requests whose staged size exceeds PM_NOALLOC_SCRATCH_BYTES, or with
  *     more than 256 models, fail with PM_EINVAL and a message giving the
- *     size needed; nothing is launched then.
+ *     size needed; nothing is launched then.  A non-finite start point (with
+ *     opts->use_p0), feature value or output fails with PM_EINVAL too.
  *   - The first call on a device looks up the array's device address
- *     (cudaGetSymbolAddress) with that device current; make that first call
- *     before any stream capture begins.
+ *     (cudaGetSymbolAddress) with that device current and keeps it for the
+ *     life of the process.  A cudaDeviceReset in this process invalidates
+ *     that address: do not call this entry point after one.
  *   - Every call on a device shares the one array and leaves its contents
  *     behind; each call rewrites everything it reads.  Calls whose work
- *     overlaps on the GPU (other host threads, other streams) race on the
- *     array: serialise them.
- *   - Blocks until the results are on the host. */
+ *     overlapped on the GPU would race on the array, so the library
+ *     serialises them: a process-wide lock is held from the first upload
+ *     until the results are on the host.
+ *   - Blocks: it synchronises `stream` before returning (the results are
+ *     copied to host memory).  It must therefore not be called while
+ *     `stream` is being captured into a CUDA graph. */
 #define PM_NOALLOC_SCRATCH_BYTES (8u << 20)
 pm_status pm_fit_batched_noalloc(const pm_model *const *models, size_t nmodels, const double *X_concat,
                                  const double *t_concat, const size_t *rows, const pm_fit_opts *opts,
                                  double *p_inout_concat, pm_fit_report *reports, void *stream);
 
-/* Differentiation entry points (device pointers; used by the PyTorch
- * autograd.Function).  X: l x n_features FP32, t: l FP32, p: n_params FP64.
- *   pm_residual:  r_k = 1 - g(p; X_k) / t_k                       (FP32)
- *   pm_residual_vjp: pbar_i = sum_k rbar_k dr_k/dp_i              (FP32 products,
- *                 FP32 compensated sums per CTA, combined in FP64; pbar overwritten)
- *   pm_jacobian:  J[k, i] = dr_k/dp_i = -dg/dp_i / t_k            (l x n_params FP32)
- * Reverse-mode differentiation of the model program, no finite differences. */
-pm_status pm_residual(const pm_model *m, const float *X, const float *t, size_t l, const double *p,
-                      float *r, void *stream);
-pm_status pm_residual_vjp(const pm_model *m, const float *X, const float *t, size_t l, const double *p,
-                          const float *rbar, double *pbar, void *stream);
-pm_status pm_jacobian(const pm_model *m, const float *X, const float *t, size_t l, const double *p,
+/* Differentiation entry points (Section "Computing Model Parameters": the
+ * model's derivatives with respect to its parameters, obtained here by
+ * reverse-mode differentiation of the model program instead of symbolic
+ * differentiation).  Device pointers; used by the PyTorch autograd.Function.
+ *   X: l x n_features FP64 row-major, t: l FP64 (> 0), p: n_params FP64.
+ * Per row the model program runs in float-float arithmetic on the FP32 pipes
+ * (each FP64 input split into a hi + lo pair of floats, about 48 bits).
+ *   pm_residual:  r_k = 1 - g(p; X_k) / t_k                        (r: l FP64)
+ *   pm_residual_vjp: pbar_i = sum_k rbar_k dr_k/dp_i               (rbar: l FP64,
+ *                 pbar: n_params FP64, overwritten; float-float reverse sweep and
+ *                 products, compensated sums per CTA, combined across CTAs with
+ *                 FP64 atomics, so the last bits may differ between runs)
+ *   pm_jacobian:  J[k, i] = dr_k/dp_i = -dg/dp_i / t_k             (l x n_params FP32:
+ *                 FP32 reverse sweep over the high parts; it steers LM steps)
+ * All three are asynchronous on `stream`; l = 0 is a no-op (pbar zeroed).
+ * PM_EINVAL for NULL pointers. */
+pm_status pm_residual(const pm_model *m, const double *X, const double *t, size_t l, const double *p,
+                      double *r, void *stream);
+pm_status pm_residual_vjp(const pm_model *m, const double *X, const double *t, size_t l, const double *p,
+                          const double *rbar, double *pbar, void *stream);
+pm_status pm_jacobian(const pm_model *m, const double *X, const double *t, size_t l, const double *p,
                       float *J, void *stream);
+
+/* Plain Levenberg-Marquardt calibration of one model at a time (Section
+ * "Computing Model Parameters"), driven by the caller: the library does the
+ * arithmetic of each step, the caller evaluates the residual and its
+ * derivatives at the points the library names (pm_residual,
+ * pm_residual_vjp, pm_jacobian -- in Python through the autograd.Function)
+ * and reads one status word per trial.  Same damping and stopping rules as
+ * the batched fit (see pm_fit_opts), with the step solve in FP64.
+ *
+ *   state:  caller-owned device buffer of PM_LM_STATE_BYTES bytes, opaque.
+ *   pm_lm_init:   start point p0 (host, n_params FP64, finite); writes p0
+ *                 to the device array p (n_params FP64); opts as for pm_fit
+ *                 (use_p0 ignored: p0 is always given; NULL = defaults).
+ *   pm_lm_step:   r (l FP64), b = J^T r (n_params FP64, from
+ *                 pm_residual_vjp with rbar = r) and J (l x n_params FP32),
+ *                 all at the current point p: on the first call after
+ *                 pm_lm_init or after an accepted step they are assembled
+ *                 into the scaled normal equations (later calls ignore them);
+ *                 then the damped system is solved and the trial point
+ *                 written to p_try (device, n_params FP64).
+ *   pm_lm_update: r_try (l FP64), the residual at p_try: accepts or rejects
+ *                 the trial, updates the damping, writes the current point
+ *                 to p, and writes flags (device int32[2]) = {status,
+ *                 accepted}: status 1 = running, PM_OK = converged,
+ *                 PM_ENOTCONV = iteration limit.
+ *   pm_lm_report: copies the state to the host (synchronises stream) and
+ *                 fills a pm_fit_report (cond is NaN: not estimated).
+ * init, step and update are asynchronous on `stream`; init's copies read
+ * host memory that may be reused once it returns.  PM_EINVAL for NULL
+ * pointers, l = 0, non-finite start points or negative options. */
+#define PM_LM_STATE_BYTES 4096
+pm_status pm_lm_init(const pm_model *m, const double *p0, const pm_fit_opts *opts, void *state, double *p,
+                     void *stream);
+pm_status pm_lm_step(void *state, const double *r, const double *b, const float *J, size_t l, double *p_try,
+                     void *stream);
+pm_status pm_lm_update(void *state, const double *r_try, size_t l, double *p, int32_t *flags, void *stream);
+pm_status pm_lm_report(const void *state, pm_fit_report *report, void *stream);
 
 /* Predict (Section "Predicting Cost"): t_out[k] = g(p; X_k) for l rows,
  * evaluated on the GPU in FP64.  X host l x n_features, p host, t_out host. */

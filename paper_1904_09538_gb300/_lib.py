@@ -104,6 +104,10 @@ SIGNATURES = {
     "pm_residual": (i32, [vp, vp, vp, c_size_t, vp, vp, vp]),
     "pm_residual_vjp": (i32, [vp, vp, vp, c_size_t, vp, vp, vp, vp]),
     "pm_jacobian": (i32, [vp, vp, vp, c_size_t, vp, vp, vp]),
+    "pm_lm_init": (i32, [vp, dp, P(pm_fit_opts), vp, vp, vp]),
+    "pm_lm_step": (i32, [vp, vp, vp, vp, c_size_t, vp, vp]),
+    "pm_lm_update": (i32, [vp, vp, c_size_t, vp, vp, vp]),
+    "pm_lm_report": (i32, [vp, P(pm_fit_report), vp]),
     "pm_predict": (i32, [vp, dp, dp, c_size_t, dp]),
 }
 

@@ -2,12 +2,17 @@
 
 Residual.apply(p, model, X, t) -> r with r_k = 1 - g(p; X_k) / t_k, computed
 by the library's residual kernel; its backward is the library's adjoint
-(vector-Jacobian product) kernel, reverse-mode over the model program.
+(vector-Jacobian product) kernel, reverse-mode over the model program.  X
+(l x n_features), t (l) and p are float64 CUDA tensors; the kernels evaluate
+in float-float arithmetic on the FP32 pipes.
 
-lm_fit() is the plain per-model calibration: a host-driven Levenberg-Marquardt
-loop (one model at a time) whose J^T r comes from autograd through Residual
-and whose J^T J comes from the adjoint kernel applied to J's columns
-(Section "Computing Model Parameters").  The batched persistent-kernel path
+lm_fit() is the plain per-model calibration (Section "Computing Model
+Parameters"): a host-driven Levenberg-Marquardt loop over one model at a
+time.  Each iteration takes J^T r from autograd through Residual (the adjoint
+kernel), J from the Jacobian kernel, and hands them to the library's step
+(pm_lm_step: damped normal-equation solve) and update (pm_lm_update: SSR,
+accept / reject, damping, stopping) calls; the loop reads one status word per
+trial and does no arithmetic itself.  The batched persistent-kernel path
 (FitPlan) computes the same fit in one launch for many models.
 """
 import ctypes
@@ -15,22 +20,32 @@ import ctypes
 import numpy as np
 import torch
 
-from ._lib import lib, check
+from ._lib import lib, check, pm_fit_opts, pm_fit_report
+
+LM_STATE_BYTES = 4096
+LM_RUNNING = 1
 
 
 def _cs():
     return ctypes.c_void_p(torch.cuda.current_stream().cuda_stream)
 
 
+def _ptr(x):
+    return ctypes.c_void_p(x.data_ptr())
+
+
+def _check_inputs(p, X, t):
+    if not (p.is_cuda and p.dtype == torch.float64 and X.dtype == torch.float64 and t.dtype == torch.float64):
+        raise TypeError("Residual: p, X and t float64 CUDA tensors")
+
+
 class Residual(torch.autograd.Function):
     @staticmethod
     def forward(ctx, p, model, X, t):
-        if not (p.is_cuda and p.dtype == torch.float64 and X.dtype == torch.float32 and t.dtype == torch.float32):
-            raise TypeError("Residual: p float64, X and t float32, all CUDA")
+        _check_inputs(p, X, t)
         p, X, t = p.contiguous(), X.contiguous(), t.contiguous()
-        r = torch.empty(t.shape[0], dtype=torch.float32, device=t.device)
-        check(lib().pm_residual(model.handle, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(t.data_ptr()),
-                                t.shape[0], ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(r.data_ptr()), _cs()))
+        r = torch.empty(t.shape[0], dtype=torch.float64, device=t.device)
+        check(lib().pm_residual(model.handle, _ptr(X), _ptr(t), t.shape[0], _ptr(p), _ptr(r), _cs()))
         ctx.save_for_backward(p, X, t)
         ctx.model = model
         return r
@@ -38,11 +53,10 @@ class Residual(torch.autograd.Function):
     @staticmethod
     def backward(ctx, rbar):
         p, X, t = ctx.saved_tensors
-        rbar = rbar.contiguous().to(torch.float32)
+        rbar = rbar.contiguous().to(torch.float64)
         pbar = torch.empty_like(p)
-        check(lib().pm_residual_vjp(ctx.model.handle, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(t.data_ptr()),
-                                    t.shape[0], ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(rbar.data_ptr()),
-                                    ctypes.c_void_p(pbar.data_ptr()), _cs()))
+        check(lib().pm_residual_vjp(ctx.model.handle, _ptr(X), _ptr(t), t.shape[0], _ptr(p), _ptr(rbar),
+                                    _ptr(pbar), _cs()))
         return pbar, None, None, None
 
 
@@ -52,71 +66,46 @@ def residual(model, X, t, p):
 
 def jacobian(model, X, t, p):
     """J[k, i] = dr_k/dp_i (FP32, l x m) from the Jacobian kernel."""
+    _check_inputs(p, X, t)
     J = torch.empty((t.shape[0], len(model.params)), dtype=torch.float32, device=t.device)
-    check(lib().pm_jacobian(model.handle, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(t.data_ptr()), t.shape[0],
-                            ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(J.data_ptr()), _cs()))
+    check(lib().pm_jacobian(model.handle, _ptr(X), _ptr(t), t.shape[0], _ptr(p), _ptr(J), _cs()))
     return J
 
 
-def _jtv(model, X, t, p, v):
-    pbar = torch.empty_like(p)
-    v = v.contiguous().to(torch.float32)
-    check(lib().pm_residual_vjp(model.handle, ctypes.c_void_p(X.data_ptr()), ctypes.c_void_p(t.data_ptr()),
-                                t.shape[0], ctypes.c_void_p(p.data_ptr()), ctypes.c_void_p(v.data_ptr()),
-                                ctypes.c_void_p(pbar.data_ptr()), _cs()))
-    return pbar
-
-
-def lm_fit(model, X, t, p0, max_iter=200, xtol=1e-12):
+def lm_fit(model, X, t, p0, max_iter=200, ftol=1e-15, xtol=1e-12):
     """Plain per-model Levenberg-Marquardt through the autograd.Function.
 
-    X: (l, nf) float32 CUDA, t: (l,) float32 CUDA, p0: start point (m,).
-    Scaled coordinates q = p / |p0|, Marquardt damping diag(J^T J), lambda
-    x10 on rejection, /10 on acceptance; steps whose predicted SSR decrease is
-    below the FP32 noise floor are accepted and end the fit.  Returns
-    (p as numpy, iterations)."""
+    X: (l, nf) float64 CUDA, t: (l,) float64 CUDA, p0: start point (m,).
+    Same damping and stopping rules as the batched fit (include/pm.h,
+    pm_fit_opts).  Returns (p as numpy, report dict)."""
     dev = t.device
-    p0 = torch.as_tensor(np.asarray(p0, dtype=np.float64), device=dev)
-    s = torch.where(p0 != 0, p0.abs(), torch.ones_like(p0))
-    q = p0 / s
-    lam = 1e-3
+    m = len(model.params)
     l = t.shape[0]
-    eps = 5.9604645e-8
-    it = 0
-
-    def ssr_b_A(q):
-        p = (q * s).detach().requires_grad_(True)
-        r = Residual.apply(p, model, X, t)
-        (b,) = torch.autograd.grad(r, p, grad_outputs=r)          # J^T r via the adjoint kernel
-        J = jacobian(model, X, t, p.detach())
-        A = torch.stack([_jtv(model, X, t, p.detach(), J[:, i]) for i in range(J.shape[1])], dim=1)
-        Sd = s
-        return float((r.detach().double() ** 2).sum()), b * Sd, A * Sd[:, None] * Sd[None, :]
-
-    ssr, b, A = ssr_b_A(q)
-    for it in range(1, max_iter + 1):
-        noise = 4 * eps * (l * ssr) ** 0.5 + l * eps * eps
-        d = torch.diagonal(A).clamp_min(1e-300)
-        accepted = False
-        for _ in range(16):
-            Ah = A / torch.sqrt(d[:, None] * d[None, :]) + lam * torch.eye(A.shape[0], dtype=A.dtype, device=dev)
-            y = torch.linalg.solve(Ah, -b / torch.sqrt(d))
-            dq = y / torch.sqrt(d)
-            pred = float(-(2 * dq @ b + dq @ A @ dq))
-            p_try = ((q + dq) * s)
+    L = lib()
+    p0 = np.ascontiguousarray(p0, dtype=np.float64)
+    state = torch.empty(LM_STATE_BYTES, dtype=torch.uint8, device=dev)
+    p = torch.empty(m, dtype=torch.float64, device=dev)
+    p_try = torch.empty_like(p)
+    flags = torch.zeros(2, dtype=torch.int32, device=dev)
+    opts = pm_fit_opts(max_iter, ftol, xtol, 1)
+    check(L.pm_lm_init(model.handle, p0.ctypes.data_as(ctypes.POINTER(ctypes.c_double)), ctypes.byref(opts),
+                       _ptr(state), _ptr(p), _cs()))
+    status = LM_RUNNING if max_iter > 0 else -4
+    while status == LM_RUNNING:
+        pg = p.clone().requires_grad_(True)
+        r = Residual.apply(pg, model, X, t)
+        (b,) = torch.autograd.grad(r, pg, grad_outputs=r)      # J^T r by the adjoint kernel
+        J = jacobian(model, X, t, pg.detach())
+        r = r.detach()
+        while True:
+            check(L.pm_lm_step(_ptr(state), _ptr(r), _ptr(b), _ptr(J), l, _ptr(p_try), _cs()))
             with torch.no_grad():
                 r_try = Residual.apply(p_try, model, X, t)
-            sn = float((r_try.double() ** 2).sum())
-            if np.isfinite(sn) and (sn <= ssr or pred <= noise):
-                accepted = True
+            check(L.pm_lm_update(_ptr(state), _ptr(r_try), l, _ptr(p), _ptr(flags), _cs()))
+            status, accepted = flags.tolist()
+            if status != LM_RUNNING or accepted:
                 break
-            lam *= 10
-        if not accepted:
-            break
-        q = q + dq
-        lam = max(lam * 0.1, 1e-12)
-        ssr_old = ssr
-        ssr, b, A = ssr_b_A(q)
-        if float(dq.norm()) <= xtol * (float(q.norm()) + xtol) or pred <= noise or ssr_old - ssr <= 1e-15 * ssr_old:
-            break
-    return (q * s).cpu().numpy(), it
+    rep = pm_fit_report()
+    check(L.pm_lm_report(_ptr(state), ctypes.byref(rep), _cs()))
+    return p.cpu().numpy(), {"status": rep.status, "iterations": rep.iterations, "residual": rep.residual,
+                             "lambda": rep.lambda_}

@@ -28,6 +28,7 @@
 #include <vector>
 
 #include "pm_df.cuh"
+#include "pm_eval.cuh"
 #include "pm_internal.h"
 #include "pm_model.h"
 
@@ -41,6 +42,11 @@ namespace {
 constexpr int MP = kMaxParamsFit;               // max parameters
 constexpr int NENT = MP * (MP + 1) / 2 + MP + 1; // A (upper), b, ssr
 constexpr double EPS_DF = 1e-13;  // relative accuracy of a float-float residual (conservative)
+// End of the iteration below the SSR's noise floor: a step of at most
+// kStepTiny (max |dq_i| over max(max |q_i|, 1), scaled coordinates), or
+// kMaxBelow such steps in a row
+constexpr double kStepTiny = 1e-9;
+constexpr int kMaxBelow = 4;
 
 struct FitJob {
     const Ins *code;
@@ -58,179 +64,6 @@ struct FitJob {
 struct FitCfg {
     int max_iter;
     double ftol, xtol;
-};
-
-// ---------------------------------------------------------------- evaluator
-__device__ __forceinline__ float fn32(int op, float x) {
-    switch (op) {
-    case OP_TANH: return tanhf(x);
-    case OP_EXP: return expf(x);
-    case OP_LOG: return logf(x);
-    default: return sqrtf(x);
-    }
-}
-__device__ __forceinline__ double fn64(int op, double x) {
-    switch (op) {
-    case OP_TANH: return tanh(x);
-    case OP_EXP: return exp(x);
-    case OP_LOG: return log(x);
-    default: return sqrt(x);
-    }
-}
-
-// Forward sweep over the SSA program; v[k] receives every value.
-template <typename T, typename F>
-__device__ T forward(const Ins *code, int n, const F *frow, const T *par, T *v) {
-    for (int k = 0; k < n; k++) {
-        const Ins in = code[k];
-        T x;
-        switch (in.op) {
-        case OP_FEAT: x = (T)frow[in.arg]; break;
-        case OP_PAR: x = par[in.arg]; break;
-        case OP_CONST: x = (T)in.c; break;
-        case OP_ADD: x = v[in.a] + v[in.b]; break;
-        case OP_SUB: x = v[in.a] - v[in.b]; break;
-        case OP_MUL: x = v[in.a] * v[in.b]; break;
-        case OP_DIV: x = v[in.a] / v[in.b]; break;
-        case OP_NEG: x = -v[in.a]; break;
-        default:
-            if (sizeof(T) == 4) x = (T)fn32(in.op, (float)v[in.a]);
-            else x = (T)fn64(in.op, (double)v[in.a]);
-        }
-        v[k] = x;
-    }
-    return v[n - 1];
-}
-
-// Forward sweep in float-float; cst[k] holds instruction k's constant as a
-// float-float value (converted once per program load, not per row).
-__device__ df forward_df(const Ins *code, const df *cst, int n, const float2 *frow, const df *par, df *v) {
-    for (int k = 0; k < n; k++) {
-        const Ins in = code[k];
-        df x;
-        switch (in.op) {
-        case OP_FEAT: { const float2 f = frow[in.arg]; x = df{f.x, f.y}; break; }
-        case OP_PAR: x = par[in.arg]; break;
-        case OP_CONST: x = cst[k]; break;
-        case OP_ADD: x = df_add(v[in.a], v[in.b]); break;
-        case OP_SUB: x = df_sub(v[in.a], v[in.b]); break;
-        case OP_MUL: x = df_mul(v[in.a], v[in.b]); break;
-        case OP_DIV: x = df_div(v[in.a], v[in.b]); break;
-        case OP_NEG: x = df_neg(v[in.a]); break;
-        case OP_TANH: x = df_tanh(v[in.a]); break;
-        case OP_EXP: x = df_exp(v[in.a]); break;
-        case OP_LOG: x = df_log(v[in.a]); break;
-        default: x = df_sqrt(v[in.a]);
-        }
-        v[k] = x;
-    }
-    return v[n - 1];
-}
-
-// d tanh(x) / dx = 1 - tanh(x)^2 = 4 e / (1 + e)^2 with e = exp(-2|x|): from the
-// argument, without the cancellation of 1 - t*t when |t| is near 1 (at x = -8
-// the FP32 value of t leaves 1 - t*t about 13 % off, enough to misdirect an
-// LM step along the saturated column)
-__device__ __forceinline__ float sech2f(float x) {
-    const float e = expf(-2.0f * fabsf(x));
-    const float d = 1.0f + e;
-    return 4.0f * e / (d * d);
-}
-
-// Reverse sweep over the high parts of float-float forward values.
-__device__ void reverse_df(const Ins *code, int n, const df *vd, float *adj, float *g, int m) {
-    for (int k = 0; k < n; k++) adj[k] = 0.0f;
-    for (int i = 0; i < m; i++) g[i] = 0.0f;
-    adj[n - 1] = 1.0f;
-    for (int k = n - 1; k >= 0; k--) {
-        const float a = adj[k];
-        if (a == 0.0f) continue;
-        const Ins in = code[k];
-        switch (in.op) {
-        case OP_PAR: g[in.arg] += a; break;
-        case OP_ADD: adj[in.a] += a; adj[in.b] += a; break;
-        case OP_SUB: adj[in.a] += a; adj[in.b] -= a; break;
-        case OP_MUL: adj[in.a] += a * vd[in.b].hi; adj[in.b] += a * vd[in.a].hi; break;
-        case OP_DIV: adj[in.a] += a / vd[in.b].hi; adj[in.b] -= a * vd[k].hi / vd[in.b].hi; break;
-        case OP_NEG: adj[in.a] -= a; break;
-        case OP_TANH: adj[in.a] += a * sech2f(vd[in.a].hi); break;
-        case OP_EXP: adj[in.a] += a * vd[k].hi; break;
-        case OP_LOG: adj[in.a] += a / vd[in.a].hi; break;
-        case OP_SQRT: adj[in.a] += a * 0.5f / vd[k].hi; break;
-        default: break;
-        }
-    }
-}
-
-// Reverse sweep: g[i] = dv[n-1]/dpar[i] (FP32).
-__device__ void reverse(const Ins *code, int n, const float *v, float *adj, float *g, int m) {
-    for (int k = 0; k < n; k++) adj[k] = 0.0f;
-    for (int i = 0; i < m; i++) g[i] = 0.0f;
-    adj[n - 1] = 1.0f;
-    for (int k = n - 1; k >= 0; k--) {
-        const float a = adj[k];
-        if (a == 0.0f) continue;
-        const Ins in = code[k];
-        switch (in.op) {
-        case OP_PAR: g[in.arg] += a; break;
-        case OP_ADD: adj[in.a] += a; adj[in.b] += a; break;
-        case OP_SUB: adj[in.a] += a; adj[in.b] -= a; break;
-        case OP_MUL: adj[in.a] += a * v[in.b]; adj[in.b] += a * v[in.a]; break;
-        case OP_DIV: adj[in.a] += a / v[in.b]; adj[in.b] -= a * v[k] / v[in.b]; break;
-        case OP_NEG: adj[in.a] -= a; break;
-        case OP_TANH: adj[in.a] += a * sech2f(v[in.a]); break;
-        case OP_EXP: adj[in.a] += a * v[k]; break;
-        case OP_LOG: adj[in.a] += a / v[in.a]; break;
-        case OP_SQRT: adj[in.a] += a * 0.5f / v[k]; break;
-        default: break;
-        }
-    }
-}
-
-// Reverse sweep in float-float (adjoints and derivatives as hi + lo): the
-// exact Jacobian of a linear model's direct solve.
-__device__ void reverse_dd(const Ins *code, int n, const df *vd, df *adj, df *g, int m) {
-    for (int k = 0; k < n; k++) adj[k] = df{0.0f, 0.0f};
-    for (int i = 0; i < m; i++) g[i] = df{0.0f, 0.0f};
-    adj[n - 1] = df{1.0f, 0.0f};
-    for (int k = n - 1; k >= 0; k--) {
-        const df a = adj[k];
-        if (a.hi == 0.0f && a.lo == 0.0f) continue;
-        const Ins in = code[k];
-        switch (in.op) {
-        case OP_PAR: g[in.arg] = df_add(g[in.arg], a); break;
-        case OP_ADD: adj[in.a] = df_add(adj[in.a], a); adj[in.b] = df_add(adj[in.b], a); break;
-        case OP_SUB: adj[in.a] = df_add(adj[in.a], a); adj[in.b] = df_sub(adj[in.b], a); break;
-        case OP_MUL:
-            adj[in.a] = df_add(adj[in.a], df_mul(a, vd[in.b]));
-            adj[in.b] = df_add(adj[in.b], df_mul(a, vd[in.a]));
-            break;
-        case OP_DIV:
-            adj[in.a] = df_add(adj[in.a], df_div(a, vd[in.b]));
-            adj[in.b] = df_sub(adj[in.b], df_div(df_mul(a, vd[k]), vd[in.b]));
-            break;
-        case OP_NEG: adj[in.a] = df_sub(adj[in.a], a); break;
-        case OP_TANH: adj[in.a] = df_add(adj[in.a], df_mul(a, df_sub(df{1.0f, 0.0f}, df_mul(vd[k], vd[k])))); break;
-        case OP_EXP: adj[in.a] = df_add(adj[in.a], df_mul(a, vd[k])); break;
-        case OP_LOG: adj[in.a] = df_add(adj[in.a], df_div(a, vd[in.a])); break;
-        case OP_SQRT: adj[in.a] = df_add(adj[in.a], df_div(df_mulf(a, 0.5f), vd[k])); break;
-        default: break;
-        }
-    }
-}
-
-// Compensated FP32 sum (TwoSum error-free transformation).
-struct CSum {
-    float s, c;
-    __device__ void init() { s = 0.0f; c = 0.0f; }
-    __device__ void add(float x) {
-        const float t = __fadd_rn(s, x);
-        const float z = __fsub_rn(t, s);
-        const float e = __fadd_rn(__fsub_rn(s, __fsub_rn(t, z)), __fsub_rn(x, z));
-        s = t;
-        c = __fadd_rn(c, e);
-    }
-    __device__ double value() const { return (double)s + (double)c; }
 };
 
 // ---------------------------------------------------------------- per-CTA state
@@ -257,7 +90,7 @@ struct Smem {
     unsigned zmask;               // start point: parameters whose column is zero at the origin
     df part[T];       // per row-group partial sums of the assembled entries
     double ssr, ssr_new, pred, lambda, med[2], noise, cond;
-    int stop;
+    int stop, below, nbelow;
     int nact, ok, rankdef, rank;
 };
 
@@ -872,7 +705,11 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
         S.s[tid] = p0 != 0.0 ? fabs(p0) : 1.0;
         S.q[tid] = p0 / S.s[tid];
     }
-    if (tid == 0) S.lambda = 1e-3;
+    if (tid == 0) {
+        S.lambda = 1e-3;
+        S.nbelow = 0;
+        S.below = 0;
+    }
     __syncthreads();
     load_code(S, jb.code, jb.n_code);
     set_params(S, S.q, m);
@@ -915,12 +752,22 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
             break;
         }
         if (tid == 0) {
-            double dn = 0.0, qn = 0.0;
+            double dn = 0.0, qn = 0.0, da = 0.0, qa = 0.0;
             for (int i = 0; i < m; i++) {
                 dn += S.dq[i] * S.dq[i];
                 qn += S.qt[i] * S.qt[i];
+                da = fmax(da, fabs(S.dq[i]));
+                qa = fmax(qa, fabs(S.qt[i]));
             }
-            S.stop = sqrt(dn) <= cfg.xtol * (sqrt(qn) + cfg.xtol) || S.pred <= noise;
+            // a step whose predicted gain is below the SSR's noise floor cannot
+            // be verified by the SSR, but its direction comes from the gradient,
+            // which stays accurate there: such steps continue until they are
+            // negligible (kStepTiny in the scaled coordinates) or kMaxBelow of
+            // them have been taken in a row
+            S.below = S.pred <= noise;
+            S.nbelow = S.below ? S.nbelow + 1 : 0;
+            S.stop = sqrt(dn) <= cfg.xtol * (sqrt(qn) + cfg.xtol) ||
+                     (S.below && (da <= kStepTiny * fmax(qa, 1.0) || S.nbelow >= kMaxBelow));
         }
         __syncthreads();
         if (tid < m) S.q[tid] = S.qt[tid];
@@ -931,7 +778,8 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
         assemble(S, jb, jb.n_code, all, true);
         set_active(S, m, all);
         if (tid < m) S.dmax[tid] = fmax(S.dmax[tid], A_at(S.acc, m, tid, tid));
-        if (tid == 0) S.stop = S.stop || (ssr_old - S.ssr) <= cfg.ftol * ssr_old;
+        // the relative-decrease test only where the decrease is measurable
+        if (tid == 0) S.stop = S.stop || (!S.below && (ssr_old - S.ssr) <= cfg.ftol * ssr_old);
         __syncthreads();
         if (S.stop) {
             converged = true;
@@ -958,58 +806,6 @@ __global__ void k_split(const double *__restrict__ a, float2 *__restrict__ b, si
         const double x = a[i];
         const float h = (float)x;
         b[i] = make_float2(h, (float)(x - (double)h));
-    }
-}
-
-// ---------------------------------------------------------------- autograd kernels
-__global__ void k_residual(const Ins *__restrict__ code, int n, int m, int nf, const float *__restrict__ X,
-                           const float *__restrict__ t, size_t l, const double *__restrict__ p, float *__restrict__ r) {
-    __shared__ float pf[MP];
-    __shared__ Ins cs[kMaxIns];
-    for (int k = threadIdx.x; k < n; k += blockDim.x) cs[k] = code[k];
-    if (threadIdx.x < m) pf[threadIdx.x] = (float)p[threadIdx.x];
-    __syncthreads();
-    float v[kMaxIns];
-    for (size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x; row < l; row += (size_t)gridDim.x * blockDim.x)
-        r[row] = 1.0f - forward<float, float>(cs, n, X + row * nf, pf, v) / t[row];
-}
-
-// mode 0: pbar += sum_k rbar_k J_k (vjp); mode 1: write J rows
-__global__ void k_jac(const Ins *__restrict__ code, int n, int m, int nf, const float *__restrict__ X,
-                      const float *__restrict__ t, size_t l, const double *__restrict__ p,
-                      const float *__restrict__ rbar, double *__restrict__ pbar, float *__restrict__ J, int mode) {
-    __shared__ float pf[MP];
-    __shared__ Ins cs[kMaxIns];
-    __shared__ double red[MP][8];
-    for (int k = threadIdx.x; k < n; k += blockDim.x) cs[k] = code[k];
-    if (threadIdx.x < m) pf[threadIdx.x] = (float)p[threadIdx.x];
-    __syncthreads();
-    float v[kMaxIns], adj[kMaxIns], g[MP];
-    CSum acc[MP];
-    for (int i = 0; i < MP; i++) acc[i].init();
-    for (size_t row = blockIdx.x * (size_t)blockDim.x + threadIdx.x; row < l; row += (size_t)gridDim.x * blockDim.x) {
-        forward<float, float>(cs, n, X + row * nf, pf, v);
-        reverse(cs, n, v, adj, g, m);
-        const float inv = -1.0f / t[row];
-        if (mode == 1) {
-            for (int i = 0; i < m; i++) J[row * m + i] = g[i] * inv;
-        } else {
-            const float w = rbar[row] * inv;
-            for (int i = 0; i < m; i++) acc[i].add(g[i] * w);
-        }
-    }
-    if (mode == 1) return;
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int i = 0; i < m; i++) {
-        double x = acc[i].value();
-        for (int o = 16; o; o >>= 1) x += __shfl_xor_sync(0xffffffffu, x, o);
-        if (lane == 0) red[i][warp] = x;
-    }
-    __syncthreads();
-    if (threadIdx.x < m) {
-        double x = 0.0;
-        for (int w = 0; w < (int)(blockDim.x >> 5); w++) x += red[threadIdx.x][w];
-        atomicAdd(&pbar[threadIdx.x], x);
     }
 }
 
@@ -1172,21 +968,6 @@ pm_status check_opts(const pm_fit_opts *o, FitCfg &cfg, int &use_p0) {
     return PM_OK;
 }
 
-pm_status ensure_device_code(const pm_model *m) {
-    int dev = 0;
-    PM_CUDA_TRY(cudaGetDevice(&dev));
-    pm_model *mm = const_cast<pm_model *>(m);
-    if (mm->d_code && mm->d_device == dev) return PM_OK;
-    if (mm->d_code) {
-        cudaFree(mm->d_code);
-        mm->d_code = nullptr;
-    }
-    PM_ALLOC_TRY(cudaMalloc(&mm->d_code, m->code.size() * sizeof(Ins)));
-    PM_CUDA_TRY(cudaMemcpy(mm->d_code, m->code.data(), m->code.size() * sizeof(Ins), cudaMemcpyHostToDevice));
-    mm->d_device = dev;
-    return PM_OK;
-}
-
 }  // namespace
 }  // namespace pm
 
@@ -1321,48 +1102,6 @@ pm_status pm_predict(const pm_model *m, const double *p, const double *X, size_t
     return s;
 }
 
-pm_status pm_residual(const pm_model *m, const float *X, const float *t, size_t l, const double *p, float *r,
-                      void *stream) {
-    if (!m || !t || !p || !r || (!X && !m->features.empty())) return fail(PM_EINVAL, "pm_residual: NULL argument");
-    if (l == 0) return PM_OK;
-    pm_status s = ensure_device_code(m);
-    if (s) return s;
-    const unsigned blocks = (unsigned)std::min<size_t>((l + 127) / 128, 1216);
-    k_residual<<<blocks, 128, 0, (cudaStream_t)stream>>>(m->d_code, (int)m->code.size(), (int)m->params.size(),
-                                                         (int)m->features.size(), X, t, l, p, r);
-    PM_CUDA_TRY(cudaGetLastError());
-    return PM_OK;
-}
-
-pm_status pm_residual_vjp(const pm_model *m, const float *X, const float *t, size_t l, const double *p,
-                          const float *rbar, double *pbar, void *stream) {
-    if (!m || !t || !p || !rbar || !pbar || (!X && !m->features.empty()))
-        return fail(PM_EINVAL, "pm_residual_vjp: NULL argument");
-    pm_status s = ensure_device_code(m);
-    if (s) return s;
-    cudaStream_t st = (cudaStream_t)stream;
-    PM_CUDA_TRY(cudaMemsetAsync(pbar, 0, m->params.size() * 8, st));
-    if (l == 0) return PM_OK;
-    const unsigned blocks = (unsigned)std::min<size_t>((l + 255) / 256, 304);
-    k_jac<<<blocks, 256, 0, st>>>(m->d_code, (int)m->code.size(), (int)m->params.size(), (int)m->features.size(), X,
-                                  t, l, p, rbar, pbar, nullptr, 0);
-    PM_CUDA_TRY(cudaGetLastError());
-    return PM_OK;
-}
-
-pm_status pm_jacobian(const pm_model *m, const float *X, const float *t, size_t l, const double *p, float *J,
-                      void *stream) {
-    if (!m || !t || !p || !J || (!X && !m->features.empty())) return fail(PM_EINVAL, "pm_jacobian: NULL argument");
-    if (l == 0) return PM_OK;
-    pm_status s = ensure_device_code(m);
-    if (s) return s;
-    const unsigned blocks = (unsigned)std::min<size_t>((l + 255) / 256, 1216);
-    k_jac<<<blocks, 256, 0, (cudaStream_t)stream>>>(m->d_code, (int)m->code.size(), (int)m->params.size(),
-                                                     (int)m->features.size(), X, t, l, p, nullptr, nullptr, J, 1);
-    PM_CUDA_TRY(cudaGetLastError());
-    return PM_OK;
-}
-
 }  // extern "C"
 
 // ---------------------------------------------------------------- allocation-free batched fit
@@ -1381,11 +1120,21 @@ constexpr size_t kNoallocMaxModels = 256;
 static void *g_scratch_addr[kMaxDevices];
 static std::mutex g_scratch_mu;
 
+constexpr size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+// Host image of the scratch's first region (job table, then every model's
+// program and start program), built here and uploaded with one copy.  Static
+// storage: the call allocates no host memory either.  A model's start program
+// is never longer than its program (kMaxIns instructions).
+constexpr size_t kStageBytes = align256(kNoallocMaxModels * sizeof(FitJob)) + kNoallocMaxModels * 2 * kMaxIns * sizeof(Ins);
+static __align__(256) unsigned char g_host_stage[kStageBytes];
+
+// Device address of g_fit_scratch on the current device, looked up on the
+// first call per device (with that device current) and cached.
 pm_status scratch_address(void **out) {
     int dev = 0;
     PM_CUDA_TRY(cudaGetDevice(&dev));
     if (dev < 0 || dev >= kMaxDevices) return fail(PM_EINVAL, "noalloc fit: device ordinal %d unsupported", dev);
-    std::lock_guard<std::mutex> lock(g_scratch_mu);
     if (!g_scratch_addr[dev]) {
         void *p = nullptr;
         cudaError_t e = cudaGetSymbolAddress(&p, g_fit_scratch);
@@ -1396,8 +1145,6 @@ pm_status scratch_address(void **out) {
     *out = g_scratch_addr[dev];
     return PM_OK;
 }
-
-size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 }  // namespace
 }  // namespace pm
@@ -1433,24 +1180,31 @@ extern "C" pm_status pm_fit_batched_noalloc(const pm_model *const *models, size_
     if (need > (size_t)PM_NOALLOC_SCRATCH_BYTES)
         return fail(PM_EINVAL, "pm_fit_batched_noalloc: request needs %zu bytes of scratch, the limit is %zu",
                     need, (size_t)PM_NOALLOC_SCRATCH_BYTES);
+    if (o_code + ncode * sizeof(Ins) > kStageBytes)
+        return fail(PM_EINVAL, "pm_fit_batched_noalloc: model programs exceed the staging area");
     for (size_t k = 0, o = 0; k < nmodels; k++)
         for (size_t r = 0; r < rows[k]; r++, o++)
             if (!finite_pos(t[o])) return fail(PM_EINVAL, "fit: model %zu row %zu: output must be finite and > 0", k, r);
     for (size_t i = 0; i < nx; i++)
         if (!std::isfinite(X[i])) return fail(PM_EINVAL, "fit: feature value %zu is not finite", i);
+    if (use_p0)
+        for (size_t i = 0; i < np; i++)
+            if (!std::isfinite(p_inout[i])) return fail(PM_EINVAL, "fit: start point %zu is not finite", i);
+    std::lock_guard<std::mutex> lock(g_scratch_mu);
     void *base = nullptr;
     if ((s = scratch_address(&base))) return s;
     unsigned char *B = (unsigned char *)base;
     cudaStream_t st = (cudaStream_t)stream;
-    FitJob jobs[kNoallocMaxModels];
+    // job table and programs: built in the host image of [0, o_x64), one upload
+    FitJob *jobs = (FitJob *)(g_host_stage + o_jobs);
+    Ins *hcode = (Ins *)(g_host_stage + o_code);
     size_t co = 0, xo = 0, to = 0, po = 0;
     for (size_t k = 0; k < nmodels; k++) {
         const pm_model *md = models[k];
         FitJob &j = jobs[k];
+        memcpy(hcode + co, md->code.data(), md->code.size() * sizeof(Ins));
+        memcpy(hcode + co + md->code.size(), md->start_code.data(), md->start_code.size() * sizeof(Ins));
         Ins *code = (Ins *)(B + o_code) + co;
-        PM_CUDA_TRY(cudaMemcpyAsync(code, md->code.data(), md->code.size() * sizeof(Ins), cudaMemcpyHostToDevice, st));
-        PM_CUDA_TRY(cudaMemcpyAsync(code + md->code.size(), md->start_code.data(), md->start_code.size() * sizeof(Ins),
-                                    cudaMemcpyHostToDevice, st));
         j.code = code;
         j.start_code = code + md->code.size();
         j.n_code = (int)md->code.size();
@@ -1470,7 +1224,9 @@ extern "C" pm_status pm_fit_batched_noalloc(const pm_model *const *models, size_
         to += rows[k];
         po += md->params.size();
     }
-    PM_CUDA_TRY(cudaMemcpyAsync(B + o_jobs, jobs, nmodels * sizeof(FitJob), cudaMemcpyHostToDevice, st));
+    // pageable-source copies return once the source has been staged, so the
+    // host image may be rebuilt by the next call as soon as this one returns
+    PM_CUDA_TRY(cudaMemcpyAsync(B + o_jobs, g_host_stage, o_code + ncode * sizeof(Ins), cudaMemcpyHostToDevice, st));
     if (nx) PM_CUDA_TRY(cudaMemcpyAsync(B + o_x64, X, nx * 8, cudaMemcpyHostToDevice, st));
     PM_CUDA_TRY(cudaMemcpyAsync(B + o_t64, t, nt * 8, cudaMemcpyHostToDevice, st));
     PM_CUDA_TRY(cudaMemcpyAsync(B + o_p, p_inout, np * 8, cudaMemcpyHostToDevice, st));
@@ -1493,6 +1249,5 @@ extern "C" pm_status pm_fit_batched_noalloc(const pm_model *const *models, size_
             reports[k].lambda = r[5];
             reports[k].cond = r[6];
         }
-    PM_CUDA_TRY(cudaStreamSynchronize(st));
     return PM_OK;
 }

@@ -61,18 +61,39 @@ def features(K, nfeat):
     return Xs, ls
 
 
+def synthetic_times(k, features, X):
+    """Outputs the workload is made from: model k (model_expr) at the TRUTH
+    parameters on the rows of X (columns named by `features`), evaluated
+    here in plain NumPy from the model's term lists -- synthetic input data,
+    made without the library -- times (1 + 1 % noise)."""
+    import pm_inputs
+    col = {f: X[:, i] for i, f in enumerate(features)}
+
+    def cost(terms):
+        return sum(TRUTH[p] * col[f] for p, f in terms)
+
+    launch = TRUTH["p_launch"] * col["f_sync_kernel_launch"] + TRUTH["p_group"] * col["f_thread_groups"]
+    if k % 2 == 0:
+        m = 4 + (k // 2) % 9
+        g = launch + cost((GMEM + ONCHIP)[:m - 2])
+    else:
+        n = 5 + (k // 2) % 8 - 3
+        cg, co = cost(GMEM[:(n + 1) // 2]), cost(ONCHIP[:n // 2])
+        pe = TRUTH["p_edge"]
+        g = launch + cg * (np.tanh(pe * (cg - co)) + 1) / 2 + co * (np.tanh(pe * (co - cg)) + 1) / 2
+    return g * (1 + 1e-2 * pm_inputs.noise((len(X),), 9900 + k))
+
+
 def problem(K):
     """K seeded calibration problems: (models, feature matrices, outputs,
     start points = 1.2 x the parameters the outputs were made with)."""
-    import pm_inputs
     from . import Model
     models = [Model("f_wall_time", model_expr(k)) for k in range(K)]
     Xs, ls = features(K, lambda k: len(models[k].features))
     ts, p0s = [], []
     for k, (m, X) in enumerate(zip(models, Xs)):
-        pt = np.array([TRUTH[n] for n in m.params])
-        ts.append(m.predict(pt, X) * (1 + 1e-2 * pm_inputs.noise((len(X),), 9900 + k)))
-        p0s.append(pt * 1.2)
+        ts.append(synthetic_times(k, m.features, X))
+        p0s.append(np.array([TRUTH[n] for n in m.params]) * 1.2)
     return models, Xs, ts, p0s, ls
 
 

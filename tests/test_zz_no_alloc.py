@@ -1,13 +1,14 @@
 """The allocation-free batched fit (pm_fit_batched_noalloc) against the
 allocating one (pm_fit_batched), through the C ABI on the GPU.
 
-Some callers cannot allocate GPU memory -- code running inside a CUDA-graph
-stream capture, latency-critical loops that must not trigger the driver's
-allocator, processes whose device memory belongs to another framework's pool.
+Some callers cannot allocate GPU memory: processes whose device memory is
+reserved by another framework's pooling allocator, and latency-critical loops
+that cannot afford the device-wide synchronisation of cudaMalloc / cudaFree.
 For them the library stages the fit in a static device array; this checks
 that two calls in a row (different data each time, so nothing from the first
 call leaks into the second) give the same parameters and statuses as the
-regular entry point, and that oversized requests are refused up front."""
+regular entry point, and that oversized requests and non-finite start points
+are refused up front."""
 import numpy as np
 import pytest
 
@@ -79,3 +80,21 @@ def test_noalloc_rejects_oversized_request():
     with pytest.raises(pm.PMError) as e:
         pm.fit_batched_noalloc([m], [X], [t])
     assert "limit" in str(e.value)
+
+
+def test_noalloc_rejects_non_finite_start_point():
+    # a NaN or an infinite start point is refused before anything is staged,
+    # as pm_fit_batched refuses it; a valid call afterwards still works
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    models, Xs, ts, p0s = problem(14, K=2)
+    for bad in (np.nan, np.inf):
+        p0 = [p.copy() for p in p0s]
+        p0[1][0] = bad
+        with pytest.raises(pm.PMError) as e:
+            pm.fit_batched_noalloc(models, Xs, ts, p0)
+        assert e.value.status == -1 and "start point" in str(e.value)
+    ref, _ = pm.fit_batched(models, Xs, ts, p0s, threads=128)
+    got, _ = pm.fit_batched_noalloc(models, Xs, ts, p0s)
+    for k in range(len(models)):
+        assert rel(got[k], ref[k]) <= TOL
