@@ -152,7 +152,9 @@ pm_status pm_counts(int32_t kernel, const pm_param *p, size_t np,
                     pm_feature *out, size_t cap, size_t *n_out);
 
 /* Size parameter over which pm_counts_desc extrapolates: counts are
- * quasi-polynomials in it of the given period and degree bound. */
+ * quasi-polynomials in it of the given period and degree bound.  period 0
+ * and degree -1 ask the library to derive them from the description (see
+ * pm_counts_desc_interp). */
 typedef struct {
     const char *name;
     int32_t period;
@@ -178,13 +180,31 @@ typedef struct {
  * variables.  Records and granularities are those of pm_counts; tags must be
  * unique (a model can name a tag only if it contains no '_').  With interp
  * (nullable), each listed parameter
- * is extrapolated exactly from degree + 2 enumerated sizes of its residue
- * class (PM_EINVAL if the extra sample contradicts the degree bound);
- * without it every loop point is enumerated (at most 2^31 statement
- * instances).  Pure host computation; *n_out and PM_ECAP as pm_counts. */
+ * is extrapolated exactly from degree + 3 enumerated sizes of its residue
+ * class, the first at one period above the residue (PM_EINVAL if either of
+ * the two extra samples contradicts the degree bound); without it every loop
+ * point is enumerated (at most 2^31 statement instances).  Pure host
+ * computation; *n_out and PM_ECAP as pm_counts. */
 pm_status pm_counts_desc(const char *description, const pm_param *p, size_t np, const pm_interp *interp,
                          size_t ninterp, pm_feature *out, size_t cap, size_t *n_out);
 
+/* Period and degree bound of the counts of a described kernel as
+ * quasi-polynomials in the size parameter `param` (the other parameters at
+ * their values in p; Section "Gathering Kernel Statistics": counts are
+ * piecewise quasi-polynomials in the sizes).  Derived from the description:
+ *   period: the lcm of the constant divisors and moduli (/ and %) applied to
+ *     expressions that depend on param -- the sources of its periodicity;
+ *   degree: over the statements, the larger of the degree of the number of
+ *     loop points (grid extents plus, per loop, the larger degree of its
+ *     bounds, which also bounds footprints, sub-group counts and barriers)
+ *     and the degrees of the access index expressions (their strides); an
+ *     index variable has the degree of its range, a product the sum of its
+ *     factors' degrees.
+ * PM_EINVAL where no bound follows: a work-group extent that depends on
+ * param, a divisor or modulus that is not constant and depends on param, a
+ * degree above 10 or a period above 2^24.  Pure host computation. */
+pm_status pm_counts_desc_interp(const char *description, const char *param, const pm_param *p, size_t np,
+                                int32_t *period, int32_t *degree);
 
 /* Compiled resources and launch shape of one kernel instance, for an
  * autotuner's pruning step (the paper's use of a model as a heuristic that

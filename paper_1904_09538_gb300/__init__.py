@@ -10,7 +10,7 @@ from ._lib import (lib, check, PMError, pm_param, pm_buffer, pm_feature, pm_run_
                    pm_fit_report)
 
 __all__ = ["kernel_lookup", "kernel_names", "counts", "kernel_buffers", "launch", "run", "run_host", "Model",
-           "FitPlan", "fit_batched", "fit_batched_noalloc", "NOALLOC_SCRATCH_BYTES", "PMError", "DTYPES"]
+           "FitPlan", "fit_batched", "counts_desc_interp", "fit_batched_noalloc", "NOALLOC_SCRATCH_BYTES", "PMError", "DTYPES"]
 
 NOALLOC_SCRATCH_BYTES = 8 << 20
 
@@ -76,8 +76,9 @@ def _counts_desc_raw(description, interp=None, **params):
     interp = interp or {}
     names = [k.encode() for k in interp]
     ip = (_lib.pm_interp * max(1, len(interp)))()
-    for i, (k, (period, degree)) in enumerate(interp.items()):
-        ip[i] = _lib.pm_interp(names[i], int(period), int(degree))
+    for i, (k, pd) in enumerate(interp.items()):
+        period, degree = (None, None) if pd is None else pd
+        ip[i] = _lib.pm_interp(names[i], 0 if period is None else int(period), -1 if degree is None else int(degree))
     cap = 64
     while True:
         out = (pm_feature * cap)()
@@ -93,8 +94,19 @@ def _counts_desc_raw(description, interp=None, **params):
 def counts_desc(description, interp=None, **params):
     """Exact feature records of a kernel given as a loop-nest description
     (pm_counts_desc).  interp: {parameter: (period, degree bound)} for sizes
-    too large to enumerate."""
+    too large to enumerate; None (or None in either place) lets the library
+    derive it from the description."""
     return _records(*_counts_desc_raw(description, interp, **params))
+
+
+def counts_desc_interp(description, param, **params):
+    """(period, degree bound) of the counts in `param`, derived from the
+    description (pm_counts_desc_interp)."""
+    arr, n, _keep = _params(params)
+    pe, de = ctypes.c_int32(), ctypes.c_int32()
+    check(lib().pm_counts_desc_interp(description.encode(), param.encode(), arr, n, ctypes.byref(pe),
+                                      ctypes.byref(de)))
+    return pe.value, de.value
 
 
 def _counts_raw(kernel, **params):

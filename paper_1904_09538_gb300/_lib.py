@@ -82,6 +82,7 @@ SIGNATURES = {
     "pm_counts": (i32, [i32, P(pm_param), c_size_t, P(pm_feature), c_size_t, P(c_size_t)]),
     "pm_counts_desc": (i32, [ctypes.c_char_p, P(pm_param), c_size_t, P(pm_interp), c_size_t, P(pm_feature), c_size_t,
                              P(c_size_t)]),
+    "pm_counts_desc_interp": (i32, [ctypes.c_char_p, ctypes.c_char_p, P(pm_param), c_size_t, P(i32), P(i32)]),
     "pm_launch": (i32, [i32, P(pm_param), c_size_t, P(vp), c_size_t, vp]),
     "pm_kernel_resources": (i32, [i32, P(pm_param), c_size_t, P(pm_resources)]),
     "pm_run": (i32, [i32, P(pm_param), c_size_t, P(vp), c_size_t, P(pm_run_opts), vp, fp, P(pm_timing)]),

@@ -23,6 +23,7 @@
 // enumerates degree + 2 sizes in the target's residue class and extrapolates
 // every field exactly with Newton forward differences in 128-bit integers;
 // the extra sample must make the (degree + 1)-th difference vanish.
+#include <algorithm>
 #include <cctype>
 #include <cstdint>
 #include <cstring>
@@ -553,6 +554,125 @@ struct Interp {
     int degree;
 };
 
+// ---------------------------------------------------------------- period and degree
+// A bound on how an expression grows with one size parameter P (the other
+// parameters fixed at their values): its polynomial degree in P, whether it
+// is a known constant (and its value), and the constant divisors and moduli
+// applied to P-dependent operands.  A thread index has the degree of its
+// extent, a loop variable the larger degree of its bounds.
+struct Deg {
+    int d;
+    bool is_const;
+    i64 v;
+};
+
+i64 gcd64(i64 a, i64 b) {
+    while (b) { const i64 t = a % b; a = b; b = t; }
+    return a < 0 ? -a : a;
+}
+
+struct Deriver {
+    int P, np;
+    const std::vector<i64> &pv;
+    i64 period = 1;
+    std::string err;
+    std::vector<int> slot_deg;   // degree of each variable slot (index and loop variables)
+    Deriver(int p, const std::vector<i64> &vals) : P(p), np((int)vals.size()), pv(vals) {
+        slot_deg.assign(np + NTH + MAXL, 0);
+    }
+    void divides(i64 c) {
+        c = c < 0 ? -c : c;
+        if (c <= 1) return;
+        period = period / gcd64(period, c) * c;
+        if (period > ((i64)1 << 24)) err = "the period in this parameter exceeds 2^24";
+    }
+    Deg eval(const Expr &e) {
+        Deg st[64];
+        int sp = 0;
+        for (const Ins &c : e.code) {
+            if (c.op == PUSH) { st[sp++] = {0, true, c.v}; continue; }
+            if (c.op == VAR) {
+                const int k = (int)c.v;
+                if (k < np) st[sp++] = k == P ? Deg{1, false, 0} : Deg{0, true, pv[k]};
+                else st[sp++] = {slot_deg[k], false, 0};
+                continue;
+            }
+            if (c.op == NEG) {
+                Deg &a = st[sp - 1];
+                if (a.is_const) a.v = -a.v;
+                continue;
+            }
+            const Deg b = st[--sp], a = st[sp - 1];
+            Deg r{0, false, 0};
+            if (a.is_const && b.is_const) {
+                Expr tmp;
+                tmp.code = {{PUSH, a.v}, {PUSH, b.v}, c};
+                r = {0, true, tmp.eval(nullptr)};
+            } else {
+                switch (c.op) {
+                case ADD: case SUB: case MIN: case MAX: r.d = std::max(a.d, b.d); break;
+                case MUL: r.d = a.d + b.d; break;
+                case DIV:
+                case MOD:
+                    if (!b.is_const) {
+                        if (a.d > 0 || b.d > 0) err = "a divisor or modulus that is not constant depends on the parameter";
+                        r.d = std::max(a.d, b.d);
+                    } else {
+                        if (a.d > 0) divides(b.v);
+                        r.d = c.op == DIV ? a.d : 0;
+                    }
+                    break;
+                default: break;
+                }
+            }
+            st[sp - 1] = r;
+        }
+        return sp ? st[0] : Deg{0, true, 0};
+    }
+};
+
+// Period and degree bound of every count of `d` as a quasi-polynomial in
+// parameter P (the others at pv): the period is the lcm of the constant
+// divisors and moduli applied to P-dependent expressions; the degree bound
+// is, over the statements, the larger of the instance-count degree (the
+// degrees of the grid extents plus, per loop, the larger degree of its
+// bounds: the number of points of the domain, which bounds the footprints,
+// sub-group counts and barriers too) and the degrees of the access index
+// expressions (their strides).  PM_EINVAL where no such bound follows from
+// the description: a work-group extent depending on P (its sub-group
+// decomposition then changes with P), or a P-dependent non-constant divisor.
+pm_status derive_interp(const Desc &d, int P, const std::vector<i64> &pv, i64 *period, int *degree) {
+    Deriver D(P, pv);
+    int grid_deg = 0;
+    for (int a = 0; a < 3; a++) {
+        const Deg g = D.eval(d.grid[a]), l = D.eval(d.group[a]);
+        if (l.d > 0 || !l.is_const) return fail(PM_EINVAL, "pm_counts_desc: the work-group extent depends on %s; "
+                                                 "state its period and degree", d.params[P].c_str());
+        D.slot_deg[D.np + a] = g.d;        // g_a ranges over the grid extent
+        D.slot_deg[D.np + 3 + a] = 0;      // l_a over a constant extent
+        grid_deg += g.d;
+    }
+    int deg = grid_deg;
+    for (const Stmt &S : d.st) {
+        int inst = grid_deg;
+        for (int li = 0; li < S.nloop; li++) {
+            const int ld = std::max(D.eval(S.lo[li]).d, D.eval(S.hi[li]).d);
+            D.slot_deg[D.np + NTH + li] = ld;
+            inst += ld;
+        }
+        for (const Expr &g : S.guards) D.eval(g);
+        deg = std::max(deg, inst);
+        for (const Access &A : S.acc) deg = std::max(deg, D.eval(A.idx).d);
+        for (int li = 0; li < MAXL; li++) D.slot_deg[D.np + NTH + li] = 0;
+    }
+    if (!D.err.empty()) return fail(PM_EINVAL, "pm_counts_desc: %s (%s); state its period and degree", D.err.c_str(),
+                                    d.params[P].c_str());
+    if (deg > 10) return fail(PM_EINVAL, "pm_counts_desc: degree bound %d in %s exceeds 10", deg, d.params[P].c_str());
+    *period = D.period;
+    *degree = deg;
+    return PM_OK;
+}
+
 pm_status counts_rec(const Desc &d, std::vector<i64> pv, const std::vector<Interp> &ip, size_t level, u64 budget,
                      std::vector<pm_feature> &out) {
     if (level == ip.size()) return count_at(d, pv, budget, out);
@@ -560,8 +680,8 @@ pm_status counts_rec(const Desc &d, std::vector<i64> pv, const std::vector<Inter
     const i64 target = pv[I.param];
     i64 rho = ((target % I.period) + I.period) % I.period;
     const i64 x0 = rho + I.period;   // first sample: one period above the residue
-    if (target <= x0 + I.period * (I.degree + 1)) return counts_rec(d, pv, ip, level + 1, budget, out);
-    const int ns = I.degree + 2;
+    if (target <= x0 + I.period * (I.degree + 2)) return counts_rec(d, pv, ip, level + 1, budget, out);
+    const int ns = I.degree + 3;   // degree + 1 samples fix the polynomial, two more check it
     std::vector<std::vector<pm_feature>> smp(ns);
     pm_status s;
     for (int j = 0; j < ns; j++) {
@@ -577,13 +697,13 @@ pm_status counts_rec(const Desc &d, std::vector<i64> pv, const std::vector<Inter
     const i128 t = (target - x0) / I.period;   // target = x0 + period * t
     out = smp[0];
     for (size_t r = 0; r < out.size(); r++) {
-        i128 diff[12][NF];   // forward differences, diff[k] = Delta^k at x0
+        i128 diff[13][NF];   // forward differences, diff[k] = Delta^k at x0
         for (int j = 0; j < ns; j++) fields(smp[j][r], diff[j]);
         for (int k = 1; k < ns; k++)
             for (int j = ns - 1; j >= k; j--)
                 for (int f = 0; f < NF; f++) diff[j][f] -= diff[j - 1][f];
         for (int f = 0; f < NF; f++)
-            if (diff[ns - 1][f] != 0)
+            if (diff[ns - 1][f] != 0 || diff[ns - 2][f] != 0)
                 return fail(PM_EINVAL, "pm_counts_desc: a count is not a polynomial of degree <= %d in %s on the residue class "
                             "(raise the degree or the period)", I.degree, d.params[I.param].c_str());
         i128 val[NF] = {0}, binom = 1;   // C(t, k)
@@ -625,9 +745,18 @@ extern "C" pm_status pm_counts_desc(const char *description, const pm_param *p, 
         size_t k = 0;
         while (k < d.params.size() && (!interp[i].name || d.params[k] != interp[i].name)) k++;
         if (k == d.params.size()) return fail(PM_EINVAL, "pm_counts_desc: interpolation over unknown parameter");
-        if (interp[i].period < 1 || interp[i].degree < 0 || interp[i].degree > 10)
+        i64 period = interp[i].period;
+        int degree = interp[i].degree;
+        if (period == 0 || degree == -1) {   // derive what the caller left open
+            i64 dp;
+            int dd;
+            if ((s = derive_interp(d, (int)k, pv, &dp, &dd))) return s;
+            if (period == 0) period = dp;
+            if (degree == -1) degree = dd;
+        }
+        if (period < 1 || degree < 0 || degree > 10)
             return fail(PM_EINVAL, "pm_counts_desc: need period >= 1 and degree 0..10");
-        ip.push_back({(int)k, (i64)interp[i].period, (int)interp[i].degree});
+        ip.push_back({(int)k, period, degree});
     }
     std::vector<pm_feature> v;
     if ((s = counts_rec(d, pv, ip, 0, (u64)1 << 31, v))) return s;
@@ -637,5 +766,26 @@ extern "C" pm_status pm_counts_desc(const char *description, const pm_param *p, 
         canonical_name(v[i]);
         out[i] = v[i];
     }
+    return PM_OK;
+}
+
+extern "C" pm_status pm_counts_desc_interp(const char *description, const char *param, const pm_param *p, size_t np,
+                                           int32_t *period, int32_t *degree) {
+    if (!description || !param || !period || !degree || (np && !p)) return fail(PM_EINVAL, "pm_counts_desc_interp: NULL argument");
+    Desc d;
+    pm_status s = parse_desc(description, d);
+    if (s) return s;
+    std::vector<i64> pv(d.params.size(), 0);
+    for (size_t i = 0; i < np; i++)
+        for (size_t k = 0; k < d.params.size(); k++)
+            if (p[i].key && d.params[k] == p[i].key) pv[k] = (i64)p[i].value;
+    size_t P = 0;
+    while (P < d.params.size() && d.params[P] != param) P++;
+    if (P == d.params.size()) return fail(PM_EINVAL, "pm_counts_desc_interp: unknown parameter '%s'", param);
+    i64 pe;
+    int de;
+    if ((s = derive_interp(d, (int)P, pv, &pe, &de))) return s;
+    *period = (int32_t)pe;
+    *degree = de;
     return PM_OK;
 }

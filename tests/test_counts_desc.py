@@ -94,3 +94,43 @@ def test_bad_descriptions_rejected(text, params):
 def test_wrong_degree_bound_detected():
     with pytest.raises(pm.PMError):
         pm.counts_desc(desc("mm_pf"), interp={"n": (16, 2)}, n=4096)   # madd count is cubic in n
+
+
+@pytest.mark.parametrize("name,param,params,want", [
+    ("mm_pf", "n", dict(n=64), (16, 3)),             # grid n/16, k loop to n/16, n*(16*g1 + l1) index
+    ("fd_tile", "n", dict(n=64), (14, 2)),           # grid (n+13)/14 on both axes
+    ("dg_nopf", "Nel", dict(Np=35, Nel=64), (16, 1)),
+    ("dg_nopf", "Np", dict(Np=35, Nel=64), (16, 2)),  # (Np+15)/16 tiles, j loop to Np, Np*Np*m index
+    ("stream2", "N", dict(N=1 << 16, s=4), (1024, 1)),   # N/(256 s) with s fixed at 4
+])
+def test_period_and_degree_derived(name, param, params, want):
+    assert pm.counts_desc_interp(desc(name), param, **params) == want
+
+
+@pytest.mark.parametrize("name,param,fixed,target,kernel,kparams", [
+    ("mm_pf", "n", {}, 4096, "mm_pf", {}),
+    ("fd_tile", "n", {}, 16383, "fd_tile", {}),
+    ("dg_nopf", "Nel", dict(Np=84), 1 << 18, "dg_nopf", dict(Np=84, L0=16, L1=16)),
+    ("stream2", "N", dict(s=8), 1 << 26, "stream", dict(s=8, L=2)),
+])
+def test_derived_extrapolation_matches_closed_forms(name, param, fixed, target, kernel, kparams):
+    got = pm.counts_desc(desc(name), interp={param: None}, **dict(fixed, **{param: target}))
+    same(got, pm.counts(kernel, **dict(kparams, **{param: target})))
+
+
+def test_derived_in_two_parameters():
+    # nested extrapolation, both periods and degrees derived: DG at Np = 84
+    # (residue 4 of 16) and Nel = 2^18
+    got = pm.counts_desc(desc("dg_nopf"), interp={"Nel": None, "Np": None}, Np=84, Nel=1 << 18)
+    same(got, pm.counts("dg_nopf", Np=84, Nel=1 << 18, L0=16, L1=16))
+
+
+@pytest.mark.parametrize("text,param", [
+    ("params n\ngrid 4\ngroup n\nstmt\n  access x global load float32 4 l0\n", "n"),          # group extent in n
+    ("params n m\ngrid n/m\ngroup 16\nstmt\n  access x global load float32 4 l0\n", "m"),    # divisor depends on m
+    ("params n\ngrid 8\ngroup 16\nstmt\n  loop i 0 n/(l0+1)\n  access x global load float32 4 i\n", "n"),
+])
+def test_underivable_period_refused(text, param):
+    with pytest.raises(pm.PMError) as e:
+        pm.counts_desc_interp(text, param, n=64, m=4)
+    assert "state its period and degree" in str(e.value)
