@@ -41,6 +41,7 @@ def parse():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fit-bench", action="store_true")
+    ap.add_argument("--no-accuracy", action="store_true", help="skip the per-variant held-out accuracy leg")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--filter", default="suite", help="comma-separated suite filter tags")
     ap.add_argument("--dump", default=None, help="write per-variant timings of the last step (JSON)")
@@ -333,6 +334,8 @@ def run_ours(args):
             orc = oracle_fit_rate()
             line["fit"]["max_param_rel_err_vs_oracle"] = fit_vs_oracle(gpu_params, orc.pop("_params"))
             line["fit"]["oracle_cpu"] = orc
+    if not args.no_accuracy:
+        line["accuracy"] = accuracy_leg()
     if rank == 0 and world == 1 and not args.no_cpu:
         line["cpu_baseline"] = cpu_baseline(variants, seconds=12.0)
     if rank == 0:
@@ -621,6 +624,44 @@ def fit_throughput(pm, torch, dev):
             "statuses_plain": {str(s): [r["status"] for _, r in plain].count(s)
                                for s in set(r["status"] for _, r in plain)},
             "_params": {"batched": batched, "plain": [pp for pp, _ in plain]}}
+
+
+def accuracy_leg(trials=3):
+    """Time-prediction accuracy per modeled variant (Section "Results": the
+    geometric mean of the relative error), bounded to well under two
+    minutes: the reduced cross-variant sweep -- the paper's eight modeled
+    variants (two matmul, four DG, two stencil tiles), the direct stencil,
+    the DG tile form and the two tensor-core tiles, each calibrated on the
+    microbenchmarks, its computation's twins and every other of its own
+    sizes, predicting the sizes held out (L2 flushed before every trial) --
+    and the model-guided autotuner at reduced sizes (24 SIMT matmul tiles at
+    n = 3840, 12 stencil tiles at n = 8192): predicted against measured
+    order."""
+    from paper_1904_09538_gb300 import autotune as A
+    from paper_1904_09538_gb300 import experiments as E
+    t0 = time.perf_counter()
+    rep = E.run_studies(trials=trials, study_list=E.sweep_studies(reduced=True), flush_l2=True)
+    by = {}
+    for name, r in rep.items():
+        if name == "sweep_tc_tiles":
+            continue
+        for v, e in r["variants"].items():
+            by[v] = {"geomean": round(e["geomean_rel_err"], 4), "max": round(e["max_rel_err"], 4),
+                     "heldout": e["n_sizes"], "fit_status": r["fit"]["status"]}
+    tcr = rep["sweep_tc_tiles"]
+    t1 = time.perf_counter()
+    tune = {}
+    for fam, r in (("mm_simt", A.rank_family(target=3840, calib_sizes=(1536, 2304), trials=trials)),
+                   ("fd_block", A.rank_stencil(target=8192, calib_sizes=(2048, 4096), trials=trials))):
+        tune[fam] = {"target_n": r["target_n"], "variants": r["n_shapes"] - r["n_pruned"], "pruned": r["n_pruned"],
+                     "spearman": round(r["spearman"], 3), "kendall": round(r["kendall"], 3),
+                     "slowdown_of_predicted_best": round(r["slowdown_of_predicted_best"], 3),
+                     "slowdown_top3": round(r["slowdown_after_timing_predicted_top_k"].get("3", float("nan")), 3)}
+    return {"heldout_by_variant": by, "trials": trials,
+            "tc_tiles_one_model": {"geomean": round(tcr["geomean_rel_err"], 4), "max": round(tcr["max_rel_err"], 4),
+                                   "spearman": round(tcr["spearman"], 3),
+                                   "faster_tile_identified": tcr["fastest_variant_identified"]},
+            "autotune": tune, "sweep_s": round(t1 - t0, 1), "autotune_s": round(time.perf_counter() - t1, 1)}
 
 
 def fit_vs_oracle(params, oracle_params):

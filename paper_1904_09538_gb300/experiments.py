@@ -71,8 +71,10 @@ def common_measurements():
     return out
 
 
-def studies():
-    """(name, model expression, measurement kernels, modeled kernels) per computation."""
+def studies(reduced=False):
+    """(name, model expression, measurement kernels, modeled kernels) per computation.
+    reduced: every third modeled size and every second twin size (a bounded
+    form for tests and benchmark runs)."""
     mm_sizes = list(range(512, 4096 + 1, 128))                # 29 sizes
     mm_twin_sizes = [512, 1024, 1536, 2048, 2560, 3072, 3584, 4096]
     mm_gm = [GENERIC] + [tagged(t, n) for t, n in (("mm-PF-a", "pfa"), ("mm-PF-b", "pfb"),
@@ -118,10 +120,22 @@ def studies():
     out.append(dict(name="fd", gmem=fd_gm, expr=linear(fd_gm),
                     measure=common_measurements() + fd_twins,
                     modeled=[(k, {"n": n}) for k in ("fd_tile", "fd_tile18", "fd_direct") for n in fd_sizes]))
+    if reduced:
+        for st in out:
+            seen = {}
+            keep = []
+            for k, p in st["measure"]:
+                if k in TWIN_KERNELS:
+                    seen[k] = seen.get(k, -1) + 1
+                    if seen[k] % 2:
+                        continue
+                keep.append((k, p))
+            st["measure"] = keep
+            st["modeled"] = st["modeled"][::3]
     return out
 
 
-def sweep_studies():
+def sweep_studies(reduced=False):
     """The cross-variant sweep: 10 modeled variants (prefetching fp32 matmul,
     BF16 tensor-core matmul with 128 x 256 and 256 x 256 tiles, DG noPF /
     uPF / dmPF / dmPF-T with 16x16 work-groups and the DG tile form, stencil
@@ -130,7 +144,12 @@ def sweep_studies():
     and the variant's own other sizes -- the paper's "few extra on-line
     calibration runs" -- and predicts the held-out sizes.  A tenth study
     calibrates one model on both tensor-core tiles and ranks them at the
-    held-out sizes."""
+    held-out sizes.
+
+    reduced: a bounded form for a benchmark run -- every second size of each
+    variant (so 4-5 held out per variant), matmul up to n = 3072, and the
+    paper's other two modeled variants (non-prefetching matmul, 18 x 18
+    stencil tile) added."""
     base = {s["name"]: s for s in studies()}
     # the A and B tile loads both scale as n^3 at a fixed tile shape, so one
     # bf16 load feature carries them
@@ -146,6 +165,14 @@ def sweep_studies():
     plan += [("dg_tile", "dg_16x16", None, [dict(Np=Np, Nel=Nel) for Np in (20, 35, 56, 84) for Nel in nels])]
     plan += [(k, "fd", None, [{"n": int(round(1024 * 2 ** (i / 7.0)))} for i in range(29)])
              for k in ("fd_tile", "fd_direct")]
+    if reduced:
+        mm_small = [{"n": n} for n in range(512, 3072 + 1, 128)]
+        plan = [(k, parent, expr, mm_small if k == "mm_pf" else sizes) for k, parent, expr, sizes in plan]
+        plan.insert(1, ("mm_nopf", "matmul", None, mm_small))
+        plan.append(("fd_tile18", "fd", None, [{"n": int(round(1024 * 2 ** (i / 7.0)))} for i in range(29)]))
+        plan = [(k, parent, expr, sizes[::2]) for k, parent, expr, sizes in plan]
+        tc_sizes = tc_sizes[::2]
+        base = {st["name"]: st for st in studies(reduced=True)}   # twins at every second size
     out = []
     for k, parent, expr, sizes in plan:
         fit = [(k, p) for i, p in enumerate(sizes) if i % 3 != 2]
@@ -160,6 +187,12 @@ def sweep_studies():
                     measure=common_measurements() + [(k, p) for k in tcs for i, p in enumerate(tc_sizes) if i % 3 != 2],
                     modeled=[(k, p) for k in tcs for i, p in enumerate(tc_sizes) if i % 3 == 2]))
     return out
+
+
+# the work-removed twins (Algorithm 3) of the modeled kernels
+TWIN_KERNELS = {"mm_pf_a", "mm_pf_b", "mm_nopf_a", "mm_nopf_b", "dg_nopf_u", "dg_nopf_dm", "dg_dmpf_u",
+                "dg_dmpf_dm", "dg_res", "dg_dmpft_u", "dg_dmpft_res", "dg_upf_u", "fd_tile_u", "fd_tile_res",
+                "fd_direct_u", "fd_direct_res", "fd_tile18_u", "fd_tile18_res"}
 
 
 class Buffers:
@@ -315,7 +348,7 @@ def choose_by_residual(residuals):
     return min(cand, key=cand.get) if cand else None
 
 
-def diagnostics(trials=10, seed=1234, flush_l2=True, cache_path=None):
+def diagnostics(trials=10, seed=1234, flush_l2=True, cache_path=None, reduced=False):
     """The paper's diagnostic experiments on this GPU.
 
     ab_ratio (Section "Data Motion Features", Table ab_pattern): average cost
@@ -334,14 +367,18 @@ def diagnostics(trials=10, seed=1234, flush_l2=True, cache_path=None):
     chooses (Section "Models Demonstrated"), and the geomean error of the
     linear, the tanh-overlap and the partial-overlap model calibrated on the
     same measurement set; per study, each model's calibration residual and
-    the model with the smaller one (the section's other indicator)."""
+    the model with the smaller one (the section's other indicator).
+
+    reduced: the studies' reduced form (studies(reduced=True)), fewer a/b
+    and matmul sizes: a bounded run for tests.  Every calibration in the
+    report carries its measured rows, for a refit elsewhere."""
     import torch
     dev = torch.device("cuda", torch.cuda.current_device())
     bufs = Buffers(torch, dev, seed)
     out = {}
     # -- a vs b pattern
     rows = []
-    for n in range(2048, 3584 + 1, 256):
+    for n in range(2048, 3584 + 1, 768 if reduced else 256):
         per = {}
         for k, tag in (("mm_pf_a", "mm-PF-a"), ("mm_pf_b", "mm-PF-b")):
             loads = Model("f_wall_time", "p_x * f_mem_access_tag:%s" % tag).feature_values(k, n=n)[0]
@@ -356,16 +393,19 @@ def diagnostics(trials=10, seed=1234, flush_l2=True, cache_path=None):
     X = np.stack([m.feature_values(k, **p) for k, p in cal])
     t = measure(cal, bufs, trials, flush_l2)
     p, rep = m.fit(X, t)
-    sizes = [512, 1024, 1536, 2048, 3072, 4096]
+    madd_rows = [{"kernel": k, "params": q, "measured_s": float(x)} for (k, q), x in zip(cal, t)]
+    sizes = [512, 1024, 2048] if reduced else [512, 1024, 1536, 2048, 3072, 4096]
     tm = measure([("mm_pf", {"n": n}) for n in sizes], bufs, trials, flush_l2)
     im = m.params.index("p_madd")
     fm = m.features.index("f_op_float32_madd")
     share = [float(p[im] * m.feature_values("mm_pf", n=n)[fm] / tt) for n, tt in zip(sizes, tm)]
-    out["madd_only"] = {"p_madd_s_per_subgroup_op": float(p[im]), "rate_flops": 64.0 / float(p[im]),
-                        "fit": rep, "mm_pf_sizes": sizes, "mm_pf_madd_share": share}
+    out["madd_only"] = {"expr": m.expr, "params": dict(zip(m.params, [float(x) for x in p])),
+                        "p_madd_s_per_subgroup_op": float(p[im]), "rate_flops": 64.0 / float(p[im]),
+                        "fit": rep, "mm_pf_sizes": sizes, "mm_pf_madd_share": share, "rows": madd_rows}
     # -- overlap analysis, linear vs tanh-overlap on the same measurement sets
     res = {}
-    for st in studies():
+    fits = {}
+    for st in studies(reduced):
         gm = st["gmem"]
         exprs = {"linear": linear(gm), "nonlinear": nonlinear(gm), "partial": partial(gm)}
         if len(set(re.findall(r"\bp_\w+", exprs["partial"]))) > 16:   # the fit's parameter limit
@@ -389,16 +429,24 @@ def diagnostics(trials=10, seed=1234, flush_l2=True, cache_path=None):
         per["calibration_residual"] = resid
         per["chosen_by_residual"] = by_resid
         res[st["name"]] = per
+        for kind in exprs:
+            r = rep_s[st["name"] + "_" + kind]
+            fits[st["name"] + "_" + kind] = {"expr": r["expr"], "params": r["params"], "fit": r["fit"],
+                                             "rows": r["measure_rows"]}
     out["overlap"] = res
+    out["calibrations"] = fits
     # -- local memory split by lid(1) stride (Section "Finite Differences"): the
     # 16x16 and 18x18 stencil tiles differ in the lid(1) stride of their local
     # accesses; calibrate a per-stride correction on the 2-D local kernels
-    fd = [st for st in studies() if st["name"] == "fd"][0]
+    fd = [st for st in studies(reduced) if st["name"] == "fd"][0]
     l2d = generate(["lmem2d"])
     split_onchip = ONCHIP + " + p_l18 * f_mem_access_local_float32_lstrides:{1:18}"
     sts = [dict(fd, name="fd_single_lmem", expr=linear(fd["gmem"]), measure=fd["measure"] + l2d),
            dict(fd, name="fd_split_lmem", expr=linear(fd["gmem"], onchip=split_onchip), measure=fd["measure"] + l2d)]
     rep_s = run_studies(trials, seed=seed, flush_l2=flush_l2, cache_path=cache_path, study_list=sts)
+    for name in ("fd_single_lmem", "fd_split_lmem"):
+        r = rep_s[name]
+        fits[name] = {"expr": r["expr"], "params": r["params"], "fit": r["fit"], "rows": r["measure_rows"]}
     per_access = {}
     for T in (16, 18):
         rows = [(k, p) for k, p in l2d if p["T"] == T]
