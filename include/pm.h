@@ -299,10 +299,11 @@ typedef struct {
  * its inputs).  A region that any host output buffer of the batch overlaps
  * is not shared (its host contents may change during the batch); each of
  * its readers copies it.  Device staging comes from the default memory pool
- * (see pm_run_host).  out: njobs timings; copy_ms (nullable): time from the
- * first input copy's start to the last output copy's end minus the
- * kernels' time; on error the failing job's index is in the message and
- * later jobs are not run. */
+ * (see pm_run_host).  out: njobs timings; copy_ms (nullable): the copies'
+ * own device time -- per job, from the moment its input copies may start
+ * to their end, plus its output copies -- summed over the jobs (the time
+ * between jobs, host work included, is not counted); on error the failing
+ * job's index is in the message and later jobs are not run. */
 pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_opts *opts, void *stream,
                             pm_timing *out, double *copy_ms);
 
@@ -311,6 +312,16 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
  * device->host (outputs with a non-NULL host pointer).  Either output
  * pointer may be NULL.  Same validation and errors as pm_run_host_batch. */
 pm_status pm_run_host_batch_bytes(const pm_host_job *jobs, size_t njobs, uint64_t *h2d_bytes, uint64_t *d2h_bytes);
+
+/* Unloaded load latency of the memory level that holds a buffer (the
+ * latency in the Little's-law bound of a pattern with few bytes in flight
+ * per work-item; not a paper feature).  buf: caller-owned device buffer of
+ * `bytes` bytes (128-byte aligned, 256 bytes .. 512 GiB), overwritten with a
+ * chain of line indices; one thread then follows `hops` links with L1-
+ * bypassing loads, timed with CUDA events on `stream`.  *ns_per_hop: mean
+ * time per dependent load -- HBM latency for a buffer much larger than L2,
+ * L2 latency for a buffer well inside it.  Blocks until done. */
+pm_status pm_probe_latency(void *buf, size_t bytes, int32_t hops, double *ns_per_hop, void *stream);
 
 /* ---------------------------------------------------------------- models */
 

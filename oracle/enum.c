@@ -1219,82 +1219,86 @@ static int setup_fdb(ctx *c) {
 /* ======================================================================
  * DG tile (GB300 form of the DG derivative): P = {Np, Nel}.  For one m
  * (gid0 < 3) and 128 elements (gid1): res[m, k, i] = sum_j D[m, i, j]
- * u[k, j] as one matrix product; 16 x 16 work-group, grid (3, ceil(Nel /
- * 128)).  Rows i are padded to NPP = 16 NB (NB = ceil(Np / 16)) with zeros,
- * j runs over Q = ceil(Np / 4) chunks of four (16-byte vectors), zero beyond
- * Np; Dt row pitch PD floats (PD >= 4 Q, PD % 32 == 4).
- *  - D staging: for row block ib < NB and chunk block qb: work-item
- *    (lid0, lid1) handles i = lid1 + 16 ib and chunk q = lid0 + 16 qb < Q;
- *    for i < Np it loads D[m, i, 4q .. 4q+3] (one 16-byte vector when
- *    Np % 4 == 0, else the j < Np elements one by one); it stores the chunk
- *    to Dt[i][q] (one 16-byte vector);
+ * u[k, j] as one matrix product.  NB = ceil(Np / 16) columns per
+ * work-item, XL = ceil(Np / NB) x-lanes: work-group XL x 16, grid
+ * (3, ceil(Nel / 128)); node rows i padded to NPP = XL NB with zeros, j in
+ * Q = ceil(Np / 2) pairs (8-byte vectors), zero beyond Np; Dt row pitch PD
+ * floats (PD >= 2 Q, PD % 32 == 2).
+ *  - D staging: for row block ib < ceil(NPP / 16) and pair block
+ *    qb < ceil(Q / XL): work-item (lid0, lid1) handles i = lid1 + 16 ib and
+ *    q = lid0 + XL qb; for q < Q and i < NPP: when i < Np it loads
+ *    D[m, i, 2q .. 2q+1] (one 8-byte vector when Np is even, else the j < Np
+ *    elements one by one); it stores the pair to Dt[i][q] (one vector);
  *  - u tile: work-item (0,0) copies the tile's rows (one bulk copy, counted
- *    per element); one barrier; when Np % 4 != 0 every work-item then
- *    re-lays the 128 rows out with pitch 4 Q (row r = lid1 + 16 rb, chunk
- *    q = lid0 + 16 qb < Q: element loads j < Np, one vector store) and a
+ *    per element); one barrier; when Np is odd every work-item then re-lays
+ *    the 128 rows out with pitch 2 Q (row r = lid1 + 16 rb, pair
+ *    q = lid0 + XL qb < Q: element loads j < Np, one vector store) and a
  *    second barrier follows;
- *  - for every chunk q < Q: vector loads Us[lid1 + 16 a][q] (a < 8) and
- *    Dt[lid0 + 16 b][q] (b < NB), 4 x 8 x NB madds;
- *  - stores res[m, k0 + lid1 + 16 a, lid0 + 16 b] for k < Nel, i < Np.
+ *  - for every pair q < Q: vector loads Us[lid1 + 16 a][q] (a < 8) and
+ *    Dt[lid0 + XL b][q] (b < NB), 2 x 8 x NB madds (one running sum over the
+ *    even j and one over the odd j per output);
+ *  - per output (b < NB, a < 8): one add of its two sums, then the store
+ *    res[m, k0 + lid1 + 16 a, lid0 + XL b] for k < Nel, i < Np.
  * ====================================================================== */
 #define DT_NB(c) (cdiv((c)->P[0], 16))
-#define DT_Q(c) (cdiv((c)->P[0], 4))
-static long long dt_pd(const ctx *c) { long long p = 4 * DT_Q(c); while (p % 32 != 4) p++; return p; }
+#define DT_XL(c) (cdiv((c)->P[0], DT_NB(c)))
+#define DT_Q(c) (cdiv((c)->P[0], 2))
+static long long dt_pd(const ctx *c) { long long p = 2 * DT_Q(c); while (p % 32 != 2) p++; return p; }
 static long long ix_dt_D(const ctx *c, const long long *g, const long long *l, const long long *lv) {
     long long Np = c->P[0];
-    return G0 * Np * Np + (L1_ + 16 * lv[0]) * Np + 4 * (L0_ + 16 * lv[1]) + lv[2];
+    return G0 * Np * Np + (L1_ + 16 * lv[0]) * Np + 2 * (L0_ + DT_XL(c) * lv[1]) + lv[2];
 }
-static long long ix_dt_D4(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+static long long ix_dt_D2(const ctx *c, const long long *g, const long long *l, const long long *lv) {
     long long Np = c->P[0];
-    return (G0 * Np * Np + (L1_ + 16 * lv[0]) * Np) / 4 + L0_ + 16 * lv[1];
+    return (G0 * Np * Np + (L1_ + 16 * lv[0]) * Np) / 2 + L0_ + DT_XL(c) * lv[1];
 }
 static long long ix_dt_Dt(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)g; return (L1_ + 16 * lv[0]) * (dt_pd(c) / 4) + L0_ + 16 * lv[1];
+    (void)g; return (L1_ + 16 * lv[0]) * (dt_pd(c) / 2) + L0_ + DT_XL(c) * lv[1];
 }
 static long long ix_dt_u(const ctx *c, const long long *g, const long long *l, const long long *lv) {
     (void)l; return 128 * c->P[0] * G1 + lv[0];
 }
 static long long ix_dt_R(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)g; return (L1_ + 16 * lv[0]) * c->P[0] + 4 * (L0_ + 16 * lv[1]) + lv[2];
+    (void)g; return (L1_ + 16 * lv[0]) * c->P[0] + 2 * (L0_ + DT_XL(c) * lv[1]) + lv[2];
 }
 static long long ix_dt_Ur(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)g; return (L1_ + 16 * lv[0]) * DT_Q(c) + L0_ + 16 * lv[1];
+    (void)g; return (L1_ + 16 * lv[0]) * DT_Q(c) + L0_ + DT_XL(c) * lv[1];
 }
 static long long ix_dt_Us(const ctx *c, const long long *g, const long long *l, const long long *lv) {
     (void)g; return (L1_ + 16 * lv[1]) * DT_Q(c) + lv[0];
 }
 static long long ix_dt_Dl(const ctx *c, const long long *g, const long long *l, const long long *lv) {
-    (void)g; return (L0_ + 16 * lv[1]) * (dt_pd(c) / 4) + lv[0];
+    (void)g; return (L0_ + DT_XL(c) * lv[1]) * (dt_pd(c) / 2) + lv[0];
 }
 static long long ix_dt_res(const ctx *c, const long long *g, const long long *l, const long long *lv) {
     long long Np = c->P[0], Nel = c->P[1];
-    return G0 * Nel * Np + (128 * G1 + L1_ + 16 * lv[1]) * Np + L0_ + 16 * lv[0];
+    return G0 * Nel * Np + (128 * G1 + L1_ + 16 * lv[1]) * Np + L0_ + DT_XL(c) * lv[0];
 }
 /* statements: 0 D vector load, 1 D element load, 2 Dt store, 3 u copy,
  * 4 raw-row element load, 5 re-laid row store, 6 Us load, 7 Dt load,
- * 8 madd, 9 res store */
+ * 8 two madds, 9 res store, 10 add of the even-j and odd-j sums */
 static void walk_dgt(ctx *c) {
-    long long Np = c->P[0], Nel = c->P[1], NB = DT_NB(c), Q = DT_Q(c), lv[3];
+    long long Np = c->P[0], Nel = c->P[1], NB = DT_NB(c), XL = DT_XL(c), Q = DT_Q(c), NPP = XL * NB, lv[3];
     long long k0 = 128 * c->g[1], rows = Nel - k0 < 128 ? Nel - k0 : 128;
-    for (lv[0] = 0; lv[0] < NB; lv[0]++)
-        for (lv[1] = 0; lv[1] < cdiv(Q, 16); lv[1]++) {
-            long long q = c->l[0] + 16 * lv[1], i = c->l[1] + 16 * lv[0];
-            if (q >= Q) continue;
+    for (lv[0] = 0; lv[0] < cdiv(NPP, 16); lv[0]++)
+        for (lv[1] = 0; lv[1] < cdiv(Q, XL); lv[1]++) {
+            long long q = c->l[0] + XL * lv[1], i = c->l[1] + 16 * lv[0];
+            if (q >= Q || i >= NPP) continue;
             if (i < Np) {
-                if (Np % 4 == 0) { lv[2] = 0; X(c, 0, lv); }
-                else for (lv[2] = 0; lv[2] < 4; lv[2]++) if (4 * q + lv[2] < Np) X(c, 1, lv);
+                if (Np % 2 == 0) { lv[2] = 0; X(c, 0, lv); }
+                else for (lv[2] = 0; lv[2] < 2; lv[2]++) if (2 * q + lv[2] < Np) X(c, 1, lv);
             }
             X(c, 2, lv);
         }
     if (c->l[0] == 0 && c->l[1] == 0)
         for (lv[0] = 0; lv[0] < rows * Np; lv[0]++) X(c, 3, lv);
     BAR(c);
-    if (Np % 4) {
+    if (Np % 2) {
         for (lv[0] = 0; lv[0] < 8; lv[0]++)
-            for (lv[1] = 0; lv[1] < cdiv(Q, 16); lv[1]++) {
-                long long q = c->l[0] + 16 * lv[1];
+            for (lv[1] = 0; lv[1] < cdiv(Q, XL); lv[1]++) {
+                long long q = c->l[0] + XL * lv[1];
                 if (q >= Q) continue;
-                for (lv[2] = 0; lv[2] < 4; lv[2]++) if (4 * q + lv[2] < Np) X(c, 4, lv);
+                for (lv[2] = 0; lv[2] < 2; lv[2]++) if (2 * q + lv[2] < Np) X(c, 4, lv);
                 X(c, 5, lv);
             }
         BAR(c);
@@ -1306,33 +1310,36 @@ static void walk_dgt(ctx *c) {
             for (lv[2] = 0; lv[2] < NB; lv[2]++) X(c, 8, lv);
     }
     for (lv[0] = 0; lv[0] < NB; lv[0]++)
-        for (lv[1] = 0; lv[1] < 8; lv[1]++)
-            if (k0 + c->l[1] + 16 * lv[1] < Nel && c->l[0] + 16 * lv[0] < Np) X(c, 9, lv);
+        for (lv[1] = 0; lv[1] < 8; lv[1]++) {
+            X(c, 10, lv);
+            if (k0 + c->l[1] + 16 * lv[1] < Nel && c->l[0] + XL * lv[0] < Np) X(c, 9, lv);
+        }
 }
 static int setup_dgt(ctx *c) {
     long long Np = c->P[0], Nel = c->P[1];
     if (Np < 1 || Np > 96 || Nel < 4 || Nel % 4 || Nel > 65535LL * 128) return -1;
     c->grid[0] = 3; c->grid[1] = cdiv(Nel, 128); c->grid[2] = 1;
-    c->wg[0] = 16; c->wg[1] = 16; c->wg[2] = 1;
+    c->wg[0] = DT_XL(c); c->wg[1] = 16; c->wg[2] = 1;
     int s0 = add_stmt(c, 2, DT_F32, 0, 0, 0);
-    stmt_site(c, s0, add_site(c, "dgt-D", MEM_GLOBAL, DIR_LOAD, "float32x4", 16, ix_dt_D4));
+    stmt_site(c, s0, add_site(c, "dgt-D", MEM_GLOBAL, DIR_LOAD, "float32x2", 8, ix_dt_D2));
     int s1 = add_stmt(c, 3, DT_F32, 0, 0, 0);
     stmt_site(c, s1, add_site(c, "dgt-D", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dt_D));
     int s2 = add_stmt(c, 2, DT_F32, 0, 0, 0);
-    stmt_site(c, s2, add_site(c, "dgt-Dt", MEM_LOCAL, DIR_STORE, "float32x4", 16, ix_dt_Dt));
+    stmt_site(c, s2, add_site(c, "dgt-Dt", MEM_LOCAL, DIR_STORE, "float32x2", 8, ix_dt_Dt));
     int s3 = add_stmt(c, 1, DT_F32, 0, 0, 0);
     stmt_site(c, s3, add_site(c, "dgt-u", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dt_u));
     int s4 = add_stmt(c, 3, DT_F32, 0, 0, 0);
     stmt_site(c, s4, add_site(c, "dgt-R", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_dt_R));
     int s5 = add_stmt(c, 2, DT_F32, 0, 0, 0);
-    stmt_site(c, s5, add_site(c, "dgt-Ur", MEM_LOCAL, DIR_STORE, "float32x4", 16, ix_dt_Ur));
+    stmt_site(c, s5, add_site(c, "dgt-Ur", MEM_LOCAL, DIR_STORE, "float32x2", 8, ix_dt_Ur));
     int s6 = add_stmt(c, 2, DT_F32, 0, 0, 0);
-    stmt_site(c, s6, add_site(c, "dgt-Us", MEM_LOCAL, DIR_LOAD, "float32x4", 16, ix_dt_Us));
+    stmt_site(c, s6, add_site(c, "dgt-Us", MEM_LOCAL, DIR_LOAD, "float32x2", 8, ix_dt_Us));
     int s7 = add_stmt(c, 2, DT_F32, 0, 0, 0);
-    stmt_site(c, s7, add_site(c, "dgt-Dl", MEM_LOCAL, DIR_LOAD, "float32x4", 16, ix_dt_Dl));
-    add_stmt(c, 3, DT_F32, 0, 0, 4);
+    stmt_site(c, s7, add_site(c, "dgt-Dl", MEM_LOCAL, DIR_LOAD, "float32x2", 8, ix_dt_Dl));
+    add_stmt(c, 3, DT_F32, 0, 0, 2);
     int s9 = add_stmt(c, 2, DT_F32, 0, 0, 0);
     stmt_site(c, s9, add_site(c, "dgt-res", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dt_res));
+    add_stmt(c, 2, DT_F32, 1, 0, 0);
     c->walk = walk_dgt;
     return 0;
 }

@@ -7,6 +7,7 @@
 //
 // Each kernel's loop domain is the one its CUDA kernel executes; the
 // formulas below count that domain's statement instances directly.
+#include <algorithm>
 #include <cstring>
 
 #include "pm_internal.h"
@@ -662,64 +663,88 @@ pm_status counts_fdb(const KP &kp, std::vector<pm_feature> &v) {
 }
 
 // ---------------------------------------------------------------- DG tile
-// 16 x 16 work-group per (m, 128 elements), grid (3, ceil(Nel / 128)); rows
-// i padded to NPP = 16 NB (NB = ceil(Np / 16)), j in Q = ceil(Np / 4)
-// chunks of four (16-byte vectors), Dt row pitch PD (PD >= 4 Q, PD % 32 ==
-// 4).  Work-item (x, y): D staging for row i = y + 16 ib and chunk
-// q = x + 16 qb < Q -- a vector load of D[m, i, 4q ..] when Np % 4 == 0
-// (else the j < Np elements one by one) for i < Np, a vector store to
-// Dt[i][q]; work-item (0, 0) copies the u tile (one bulk copy, counted per
-// element); when Np % 4 != 0 the 128 rows are re-laid out with pitch 4 Q
-// (element loads, vector stores) behind a second barrier; then per chunk: 8
-// vector loads of Us[y + 16 a][q], NB of Dt[x + 16 b][q], 4 x 8 x NB madds;
-// stores res[m, k0 + y + 16 a, x + 16 b].  A sub-group is lanes (x, y) with
-// y in {2 w, 2 w + 1}.
+// XL x 16 work-group per (m, 128 elements), grid (3, ceil(Nel / 128)):
+// NB = ceil(Np / 16) columns per work-item, XL = ceil(Np / NB) x-lanes, node
+// rows padded to NPP = XL NB, j in Q = ceil(Np / 2) pairs (8-byte vectors),
+// Dt row pitch PD (PD >= 2 Q, PD % 32 == 2).  Work-item (x, y): D staging for
+// row i = y + 16 ib (ib < ceil(NPP / 16)) and pair q = x + XL qb < Q -- a
+// vector load of D[m, i, 2q ..] when Np is even (else the j < Np elements one
+// by one) for i < Np, a vector store to Dt[i][q] for i < NPP; work-item
+// (0, 0) copies the u tile (one bulk copy, counted per element); when Np is
+// odd the 128 rows are re-laid out with pitch 2 Q (element loads, vector
+// stores) behind a second barrier; then per pair: 8 vector loads of
+// Us[y + 16 a][q], NB of Dt[x + XL b][q], 2 x 8 x NB madds (running sums
+// over the even and the odd j); per output one add of its two sums, then
+// the store res[m, k0 + y + 16 a, x + XL b] (k < Nel, i < Np).  A sub-group is 32
+// consecutive linear ids t = x + XL y; its count for a statement instance is
+// taken over the work-group's lanes directly (at most 256 of them).
 pm_status counts_dgt(const KP &kp, std::vector<pm_feature> &v) {
-    const i64 Np = kp.i(0), Nel = kp.i(1), NB = cdiv(Np, 16), Q = cdiv(Np, 4), QB = cdiv(Q, 16);
-    i64 PD = 4 * Q;
-    while (PD % 32 != 4) PD++;
-    const bool v4 = Np % 4 == 0;
+    const i64 Np = kp.i(0), Nel = kp.i(1), NB = cdiv(Np, 16), XL = cdiv(Np, NB), NPP = XL * NB;
+    const i64 Q = cdiv(Np, 2), QB = cdiv(Q, XL), RB = cdiv(NPP, 16), NT = 16 * XL, NW = cdiv(NT, 32);
+    i64 PD = 2 * Q;
+    while (PD % 32 != 2) PD++;
+    const bool even = Np % 2 == 0;
     const i64 T = cdiv(Nel, 128), Tfull = Nel / 128, rlast = Nel % 128, G = 3 * T;
-    const u64 uG = (u64)G, uNp = (u64)Np, uQ = (u64)Q, uNB = (u64)NB, uQB = (u64)QB;
-    Out o(v);
-    o.op(0, 2, uG * 256 * 32 * uNB * uQ, uG * 8 * 32 * uNB * uQ);
-    // sub-groups with a row y + 16 ib < Np, summed over the row blocks ib
-    u64 sg_in = 0;
-    for (i64 ib = 0; ib < NB; ib++)
-        for (i64 w = 0; w < 8; w++) sg_in += (2 * w + 16 * ib < Np);
-    // (chunk block, element) pairs with an element j < Np in some lane
-    u64 qe = 0;
-    for (i64 qb = 0; qb < QB; qb++)
-        for (i64 e = 0; e < 4; e++) qe += (64 * qb + e < Np);
-    auto sg_rows = [](i64 r) {
+    const u64 uG = (u64)G, uNp = (u64)Np, uQ = (u64)Q, uNB = (u64)NB;
+    // active sub-groups of one work-group for a lane predicate pred(x, y)
+    auto sg = [&](auto pred) {
         u64 n = 0;
-        for (i64 a = 0; a < 8; a++)
-            for (i64 w = 0; w < 8; w++) n += (2 * w + 16 * a < r);
+        for (i64 w = 0; w < NW; w++) {
+            bool any = false;
+            for (i64 t = 32 * w; t < std::min(32 * w + 32, NT) && !any; t++) any = pred(t % XL, t / XL);
+            n += any;
+        }
         return n;
     };
+    u64 sg_D = 0, sg_Dt = 0, sg_R = 0, sg_Ur = 0, sg_res_full = 0, sg_res_last = 0;
+    for (i64 ib = 0; ib < RB; ib++)
+        for (i64 qb = 0; qb < QB; qb++) {
+            auto in = [&](i64 x, i64 y) { return x + XL * qb < Q && y + 16 * ib < Np; };
+            if (even) {
+                sg_D += sg(in);
+            } else {
+                for (i64 e = 0; e < 2; e++)
+                    sg_D += sg([&](i64 x, i64 y) { return in(x, y) && 2 * (x + XL * qb) + e < Np; });
+            }
+            sg_Dt += sg([&](i64 x, i64 y) { return x + XL * qb < Q && y + 16 * ib < NPP; });
+        }
+    for (i64 qb = 0; qb < QB; qb++) {
+        for (i64 e = 0; e < 2; e++)
+            sg_R += 8 * sg([&](i64 x, i64) { return x + XL * qb < Q && 2 * (x + XL * qb) + e < Np; });
+        sg_Ur += 8 * sg([&](i64 x, i64) { return x + XL * qb < Q; });
+    }
+    for (i64 b = 0; b < NB; b++)
+        for (i64 a = 0; a < 8; a++) {
+            sg_res_full += sg([&](i64 x, i64) { return x + XL * b < Np; });
+            if (rlast) sg_res_last += sg([&](i64 x, i64 y) { return x + XL * b < Np && y + 16 * a < rlast; });
+        }
+    Out o(v);
+    o.op(0, 0, uG * (u64)NT * 8 * uNB, uG * (u64)NW * 8 * uNB);
+    o.op(0, 2, uG * (u64)NT * 8 * uNB * uQ * 2, uG * (u64)NW * 8 * uNB * uQ * 2);
     auto site = [&](const char *tag, int mem, int dir, bool vec, i64 l0, i64 l1, i64 g0, i64 g1, i64 loop, u64 wi,
-                    u64 sg, u64 foot) {
+                    u64 sgc, u64 foot) {
         Site x{};
-        x.tag = tag; x.mem = mem; x.dir = dir; x.dtype = vec ? "float32x4" : "float32"; x.dsize = vec ? 16 : 4;
+        x.tag = tag; x.mem = mem; x.dir = dir; x.dtype = vec ? "float32x2" : "float32"; x.dsize = vec ? 8 : 4;
         x.nl = 2; x.l[0] = l0; x.l[1] = l1; x.ng = 2; x.g[0] = g0; x.g[1] = g1; x.loop = loop;
-        x.wi = wi; x.sg = sg; x.foot = foot;
+        x.wi = wi; x.sg = sgc; x.foot = foot;
         o.site(x);
     };
-    if (v4)
-        site("dgt-D", GL, LD, true, 1, Np / 4, Np * Np / 4, 0, 16, uG * uNp * uQ, uG * uQB * sg_in, 3 * uNp * uQ);
+    if (even)
+        site("dgt-D", GL, LD, true, 1, Np / 2, Np * Np / 2, 0, XL, uG * uNp * uQ, uG * sg_D, 3 * uNp * uQ);
     else
-        site("dgt-D", GL, LD, false, 4, Np, Np * Np, 0, 1, uG * uNp * uNp, uG * sg_in * qe, 3 * uNp * uNp);
-    site("dgt-Dt", LO, ST, true, 1, PD / 4, 0, 0, 16, uG * 16 * uNB * uQ, uG * 8 * uNB * uQB, 16 * uNB * uQ);
+        site("dgt-D", GL, LD, false, 2, Np, Np * Np, 0, 1, uG * uNp * uNp, uG * sg_D, 3 * uNp * uNp);
+    site("dgt-Dt", LO, ST, true, 1, PD / 2, 0, 0, XL, uG * (u64)NPP * uQ, uG * sg_Dt, (u64)NPP * uQ);
     site("dgt-u", GL, LD, false, 0, 0, 0, 128 * Np, 1, 3 * (u64)Nel * uNp, 3 * (u64)Nel * uNp, (u64)Nel * uNp);
-    if (!v4) {
-        site("dgt-R", LO, LD, false, 4, Np, 0, 0, 1, uG * 128 * uNp, uG * 64 * qe, 128 * uNp);
-        site("dgt-Ur", LO, ST, true, 1, Q, 0, 0, 16, uG * 128 * uQ, uG * 64 * uQB, 128 * uQ);
+    if (!even) {
+        site("dgt-R", LO, LD, false, 2, Np, 0, 0, 1, uG * 128 * uNp, uG * sg_R, 128 * uNp);
+        site("dgt-Ur", LO, ST, true, 1, Q, 0, 0, XL, uG * 128 * uQ, uG * sg_Ur, 128 * uQ);
     }
-    site("dgt-Us", LO, LD, true, 0, Q, 0, 0, 16 * Q, uG * 256 * 8 * uQ, uG * 64 * uQ, 128 * uQ);
-    site("dgt-Dl", LO, LD, true, PD / 4, 0, 0, 0, 4 * PD, uG * 256 * uNB * uQ, uG * 8 * uNB * uQ, 16 * uNB * uQ);
+    site("dgt-Us", LO, LD, true, 0, Q, 0, 0, 16 * Q, uG * (u64)NT * 8 * uQ, uG * (u64)NW * 8 * uQ, 128 * uQ);
+    site("dgt-Dl", LO, LD, true, PD / 2, 0, 0, 0, XL * PD / 2, uG * (u64)NT * uNB * uQ, uG * (u64)NW * uNB * uQ,
+         (u64)NPP * uQ);
     site("dgt-res", GL, ST, false, 1, Np, Nel * Np, 128 * Np, 16 * Np, 3 * (u64)Nel * uNp,
-         3 * uNB * ((u64)Tfull * 64 + (rlast ? sg_rows(rlast) : 0)), 3 * (u64)Nel * uNp);
-    o.finish(v4 ? 1 : 2, uG);
+         3 * ((u64)Tfull * sg_res_full + sg_res_last), 3 * (u64)Nel * uNp);
+    o.finish(even ? 1 : 2, uG);
     return PM_OK;
 }
 

@@ -142,7 +142,11 @@ __global__ void __launch_bounds__((BX / V) * BY) k_fd_block(const __grid_constan
                                                          float *__restrict__ res, int n, float c0, float c1) {
     constexpr int TW = BX + 4, TH = BY + 2;
     extern __shared__ __align__(128) unsigned char smem_raw[];
-    float *T = reinterpret_cast<float *>((((uintptr_t)smem_raw + 127) & ~(uintptr_t)127));
+    // align by an offset into the shared array itself: a pointer that went
+    // through an integer would lose the shared address space, and every
+    // access through it would become a generic load or store
+    const unsigned pad = (128u - ((unsigned)__cvta_generic_to_shared(smem_raw) & 127u)) & 127u;
+    float *T = reinterpret_cast<float *>(smem_raw + pad);
     uint64_t *bar = reinterpret_cast<uint64_t *>(T + TW * TH + 2);   // 8-byte aligned (TW * TH even)
     const int lx = threadIdx.x, ly = threadIdx.y;
     const bool leader = lx == 0 && ly == 0;
@@ -209,41 +213,46 @@ pm_status launch_fdb_v(int BX, int BY, void *const *b, int n, float c0, float c1
 // ---------------------------------------------------------------- DG tile
 // res[m, k, i] = sum_j D[m, i, j] u[k, j] for one m (blockIdx.x < 3) and
 // 128 elements k (blockIdx.y) per CTA, as one product C (128 x NPP) =
-// U (128 x Np4) Dt^T: Dt's rows padded to NPP = 16 NB with zeros, j padded
-// to Np4 = 4 Q with zeros, row pitch PD (PD % 32 == 4: conflict-free
-// 16-byte loads across 16 rows).  CTA 16 x 16: thread (x, y) accumulates
-// rows y + 16 a (a < 8) and columns x + 16 b (b < NB) in registers,
-// reading 16-byte vectors of u and D (four j per load).  The three CTAs of
-// a tile are adjacent in launch order, so the tile is read from HBM once.
-// The u tile (contiguous, rows x Np floats) arrives by one bulk copy on the
-// TMA engine while the threads stage D with 16-byte loads and stores; when
-// Np % 4 != 0 the rows are then re-laid out with pitch Np4 behind a second
-// barrier.  Small register tiles keep two or more CTAs per SM, so one CTA's
-// staging and stores overlap another's multiply-adds.  The mbarrier wait is
-// bounded (error word; a thread that gives up still passes the second
-// barrier and stores nothing).
+// U (128 x 2Q) Dt^T.  NB = ceil(Np / 16) columns per thread over
+// XL = ceil(Np / NB) x-lanes (XL x 16 threads), so the rows of Dt are padded
+// only to NPP = XL NB (exact for Np = 20, 56, 84); j runs in Q = ceil(Np / 2)
+// pairs.  Operands are read as 8-byte pairs: on GB300 a warp-wide 8-byte
+// shared load that only a few addresses feed (the u rows: 2-4 per warp)
+// costs about a quarter of a 16-byte one, and the XL distinct Dt rows of a
+// warp fall in distinct bank pairs (row pitch PD % 32 == 2).  Thread (x, y)
+// accumulates rows y + 16 a (a < 8) and columns x + XL b (b < NB) in
+// registers.  The three CTAs of a tile are adjacent in launch order, so the
+// tile is read from HBM once.  The u tile (contiguous, rows x Np floats)
+// arrives by one bulk copy on the TMA engine while the threads stage D with
+// 8-byte loads and stores; when Np is odd the rows are then re-laid out with
+// pitch 2Q behind a second barrier.  The mbarrier wait is bounded (error
+// word; a thread that gives up still passes the second barrier and stores
+// nothing).
 static __device__ int g_dgt_timeout;
 
-__host__ __device__ constexpr int dgt_pd(int Q) { return 4 * Q + ((36 - (4 * Q) % 32) % 32); }
+__host__ __device__ constexpr int dgt_pd(int Q) { return 2 * Q + ((34 - (2 * Q) % 32) % 32); }
+__host__ __device__ constexpr int dgt_xl(int Np, int NB) { return (Np + NB - 1) / NB; }
 
 size_t dgt_smem(int Np) {
-    const int Q = (Np + 3) / 4, NB = (Np + 15) / 16;
-    return 16 + (size_t)128 * 4 * Q * 4 + (Np % 4 ? (size_t)128 * Np * 4 : 0) + (size_t)16 * NB * dgt_pd(Q) * 4 + 8;
+    const int Q = (Np + 1) / 2, NB = (Np + 15) / 16, NPP = dgt_xl(Np, NB) * NB;
+    return (size_t)128 * 2 * Q * 4 + (Np % 2 ? (size_t)128 * Np * 4 : 0) + (size_t)NPP * dgt_pd(Q) * 4 + 8;
 }
 
 // NPC: Np fixed at compile time (the paper's sizes), 0 = taken from the argument
 template <int NB, int NPC>
-__global__ void __launch_bounds__(256, NB <= 3 ? 3 : 2) k_dg_tile(const float *__restrict__ D,
+__global__ void __launch_bounds__(NPC ? 16 * dgt_xl(NPC, NB) : 256, NB <= 3 ? 3 : 2) k_dg_tile(const float *__restrict__ D,
                                                                   const float *__restrict__ u,
                                                                   float *__restrict__ res, int np_arg, int Nel) {
+    constexpr int QBM = NB / 2 + 2;   // bound on ceil(Q / XL)
     const int Np = NPC ? NPC : np_arg;
-    const int Q = (Np + 3) / 4, QB = (Q + 15) / 16, PD = dgt_pd(Q), P4 = PD / 4;
-    const bool v4 = (Np & 3) == 0;
+    const int XL = dgt_xl(Np, NB), NPP = XL * NB, Q = (Np + 1) / 2, PD = dgt_pd(Q), P2 = PD / 2;
+    const int QB = (Q + XL - 1) / XL, RB = (NPP + 15) / 16;
+    const bool even = (Np & 1) == 0;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    float *Us = reinterpret_cast<float *>((((uintptr_t)smem_raw + 15) & ~(uintptr_t)15));
-    float *R = Us + 128 * 4 * Q;                    // raw rows (Np % 4 != 0 only)
-    float *Dt = R + (v4 ? 0 : 128 * Np);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(Dt + 16 * NB * PD);
+    float *Us = reinterpret_cast<float *>(smem_raw);   // 16-byte aligned; stays a shared-space pointer
+    float *R = Us + 128 * 2 * Q;                       // raw rows (odd Np only)
+    float *Dt = R + (even ? 0 : 128 * Np);
+    uint64_t *bar = reinterpret_cast<uint64_t *>(Dt + NPP * PD);
     const int x = threadIdx.x, y = threadIdx.y, m = blockIdx.x;
     const bool leader = x == 0 && y == 0;
     const long long k0 = 128LL * blockIdx.y;
@@ -253,26 +262,24 @@ __global__ void __launch_bounds__(256, NB <= 3 ? 3 : 2) k_dg_tile(const float *_
         mbar_init_fence();
         const uint32_t bytes = (uint32_t)rows * (uint32_t)Np * 4u;
         mbar_expect_tx(bar, bytes);
-        bulk_load(v4 ? Us : R, u + k0 * Np, bytes, bar);
+        bulk_load(even ? Us : R, u + k0 * Np, bytes, bar);
     }
     // D staging: all of a thread's loads in flight before its stores
     {
-        float4 dv[NB][2];
+        float2 dv[NB][QBM];
 #pragma unroll
         for (int ib = 0; ib < NB; ib++)
 #pragma unroll
-            for (int qb = 0; qb < 2; qb++) {
-                const int i = y + 16 * ib, q = x + 16 * qb;
-                float4 d = make_float4(0.0f, 0.0f, 0.0f, 0.0f);
-                if (qb < QB && q < Q && i < Np) {
-                    const float *src = D + (m * Np + i) * Np + 4 * q;
-                    if (v4) {
-                        d = __ldg(reinterpret_cast<const float4 *>(src));
+            for (int qb = 0; qb < QBM; qb++) {
+                const int i = y + 16 * ib, q = x + XL * qb;
+                float2 d = make_float2(0.0f, 0.0f);
+                if (ib < RB && qb < QB && q < Q && i < Np) {
+                    const float *src = D + (m * Np + i) * Np + 2 * q;
+                    if (even) {
+                        d = __ldg(reinterpret_cast<const float2 *>(src));
                     } else {
                         d.x = __ldg(src);
-                        if (4 * q + 1 < Np) d.y = __ldg(src + 1);
-                        if (4 * q + 2 < Np) d.z = __ldg(src + 2);
-                        if (4 * q + 3 < Np) d.w = __ldg(src + 3);
+                        if (2 * q + 1 < Np) d.y = __ldg(src + 1);
                     }
                 }
                 dv[ib][qb] = d;
@@ -280,64 +287,58 @@ __global__ void __launch_bounds__(256, NB <= 3 ? 3 : 2) k_dg_tile(const float *_
 #pragma unroll
         for (int ib = 0; ib < NB; ib++)
 #pragma unroll
-            for (int qb = 0; qb < 2; qb++) {
-                const int q = x + 16 * qb;
-                if (qb < QB && q < Q) reinterpret_cast<float4 *>(Dt + (y + 16 * ib) * PD)[q] = dv[ib][qb];
+            for (int qb = 0; qb < QBM; qb++) {
+                const int i = y + 16 * ib, q = x + XL * qb;
+                if (ib < RB && qb < QB && q < Q && i < NPP) reinterpret_cast<float2 *>(Dt + i * PD)[q] = dv[ib][qb];
             }
     }
     __syncthreads();
     const bool ok = mbar_wait_bounded(bar, 0, &g_dgt_timeout, 1ll << 26);
     if (!ok && leader) mbar_wait_bounded(bar, 0, &g_dgt_timeout, 1ll << 26);   // drain our own copy
-    if (!v4) {
+    if (!even) {
         if (ok)
 #pragma unroll
             for (int rb = 0; rb < 8; rb++)
                 for (int qb = 0; qb < QB; qb++) {
-                    const int r = y + 16 * rb, q = x + 16 * qb;
+                    const int r = y + 16 * rb, q = x + XL * qb;
                     if (q >= Q) continue;
-                    const float *src = R + r * Np + 4 * q;
-                    float4 t = make_float4(src[0], 0.0f, 0.0f, 0.0f);
-                    if (4 * q + 1 < Np) t.y = src[1];
-                    if (4 * q + 2 < Np) t.z = src[2];
-                    if (4 * q + 3 < Np) t.w = src[3];
-                    reinterpret_cast<float4 *>(Us + r * 4 * Q)[q] = t;
+                    const float *src = R + r * Np + 2 * q;
+                    const float2 t = make_float2(src[0], 2 * q + 1 < Np ? src[1] : 0.0f);
+                    reinterpret_cast<float2 *>(Us + r * 2 * Q)[q] = t;
                 }
         __syncthreads();
     }
     if (!ok) return;
-    float acc[8][NB];
+    // acc[a][b] = (sum over even j, sum over odd j): one paired FMA (FFMA2)
+    // per loaded pair of u and D values, combined by one add at the end
+    float2 acc[8][NB];
 #pragma unroll
     for (int a = 0; a < 8; a++)
 #pragma unroll
-        for (int b = 0; b < NB; b++) acc[a][b] = 0.0f;
-    const float4 *U4 = reinterpret_cast<const float4 *>(Us) + y * Q;
-    const float4 *D4 = reinterpret_cast<const float4 *>(Dt) + x * P4;
-#pragma unroll(NPC ? 3 : 1)
+        for (int b = 0; b < NB; b++) acc[a][b] = make_float2(0.0f, 0.0f);
+    const float2 *U2 = reinterpret_cast<const float2 *>(Us) + y * Q;
+    const float2 *D2 = reinterpret_cast<const float2 *>(Dt) + x * P2;
+#pragma unroll((NPC && NB < 6) ? 2 : 1)
     for (int q = 0; q < Q; q++) {
-        float4 av[8];
+        float2 av[8];
 #pragma unroll
-        for (int a = 0; a < 8; a++) av[a] = U4[16 * a * Q + q];
+        for (int a = 0; a < 8; a++) av[a] = U2[16 * a * Q + q];
 #pragma unroll
         for (int b = 0; b < NB; b++) {
-            const float4 bv = D4[16 * b * P4 + q];
+            const float2 bv = D2[XL * b * P2 + q];
 #pragma unroll
-            for (int a = 0; a < 8; a++) {
-                float t = __fmaf_rn(av[a].x, bv.x, acc[a][b]);
-                t = __fmaf_rn(av[a].y, bv.y, t);
-                t = __fmaf_rn(av[a].z, bv.z, t);
-                acc[a][b] = __fmaf_rn(av[a].w, bv.w, t);
-            }
+            for (int a = 0; a < 8; a++) acc[a][b] = __ffma2_rn(av[a], bv, acc[a][b]);
         }
     }
     float *out = res + (long long)m * Nel * Np;
 #pragma unroll
     for (int b = 0; b < NB; b++) {
-        const int i = x + 16 * b;
-        if (i >= Np) continue;
+        const int i = x + XL * b;
 #pragma unroll
         for (int a = 0; a < 8; a++) {
+            const float r = __fadd_rn(acc[a][b].x, acc[a][b].y);
             const long long k = k0 + y + 16 * a;
-            if (k < Nel) out[k * Np + i] = acc[a][b];
+            if (i < Np && k < Nel) out[k * Np + i] = r;
         }
     }
 }
@@ -347,8 +348,8 @@ pm_status launch_dgt_t(void *const *b, int Np, int Nel, cudaStream_t st) {
     const size_t smem = dgt_smem(Np);
     auto fn = k_dg_tile<NB, NPC>;
     PM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-    launch_k(fn, dim3(3, (unsigned)((Nel + 127) / 128)), dim3(16, 16), smem, st, (const float *)b[0],
-             (const float *)b[1], (float *)b[2], Np, Nel);
+    launch_k(fn, dim3(3, (unsigned)((Nel + 127) / 128)), dim3((unsigned)dgt_xl(Np, NB), 16), smem, st,
+             (const float *)b[0], (const float *)b[1], (float *)b[2], Np, Nel);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
 }

@@ -389,10 +389,11 @@ def test_run_host_batch_shared_input_regions():
 
 
 # DG tile (128 elements per CTA, D staged transposed in shared memory, the
-# u tile by one bulk copy): ragged Np (column padding) and ragged Nel (last
+# u tile by one bulk copy, ceil(Np / ceil(Np / 16)) column lanes): odd Np
+# (re-laid rows), Np with padded rows (33, 35, 63, 95) and ragged Nel (last
 # tile of 4..124 elements), guard bands checked by run_kernel
 @pytest.mark.parametrize("Np,Nel", [(20, 132), (35, 256), (56, 4), (84, 260), (1, 8), (17, 132), (96, 136),
-                                    (84, 1024), (16, 384)])
+                                    (84, 1024), (16, 384), (33, 132), (63, 200), (95, 8), (2, 12)])
 def test_dg_tile(Np, Nel):
     D, u = pm_inputs.normal((3, Np, Np), 21), pm_inputs.normal((Nel, Np), 22)
     (res,) = run_kernel("dg_tile", [D, u], Np=Np, Nel=Nel)
@@ -417,9 +418,10 @@ def test_dg_tile_full_size_sampled_and_timed(Np):
 def test_dg_tile_resources():
     dev()
     r = pm.resources("dg_tile", Np=84, Nel=1 << 18)
-    assert r["threads_per_block"] == 256 and r["grid_blocks"] == 3 * (1 << 18) // 128
+    # Np = 84: NB = 6 columns per thread over 14 x-lanes (no padded rows), 14 x 16 threads
+    assert r["threads_per_block"] == 14 * 16 and r["grid_blocks"] == 3 * (1 << 18) // 128
     assert r["local_bytes_per_thread"] == 0 and r["blocks_per_sm"] >= 2
-    assert r["dynamic_smem_bytes"] >= (128 * 84 + 96 * 100) * 4
+    assert r["dynamic_smem_bytes"] >= (128 * 84 + 84 * 98) * 4
 
 
 def test_run_host_batch_outputs_left_on_device():

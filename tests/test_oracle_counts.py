@@ -372,34 +372,37 @@ def test_tensor_core_closed_forms(kernel, R, n):
     assert single(fs, "groups") == (n // 256) * (n // R) and single(fs, "sync") == 3
 
 
-@pytest.mark.parametrize("Np,Nel", [(20, 132), (35, 256), (84, 128), (17, 4)])
+@pytest.mark.parametrize("Np,Nel", [(20, 132), (35, 256), (84, 128), (17, 4), (56, 256)])
 def test_dg_tile_closed_forms(Np, Nel):
-    # the DG product, one work-group per (m, 128 elements), j in 16-byte
-    # chunks: every D row block of its m loaded once per work-group (as
-    # vectors when Np % 4 == 0), every u element once per m (one bulk copy,
-    # uniform), every result stored once; padded rows, padded j and rows of a
-    # partial tile add multiply-adds (4 x 8 x NB per chunk per work-item),
-    # never stores
+    # the DG product, one work-group per (m, 128 elements), NB = ceil(Np/16)
+    # columns per work-item over XL = ceil(Np/NB) x-lanes, j in 8-byte pairs:
+    # every D row of its m loaded once per work-group (as vectors when Np is
+    # even), every u element once per m (one bulk copy, uniform), every result
+    # stored once; padded rows (XL NB > Np), padded j and rows of a partial
+    # tile add multiply-adds (2 x 8 x NB per pair per work-item), never stores;
+    # each output's even-j and odd-j running sums are combined by one add
     fs = features("dg_tile", Np=Np, Nel=Nel)
-    T, NB, Q = -(-Nel // 128), -(-Np // 16), -(-Np // 4)
+    T, NB, Q = -(-Nel // 128), -(-Np // 16), -(-Np // 2)
+    XL = -(-Np // NB)
     G = 3 * T
-    assert op(fs, "float32", "madd", wi=True) == G * 256 * 8 * NB * 4 * Q >= 3 * Nel * Np * Np
-    if Np % 16 == 0 and Nel % 128 == 0:
+    assert op(fs, "float32", "madd", wi=True) == G * 16 * XL * 8 * NB * 2 * Q >= 3 * Nel * Np * Np
+    assert op(fs, "float32", "add", wi=True) == G * 16 * XL * 8 * NB   # even-j and odd-j sums combined
+    if XL * NB == Np and Np % 2 == 0 and Nel % 128 == 0:
         assert op(fs, "float32", "madd", wi=True) == 3 * Nel * Np * Np
     d = by_tag(fs, "dgt-D")
-    if Np % 4 == 0:
-        assert d["dtype"] == "float32x4" and d["count_wi"] == G * Np * Np // 4 and d["lstr"] == (1, Np // 4)
-        assert d["footprint"] == 3 * Np * Np // 4 and d["gstr"] == (Np * Np // 4, 0)
+    if Np % 2 == 0:
+        assert d["dtype"] == "float32x2" and d["count_wi"] == G * Np * Np // 2 and d["lstr"] == (1, Np // 2)
+        assert d["footprint"] == 3 * Np * Np // 2 and d["gstr"] == (Np * Np // 2, 0)
     else:
-        assert d["dtype"] == "float32" and d["count_wi"] == G * Np * Np and d["lstr"] == (4, Np)
+        assert d["dtype"] == "float32" and d["count_wi"] == G * Np * Np and d["lstr"] == (2, Np)
         assert d["footprint"] == 3 * Np * Np and d["gstr"] == (Np * Np, 0)
     uu = by_tag(fs, "dgt-u")
     assert uu["count_wi"] == uu["count"] == 3 * Nel * Np and uu["footprint"] == Nel * Np and uu["lstr"] == (0, 0)
     r = by_tag(fs, "dgt-res")
     assert r["count_wi"] == r["footprint"] == 3 * Nel * Np and r["lstr"] == (1, Np)
     assert r["gstr"] == (Nel * Np, 128 * Np)
-    assert by_tag(fs, "dgt-Us")["count_wi"] == G * 256 * 8 * Q
-    assert by_tag(fs, "dgt-Dl")["count_wi"] == G * 256 * NB * Q
-    pd = by_tag(fs, "dgt-Dl")["lstr"][0] * 4
-    assert pd % 32 == 4 and pd >= 4 * Q
-    assert single(fs, "sync") == (1 if Np % 4 == 0 else 2) and single(fs, "groups") == G
+    assert by_tag(fs, "dgt-Us")["count_wi"] == G * 16 * XL * 8 * Q
+    assert by_tag(fs, "dgt-Dl")["count_wi"] == G * 16 * XL * NB * Q
+    pd = by_tag(fs, "dgt-Dl")["lstr"][0] * 2
+    assert pd % 32 == 2 and pd >= 2 * Q
+    assert single(fs, "sync") == (1 if Np % 2 == 0 else 2) and single(fs, "groups") == G
