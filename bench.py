@@ -316,6 +316,8 @@ def run_ours(args):
         nsum[idx] += n
     mean_s = [tsum[i] / nsum[i] * 1e-3 if nsum[i] else None for i in range(len(variants))]
     line["suite_roofline"] = suite_roofline(variants, mean_s, peaks["hbm_gbs"], sm_count, clk.get("sm_mhz"))
+    line["suite_roofline"]["stream_bounds"] = stream_bounds(pm, torch, variants, mean_s, peaks["hbm_gbs"], sm_count,
+                                                            bufs_for)
     if world > 1:
         line["ranks"] = rank_reports
     if args.dump and rank == 0:
@@ -402,6 +404,79 @@ def suite_roofline(variants, mean_s, hbm_gbs, sm_count, sm_mhz, l2_bytes=None):
         "fma_f64_madd_tflops": summary(f64),
         "smem_vs_bandwidth": {k: summary(v) for k, v in sorted(smem.items())},
     }
+
+
+def stream_bounds(pm, torch, variants, mean_s, hbm_gbs, sm_count, bufs_for, l2_bytes=None):
+    """The bound that applies to each stream variant of at least 4x the L2
+    size, the smallest of:
+      hbm      the measured copy rate;
+      pattern  the same kernel instantiation with its working set in L2,
+               timed warm at two sizes (about 24 and 96 MiB): the marginal
+               rate, bytes over time between them, is what the memory system
+               delivers this access pattern with DRAM out of the way (for
+               lid(0) strides of 8 or more the L2 request rate);
+      little   Little's law with the unloaded HBM latency: resident
+               work-items x bytes each has in flight (its L loads, then its
+               store) / latency, for all SMs (pm_probe_latency on a 1 GiB
+               buffer; the resident count from pm_kernel_resources).
+    Returns the latencies, and per lid(0) stride / shape the fraction of the
+    applicable bound (min / median / max) with the variants below 0.8."""
+    from paper_1904_09538_gb300 import suite as S
+    l2 = l2_bytes or S.L2_BYTES
+    dev = torch.cuda.current_device()
+    big = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+    lat_hbm = pm.probe_latency(big, hops=100000)
+    del big
+    small = torch.empty(16 << 20, dtype=torch.uint8, device=dev)
+    lat_l2 = pm.probe_latency(small, hops=100000)
+    del small
+    ceil, res_cache, per, below = {}, {}, {}, []
+    for (k, p), t in zip(variants, mean_s):
+        nbytes = S.algorithmic_bytes(k, p)
+        if k != "stream" or t is None or t <= 0 or nbytes < 4 * l2:
+            continue
+        key = tuple(sorted((a, b) for a, b in p.items() if a != "N"))
+        if key not in ceil:
+            pts = []
+            try:
+                for target in (24 << 20, 96 << 20):
+                    q = dict(p)
+                    n = p["N"]
+                    while n > 1 and S.algorithmic_bytes(k, dict(q, N=n)) > target:
+                        n //= 2
+                    q["N"] = n
+                    tm = pm.run(k, bufs_for(k, q), warmup=3, trials=20, flush_l2=False, **q)
+                    pts.append((S.algorithmic_bytes(k, q), tm["median_ms"] * 1e-3))
+                (b1, t1), (b2, t2) = pts
+                ceil[key] = (b2 - b1) / (t2 - t1) / 1e9 if t2 > t1 and b2 > b1 else None
+            except pm.PMError:   # no valid L2-resident size of this shape
+                ceil[key] = None
+        if key not in res_cache:
+            r = pm.resources(k, **p)
+            res_cache[key] = r["blocks_per_sm"] * r["threads_per_block"]
+        esize = 16 if p.get("vec", 0) else (8 if p.get("dtype", 0) else 4)
+        little = sm_count * res_cache[key] * esize * (p.get("L", 1) + 1) / (lat_hbm * 1e-9) / 1e9
+        cands = {"hbm": hbm_gbs, "little": little}
+        if ceil[key]:
+            cands["pattern"] = ceil[key]
+        kind = min(cands, key=cands.get)
+        got = nbytes / t / 1e9
+        frac = got / cands[kind]
+        skey = "2d" if p.get("shape", 0) == 1 else "s%d" % p["s"]
+        per.setdefault(skey, []).append((frac, kind, cands[kind]))
+        if frac < 0.8:
+            below.append({"params": p, "gbs": round(got, 1), "bound": kind, "bound_gbs": round(cands[kind], 1),
+                          "frac": round(frac, 3)})
+
+    def summ(v):
+        fr = sorted(x[0] for x in v)
+        kinds = sorted(set(x[1] for x in v))
+        return {"n": len(v), "min": round(fr[0], 3), "median": round(fr[len(fr) // 2], 3), "max": round(fr[-1], 3),
+                "bounds": kinds, "bound_gbs_median": round(sorted(x[2] for x in v)[len(v) // 2], 1)}
+    allf = [x[0] for v in per.values() for x in v]
+    return {"hbm_latency_ns": round(lat_hbm, 1), "l2_latency_ns": round(lat_l2, 1),
+            "variants": len(allf), "at_least_0.8_of_bound": sum(f >= 0.8 for f in allf),
+            "by_stride": {k: summ(v) for k, v in sorted(per.items())}, "below_0.8": below}
 
 
 def calibrated_rates(fitted, sm_count, sm_mhz):
@@ -539,19 +614,24 @@ def e2e_measure(pm, S, variants, torch, trials, fit_and_predict, fit_sizes, step
     torch.cuda.synchronize()
     # `steps` timed steps (the host link is shared with the machine's other
     # GPUs, so one step is a thin sample): aggregate throughput, each step kept
-    step_ms, copy_list = [], []
+    step_ms, copy_list, kern_list, fit_list = [], [], [], []
     for _ in range(steps):
         t0 = time.perf_counter()
         tms, copy_ms = pm.run_host_batch(jobs, warmup=0, trials=trials, outlier_factor=0.0)
+        t1 = time.perf_counter()
         fit_and_predict({i: t["mean_ms"] * 1e-3 for i, t in enumerate(tms)})
         torch.cuda.synchronize()
         step_ms.append((time.perf_counter() - t0) * 1e3)
+        fit_list.append((time.perf_counter() - t1) * 1e3)
         copy_list.append(copy_ms)
+        kern_list.append(sum(t["mean_ms"] * t["n_trials"] for t in tms))
     os.sched_setaffinity(0, saved)
     dt = sum(step_ms) * 1e-3
     return {"value": round(steps * nbytes / dt / 1e9, 2), "unit": "GB/s", "h2d_bytes_per_step": int(h2d),
             "d2h_bytes_per_step": int(d2h), "steps": steps, "ms_per_step": round(dt * 1e3 / steps, 2),
             "step_ms": [round(x, 1) for x in step_ms], "copy_ms": [round(x, 1) for x in copy_list],
+            "kernel_ms": [round(x, 1) for x in kern_list], "fit_predict_ms": [round(x, 1) for x in fit_list],
+            "other_ms": [round(a - b - c - d, 1) for a, b, c, d in zip(step_ms, copy_list, kern_list, fit_list)],
             "link": dict(link, copies_at_link_rate_ms=round((h2d / link["h2d_gbs"] + d2h / link["d2h_gbs"]) / 1e6, 1)),
             "host_cpus": len(local) if local else None}
 

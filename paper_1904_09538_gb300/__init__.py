@@ -180,6 +180,15 @@ def run(kernel, bufs, warmup=2, trials=60, outlier_factor=5.0, stream=None, want
     return out
 
 
+def probe_latency(buf, hops=100000, stream=None):
+    """pm_probe_latency on a device tensor (its bytes are overwritten): mean
+    nanoseconds per dependent load from the level that holds it."""
+    ns = ctypes.c_double()
+    check(lib().pm_probe_latency(ctypes.c_void_p(buf.data_ptr()), buf.numel() * buf.element_size(), int(hops),
+                                 ctypes.byref(ns), _stream(stream)))
+    return ns.value
+
+
 def run_host(kernel, host_arrays, warmup=2, trials=60, outlier_factor=5.0, stream=None, flush_l2=False, **params):
     """pm_run with host (NumPy) buffers: copies in, runs, copies out."""
     arr, n, _keep = _params(params)

@@ -89,6 +89,7 @@ SIGNATURES = {
     "pm_run_host": (i32, [i32, P(pm_param), c_size_t, P(vp), c_size_t, P(pm_run_opts), vp, fp, P(pm_timing), dp]),
     "pm_run_host_batch": (i32, [P(pm_host_job), c_size_t, P(pm_run_opts), vp, P(pm_timing), dp]),
     "pm_run_host_batch_bytes": (i32, [P(pm_host_job), c_size_t, P(ctypes.c_uint64), P(ctypes.c_uint64)]),
+    "pm_probe_latency": (i32, [vp, c_size_t, i32, dp, vp]),
     "pm_model_create": (i32, [ctypes.c_char_p, ctypes.c_char_p, P(vp)]),
     "pm_model_destroy": (None, [vp]),
     "pm_model_info": (i32, [vp, P(c_size_t), P(c_size_t)]),

@@ -13,6 +13,10 @@ namespace pm {
 pm_status fail(pm_status s, const char *fmt, ...);
 void clear_error();
 bool alloc_fault_injected();   // pm_test_fail_allocation countdown (true: fail this allocation)
+// Raise the release threshold of the current device's default memory pool to
+// the maximum (once per device), so memory freed with cudaFreeAsync stays
+// reserved for the next cudaMallocAsync instead of being unmapped.
+pm_status retain_staging_pool();
 void set_fail_allocation(int n);
 
 // An allocation: PM_ENOMEM when it is refused for lack of memory (or a test

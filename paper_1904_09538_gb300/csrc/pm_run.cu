@@ -34,7 +34,7 @@ static size_t dtype_size(int dt) { return dt == PM_F32 ? 4 : dt == PM_F64 ? 8 : 
 // pm_run_host stages through the device's default memory pool; keeping the
 // freed staging memory reserved (instead of unmapping it at every
 // synchronisation) saves remapping gigabytes on every call.
-static pm_status retain_staging_pool() {
+pm_status retain_staging_pool() {
     static bool done[64];
     static std::mutex mu;
     int dev = 0;
@@ -401,12 +401,13 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
         return false;
     };
     cudaStream_t up = nullptr, down = nullptr;
-    EventPool ev;   // per job: inputs copied, kernels done, outputs copied
+    EventPool ev;   // per job: inputs copied, kernels done, outputs copied; then per job: copies begin (in, out)
     pm_status rc = PM_OK;
     if (cudaStreamCreateWithFlags(&up, cudaStreamNonBlocking) != cudaSuccess ||
         cudaStreamCreateWithFlags(&down, cudaStreamNonBlocking) != cudaSuccess)
         rc = fail(PM_ECUDA, "pm_run_host_batch: stream creation failed");
-    if (rc == PM_OK) rc = ev.make(3 * njobs + 2);
+    if (rc == PM_OK) rc = ev.make(5 * njobs + 2);
+    cudaEvent_t *beg = ev.ev.data() + 3 * njobs + 2;   // beg[2 i]: input copies begin, beg[2 i + 1]: output copies
     double kernels_ms = 0.0;
     for (size_t i = 0; i < njobs && rc == PM_OK; i++) {
         BatchJob &j = J[i];
@@ -418,6 +419,7 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
             if (clash(i - 1)) cudaStreamWaitEvent(up, ev.ev[3 * (i - 1) + 2], 0);
         }
         if (i == 0) cudaEventRecord(ev.ev[3 * njobs], up);
+        cudaEventRecord(beg[2 * i], up);
         std::vector<void *> bufs(j.spec.size(), nullptr);
         for (size_t b = 0; b < j.spec.size() && rc == PM_OK; b++) {
             const int k = j.shared[b];
@@ -458,6 +460,7 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
         kernels_ms += t.mean_ms * t.n_trials;
         cudaEventRecord(e_k, cs);
         cudaStreamWaitEvent(down, e_k, 0);
+        cudaEventRecord(beg[2 * i + 1], down);
         for (size_t b = 0; b < j.spec.size() && rc == PM_OK; b++)
             if (j.spec[b].role == PM_OUT && jobs[i].host_bufs[b] &&
                 cudaMemcpyAsync(jobs[i].host_bufs[b], j.dev[b], buf_bytes(j.spec[b]), cudaMemcpyDeviceToHost, down) !=
@@ -485,13 +488,79 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
     for (SharedIn &e : sh)   // shared inputs of a batch that stopped early
         if (e.dev) cudaFree(e.dev);
     if (rc == PM_OK && copy_ms && njobs) {
-        float total = 0;
-        cudaEventElapsedTime(&total, ev.ev[3 * njobs], ev.ev[3 * njobs + 1]);
-        *copy_ms = std::max(0.0, (double)total - kernels_ms);
+        // the copies' own device time: each job's input copies (after it may
+        // start) and output copies, summed; the time between them (kernels,
+        // host work between jobs) is not included
+        double tot = 0.0;
+        for (size_t i = 0; i < njobs; i++) {
+            float a = 0.0f, b = 0.0f;
+            cudaEventElapsedTime(&a, beg[2 * i], ev.ev[3 * i]);
+            cudaEventElapsedTime(&b, beg[2 * i + 1], ev.ev[3 * i + 2]);
+            tot += (double)a + (double)b;
+        }
+        *copy_ms = tot;
     }
+    (void)kernels_ms;
     if (up) cudaStreamDestroy(up);
     if (down) cudaStreamDestroy(down);
     return rc;
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------- load latency probe
+// A pointer chase over 128-byte lines: line i holds the index of line
+// (i + stride) mod nlines, stride coprime with nlines (every line visited
+// once per cycle), read with L1-bypassing loads by one thread, so each hop
+// waits for the previous one: the unloaded latency of the level that holds
+// the buffer (HBM for a buffer far larger than L2, L2 for a small one).
+namespace pm {
+namespace {
+__global__ void k_chase_init(uint32_t *next, uint32_t nlines, uint32_t stride) {
+    for (size_t i = blockIdx.x * (size_t)blockDim.x + threadIdx.x; i < nlines; i += (size_t)gridDim.x * blockDim.x)
+        next[i * 32] = (uint32_t)((i + stride) % nlines);
+}
+__global__ void k_chase(const uint32_t *__restrict__ next, uint32_t nlines, uint32_t hops, uint32_t *sink) {
+    uint32_t p = 0;
+    for (uint32_t h = 0; h < hops; h++) {
+        p = __ldcg(next + (size_t)p * 32);
+        if (p >= nlines) break;   // cannot happen for an initialised chain; keeps every read in bounds
+    }
+    *sink = p;
+}
+uint64_t gcd_u64(uint64_t a, uint64_t b) {
+    while (b) { const uint64_t t = a % b; a = b; b = t; }
+    return a;
+}
+}  // namespace
+}  // namespace pm
+
+extern "C" pm_status pm_probe_latency(void *buf, size_t bytes, int32_t hops, double *ns_per_hop, void *stream) {
+    using namespace pm;
+    if (!buf || !ns_per_hop || hops < 1 || bytes < 256 || bytes / 128 > 0xffffffffull || (uintptr_t)buf % 128)
+        return fail(PM_EINVAL, "pm_probe_latency: need a 128-byte aligned buffer of 256 bytes .. 512 GiB and hops >= 1");
+    const uint32_t nlines = (uint32_t)(bytes / 128);
+    uint64_t s = (uint64_t)(nlines * 0.6180339887) | 1u;
+    while (s < 2 || gcd_u64(s, nlines) != 1) s += 1;
+    s %= nlines;
+    if (s == 0) s = 1;
+    cudaStream_t st = (cudaStream_t)stream;
+    uint32_t *next = (uint32_t *)buf;
+    k_chase_init<<<1216, 256, 0, st>>>(next, nlines, (uint32_t)s);
+    PM_CUDA_TRY(cudaGetLastError());
+    // the sink: the word after the first line's index (never an index slot)
+    uint32_t *sink = next + 1;
+    EventPool ev;
+    pm_status rc = ev.make(2);
+    if (rc) return rc;
+    k_chase<<<1, 1, 0, st>>>(next, nlines, (uint32_t)std::min<int32_t>(hops, 64), sink);   // warm-up
+    PM_CUDA_TRY(cudaEventRecord(ev.ev[0], st));
+    k_chase<<<1, 1, 0, st>>>(next, nlines, (uint32_t)hops, sink);
+    PM_CUDA_TRY(cudaEventRecord(ev.ev[1], st));
+    PM_CUDA_TRY(cudaEventSynchronize(ev.ev[1]));
+    PM_CUDA_TRY(cudaGetLastError());
+    float ms = 0.0f;
+    PM_CUDA_TRY(cudaEventElapsedTime(&ms, ev.ev[0], ev.ev[1]));
+    *ns_per_hop = (double)ms * 1e6 / hops;
+    return PM_OK;
+}
