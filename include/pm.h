@@ -519,7 +519,10 @@ pm_status pm_lm_update(void *state, const double *r_try, size_t l, double *p, in
 pm_status pm_lm_report(const void *state, pm_fit_report *report, void *stream);
 
 /* Predict (Section "Predicting Cost"): t_out[k] = g(p; X_k) for l rows,
- * evaluated on the GPU in FP64.  X host l x n_features, p host, t_out host. */
+ * evaluated on the GPU in FP64.  X host l x n_features, p host, t_out host.
+ * Device staging comes from the default memory pool on the legacy default
+ * stream (see pm_run_host: the pool keeps freed memory reserved), so
+ * repeated calls make no cudaMalloc / cudaFree.  Blocks until done. */
 pm_status pm_predict(const pm_model *m, const double *p, const double *X, size_t l, double *t_out);
 
 /* Thread-local, library-owned message of the last failure ("" if none). */

@@ -89,7 +89,7 @@ struct Smem {
     double sbig;                  // start point: max |p| of its linear fit
     unsigned zmask;               // start point: parameters whose column is zero at the origin
     df part[T];       // per row-group partial sums of the assembled entries
-    double ssr, ssr_new, pred, lambda, med[2], noise, cond;
+    double ssr, pred, lambda, med[2], noise, cond;
     int stop, below, nbelow;
     int nact, ok, rankdef, rank;
 };
@@ -735,13 +735,17 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
             }
             if (tid < m) S.qt[tid] = S.q[tid] + S.dq[tid];
             __syncthreads();
+            // a predicted decrease below the noise floor is accepted whatever
+            // the SSR says, so its SSR pass is skipped (the assembly at the
+            // new point computes the SSR; a non-finite one is undone there)
+            if (S.pred <= noise) {
+                accepted = true;
+                break;
+            }
             set_params(S, S.qt, m);
             const double sn = ssr_pass(S, jb, jb.n_code);
-            const double pred = S.pred;
-            if (isfinite(sn) && (sn <= ssr_old || pred <= noise)) {
+            if (isfinite(sn) && sn <= ssr_old) {
                 accepted = true;
-                if (tid == 0) S.ssr_new = sn;
-                __syncthreads();
                 break;
             }
             if (tid == 0) S.lambda *= 10.0;
@@ -776,6 +780,16 @@ __global__ void __launch_bounds__(T) k_fit(const FitJob *__restrict__ jobs, FitC
         iters++;
         set_params(S, S.q, m);
         assemble(S, jb, jb.n_code, all, true);
+        if (!isfinite(S.ssr)) {
+            // an unverified step that left the model's domain: back to the
+            // previous point, which ends the fit
+            if (tid < m) S.q[tid] -= S.dq[tid];
+            __syncthreads();
+            set_params(S, S.q, m);
+            assemble(S, jb, jb.n_code, all, true);
+            if (tid == 0) S.stop = 1;
+            iters--;
+        }
         set_active(S, m, all);
         if (tid < m) S.dmax[tid] = fmax(S.dmax[tid], A_at(S.acc, m, tid, tid));
         // the relative-decrease test only where the decrease is measurable
@@ -1076,29 +1090,35 @@ pm_status pm_predict(const pm_model *m, const double *p, const double *X, size_t
     if (!m || !p || !t_out || (l && !X && !m->features.empty())) return fail(PM_EINVAL, "pm_predict: NULL argument");
     if (l == 0) return PM_OK;
     const size_t nf = m->features.size(), np = m->params.size();
+    pm_status s = retain_staging_pool();
+    if (s) return s;
+    // stream-ordered staging from the device's memory pool (kept reserved):
+    // no cudaMalloc / cudaFree per call, which would synchronise the device
+    // and slow the host-to-device copies issued after it
+    cudaStream_t st = 0;
     double *dX = nullptr, *dp = nullptr, *dout = nullptr;
     Ins *dc = nullptr;
-    pm_status s = PM_OK;
-    auto alloc = [](void **p, size_t b) { return !alloc_fault_injected() && cudaMalloc(p, b) == cudaSuccess; };
+    auto alloc = [&](void **q, size_t b) { return !alloc_fault_injected() && cudaMallocAsync(q, b, st) == cudaSuccess; };
     if (!alloc((void **)&dX, std::max<size_t>(l * nf, 1) * 8) || !alloc((void **)&dp, np * 8) ||
         !alloc((void **)&dout, l * 8) || !alloc((void **)&dc, m->code.size() * sizeof(Ins)))
         s = fail(PM_ENOMEM, "pm_predict: device allocation failed");
-    if (!s && nf && cudaMemcpy(dX, X, l * nf * 8, cudaMemcpyHostToDevice) != cudaSuccess)
+    if (!s && nf && cudaMemcpyAsync(dX, X, l * nf * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
         s = fail(PM_ECUDA, "pm_predict: copy failed");
-    if (!s && cudaMemcpy(dp, p, np * 8, cudaMemcpyHostToDevice) != cudaSuccess) s = fail(PM_ECUDA, "pm_predict: copy failed");
-    if (!s && cudaMemcpy(dc, m->code.data(), m->code.size() * sizeof(Ins), cudaMemcpyHostToDevice) != cudaSuccess)
+    if (!s && cudaMemcpyAsync(dp, p, np * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        s = fail(PM_ECUDA, "pm_predict: copy failed");
+    if (!s && cudaMemcpyAsync(dc, m->code.data(), m->code.size() * sizeof(Ins), cudaMemcpyHostToDevice, st) != cudaSuccess)
         s = fail(PM_ECUDA, "pm_predict: copy failed");
     if (!s) {
         const unsigned blocks = (unsigned)std::min<size_t>((l + 127) / 128, 1216);
-        k_predict<<<blocks, 128>>>(dc, (int)m->code.size(), (int)nf, dX, l, dp, dout, (int)np);
+        k_predict<<<blocks, 128, 0, st>>>(dc, (int)m->code.size(), (int)nf, dX, l, dp, dout, (int)np);
         cudaError_t e = cudaGetLastError();
-        if (e == cudaSuccess) e = cudaMemcpy(t_out, dout, l * 8, cudaMemcpyDeviceToHost);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(t_out, dout, l * 8, cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);
         if (e != cudaSuccess) s = fail(PM_ECUDA, "pm_predict: %s", cudaGetErrorString(e));
     }
-    cudaFree(dX);
-    cudaFree(dp);
-    cudaFree(dout);
-    cudaFree(dc);
+    for (void *q : {(void *)dX, (void *)dp, (void *)dout, (void *)dc})
+        if (q) cudaFreeAsync(q, st);
+    cudaStreamSynchronize(st);
     return s;
 }
 

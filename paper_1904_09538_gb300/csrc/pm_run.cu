@@ -151,7 +151,8 @@ static pm_status timed(const KP &kp, void *const *bufs, size_t nbufs, const pm_r
         for (int t = 0; t < o.trials; t++) trial_ms[t] = ms[t];
     std::vector<float> sorted = ms;
     std::sort(sorted.begin(), sorted.end());
-    double med = o.trials % 2 ? sorted[o.trials / 2] : 0.5 * (sorted[o.trials / 2 - 1] + sorted[o.trials / 2]);
+    const double med = o.trials % 2 ? (double)sorted[o.trials / 2]
+                                    : 0.5 * ((double)sorted[o.trials / 2 - 1] + (double)sorted[o.trials / 2]);
     double sum = 0.0, mn = 1e300, mx = 0.0;
     int kept = 0;
     for (float v : ms) {

@@ -48,11 +48,13 @@ __global__ void __launch_bounds__((BM / 8) * (BN / 8)) k_mm_simt(const float4 *_
     const int l0 = threadIdx.x, l1 = threadIdx.y;
     const size_t n4 = (size_t)n / 4;
     const size_t arow0 = (size_t)BM * blockIdx.y;
-    float acc[8][8];
+    // acc[i][h] = C(row i, columns 2h and 2h + 1): two fused multiply-adds per
+    // paired instruction (FFMA2), each the same single-rounded FMA as before
+    float2 acc[8][4];
 #pragma unroll
     for (int i = 0; i < 8; i++)
 #pragma unroll
-        for (int j = 0; j < 8; j++) acc[i][j] = 0.0f;
+        for (int h = 0; h < 4; h++) acc[i][h] = make_float2(0.0f, 0.0f);
     const int K = n / BK;
     for (int kt = 0; kt < K; kt++) {
         __syncthreads();
@@ -92,11 +94,14 @@ __global__ void __launch_bounds__((BM / 8) * (BN / 8)) k_mm_simt(const float4 *_
             const float4 b0 = reinterpret_cast<const float4 *>(Bs)[kk * NC + l0];
             const float4 b1 = reinterpret_cast<const float4 *>(Bs)[kk * NC + L0 + l0];
             const float a[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
-            const float b[8] = {b0.x, b0.y, b0.z, b0.w, b1.x, b1.y, b1.z, b1.w};
+            const float2 b[4] = {make_float2(b0.x, b0.y), make_float2(b0.z, b0.w), make_float2(b1.x, b1.y),
+                                 make_float2(b1.z, b1.w)};
 #pragma unroll
-            for (int i = 0; i < 8; i++)
+            for (int i = 0; i < 8; i++) {
+                const float2 ai = make_float2(a[i], a[i]);
 #pragma unroll
-                for (int j = 0; j < 8; j++) acc[i][j] = __fmaf_rn(a[i], b[j], acc[i][j]);
+                for (int h = 0; h < 4; h++) acc[i][h] = __ffma2_rn(ai, b[h], acc[i][h]);
+            }
         }
     }
 #pragma unroll
@@ -105,7 +110,7 @@ __global__ void __launch_bounds__((BM / 8) * (BN / 8)) k_mm_simt(const float4 *_
 #pragma unroll
         for (int h = 0; h < 2; h++)
             C4[n4 * row + (size_t)NC * blockIdx.x + l0 + L0 * h] =
-                make_float4(acc[i][4 * h], acc[i][4 * h + 1], acc[i][4 * h + 2], acc[i][4 * h + 3]);
+                make_float4(acc[i][2 * h].x, acc[i][2 * h].y, acc[i][2 * h + 1].x, acc[i][2 * h + 1].y);
     }
 }
 
