@@ -295,15 +295,19 @@ typedef struct {
  * memory, that pair of copies is serialised instead.  Input buffers that
  * start at the same host address in several jobs are one shared region: it
  * is copied once, by its first reader, at the largest extent any reader
- * reads, and freed after its last reader's kernels (every kernel only reads
- * its inputs).  A region that any host output buffer of the batch overlaps
- * is not shared (its host contents may change during the batch); each of
- * its readers copies it.  Device staging comes from the default memory pool
- * (see pm_run_host).  out: njobs timings; copy_ms (nullable): the copies'
- * own device time -- per job, from the moment its input copies may start
- * to their end, plus its output copies -- summed over the jobs (the time
- * between jobs, host work included, is not counted); on error the failing
- * job's index is in the message and later jobs are not run. */
+ * reads (every kernel only reads its inputs).  A region that any host
+ * output buffer of the batch overlaps is not shared (its host contents may
+ * change during the batch); each of its readers copies it.  Device staging
+ * is one allocation per batch from the default memory pool (see
+ * pm_run_host): the shared regions, then two slots for the jobs' own
+ * buffers used by consecutive jobs in turn (a job's input copies wait until
+ * the job two before it has copied its outputs out of its slot), so every
+ * shared region stays resident for the whole batch.  out: njobs timings;
+ * copy_ms (nullable): the copies' own device time -- per job, from the
+ * moment its input copies may start to their end, plus its output copies --
+ * summed over the jobs (the time between jobs, host work included, is not
+ * counted); on error the failing job's index is in the message and later
+ * jobs are not run. */
 pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_opts *opts, void *stream,
                             pm_timing *out, double *copy_ms);
 

@@ -278,17 +278,15 @@ namespace {
 struct BatchJob {
     KP kp;
     std::vector<BufSpec> spec;
-    std::vector<void *> dev;
     std::vector<int> shared;   // per buffer: index into the shared inputs, or -1
 };
 
 // An input region several jobs of a batch read: every input buffer that
-// starts at the same host address.  It is copied once, at the largest extent
-// any of its readers reads, and freed after its last reader's kernels.
+// starts at the same host address.  It is copied once, by its first reader,
+// at the largest extent any of its readers reads.
 struct SharedIn {
     const char *host;
     size_t bytes;
-    size_t last;
     int readers;
     void *dev;
 };
@@ -322,11 +320,10 @@ pm_status batch_plan(const char *who, const pm_host_job *jobs, size_t njobs, std
             for (size_t e = 0; e < sh.size(); e++)
                 if (sh[e].host == h) k = (int)e;
             if (k < 0) {
-                sh.push_back(SharedIn{h, 0, i, 0, nullptr});
+                sh.push_back(SharedIn{h, 0, 0, nullptr});
                 k = (int)sh.size() - 1;
             }
             sh[k].bytes = std::max(sh[k].bytes, buf_bytes(J[i].spec[b]));
-            sh[k].last = i;
             sh[k].readers++;
             J[i].shared[b] = k;
         }
@@ -409,42 +406,64 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
         rc = fail(PM_ECUDA, "pm_run_host_batch: stream creation failed");
     if (rc == PM_OK) rc = ev.make(5 * njobs + 2);
     cudaEvent_t *beg = ev.ev.data() + 3 * njobs + 2;   // beg[2 i]: input copies begin, beg[2 i + 1]: output copies
+    // Device staging: one slab from the memory pool per batch -- the shared
+    // regions at fixed offsets, then two slots for the jobs' own buffers,
+    // used by consecutive jobs in turn (a job's inputs never overwrite the
+    // slot the previous job's outputs are still being copied from).  One
+    // allocation of the same size every batch: the pool reuses it.
+    auto al = [](size_t x) { return (x + 255) & ~(size_t)255; };
+    size_t sh_total = 0, priv_max = 0;
+    std::vector<size_t> sh_off(sh.size());
+    for (size_t k = 0; k < sh.size(); k++) {
+        sh_off[k] = sh_total;
+        sh_total += al(sh[k].bytes);
+    }
+    for (size_t i = 0; i < njobs; i++) {
+        size_t priv = 0;
+        for (size_t b = 0; b < J[i].spec.size(); b++)
+            if (J[i].shared[b] < 0) priv += al(buf_bytes(J[i].spec[b]));
+        priv_max = std::max(priv_max, priv);
+    }
+    unsigned char *slab = nullptr;
+    if (rc == PM_OK && njobs) {
+        if (alloc_fault_injected() || cudaMallocAsync((void **)&slab, std::max<size_t>(sh_total + 2 * priv_max, 256), up) !=
+                                          cudaSuccess) {
+            slab = nullptr;
+            rc = fail(PM_ENOMEM, "pm_run_host_batch: allocation of %zu staging bytes failed", sh_total + 2 * priv_max);
+        }
+    }
     double kernels_ms = 0.0;
     for (size_t i = 0; i < njobs && rc == PM_OK; i++) {
         BatchJob &j = J[i];
         cudaEvent_t e_in = ev.ev[3 * i], e_k = ev.ev[3 * i + 1], e_out = ev.ev[3 * i + 2];
-        j.dev.assign(j.spec.size(), nullptr);
         if (i > 0) {
             // inputs of job i after job i-1's kernels (and after its output copy if they alias)
             cudaStreamWaitEvent(up, ev.ev[3 * (i - 1) + 1], 0);
             if (clash(i - 1)) cudaStreamWaitEvent(up, ev.ev[3 * (i - 1) + 2], 0);
         }
+        if (i > 1) cudaStreamWaitEvent(up, ev.ev[3 * (i - 2) + 2], 0);   // job i-2's outputs left this slot
         if (i == 0) cudaEventRecord(ev.ev[3 * njobs], up);
         cudaEventRecord(beg[2 * i], up);
         std::vector<void *> bufs(j.spec.size(), nullptr);
+        unsigned char *slot = slab + sh_total + (i % 2) * priv_max;
         for (size_t b = 0; b < j.spec.size() && rc == PM_OK; b++) {
             const int k = j.shared[b];
             if (k >= 0) {   // a shared input: copied by its first reader only
                 SharedIn &e = sh[k];
                 if (!e.dev) {
-                    if (alloc_fault_injected() || cudaMallocAsync(&e.dev, e.bytes, up) != cudaSuccess) {
-                        e.dev = nullptr;
-                        rc = fail(PM_ENOMEM, "pm_run_host_batch: job %zu: allocation of shared %s failed", i,
-                                  j.spec[b].name);
-                    } else if (cudaMemcpyAsync(e.dev, e.host, e.bytes, cudaMemcpyHostToDevice, up) != cudaSuccess)
+                    e.dev = slab + sh_off[k];
+                    if (cudaMemcpyAsync(e.dev, e.host, e.bytes, cudaMemcpyHostToDevice, up) != cudaSuccess)
                         rc = fail(PM_ECUDA, "pm_run_host_batch: job %zu: host-to-device copy failed", i);
                 }
                 bufs[b] = e.dev;
                 continue;
             }
             const size_t bytes = buf_bytes(j.spec[b]);
-            if (alloc_fault_injected() || cudaMallocAsync(&j.dev[b], bytes, up) != cudaSuccess) {
-                j.dev[b] = nullptr;
-                rc = fail(PM_ENOMEM, "pm_run_host_batch: job %zu: allocation of %s failed", i, j.spec[b].name);
-            } else if (j.spec[b].role == PM_IN &&
-                       cudaMemcpyAsync(j.dev[b], jobs[i].host_bufs[b], bytes, cudaMemcpyHostToDevice, up) != cudaSuccess)
+            bufs[b] = slot;
+            slot += al(bytes);
+            if (j.spec[b].role == PM_IN &&
+                cudaMemcpyAsync(bufs[b], jobs[i].host_bufs[b], bytes, cudaMemcpyHostToDevice, up) != cudaSuccess)
                 rc = fail(PM_ECUDA, "pm_run_host_batch: job %zu: host-to-device copy failed", i);
-            bufs[b] = j.dev[b];
         }
         if (rc != PM_OK) break;
         cudaEventRecord(e_in, up);
@@ -464,18 +483,10 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
         cudaEventRecord(beg[2 * i + 1], down);
         for (size_t b = 0; b < j.spec.size() && rc == PM_OK; b++)
             if (j.spec[b].role == PM_OUT && jobs[i].host_bufs[b] &&
-                cudaMemcpyAsync(jobs[i].host_bufs[b], j.dev[b], buf_bytes(j.spec[b]), cudaMemcpyDeviceToHost, down) !=
+                cudaMemcpyAsync(jobs[i].host_bufs[b], bufs[b], buf_bytes(j.spec[b]), cudaMemcpyDeviceToHost, down) !=
                     cudaSuccess)
                 rc = fail(PM_ECUDA, "pm_run_host_batch: job %zu: device-to-host copy failed", i);
         cudaEventRecord(e_out, down);
-        for (void *d : j.dev)
-            if (d) cudaFreeAsync(d, down);
-        j.dev.clear();
-        for (SharedIn &e : sh)   // shared inputs whose last reader has run
-            if (e.last == i && e.dev) {
-                cudaFreeAsync(e.dev, down);
-                e.dev = nullptr;
-            }
     }
     if (up) cudaStreamSynchronize(up);
     if (down) {
@@ -483,11 +494,10 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
         cudaStreamSynchronize(down);
     }
     cudaStreamSynchronize(cs);
-    for (auto &j : J)   // buffers of a job that failed before its output copy
-        for (void *d : j.dev)
-            if (d) cudaFree(d);
-    for (SharedIn &e : sh)   // shared inputs of a batch that stopped early
-        if (e.dev) cudaFree(e.dev);
+    if (slab) {   // every stream that used it has drained
+        cudaFreeAsync(slab, cs);
+        cudaStreamSynchronize(cs);
+    }
     if (rc == PM_OK && copy_ms && njobs) {
         // the copies' own device time: each job's input copies (after it may
         // start) and output copies, summed; the time between them (kernels,
