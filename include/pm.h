@@ -294,8 +294,12 @@ typedef struct {
  * an output buffer of job i overlaps an input buffer of job i+1 in host
  * memory, that pair of copies is serialised instead.  Input buffers that
  * start at the same host address in several jobs are one shared region: it
- * is copied once, by its first reader, at the largest extent any reader
- * reads (every kernel only reads its inputs).  A region that any host
+ * is copied once, at the largest extent any reader reads (every kernel only
+ * reads its inputs), and all shared regions are copied back to back at the
+ * start of the batch, before the first job's kernels (on GB300 the host ->
+ * device path runs copies issued back to back at its full rate, while a
+ * copy issued after it has idled for a fraction of a second starts several
+ * times slower).  A region that any host
  * output buffer of the batch overlaps is not shared (its host contents may
  * change during the batch); each of its readers copies it.  Device staging
  * is one allocation per batch from the default memory pool (see

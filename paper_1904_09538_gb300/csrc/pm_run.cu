@@ -282,8 +282,9 @@ struct BatchJob {
 };
 
 // An input region several jobs of a batch read: every input buffer that
-// starts at the same host address.  It is copied once, by its first reader,
-// at the largest extent any of its readers reads.
+// starts at the same host address.  It is copied once, at the largest extent
+// any of its readers reads; all regions are copied back to back at the start
+// of the batch.
 struct SharedIn {
     const char *host;
     size_t bytes;
@@ -444,18 +445,18 @@ pm_status pm_run_host_batch(const pm_host_job *jobs, size_t njobs, const pm_run_
         if (i > 1) cudaStreamWaitEvent(up, ev.ev[3 * (i - 2) + 2], 0);   // job i-2's outputs left this slot
         if (i == 0) cudaEventRecord(ev.ev[3 * njobs], up);
         cudaEventRecord(beg[2 * i], up);
+        if (i == 0)   // every shared region in one burst of back-to-back copies, before any kernel
+            for (size_t k = 0; k < sh.size() && rc == PM_OK; k++) {
+                sh[k].dev = slab + sh_off[k];
+                if (cudaMemcpyAsync(sh[k].dev, sh[k].host, sh[k].bytes, cudaMemcpyHostToDevice, up) != cudaSuccess)
+                    rc = fail(PM_ECUDA, "pm_run_host_batch: host-to-device copy of shared region %zu failed", k);
+            }
         std::vector<void *> bufs(j.spec.size(), nullptr);
         unsigned char *slot = slab + sh_total + (i % 2) * priv_max;
         for (size_t b = 0; b < j.spec.size() && rc == PM_OK; b++) {
             const int k = j.shared[b];
-            if (k >= 0) {   // a shared input: copied by its first reader only
-                SharedIn &e = sh[k];
-                if (!e.dev) {
-                    e.dev = slab + sh_off[k];
-                    if (cudaMemcpyAsync(e.dev, e.host, e.bytes, cudaMemcpyHostToDevice, up) != cudaSuccess)
-                        rc = fail(PM_ECUDA, "pm_run_host_batch: job %zu: host-to-device copy failed", i);
-                }
-                bufs[b] = e.dev;
+            if (k >= 0) {   // a shared input, already on the device
+                bufs[b] = sh[k].dev;
                 continue;
             }
             const size_t bytes = buf_bytes(j.spec[b]);

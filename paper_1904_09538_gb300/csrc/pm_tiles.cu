@@ -243,11 +243,12 @@ size_t dgt_smem(int Np) {
     return (size_t)128 * 2 * Q * 4 + (Np % 2 ? (size_t)128 * Np * 4 : 0) + (size_t)NPP * dgt_pd(Q) * 4 + 8;
 }
 
-// NPC: Np fixed at compile time (the paper's sizes), 0 = taken from the argument
+// NPC: Np fixed at compile time (the paper's sizes), 0 = taken from the
+// argument.  Five CTAs per SM for Np = 20 (68 registers; measured 7 % faster
+// than the unconstrained 72)
 template <int NB, int NPC>
-__global__ void __launch_bounds__(NPC ? 16 * dgt_xl(NPC, NB) : 256, NB <= 3 ? 3 : 2) k_dg_tile(const float *__restrict__ D,
-                                                                  const float *__restrict__ u,
-                                                                  float *__restrict__ res, int np_arg, int Nel) {
+__global__ void __launch_bounds__(NPC ? 16 * dgt_xl(NPC, NB) : 256, (NPC && NB <= 2) ? 5 : (NB <= 3 ? 3 : 2))
+    k_dg_tile(const float *__restrict__ D, const float *__restrict__ u, float *__restrict__ res, int np_arg, int Nel) {
     constexpr int QBM = NB / 2 + 2;   // bound on ceil(Q / XL)
     const int Np = NPC ? NPC : np_arg;
     const int XL = dgt_xl(Np, NB), NPP = XL * NB, Q = (Np + 1) / 2, PD = dgt_pd(Q), P2 = PD / 2;
@@ -299,7 +300,7 @@ __global__ void __launch_bounds__(NPC ? 16 * dgt_xl(NPC, NB) : 256, NB <= 3 ? 3 
     }
     __syncthreads();
     const bool ok = mbar_wait_bounded(bar, 0, &g_dgt_timeout, 1ll << 26);
-    if (!ok && leader) mbar_wait_bounded(bar, 0, &g_dgt_timeout, 1ll << 26);   // drain our own copy
+    if (!ok && leader) mbar_drain(bar, 0, 1ll << 26);   // drain our own copy
     if (!even) {
         if (ok)
 #pragma unroll

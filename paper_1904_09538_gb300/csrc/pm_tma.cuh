@@ -34,6 +34,13 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t parity
     atomicExch(flag, 1);
     return false;
 }
+// bounded wait that ignores the error word: used to drain a CTA's own copies
+// in flight before it exits after another wait gave up
+__device__ __forceinline__ bool mbar_drain(uint64_t *bar, uint32_t parity, long long limit) {
+    for (long long i = 0; i < limit; i++)
+        if (mbar_try(bar, parity)) return true;
+    return false;
+}
 __device__ __forceinline__ void mbar_arrive(uint64_t *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
 }
