@@ -545,6 +545,16 @@ const char *pm_last_error(void);
  * n < 0. */
 pm_status pm_test_fail_allocation(int32_t n);
 
+/* Test hook (failure detection without a GPU fault): one CTA waits, with
+ * the bounded mbarrier wait and the device error word of the TMA-staged
+ * dg_tile kernel, on an mbarrier phase that nothing completes (no arrival,
+ * no copy in flight); after `polls` polls (1..2^20) the wait gives up and
+ * sets the word, and the host reads and clears it as after a dg_tile
+ * launch.  The call synchronizes `stream` (NULL: the legacy default
+ * stream).  Returns PM_ETIMEOUT when the wait gave up, as it always does;
+ * the context stays usable.  PM_EINVAL for polls out of range. */
+pm_status pm_test_bounded_wait(int64_t polls, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -75,6 +75,7 @@ fp = P(ctypes.c_float)
 SIGNATURES = {
     "pm_last_error": (ctypes.c_char_p, []),
     "pm_test_fail_allocation": (i32, [i32]),
+    "pm_test_bounded_wait": (i32, [ctypes.c_int64, vp]),
     "pm_kernel_lookup": (i32, [ctypes.c_char_p, P(i32)]),
     "pm_kernel_count": (i32, [P(i32)]),
     "pm_kernel_name": (i32, [i32, P(ctypes.c_char_p)]),

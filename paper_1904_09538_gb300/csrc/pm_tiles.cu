@@ -165,7 +165,7 @@ __global__ void __launch_bounds__((BX / V) * BY) k_fd_block(const __grid_constan
         tma_load_2d(T, &tmU, bar, BX * blockIdx.x, BY * blockIdx.y);
     }
     bool ok = mbar_wait_bounded(bar, 0, &g_fdb_timeout, 1ll << 26);
-    if (!ok && leader) mbar_wait_bounded(bar, 0, &g_fdb_timeout, 1ll << 26);   // drain our own copy
+    if (!ok && leader) mbar_drain(bar, 0, 1ll << 26);   // drain our own copy
     if (!ok) return;
     const float *r0 = T + ly * TW + V * lx;       // north row
     const float *r1 = r0 + TW;                    // centre row
@@ -360,6 +360,18 @@ pm_status launch_dgt_t(void *const *b, int Np, int Nel, cudaStream_t st) {
     return PM_OK;
 }
 
+// Test of the bounded-wait path: one thread waits on an mbarrier whose
+// phase nothing completes (no arrival, no copy), through the dg_tile kernel's
+// wait and error word.
+__global__ void k_wait_nothing(long long polls) {
+    __shared__ uint64_t bar;
+    if (threadIdx.x == 0) {
+        mbar_init(&bar, 1);
+        mbar_init_fence();
+        mbar_wait_bounded(&bar, 0, &g_dgt_timeout, polls);
+    }
+}
+
 }  // namespace
 
 pm_status dgt_check_timeout() {
@@ -425,3 +437,13 @@ pm_status launch_tiles(const KP &kp, void *const *b, void *stream) {
 }
 
 }  // namespace pm
+
+extern "C" pm_status pm_test_bounded_wait(int64_t polls, void *stream) {
+    using namespace pm;
+    if (polls < 1 || polls > (1 << 20)) return fail(PM_EINVAL, "pm_test_bounded_wait: polls must be 1..2^20");
+    cudaStream_t st = (cudaStream_t)stream;
+    k_wait_nothing<<<1, 32, 0, st>>>((long long)polls);
+    PM_CUDA_TRY(cudaGetLastError());
+    PM_CUDA_TRY(cudaStreamSynchronize(st));
+    return dgt_check_timeout();
+}

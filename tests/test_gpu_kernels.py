@@ -401,6 +401,27 @@ def test_dg_tile(Np, Nel):
     assert cond_err(res.reshape(3, Nel, Np), ref, rabs) <= TOL
 
 
+def test_bounded_wait_gives_up_and_reports_timeout():
+    # failure detection without a GPU fault: a wait on an mbarrier phase that
+    # nothing completes gives up after its poll limit through the dg_tile
+    # kernel's wait and error word; the host reads PM_ETIMEOUT, clears the
+    # word, and the context keeps working (a dg_tile launch afterwards is
+    # exact and reports no timeout); polls out of range are refused
+    dev()
+    L = pm.lib()
+    for polls in (1, 4096):
+        assert L.pm_test_bounded_wait(polls, None) == -6, pm.lib().pm_last_error()
+    assert L.pm_test_bounded_wait(0, None) == -1 and L.pm_test_bounded_wait(1 << 21, None) == -1
+    D, u = pm_inputs.normal((3, 20, 20), 21), pm_inputs.normal((132, 20), 22)
+    (res,) = run_kernel("dg_tile", [D, u], Np=20, Nel=132)
+    ref, rabs = refs.dg(D, u)
+    assert cond_err(res.reshape(3, 132, 20), ref, rabs) <= TOL
+    d = dev()
+    bufs = [torch.from_numpy(D).to(d), torch.from_numpy(u).to(d), torch.empty(3 * 132 * 20, device=d)]
+    tm = pm.run("dg_tile", bufs, warmup=0, trials=2, Np=20, Nel=132)   # reads the error word
+    assert tm["n_trials"] == 2
+
+
 @pytest.mark.parametrize("Np", [20, 35, 56, 84])
 def test_dg_tile_full_size_sampled_and_timed(Np):
     Nel = 1 << 18
