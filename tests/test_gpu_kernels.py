@@ -3,6 +3,10 @@ inputs, through the C ABI.  Bit-exact where the kernel's operation order is
 fixed (suite kernels, work-removed twins); within 1e-5 of the FP64
 reference, relative to sum |terms| (condition-aware), for matmul, DG and
 stencil.  Buffers carry guard bands that must stay untouched."""
+import os
+import subprocess
+import sys
+
 import numpy as np
 import pytest
 
@@ -15,6 +19,7 @@ from oracle import refs  # noqa: E402
 
 TOL = 1e-5
 GUARD = 64
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 SENT = {np.float32: 1234.5, np.float64: -4321.25}
 
 
@@ -399,6 +404,18 @@ def test_dg_tile(Np, Nel):
     (res,) = run_kernel("dg_tile", [D, u], Np=Np, Nel=Nel)
     ref, rabs = refs.dg(D, u)
     assert cond_err(res.reshape(3, Nel, Np), ref, rabs) <= TOL
+
+
+def test_tma_kernel_resources_as_first_cuda_call():
+    # a resource query of a TMA-staged kernel encodes a tensor map; as the
+    # first CUDA call of a process (no context current yet) it must work too
+    dev()
+    code = ("import paper_1904_09538_gb300 as pm; "
+            "r = pm.resources('fd_block', n=8192, BX=64, BY=16, V=8); "
+            "assert r['grid_blocks'] == (8192 // 64) * (8192 // 16), r; "
+            "r = pm.resources('mm_tc', n=1024); assert r['grid_blocks'] > 0; print('ok')")
+    out = subprocess.run([sys.executable, "-c", code], cwd=ROOT, capture_output=True, text=True, timeout=300)
+    assert out.returncode == 0 and out.stdout.strip().endswith("ok"), out.stderr[-2000:]
 
 
 def test_bounded_wait_gives_up_and_reports_timeout():
