@@ -78,7 +78,17 @@ typedef struct {
  * TMEM columns sharing each Bt box, 3-stage ring, one CTA per SM); the DG
  * tile form "dg_tile" (parameters Np <= 96 and Nel, a multiple of 4; buffers
  * diff_mat, u, res as for dg_nopf; 16 x 16 work-groups of 128 elements, D
- * staged transposed in shared memory, u tiles by one bulk TMA copy); the TMA-staged
+ * staged transposed in shared memory, u tiles by one bulk TMA copy); its
+ * tensor-core form "dg_tc" (parameters Np, one of the tetrahedral node
+ * counts 4, 10, 20, 35, 56, 84, Nel a multiple of 4 (<= 2^24), P the
+ * persistent CTAs per m-group, 0 = one wave of a GB300, and A the place of
+ * the u operand, 0 = shared memory, 1 = tensor memory, -1 (default) = 1 for
+ * Np > 20 else 0; buffers as for dg_nopf): the product of each
+ * 128-element tile with the stacked operator rows on tcgen05.mma kind::tf32,
+ * every operand split into a TF32 head and its FP32 remainder and three
+ * passes (head x head, head x remainder, remainder x head) accumulated in
+ * FP32 in tensor memory, so the result carries FP32-level accuracy; u tiles
+ * by TMA when Np % 4 == 0, the res blocks by bulk copies; the TMA-staged
  * stencil tile family "fd_block" (parameters n, BX, BY, c0, c1, V = 4 or 8
  * outputs per work-item; input u of (n + 2) rows with row pitch n + 4).
  * Returns PM_EUNKNOWN_KERNEL for other names. */

@@ -46,6 +46,7 @@ static constexpr double REQ = std::numeric_limits<double>::quiet_NaN();
 #define P_TC {"n", "pipe", nullptr}, {REQ, 1}, {1, 1}
 #define P_TCW {"n", nullptr}, {REQ}, {1}
 #define P_DGT {"Np", "Nel", nullptr}, {REQ, REQ}, {1, 1}
+#define P_DGC {"Np", "Nel", "P", "A", nullptr}, {REQ, REQ, 0, -1}, {1, 1, 1, 1}
 #define P_FDB {"n", "BX", "BY", "c0", "c1", "V", nullptr}, {REQ, 64, 8, -4.0, 1.0, 4}, {1, 1, 1, 0, 0, 1}
 
 static const KernelDef KDEFS[] = {
@@ -88,6 +89,7 @@ static const KernelDef KDEFS[] = {
     {"smem2d", FAM_SMEM2D, 0, P_SMEM2D},
     {"mm_tc256", FAM_TC, 1, P_TCW},
     {"dg_tile", FAM_DGT, 0, P_DGT},
+    {"dg_tc", FAM_DGC, 0, P_DGC},
 };
 
 const KernelDef *kernel_def(int32_t id) {

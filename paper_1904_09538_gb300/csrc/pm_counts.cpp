@@ -823,6 +823,16 @@ pm_status validate(const KP &kp) {
     case FAM_FD:
         if (kp.i(0) < 1 || kp.i(0) > 46000) return fail(PM_EINVAL, "%s: n must be 1..46000", nm);
         return PM_OK;
+    case FAM_DGC: {
+        const i64 Np = kp.i(0), Nel = kp.i(1), P = kp.i(2);
+        if (Np != 4 && Np != 10 && Np != 20 && Np != 35 && Np != 56 && Np != 84)
+            return fail(PM_EINVAL, "%s: Np must be 4, 10, 20, 35, 56 or 84", nm);
+        if (Nel < 4 || Nel % 4 || Nel > (1LL << 24))
+            return fail(PM_EINVAL, "%s: Nel must be a positive multiple of 4 (<= 2^24)", nm);
+        if (P < 0 || P > 4096) return fail(PM_EINVAL, "%s: P must be 0 (default) or 1..4096", nm);
+        if (kp.i(3) < -1 || kp.i(3) > 1) return fail(PM_EINVAL, "%s: A must be -1 (default), 0 or 1", nm);
+        return PM_OK;
+    }
     case FAM_DGT:
         if (kp.i(0) < 1 || kp.i(0) > 96) return fail(PM_EINVAL, "%s: Np must be 1..96", nm);
         if (kp.i(1) < 4 || kp.i(1) % 4 || kp.i(1) > 65535LL * 128)
@@ -944,7 +954,8 @@ pm_status buffers(const KP &kp, std::vector<BufSpec> &b) {
         }
         break;
     }
-    case FAM_DGT: {
+    case FAM_DGT:
+    case FAM_DGC: {
         uint64_t Np = (uint64_t)kp.i(0), Nel = (uint64_t)kp.i(1);
         b.push_back({"diff_mat", PM_F32, PM_IN, 3 * Np * Np});
         b.push_back({"u", PM_F32, PM_IN, Nel * Np});

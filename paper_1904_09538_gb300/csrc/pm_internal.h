@@ -41,7 +41,7 @@ void set_fail_allocation(int n);
 
 // ---- kernel registry ------------------------------------------------------
 enum Family { FAM_STREAM, FAM_FMA, FAM_SMEM, FAM_BARRIER, FAM_OVERLAP, FAM_EMPTY, FAM_MM, FAM_DG, FAM_FD, FAM_SIMT, FAM_TC, FAM_FDB,
-              FAM_SMEM2D, FAM_DGT };
+              FAM_SMEM2D, FAM_DGT, FAM_DGC };
 
 constexpr int kMaxParams = 8;
 
@@ -108,6 +108,18 @@ pm_status launch_tc(const KP &kp, void *const *bufs, void *stream);
 pm_status tc_check_timeout();
 pm_status fdb_check_timeout();
 pm_status dgt_check_timeout();
+pm_status launch_dgc(const KP &kp, void *const *bufs, void *stream);
+pm_status dgc_check_timeout();
+// dg_tc geometry shared by the launch and the counts: m per CTA, CTAs per SM,
+// shared-memory stages and output staging buffers of the u operand's form
+// (the stages and buffers of A = 0; A = 1 has 4 raw stages when Np % 4 == 0
+// and 2 staging buffers)
+struct DgcShape {
+    int ms, r, st, ob;
+};
+DgcShape dgc_geometry(int Np, int A);
+int dgc_resolve_a(int Np, int A);                      // -1: the library's choice for Np
+int dgc_resolve_p(int Np, int64_t Nel, int A, int P);  // 0: one wave of a GB300
 // 2-D tensor map (TMA descriptor) over a row-major matrix; `map` must point
 // to a CUtensorMap (64-byte aligned, 128 bytes).
 pm_status tensor_map_2d(struct CUtensorMap_st *map, int bf16, const void *ptr, uint64_t cols, uint64_t rows,

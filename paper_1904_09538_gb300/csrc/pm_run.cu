@@ -25,6 +25,7 @@ static pm_status launch_any(const KP &kp, void *const *bufs, size_t nbufs, void 
     case FAM_MM: case FAM_DG: case FAM_FD: return launch_modeled(kp, bufs, stream);
     case FAM_SIMT: case FAM_FDB: case FAM_DGT: return launch_tiles(kp, bufs, stream);
     case FAM_TC: return launch_tc(kp, bufs, stream);
+    case FAM_DGC: return launch_dgc(kp, bufs, stream);
     default: return launch_suite(kp, bufs, stream);
     }
 }
@@ -145,6 +146,7 @@ static pm_status timed(const KP &kp, void *const *bufs, size_t nbufs, const pm_r
     if (kp.def->fam == FAM_TC && (s = tc_check_timeout())) return s;
     if (kp.def->fam == FAM_FDB && (s = fdb_check_timeout())) return s;
     if (kp.def->fam == FAM_DGT && (s = dgt_check_timeout())) return s;
+    if (kp.def->fam == FAM_DGC && (s = dgc_check_timeout())) return s;
     std::vector<float> ms(o.trials);
     for (int t = 0; t < o.trials; t++) PM_CUDA_TRY(cudaEventElapsedTime(&ms[t], pool.ev[2 * t], pool.ev[2 * t + 1]));
     if (trial_ms)

@@ -406,6 +406,35 @@ def test_dg_tile(Np, Nel):
     assert cond_err(res.reshape(3, Nel, Np), ref, rabs) <= TOL
 
 
+# dg_tc: the tensor-core form (TF32 head/remainder split, three passes);
+# ragged last tiles, one and three CTAs per m-group (the ring and the two
+# accumulators wrap many times), every supported node count
+@pytest.mark.parametrize("Np,Nel,P", [(20, 132, 0), (20, 4, 0), (35, 256, 0), (56, 260, 0), (84, 1024, 0),
+                                      (84, 132, 0), (4, 8, 0), (10, 300, 0), (20, 4100, 1), (35, 1028, 3),
+                                      (56, 2052, 1), (84, 3076, 2), (10, 1 << 12, 1), (4, 1 << 12, 0)])
+@pytest.mark.parametrize("A", [0, 1])
+def test_dg_tc(Np, Nel, P, A):
+    D, u = pm_inputs.normal((3, Np, Np), 21), pm_inputs.normal((Nel, Np), 22)
+    (res,) = run_kernel("dg_tc", [D, u], Np=Np, Nel=Nel, P=P, A=A)
+    ref, rabs = refs.dg(D, u)
+    assert cond_err(res.reshape(3, Nel, Np), ref, rabs) <= TOL
+
+
+@pytest.mark.parametrize("Np", [20, 35, 56, 84])
+@pytest.mark.parametrize("A", [0, 1])
+def test_dg_tc_full_size_sampled_and_timed(Np, A):
+    Nel = 1 << 18
+    D, u = pm_inputs.normal((3, Np, Np), 41), pm_inputs.normal((Nel, Np), 42)
+    d = dev()
+    res = torch.full((3 * Nel * Np,), float("nan"), device=d)
+    bufs = [torch.from_numpy(D).to(d), torch.from_numpy(u).to(d), res]
+    tm = pm.run("dg_tc", bufs, warmup=2, trials=5, Np=Np, Nel=Nel, A=A)
+    ks = np.unique(np.concatenate([pm_inputs.integers((512,), 43, 0, Nel - 1), [0, Nel - 1]]))
+    ref, rabs = refs.dg(D, u[ks])
+    got = res.cpu().numpy().reshape(3, Nel, Np)[:, ks, :]
+    assert cond_err(got, ref, rabs) <= TOL and tm["mean_ms"] > 0
+
+
 def test_tma_kernel_resources_as_first_cuda_call():
     # a resource query of a TMA-staged kernel encodes a tensor map; as the
     # first CUDA call of a process (no context current yet) it must work too
