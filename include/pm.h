@@ -80,10 +80,13 @@ typedef struct {
  * diff_mat, u, res as for dg_nopf; 16 x 16 work-groups of 128 elements, D
  * staged transposed in shared memory, u tiles by one bulk TMA copy); its
  * tensor-core form "dg_tc" (parameters Np, one of the tetrahedral node
- * counts 4, 10, 20, 35, 56, 84, Nel a multiple of 4 (<= 2^24), P the
- * persistent CTAs per m-group, 0 = one wave of a GB300, and A the place of
- * the u operand, 0 = shared memory, 1 = tensor memory, -1 (default) = 1 for
- * Np > 20 else 0; buffers as for dg_nopf): the product of each
+ * counts 4, 10, 20, 35, 56, 84, Nel a multiple of 4 (<= 2^24), A the
+ * place of the u operand, 0 = shared memory, 1 = tensor memory, -1
+ * (default) = 1 for Np > 20 else 0, and P the persistent CTAs per m-group,
+ * 0 (default) = min(ceil(Nel / 128), 152 R / G), one wave of a GB300's 152
+ * SMs with R = 2 CTAs per SM for A = 0 and Np <= 20, else 1, and G = 1
+ * m-group for Np <= 40 (the three m in one CTA), else 3; the grid is (G, P);
+ * buffers as for dg_nopf): the product of each
  * 128-element tile with the stacked operator rows on tcgen05.mma kind::tf32,
  * every operand split into a TF32 head and its FP32 remainder and three
  * passes (head x head, head x remainder, remainder x head) accumulated in

@@ -90,12 +90,13 @@ KERNELS["mm_simt"] = (("n", "BM", "BN", "BK"), (2, 2))
 KERNELS["mm_tc"] = (("n",), (1, 2))
 KERNELS["mm_tc256"] = (("n",), (1, 2))
 KERNELS["dg_tile"] = (("Np", "Nel"), (2, 2))
+KERNELS["dg_tc"] = (("Np", "Nel", "P", "A"), (1, 2))
 KERNELS["fd_block"] = (("n", "BX", "BY", "V"), (2, 2))
 KERNELS["smem2d"] = (("R", "T", "G"), (2, 1))
 
 # default parameter values (dtype 0 = float32)
 DEFAULTS = {"dtype": 0, "vec": 0, "s": 1, "L": 1, "shape": 0, "W": 16, "op": 2, "sync": 0, "L0": 16, "L1": 16,
-            "BX": 64, "BY": 8, "T": 16, "V": 4}
+            "BX": 64, "BY": 8, "T": 16, "V": 4, "P": 0, "A": -1}
 
 
 def dims(kernel, params):

@@ -43,7 +43,7 @@
 
 enum { MEM_GLOBAL = 0, MEM_LOCAL = 1 };
 enum { DIR_LOAD = 0, DIR_STORE = 1 };
-enum { DT_F32 = 0, DT_F64 = 1, DT_BF16 = 2 };
+enum { DT_F32 = 0, DT_F64 = 1, DT_BF16 = 2, DT_TF32 = 3 };
 
 typedef struct ctx ctx;
 typedef long long (*idx_fn)(const ctx *c, const long long *g, const long long *l, const long long *lv);
@@ -119,7 +119,7 @@ struct ctx {
     long long g[3], l[3];
     /* accumulators */
     site_stat ss[MAXSITE];
-    unsigned long long op_wi[3][3], op_sg[3][3];  /* [dtype][add,mul,madd] */
+    unsigned long long op_wi[4][3], op_sg[4][3];  /* [dtype][add,mul,madd] */
     unsigned long long stmt_sg[MAXSTMT], stmt_wi[MAXSTMT];
     long long bar_cur, bar_min, bar_max;
     kset sgset;              /* distinct statement instances of the current SG */
@@ -1345,6 +1345,178 @@ static int setup_dgt(ctx *c) {
 }
 
 /* ======================================================================
+ * DG derivative on the tensor cores ("dg_tc"), res[m, k, i] =
+ * sum_j D[m, i, j] u[k, j], TF32 head/remainder split in three passes.
+ * P = {Np, Nel, P, A}.  Np in {4, 10, 20, 35, 56, 84}; Nel a multiple of 4.
+ * The kernel's definition of its launch:
+ *   MS = 3 m per work-group for Np <= 40, else 1; G = 3 / MS m-groups;
+ *   A < 0 means A = (Np > 20); R = 2 work-groups per SM for A = 0 and
+ *   Np <= 20, else 1; P = 0 means min(T, 152 R / G), T = ceil(Nel / 128);
+ *   grid (G, P), work-group of 320 work-items (1-D).
+ * NP8 = Np rounded up to 8, NR = MS NP8 rounded up to 16 (MMA N), KA =
+ * ceil(Np / 32) atoms of 32 columns, KS = ceil(Np / 8) k steps, CN(a) =
+ * 2 min(4, KS - 4a) chunks of atom a.  Work-group (g, p) serves tiles
+ * t = p + P lt < T; rows(t) = min(128, Nel - 128 t).  Per work-item tid:
+ *  - tid < NP8, m-block mm < MS, chunk ac < 8 KA: element loads
+ *    D[m, tid, 4 ac + x] (m = mm when MS = 3, else g) for tid, 4 ac + x < Np;
+ *    one statement with 4 adds and two 16-byte local stores (head,
+ *    remainder) at row mm NP8 + tid, chunk ac;
+ *  - tid < NR - MS NP8: two zero stores per chunk ac of padding row
+ *    MS NP8 + tid;  one barrier;
+ *  - per tile, Np % 4 == 0: work-item 256 copies element (r, cc) of the box
+ *    at row 128 t, column 32 a for r < rows(t), 32 a + cc < Np;
+ *  - per tile, converter 128 <= tid < 256, r = tid - 128, atom a, chunk
+ *    c < CN(a): Np % 4 == 0: a 16-byte local load of (r, c); else element
+ *    loads u[128 t + r, 32 a + 4 c + x] for 128 t + r < Nel, 32 a + 4 c + x
+ *    < Np; one statement of 4 adds with, for A = 0, two 16-byte local
+ *    stores (r, c);
+ *  - per tile, work-item 288, atom a, k step kk < min(4, KS - 4a): 3 x 128 x
+ *    NR x 8 TF32 multiply-adds;
+ *  - per tile, epilogue tid < 128, per m-block mm: the row's Np / 4 16-byte
+ *    local stores (Np % 4 == 0, else Np element stores), and work-item 0
+ *    stores the rows(t) x Np elements of res[m, 128 t .., :] (m = mm when
+ *    MS = 3, else g);
+ *  - two barriers at the end.
+ * The epilogue's own synchronisation (named barriers over its 128
+ * work-items) is not a work-group barrier and is not counted: every
+ * work-item passes the same three work-group barriers.
+ * Local sites are indexed by the logical (row, chunk) position in one ring
+ * stage or staging buffer.
+ * ====================================================================== */
+#define DC_NP(c) ((c)->P[0])
+#define DC_MS(c) (DC_NP(c) <= 40 ? 3 : 1)
+#define DC_NP8(c) ((DC_NP(c) + 7) / 8 * 8)
+#define DC_NR(c) ((DC_MS(c) * DC_NP8(c) + 15) / 16 * 16)
+#define DC_KA(c) (cdiv(DC_NP(c), 32))
+#define DC_KS(c) (cdiv(DC_NP(c), 8))
+static long long dc_m(const ctx *c, const long long *g, long long mm) { return DC_MS(c) == 3 ? mm : G0; }
+static long long dc_tile(const ctx *c, const long long *g, long long lt) { return G1 + c->D[0] * lt; }
+static long long ix_dc_D(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long Np = DC_NP(c);
+    return (dc_m(c, g, lv[0]) * Np + L0_) * Np + 4 * lv[1] + lv[2];
+}
+static long long ix_dc_B(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; return (lv[0] * DC_NP8(c) + L0_) * 8 * DC_KA(c) + lv[1];
+}
+static long long ix_dc_ubox(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)l; long long Np = DC_NP(c), a = lv[1] / 128, r = lv[1] % 128;
+    return (128 * dc_tile(c, g, lv[0]) + r) * Np + 32 * a + lv[2];
+}
+static long long ix_dc_ug(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    long long Np = DC_NP(c);
+    return (128 * dc_tile(c, g, lv[0]) + (L0_ - 128)) * Np + 4 * lv[1] + lv[2];
+}
+static long long ix_dc_U(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; (void)c; return (L0_ - 128) * 8 + lv[2];
+}
+static long long ix_dc_O(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; long long Np = DC_NP(c); return L0_ * (Np % 4 == 0 ? Np / 4 : Np) + lv[2];
+}
+static long long ix_dc_res(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)l; long long Np = DC_NP(c), Nel = c->P[1];
+    return (dc_m(c, g, lv[1]) * Nel + 128 * dc_tile(c, g, lv[0])) * Np + lv[2];
+}
+/* statements: 0 D element load, 1 split + operator stores, 2 padding stores,
+ * 3 u box element copy, 4 u element load, 5 staged-chunk load, 6 split (+
+ * stores for A = 0), 7 MMA k step, 8 staging store, 9 res element copy */
+static void walk_dgc(ctx *c) {
+    long long Np = DC_NP(c), Nel = c->P[1], P = c->D[0], MS = DC_MS(c), NP8 = DC_NP8(c), NR = DC_NR(c);
+    long long KA = DC_KA(c), KS = DC_KS(c), T = cdiv(Nel, 128), tid = c->l[0], lv[3];
+    if (tid < NP8)
+        for (lv[0] = 0; lv[0] < MS; lv[0]++)
+            for (lv[1] = 0; lv[1] < 8 * KA; lv[1]++) {
+                for (lv[2] = 0; lv[2] < 4; lv[2]++)
+                    if (tid < Np && 4 * lv[1] + lv[2] < Np) X(c, 0, lv);
+                X(c, 1, lv);
+            }
+    if (tid < NR - MS * NP8) {
+        lv[0] = MS;
+        for (lv[1] = 0; lv[1] < 8 * KA; lv[1]++) X(c, 2, lv);
+    }
+    BAR(c);
+    for (long long lt = 0; c->g[1] + P * lt < T; lt++) {
+        const long long t = c->g[1] + P * lt, rows = Nel - 128 * t < 128 ? Nel - 128 * t : 128;
+        lv[0] = lt;
+        if (tid == 256 && Np % 4 == 0)
+            for (long long a = 0; a < KA; a++)
+                for (long long r = 0; r < rows; r++) {
+                    lv[1] = 128 * a + r;
+                    for (lv[2] = 0; lv[2] < 32 && 32 * a + lv[2] < Np; lv[2]++) X(c, 3, lv);
+                }
+        if (tid >= 128 && tid < 256) {
+            const long long r = tid - 128;
+            for (long long a = 0; a < KA; a++) {
+                const long long cn = 2 * (KS - 4 * a < 4 ? KS - 4 * a : 4);
+                for (long long ch = 0; ch < cn; ch++) {
+                    if (Np % 4 == 0) {
+                        lv[1] = a; lv[2] = ch;
+                        X(c, 5, lv);
+                    } else {
+                        lv[1] = 8 * a + ch;
+                        for (lv[2] = 0; lv[2] < 4; lv[2]++)
+                            if (128 * t + r < Nel && 32 * a + 4 * ch + lv[2] < Np) X(c, 4, lv);
+                    }
+                    lv[1] = a; lv[2] = ch;
+                    X(c, 6, lv);
+                }
+            }
+        }
+        if (tid == 288)
+            for (lv[1] = 0; lv[1] < KA; lv[1]++)
+                for (lv[2] = 0; lv[2] < 4 && 4 * lv[1] + lv[2] < KS; lv[2]++) X(c, 7, lv);
+        if (tid < 128) {
+            for (lv[1] = 0; lv[1] < MS; lv[1]++) {
+                for (lv[2] = 0; lv[2] < (Np % 4 == 0 ? Np / 4 : Np); lv[2]++) X(c, 8, lv);
+                if (tid == 0)
+                    for (lv[2] = 0; lv[2] < rows * Np; lv[2]++) X(c, 9, lv);
+            }
+        }
+    }
+    BAR(c);
+    BAR(c);
+    (void)NR;
+}
+static int setup_dgc(ctx *c) {
+    long long Np = DC_NP(c), Nel = c->P[1], P = c->P[2], A = c->P[3];
+    if (Np != 4 && Np != 10 && Np != 20 && Np != 35 && Np != 56 && Np != 84) return -1;
+    if (Nel < 4 || Nel % 4 || P < 0 || A < -1 || A > 1) return -1;
+    if (A < 0) A = Np > 20;
+    const long long MS = DC_MS(c), G = 3 / MS, R = (A == 0 && Np <= 20) ? 2 : 1, T = cdiv(Nel, 128);
+    if (P == 0) P = T < 152 * R / G ? T : 152 * R / G;
+    c->D[0] = P;
+    c->grid[0] = G; c->grid[1] = P; c->grid[2] = 1;
+    c->wg[0] = 320; c->wg[1] = 1; c->wg[2] = 1;
+    const int tf = (Np % 4 == 0);
+    int s0 = add_stmt(c, 3, DT_F32, 0, 0, 0);
+    stmt_site(c, s0, add_site(c, "dgc-D", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dc_D));
+    int sBh = add_site(c, "dgc-Bh", MEM_LOCAL, DIR_STORE, "float32x4", 16, ix_dc_B);
+    int sBl = add_site(c, "dgc-Bl", MEM_LOCAL, DIR_STORE, "float32x4", 16, ix_dc_B);
+    int s1 = add_stmt(c, 2, DT_F32, 4, 0, 0);
+    stmt_site(c, s1, sBh); stmt_site(c, s1, sBl);
+    int s2 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+    stmt_site(c, s2, sBh); stmt_site(c, s2, sBl);
+    int s3 = add_stmt(c, 3, DT_F32, 0, 0, 0);
+    stmt_site(c, s3, add_site(c, "dgc-u", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dc_ubox));
+    int s4 = add_stmt(c, 3, DT_F32, 0, 0, 0);
+    stmt_site(c, s4, add_site(c, "dgc-u", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dc_ug));
+    int s5 = add_stmt(c, 3, DT_F32, 0, 0, 0);
+    stmt_site(c, s5, add_site(c, "dgc-Ur", MEM_LOCAL, DIR_LOAD, "float32x4", 16, ix_dc_U));
+    int s6 = add_stmt(c, 3, DT_F32, 4, 0, 0);
+    if (A == 0) {
+        stmt_site(c, s6, add_site(c, "dgc-Uh", MEM_LOCAL, DIR_STORE, "float32x4", 16, ix_dc_U));
+        stmt_site(c, s6, add_site(c, "dgc-Ul", MEM_LOCAL, DIR_STORE, "float32x4", 16, ix_dc_U));
+    }
+    add_stmt(c, 3, DT_TF32, 0, 0, (int)(3 * 128 * DC_NR(c) * 8));
+    int s8 = add_stmt(c, 3, DT_F32, 0, 0, 0);
+    stmt_site(c, s8, add_site(c, "dgc-O", MEM_LOCAL, DIR_STORE, tf ? "float32x4" : "float32", tf ? 16 : 4, ix_dc_O));
+    int s9 = add_stmt(c, 3, DT_F32, 0, 0, 0);
+    stmt_site(c, s9, add_site(c, "dgc-res", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dc_res));
+    (void)s0; (void)s3; (void)s4; (void)s5;
+    c->walk = walk_dgc;
+    return 0;
+}
+
+/* ======================================================================
  * Public oracle entry: enumerate every (group, sub-group, lane) point.
  * ====================================================================== */
 typedef struct {
@@ -1419,6 +1591,7 @@ static const struct { const char *name; int fam, v; } KTAB[] = {
     {"smem2d", 12, 0},
     {"mm_tc256", 10, 1},
     {"dg_tile", 13, 0},
+    {"dg_tc", 14, 0},
 };
 
 static int counts_impl(const char *kernel, const char *remove, const long long *P, int nP, orec *out, int cap,
@@ -1455,6 +1628,7 @@ static int counts_impl(const char *kernel, const char *remove, const long long *
     case 11: rc = setup_fdb(c); break;
     case 12: rc = setup_smem2d(c); break;
     case 13: rc = setup_dgt(c); break;
+    case 14: rc = setup_dgc(c); break;
     }
     if (rc) { free(c); return -2; }
     if (remove && make_twin(c, remove)) { free(c); return -5; }
@@ -1484,8 +1658,8 @@ static int counts_impl(const char *kernel, const char *remove, const long long *
     int n = 0;
 #define EMIT() do { if (n >= cap) { rc = -4; goto done; } memset(&out[n], 0, sizeof(orec)); } while (0)
     static const char *opn[3] = {"add", "mul", "madd"};
-    static const char *dtn[3] = {"float32", "float64", "bfloat16"};
-    for (int dt = 0; dt < 3; dt++)
+    static const char *dtn[4] = {"float32", "float64", "bfloat16", "tfloat32"};
+    for (int dt = 0; dt < 4; dt++)
         for (int o = 0; o < 3; o++)
             if (c->op_wi[dt][o]) {
                 EMIT();

@@ -40,6 +40,8 @@ INSTANCES = [
     ("dg_dmpf_dm", dict(Np=35, Nel=256)), ("dg_res", dict(Np=35, Nel=256)), ("dg_upf_u", dict(Np=35, Nel=256)),
     ("dg_dmpft_u", dict(Np=35, Nel=256)), ("dg_dmpft_res", dict(Np=35, Nel=256)),
     ("dg_tile", dict(Np=35, Nel=256)), ("dg_tile", dict(Np=20, Nel=256)),
+    ("dg_tc", dict(Np=20, Nel=256)), ("dg_tc", dict(Np=35, Nel=256)), ("dg_tc", dict(Np=35, Nel=256, A=0)),
+    ("dg_tc", dict(Np=84, Nel=256, A=0)), ("dg_tc", dict(Np=84, Nel=256)),
     ("fd_tile", dict(n=45)), ("fd_tile18", dict(n=45)), ("fd_direct", dict(n=45)),
     ("fd_tile_u", dict(n=45)), ("fd_tile_res", dict(n=45)), ("fd_direct_u", dict(n=45)),
     ("fd_direct_res", dict(n=45)), ("fd_tile18_u", dict(n=45)), ("fd_tile18_res", dict(n=45)),

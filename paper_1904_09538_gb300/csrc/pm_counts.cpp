@@ -629,6 +629,88 @@ pm_status counts_tc(const KP &kp, std::vector<pm_feature> &v) {
     return PM_OK;
 }
 
+// ---------------------------------------------------------------- DG on the tensor cores
+// Grid (G, P) of 320-thread work-groups (G = 3 / MS m-groups, P persistent
+// work-groups per m-group, the default resolved as the launch resolves it);
+// work-group (g, p) serves the tiles t = p, p + P, ... of 128 elements.
+//   threads i < NP8, per m of the group (MS of them) and chunk ac < 8 KA of
+//   the operator row: loads D[m, i, 4 ac + x] (i, 4 ac + x < Np), 4 adds
+//   (the head/remainder split), two 16-byte shared stores (head, remainder);
+//   threads below NR - MS NP8: two zero stores per chunk of the padding rows;
+//   one barrier;
+//   per tile and atom a (chunks c < CN(a) = 2 min(4, KS - 4a)):
+//     Np % 4 == 0: thread 256 copies the in-range part of the 128 x 32 box
+//       (counted per element, uniform); converter thread r = tid - 128 loads
+//       chunk c of its row from the staged atom (16-byte shared load);
+//     else: converter thread r loads the row's four elements of chunk c from
+//       global memory (k = 128 t + r < Nel, j < Np);
+//     converter: 4 adds per chunk; with A = 0 two 16-byte shared stores
+//       (head, remainder); with A = 1 the chunk goes to tensor memory;
+//     thread 288: per k step 3 MMAs of 128 x NR x 8 TF32 multiply-adds;
+//   per tile, epilogue threads tid < 128, per m: the store of the thread's
+//   row to the staging buffer (Np / 4 16-byte stores, or Np 4-byte stores
+//   when Np % 4 != 0), and thread 0 copies the block's rows x Np elements to
+//   res (counted per element, uniform);
+//   two barriers at the end.  The epilogue warps' named barriers among
+//   themselves (128 of the 320 threads) are not work-group barriers and are
+//   not counted: every thread passes the same three work-group barriers.
+// Shared-memory sites are given by their logical position (row, chunk) in
+// one ring stage or staging buffer: the swizzle permutes 16-byte chunks
+// within a 128-byte row and the ring rotates whole stages, which changes
+// neither counts nor footprints.
+pm_status counts_dgc(const KP &kp, std::vector<pm_feature> &v) {
+    const i64 Np = kp.i(0), Nel = kp.i(1);
+    const int A = dgc_resolve_a((int)Np, (int)kp.i(3));
+    const i64 P = dgc_resolve_p((int)Np, Nel, A, (int)kp.i(2));
+    const i64 MS = Np <= 40 ? 3 : 1, G = 3 / MS, NP8 = (Np + 7) / 8 * 8, NR = (MS * NP8 + 15) / 16 * 16;
+    const i64 KA = cdiv(Np, 32), KS = cdiv(Np, 8), CN0 = 2 * std::min<i64>(4, KS), PAD = NR - MS * NP8;
+    const bool tma = Np % 4 == 0;
+    const i64 T = cdiv(Nel, 128), Tf = Nel / 128, rl = Nel % 128;
+    const u64 sum_sg_rows = (u64)(4 * Tf + (rl ? cdiv(rl, 32) : 0));   // sum over tiles of ceil(rows / 32)
+    const u64 GP = (u64)(G * P), GT = (u64)(G * T), uNp = (u64)Np;
+    Out o(v);
+    auto site = [&](const char *tag, int mem, int dir, const char *dt, int ds, i64 l0, i64 g0, i64 g1, u64 wi, u64 sg,
+                    u64 foot) {
+        Site x{};
+        x.tag = tag; x.mem = mem; x.dir = dir; x.dtype = dt; x.dsize = ds;
+        x.nl = 1; x.l[0] = l0; x.ng = 2; x.g[0] = g0; x.g[1] = g1; x.loop = 1;
+        x.wi = wi; x.sg = sg; x.foot = foot;
+        o.site(x);
+    };
+    // operator staging
+    site("dgc-D", GL, LD, "float32", 4, Np, MS == 1 ? Np * Np : 0, 0, GP * (u64)MS * uNp * uNp,
+         GP * (u64)MS * uNp * (u64)cdiv(Np, 32), (u64)(3 * Np * Np));
+    const u64 bst = (u64)(8 * KA) * (u64)NR * GP;
+    const u64 bsg = (u64)(8 * KA) * GP * (u64)(MS * cdiv(NP8, 32) + cdiv(PAD, 32));
+    site("dgc-Bh", LO, ST, "float32x4", 16, 8 * KA, 0, 0, bst, bsg, (u64)(NR * 8 * KA));
+    site("dgc-Bl", LO, ST, "float32x4", 16, 8 * KA, 0, 0, bst, bsg, (u64)(NR * 8 * KA));
+    o.op(0, 0, 4 * GP * (u64)(MS * NP8 * 8 * KA), 4 * GP * (u64)(MS * cdiv(NP8, 32) * 8 * KA));
+    // u operand
+    const u64 uel = (u64)(G * Nel) * uNp;
+    if (tma) site("dgc-u", GL, LD, "float32", 4, 0, 0, 128 * Np, uel, uel, (u64)(Nel * Np));
+    else site("dgc-u", GL, LD, "float32", 4, Np, 0, 128 * Np, uel, (u64)G * uNp * sum_sg_rows, (u64)(Nel * Np));
+    const u64 cwi = GT * (u64)(2 * KS) * 128, csg = GT * (u64)(2 * KS) * 4;
+    if (tma) site("dgc-Ur", LO, LD, "float32x4", 16, 8, 0, 0, cwi, csg, (u64)(128 * CN0));
+    if (A == 0) {
+        site("dgc-Uh", LO, ST, "float32x4", 16, 8, 0, 0, cwi, csg, (u64)(128 * CN0));
+        site("dgc-Ul", LO, ST, "float32x4", 16, 8, 0, 0, cwi, csg, (u64)(128 * CN0));
+    }
+    o.op(0, 0, 4 * cwi, 4 * csg);
+    // epilogue
+    if (Np % 4 == 0)
+        site("dgc-O", LO, ST, "float32x4", 16, Np / 4, 0, 0, GT * (u64)MS * 128 * (uNp / 4),
+             GT * (u64)MS * 4 * (uNp / 4), (u64)(128 * Np / 4));
+    else
+        site("dgc-O", LO, ST, "float32", 4, Np, 0, 0, GT * (u64)MS * 128 * uNp, GT * (u64)MS * 4 * uNp,
+             (u64)(128 * Np));
+    const u64 rel = (u64)(3 * Nel) * uNp;
+    site("dgc-res", GL, ST, "float32", 4, 0, MS == 1 ? Nel * Np : 0, 128 * Np, rel, rel, rel);
+    const u64 mm = GT * (u64)KS * 3 * 128 * (u64)NR * 8;
+    v.push_back(op_rec("tfloat32", "madd", mm, mm));
+    o.finish(3, GP);
+    return PM_OK;
+}
+
 // ---------------------------------------------------------------- stencil tile family
 // Work-group (BX/4) x BY, input pitch P = n + 4; work-item (0,0) copies the
 // (BY+2) x (BX+4) box element by element (uniform: per sub-group); every
@@ -886,6 +968,7 @@ pm_status counts(const KP &kp, std::vector<pm_feature> &out) {
     case FAM_TC: return counts_tc(kp, out);
     case FAM_FDB: return counts_fdb(kp, out);
     case FAM_DGT: return counts_dgt(kp, out);
+    case FAM_DGC: return counts_dgc(kp, out);
     }
     return fail(PM_EINVAL, "unknown family");
 }

@@ -136,10 +136,10 @@ def studies(reduced=False):
 
 
 def sweep_studies(reduced=False):
-    """The cross-variant sweep: 10 modeled variants (prefetching fp32 matmul,
+    """The cross-variant sweep: 11 modeled variants (prefetching fp32 matmul,
     BF16 tensor-core matmul with 128 x 256 and 256 x 256 tiles, DG noPF /
-    uPF / dmPF / dmPF-T with 16x16 work-groups and the DG tile form, stencil
-    16x16 tile and direct) at ~30 sizes each.  Every third size is held out; each variant's
+    uPF / dmPF / dmPF-T with 16x16 work-groups, the DG tile form and its
+    tensor-core form, stencil 16x16 tile and direct) at ~30 sizes each.  Every third size is held out; each variant's
     model is calibrated on the microbenchmarks (plus its computation's twins)
     and the variant's own other sizes -- the paper's "few extra on-line
     calibration runs" -- and predicts the held-out sizes.  A tenth study
@@ -159,10 +159,18 @@ def sweep_studies(reduced=False):
     nels = sorted({int(round(2 ** (14 + 4 * i / 7.0) / 32)) * 32 for i in range(8)})
     dg_sizes = [dict(Np=Np, Nel=Nel, L0=16, L1=16) for Np in (20, 35, 56, 84) for Nel in nels]
     tc_sizes = [{"n": n} for n in range(1024, 8192 + 1, 256)]
+    # the tensor-core DG form: no microbenchmark carries its TF32 multiply-adds,
+    # its TMA-box u loads or its bulk res stores, so (as for the tensor-core
+    # matmul) its own sizes calibrate those costs; the empty kernels fix the
+    # launch and group terms
+    dgc_expr = nonlinear([tagged("dgc-u", "dcu"), tagged("dgc-res", "dcr")],
+                         overhead="p_launch * f_sync_kernel_launch + p_group * f_thread_groups",
+                         onchip="p_tf * f_op_tfloat32_madd + p_lm4 * f_mem_access_local_float32x4")
     plan = [("mm_pf", "matmul", None, [{"n": n} for n in range(512, 4096 + 1, 128)]),
             ("mm_tc", None, tc_expr, tc_sizes), ("mm_tc256", None, tc_expr, tc_sizes)]
     plan += [(k, "dg_16x16", None, dg_sizes) for k in ("dg_nopf", "dg_upf", "dg_dmpf", "dg_dmpft")]
     plan += [("dg_tile", "dg_16x16", None, [dict(Np=Np, Nel=Nel) for Np in (20, 35, 56, 84) for Nel in nels])]
+    plan += [("dg_tc", "launch", dgc_expr, [dict(Np=Np, Nel=Nel) for Np in (20, 35, 56, 84) for Nel in nels])]
     plan += [(k, "fd", None, [{"n": int(round(1024 * 2 ** (i / 7.0)))} for i in range(29)])
              for k in ("fd_tile", "fd_direct")]
     if reduced:
@@ -177,7 +185,10 @@ def sweep_studies(reduced=False):
     for k, parent, expr, sizes in plan:
         fit = [(k, p) for i, p in enumerate(sizes) if i % 3 != 2]
         held = [(k, p) for i, p in enumerate(sizes) if i % 3 == 2]
-        measure = (base[parent]["measure"] if parent else common_measurements()) + fit
+        if parent == "launch":
+            measure = generate(["launch"]) + fit
+        else:
+            measure = (base[parent]["measure"] if parent else common_measurements()) + fit
         out.append(dict(name="sweep_" + k, expr=expr or base[parent]["expr"], measure=measure, modeled=held))
     # both tensor-core tile shapes in one calibration: their bf16 loads per
     # multiply-add differ (3/256 and 2/256), which separates the load and

@@ -145,6 +145,7 @@ GENERATORS = [
     Generator("dg_dmpft", ["dg", "modeled"], {"Np": [20, 35, 56, 84], "Nel": POW(14, 18), "L0": [16, 32]},
               lambda p: dict(p, L1=256 // p["L0"])),
     Generator("dg_tile", ["dg", "modeled", "dg_tile"], {"Np": [20, 35, 56, 84], "Nel": POW(14, 18)}),
+    Generator("dg_tc", ["dg", "modeled", "dg_tc"], {"Np": [20, 35, 56, 84], "Nel": POW(14, 18)}),
     Generator("fd_tile", ["finite_diff", "modeled"], {"n": POW(10, 14)}),
     Generator("fd_tile18", ["finite_diff", "modeled"], {"n": POW(10, 14)}),
     Generator("fd_direct", ["finite_diff", "modeled"], {"n": POW(10, 14)}),

@@ -200,3 +200,14 @@ def test_smem2d(R, T, G):
                                     (96, 136)])
 def test_dg_tile(Np, Nel):
     compare("dg_tile", Np=Np, Nel=Nel)
+
+
+# the tensor-core DG: both operand forms, the TMA (Np % 4 == 0) and the
+# direct-load paths, ragged last tiles, persistent grids smaller and larger
+# than the tile count, the default grid
+@pytest.mark.parametrize("Np,Nel,P,A", [(20, 260, 0, -1), (20, 132, 0, 1), (4, 8, 0, -1), (10, 300, 0, 0),
+                                        (10, 300, 0, 1), (35, 256, 0, 0), (35, 260, 0, -1), (56, 132, 0, 0),
+                                        (56, 516, 0, -1), (84, 388, 2, -1), (84, 132, 0, 0), (20, 1028, 3, 0),
+                                        (35, 644, 2, 0), (84, 260, 5, 1), (56, 4, 0, 1)])
+def test_dg_tc(Np, Nel, P, A):
+    compare("dg_tc", Np=Np, Nel=Nel, P=P, A=A)

@@ -68,6 +68,9 @@ def test_counts_cap_protocol():
     ("mm_tc256", dict(n=384)), ("mm_tc256", dict(n=32768 + 256)),
     ("dg_tile", dict(Np=20, Nel=130)), ("dg_tile", dict(Np=97, Nel=128)), ("dg_tile", dict(Np=20, Nel=65536 * 128)),
     ("dg_tile", dict(Np=0, Nel=128)),
+    ("dg_tc", dict(Np=21, Nel=128)), ("dg_tc", dict(Np=20, Nel=130)), ("dg_tc", dict(Np=20, Nel=0)),
+    ("dg_tc", dict(Np=84, Nel=(1 << 24) + 4)), ("dg_tc", dict(Np=20, Nel=128, P=-1)),
+    ("dg_tc", dict(Np=20, Nel=128, P=4097)), ("dg_tc", dict(Np=20, Nel=128, A=2)),
     ("fd_block", dict(n=100, BX=64, BY=8)), ("fd_block", dict(n=256, BX=64, BY=8, V=2)),
     ("fd_tile", dict(n=0)), ("dg_upf", dict(Np=20, Nel=32, L0=32, L1=8)), ("dg_nopf", dict(Np=0, Nel=32)),
     ("smem2d", dict(R=8, T=17, G=1)), ("stream", dict(N=1000)), ("stream", dict(N=1 << 20, s=3)),
@@ -84,6 +87,19 @@ def test_missing_and_unknown_parameters_rejected():
         pm.counts("mm_pf", n=64, bogus=1)
     with pytest.raises(pm.PMError):
         pm.counts("mm_pf", n=64.5)          # integer parameter
+
+
+def test_dg_tc_counts_at_largest_size():
+    # 2^24 elements, Np = 84 (one m per work-group, three m-groups): the
+    # closed forms do not overflow; the default grid is 50 work-groups per
+    # m-group (one wave of 152 SMs, one per SM)
+    Np, Nel = 84, 1 << 24
+    r = pm.counts("dg_tc", Np=Np, Nel=Nel)
+    T = Nel // 128
+    assert rec(r, "f_op_tfloat32_madd")["count"] == 3 * T * 11 * 3 * 128 * 96 * 8
+    assert rec(r, "f_mem_access_tag:dgc-res")["count"] == 3 * Nel * Np
+    assert rec(r, "f_mem_access_tag:dgc-u")["count"] == 3 * Nel * Np
+    assert rec(r, "f_thread_groups")["count"] == 3 * 50
 
 
 def test_dg_tile_counts_at_largest_size():

@@ -372,6 +372,39 @@ def test_tensor_core_closed_forms(kernel, R, n):
     assert single(fs, "groups") == (n // 256) * (n // R) and single(fs, "sync") == 3
 
 
+@pytest.mark.parametrize("Np,Nel,P,A", [(20, 260, 0, 0), (35, 256, 2, 1), (84, 388, 0, 1), (10, 132, 3, 0),
+                                        (56, 128, 0, 0)])
+def test_dg_tc_closed_forms(Np, Nel, P, A):
+    # the tensor-core DG: every u element reaches each m-group once (TMA box
+    # element by element, uniform, when Np % 4 == 0, else per work-item),
+    # every result stored once (bulk copy, uniform); the multiply-adds are
+    # three TF32 passes over the padded product 128 x NR x 8 KS per tile
+    # (NR = 3 NP8 or NP8 rounded up to 16), at least three times the useful
+    # 3 Nel Np^2; each operator element is loaded once per work-group; all
+    # work-items pass the same three work-group barriers
+    fs = features("dg_tc", Np=Np, Nel=Nel, P=P, A=A)
+    MS = 3 if Np <= 40 else 1
+    G, T, NP8, KS = 3 // MS, -(-Nel // 128), -(-Np // 8) * 8, -(-Np // 8)
+    NR = -(-(MS * NP8) // 16) * 16
+    R = 2 if (A == 0 and Np <= 20) else 1
+    Pr = P if P else min(T, 152 * R // G)
+    assert single(fs, "groups") == G * Pr and single(fs, "sync") == 3
+    mm = op(fs, "tfloat32", "madd", wi=True)
+    assert mm == G * T * KS * 3 * 128 * NR * 8 >= 3 * (3 * Nel * Np * Np)
+    uu = by_tag(fs, "dgc-u")
+    assert uu["count_wi"] == G * Nel * Np and uu["footprint"] == Nel * Np and uu["gstr"] == (0, 128 * Np)
+    assert uu["lstr"] == ((0,) if Np % 4 == 0 else (Np,))
+    r = by_tag(fs, "dgc-res")
+    assert r["count_wi"] == r["count"] == r["footprint"] == 3 * Nel * Np and r["lstr"] == (0,)
+    assert r["gstr"] == ((Nel * Np if MS == 1 else 0), 128 * Np)
+    d = by_tag(fs, "dgc-D")
+    assert d["count_wi"] == G * Pr * MS * Np * Np and d["footprint"] == 3 * Np * Np
+    # the split: one subtraction per operator and per converted u element
+    adds = op(fs, "float32", "add", wi=True)
+    assert adds == 4 * G * Pr * MS * NP8 * 8 * (-(-Np // 32)) + 4 * G * T * 2 * KS * 128
+    assert any(f["kind"] == "mem" and f["tag"] == "dgc-Uh" for f in fs) == (A == 0)
+
+
 @pytest.mark.parametrize("Np,Nel", [(20, 132), (35, 256), (84, 128), (17, 4), (56, 256)])
 def test_dg_tile_closed_forms(Np, Nel):
     # the DG product, one work-group per (m, 128 elements), NB = ceil(Np/16)
