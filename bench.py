@@ -42,6 +42,7 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-fit-bench", action="store_true")
     ap.add_argument("--no-accuracy", action="store_true", help="skip the per-variant held-out accuracy leg")
+    ap.add_argument("--no-tiles", action="store_true", help="skip the modeled computations' GB300 kernels leg")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--filter", default="suite", help="comma-separated suite filter tags")
     ap.add_argument("--dump", default=None, help="write per-variant timings of the last step (JSON)")
@@ -336,6 +337,8 @@ def run_ours(args):
             orc = oracle_fit_rate()
             line["fit"]["max_param_rel_err_vs_oracle"] = fit_vs_oracle(gpu_params, orc.pop("_params"))
             line["fit"]["oracle_cpu"] = orc
+    if not args.no_tiles:
+        line["tile_kernels"] = tile_kernels_leg(pm, torch, dev, peaks, clk.get("sm_mhz"))
     if not args.no_accuracy:
         line["accuracy"] = accuracy_leg()
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -704,6 +707,87 @@ def fit_throughput(pm, torch, dev):
             "statuses_plain": {str(s): [r["status"] for _, r in plain].count(s)
                                for s in set(r["status"] for _, r in plain)},
             "_params": {"batched": batched, "plain": [pp for pp, _ in plain]}}
+
+
+def tile_kernels_leg(pm, torch, dev, peaks, sm_mhz, trials=10):
+    """The modeled computations' GB300 kernels against their rooflines, each
+    timed alone (pm_run, L2 flushed before every trial, median of `trials`;
+    every footprint is larger than L2): the DG derivative on the tensor cores
+    (dg_tc) and in its SIMT tile form (dg_tile) at Np = 20, 35, 56, 84 and
+    Nel = 2^20, the stencil's best tile shape at n = 16384, the 256 x 256
+    BF16 tensor-core matmul at n = 8192 and the best SIMT matmul tile at
+    n = 7680.  Bounds: HBM = the measured copy rate for every algorithmic
+    byte (DG: 4 (4 Nel Np + 3 Np^2); stencil: 4 ((n + 2)(n + 4) + n^2));
+    BF16 = the measured cuBLAS burst; TF32 = that x the nominal TF32 / BF16
+    ratio 1.1 / 2.25, for the multiply-adds dg_tc issues (three passes over
+    the padded product, from its counts); FP32 = SMs x 128 lanes x 2 x the
+    sampled SM clock.  frac = the larger of the kernel's bound times over
+    its median time."""
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    clk = (sm_mhz or 2070.0) * 1e6
+    hbm = peaks["hbm_gbs"] * 1e9
+    bf16 = peaks.get("bf16_tflops", 1900.0) * 1e12
+    tf32 = bf16 * 1.1 / 2.25
+    fp32 = sms * 128 * 2 * clk
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(5)
+
+    def buffers(kernel, p):
+        out = []
+        for b in pm.kernel_buffers(kernel, **p):
+            n = int(b["elems"])
+            if getattr(b["dtype"], "__name__", "") == "uint16":   # bf16 bit patterns
+                x = (torch.rand(n, device=dev, generator=gen) * 2 - 1).to(torch.bfloat16).view(torch.int16)
+            else:
+                x = torch.rand(n, device=dev, generator=gen) * 2 - 1
+            out.append(x)
+        return out
+
+    def timed(kernel, p):
+        bufs = buffers(kernel, p)
+        tm = pm.run(kernel, bufs, warmup=3, trials=trials, flush_l2=True, **p)
+        del bufs
+        return tm["median_ms"] * 1e-3
+
+    out = {}
+    nel = 1 << 20
+    for np_ in (20, 35, 56, 84):
+        bts = 4.0 * (4 * nel * np_ + 3 * np_ * np_)
+        fl = 6.0 * nel * np_ * np_
+        for k in ("dg_tc", "dg_tile"):
+            p = dict(Np=np_, Nel=nel)
+            s = timed(k, p)
+            rec = {"ms": round(s * 1e3, 4), "GB/s": round(bts / s / 1e9, 1), "TFLOP/s": round(fl / s / 1e12, 2),
+                   "hbm_frac": round(bts / s / hbm, 3)}
+            if k == "dg_tc":
+                mm = sum(r["count_wi"] for r in pm.counts(k, **p) if r["kind"] == "op" and r["dtype"] == "tfloat32")
+                t_tc = 2.0 * mm / tf32
+                rec["tf32_bound_ms"] = round(t_tc * 1e3, 4)
+                rec["bound"] = "hbm" if bts / hbm >= t_tc else "tf32"
+                rec["frac"] = round(max(bts / hbm, t_tc) / s, 3)
+            else:
+                rec["fp32_frac"] = round(fl / s / fp32, 3)
+                rec["bound"] = "hbm" if bts / hbm >= fl / fp32 else "fp32"
+                rec["frac"] = round(max(bts / hbm, fl / fp32) / s, 3)
+            out["%s_Np%d" % (k, np_)] = rec
+    n = 16384
+    p = dict(n=n, BX=32, BY=16, V=8)
+    s = timed("fd_block", p)
+    bts = 4.0 * ((n + 2) * (n + 4) + n * n)
+    out["fd_block_32x16_v8"] = {"ms": round(s * 1e3, 4), "GB/s": round(bts / s / 1e9, 1), "bound": "hbm",
+                                "frac": round(bts / s / hbm, 3)}
+    n = 8192
+    s = timed("mm_tc256", dict(n=n))
+    out["mm_tc256"] = {"ms": round(s * 1e3, 4), "TFLOP/s": round(2.0 * n ** 3 / s / 1e12, 1), "bound": "bf16",
+                       "frac": round(2.0 * n ** 3 / s / bf16, 3)}
+    n = 7680
+    p = dict(n=n, BM=128, BN=128, BK=32)
+    s = timed("mm_simt", p)
+    out["mm_simt_128x128x32"] = {"ms": round(s * 1e3, 4), "TFLOP/s": round(2.0 * n ** 3 / s / 1e12, 2),
+                                 "bound": "fp32", "frac": round(2.0 * n ** 3 / s / fp32, 3)}
+    out["peaks"] = {"hbm_gbs": peaks["hbm_gbs"], "bf16_tflops": peaks.get("bf16_tflops"),
+                    "tf32_tflops": round(tf32 / 1e12, 1), "fp32_tflops": round(fp32 / 1e12, 2), "sm_mhz": sm_mhz}
+    return out
 
 
 def accuracy_leg(trials=3):
