@@ -186,14 +186,6 @@ __device__ __forceinline__ void split4(float4 v, float4 &h, float4 &l) {
     h = make_float4(tf32_head(v.x), tf32_head(v.y), tf32_head(v.z), tf32_head(v.w));
     l = make_float4(__fsub_rn(v.x, h.x), __fsub_rn(v.y, h.y), __fsub_rn(v.z, h.z), __fsub_rn(v.w, h.w));
 }
-// 0.0f the compiler cannot see through: the padding elements of a chunk go
-// through the head/remainder split like the others (one subtraction each),
-// so the executed adds are the counted ones whatever the unrolling
-__device__ __forceinline__ float opaque_zero() {
-    uint32_t z;
-    asm volatile("mov.b32 %0, 0;" : "=r"(z));
-    return __uint_as_float(z);
-}
 // physical byte offset of logical 16-byte chunk c of row r in a swizzled atom
 __device__ __forceinline__ uint32_t swz(int r, int c) { return (uint32_t)(r * 128 + ((c ^ (r & 7)) << 4)); }
 
@@ -260,7 +252,6 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
     }
     // operator rows: thread i stages row mm * NP8 + i of each of the CTA's m,
     // then the padding rows MS * NP8 .. NR - 1 (zero)
-    const float zero = opaque_zero();
     if (threadIdx.x < NP8) {
         const int i = threadIdx.x;
         for (int mm = 0; mm < MS; mm++) {
@@ -269,10 +260,10 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
             for (int ac = 0; ac < 8 * KA; ac++) {
                 const int j0 = 4 * ac;
                 float4 v;
-                v.x = (i < NP && j0 < NP) ? __ldg(drow + j0) : zero;
-                v.y = (i < NP && j0 + 1 < NP) ? __ldg(drow + j0 + 1) : zero;
-                v.z = (i < NP && j0 + 2 < NP) ? __ldg(drow + j0 + 2) : zero;
-                v.w = (i < NP && j0 + 3 < NP) ? __ldg(drow + j0 + 3) : zero;
+                v.x = (i < NP && j0 < NP) ? __ldg(drow + j0) : 0.0f;
+                v.y = (i < NP && j0 + 1 < NP) ? __ldg(drow + j0 + 1) : 0.0f;
+                v.z = (i < NP && j0 + 2 < NP) ? __ldg(drow + j0 + 2) : 0.0f;
+                v.w = (i < NP && j0 + 3 < NP) ? __ldg(drow + j0 + 3) : 0.0f;
                 float4 h, l;
                 split4(v, h, l);
                 const uint32_t off = (uint32_t)((ac >> 3) * NR * 128) + swz(n, ac & 7);
@@ -376,10 +367,10 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
                         const int j0 = 32 * a + 4 * c;
                         const float *src = u + k * NP + j0;
                         const bool in = k < Nel;
-                        v.x = (in && j0 < NP) ? __ldg(src) : zero;
-                        v.y = (in && j0 + 1 < NP) ? __ldg(src + 1) : zero;
-                        v.z = (in && j0 + 2 < NP) ? __ldg(src + 2) : zero;
-                        v.w = (in && j0 + 3 < NP) ? __ldg(src + 3) : zero;
+                        v.x = (in && j0 < NP) ? __ldg(src) : 0.0f;
+                        v.y = (in && j0 + 1 < NP) ? __ldg(src + 1) : 0.0f;
+                        v.z = (in && j0 + 2 < NP) ? __ldg(src + 2) : 0.0f;
+                        v.w = (in && j0 + 3 < NP) ? __ldg(src + 3) : 0.0f;
                     }
                     split4(v, h[c], l[c]);
                     if (!TS) {
