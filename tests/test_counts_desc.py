@@ -1,6 +1,7 @@
 """pm_counts_desc: features of kernels given as loop-nest descriptions.
-The descriptions in tests/descriptors/ restate four registry kernels from
-their definitions; their counts must equal the library's closed forms record
+The descriptions in tests/descriptors/ restate eleven registry kernels (the
+three modeled computations, two work-removed twins, the arithmetic, local
+memory and stream microbenchmarks) from their definitions; their counts must equal the library's closed forms record
 for record -- by enumeration at small sizes, by quasi-polynomial
 extrapolation at large ones -- and the oracle's brute force.  CPU only."""
 import os
@@ -64,10 +65,44 @@ def test_stream_two_parameters(s):
          pm.counts("stream", N=1 << 26, s=s, L=2))
 
 
+# the other restated registry kernels: (description, its parameters, registry
+# kernel, its parameters) at small sizes, and at full size with the period and
+# degree bound of the interpolated parameter derived from the description
+RESTATED = [
+    ("mm_nopf", dict(n=48), "mm_nopf", {}),
+    ("mm_pf_a", dict(n=48), "mm_pf_a", {}),
+    ("mm_pf_b", dict(n=64), "mm_pf_b", {}),
+    ("fd_direct", dict(n=45), "fd_direct", {}),
+    ("fd_tile18", dict(n=45), "fd_tile18", {}),
+    ("fma_madd", dict(F=1024, G=3), "fma", dict(op=2, dtype=0)),
+    ("smem_sync", dict(R=64, G=2), "smem", dict(sync=1)),
+]
+
+
+@pytest.mark.parametrize("name,params,kernel,kparams", RESTATED)
+def test_restated_kernels_enumerated(name, params, kernel, kparams):
+    same(pm.counts_desc(desc(name), **params), pm.counts(kernel, **dict(kparams, **params)))
+
+
+@pytest.mark.parametrize("name,param,params,kernel,kparams,want", [
+    ("mm_nopf", "n", dict(n=4096), "mm_nopf", {}, (16, 3)),
+    ("mm_pf_a", "n", dict(n=4096), "mm_pf_a", {}, (16, 3)),
+    ("fd_direct", "n", dict(n=16383), "fd_direct", {}, (16, 2)),
+    ("fd_tile18", "n", dict(n=16384), "fd_tile18", {}, (16, 2)),
+    ("fma_madd", "F", dict(F=65536, G=8), "fma", dict(op=2, dtype=0), (32, 1)),
+    ("smem_sync", "R", dict(R=16384, G=608), "smem", dict(sync=1), (4, 1)),
+])
+def test_restated_kernels_extrapolated(name, param, params, kernel, kparams, want):
+    assert pm.counts_desc_interp(desc(name), param, **params) == want
+    same(pm.counts_desc(desc(name), interp={param: None}, **params), pm.counts(kernel, **dict(kparams, **params)))
+
+
 def test_matches_oracle_brute_force():
     same(pm.counts_desc(desc("mm_pf"), n=48), ofeatures("mm_pf", n=48))
     same(pm.counts_desc(desc("fd_tile"), n=29), ofeatures("fd_tile", n=29))
     same(pm.counts_desc(desc("dg_nopf"), Np=35, Nel=32), ofeatures("dg_nopf", Np=35, Nel=32, L0=16, L1=16))
+    same(pm.counts_desc(desc("fd_tile18"), n=29), ofeatures("fd_tile18", n=29))
+    same(pm.counts_desc(desc("smem_sync"), R=16, G=2), ofeatures("smem", R=16, sync=1, G=2))
 
 
 def test_model_rows_from_descriptions():
