@@ -6,7 +6,9 @@
 //     barrier;
 //     A tile, rows lid1 + L1 r (r < 8), vector columns lid0 + L0 q (< BK/4),
 //       one 16-byte load each, stored transposed (k-major, rows padded to
-//       BM + 4 floats) as four floats;
+//       BM + 4 floats) as four floats, the row's quad of four XOR-ed with
+//       the k chunk (bits 0-2) so that a warp's transposed stores are
+//       conflict-free (the counts give the logical position k, row);
 //     B tile, rows lid1 + L1 r (< BK), vector columns lid0 + L0 q (q < 2),
 //       one 16-byte load and one 16-byte shared store each;
 //     barrier;
@@ -41,7 +43,7 @@ __global__ void __launch_bounds__((BM / 8) * (BN / 8)) k_mm_simt(const float4 *_
                                                               float4 *__restrict__ C4, int n) {
     constexpr int L0 = BN / 8, L1 = BM / 8, KC = BK / 4, NC = BN / 4;
     constexpr int QA = (KC + L0 - 1) / L0, RB = (BK + L1 - 1) / L1;
-    constexpr int BMP = BM + 4;       // padded row: a warp's 8 transposed-store columns hit 4 banks, not 1
+    constexpr int BMP = BM + 4;       // padded row (16-byte aligned rows of the transposed tile)
     extern __shared__ __align__(16) float smem[];
     float *As = smem;                 // [BK][BMP]
     float *Bs = smem + BK * BMP;      // [BK][BN]
@@ -66,10 +68,13 @@ __global__ void __launch_bounds__((BM / 8) * (BN / 8)) k_mm_simt(const float4 *_
                 const int c = l0 + L0 * q;
                 if (c < KC) {
                     const float4 v = A4[n4 * (arow0 + row) + (size_t)KC * kt + c];
-                    As[(4 * c + 0) * BMP + row] = v.x;
-                    As[(4 * c + 1) * BMP + row] = v.y;
-                    As[(4 * c + 2) * BMP + row] = v.z;
-                    As[(4 * c + 3) * BMP + row] = v.w;
+                    // row quad XOR-swizzled by the k chunk: a warp's transposed
+                    // stores (k rows 4c + e, c over the lanes) fall in distinct banks
+                    const int pr = (((row >> 2) ^ (c & 7)) << 2) | (row & 3);
+                    As[(4 * c + 0) * BMP + pr] = v.x;
+                    As[(4 * c + 1) * BMP + pr] = v.y;
+                    As[(4 * c + 2) * BMP + pr] = v.z;
+                    As[(4 * c + 3) * BMP + pr] = v.w;
                 }
             }
         }
@@ -88,8 +93,9 @@ __global__ void __launch_bounds__((BM / 8) * (BN / 8)) k_mm_simt(const float4 *_
         __syncthreads();
 #pragma unroll 4
         for (int kk = 0; kk < BK; kk++) {
-            const float4 a0 = reinterpret_cast<const float4 *>(As)[kk * (BMP / 4) + 2 * l1];
-            const float4 a1 = reinterpret_cast<const float4 *>(As)[kk * (BMP / 4) + 2 * l1 + 1];
+            const int sw = (kk >> 2) & 7;   // the swizzle of k row kk
+            const float4 a0 = reinterpret_cast<const float4 *>(As)[kk * (BMP / 4) + ((2 * l1) ^ sw)];
+            const float4 a1 = reinterpret_cast<const float4 *>(As)[kk * (BMP / 4) + ((2 * l1 + 1) ^ sw)];
             // vectors lid0 and L0 + lid0: consecutive threads read consecutive 16-byte words
             const float4 b0 = reinterpret_cast<const float4 *>(Bs)[kk * NC + l0];
             const float4 b1 = reinterpret_cast<const float4 *>(Bs)[kk * NC + L0 + l0];
