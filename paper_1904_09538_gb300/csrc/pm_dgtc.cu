@@ -308,6 +308,9 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
                 if (uu > 0 && !dgc_wait(&S->tempty[b], (uint32_t)((uu - 1) & 1))) break;
                 tc_after();
                 const uint32_t d = tmem + (uint32_t)(b * C::ACC);
+                // unrolled: every atom's k steps and operand offsets are
+                // compile-time, so the MMAs issue back to back
+#pragma unroll
                 for (int a = 0; a < KA; a++, it++) {
                     const int s = TS ? it % SA : it % ST, r = TS ? it / SA : it / ST;
                     if (!dgc_wait(&S->ready[s], (uint32_t)(r & 1))) { ok = false; break; }
@@ -348,6 +351,7 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
         for (int t = p; t < T; t += P) {
             bool ok = true;
             const long long k = 128LL * t + r;
+#pragma unroll
             for (int a = 0; a < KA; a++, it++) {
                 const int CN = 2 * min(4, KS - 4 * a);   // chunks of this atom the MMA reads
                 const int s = it % ST, rs = it / ST;
