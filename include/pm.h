@@ -82,10 +82,11 @@ typedef struct {
  * tensor-core form "dg_tc" (parameters Np, one of the tetrahedral node
  * counts 4, 10, 20, 35, 56, 84, Nel a multiple of 4 (<= 2^24), A the
  * place of the u operand, 0 = shared memory, 1 = tensor memory, -1
- * (default) = 1 for Np > 20 else 0, and P the persistent CTAs per m-group,
- * 0 (default) = min(ceil(Nel / 128), 152 R / G), one wave of a GB300's 152
- * SMs with R = 2 CTAs per SM for A = 0 and Np <= 20, else 1, and G = 1
- * m-group for Np <= 40 (the three m in one CTA), else 3; the grid is (G, P);
+ * (default) = 1 for Np = 35 and 84 (20 < Np <= 40 or Np > 64) else 0, and
+ * P the persistent CTAs per m-group, 0 (default) = min(ceil(Nel / 128),
+ * 152 R / G), one wave of a GB300's 152 SMs with R = 2 CTAs per SM for
+ * A = 0 and Np <= 20, else 1, and G = 1 m-group (the three m in one CTA)
+ * for Np <= 40 and, with A = 0, for Np <= 64, else 3; the grid is (G, P);
  * buffers as for dg_nopf): the product of each
  * 128-element tile with the stacked operator rows on tcgen05.mma kind::tf32,
  * every operand split into a TF32 head and its FP32 remainder and three

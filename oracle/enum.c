@@ -1349,8 +1349,9 @@ static int setup_dgt(ctx *c) {
  * sum_j D[m, i, j] u[k, j], TF32 head/remainder split in three passes.
  * P = {Np, Nel, P, A}.  Np in {4, 10, 20, 35, 56, 84}; Nel a multiple of 4.
  * The kernel's definition of its launch:
- *   MS = 3 m per work-group for Np <= 40, else 1; G = 3 / MS m-groups;
- *   A < 0 means A = (Np > 20); R = 2 work-groups per SM for A = 0 and
+ *   A < 0 means A = 1 for 20 < Np <= 40 and for Np > 64, else 0;
+ *   MS = 3 m per work-group for Np <= 40 and, with A = 0, for Np <= 64,
+ *   else 1; G = 3 / MS m-groups; R = 2 work-groups per SM for A = 0 and
  *   Np <= 20, else 1; P = 0 means min(T, 152 R / G), T = ceil(Nel / 128);
  *   grid (G, P), work-group of 320 work-items (1-D).
  * NP8 = Np rounded up to 8, NR = MS NP8 rounded up to 16 (MMA N), KA =
@@ -1384,7 +1385,7 @@ static int setup_dgt(ctx *c) {
  * stage or staging buffer.
  * ====================================================================== */
 #define DC_NP(c) ((c)->P[0])
-#define DC_MS(c) (DC_NP(c) <= 40 ? 3 : 1)
+#define DC_MS(c) ((c)->D[1])
 #define DC_NP8(c) ((DC_NP(c) + 7) / 8 * 8)
 #define DC_NR(c) ((DC_MS(c) * DC_NP8(c) + 15) / 16 * 16)
 #define DC_KA(c) (cdiv(DC_NP(c), 32))
@@ -1480,7 +1481,8 @@ static int setup_dgc(ctx *c) {
     long long Np = DC_NP(c), Nel = c->P[1], P = c->P[2], A = c->P[3];
     if (Np != 4 && Np != 10 && Np != 20 && Np != 35 && Np != 56 && Np != 84) return -1;
     if (Nel < 4 || Nel % 4 || P < 0 || A < -1 || A > 1) return -1;
-    if (A < 0) A = Np > 20;
+    if (A < 0) A = (Np > 20 && Np <= 40) || Np > 64;
+    c->D[1] = (Np <= 40 || (A == 0 && Np <= 64)) ? 3 : 1;
     const long long MS = DC_MS(c), G = 3 / MS, R = (A == 0 && Np <= 20) ? 2 : 1, T = cdiv(Nel, 128);
     if (P == 0) P = T < 152 * R / G ? T : 152 * R / G;
     c->D[0] = P;

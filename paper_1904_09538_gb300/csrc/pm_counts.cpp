@@ -630,7 +630,8 @@ pm_status counts_tc(const KP &kp, std::vector<pm_feature> &v) {
 }
 
 // ---------------------------------------------------------------- DG on the tensor cores
-// Grid (G, P) of 320-thread work-groups (G = 3 / MS m-groups, P persistent
+// Grid (G, P) of 320-thread work-groups (G = 3 / MS m-groups: MS = 3 m per
+// work-group for Np <= 40, and for Np <= 64 with A = 0; P persistent
 // work-groups per m-group, the default resolved as the launch resolves it);
 // work-group (g, p) serves the tiles t = p, p + P, ... of 128 elements.
 //   threads i < NP8, per m of the group (MS of them) and chunk ac < 8 KA of
@@ -662,7 +663,7 @@ pm_status counts_dgc(const KP &kp, std::vector<pm_feature> &v) {
     const i64 Np = kp.i(0), Nel = kp.i(1);
     const int A = dgc_resolve_a((int)Np, (int)kp.i(3));
     const i64 P = dgc_resolve_p((int)Np, Nel, A, (int)kp.i(2));
-    const i64 MS = Np <= 40 ? 3 : 1, G = 3 / MS, NP8 = (Np + 7) / 8 * 8, NR = (MS * NP8 + 15) / 16 * 16;
+    const i64 MS = dgc_geometry((int)Np, A).ms, G = 3 / MS, NP8 = (Np + 7) / 8 * 8, NR = (MS * NP8 + 15) / 16 * 16;
     const i64 KA = cdiv(Np, 32), KS = cdiv(Np, 8), CN0 = 2 * std::min<i64>(4, KS), PAD = NR - MS * NP8;
     const bool tma = Np % 4 == 0;
     const i64 T = cdiv(Nel, 128), Tf = Nel / 128, rl = Nel % 128;

@@ -1,8 +1,9 @@
 // DG derivative on the 5th-generation tensor cores ("dg_tc"):
 //   res[m, k, i] = sum_j D[m, i, j] u[k, j]      (Section "DG")
 // as one product per 128-element tile: C (128 x NR) = U (128 x Np) Ds^T,
-// Ds the operator rows stacked over the CTA's m (MS = 3 for Np <= 40, else
-// one m per CTA), on tcgen05.mma kind::tf32 with FP32 accumulation in TMEM.
+// Ds the operator rows stacked over the CTA's m (MS = 3 for Np <= 40, and
+// for Np <= 64 when the u operand is in shared memory; else one m per CTA),
+// on tcgen05.mma kind::tf32 with FP32 accumulation in TMEM.
 //
 // FP32 accuracy from TF32 operands: every operand value x is split into a
 // head x_h (x rounded to nearest at TF32's 10 mantissa bits, low 13 bits
@@ -83,7 +84,10 @@ __host__ __device__ constexpr int pow2_cols(int c) { return c <= 32 ? 32 : c <= 
 
 template <int NP, bool TS>
 struct Dgc {
-    static constexpr DgcShape S = dgc_shape0(NP);
+    // the shared-memory form holds the three m's operator rows for Np <= 64
+    // (N = 3 NP8 <= 176), the tensor-memory form (accumulators 128 columns
+    // apart) only for Np <= 40
+    static constexpr DgcShape S = (!TS && NP > 40 && NP <= 64) ? DgcShape{3, 1, 2, 2} : dgc_shape0(NP);
     static constexpr int MS = S.ms, G = 3 / S.ms;
     static constexpr int R = TS ? 1 : S.r;                          // CTAs per SM
     static constexpr int ST = TS ? (NP % 4 == 0 ? 4 : 1) : S.st;    // shared-memory stages
@@ -509,12 +513,15 @@ pm_status launch_dgc_np(void *const *b, int Nel, int P, int A, cudaStream_t st) 
 }  // namespace
 
 DgcShape dgc_geometry(int Np, int A) {
+    if (!A && Np > 40 && Np <= 64) return DgcShape{3, 1, 2, 2};
     DgcShape s = dgc_shape0(Np);
     if (A) s.r = 1;
     return s;
 }
 
-int dgc_resolve_a(int Np, int A) { return A < 0 ? (Np > 20 ? 1 : 0) : A; }
+// the faster form per node count (timed on GB300): tensor memory for
+// 20 < Np <= 40 and Np > 64, shared memory (three m per CTA up to Np = 64)
+int dgc_resolve_a(int Np, int A) { return A < 0 ? (((Np > 20 && Np <= 40) || Np > 64) ? 1 : 0) : A; }
 
 int dgc_resolve_p(int Np, int64_t Nel, int A, int P) {
     if (P > 0) return P;

@@ -373,7 +373,7 @@ def test_tensor_core_closed_forms(kernel, R, n):
 
 
 @pytest.mark.parametrize("Np,Nel,P,A", [(20, 260, 0, 0), (35, 256, 2, 1), (84, 388, 0, 1), (10, 132, 3, 0),
-                                        (56, 128, 0, 0)])
+                                        (56, 128, 0, 0), (56, 260, 0, 1), (56, 516, 2, -1), (84, 132, 0, -1)])
 def test_dg_tc_closed_forms(Np, Nel, P, A):
     # the tensor-core DG: every u element reaches each m-group once (TMA box
     # element by element, uniform, when Np % 4 == 0, else per work-item),
@@ -383,7 +383,9 @@ def test_dg_tc_closed_forms(Np, Nel, P, A):
     # 3 Nel Np^2; each operator element is loaded once per work-group; all
     # work-items pass the same three work-group barriers
     fs = features("dg_tc", Np=Np, Nel=Nel, P=P, A=A)
-    MS = 3 if Np <= 40 else 1
+    if A < 0:
+        A = 1 if (20 < Np <= 40 or Np > 64) else 0
+    MS = 3 if (Np <= 40 or (A == 0 and Np <= 64)) else 1
     G, T, NP8, KS = 3 // MS, -(-Nel // 128), -(-Np // 8) * 8, -(-Np // 8)
     NR = -(-(MS * NP8) // 16) * 16
     R = 2 if (A == 0 and Np <= 20) else 1
