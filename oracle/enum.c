@@ -1366,11 +1366,14 @@ static int setup_dgt(ctx *c) {
  *    MS NP8 + tid;  one barrier;
  *  - per tile, Np % 4 == 0: work-item 256 copies element (r, cc) of the box
  *    at row 128 t, column 32 a for r < rows(t), 32 a + cc < Np;
+ *  - per tile, Np % 4 != 0 and A = 1: work-item 256 copies the tile's
+ *    rows(t) x Np elements of u (one bulk copy);
  *  - per tile, converter 128 <= tid < 256, r = tid - 128, atom a, chunk
  *    c < CN(a): Np % 4 == 0: a 16-byte local load of (r, c); else element
- *    loads u[128 t + r, 32 a + 4 c + x] for 128 t + r < Nel, 32 a + 4 c + x
- *    < Np; one statement of 4 adds with, for A = 0, two 16-byte local
- *    stores (r, c);
+ *    loads of u[128 t + r, 32 a + 4 c + x] (from the staged rows, local, for
+ *    A = 1; from global memory for A = 0) for 128 t + r < Nel,
+ *    32 a + 4 c + x < Np; one statement of 4 adds with, for A = 0, two
+ *    16-byte local stores (r, c);
  *  - per tile, work-item 288, atom a, k step kk < min(4, KS - 4a): 3 x 128 x
  *    NR x 8 TF32 multiply-adds;
  *  - per tile, epilogue tid < 128, per m-block mm: the row's Np / 4 16-byte
@@ -1407,6 +1410,12 @@ static long long ix_dc_ug(const ctx *c, const long long *g, const long long *l, 
     long long Np = DC_NP(c);
     return (128 * dc_tile(c, g, lv[0]) + (L0_ - 128)) * Np + 4 * lv[1] + lv[2];
 }
+static long long ix_dc_ubulk(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)l; return 128 * dc_tile(c, g, lv[0]) * DC_NP(c) + lv[1];
+}
+static long long ix_dc_R(const ctx *c, const long long *g, const long long *l, const long long *lv) {
+    (void)g; return (L0_ - 128) * DC_NP(c) + 4 * lv[1] + lv[2];
+}
 static long long ix_dc_U(const ctx *c, const long long *g, const long long *l, const long long *lv) {
     (void)g; (void)c; return (L0_ - 128) * 8 + lv[2];
 }
@@ -1419,7 +1428,8 @@ static long long ix_dc_res(const ctx *c, const long long *g, const long long *l,
 }
 /* statements: 0 D element load, 1 split + operator stores, 2 padding stores,
  * 3 u box element copy, 4 u element load, 5 staged-chunk load, 6 split (+
- * stores for A = 0), 7 MMA k step, 8 staging store, 9 res element copy */
+ * stores for A = 0), 7 MMA k step, 8 staging store, 9 res element copy,
+ * 10 u tile element copy (bulk), 11 staged-row element load */
 static void walk_dgc(ctx *c) {
     long long Np = DC_NP(c), Nel = c->P[1], P = c->D[0], MS = DC_MS(c), NP8 = DC_NP8(c), NR = DC_NR(c);
     long long KA = DC_KA(c), KS = DC_KS(c), T = cdiv(Nel, 128), tid = c->l[0], lv[3];
@@ -1438,6 +1448,8 @@ static void walk_dgc(ctx *c) {
     for (long long lt = 0; c->g[1] + P * lt < T; lt++) {
         const long long t = c->g[1] + P * lt, rows = Nel - 128 * t < 128 ? Nel - 128 * t : 128;
         lv[0] = lt;
+        if (tid == 256 && Np % 4 != 0 && c->D[2])
+            for (lv[1] = 0; lv[1] < rows * Np; lv[1]++) X(c, 10, lv);
         if (tid == 256 && Np % 4 == 0)
             for (long long a = 0; a < KA; a++)
                 for (long long r = 0; r < rows; r++) {
@@ -1455,7 +1467,7 @@ static void walk_dgc(ctx *c) {
                     } else {
                         lv[1] = 8 * a + ch;
                         for (lv[2] = 0; lv[2] < 4; lv[2]++)
-                            if (128 * t + r < Nel && 32 * a + 4 * ch + lv[2] < Np) X(c, 4, lv);
+                            if (128 * t + r < Nel && 32 * a + 4 * ch + lv[2] < Np) X(c, c->D[2] ? 11 : 4, lv);
                     }
                     lv[1] = a; lv[2] = ch;
                     X(c, 6, lv);
@@ -1483,6 +1495,7 @@ static int setup_dgc(ctx *c) {
     if (Nel < 4 || Nel % 4 || P < 0 || A < -1 || A > 1) return -1;
     if (A < 0) A = (Np > 20 && Np <= 40) || Np > 64;
     c->D[1] = (Np <= 40 || (A == 0 && Np <= 64)) ? 3 : 1;
+    c->D[2] = (A == 1 && Np % 4 != 0);   /* u tiles by one bulk copy each */
     const long long MS = DC_MS(c), G = 3 / MS, R = (A == 0 && Np <= 20) ? 2 : 1, T = cdiv(Nel, 128);
     if (P == 0) P = T < 152 * R / G ? T : 152 * R / G;
     c->D[0] = P;
@@ -1513,7 +1526,11 @@ static int setup_dgc(ctx *c) {
     stmt_site(c, s8, add_site(c, "dgc-O", MEM_LOCAL, DIR_STORE, tf ? "float32x4" : "float32", tf ? 16 : 4, ix_dc_O));
     int s9 = add_stmt(c, 3, DT_F32, 0, 0, 0);
     stmt_site(c, s9, add_site(c, "dgc-res", MEM_GLOBAL, DIR_STORE, "float32", 4, ix_dc_res));
-    (void)s0; (void)s3; (void)s4; (void)s5;
+    int s10 = add_stmt(c, 2, DT_F32, 0, 0, 0);
+    stmt_site(c, s10, add_site(c, "dgc-u", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dc_ubulk));
+    int s11 = add_stmt(c, 3, DT_F32, 0, 0, 0);
+    stmt_site(c, s11, add_site(c, "dgc-R", MEM_LOCAL, DIR_LOAD, "float32", 4, ix_dc_R));
+    (void)s0; (void)s3; (void)s4; (void)s5; (void)s10; (void)s11;
     c->walk = walk_dgc;
     return 0;
 }

@@ -643,8 +643,12 @@ pm_status counts_tc(const KP &kp, std::vector<pm_feature> &v) {
 //     Np % 4 == 0: thread 256 copies the in-range part of the 128 x 32 box
 //       (counted per element, uniform); converter thread r = tid - 128 loads
 //       chunk c of its row from the staged atom (16-byte shared load);
-//     else: converter thread r loads the row's four elements of chunk c from
-//       global memory (k = 128 t + r < Nel, j < Np);
+//     else, A = 1: thread 256 copies the tile's rows x Np elements (one bulk
+//       copy per tile, counted per element, uniform); converter thread r
+//       loads the row's four elements of chunk c from it (4-byte shared
+//       loads, k = 128 t + r < Nel, j < Np);
+//     else, A = 0: converter thread r loads the row's four elements of chunk
+//       c from global memory (k = 128 t + r < Nel, j < Np);
 //     converter: 4 adds per chunk; with A = 0 two 16-byte shared stores
 //       (head, remainder); with A = 1 the chunk goes to tensor memory;
 //     thread 288: per k step 3 MMAs of 128 x NR x 8 TF32 multiply-adds;
@@ -688,8 +692,12 @@ pm_status counts_dgc(const KP &kp, std::vector<pm_feature> &v) {
     o.op(0, 0, 4 * GP * (u64)(MS * NP8 * 8 * KA), 4 * GP * (u64)(MS * cdiv(NP8, 32) * 8 * KA));
     // u operand
     const u64 uel = (u64)(G * Nel) * uNp;
-    if (tma) site("dgc-u", GL, LD, "float32", 4, 0, 0, 128 * Np, uel, uel, (u64)(Nel * Np));
+    const bool bulk = !tma && A == 1;   // A = 1, Np % 4 != 0: one bulk copy of the tile's rows
+    if (tma || bulk) site("dgc-u", GL, LD, "float32", 4, 0, 0, 128 * Np, uel, uel, (u64)(Nel * Np));
     else site("dgc-u", GL, LD, "float32", 4, Np, 0, 128 * Np, uel, (u64)G * uNp * sum_sg_rows, (u64)(Nel * Np));
+    if (bulk)
+        site("dgc-R", LO, LD, "float32", 4, Np, 0, 0, uel, (u64)G * uNp * sum_sg_rows,
+             (u64)(std::min<i64>(128, Nel) * Np));
     const u64 cwi = GT * (u64)(2 * KS) * 128, csg = GT * (u64)(2 * KS) * 4;
     if (tma) site("dgc-Ur", LO, LD, "float32x4", 16, 8, 0, 0, cwi, csg, (u64)(128 * CN0));
     if (A == 0) {

@@ -30,8 +30,9 @@
 //       (tile, atom), 128-byte swizzle, zero fill beyond Np and Nel) into a
 //       ring of raw atoms; warp 8 also allocates and frees the TMEM;
 //   warps 4-7: converters -- thread r = element row r of the tile: its
-//       chunks of each atom (from the staged atom, or from global memory,
-//       guarded, when Np % 4 != 0) split into head and remainder;
+//       chunks of each atom (from the staged atom; when Np % 4 != 0 from
+//       the tile's rows staged by one bulk copy (A = 1) or from global
+//       memory (A = 0), guarded) split into head and remainder;
 //   warp 9 lane 0: MMA issuer -- per atom 3 MMAs per k step into one of two
 //       TMEM accumulators; commits free the operand stage and hand over the
 //       accumulator;
@@ -90,8 +91,11 @@ struct Dgc {
     static constexpr DgcShape S = (!TS && NP > 40 && NP <= 64) ? DgcShape{3, 1, 2, 2} : dgc_shape0(NP);
     static constexpr int MS = S.ms, G = 3 / S.ms;
     static constexpr int R = TS ? 1 : S.r;                          // CTAs per SM
-    static constexpr int ST = TS ? (NP % 4 == 0 ? 4 : 1) : S.st;    // shared-memory stages
-    static constexpr int SBYTES = TS ? ATOM : 2 * ATOM;             // bytes per shared-memory stage
+    // A = 1 with Np % 4 != 0: whole u tiles (row-major, one bulk copy each)
+    static constexpr bool BULK = TS && NP % 4 != 0;
+    static constexpr int RAWB = (128 * NP * 4 + 1023) / 1024 * 1024;
+    static constexpr int ST = TS ? (NP % 4 == 0 ? 4 : 2) : S.st;    // shared-memory stages
+    static constexpr int SBYTES = TS ? (BULK ? RAWB : ATOM) : 2 * ATOM;   // bytes per shared-memory stage
     static constexpr int OB = TS ? 2 : S.ob;
     static constexpr int NP8 = (NP + 7) / 8 * 8;
     static constexpr int NR = (MS * NP8 + 15) / 16 * 16;            // MMA N
@@ -101,7 +105,7 @@ struct Dgc {
     static constexpr int ACC = TS ? 128 : TCOLS / 2;                // column of accumulator 1
     static constexpr int BBYTES = KA * NR * 128;                    // one operator copy (head or remainder)
     static constexpr int OBYTES = 128 * NP * 4;
-    static constexpr int RING = (TS && NP % 4 != 0) ? 0 : ST * SBYTES;
+    static constexpr int RING = ST * SBYTES;
     static constexpr int BAR_OFF = RING + 2 * BBYTES + OB * OBYTES;
     static constexpr size_t NEED = (size_t)BAR_OFF + 256 + 1024;
     // A = 1 holds all 512 TMEM columns: at least 116 KB keeps it at one CTA per SM
@@ -178,6 +182,11 @@ __device__ __forceinline__ float4 lds4(uint32_t a) {
 __device__ __forceinline__ void sts4(uint32_t a, float4 v) {
     asm volatile("st.shared.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z), "f"(v.w) : "memory");
 }
+__device__ __forceinline__ float lds1(uint32_t a) {
+    float v;
+    asm volatile("ld.shared.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+    return v;
+}
 __device__ __forceinline__ void sts1(uint32_t a, float v) {
     asm volatile("st.shared.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
 }
@@ -222,6 +231,7 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
             float *__restrict__ res, int Nel) {
     using C = Dgc<NP, TS>;
     constexpr int MS = C::MS, ST = C::ST, OB = C::OB, NP8 = C::NP8, NR = C::NR, KA = C::KA, KS = C::KS;
+    constexpr bool BULK = C::BULK;
     extern __shared__ __align__(1024) unsigned char smem_raw[];
     const uint32_t sraw = smem_u32(smem_raw);
     const uint32_t sbase = (sraw + 1023u) & ~1023u;
@@ -290,7 +300,18 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
     const uint32_t tmem = S->tmem_base;
 
     if (warp == 8) {
-        if (TMA_U && lane == 0) {
+        if (BULK && lane == 0) {
+            // one bulk copy of the tile's rows (contiguous in u) per tile
+            int it = 0;
+            for (int t = p; t < T; t += P, it++) {
+                const int s = it % ST, r = it / ST;
+                if (r > 0 && !dgc_wait(&S->empty[s], (uint32_t)((r - 1) & 1))) break;
+                const uint32_t bytes = (uint32_t)min(128LL, (long long)Nel - 128LL * t) * NP * 4u;
+                mbar_expect_tx(&S->full[s], bytes);
+                bulk_load(gbase + s * C::SBYTES, u + 128LL * t * NP, bytes, &S->full[s]);
+                S->issued = it + 1;
+            }
+        } else if (TMA_U && lane == 0) {
             int it = 0;
             bool ok = true;
             for (int t = p; t < T && ok; t += P)
@@ -351,10 +372,15 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
     } else if (warp >= 4) {
         // converters: thread r = element row r of the tile (TMEM lane r)
         const int q = warp - 4, r = 32 * q + lane;
-        int it = 0;
-        for (int t = p; t < T; t += P) {
+        int it = 0, itile = 0;
+        for (int t = p; t < T; t += P, itile++) {
             bool ok = true;
             const long long k = 128LL * t + r;
+            const uint32_t raw = sbase + (uint32_t)((itile % ST) * C::SBYTES);   // BULK: the tile's rows
+            if (BULK) {
+                const bool got = dgc_wait(&S->full[itile % ST], (uint32_t)((itile / ST) & 1));
+                if (!__all_sync(0xffffffffu, got)) break;
+            }
 #pragma unroll
             for (int a = 0; a < KA; a++, it++) {
                 const int CN = 2 * min(4, KS - 4 * a);   // chunks of this atom the MMA reads
@@ -371,6 +397,14 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
                     float4 v;
                     if (TMA_U) {
                         v = lds4(hs + swz(r, c));
+                    } else if (BULK) {
+                        const int j0 = 32 * a + 4 * c;
+                        const uint32_t src = raw + (uint32_t)((r * NP + j0) * 4);
+                        const bool in = k < Nel;
+                        v.x = (in && j0 < NP) ? lds1(src) : 0.0f;
+                        v.y = (in && j0 + 1 < NP) ? lds1(src + 4) : 0.0f;
+                        v.z = (in && j0 + 2 < NP) ? lds1(src + 8) : 0.0f;
+                        v.w = (in && j0 + 3 < NP) ? lds1(src + 12) : 0.0f;
                     } else {
                         const int j0 = 32 * a + 4 * c;
                         const float *src = u + k * NP + j0;
@@ -415,6 +449,10 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
                     __syncwarp();
                     if (lane == 0) mbar_arrive(&S->ready[s]);
                 }
+            }
+            if (BULK) {
+                __syncwarp();
+                if (lane == 0) mbar_arrive(&S->empty[itile % ST]);   // the raw tile is consumed
             }
             if (!ok) break;
         }
@@ -469,7 +507,7 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
     }
     tc_before();
     __syncthreads();
-    if (TMA_U && threadIdx.x == 256 && *(volatile int *)&g_dgc_timeout) {
+    if ((TMA_U || BULK) && threadIdx.x == 256 && *(volatile int *)&g_dgc_timeout) {
         // drain: every stage's last issued copy lands before the shared memory goes away
         const int issued = S->issued;
         for (int s = 0; s < ST && s < issued; s++) {

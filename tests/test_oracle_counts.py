@@ -395,7 +395,13 @@ def test_dg_tc_closed_forms(Np, Nel, P, A):
     assert mm == G * T * KS * 3 * 128 * NR * 8 >= 3 * (3 * Nel * Np * Np)
     uu = by_tag(fs, "dgc-u")
     assert uu["count_wi"] == G * Nel * Np and uu["footprint"] == Nel * Np and uu["gstr"] == (0, 128 * Np)
-    assert uu["lstr"] == ((0,) if Np % 4 == 0 else (Np,))
+    # Np % 4 == 0: TMA boxes; else A = 1: one bulk copy per tile (both uniform);
+    # else per work-item loads from global memory
+    bulk = Np % 4 != 0 and A == 1
+    assert uu["lstr"] == ((0,) if (Np % 4 == 0 or bulk) else (Np,))
+    if bulk:
+        rr = by_tag(fs, "dgc-R")   # the converters' reads of the staged rows
+        assert rr["count_wi"] == G * Nel * Np and rr["lstr"] == (Np,) and rr["footprint"] == min(128, Nel) * Np
     r = by_tag(fs, "dgc-res")
     assert r["count_wi"] == r["count"] == r["footprint"] == 3 * Nel * Np and r["lstr"] == (0,)
     assert r["gstr"] == ((Nel * Np if MS == 1 else 0), 128 * Np)
