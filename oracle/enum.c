@@ -1353,7 +1353,7 @@ static int setup_dgt(ctx *c) {
  *   MS = 3 m per work-group for Np <= 40 and, with A = 0, for Np <= 64,
  *   else 1; G = 3 / MS m-groups; R = 2 work-groups per SM for A = 0 and
  *   Np <= 20, else 1; P = 0 means min(T, 152 R / G), T = ceil(Nel / 128);
- *   grid (G, P), work-group of 320 work-items (1-D).
+ *   grid (G, P), work-group of 320 work-items (1-D), 352 for A = 1.
  * NP8 = Np rounded up to 8, NR = MS NP8 rounded up to 16 (MMA N), KA =
  * ceil(Np / 32) atoms of 32 columns, KS = ceil(Np / 8) k steps, CN(a) =
  * 2 min(4, KS - 4a) chunks of atom a.  Work-group (g, p) serves tiles
@@ -1374,8 +1374,9 @@ static int setup_dgt(ctx *c) {
  *    A = 1; from global memory for A = 0) for 128 t + r < Nel,
  *    32 a + 4 c + x < Np; one statement of 4 adds with, for A = 0, two
  *    16-byte local stores (r, c);
- *  - per tile, work-item 288, atom a, k step kk < min(4, KS - 4a): 3 x 128 x
- *    NR x 8 TF32 multiply-adds;
+ *  - per tile, work-item 288 (A = 1: 288 for the work-group's even-numbered
+ *    tiles lt, 320 for the odd ones), atom a, k step kk < min(4, KS - 4a):
+ *    3 x 128 x NR x 8 TF32 multiply-adds;
  *  - per tile, epilogue tid < 128, per m-block mm: the row's Np / 4 16-byte
  *    local stores (Np % 4 == 0, else Np element stores), and work-item 0
  *    stores the rows(t) x Np elements of res[m, 128 t .., :] (m = mm when
@@ -1474,7 +1475,7 @@ static void walk_dgc(ctx *c) {
                 }
             }
         }
-        if (tid == 288)
+        if (tid == (c->D[3] && (lt & 1) ? 320 : 288))
             for (lv[1] = 0; lv[1] < KA; lv[1]++)
                 for (lv[2] = 0; lv[2] < 4 && 4 * lv[1] + lv[2] < KS; lv[2]++) X(c, 7, lv);
         if (tid < 128) {
@@ -1496,11 +1497,12 @@ static int setup_dgc(ctx *c) {
     if (A < 0) A = (Np > 20 && Np <= 40) || Np > 64;
     c->D[1] = (Np <= 40 || (A == 0 && Np <= 64)) ? 3 : 1;
     c->D[2] = (A == 1 && Np % 4 != 0);   /* u tiles by one bulk copy each */
+    c->D[3] = A;                          /* A = 1: two MMA work-items, alternate tiles */
     const long long MS = DC_MS(c), G = 3 / MS, R = (A == 0 && Np <= 20) ? 2 : 1, T = cdiv(Nel, 128);
     if (P == 0) P = T < 152 * R / G ? T : 152 * R / G;
     c->D[0] = P;
     c->grid[0] = G; c->grid[1] = P; c->grid[2] = 1;
-    c->wg[0] = 320; c->wg[1] = 1; c->wg[2] = 1;
+    c->wg[0] = A == 1 ? 352 : 320; c->wg[1] = 1; c->wg[2] = 1;
     const int tf = (Np % 4 == 0);
     int s0 = add_stmt(c, 3, DT_F32, 0, 0, 0);
     stmt_site(c, s0, add_site(c, "dgc-D", MEM_GLOBAL, DIR_LOAD, "float32", 4, ix_dc_D));

@@ -630,7 +630,7 @@ pm_status counts_tc(const KP &kp, std::vector<pm_feature> &v) {
 }
 
 // ---------------------------------------------------------------- DG on the tensor cores
-// Grid (G, P) of 320-thread work-groups (G = 3 / MS m-groups: MS = 3 m per
+// Grid (G, P) of 320-thread work-groups, 352 with A = 1 (G = 3 / MS m-groups: MS = 3 m per
 // work-group for Np <= 40, and for Np <= 64 with A = 0; P persistent
 // work-groups per m-group, the default resolved as the launch resolves it);
 // work-group (g, p) serves the tiles t = p, p + P, ... of 128 elements.
@@ -651,13 +651,14 @@ pm_status counts_tc(const KP &kp, std::vector<pm_feature> &v) {
 //       c from global memory (k = 128 t + r < Nel, j < Np);
 //     converter: 4 adds per chunk; with A = 0 two 16-byte shared stores
 //       (head, remainder); with A = 1 the chunk goes to tensor memory;
-//     thread 288: per k step 3 MMAs of 128 x NR x 8 TF32 multiply-adds;
+//     thread 288 (A = 1: 288 and 320 on alternate tiles): per k step 3 MMAs
+//       of 128 x NR x 8 TF32 multiply-adds;
 //   per tile, epilogue threads tid < 128, per m: the store of the thread's
 //   row to the staging buffer (Np / 4 16-byte stores, or Np 4-byte stores
 //   when Np % 4 != 0), and thread 0 copies the block's rows x Np elements to
 //   res (counted per element, uniform);
 //   two barriers at the end.  The epilogue warps' named barriers among
-//   themselves (128 of the 320 threads) are not work-group barriers and are
+//   themselves (128 of the threads) are not work-group barriers and are
 //   not counted: every thread passes the same three work-group barriers.
 // Shared-memory sites are given by their logical position (row, chunk) in
 // one ring stage or staging buffer: the swizzle permutes 16-byte chunks

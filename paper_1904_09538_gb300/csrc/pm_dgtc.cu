@@ -21,7 +21,7 @@
 // (NP8 = Np rounded up to 8, so each m's accumulator columns start on a
 // multiple of 8), zero for i >= Np and for the padding rows up to NR.
 //
-// Persistent CTAs of 320 threads on a grid (G, P), G = 3 / MS m-groups:
+// Persistent CTAs of 320 threads (352 with A = 1) on a grid (G, P), G = 3 / MS m-groups:
 // CTA (g, p) serves m-group g and the tiles t = p, p + P, ... (the G CTAs of
 // one p are adjacent in launch order, so a u tile comes from HBM once):
 //   all threads, once: stage Ds_h and Ds_l from D (thread i = operator row i
@@ -35,7 +35,11 @@
 //       memory (A = 0), guarded) split into head and remainder;
 //   warp 9 lane 0: MMA issuer -- per atom 3 MMAs per k step into one of two
 //       TMEM accumulators; commits free the operand stage and hand over the
-//       accumulator;
+//       accumulator.  With A = 1 warps 9 and 10 issue, each the tiles of one
+//       accumulator (alternate tiles): an MMA instruction leaves its thread
+//       only about when the tensor core takes it up, so every wait, commit and
+//       address step of a single issuer leaves the tensor pipe idle, and the
+//       second issuer's MMAs fill those gaps;
 //   warps 0-3: epilogue -- warp w reads TMEM lanes 32w.. (its 32 elements),
 //       writes each m's 128 x Np block row-major into one of OB staging
 //       buffers, and one thread stores it with one bulk copy (contiguous in
@@ -72,7 +76,6 @@ static __device__ int g_dgc_timeout;
 namespace {
 
 constexpr long long DGC_WAIT = 1ll << 26;
-constexpr int DGC_THREADS = 320;
 constexpr int ATOM = 128 * 128;   // 128 rows x 32 FP32 columns
 constexpr int SA = 4;             // TMEM operand stages (A = 1)
 constexpr int kGB300SMs = 152;    // default persistent grid: resident CTAs of one GB300
@@ -97,6 +100,16 @@ struct Dgc {
     static constexpr int ST = TS ? (NP % 4 == 0 ? 4 : 2) : S.st;    // shared-memory stages
     static constexpr int SBYTES = TS ? (BULK ? RAWB : ATOM) : 2 * ATOM;   // bytes per shared-memory stage
     static constexpr int OB = TS ? 2 : S.ob;
+    // MMA issuers: two in the tensor-memory form (alternate tiles).  Sound
+    // because an issuer's wait for atom x on operand slot x % SA always finds
+    // the slot's previous use (atom x - SA) converted: the converters work in
+    // atom order and the issuer has consumed atom x - 1 of its tile, or for a
+    // tile's first atom the last atom x - KA - 1 of its previous tile, both
+    // >= x - SA for KA <= 3.  The shared-memory form keeps one issuer: with as
+    // many stages as atoms per tile (ST = KA at Np = 56 and 84) a parity wait
+    // could not tell the awaited phase from the one two uses back.
+    static constexpr int NI = TS ? 2 : 1;
+    static constexpr int THREADS = 320 + 32 * (NI - 1);
     static constexpr int NP8 = (NP + 7) / 8 * 8;
     static constexpr int NR = (MS * NP8 + 15) / 16 * 16;            // MMA N
     static constexpr int KA = (NP + 31) / 32;
@@ -115,6 +128,7 @@ struct Dgc {
                                     | ((uint32_t)(NR >> 3) << 17)       // N
                                     | ((uint32_t)(128 >> 4) << 24);     // M = 128
     static_assert(NR >= 16 && NR <= 256 && NR % 16 == 0, "MMA N out of range");
+    static_assert(NI == 1 || KA + 1 <= SA, "two issuers need a free operand slot beyond a tile's atoms");
     static_assert(NR <= ACC, "accumulators overlap");
     static_assert(ST >= 1 && ST <= 4, "ring depth");
     static_assert(SMEM <= 227 * 1024, "shared memory");
@@ -226,7 +240,7 @@ __device__ __forceinline__ void bulk_wait_read() {
 __device__ __forceinline__ void bulk_wait_all() { asm volatile("cp.async.bulk.wait_group 0;" ::: "memory"); }
 
 template <int NP, bool TMA_U, bool TS>
-__global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
+__global__ void __launch_bounds__(Dgc<NP, TS>::THREADS, (Dgc<NP, TS>::R))
     k_dg_tc(const __grid_constant__ CUtensorMap tmU, const float *__restrict__ D, const float *__restrict__ u,
             float *__restrict__ res, int Nel) {
     using C = Dgc<NP, TS>;
@@ -253,7 +267,7 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
             mbar_init(&S->tfull[b], 1);
             mbar_init(&S->tempty[b], 4);
         }
-        mbar_init(&S->done, 1);
+        mbar_init(&S->done, C::NI);   // each issuer's last commit
         S->issued = 0;
         mbar_init_fence();
     }
@@ -324,12 +338,16 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
                 }
         }
         __syncwarp();
-    } else if (warp == 9) {
+    } else if (warp == 9 || warp == 10) {
         if (lane == 0) {
-            int it = 0, lt = 0;
+            // issuer ki serves the CTA's tiles lt = ki, ki + NI, ... (NI = 2:
+            // always accumulator ki)
+            const int ki = warp - 9;
+            int lt = ki;
             bool ok = true;
-            for (int t = p; t < T && ok; t += P, lt++) {
+            for (int t = p + ki * P; t < T && ok; t += C::NI * P, lt += C::NI) {
                 const int b = lt & 1, uu = lt >> 1;
+                int it = lt * KA;
                 if (uu > 0 && !dgc_wait(&S->tempty[b], (uint32_t)((uu - 1) & 1))) break;
                 tc_after();
                 const uint32_t d = tmem + (uint32_t)(b * C::ACC);
@@ -422,6 +440,11 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
                 }
                 if (TS) {
                     if (TMA_U) {
+                        // this lane's shared reads of the raw atom are ordered
+                        // before the TMA engine's next write into the stage
+                        // (async proxy): a release on the barrier alone orders
+                        // them only against generic accesses
+                        fence_async_smem();
                         __syncwarp();
                         if (lane == 0) mbar_arrive(&S->empty[s]);   // the raw atom is consumed
                     }
@@ -451,6 +474,7 @@ __global__ void __launch_bounds__(DGC_THREADS, (Dgc<NP, TS>::R))
                 }
             }
             if (BULK) {
+                fence_async_smem();   // the staged rows' reads before the next bulk copy into them
                 __syncwarp();
                 if (lane == 0) mbar_arrive(&S->empty[itile % ST]);   // the raw tile is consumed
             }
@@ -537,7 +561,7 @@ pm_status launch_dgc_t(void *const *b, int Nel, int P, cudaStream_t st) {
     }
     auto fn = k_dg_tc<NP, NP % 4 == 0, TS>;
     PM_CUDA_TRY(cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)C::SMEM));
-    launch_k(fn, dim3((unsigned)C::G, (unsigned)P), dim3(DGC_THREADS), C::SMEM, st, tm, (const float *)b[0],
+    launch_k(fn, dim3((unsigned)C::G, (unsigned)P), dim3(C::THREADS), C::SMEM, st, tm, (const float *)b[0],
              (const float *)b[1], (float *)b[2], Nel);
     PM_CUDA_TRY(cudaGetLastError());
     return PM_OK;
