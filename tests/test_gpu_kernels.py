@@ -435,6 +435,29 @@ def test_dg_tc_full_size_sampled_and_timed(Np, A):
     assert cond_err(got, ref, rabs) <= TOL and tm["mean_ms"] > 0
 
 
+@pytest.mark.parametrize("Np,launches", [(56, 40), (84, 16), (35, 16)])
+def test_dg_tc_tensor_memory_form_repeated_launches_every_output(Np, launches):
+    # the u operand in tensor memory, many persistent work-groups (one wave),
+    # every output of every launch against the oracle: the raw stages are
+    # reused from the third tile on, and a converter that frees a stage before
+    # its reads are ordered against the next copy corrupts rows of that tile
+    # now and then, so one launch is not enough
+    Nel = 1 << 18
+    D, u = pm_inputs.normal((3, Np, Np), 51), pm_inputs.normal((Nel, Np), 52)
+    ref, rabs = refs.dg(D, u)
+    d = dev()
+    ref_d = torch.from_numpy(ref).to(d)
+    inv_d = 1.0 / torch.from_numpy(np.maximum(rabs, 1e-300)).to(d)
+    bufs = [torch.from_numpy(D).to(d), torch.from_numpy(u).to(d), torch.empty(3 * Nel * Np, device=d)]
+    worst = 0.0
+    for _ in range(launches):
+        bufs[2].fill_(float("nan"))
+        pm.run("dg_tc", bufs, warmup=0, trials=1, Np=Np, Nel=Nel, A=1)
+        err = ((bufs[2].view(3, Nel, Np).double() - ref_d).abs() * inv_d).nan_to_num(nan=float("inf"))
+        worst = max(worst, float(err.max()))
+    assert worst <= TOL, worst
+
+
 def test_tma_kernel_resources_as_first_cuda_call():
     # a resource query of a TMA-staged kernel encodes a tensor map; as the
     # first CUDA call of a process (no context current yet) it must work too
