@@ -250,10 +250,11 @@ size_t dgt_smem(int Np) {
 }
 
 // NPC: Np fixed at compile time (the paper's sizes), 0 = taken from the
-// argument.  Five CTAs per SM for Np = 20 (68 registers; measured 7 % faster
+// argument.  Six CTAs per SM for Np = 20 (64 registers, no spills; measured
+// 4 % faster than five at 68 registers at 2^20 elements, which was 7 % faster
 // than the unconstrained 72)
 template <int NB, int NPC>
-__global__ void __launch_bounds__(NPC ? 16 * dgt_xl(NPC, NB) : 256, (NPC && NB <= 2) ? 5 : (NB <= 3 ? 3 : 2))
+__global__ void __launch_bounds__(NPC ? 16 * dgt_xl(NPC, NB) : 256, (NPC && NB <= 2) ? 6 : (NB <= 3 ? 3 : 2))
     k_dg_tile(const float *__restrict__ D, const float *__restrict__ u, float *__restrict__ res, int np_arg, int Nel) {
     constexpr int QBM = NB / 2 + 2;   // bound on ceil(Q / XL)
     const int Np = NPC ? NPC : np_arg;
