@@ -289,8 +289,8 @@ bool parse_strides(const std::string &body, std::vector<Cons> &out) {
 }
 
 bool is_dtype(const std::string &f) {
-    return f == "float32" || f == "float64" || f == "float32x4" || f == "float64x2" || f == "bfloat16" ||
-           f == "tfloat32";
+    return f == "float32" || f == "float64" || f == "float32x2" || f == "float32x4" || f == "float64x2" ||
+           f == "bfloat16" || f == "tfloat32";
 }
 
 pm_status parse_desc(const std::string &name, Desc &d) {

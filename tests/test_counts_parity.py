@@ -143,10 +143,14 @@ def test_feature_values_match_oracle():
             "p_madd * f_op_float32_madd + p_add * f_op_float32_add + p_mul * f_op_float32_mul + "
             "p_lmem * f_mem_access_local_float32 + "
             "p_g * f_mem_access_global_float32_lstrides:{0:1;1:>1}_gstrides:{0:16;1:>16}_afr:1 + "
-            "p_a * f_mem_access_tag:mm-PF-a + p_b * f_mem_access_global_float32_load_gstrides:{0:16}_afr:>1")
+            "p_a * f_mem_access_tag:mm-PF-a + p_b * f_mem_access_global_float32_load_gstrides:{0:16}_afr:>1 + "
+            "p_v2 * f_mem_access_local_float32x2 + p_v2l * f_mem_access_local_float32x2_load + "
+            "p_v4 * f_mem_access_local_float32x4 + p_du * f_mem_access_tag:dgt-u")
     m = pm.Model("f_wall_time", expr)
     for kernel, params in (("mm_pf", dict(n=48)), ("mm_nopf", dict(n=32)), ("fd_tile", dict(n=29)),
-                           ("dg_dmpf", dict(Np=35, Nel=64, L0=32, L1=8)), ("stream", dict(N=4096, shape=1, W=32))):
+                           ("dg_dmpf", dict(Np=35, Nel=64, L0=32, L1=8)), ("stream", dict(N=4096, shape=1, W=32)),
+                           ("dg_tile", dict(Np=20, Nel=300)), ("dg_tile", dict(Np=35, Nel=260)),
+                           ("mm_simt", dict(n=128, BM=64, BN=64, BK=32))):
         row = m.feature_values(kernel, **params)
         recs = ofeatures(kernel, **params)
         want = [ofeature_value(f, recs) for f in m.features]

@@ -44,14 +44,16 @@ def test_matmul_study_calibration_matches_oracle():
     assert math.isfinite(rep["geomean_rel_err"])
 
 
-def test_dg_tc_sweep_calibration_matches_oracle():
-    # the tensor-core DG study of the sweep at a reduced size set (the empty
-    # kernels and every other of its own sizes): the library's calibration
-    # and the oracle's refit of the same measured rows reach the same optimum
+@pytest.mark.parametrize("variant", ["dg_tc", "dg_tile"])
+def test_dg_tile_forms_sweep_calibration_matches_oracle(variant):
+    # the tensor-core DG and DG tile studies of the sweep (own models) at a
+    # reduced size set (the empty kernels and every other of their own
+    # sizes): the library's calibration and the oracle's refit of the same
+    # measured rows reach the same optimum
     if not torch.cuda.is_available():
         pytest.skip("no CUDA device")
-    st = [s for s in E.sweep_studies(reduced=True) if s["name"] == "sweep_dg_tc"][0]
-    rep = E.run_studies(trials=3, study_list=[st])["sweep_dg_tc"]
+    st = [s for s in E.sweep_studies(reduced=True) if s["name"] == "sweep_" + variant][0]
+    rep = E.run_studies(trials=3, study_list=[st])["sweep_" + variant]
     assert rep["fit"]["status"] in (0, -4), rep["fit"]
     m = pm.Model("f_wall_time", st["expr"])
     om = OModel("f_wall_time", st["expr"])
@@ -63,7 +65,7 @@ def test_dg_tc_sweep_calibration_matches_oracle():
     ssr_o = float(np.sum((1 - np.array(ofit.predict(om, po, F)) / t) ** 2))
     ssr_g = float(np.sum((1 - np.array([r["fitted_s"] for r in rows]) / t) ** 2))
     assert ssr_g <= ssr_o * (1 + 1e-4), (ssr_g, ssr_o)
-    assert math.isfinite(rep["geomean_rel_err"]) and rep["variants"]["dg_tc"]["n_sizes"] >= 4
+    assert math.isfinite(rep["geomean_rel_err"]) and rep["variants"][variant]["n_sizes"] >= 4
 
 
 def test_study_resumes_from_timing_cache(tmp_path):
