@@ -51,6 +51,28 @@ def partial(gmem_terms, overhead=OVERHEAD, onchip=ONCHIP):
     return "%s + %s + p_part * (%s)" % (overhead, hi, lo)
 
 
+ARITH = "p_madd * f_op_float32_madd + p_add * f_op_float32_add + p_mul * f_op_float32_mul"
+LOCAL = "p_lmem * f_mem_access_local_float32"
+
+
+def soft_max(a, b, edge):
+    """Eq. tanh's a s(a - b) + b s(b - a), s(x) = (tanh(edge x) + 1) / 2, written
+    as b + (a - b) s(a - b) (equal since s(x) + s(-x) = 1), which repeats a
+    and b fewer times in the model's program."""
+    return "(%s + (%s - %s) * (tanh(%s * (%s - %s)) + 1) / 2)" % (b, a, b, edge, a, b)
+
+
+def overlap2(gmem_terms, overhead=OVERHEAD, arith=ARITH, local=LOCAL):
+    """Eq. tanh between global-memory and on-chip work, the on-chip side
+    itself the same overlap of arithmetic and local memory (second switch
+    p_e2) instead of their sum: on GB300 the FMA pipe and the shared-memory
+    pipe issue side by side, so a kernel whose inner loop pairs every
+    multiply-add with local loads (the tiled matmuls) costs about the larger
+    of the two, not their sum."""
+    cg = "(%s)" % " + ".join(gmem_terms)
+    return "%s + %s" % (overhead, soft_max(cg, soft_max("(%s)" % arith, "(%s)" % local, "p_e2"), "p_edge"))
+
+
 def linear(gmem_terms, overhead=OVERHEAD, onchip=ONCHIP):
     return "%s + %s + %s" % (overhead, " + ".join(gmem_terms), onchip)
 
@@ -81,7 +103,7 @@ def studies(reduced=False):
                                                    ("mm-noPF-a", "npa"), ("mm-noPF-b", "npb"))]
     mm = dict(
         name="matmul", gmem=mm_gm,
-        expr=nonlinear(mm_gm),
+        expr=overlap2(mm_gm),
         measure=common_measurements() + [(k, {"n": n}) for k in ("mm_pf_a", "mm_pf_b", "mm_nopf_a", "mm_nopf_b")
                                          for n in mm_twin_sizes],
         modeled=[(k, {"n": n}) for k in ("mm_pf", "mm_nopf") for n in mm_sizes],
@@ -171,10 +193,12 @@ def sweep_studies(reduced=False):
     # matches; its u loads and res stores have equal counts (3 Nel Np each), so
     # one cost carries both, and its shared reads grow with its multiply-adds
     # (a fit with both gave the memory term a negative cost), so the
-    # multiply-adds carry the on-chip side; its own sizes calibrate them
-    dgt_expr = nonlinear(["p_dtm * (f_mem_access_tag:dgt-u + f_mem_access_tag:dgt-res)"],
-                         overhead="p_launch * f_sync_kernel_launch + p_group * f_thread_groups",
-                         onchip="p_madd * f_op_float32_madd")
+    # multiply-adds carry the on-chip side; its own sizes calibrate them.
+    # Linear: on these rows the tanh overlap's switch goes to zero (the
+    # linear model's optimum) or to a local optimum that depends on the path
+    dgt_expr = linear(["p_dtm * (f_mem_access_tag:dgt-u + f_mem_access_tag:dgt-res)"],
+                      overhead="p_launch * f_sync_kernel_launch + p_group * f_thread_groups",
+                      onchip="p_madd * f_op_float32_madd")
     plan = [("mm_pf", "matmul", None, [{"n": n} for n in range(512, 4096 + 1, 128)]),
             ("mm_tc", None, tc_expr, tc_sizes), ("mm_tc256", None, tc_expr, tc_sizes)]
     plan += [(k, "dg_16x16", None, dg_sizes) for k in ("dg_nopf", "dg_upf", "dg_dmpf", "dg_dmpft")]
