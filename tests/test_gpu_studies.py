@@ -44,6 +44,34 @@ def test_matmul_study_calibration_matches_oracle():
     assert math.isfinite(rep["geomean_rel_err"])
 
 
+def test_matmul_onchip_overlap_study_reaches_the_oracle_optimum():
+    # the extension model (on-chip side itself the tanh overlap of arithmetic
+    # and local memory) on the reduced matmul study's measurements: the
+    # library's calibration reaches the SSR of the oracle's refit of the same
+    # rows (its second switch, like p_edge, may end the fit at the iteration
+    # cap once the SSR stops moving)
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    mm = [s for s in E.studies() if s["name"] == "matmul_onchip_overlap"][0]
+    twins = [(k, p) for k, p in mm["measure"] if k.startswith("mm_") and p["n"] in (1024, 2048, 3072, 4096)]
+    common = [(k, p) for k, p in mm["measure"] if not k.startswith("mm_")]
+    st = dict(mm, name="mm_small_overlap2", measure=common + twins,
+              modeled=[(k, {"n": n}) for k in ("mm_pf", "mm_nopf") for n in (1536, 2560, 3584)])
+    rep = E.run_studies(trials=5, study_list=[st])["mm_small_overlap2"]
+    assert rep["fit"]["status"] in (0, -4), rep["fit"]
+    m = pm.Model("f_wall_time", st["expr"])
+    om = OModel("f_wall_time", st["expr"])
+    rows = rep["measure_rows"]
+    X = np.stack([m.feature_values(r["kernel"], **r["params"]) for r in rows])
+    t = np.array([r["measured_s"] for r in rows])
+    F = [dict(zip(om.features, x)) for x in X]
+    po, _ = ofit.fit(om, F, t)
+    ssr_o = float(np.sum((1 - np.array(ofit.predict(om, po, F)) / t) ** 2))
+    ssr_g = float(np.sum((1 - np.array([r["fitted_s"] for r in rows]) / t) ** 2))
+    assert ssr_g <= ssr_o * (1 + 1e-3), (ssr_g, ssr_o)
+    assert math.isfinite(rep["geomean_rel_err"])
+
+
 @pytest.mark.parametrize("variant", ["dg_tc", "dg_tile"])
 def test_dg_tile_forms_sweep_calibration_matches_oracle(variant):
     # the tensor-core DG and DG tile studies of the sweep (own models) at a
