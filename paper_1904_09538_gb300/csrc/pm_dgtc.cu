@@ -57,8 +57,8 @@
 //       converters.  TMEM: all 512 columns (accumulators at 0 and 128), one
 //       CTA per SM.
 // Every mbarrier wait is bounded: on expiry the kernel sets an error word,
-// the roles stop, the producer drains its copies in flight, the MMA issuer's
-// last commit is awaited (bounded) before the TMEM is freed.  The epilogue
+// the roles stop, the producer drains its copies in flight, the MMA issuers'
+// last commits are awaited (bounded) before the TMEM is freed.  The epilogue
 // warps agree on every accumulator hand-over through a reducing named
 // barrier, so none of them waits at a named barrier that the others left.
 #include <algorithm>
