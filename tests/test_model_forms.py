@@ -65,3 +65,16 @@ def test_every_study_model_fits_the_library_program():
         assert sorted(m.features) == sorted(om.features), st["name"]
     names = {st["name"] for st in sts}
     assert {"matmul", "matmul_onchip_overlap", "sweep_dg_tile", "sweep_dg_tc"} <= names
+
+
+def test_dg_tile_sweep_model_is_linear_in_its_parameters():
+    # both fit paths solve a model linear in p directly (one optimum), which
+    # the DG tile form's sweep model relies on
+    from oracle import fit as ofit
+    st = [s for s in E.sweep_studies(reduced=True) if s["name"] == "sweep_dg_tile"][0]
+    om = OModel("f_wall_time", st["expr"])
+    m = pm.Model("f_wall_time", st["expr"])
+    rows = [(k, p) for k, p in st["measure"]][:12]
+    F = [dict(zip(m.features, m.feature_values(k, **p))) for k, p in rows]
+    assert ofit.is_linear(om, F)
+    assert "f_mem_access_tag:dgt-u" in om.features and "f_op_float32_madd" in om.features
