@@ -800,16 +800,23 @@ def accuracy_leg(trials=3):
     sizes, predicting the sizes held out (L2 flushed before every trial) --
     and the model-guided autotuner at reduced sizes (24 SIMT matmul tiles at
     n = 3840, 12 stencil tiles at n = 8192): predicted against measured
-    order."""
+    order.  The prefetching matmul is also reported with the on-chip costs
+    themselves overlapped (mm_pf_onchip_overlap, the same measurements)."""
     from paper_1904_09538_gb300 import autotune as A
     from paper_1904_09538_gb300 import experiments as E
     t0 = time.perf_counter()
-    rep = E.run_studies(trials=trials, study_list=E.sweep_studies(reduced=True), flush_l2=True)
+    sweep = E.sweep_studies(reduced=True)
+    mm_gm = [s for s in E.studies() if s["name"] == "matmul"][0]["gmem"]
+    sweep.append(dict([s for s in sweep if s["name"] == "sweep_mm_pf"][0], name="sweep_mm_pf_onchip_overlap",
+                      expr=E.overlap2(mm_gm)))
+    rep = E.run_studies(trials=trials, study_list=sweep, flush_l2=True)
     by = {}
     for name, r in rep.items():
         if name == "sweep_tc_tiles":
             continue
         for v, e in r["variants"].items():
+            if name == "sweep_mm_pf_onchip_overlap":
+                v = "mm_pf_onchip_overlap"
             by[v] = {"geomean": round(e["geomean_rel_err"], 4), "max": round(e["max_rel_err"], 4),
                      "heldout": e["n_sizes"], "fit_status": r["fit"]["status"]}
     tcr = rep["sweep_tc_tiles"]
